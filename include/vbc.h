@@ -1,0 +1,194 @@
+/*
+ * vbc.h -- C ABI of libvbc.so: the valency-bounding correction (VBC) force and
+ * energy evaluation, its cell-list neighbour build and a Langevin integrator,
+ * all running as CUDA kernels on one GPU (sm_103a).
+ *
+ * The method (paper "Valency-bounding correction potential for coarse-grained
+ * molecular dynamics simulations", Sec. 2):
+ *   omega(x; x1, x2) = 1 (x <= x1), (1 - ((x - x1)/(x2 - x1))^2)^2, 0 (x >= x2)  Eq. (omega)
+ *   n_i   = sum_{j != i} omega(r_ij; r_l, r_h)                                 Eq. (counter)
+ *   Psi   = omega(n_i; f - delta, f - delta + 1) omega(n_j; f - delta, f - delta + 1)
+ *                                                                  Eqs. (Psi), (Psidelta)
+ *   V^    = V_r + Psi V_a,  U = sum_{i<j} V^(r_ij)                              Eq. (Vhat)
+ *   V_r   = E_r (1 - (r/r_r)^2)^2 for r < r_r;  V_a = -E_a (1 - u^2)^2 for
+ *           r_r < r < r_a, u = (r - (r_a + r_r)/2) / ((r_a - r_r)/2)             Eq. (softcore)
+ * Forces are -grad U including the chain-rule terms through dPsi/dn (the
+ * paper's two passes over the neighbour list, Sec. 2): with s_i the switch of
+ * particle i and A_i = s_i' sum_j s_j V_a(r_ij) = dU/dn_i,
+ *   F_i = -sum_j [V_r'(r) + s_i s_j V_a'(r) + (A_i + A_j) omega'(r)] (x_i - x_j)/r.
+ *
+ * Conventions for every call:
+ *   - Units are reduced: lengths in r_r (usually 1), energies as given, unit mass.
+ *   - Arrays of positions, velocities and forces are row-major [n][3] doubles
+ *     in the caller's particle order.  The library keeps its own copy of the
+ *     state in device memory it owns (sorted along a Morton curve internally)
+ *     and un-permutes every output.  Caller pointers are borrowed for the
+ *     duration of the call only.
+ *   - `*_on_device` flags say whether caller pointers are device (1) or host
+ *     (0) memory.  Host memory may be pageable or pinned.
+ *   - All work is enqueued on the system's stream (the one given at creation,
+ *     or a stream the library creates).  Calls return after the outputs the
+ *     caller asked for are written.
+ *   - Return value: VBC_OK (0) or a negative VBC_ERR_* code; no call aborts
+ *     the process.  vbc_last_error() gives a message for the calling thread.
+ */
+#ifndef VBC_H
+#define VBC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    VBC_OK = 0,
+    VBC_ERR_INVALID_ARG = -1,   /* bad size, parameter, pointer or box */
+    VBC_ERR_CUDA = -2,          /* a CUDA runtime call failed (message has the detail) */
+    VBC_ERR_OOM = -3,           /* device allocation failed */
+    VBC_ERR_NLIST_OVERFLOW = -4,/* neighbour list still overflows after growing to its limit */
+    VBC_ERR_UNSTABLE = -5       /* non-finite position or velocity produced */
+};
+
+/* Precision of the pair arithmetic. */
+enum {
+    VBC_FP32_SPLIT = 0, /* FP32 pair arithmetic on 32-bit fixed-point positions; exact
+                           integer squared distances and fixed-point sums for the counts;
+                           FP64 state (positions, velocities) and FP64 energy/virial */
+    VBC_FP64 = 1        /* FP64 pair arithmetic on 64-bit fixed-point positions */
+};
+
+/* VBC(r_l, r_h, delta) on the polynomial soft core (Sec. 2 and Sec. 4 "bond lifetimes").
+ * Requirements: 0 < r_r < r_a, 0 <= r_l < r_h, E_r >= 0, E_a >= 0.  The standard VBC
+ * is r_r = 1, r_a = r_l = 1.5, r_h = 2, delta = 0; the optimised one is
+ * r_l = 1.29, r_h = 1.50, delta = 0.30 (in units of r_r). */
+typedef struct {
+    double r_r, r_a, r_l, r_h;  /* repulsive range, attractive range, counting radii */
+    double E_r, E_a;            /* repulsive barrier height, attractive well depth */
+    double f, delta;            /* valency and threshold shift (f may be non-integer) */
+} vbc_pair_params;
+
+typedef struct {
+    int64_t n;                /* particles, 1 <= n <= 2^31 - 1 */
+    double box[3];            /* periodic orthorhombic box edges; VBC_FP32_SPLIT needs a cube.
+                                 Each edge must hold >= 3 cells of r_c + skin, where
+                                 r_c = max(r_r, r_a, r_h). */
+    const double* pos;        /* [n][3] initial positions (any image; unwrapped positions
+                                 are tracked from here on) */
+    const double* vel;        /* [n][3] initial velocities, or NULL for zeros */
+    vbc_pair_params params;
+    double skin;              /* Verlet skin; the list radius is r_c + skin (skin > 0) */
+    uint64_t seed;            /* key of the Langevin noise (Philox4x32-10) */
+    int32_t precision;        /* VBC_FP32_SPLIT or VBC_FP64 */
+    int32_t nlist_cap;        /* initial neighbour-list capacity per particle, 0 = automatic */
+    void* stream;             /* cudaStream_t to enqueue on, or NULL for a library-owned stream */
+    int32_t inputs_on_device; /* pos/vel are device pointers */
+} vbc_config;
+
+typedef struct vbc_system vbc_system;
+
+/* Diagnostics of the last evaluation / of the run so far. */
+typedef struct {
+    int64_t n;
+    int64_t step;              /* Langevin steps taken (the noise counter) */
+    int64_t rebuilds;          /* neighbour-list builds so far */
+    int32_t nlist_cap;         /* current capacity per particle */
+    int32_t nlist_max;         /* longest list at the last build */
+    double nlist_mean;         /* mean list length at the last build */
+    int64_t pairs_within_rc;   /* unordered pairs with r < r_c at the last energy evaluation */
+    int64_t in_window;         /* particles with f - delta < n_i < f - delta + 1 (last count pass) */
+} vbc_stats;
+
+/*
+ * Create a system: copy the configuration in, allocate device memory, build
+ * the neighbour list.  On success *out owns everything; release it with
+ * vbc_destroy.  Errors: INVALID_ARG (n < 1, non-positive box, box too small,
+ * non-cubic box with VBC_FP32_SPLIT, bad parameters, NULL pos/out), OOM, CUDA.
+ */
+int vbc_create_system(const vbc_config* cfg, vbc_system** out);
+
+/* Force a neighbour-list rebuild now (Morton sort of the particles, cell list,
+ * Verlet list of radius r_c + skin).  Rebuilds also happen automatically when a
+ * particle has moved more than skin/2 since the last build. */
+int vbc_build_neighbors(vbc_system* sys);
+
+/*
+ * One VBC force/energy evaluation at the current positions (Sec. 2: pass 1
+ * counts, chain-rule pass, pass 2 forces).  Every output is optional (NULL):
+ *   F      [n][3]  forces -grad U
+ *   counts [n]     smoothed neighbour counts n_i (Eq. counter)
+ *   energy [1]     U = sum_{i<j} V^(r_ij) (Eq. Vhat), accumulated in FP64
+ *   virial [1]     W = sum_{i<j} (x_i - x_j) . F_ij, accumulated in FP64
+ * outputs_on_device says whether the four pointers are device memory.
+ */
+int vbc_compute_forces(vbc_system* sys, double* F, double* counts, double* energy,
+                       double* virial, int outputs_on_device);
+
+/*
+ * Per-particle intermediates of the last vbc_compute_forces, for diagnostics:
+ * s [n] = omega(n_i; f - delta, f - delta + 1), ds [n] = ds/dn, A [n] = dU/dn_i.
+ * Any pointer may be NULL.
+ */
+int vbc_get_switch(vbc_system* sys, double* s, double* ds, double* A, int outputs_on_device);
+
+/*
+ * The Verlet list of the last build, in caller order, for diagnostics:
+ * nnb [n] list lengths (pairs within r_c + skin at build time), nbr [n][cap]
+ * neighbour indices (the first min(nnb[i], cap) entries of row i are written).
+ * Lists are complete (every pair closer than r_c + skin at the build) and
+ * hold no pair at or beyond that radius.
+ */
+int vbc_get_neighbors(vbc_system* sys, int32_t* nnb, int32_t* nbr, int32_t cap, int outputs_on_device);
+
+/*
+ * Advance nsteps Langevin steps (BAOAB splitting, unit mass): half kick, half
+ * drift, exact Ornstein-Uhlenbeck velocity update with c1 = exp(-gamma dt) and
+ * noise sqrt((1 - c1^2) kT) xi, half drift, force evaluation, half kick.  The
+ * three normals xi of particle id at step counter k come from
+ * Philox4x32-10 (counter (k lo, k hi, id, 0), key (seed lo, seed hi)) through
+ * Box-Muller on u = ((word >> 9) + 1/2) / 2^23.  Requires dt > 0, kT >= 0,
+ * gamma >= 0.  Errors: UNSTABLE if a position or velocity becomes
+ * non-finite (the state is then the one of the failing step).
+ */
+int vbc_step_langevin(vbc_system* sys, int64_t nsteps, double dt, double kT, double gamma);
+
+/* Checkpoint: copy out unwrapped positions, velocities and the step counter
+ * (any pointer may be NULL).  Restoring them with vbc_set_state resumes the
+ * same trajectory bit for bit. */
+int vbc_get_state(vbc_system* sys, double* pos, double* vel, int64_t* step, int on_device);
+int vbc_set_state(vbc_system* sys, const double* pos, const double* vel, int64_t step,
+                  int on_device);
+
+/* Change the pair parameters of an existing system (same cut-off or smaller:
+ * r_c + skin must still fit the cell grid built at creation). */
+int vbc_set_params(vbc_system* sys, const vbc_pair_params* params);
+
+int vbc_get_stats(vbc_system* sys, vbc_stats* out);
+
+/*
+ * Per-kernel timing with CUDA events on the system's stream.  enable != 0
+ * starts recording one event pair around every kernel launch (up to
+ * max_launches launches; further launches are not timed); enable == 0 stops.
+ * vbc_profile_read synchronises the stream and returns, for kernel class
+ * `which` (VBC_K_*), the summed device time in milliseconds and the number of
+ * timed launches.
+ */
+enum { VBC_K_REBUILD = 0, VBC_K_COUNT = 1, VBC_K_CHAIN = 2, VBC_K_FORCE = 3, VBC_K_ENERGY = 4,
+       VBC_K_NCLASSES = 5 };
+int vbc_profile(vbc_system* sys, int enable, int64_t max_launches);
+int vbc_profile_read(vbc_system* sys, int which, double* total_ms, int64_t* launches);
+
+/* Number of kernel launches the library has issued (all kinds) since creation. */
+int64_t vbc_kernel_launches(vbc_system* sys);
+
+/* Release everything the system owns.  NULL is accepted. */
+void vbc_destroy(vbc_system* sys);
+
+/* Message describing the last error of the calling thread ("" if none). */
+const char* vbc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VBC_H */

@@ -1,0 +1,850 @@
+// vbc_api.cu -- host runtime and C ABI of libvbc.so (declared in include/vbc.h).
+//
+// A vbc_system owns every device buffer of one particle system and enqueues
+// all work on one CUDA stream.  The host never waits for the device inside a
+// run of steps: neighbour-list rebuilds are decided on the device, and the
+// host reads the status words once, when the call ends.  If a rebuild found a
+// list longer than the capacity, every later kernel of the call stopped
+// without touching the state; the host then grows the list and resumes from
+// the iteration that stopped, so the trajectory is the same as with a large
+// enough list from the start.
+#include "vbc.h"
+#include "vbc_kernels.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace vbc;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define VBC_CUDA(call)                                                                           \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail(e_ == cudaErrorMemoryAllocation ? VBC_ERR_OOM : VBC_ERR_CUDA,            \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define VBC_TRY(expr)           \
+    do {                        \
+        int rc_ = (expr);       \
+        if (rc_ != VBC_OK) return rc_; \
+    } while (0)
+
+constexpr int MAX_CAP = 8192;   // longest neighbour list the library will grow to
+constexpr int MAX_RETRIES = 8;
+
+int blocks_for(int64_t n, int tpb) { return (int)((n + tpb - 1) / tpb); }
+
+}  // namespace
+
+struct vbc_system {
+    int64_t n = 0;
+    int prec = VBC_FP32_SPLIT;
+    double box[3] = {0, 0, 0};
+    vbc_pair_params prm{};
+    double skin = 0.0;
+    uint64_t seed = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+
+    Geom geom{};
+    Coef coef{};
+    double rcut = 0.0, rlist = 0.0;
+    unsigned long long rlist2_fix = 0;
+    int cap = 0;
+
+    // device buffers (particle arrays in sorted order)
+    double *x = nullptr, *v = nullptr, *xt = nullptr, *vt = nullptr;  // [3][n] each
+    int *id = nullptr, *idt = nullptr;
+    void *pos[2] = {nullptr, nullptr};
+    void *post = nullptr, *xref = nullptr;
+    int cur = 0;
+    int *nbr = nullptr, *nnb = nullptr;
+    int *cell_of = nullptr, *slot_of = nullptr, *order = nullptr;
+    int *cell_count = nullptr, *cell_start = nullptr, *morton_rank = nullptr, *chunk_sum = nullptr;
+    void *ds = nullptr, *sA = nullptr;
+    Status* st = nullptr;
+    Status* st_host = nullptr;  // pinned
+    double* partial = nullptr;
+    long long* ppairs = nullptr;
+    double* red = nullptr;       // [2] U, W
+    double* red_host = nullptr;  // pinned [2]
+    long long* win = nullptr;
+    int nblk_energy = 0;
+
+    int64_t step = 0;
+    int64_t launches = 0;
+
+    // per-kernel event timing
+    bool prof = false;
+    int64_t prof_max = 0;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_class;
+    int64_t ev_used = 0;
+
+    size_t pos_bytes() const { return prec == VBC_FP64 ? sizeof(P64) : sizeof(int4); }
+    size_t real_bytes() const { return prec == VBC_FP64 ? sizeof(double) : sizeof(float); }
+};
+
+namespace {
+
+// ------------------------------------------------------------------ timing helpers
+struct Timed {
+    vbc_system* s;
+    int cls;
+    int64_t slot = -1;
+    Timed(vbc_system* sys, int c) : s(sys), cls(c)
+    {
+        if (s->prof && s->ev_used < s->prof_max) {
+            slot = s->ev_used++;
+            cudaEventRecord(s->ev[2 * slot], s->stream);
+            s->ev_class[slot] = cls;
+        }
+    }
+    ~Timed()
+    {
+        if (slot >= 0) cudaEventRecord(s->ev[2 * slot + 1], s->stream);
+    }
+};
+
+int check_launch(vbc_system* s, int count = 1)
+{
+    s->launches += count;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(VBC_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    return VBC_OK;
+}
+
+__global__ void k_set_flag(Status* st, int which, int value)
+{
+    if (which == 0) st->rebuild = value;
+}
+
+__global__ void k_clear_halt(Status* st)
+{
+    st->overflow = 0;
+    st->frozen = 0;
+    st->crowded = 0;
+    st->rebuild = 1;
+}
+
+// ------------------------------------------------------------------ parameters
+int make_coef(const vbc_pair_params& p, const Geom& g, Coef& c)
+{
+    if (!(p.r_r > 0) || !(p.r_a > p.r_r) || !(p.r_l >= 0) || !(p.r_h > p.r_l) || !(p.E_r >= 0) ||
+        !(p.E_a >= 0) || !std::isfinite(p.f) || !std::isfinite(p.delta) || !std::isfinite(p.r_h) ||
+        !std::isfinite(p.r_a) || !std::isfinite(p.E_r) || !std::isfinite(p.E_a))
+        return fail(VBC_ERR_INVALID_ARG,
+                    "invalid pair parameters: need 0 < r_r < r_a, 0 <= r_l < r_h, E_r >= 0, E_a >= 0, "
+                    "finite f and delta");
+    c = Coef{};
+    c.r_r = p.r_r; c.r_a = p.r_a; c.r_l = p.r_l; c.r_h = p.r_h;
+    c.E_r = p.E_r; c.E_a = p.E_a; c.f = p.f; c.delta = p.delta;
+    c.rr2 = p.r_r * p.r_r;
+    c.ra2 = p.r_a * p.r_a;
+    c.rl2 = p.r_l * p.r_l;
+    c.rh2 = p.r_h * p.r_h;
+    const double rc = std::max(p.r_r, std::max(p.r_a, p.r_h));
+    c.rc2 = rc * rc;
+    c.rm = 0.5 * (p.r_a + p.r_r);
+    c.h = 0.5 * (p.r_a - p.r_r);
+    c.w = p.r_h - p.r_l;
+    c.fd = p.f - p.delta;
+    c.rr2f = (float)c.rr2; c.ra2f = (float)c.ra2; c.rl2f = (float)c.rl2; c.rh2f = (float)c.rh2;
+    c.rc2f = (float)c.rc2;
+    c.rlf = (float)p.r_l;
+    c.rmf = (float)c.rm;
+    c.hinvf = (float)(1.0 / c.h);
+    c.winvf = (float)(1.0 / c.w);
+    c.wf = (float)c.w;
+    c.Er4f = (float)(4.0 * p.E_r / c.rr2);
+    c.rr2invf = (float)(1.0 / c.rr2);
+    c.Eaf = (float)p.E_a;
+    c.Ea4hf = (float)(4.0 * p.E_a / c.h);
+    const double s2 = g.s32d[0] * g.s32d[0];
+    c.rl2_fix = (unsigned long long)std::llround(c.rl2 / s2);
+    c.rh2_fix = (unsigned long long)std::llround(c.rh2 / s2);
+    // threshold f - delta in 2^-31 fixed point, clamped far outside any reachable count
+    const double fd = std::min(std::max(c.fd, -1.0e9), 1.0e9);
+    double fi = std::floor(fd);
+    long long frac = std::llround((fd - fi) * 2147483648.0);
+    if (frac >= 2147483648LL) {
+        fi += 1.0;
+        frac -= 2147483648LL;
+    }
+    c.fd_int = (long long)fi;
+    c.fd_frac_fix = frac;
+    return VBC_OK;
+}
+
+uint32_t spread3(uint32_t v)  // 10 bits -> every third bit
+{
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+// ------------------------------------------------------------------ allocation
+template <class T>
+int dalloc(T*& p, size_t count)
+{
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess)
+        return fail(e == cudaErrorMemoryAllocation ? VBC_ERR_OOM : VBC_ERR_CUDA, "cudaMalloc(%zu B): %s",
+                    count * sizeof(T), cudaGetErrorString(e));
+    p = (T*)q;
+    return VBC_OK;
+}
+
+int dalloc_bytes(void*& p, size_t bytes)
+{
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 1));
+    if (e != cudaSuccess)
+        return fail(e == cudaErrorMemoryAllocation ? VBC_ERR_OOM : VBC_ERR_CUDA, "cudaMalloc(%zu B): %s", bytes,
+                    cudaGetErrorString(e));
+    return VBC_OK;
+}
+
+void free_all(vbc_system* s)
+{
+    void* bufs[] = {s->x, s->v, s->xt, s->vt, s->id, s->idt, s->pos[0], s->pos[1], s->post, s->xref,
+                    s->nbr, s->nnb, s->cell_of, s->slot_of, s->order, s->cell_count, s->cell_start,
+                    s->morton_rank, s->chunk_sum, s->ds, s->sA, s->st, s->partial, s->ppairs, s->red, s->win};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (s->st_host) cudaFreeHost(s->st_host);
+    if (s->red_host) cudaFreeHost(s->red_host);
+    for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
+    s->ev.clear();
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+}
+
+// ------------------------------------------------------------------ launches
+template <class M>
+int enqueue_rebuild(vbc_system* s, int iter)
+{
+    using pos_t = typename M::pos_t;
+    Timed t(s, VBC_K_REBUILD);
+    const int n = (int)s->n;
+    const int nb = blocks_for(n, TPB);
+    pos_t* pos = (pos_t*)s->pos[s->cur];
+    k_bin<M><<<nb, TPB, 0, s->stream>>>(pos, n, s->geom, s->morton_rank, s->cell_of, s->slot_of, s->cell_count,
+                                        s->st);
+    const int nchunk = blocks_for(s->geom.ncell, SCAN_CHUNK);
+    k_scan_sums<<<nchunk, SCAN_TPB, 0, s->stream>>>(s->cell_count, s->geom.ncell, s->chunk_sum, s->st);
+    k_scan_apply<<<nchunk, SCAN_TPB, 0, s->stream>>>(s->cell_count, s->geom.ncell, s->chunk_sum, s->cell_start,
+                                                      s->st);
+    k_scatter<<<nb, TPB, 0, s->stream>>>(n, s->cell_of, s->slot_of, s->cell_start, s->order, s->st);
+    k_cellsort<<<blocks_for(s->geom.ncell, TPB), TPB, 0, s->stream>>>(s->geom.ncell, s->cell_start, s->id,
+                                                                       s->order, s->st);
+    k_permute<M><<<nb, TPB, 0, s->stream>>>(n, s->order, s->x, s->v, s->id, pos, s->xt, s->vt, s->idt,
+                                            (pos_t*)s->post, s->st);
+    k_copyback<M><<<nb, TPB, 0, s->stream>>>(n, s->xt, s->vt, s->idt, (const pos_t*)s->post, s->x, s->v, s->id,
+                                             pos, (pos_t*)s->xref, s->st);
+    k_nlist<M><<<nb, TPB, 0, s->stream>>>(n, s->geom, pos, s->morton_rank, s->cell_start, s->rlist2_fix,
+                                          s->rlist * s->rlist, s->cap, s->nbr, s->nnb, s->st, iter);
+    return check_launch(s, 8);
+}
+
+template <class M>
+int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window)
+{
+    using pos_t = typename M::pos_t;
+    using real = typename M::real;
+    using real2 = typename M::real2;
+    const int n = (int)s->n;
+    const int nb = blocks_for(n, TPB);
+    const pos_t* pos = (const pos_t*)s->pos[s->cur];
+    CountOut out{n_out, want_window ? s->win : nullptr};
+    {
+        Timed t(s, VBC_K_COUNT);
+        k_count<M><<<nb, TPB, 0, s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb, s->id, (real*)s->ds,
+                                              (real2*)s->sA, out, s->st);
+    }
+    {
+        Timed t(s, VBC_K_CHAIN);
+        k_chain<M><<<nb, TPB, 0, s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb, (const real*)s->ds,
+                                              (real2*)s->sA, s->st);
+    }
+    return check_launch(s, 2);
+}
+
+template <class M, int EPI>
+int enqueue_force(vbc_system* s, const StepArgs& a)
+{
+    using pos_t = typename M::pos_t;
+    using real2 = typename M::real2;
+    const int n = (int)s->n;
+    const pos_t* pos = (const pos_t*)s->pos[s->cur];
+    pos_t* pos_next = (pos_t*)s->pos[s->cur ^ 1];
+    {
+        Timed t(s, VBC_K_FORCE);
+        k_force<M, EPI><<<blocks_for(n, TPB), TPB, 0, s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb, s->id,
+                                                                  (const real2*)s->sA, pos_next,
+                                                                  (const pos_t*)s->xref, a, s->st);
+    }
+    VBC_TRY(check_launch(s));
+    if (EPI == EPI_START || EPI == EPI_FINISH_START) s->cur ^= 1;
+    return VBC_OK;
+}
+
+template <class M>
+int enqueue_energy(vbc_system* s)
+{
+    using pos_t = typename M::pos_t;
+    using real2 = typename M::real2;
+    const int n = (int)s->n;
+    {
+        Timed t(s, VBC_K_ENERGY);
+        k_energy<M><<<s->nblk_energy, RED_TPB, 0, s->stream>>>(n, s->geom, s->coef, (const pos_t*)s->pos[s->cur],
+                                                                s->nbr, s->nnb, (const real2*)s->sA, s->partial,
+                                                                s->ppairs, s->st);
+        k_reduce_final<<<1, RED_TPB, 0, s->stream>>>(s->nblk_energy, s->partial, s->ppairs, s->red, s->st);
+    }
+    return check_launch(s, 2);
+}
+
+int force_rebuild_flag(vbc_system* s)
+{
+    k_set_flag<<<1, 1, 0, s->stream>>>(s->st, 0, 1);
+    return check_launch(s);
+}
+
+int read_status(vbc_system* s)
+{
+    VBC_CUDA(cudaMemcpyAsync(s->st_host, s->st, sizeof(Status), cudaMemcpyDeviceToHost, s->stream));
+    VBC_CUDA(cudaStreamSynchronize(s->stream));
+    return VBC_OK;
+}
+
+// Grow the list after an overflow; the caller resumes the interrupted work.
+int grow_list(vbc_system* s)
+{
+    const int need = s->st_host->max_nnb;
+    if (need > MAX_CAP)
+        return fail(VBC_ERR_NLIST_OVERFLOW, "a particle has %d neighbours within r_c + skin, above the limit %d",
+                    need, MAX_CAP);
+    int cap = std::max(s->cap * 2, need + need / 4 + 8);
+    cap = std::min(cap, MAX_CAP);
+    cap = (cap + 7) & ~7;
+    VBC_CUDA(cudaStreamSynchronize(s->stream));
+    VBC_CUDA(cudaFree(s->nbr));
+    s->nbr = nullptr;
+    VBC_TRY(dalloc(s->nbr, (size_t)cap * (size_t)s->n));
+    s->cap = cap;
+    k_clear_halt<<<1, 1, 0, s->stream>>>(s->st);
+    return check_launch(s);
+}
+
+int halt_error(vbc_system* s)
+{
+    if (s->st_host->crowded)
+        return fail(VBC_ERR_UNSTABLE, "more than %d particles in one cell: the system has collapsed or blown up",
+                    MAX_CELL);
+    if (s->st_host->frozen) return fail(VBC_ERR_UNSTABLE, "a position or velocity became non-finite");
+    return VBC_OK;
+}
+
+// One force evaluation with optional outputs (device pointers or null).
+template <class M>
+int compute_impl(vbc_system* s, double* F_dev, double* n_dev, bool energy)
+{
+    for (int attempt = 0;; ++attempt) {
+        VBC_CUDA(cudaMemsetAsync(s->win, 0, sizeof(long long), s->stream));
+        VBC_TRY(enqueue_rebuild<M>(s, 0));
+        VBC_TRY(enqueue_count_chain<M>(s, n_dev, true));
+        StepArgs a{};
+        a.F_out = F_dev;
+        VBC_TRY((enqueue_force<M, EPI_FORCE>(s, a)));
+        if (energy) VBC_TRY(enqueue_energy<M>(s));
+        VBC_TRY(read_status(s));
+        VBC_TRY(halt_error(s));
+        if (!s->st_host->overflow) break;
+        if (attempt >= MAX_RETRIES) return fail(VBC_ERR_NLIST_OVERFLOW, "neighbour list kept overflowing");
+        VBC_TRY(grow_list(s));
+    }
+    return VBC_OK;
+}
+
+template <class M>
+int steps_impl(vbc_system* s, int64_t nsteps, double dt, double kT, double gamma)
+{
+    StepArgs a{};
+    a.x = s->x;
+    a.v = s->v;
+    a.dt = dt;
+    a.c1 = std::exp(-gamma * dt);
+    a.c2 = std::sqrt(std::max(0.0, (1.0 - a.c1 * a.c1) * kT));
+    a.seed = s->seed;
+    a.half_skin2 = (float)(0.25 * s->skin * s->skin);
+    int64_t it0 = 0;  // iteration to (re)start from; 0 = the opening half step
+    for (int attempt = 0;; ++attempt) {
+        for (int64_t it = it0; it <= nsteps; ++it) {
+            VBC_TRY(enqueue_rebuild<M>(s, (int)std::min<int64_t>(it, 0x7fffffff)));
+            VBC_TRY(enqueue_count_chain<M>(s, nullptr, false));
+            a.step = s->step + it;
+            if (it == 0) {
+                VBC_TRY((enqueue_force<M, EPI_START>(s, a)));
+            } else if (it < nsteps) {
+                VBC_TRY((enqueue_force<M, EPI_FINISH_START>(s, a)));
+            } else {
+                VBC_TRY((enqueue_force<M, EPI_FINISH>(s, a)));
+            }
+        }
+        VBC_TRY(read_status(s));
+        VBC_TRY(halt_error(s));
+        if (!s->st_host->overflow) break;
+        if (attempt >= MAX_RETRIES) return fail(VBC_ERR_NLIST_OVERFLOW, "neighbour list kept overflowing");
+        // The build of iteration frozen_iter overflowed: every kernel after it
+        // returned at once.  The position buffer flips only on START
+        // epilogues that ran, so recompute which one is current.
+        it0 = s->st_host->frozen_iter;
+        const int64_t flips_enqueued = nsteps;        // iterations 0..nsteps-1 flip
+        const int64_t flips_done = it0;               // iterations 0..it0-1 ran
+        if ((flips_enqueued - flips_done) & 1) s->cur ^= 1;
+        VBC_TRY(grow_list(s));
+    }
+    s->step += nsteps;
+    return VBC_OK;
+}
+
+int check_sys(vbc_system* s)
+{
+    if (!s) return fail(VBC_ERR_INVALID_ARG, "system handle is NULL");
+    cudaError_t e = cudaSetDevice(s->device);
+    if (e != cudaSuccess) return fail(VBC_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    return VBC_OK;
+}
+
+// Copies n*per doubles from caller memory (host or device) into device buffer dst.
+int stage_in(vbc_system* s, double* dst, const double* src, size_t count, int on_device)
+{
+    VBC_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(double),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->stream));
+    return VBC_OK;
+}
+
+template <class M>
+int load_state(vbc_system* s, const double* pos, const double* vel, int on_device)
+{
+    // caller arrays -> staging (xt holds positions, vt velocities) -> sorted SoA
+    VBC_TRY(stage_in(s, s->xt, pos, 3 * (size_t)s->n, on_device));
+    if (vel) VBC_TRY(stage_in(s, s->vt, vel, 3 * (size_t)s->n, on_device));
+    k_load_state<M><<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>((int)s->n, s->geom, s->xt, vel ? s->vt : nullptr,
+                                                                  s->id, s->x, s->v,
+                                                                  (typename M::pos_t*)s->pos[s->cur]);
+    VBC_TRY(check_launch(s));
+    k_clear_halt<<<1, 1, 0, s->stream>>>(s->st);  // also requests a rebuild
+    return check_launch(s);
+}
+
+template <class M>
+int build_now(vbc_system* s)
+{
+    for (int attempt = 0;; ++attempt) {
+        VBC_TRY(force_rebuild_flag(s));
+        VBC_TRY(enqueue_rebuild<M>(s, 0));
+        VBC_TRY(read_status(s));
+        VBC_TRY(halt_error(s));
+        if (!s->st_host->overflow) return VBC_OK;
+        if (attempt >= MAX_RETRIES) return fail(VBC_ERR_NLIST_OVERFLOW, "neighbour list kept overflowing");
+        VBC_TRY(grow_list(s));
+    }
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+const char* vbc_last_error(void) { return g_err.c_str(); }
+
+int vbc_create_system(const vbc_config* cfg, vbc_system** out)
+{
+    g_err.clear();
+    if (!cfg || !out) return fail(VBC_ERR_INVALID_ARG, "cfg and out must not be NULL");
+    *out = nullptr;
+    if (cfg->n < 1 || cfg->n > 0x7fffffffLL) return fail(VBC_ERR_INVALID_ARG, "n must be in [1, 2^31 - 1]");
+    if (!cfg->pos) return fail(VBC_ERR_INVALID_ARG, "pos must not be NULL");
+    if (cfg->precision != VBC_FP32_SPLIT && cfg->precision != VBC_FP64)
+        return fail(VBC_ERR_INVALID_ARG, "precision must be VBC_FP32_SPLIT or VBC_FP64");
+    if (!(cfg->skin > 0) || !std::isfinite(cfg->skin)) return fail(VBC_ERR_INVALID_ARG, "skin must be > 0");
+    for (int a = 0; a < 3; ++a)
+        if (!(cfg->box[a] > 0) || !std::isfinite(cfg->box[a]))
+            return fail(VBC_ERR_INVALID_ARG, "box edges must be positive and finite");
+    if (cfg->precision == VBC_FP32_SPLIT && !(cfg->box[0] == cfg->box[1] && cfg->box[1] == cfg->box[2]))
+        return fail(VBC_ERR_INVALID_ARG, "VBC_FP32_SPLIT needs a cubic box (use VBC_FP64 otherwise)");
+    if (cfg->nlist_cap < 0) return fail(VBC_ERR_INVALID_ARG, "nlist_cap must be >= 0");
+
+    vbc_system* s = new vbc_system();
+    s->n = cfg->n;
+    s->prec = cfg->precision;
+    s->prm = cfg->params;
+    s->skin = cfg->skin;
+    s->seed = cfg->seed;
+    for (int a = 0; a < 3; ++a) s->box[a] = cfg->box[a];
+
+    auto bail = [&](int rc) {
+        free_all(s);
+        delete s;
+        return rc;
+    };
+
+    // geometry and cell grid
+    Geom& g = s->geom;
+    s->rcut = std::max(s->prm.r_r, std::max(s->prm.r_a, s->prm.r_h));
+    s->rlist = s->rcut + s->skin;
+    for (int a = 0; a < 3; ++a) {
+        g.L[a] = s->box[a];
+        g.inv32[a] = 4294967296.0 / s->box[a];
+        g.s32d[a] = s->box[a] / 4294967296.0;
+        g.s64[a] = s->box[a] / 18446744073709551616.0;
+        const double ncd = std::floor(s->box[a] / s->rlist);
+        if (!(ncd >= 3.0))
+            return bail(fail(VBC_ERR_INVALID_ARG,
+                             "box edge %g holds fewer than 3 cells of r_c + skin = %g", s->box[a], s->rlist));
+        g.nc[a] = (int)std::min(ncd, 1024.0);
+    }
+    if ((double)g.nc[0] * g.nc[1] * g.nc[2] > 2.0e9) return bail(fail(VBC_ERR_INVALID_ARG, "cell grid too large"));
+    g.ncell = g.nc[0] * g.nc[1] * g.nc[2];
+    g.s32 = (float)g.s32d[0];
+    g.s32sq = (float)(g.s32d[0] * g.s32d[0]);
+    {
+        int rc = make_coef(s->prm, g, s->coef);
+        if (rc) return bail(rc);
+    }
+    s->rlist2_fix = (unsigned long long)std::llround(s->rlist * s->rlist / (g.s32d[0] * g.s32d[0]));
+
+    // initial list capacity from the mean density
+    const double rho = (double)s->n / (s->box[0] * s->box[1] * s->box[2]);
+    const double kbar = rho * 4.18879020478639098 * s->rlist * s->rlist * s->rlist;  // 4 pi / 3
+    int cap = cfg->nlist_cap > 0 ? cfg->nlist_cap : (int)std::ceil(1.5 * kbar + 8.0 * std::sqrt(kbar) + 16.0);
+    cap = std::min(std::max(cap, 1), MAX_CAP);
+    s->cap = cap;
+
+    {
+        cudaError_t e = cudaGetDevice(&s->device);
+        if (e != cudaSuccess) return bail(fail(VBC_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e)));
+    }
+    if (cfg->stream) {
+        s->stream = (cudaStream_t)cfg->stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(fail(VBC_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)));
+        s->own_stream = true;
+    }
+
+    const size_t n = (size_t)s->n;
+    int rc = VBC_OK;
+#define ALLOC(expr) \
+    if ((rc = (expr)) != VBC_OK) return bail(rc)
+    ALLOC(dalloc(s->x, 3 * n));
+    ALLOC(dalloc(s->v, 3 * n));
+    ALLOC(dalloc(s->xt, 3 * n));
+    ALLOC(dalloc(s->vt, 3 * n));
+    ALLOC(dalloc(s->id, n));
+    ALLOC(dalloc(s->idt, n));
+    ALLOC(dalloc_bytes(s->pos[0], n * s->pos_bytes()));
+    ALLOC(dalloc_bytes(s->pos[1], n * s->pos_bytes()));
+    ALLOC(dalloc_bytes(s->post, n * s->pos_bytes()));
+    ALLOC(dalloc_bytes(s->xref, n * s->pos_bytes()));
+    ALLOC(dalloc(s->nbr, (size_t)cap * n));
+    ALLOC(dalloc(s->nnb, n));
+    ALLOC(dalloc(s->cell_of, n));
+    ALLOC(dalloc(s->slot_of, n));
+    ALLOC(dalloc(s->order, n));
+    ALLOC(dalloc(s->cell_count, (size_t)g.ncell));
+    ALLOC(dalloc(s->cell_start, (size_t)g.ncell + 1));
+    ALLOC(dalloc(s->morton_rank, (size_t)g.ncell));
+    ALLOC(dalloc(s->chunk_sum, (size_t)blocks_for(g.ncell, SCAN_CHUNK)));
+    ALLOC(dalloc_bytes(s->ds, n * s->real_bytes()));
+    ALLOC(dalloc_bytes(s->sA, n * 2 * s->real_bytes()));
+    ALLOC(dalloc(s->st, 1));
+    s->nblk_energy = blocks_for(s->n, RED_TPB);
+    ALLOC(dalloc(s->partial, 2 * (size_t)s->nblk_energy));
+    ALLOC(dalloc(s->ppairs, (size_t)s->nblk_energy));
+    ALLOC(dalloc(s->red, 2));
+    ALLOC(dalloc(s->win, 1));
+#undef ALLOC
+    if (cudaMallocHost((void**)&s->st_host, sizeof(Status)) != cudaSuccess ||
+        cudaMallocHost((void**)&s->red_host, 2 * sizeof(double)) != cudaSuccess)
+        return bail(fail(VBC_ERR_OOM, "pinned host allocation failed"));
+
+    // Morton order of the cells: rank of each linear cell index along the curve
+    {
+        std::vector<std::pair<uint32_t, int>> code((size_t)g.ncell);
+        for (int z = 0; z < g.nc[2]; ++z)
+            for (int y = 0; y < g.nc[1]; ++y)
+                for (int x = 0; x < g.nc[0]; ++x) {
+                    const int lin = (z * g.nc[1] + y) * g.nc[0] + x;
+                    code[lin] = {spread3((uint32_t)x) | (spread3((uint32_t)y) << 1) | (spread3((uint32_t)z) << 2), lin};
+                }
+        std::sort(code.begin(), code.end());
+        std::vector<int> rank((size_t)g.ncell);
+        for (int r = 0; r < g.ncell; ++r) rank[code[r].second] = r;
+        if (cudaMemcpy(s->morton_rank, rank.data(), rank.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(fail(VBC_ERR_CUDA, "upload of the Morton table failed"));
+    }
+    if (cudaMemsetAsync(s->cell_count, 0, (size_t)g.ncell * sizeof(int), s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->st, 0, sizeof(Status), s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->nnb, 0, n * sizeof(int), s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->sA, 0, n * 2 * s->real_bytes(), s->stream) != cudaSuccess)
+        return bail(fail(VBC_ERR_CUDA, "initial memset failed"));
+    k_iota<<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>((int)s->n, s->id);
+    if ((rc = check_launch(s)) != VBC_OK) return bail(rc);
+    if (s->prec == VBC_FP64) {
+        if ((rc = load_state<ModeF64>(s, cfg->pos, cfg->vel, cfg->inputs_on_device)) != VBC_OK) return bail(rc);
+        if ((rc = build_now<ModeF64>(s)) != VBC_OK) return bail(rc);
+    } else {
+        if ((rc = load_state<ModeF32>(s, cfg->pos, cfg->vel, cfg->inputs_on_device)) != VBC_OK) return bail(rc);
+        if ((rc = build_now<ModeF32>(s)) != VBC_OK) return bail(rc);
+    }
+    *out = s;
+    return VBC_OK;
+}
+
+void vbc_destroy(vbc_system* s)
+{
+    if (!s) return;
+    cudaSetDevice(s->device);
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    free_all(s);
+    delete s;
+}
+
+int vbc_build_neighbors(vbc_system* s)
+{
+    VBC_TRY(check_sys(s));
+    return s->prec == VBC_FP64 ? build_now<ModeF64>(s) : build_now<ModeF32>(s);
+}
+
+int vbc_compute_forces(vbc_system* s, double* F, double* counts, double* energy, double* virial,
+                       int outputs_on_device)
+{
+    VBC_TRY(check_sys(s));
+    const size_t n = (size_t)s->n;
+    // host outputs are staged through the scratch halves (free once the rebuild ran)
+    double* F_dev = F ? (outputs_on_device ? F : s->xt) : nullptr;
+    double* n_dev = counts ? (outputs_on_device ? counts : s->vt) : nullptr;
+    const bool want_e = energy || virial;
+    VBC_TRY(s->prec == VBC_FP64 ? compute_impl<ModeF64>(s, F_dev, n_dev, want_e)
+                                : compute_impl<ModeF32>(s, F_dev, n_dev, want_e));
+    if (F && !outputs_on_device)
+        VBC_CUDA(cudaMemcpyAsync(F, s->xt, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    if (counts && !outputs_on_device)
+        VBC_CUDA(cudaMemcpyAsync(counts, s->vt, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    if (want_e) {
+        VBC_CUDA(cudaMemcpyAsync(s->red_host, s->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        if (outputs_on_device) {
+            if (energy) VBC_CUDA(cudaMemcpyAsync(energy, s->red, sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+            if (virial)
+                VBC_CUDA(cudaMemcpyAsync(virial, s->red + 1, sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+        }
+    }
+    VBC_CUDA(cudaStreamSynchronize(s->stream));
+    if (want_e && !outputs_on_device) {
+        if (energy) *energy = s->red_host[0];
+        if (virial) *virial = s->red_host[1];
+    }
+    return VBC_OK;
+}
+
+int vbc_get_switch(vbc_system* s, double* sw, double* dsw, double* A, int outputs_on_device)
+{
+    VBC_TRY(check_sys(s));
+    const size_t n = (size_t)s->n;
+    // staging: xt holds three n-long slices
+    double* d_s = sw ? (outputs_on_device ? sw : s->xt) : nullptr;
+    double* d_ds = dsw ? (outputs_on_device ? dsw : s->xt + n) : nullptr;
+    double* d_A = A ? (outputs_on_device ? A : s->xt + 2 * n) : nullptr;
+    if (s->prec == VBC_FP64)
+        k_store_switch<ModeF64><<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>(
+            (int)n, s->id, (const double*)s->ds, (const double2*)s->sA, d_s, d_ds, d_A);
+    else
+        k_store_switch<ModeF32><<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>(
+            (int)n, s->id, (const float*)s->ds, (const float2*)s->sA, d_s, d_ds, d_A);
+    VBC_TRY(check_launch(s));
+    if (!outputs_on_device) {
+        if (sw) VBC_CUDA(cudaMemcpyAsync(sw, d_s, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        if (dsw) VBC_CUDA(cudaMemcpyAsync(dsw, d_ds, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        if (A) VBC_CUDA(cudaMemcpyAsync(A, d_A, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    }
+    VBC_CUDA(cudaStreamSynchronize(s->stream));
+    return VBC_OK;
+}
+
+int vbc_get_neighbors(vbc_system* s, int32_t* nnb, int32_t* nbr, int32_t cap, int outputs_on_device)
+{
+    VBC_TRY(check_sys(s));
+    if (nbr && cap < 1) return fail(VBC_ERR_INVALID_ARG, "cap must be >= 1");
+    const size_t n = (size_t)s->n;
+    int* d_nnb = nullptr;
+    int* d_nbr = nullptr;
+    if (outputs_on_device) {
+        d_nnb = nnb;
+        d_nbr = nbr;
+    } else {
+        if (nnb) VBC_TRY(dalloc(d_nnb, n));
+        if (nbr) {
+            if (dalloc(d_nbr, n * (size_t)cap) != VBC_OK) {
+                if (d_nnb) cudaFree(d_nnb);
+                return VBC_ERR_OOM;
+            }
+            cudaMemsetAsync(d_nbr, 0xff, n * (size_t)cap * sizeof(int), s->stream);
+        }
+    }
+    k_store_nlist<<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>((int)n, cap, s->id, s->nbr, s->nnb, d_nnb, d_nbr);
+    int rc = check_launch(s);
+    if (rc == VBC_OK && !outputs_on_device) {
+        if (nnb && cudaMemcpyAsync(nnb, d_nnb, n * sizeof(int), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+            rc = fail(VBC_ERR_CUDA, "copy of the list lengths failed");
+        if (nbr && rc == VBC_OK &&
+            cudaMemcpyAsync(nbr, d_nbr, n * (size_t)cap * sizeof(int), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+            rc = fail(VBC_ERR_CUDA, "copy of the lists failed");
+    }
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess && rc == VBC_OK) rc = fail(VBC_ERR_CUDA, "sync failed");
+    if (!outputs_on_device) {
+        if (d_nnb) cudaFree(d_nnb);
+        if (d_nbr) cudaFree(d_nbr);
+    }
+    return rc;
+}
+
+int vbc_step_langevin(vbc_system* s, int64_t nsteps, double dt, double kT, double gamma)
+{
+    VBC_TRY(check_sys(s));
+    if (nsteps < 0) return fail(VBC_ERR_INVALID_ARG, "nsteps must be >= 0");
+    if (!(dt > 0) || !std::isfinite(dt) || !(kT >= 0) || !std::isfinite(kT) || !(gamma >= 0) ||
+        !std::isfinite(gamma))
+        return fail(VBC_ERR_INVALID_ARG, "need dt > 0, kT >= 0, gamma >= 0 (finite)");
+    if (nsteps == 0) return VBC_OK;
+    return s->prec == VBC_FP64 ? steps_impl<ModeF64>(s, nsteps, dt, kT, gamma)
+                               : steps_impl<ModeF32>(s, nsteps, dt, kT, gamma);
+}
+
+int vbc_get_state(vbc_system* s, double* pos, double* vel, int64_t* step, int on_device)
+{
+    VBC_TRY(check_sys(s));
+    const size_t n = (size_t)s->n;
+    double* dp = pos ? (on_device ? pos : s->xt) : nullptr;
+    double* dv = vel ? (on_device ? vel : s->vt) : nullptr;
+    k_store_state<<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>((int)n, s->id, s->x, s->v, dp, dv);
+    VBC_TRY(check_launch(s));
+    if (pos && !on_device) VBC_CUDA(cudaMemcpyAsync(pos, s->xt, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    if (vel && !on_device) VBC_CUDA(cudaMemcpyAsync(vel, s->vt, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    VBC_CUDA(cudaStreamSynchronize(s->stream));
+    if (step) *step = s->step;
+    return VBC_OK;
+}
+
+int vbc_set_state(vbc_system* s, const double* pos, const double* vel, int64_t step, int on_device)
+{
+    VBC_TRY(check_sys(s));
+    if (!pos) return fail(VBC_ERR_INVALID_ARG, "pos must not be NULL");
+    if (step < 0) return fail(VBC_ERR_INVALID_ARG, "step must be >= 0");
+    VBC_TRY(s->prec == VBC_FP64 ? load_state<ModeF64>(s, pos, vel, on_device)
+                                : load_state<ModeF32>(s, pos, vel, on_device));
+    s->step = step;
+    VBC_TRY(s->prec == VBC_FP64 ? build_now<ModeF64>(s) : build_now<ModeF32>(s));
+    return VBC_OK;
+}
+
+int vbc_set_params(vbc_system* s, const vbc_pair_params* p)
+{
+    VBC_TRY(check_sys(s));
+    if (!p) return fail(VBC_ERR_INVALID_ARG, "params must not be NULL");
+    const double rc = std::max(p->r_r, std::max(p->r_a, p->r_h));
+    if (!(rc + s->skin <= s->rlist + 1e-12))
+        return fail(VBC_ERR_INVALID_ARG, "new cut-off %g exceeds the list radius %g - skin", rc, s->rlist);
+    Coef c;
+    VBC_TRY(make_coef(*p, s->geom, c));
+    VBC_CUDA(cudaStreamSynchronize(s->stream));
+    s->prm = *p;
+    s->coef = c;
+    return VBC_OK;
+}
+
+int vbc_get_stats(vbc_system* s, vbc_stats* out)
+{
+    VBC_TRY(check_sys(s));
+    if (!out) return fail(VBC_ERR_INVALID_ARG, "out must not be NULL");
+    VBC_TRY(read_status(s));
+    out->n = s->n;
+    out->step = s->step;
+    out->rebuilds = s->st_host->rebuilds;
+    out->nlist_cap = s->cap;
+    out->nlist_max = s->st_host->max_nnb;
+    out->nlist_mean = (double)s->st_host->nnb_sum / (double)s->n;
+    out->pairs_within_rc = s->st_host->pairs;
+    long long w = 0;
+    VBC_CUDA(cudaMemcpy(&w, s->win, sizeof(long long), cudaMemcpyDeviceToHost));
+    out->in_window = w;
+    return VBC_OK;
+}
+
+int vbc_profile(vbc_system* s, int enable, int64_t max_launches)
+{
+    VBC_TRY(check_sys(s));
+    if (!enable) {
+        s->prof = false;
+        return VBC_OK;
+    }
+    if (max_launches < 1 || max_launches > (1 << 22)) return fail(VBC_ERR_INVALID_ARG, "max_launches out of range");
+    VBC_CUDA(cudaStreamSynchronize(s->stream));
+    for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
+    s->ev.assign(2 * (size_t)max_launches, nullptr);
+    for (auto& e : s->ev) VBC_CUDA(cudaEventCreate(&e));
+    s->ev_class.assign((size_t)max_launches, -1);
+    s->ev_used = 0;
+    s->prof_max = max_launches;
+    s->prof = true;
+    return VBC_OK;
+}
+
+int vbc_profile_read(vbc_system* s, int which, double* total_ms, int64_t* launches)
+{
+    VBC_TRY(check_sys(s));
+    if (which < 0 || which >= VBC_K_NCLASSES) return fail(VBC_ERR_INVALID_ARG, "unknown kernel class");
+    VBC_CUDA(cudaStreamSynchronize(s->stream));
+    double tot = 0.0;
+    int64_t cnt = 0;
+    for (int64_t k = 0; k < s->ev_used; ++k) {
+        if (s->ev_class[k] != which) continue;
+        float ms = 0.0f;
+        VBC_CUDA(cudaEventElapsedTime(&ms, s->ev[2 * k], s->ev[2 * k + 1]));
+        tot += ms;
+        ++cnt;
+    }
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = cnt;
+    return VBC_OK;
+}
+
+int64_t vbc_kernel_launches(vbc_system* s) { return s ? s->launches : 0; }
+
+}  // extern "C"

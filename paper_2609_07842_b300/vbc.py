@@ -1,0 +1,276 @@
+"""ctypes binding of libvbc.so (C ABI in include/vbc.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Arrays may be numpy arrays (host memory) or CUDA torch tensors
+(device memory, passed by pointer); torch supplies device memory and the
+stream, nothing else.  There is no CPU fallback: if the library cannot be
+loaded, or a call fails, a VBCError is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libvbc.so")
+
+VBC_OK = 0
+VBC_ERR_INVALID_ARG = -1
+VBC_ERR_CUDA = -2
+VBC_ERR_OOM = -3
+VBC_ERR_NLIST_OVERFLOW = -4
+VBC_ERR_UNSTABLE = -5
+VBC_FP32_SPLIT = 0
+VBC_FP64 = 1
+K_REBUILD, K_COUNT, K_CHAIN, K_FORCE, K_ENERGY = range(5)
+
+#: every function the header declares
+EXPORTS = ("vbc_create_system", "vbc_build_neighbors", "vbc_compute_forces", "vbc_get_switch",
+           "vbc_get_neighbors",
+           "vbc_step_langevin", "vbc_get_state", "vbc_set_state", "vbc_set_params", "vbc_get_stats",
+           "vbc_profile", "vbc_profile_read", "vbc_kernel_launches", "vbc_destroy", "vbc_last_error")
+
+
+class VBCError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libvbc error {code}: {msg}")
+        self.code = code
+
+
+class PairParams(ctypes.Structure):
+    """VBC(r_l, r_h, delta) on the polynomial soft core (Sec. 2)."""
+    _fields_ = [(k, ctypes.c_double) for k in ("r_r", "r_a", "r_l", "r_h", "E_r", "E_a", "f", "delta")]
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("box", ctypes.c_double * 3), ("pos", ctypes.c_void_p),
+                ("vel", ctypes.c_void_p), ("params", PairParams), ("skin", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32), ("nlist_cap", ctypes.c_int32),
+                ("stream", ctypes.c_void_p), ("inputs_on_device", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("step", ctypes.c_int64), ("rebuilds", ctypes.c_int64),
+                ("nlist_cap", ctypes.c_int32), ("nlist_max", ctypes.c_int32), ("nlist_mean", ctypes.c_double),
+                ("pairs_within_rc", ctypes.c_int64), ("in_window", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libvbc.so from the package directory (built by build.py)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_2609_07842_b300.build` "
+                          "(the VBC path has no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, dp, i64, i32 = ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_int
+    L.vbc_create_system.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(vp)]
+    L.vbc_build_neighbors.argtypes = [vp]
+    L.vbc_compute_forces.argtypes = [vp, vp, vp, vp, vp, i32]
+    L.vbc_get_switch.argtypes = [vp, vp, vp, vp, i32]
+    L.vbc_get_neighbors.argtypes = [vp, vp, vp, ctypes.c_int32, i32]
+    L.vbc_step_langevin.argtypes = [vp, i64, dp, dp, dp]
+    L.vbc_get_state.argtypes = [vp, vp, vp, ctypes.POINTER(i64), i32]
+    L.vbc_set_state.argtypes = [vp, vp, vp, i64, i32]
+    L.vbc_set_params.argtypes = [vp, ctypes.POINTER(PairParams)]
+    L.vbc_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+    L.vbc_profile.argtypes = [vp, i32, i64]
+    L.vbc_profile_read.argtypes = [vp, i32, ctypes.POINTER(dp), ctypes.POINTER(i64)]
+    L.vbc_kernel_launches.argtypes = [vp]
+    L.vbc_kernel_launches.restype = i64
+    L.vbc_destroy.argtypes = [vp]
+    L.vbc_destroy.restype = None
+    L.vbc_last_error.argtypes = []
+    L.vbc_last_error.restype = ctypes.c_char_p
+    for name in ("vbc_create_system", "vbc_build_neighbors", "vbc_compute_forces", "vbc_get_switch",
+                 "vbc_get_neighbors", "vbc_step_langevin", "vbc_get_state", "vbc_set_state", "vbc_set_params", "vbc_get_stats",
+                 "vbc_profile", "vbc_profile_read"):
+        getattr(L, name).restype = i32
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != VBC_OK:
+        raise VBCError(rc, load().vbc_last_error().decode())
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, on_device: bool | None = None):
+    """(pointer, on_device) of a numpy array or torch tensor (float64, contiguous)."""
+    if a is None:
+        return None, on_device
+    if _is_torch(a):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("tensors must be contiguous float64")
+        dev = a.is_cuda
+        return ctypes.c_void_p(a.data_ptr()), dev
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+        raise TypeError("arrays must be C-contiguous float64 numpy arrays or torch tensors")
+    return ctypes.c_void_p(a.ctypes.data), False
+
+
+def _same_side(items):
+    sides = {d for _, d in items if d is not None}
+    if len(sides) > 1:
+        raise TypeError("all arrays of one call must be on the same side (host or device)")
+    return int(sides.pop()) if sides else 0
+
+
+def params(**kw) -> PairParams:
+    """Pair parameters; defaults are the standard VBC (r_r=1, r_a=r_l=1.5, r_h=2, E_r=20, E_a=2,
+    f=2, delta=0)."""
+    d = dict(r_r=1.0, r_a=1.5, r_l=1.5, r_h=2.0, E_r=20.0, E_a=2.0, f=2.0, delta=0.0)
+    d.update(kw)
+    return PairParams(**d)
+
+
+@dataclass
+class Result:
+    F: object = None
+    counts: object = None
+    energy: float | None = None
+    virial: float | None = None
+    extra: dict = field(default_factory=dict)
+
+
+class System:
+    """One particle system resident on the GPU (vbc_create_system ... vbc_destroy)."""
+
+    def __init__(self, pos, box, prm: PairParams | None = None, vel=None, skin: float = 0.4,
+                 seed: int = 1, precision: int = VBC_FP32_SPLIT, nlist_cap: int = 0, stream=None):
+        L = load()
+        prm = prm if prm is not None else params()
+        b = np.broadcast_to(np.asarray(box, dtype=np.float64), (3,))
+        n = int(pos.shape[0])
+        pp, pdev = _ptr(pos)
+        vv, vdev = _ptr(vel)
+        on_dev = _same_side([(pp, pdev), (vv, vdev)])
+        if stream is None and on_dev:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        cfg = _Config(n=n, box=(ctypes.c_double * 3)(*b), pos=pp, vel=vv, params=prm, skin=skin,
+                      seed=seed, precision=precision, nlist_cap=nlist_cap,
+                      stream=ctypes.c_void_p(stream) if stream else None, inputs_on_device=on_dev)
+        h = ctypes.c_void_p()
+        _check(L.vbc_create_system(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self.n = n
+        self.box = b.copy()
+        self.precision = precision
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            load().vbc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls
+    def build_neighbors(self):
+        _check(load().vbc_build_neighbors(self._h))
+
+    def compute(self, F=None, counts=None, energy: bool = False, virial: bool = False) -> Result:
+        """One force/energy evaluation (vbc_compute_forces).  F [n,3] and counts [n] are caller
+        buffers: numpy (host) or CUDA tensors (device); pass True to get new numpy arrays."""
+        if F is True:
+            F = np.zeros((self.n, 3))
+        if counts is True:
+            counts = np.zeros(self.n)
+        fp, fd = _ptr(F)
+        cp, cd = _ptr(counts)
+        dev = _same_side([(fp, fd), (cp, cd)])
+        buf = None
+        if dev and (energy or virial):
+            import torch
+            buf = torch.zeros(2, dtype=torch.float64, device="cuda")
+            ep = ctypes.c_void_p(buf.data_ptr()) if energy else None
+            wp = ctypes.c_void_p(buf.data_ptr() + 8) if virial else None
+        else:
+            e, w = ctypes.c_double(0.0), ctypes.c_double(0.0)
+            ep = ctypes.byref(e) if energy else None
+            wp = ctypes.byref(w) if virial else None
+        _check(load().vbc_compute_forces(self._h, fp, cp, ep, wp, dev))
+        if buf is not None:
+            vals = buf.cpu().numpy()
+            ev, wv = float(vals[0]), float(vals[1])
+        else:
+            ev, wv = e.value, w.value
+        return Result(F=F, counts=counts, energy=ev if energy else None, virial=wv if virial else None)
+
+    def switch(self):
+        """(s, ds/dn, A) per particle from the last evaluation, as numpy arrays."""
+        s, ds, A = np.zeros(self.n), np.zeros(self.n), np.zeros(self.n)
+        _check(load().vbc_get_switch(self._h, _ptr(s)[0], _ptr(ds)[0], _ptr(A)[0], 0))
+        return s, ds, A
+
+    def neighbors(self, cap: int = 256):
+        """(nnb [n], nbr [n, cap]) of the last build in caller indices; unused slots are -1."""
+        nnb = np.zeros(self.n, dtype=np.int32)
+        nbr = np.full((self.n, cap), -1, dtype=np.int32)
+        _check(load().vbc_get_neighbors(self._h, ctypes.c_void_p(nnb.ctypes.data),
+                                        ctypes.c_void_p(nbr.ctypes.data), cap, 0))
+        return nnb, nbr
+
+    def step(self, nsteps: int, dt: float, kT: float, gamma: float):
+        _check(load().vbc_step_langevin(self._h, int(nsteps), dt, kT, gamma))
+
+    def get_state(self, pos=None, vel=None):
+        if pos is None:
+            pos = np.zeros((self.n, 3))
+        if vel is None:
+            vel = np.zeros((self.n, 3))
+        pp, pd = _ptr(pos)
+        vv, vd = _ptr(vel)
+        dev = _same_side([(pp, pd), (vv, vd)])
+        st = ctypes.c_int64(0)
+        _check(load().vbc_get_state(self._h, pp, vv, ctypes.byref(st), dev))
+        return pos, vel, st.value
+
+    def set_state(self, pos, vel=None, step: int = 0):
+        pp, pd = _ptr(pos)
+        vv, vd = _ptr(vel)
+        dev = _same_side([(pp, pd), (vv, vd)])
+        _check(load().vbc_set_state(self._h, pp, vv, int(step), dev))
+
+    def set_params(self, prm: PairParams):
+        _check(load().vbc_set_params(self._h, ctypes.byref(prm)))
+
+    def stats(self) -> Stats:
+        s = Stats()
+        _check(load().vbc_get_stats(self._h, ctypes.byref(s)))
+        return s
+
+    def profile(self, enable: bool, max_launches: int = 1 << 16):
+        _check(load().vbc_profile(self._h, int(enable), int(max_launches)))
+
+    def profile_read(self, which: int):
+        ms = ctypes.c_double(0.0)
+        cnt = ctypes.c_int64(0)
+        _check(load().vbc_profile_read(self._h, which, ctypes.byref(ms), ctypes.byref(cnt)))
+        return ms.value, cnt.value
+
+    def kernel_launches(self) -> int:
+        return int(load().vbc_kernel_launches(self._h))

@@ -1,0 +1,96 @@
+"""C-ABI boundary checks that need no GPU: the library builds and loads, it
+exports every function include/vbc.h declares, and argument validation
+rejects bad configurations before any CUDA call is made."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2609_07842_b300 import build as vbuild
+from paper_2609_07842_b300 import vbc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    vbuild.build()
+    return vbc.load()
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "vbc.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(vbc_[a-z_]+)\s*\(", txt)))
+
+
+def test_header_and_binding_agree():
+    assert sorted(vbc.EXPORTS) == _declared()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+    out = os.popen(f"nm -D --defined-only {vbc.LIB_PATH}").read()
+    for name in _declared():
+        assert re.search(rf"\bT {name}\b", out), name
+
+
+def test_library_targets_sm103a():
+    assert "arch=compute_103a,code=sm_103a" in " ".join(vbuild.NVCC_FLAGS)
+
+
+def _cfg(n=100, box=(12.0, 12.0, 12.0), prec=vbc.VBC_FP32_SPLIT, skin=0.4, **prm):
+    pos = np.zeros((max(n, 1), 3))
+    c = vbc._Config(n=n, box=(ctypes.c_double * 3)(*box), pos=ctypes.c_void_p(pos.ctypes.data), vel=None,
+                    params=vbc.params(**prm), skin=skin, seed=1, precision=prec, nlist_cap=0,
+                    stream=None, inputs_on_device=0)
+    return c, pos
+
+
+@pytest.mark.parametrize("kw,needle", [
+    (dict(n=0), "n must be"),
+    (dict(box=(12.0, 12.0, -1.0)), "box edges"),
+    (dict(box=(12.0, 12.0, 13.0)), "cubic"),
+    (dict(box=(6.0, 6.0, 6.0)), "fewer than 3 cells"),
+    (dict(skin=0.0), "skin"),
+    (dict(prec=7), "precision"),
+    (dict(r_a=0.5), "pair parameters"),
+    (dict(r_l=2.0, r_h=1.0), "pair parameters"),
+    (dict(E_a=-1.0), "pair parameters"),
+    (dict(f=float("nan")), "pair parameters"),
+])
+def test_create_rejects_bad_arguments(lib, kw, needle):
+    c, _keep = _cfg(**kw)
+    h = ctypes.c_void_p()
+    rc = lib.vbc_create_system(ctypes.byref(c), ctypes.byref(h))
+    assert rc == vbc.VBC_ERR_INVALID_ARG
+    assert needle in lib.vbc_last_error().decode()
+    assert not h.value
+
+
+def test_null_arguments(lib):
+    assert lib.vbc_create_system(None, None) == vbc.VBC_ERR_INVALID_ARG
+    assert lib.vbc_build_neighbors(None) == vbc.VBC_ERR_INVALID_ARG
+    assert lib.vbc_step_langevin(None, 1, 0.01, 1.0, 1.0) == vbc.VBC_ERR_INVALID_ARG
+    assert lib.vbc_compute_forces(None, None, None, None, None, 0) == vbc.VBC_ERR_INVALID_ARG
+    lib.vbc_destroy(None)  # accepted
+
+
+def test_orthorhombic_box_allowed_in_fp64_until_device_needed(lib):
+    """A non-cubic box passes validation in FP64 mode; without a GPU the call then
+    fails with a CUDA error (not a crash, not a CPU fallback)."""
+    import torch
+    c, _keep = _cfg(box=(12.0, 13.0, 14.0), prec=vbc.VBC_FP64)
+    h = ctypes.c_void_p()
+    rc = lib.vbc_create_system(ctypes.byref(c), ctypes.byref(h))
+    if torch.cuda.is_available():
+        assert rc == vbc.VBC_OK
+        lib.vbc_destroy(h)
+    else:
+        assert rc in (vbc.VBC_ERR_CUDA, vbc.VBC_ERR_OOM)
+        assert not h.value
