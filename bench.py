@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the VBC path on B300.
+
+One bench step = one BAOAB Langevin timestep of the whole path: neighbour-list
+rebuild when due (amortised), pass 1 counts, chain-rule pass, pass 2 forces
+fused with the integrator update.  Workload: N = 1,000,000 identical particles,
+uniform random in a periodic cube at number density 0.5, standard VBC(1.5, 2.0, 0)
+on the polynomial soft core (E_r = 20, E_a = 8), valency 2, dt = 0.005, kT = 1,
+gamma = 1, skin 0.4; FP32 pair arithmetic with FP64 state and reductions.
+The system is equilibrated (untimed) before the W warm-up and K timed steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank runs an
+independent replica of the workload on its own GPU (the path has no exchange
+step between systems), and value = total timesteps of all replicas / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "VBC pair-interactions/s and MD timesteps/s at N=1M on 1 B300, % HBM roofline; p50/p99 served"
+UNIT = "timesteps/s"
+FALLBACK_HBM_GBS = 6400.0
+KERNEL_SOURCES = ("paper_2609_07842_b300/csrc/vbc_kernels.cuh", "paper_2609_07842_b300/csrc/vbc_device.cuh")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_kernel_traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("b300", "reference"), default="b300")
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--rho", type=float, default=0.5)
+    ap.add_argument("--valency", type=float, default=2.0)
+    ap.add_argument("--E_a", type=float, default=8.0)
+    ap.add_argument("--equil", type=int, default=500, help="untimed equilibration steps")
+    ap.add_argument("--e2e-chunk", type=int, default=1000, help="steps per host round trip in the e2e leg")
+    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle time for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+DT, KT, GAMMA, SKIN, SEED = 0.005, 1.0, 1.0, 0.4, 3
+
+
+def workload(args):
+    return {
+        "workload": (f"uniform fluid N={args.n:,} rho={args.rho}, standard VBC(1.5,2.0,0) soft core "
+                     f"E_r=20 E_a={args.E_a:g} valency {args.valency:g}, BAOAB dt={DT} kT={KT} gamma={GAMMA}, "
+                     f"skin {SKIN}"),
+        "n": args.n, "rho": args.rho, "valency": args.valency, "E_a": args.E_a,
+        "equilibration_steps": args.equil,
+        "precision": "FP32 pair arithmetic, FP64 state and energy",
+        "l2": "no flush: working set per step (~0.4 GB) > L2 (126 MB)",
+    }
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def start_clocks(local):
+    try:
+        return subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_Q}", "--format=csv,noheader,nounits",
+                                 "-lms", "100", "-i", str(local)], stdout=subprocess.PIPE,
+                                stderr=subprocess.DEVNULL, text=True)
+    except (OSError, ValueError):
+        return None
+
+
+def stop_clocks(proc):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        out, _ = proc.communicate(timeout=5)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+        out, _ = proc.communicate()
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in out.splitlines():
+        t = [x.strip() for x in line.split(",")]
+        if len(t) < 9:
+            continue
+        try:
+            sm.append(float(t[1]))
+            smax.append(float(t[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, t[5:9]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(n):
+    """DRAM bytes per launch of the fused force kernel from the committed ncu summary,
+    scaled to n particles; None when the kernel changed since the capture."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            t = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if t.get("kernel_sources_sha256_16") != kernel_hash():
+        return None
+    return t["dram_bytes_per_particle"] * n
+
+
+def force_bytes_per_particle(k):
+    """Algorithmic HBM bytes per particle of one fused force + BAOAB launch: list 4k, list
+    length 4, own fixed-point position 16, own (s, A) 8, id 4, FP64 x and v read + write 96,
+    next fixed-point position 16, position at the last build 16."""
+    return 4.0 * k + 160.0
+
+
+def step_bytes_per_particle(k, phi, rebuild_every):
+    """Algorithmic bytes per particle-step of the whole path: count (4k + 32), chain
+    (4 + phi (4k + 24)), force (4k + 160), amortised rebuild (~(4k + 220) / R)."""
+    rb = (4.0 * k + 220.0) / rebuild_every if rebuild_every > 0 else 0.0
+    return (4.0 * k + 32.0) + (4.0 + phi * (4.0 * k + 24.0)) + force_bytes_per_particle(k) + rb
+
+
+# ------------------------------------------------------------------ reference arm (the oracle)
+def run_oracle(args, steps, budget):
+    import oracle
+    from paper_2609_07842_b300 import inputs
+    pos, L = inputs.uniform_positions(args.n, args.rho, seed=SEED)
+    vel = inputs.maxwell_velocities(args.n, KT, seed=SEED + 1)
+    p = oracle.Params(E_a=args.E_a, f=args.valency)
+    t0 = time.perf_counter()
+    x, v, st = oracle.baoab(pos, vel, L, p, 1, DT, KT, GAMMA, seed=SEED, mode=1)  # first step + warm caches
+    t_first = time.perf_counter() - t0
+    # an n-step call evaluates forces n + 1 times; size the sample to the budget
+    k = int(max(1, min(steps, budget / max(t_first / 2.0, 1e-9) - 1)))
+    t0 = time.perf_counter()
+    x, v, st = oracle.baoab(x, v, L, p, k, DT, KT, GAMMA, seed=SEED, step=st, mode=1)
+    dt = time.perf_counter() - t0
+    return k / dt, k, dt, oracle.num_threads()
+
+
+def reference_main(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    budget = max(10.0, min(120.0, args.cpu_budget * 3))
+    value, k, secs, cores = run_oracle(args, args.steps, budget)
+    sample = (f"{k} BAOAB steps of the full N={args.n:,} system with the FP64 oracle (cell-list mode, "
+              f"OpenMP), {secs:.1f} s; time-bounded sample of the requested {args.steps} steps")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {**workload(args), "precision": "FP64 oracle (cell-list mode)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ B300 arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_main(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2609_07842_b300 import inputs, vbc
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    pos, L = inputs.uniform_positions(args.n, args.rho, seed=SEED + rank)
+    vel = inputs.maxwell_velocities(args.n, KT, seed=SEED + 1 + rank)
+    prm = vbc.params(E_a=args.E_a, f=args.valency)
+    sys_ = vbc.System(pos, L, prm, vel=vel, skin=SKIN, seed=SEED + rank, stream=stream.cuda_stream)
+
+    # untimed equilibration + warm-up
+    sys_.step(args.equil, DT, KT, GAMMA)
+    sys_.step(max(args.warmup, 3), DT, KT, GAMMA)
+    st0 = sys_.stats()
+
+    # ---- timed region (device time, library stream = torch current stream)
+    sys_.profile(True, max_launches=4 * (args.steps + 2) + 16)
+    launches0 = sys_.kernel_launches()
+    clocks = start_clocks(local)
+    time.sleep(0.3 if clocks else 0.0)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sys_.step(args.steps, DT, KT, GAMMA)
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = stop_clocks(clocks)
+    launches = sys_.kernel_launches() - launches0
+    force_ms, force_n = sys_.profile_read(vbc.K_FORCE)
+    count_ms, count_n = sys_.profile_read(vbc.K_COUNT)
+    chain_ms, chain_n = sys_.profile_read(vbc.K_CHAIN)
+    reb_ms, reb_n = sys_.profile_read(vbc.K_REBUILD)
+    sys_.profile(False)
+    st1 = sys_.stats()
+
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # pair interactions (unordered pairs with r < r_c) at the end configuration
+    r = sys_.compute(energy=True)
+    st2 = sys_.stats()
+    pairs = st2.pairs_within_rc
+    k_mean = st1.nlist_mean
+    rebuilds = st1.rebuilds - st0.rebuilds
+    rebuild_every = args.steps / rebuilds if rebuilds > 0 else float("inf")
+    phi = st2.in_window / args.n
+
+    steps_per_s = args.steps / (ms / 1e3) * world
+    peak, peak_kind = hbm_peak()
+    fb = force_bytes_per_particle(k_mean) * args.n
+    force_avg_s = force_ms / 1e3 / max(force_n, 1)
+    achieved = fb / force_avg_s / 1e9
+    traffic = ncu_traffic(args.n)
+    step_b = step_bytes_per_particle(k_mean, phi, rebuild_every if rebuilds else 0) * args.n
+    step_gbs = step_b * (args.steps / (ms / 1e3)) / 1e9
+
+    # ---- e2e: the same steps through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        chunk = max(1, min(args.e2e_chunk, args.steps))
+        hp = torch.empty((args.n, 3), dtype=torch.float64).pin_memory().numpy()
+        hv = torch.empty((args.n, 3), dtype=torch.float64).pin_memory().numpy()
+        _, _, stp = sys_.get_state(hp, hv)
+        barrier()
+        t0 = time.perf_counter()
+        done = 0
+        while done < args.steps:
+            c = min(chunk, args.steps - done)
+            sys_.set_state(hp, hv, step=stp)         # h2d: positions + velocities
+            sys_.step(c, DT, KT, GAMMA)
+            _, _, stp = sys_.get_state(hp, hv)       # d2h: positions + velocities
+            done += c
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        nchunks = -(-args.steps // chunk)
+        e2e = {"value": args.steps / e2e_s * world, "unit": UNIT,
+               "h2d_bytes_per_step": int(48 * args.n * nchunks / args.steps),
+               "d2h_bytes_per_step": int(48 * args.n * nchunks / args.steps),
+               "chunk_steps": chunk}
+
+    # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, k, secs, cores = run_oracle(args, args.steps, args.cpu_budget)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{k} BAOAB steps of the full N={args.n:,} system, FP64 oracle in cell-list mode "
+                         f"(OpenMP), {secs:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": steps_per_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload(args),
+            "pair_interactions_per_s": pairs * steps_per_s,
+            "pairs_within_rc": pairs,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_force (pass 2 fused with BAOAB)", "peak_source": peak_kind,
+                         "algorithmic_bytes_per_launch": fb, "avg_launch_ms": force_avg_s * 1e3,
+                         "launches": force_n},
+            "step_roofline": {"achieved": step_gbs, "frac": step_gbs / peak,
+                              "algorithmic_bytes_per_step": step_b,
+                              "bytes_per_particle_step": step_b / args.n},
+            "kernel_ms_per_step": {"rebuild": reb_ms / args.steps, "count": count_ms / args.steps,
+                                   "chain": chain_ms / args.steps, "force": force_ms / args.steps},
+            "nlist_mean": k_mean, "in_window_fraction": phi, "steps_per_rebuild": rebuild_every,
+            "energy_per_particle": r.energy / args.n,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    sys_.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -15,7 +15,9 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -95,6 +97,7 @@ struct vbc_system {
 
     int64_t step = 0;
     int64_t launches = 0;
+    int unroll = 4;  // list entries per batch in the pass kernels (1, 2, 4 or 8)
 
     // per-kernel event timing
     bool prof = false;
@@ -271,6 +274,18 @@ int enqueue_rebuild(vbc_system* s, int iter)
     return check_launch(s, 8);
 }
 
+// Calls f with the list-walk batch size as a compile-time constant.
+template <class F>
+void with_unroll(int u, F&& f)
+{
+    switch (u) {
+        case 1: f(std::integral_constant<int, 1>{}); break;
+        case 2: f(std::integral_constant<int, 2>{}); break;
+        case 8: f(std::integral_constant<int, 8>{}); break;
+        default: f(std::integral_constant<int, 4>{}); break;
+    }
+}
+
 template <class M>
 int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window)
 {
@@ -281,16 +296,23 @@ int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window)
     const int nb = blocks_for(n, TPB);
     const pos_t* pos = (const pos_t*)s->pos[s->cur];
     CountOut out{n_out, want_window ? s->win : nullptr};
-    {
-        Timed t(s, VBC_K_COUNT);
-        k_count<M><<<nb, TPB, 0, s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb, s->id, (real*)s->ds,
-                                              (real2*)s->sA, out, s->st);
-    }
-    {
-        Timed t(s, VBC_K_CHAIN);
-        k_chain<M><<<nb, TPB, 0, s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb, (const real*)s->ds,
-                                              (real2*)s->sA, s->st);
-    }
+    with_unroll(s->unroll, [&](auto U) {
+        {
+            Timed t(s, VBC_K_COUNT);
+            if constexpr (M::fp64)
+                k_count_f64<<<nb, TPB, 0, s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb, s->id,
+                                                       (real*)s->ds, (real2*)s->sA, out, s->st);
+            else
+                k_count_f32<decltype(U)::value><<<nb, TPB, 0, s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb,
+                                                                           s->id, (real*)s->ds, (real2*)s->sA, out,
+                                                                           s->st);
+        }
+        {
+            Timed t(s, VBC_K_CHAIN);
+            k_chain<M, decltype(U)::value><<<nb, TPB, 0, s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb,
+                                                                       (const real*)s->ds, (real2*)s->sA, s->st);
+        }
+    });
     return check_launch(s, 2);
 }
 
@@ -302,12 +324,12 @@ int enqueue_force(vbc_system* s, const StepArgs& a)
     const int n = (int)s->n;
     const pos_t* pos = (const pos_t*)s->pos[s->cur];
     pos_t* pos_next = (pos_t*)s->pos[s->cur ^ 1];
-    {
+    with_unroll(s->unroll, [&](auto U) {
         Timed t(s, VBC_K_FORCE);
-        k_force<M, EPI><<<blocks_for(n, TPB), TPB, 0, s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb, s->id,
-                                                                  (const real2*)s->sA, pos_next,
-                                                                  (const pos_t*)s->xref, a, s->st);
-    }
+        k_force<M, EPI, decltype(U)::value><<<blocks_for(n, TPB), TPB, 0, s->stream>>>(
+            n, s->geom, s->coef, pos, s->nbr, s->nnb, s->id, (const real2*)s->sA, pos_next, (const pos_t*)s->xref, a,
+            s->st);
+    });
     VBC_TRY(check_launch(s));
     if (EPI == EPI_START || EPI == EPI_FINISH_START) s->cur ^= 1;
     return VBC_OK;
@@ -502,6 +524,11 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     if (cfg->nlist_cap < 0) return fail(VBC_ERR_INVALID_ARG, "nlist_cap must be >= 0");
 
     vbc_system* s = new vbc_system();
+    // tuning knob for experiments: list entries per batch in the pass kernels
+    if (const char* e = std::getenv("VBC_WALK_UNROLL")) {
+        const int u = std::atoi(e);
+        if (u == 1 || u == 2 || u == 4 || u == 8) s->unroll = u;
+    }
     s->n = cfg->n;
     s->prec = cfg->precision;
     s->prm = cfg->params;

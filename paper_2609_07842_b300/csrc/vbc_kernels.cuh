@@ -303,6 +303,30 @@ __global__ void __launch_bounds__(TPB) k_nlist(int n, Geom g, const typename M::
     }
 }
 
+// ================================================================ list walk
+// Visits the list of particle i in batches of U entries: the U indices are
+// loaded first (each a coalesced 128-byte row across the warp), then the U
+// neighbour positions (gathers served by L1/L2), then the U pair bodies run.
+// Batching keeps U independent loads in flight per thread, which the
+// dependent index -> position chain would otherwise serialise.  Padding
+// slots of the last batch point at i itself and are skipped.
+template <class M, int U, class Body>
+__device__ __forceinline__ void walk_list(int i, int n, int m, const int* __restrict__ nbr,
+                                          const typename M::pos_t* __restrict__ pos, Body&& body)
+{
+    for (int k0 = 0; k0 < m; k0 += U) {
+        int jj[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) jj[u] = (k0 + u < m) ? __ldg(nbr + (size_t)(k0 + u) * n + i) : i;
+        typename M::pos_t pj[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) pj[u] = pos[jj[u]];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (k0 + u < m) body(jj[u], pj[u]);
+    }
+}
+
 // ================================================================ pass 1: counts
 // FP32-split: neighbours with r <= r_l add exactly 1 (an integer); window
 // neighbours add omega in 2^-31 fixed point, evaluated from the exact integer
@@ -329,17 +353,11 @@ __device__ __forceinline__ void switch_from_fix(long long T, float& s, float& ds
     }
 }
 
-template <class M>
-__global__ void __launch_bounds__(TPB) k_count(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
-                                               const int* __restrict__ nbr, const int* __restrict__ nnb,
-                                               const int* __restrict__ id, typename M::real* __restrict__ ds_out,
-                                               typename M::real2* __restrict__ sA, CountOut out, Status* st);
-
-template <>
-__global__ void __launch_bounds__(TPB) k_count<ModeF32>(int n, Geom g, Coef c, const int4* __restrict__ pos,
-                                                        const int* __restrict__ nbr, const int* __restrict__ nnb,
-                                                        const int* __restrict__ id, float* __restrict__ ds_out,
-                                                        float2* __restrict__ sA, CountOut out, Status* st)
+template <int U>
+__global__ void __launch_bounds__(TPB) k_count_f32(int n, Geom g, Coef c, const int4* __restrict__ pos,
+                                                   const int* __restrict__ nbr, const int* __restrict__ nnb,
+                                                   const int* __restrict__ id, float* __restrict__ ds_out,
+                                                   float2* __restrict__ sA, CountOut out, Status* st)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) st->rebuild = 0;
     if (halted(st)) return;
@@ -350,9 +368,7 @@ __global__ void __launch_bounds__(TPB) k_count<ModeF32>(int n, Geom g, Coef c, c
         const int m = nnb[i];
         unsigned full = 0;
         unsigned long long q = 0;
-        for (int k = 0; k < m; ++k) {
-            const int j = __ldg(nbr + (size_t)k * n + i);
-            const int4 pj = __ldg(pos + j);
+        walk_list<ModeF32, U>(i, n, m, nbr, pos, [&](int, const int4& pj) {
             const int dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
             const unsigned long long r2 = (unsigned long long)((long long)dx * dx) +
                                           (unsigned long long)((long long)dy * dy) +
@@ -369,7 +385,7 @@ __global__ void __launch_bounds__(TPB) k_count<ModeF32>(int n, Geom g, Coef c, c
                     q += (unsigned long long)__float2uint_rn(qq * qq * 2147483648.0f);
                 }
             }
-        }
+        });
         const long long T = ((long long)full - c.fd_int) * 2147483648LL + (long long)q - c.fd_frac_fix;
         float s, ds;
         switch_from_fix(T, s, ds);
@@ -384,8 +400,7 @@ __global__ void __launch_bounds__(TPB) k_count<ModeF32>(int n, Geom g, Coef c, c
     }
 }
 
-template <>
-__global__ void __launch_bounds__(TPB) k_count<ModeF64>(int n, Geom g, Coef c, const P64* __restrict__ pos,
+__global__ void __launch_bounds__(TPB) k_count_f64(int n, Geom g, Coef c, const P64* __restrict__ pos,
                                                         const int* __restrict__ nbr, const int* __restrict__ nnb,
                                                         const int* __restrict__ id, double* __restrict__ ds_out,
                                                         double2* __restrict__ sA, CountOut out, Status* st)
@@ -420,7 +435,7 @@ __global__ void __launch_bounds__(TPB) k_count<ModeF64>(int n, Geom g, Coef c, c
 
 // ================================================================ chain-rule pass
 // A_i = s'_i sum_j s_j V_a(r_ij) for particles inside the switching window.
-template <class M>
+template <class M, int U>
 __global__ void __launch_bounds__(TPB) k_chain(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
                                                const int* __restrict__ nbr, const int* __restrict__ nnb,
                                                const typename M::real* __restrict__ ds,
@@ -436,10 +451,9 @@ __global__ void __launch_bounds__(TPB) k_chain(int n, Geom g, Coef c, const type
     const int m = nnb[i];
     const real* s_only = reinterpret_cast<const real*>(sA);  // s_j at even offsets
     real acc = 0;
-    for (int k = 0; k < m; ++k) {
-        const int j = nbr[(size_t)k * n + i];
+    walk_list<M, U>(i, n, m, nbr, pos, [&](int j, const typename M::pos_t& pj) {
         real dx, dy, dz;
-        M::delta(pi, pos[j], g, dx, dy, dz);
+        M::delta(pi, pj, g, dx, dy, dz);
         const real r2 = dx * dx + dy * dy + dz * dz;
         if constexpr (M::fp64) {
             if (r2 > c.rr2 && r2 < c.ra2) acc += s_only[2 * j] * Va_d(sqrt(r2), c);
@@ -451,7 +465,7 @@ __global__ void __launch_bounds__(TPB) k_chain(int n, Geom g, Coef c, const type
                 acc += s_only[2 * j] * (-c.Eaf * q * q);
             }
         }
-    }
+    });
     sA[i].y = dsi * acc;
 }
 
@@ -466,7 +480,7 @@ struct StepArgs {
     float half_skin2;     // (skin / 2)^2
 };
 
-template <class M, int EPI>
+template <class M, int EPI, int U>
 __global__ void __launch_bounds__(TPB) k_force(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
                                                const int* __restrict__ nbr, const int* __restrict__ nnb,
                                                const int* __restrict__ id,
@@ -485,13 +499,12 @@ __global__ void __launch_bounds__(TPB) k_force(int n, Geom g, Coef c, const type
     const typename M::real2 sai = sA[i];
     const int m = nnb[i];
     real fx = 0, fy = 0, fz = 0;
-    for (int k = 0; k < m; ++k) {
-        const int j = __ldg(nbr + (size_t)k * n + i);
+    walk_list<M, U>(i, n, m, nbr, pos, [&](int j, const typename M::pos_t& pj) {
         real dx, dy, dz;
-        M::delta(pi, pos[j], g, dx, dy, dz);
+        M::delta(pi, pj, g, dx, dy, dz);
         const real r2 = dx * dx + dy * dy + dz * dz;
         if constexpr (M::fp64) {
-            if (r2 >= c.rc2) continue;
+            if (r2 >= c.rc2) return;
             const typename M::real2 saj = sA[j];
             const double r = sqrt(r2);
             double gr = dVr_over_r_d(r2, c);
@@ -500,7 +513,7 @@ __global__ void __launch_bounds__(TPB) k_force(int n, Geom g, Coef c, const type
             fy -= gr * dy;
             fz -= gr * dz;
         } else {
-            if (r2 >= c.rc2f) continue;
+            if (r2 >= c.rc2f) return;
             const float2 saj = __ldg(sA + j);
             const float rinv = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
             const float r = r2 * rinv;
@@ -520,7 +533,7 @@ __global__ void __launch_bounds__(TPB) k_force(int n, Geom g, Coef c, const type
             fy -= gr * dy;
             fz -= gr * dz;
         }
-    }
+    });
     if constexpr (EPI == EPI_FORCE) {
         if (a.F_out) {
             const int o = id[i];
