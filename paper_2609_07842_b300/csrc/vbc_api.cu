@@ -93,11 +93,27 @@ struct vbc_system {
     double* red = nullptr;       // [2] U, W
     double* red_host = nullptr;  // pinned [2]
     long long* win = nullptr;
+    double2* e_sd = nullptr;     // FP64 (s, s') of the energy evaluation
+    double* e_A = nullptr;       // FP64 A of the energy evaluation
     int nblk_energy = 0;
 
     int64_t step = 0;
     int64_t launches = 0;
     int unroll = 4;  // list entries per batch in the pass kernels (1, 2, 4 or 8)
+
+    // CUDA graphs of two FINISH_START iterations, one per parity of the
+    // position buffer at the first of the two (see steps_impl)
+    bool use_graphs = true;
+    bool capturing = false;
+    cudaStream_t cap_stream = nullptr, body_stream = nullptr;
+    struct PairGraph {
+        cudaGraphExec_t exec = nullptr;
+        double dt = 0, c1 = 0, c2 = 0;
+        const void* nbr = nullptr;
+        long long coef_version = -1;
+        int unroll = 0;
+    } pair_graph[2];
+    long long coef_version = 0;
 
     // per-kernel event timing
     bool prof = false;
@@ -133,7 +149,7 @@ struct Timed {
 
 int check_launch(vbc_system* s, int count = 1)
 {
-    s->launches += count;
+    if (!s->capturing) s->launches += count;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(VBC_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
     return VBC_OK;
@@ -188,6 +204,13 @@ int make_coef(const vbc_pair_params& p, const Geom& g, Coef& c)
     const double s2 = g.s32d[0] * g.s32d[0];
     c.rl2_fix = (unsigned long long)std::llround(c.rl2 / s2);
     c.rh2_fix = (unsigned long long)std::llround(c.rh2 / s2);
+    {
+        const double rl_s = p.r_l / g.s32d[0], w_s = c.w / g.s32d[0];
+        c.rl_s.hi = (float)rl_s;
+        c.rl_s.lo = (float)(rl_s - (double)c.rl_s.hi);
+        c.w_s.hi = (float)w_s;
+        c.w_s.lo = (float)(w_s - (double)c.w_s.hi);
+    }
     // threshold f - delta in 2^-31 fixed point, clamped far outside any reachable count
     const double fd = std::min(std::max(c.fd, -1.0e9), 1.0e9);
     double fi = std::floor(fd);
@@ -237,19 +260,24 @@ void free_all(vbc_system* s)
 {
     void* bufs[] = {s->x, s->v, s->xt, s->vt, s->id, s->idt, s->pos[0], s->pos[1], s->post, s->xref,
                     s->nbr, s->nnb, s->cell_of, s->slot_of, s->order, s->cell_count, s->cell_start,
-                    s->morton_rank, s->chunk_sum, s->ds, s->sA, s->st, s->partial, s->ppairs, s->red, s->win};
+                    s->morton_rank, s->chunk_sum, s->ds, s->sA, s->st, s->partial, s->ppairs, s->red, s->win,
+                    s->e_sd, s->e_A};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (s->st_host) cudaFreeHost(s->st_host);
     if (s->red_host) cudaFreeHost(s->red_host);
     for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
     s->ev.clear();
+    for (auto& pg : s->pair_graph)
+        if (pg.exec) cudaGraphExecDestroy(pg.exec);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    if (s->body_stream) cudaStreamDestroy(s->body_stream);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
 }
 
 // ------------------------------------------------------------------ launches
 template <class M>
-int enqueue_rebuild(vbc_system* s, int iter)
+int enqueue_rebuild(vbc_system* s)
 {
     using pos_t = typename M::pos_t;
     Timed t(s, VBC_K_REBUILD);
@@ -270,7 +298,7 @@ int enqueue_rebuild(vbc_system* s, int iter)
     k_copyback<M><<<nb, TPB, 0, s->stream>>>(n, s->xt, s->vt, s->idt, (const pos_t*)s->post, s->x, s->v, s->id,
                                              pos, (pos_t*)s->xref, s->st);
     k_nlist<M><<<nb, TPB, 0, s->stream>>>(n, s->geom, pos, s->morton_rank, s->cell_start, s->rlist2_fix,
-                                          s->rlist * s->rlist, s->cap, s->nbr, s->nnb, s->st, iter);
+                                          s->rlist * s->rlist, s->cap, s->nbr, s->nnb, s->st);
     return check_launch(s, 8);
 }
 
@@ -339,16 +367,18 @@ template <class M>
 int enqueue_energy(vbc_system* s)
 {
     using pos_t = typename M::pos_t;
-    using real2 = typename M::real2;
     const int n = (int)s->n;
     {
         Timed t(s, VBC_K_ENERGY);
-        k_energy<M><<<s->nblk_energy, RED_TPB, 0, s->stream>>>(n, s->geom, s->coef, (const pos_t*)s->pos[s->cur],
-                                                                s->nbr, s->nnb, (const real2*)s->sA, s->partial,
-                                                                s->ppairs, s->st);
+        const pos_t* pos = (const pos_t*)s->pos[s->cur];
+        const int nb = blocks_for(n, TPB);
+        k_count_e<M><<<nb, TPB, 0, s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb, s->e_sd, s->st);
+        k_chain_e<M><<<nb, TPB, 0, s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb, s->e_sd, s->e_A, s->st);
+        k_energy<M><<<s->nblk_energy, RED_TPB, 0, s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb, s->e_sd,
+                                                                s->e_A, s->partial, s->ppairs, s->st);
         k_reduce_final<<<1, RED_TPB, 0, s->stream>>>(s->nblk_energy, s->partial, s->ppairs, s->red, s->st);
     }
-    return check_launch(s, 2);
+    return check_launch(s, 4);
 }
 
 int force_rebuild_flag(vbc_system* s)
@@ -398,7 +428,7 @@ int compute_impl(vbc_system* s, double* F_dev, double* n_dev, bool energy)
 {
     for (int attempt = 0;; ++attempt) {
         VBC_CUDA(cudaMemsetAsync(s->win, 0, sizeof(long long), s->stream));
-        VBC_TRY(enqueue_rebuild<M>(s, 0));
+        VBC_TRY(enqueue_rebuild<M>(s));
         VBC_TRY(enqueue_count_chain<M>(s, n_dev, true));
         StepArgs a{};
         a.F_out = F_dev;
@@ -413,6 +443,126 @@ int compute_impl(vbc_system* s, double* F_dev, double* n_dev, bool energy)
     return VBC_OK;
 }
 
+// One loop iteration with direct launches: gate, rebuild (early exit unless
+// due), count, chain, force with the epilogue of iteration `it`.
+template <class M>
+int direct_iteration(vbc_system* s, const StepArgs& a, int64_t it, int64_t nsteps)
+{
+    k_gate<<<1, 1, 0, s->stream>>>(s->st, 0, 0);
+    VBC_TRY(check_launch(s));
+    VBC_TRY(enqueue_rebuild<M>(s));
+    VBC_TRY(enqueue_count_chain<M>(s, nullptr, false));
+    if (it == 0) return enqueue_force<M, EPI_START>(s, a);
+    if (it < nsteps) return enqueue_force<M, EPI_FINISH_START>(s, a);
+    return enqueue_force<M, EPI_FINISH>(s, a);
+}
+
+int graph_error(vbc_system* s, const char* what, cudaError_t e)
+{
+    s->capturing = false;
+    return fail(VBC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Captures two FINISH_START iterations starting on position buffer c into
+// one executable graph.  Each iteration is: k_gate -> IF(rebuild due){the
+// eight rebuild kernels} -> count -> chain -> force, so steps that need no
+// rebuild launch no rebuild kernel at all.
+template <class M>
+int build_pair_graph(vbc_system* s, int c, const StepArgs& a)
+{
+    auto& pg = s->pair_graph[c];
+    if (pg.exec) {
+        cudaGraphExecDestroy(pg.exec);
+        pg.exec = nullptr;
+    }
+    if (!s->cap_stream) VBC_CUDA(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+    if (!s->body_stream) VBC_CUDA(cudaStreamCreateWithFlags(&s->body_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    VBC_CUDA(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h[2];
+    for (int k = 0; k < 2; ++k) {
+        cudaError_t e = cudaGraphConditionalHandleCreate(&h[k], g, 0, cudaGraphCondAssignDefault);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return graph_error(s, "cudaGraphConditionalHandleCreate", e);
+        }
+    }
+    const int saved_cur = s->cur;
+    cudaStream_t saved_stream = s->stream;
+    s->cur = c;
+    s->stream = s->cap_stream;
+    s->capturing = true;
+    int rc = VBC_OK;
+    cudaError_t e = cudaStreamBeginCaptureToGraph(s->cap_stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) rc = graph_error(s, "cudaStreamBeginCaptureToGraph", e);
+    for (int k = 0; k < 2 && rc == VBC_OK; ++k) {
+        k_gate<<<1, 1, 0, s->cap_stream>>>(s->st, h[k], 1);
+        cudaStreamCaptureStatus cst;
+        cudaGraph_t cg = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        const cudaGraphEdgeData* ed = nullptr;
+        size_t nd = 0;
+        e = cudaStreamGetCaptureInfo(s->cap_stream, &cst, nullptr, &cg, &deps, &ed, &nd);
+        if (e != cudaSuccess) { rc = graph_error(s, "cudaStreamGetCaptureInfo", e); break; }
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h[k];
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cn = nullptr;
+        e = cudaGraphAddNode(&cn, cg, deps, ed, nd, &cp);
+        if (e != cudaSuccess) { rc = graph_error(s, "cudaGraphAddNode(conditional)", e); break; }
+        e = cudaStreamUpdateCaptureDependencies(s->cap_stream, &cn, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (e != cudaSuccess) { rc = graph_error(s, "cudaStreamUpdateCaptureDependencies", e); break; }
+        // the rebuild kernels go into the conditional's body graph
+        e = cudaStreamBeginCaptureToGraph(s->body_stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) { rc = graph_error(s, "capture of the rebuild body", e); break; }
+        s->stream = s->body_stream;
+        rc = enqueue_rebuild<M>(s);
+        s->stream = s->cap_stream;
+        cudaGraph_t body = nullptr;
+        e = cudaStreamEndCapture(s->body_stream, &body);
+        if (rc == VBC_OK && e != cudaSuccess) rc = graph_error(s, "end of the rebuild body capture", e);
+        if (rc == VBC_OK) rc = enqueue_count_chain<M>(s, nullptr, false);
+        if (rc == VBC_OK) rc = enqueue_force<M, EPI_FINISH_START>(s, a);
+    }
+    cudaGraph_t out = nullptr;
+    e = cudaStreamEndCapture(s->cap_stream, &out);
+    if (rc == VBC_OK && e != cudaSuccess) rc = graph_error(s, "cudaStreamEndCapture", e);
+    s->capturing = false;
+    s->stream = saved_stream;
+    s->cur = saved_cur;
+    if (rc == VBC_OK) {
+        e = cudaGraphInstantiate(&pg.exec, g, 0);
+        if (e != cudaSuccess) rc = graph_error(s, "cudaGraphInstantiate", e);
+    }
+    cudaGraphDestroy(g);
+    if (rc != VBC_OK) {
+        pg.exec = nullptr;
+        return rc;
+    }
+    pg.dt = a.dt;
+    pg.c1 = a.c1;
+    pg.c2 = a.c2;
+    pg.nbr = s->nbr;
+    pg.coef_version = s->coef_version;
+    pg.unroll = s->unroll;
+    return VBC_OK;
+}
+
+template <class M>
+int launch_pair_graph(vbc_system* s, const StepArgs& a)
+{
+    auto& pg = s->pair_graph[s->cur];
+    if (!pg.exec || pg.dt != a.dt || pg.c1 != a.c1 || pg.c2 != a.c2 || pg.nbr != s->nbr ||
+        pg.coef_version != s->coef_version || pg.unroll != s->unroll)
+        VBC_TRY(build_pair_graph<M>(s, s->cur, a));
+    VBC_CUDA(cudaGraphLaunch(pg.exec, s->stream));
+    s->launches += 8;  // two gates, two count/chain/force triples (rebuild bodies counted on the device)
+    return VBC_OK;
+}
+
 template <class M>
 int steps_impl(vbc_system* s, int64_t nsteps, double dt, double kT, double gamma)
 {
@@ -424,18 +574,23 @@ int steps_impl(vbc_system* s, int64_t nsteps, double dt, double kT, double gamma
     a.c2 = std::sqrt(std::max(0.0, (1.0 - a.c1 * a.c1) * kT));
     a.seed = s->seed;
     a.half_skin2 = (float)(0.25 * s->skin * s->skin);
-    int64_t it0 = 0;  // iteration to (re)start from; 0 = the opening half step
+    // Iteration 0 opens step 0 (forces at the initial state, then B A O A);
+    // iteration it in [1, nsteps) closes step it-1 and opens step it;
+    // iteration nsteps closes the last step.  Iterations 1..nsteps-1 run in
+    // pairs through a CUDA graph unless per-kernel timing is on.
+    int64_t it0 = 0;
     for (int attempt = 0;; ++attempt) {
-        for (int64_t it = it0; it <= nsteps; ++it) {
-            VBC_TRY(enqueue_rebuild<M>(s, (int)std::min<int64_t>(it, 0x7fffffff)));
-            VBC_TRY(enqueue_count_chain<M>(s, nullptr, false));
-            a.step = s->step + it;
-            if (it == 0) {
-                VBC_TRY((enqueue_force<M, EPI_START>(s, a)));
-            } else if (it < nsteps) {
-                VBC_TRY((enqueue_force<M, EPI_FINISH_START>(s, a)));
+        k_set_iter<<<1, 1, 0, s->stream>>>(s->st, it0 - 1, s->step);
+        VBC_TRY(check_launch(s));
+        const int cur0 = s->cur;
+        int64_t it = it0;
+        while (it <= nsteps) {
+            if (s->use_graphs && !s->prof && it >= 1 && it + 1 <= nsteps - 1) {
+                VBC_TRY(launch_pair_graph<M>(s, a));  // two buffer flips: s->cur unchanged
+                it += 2;
             } else {
-                VBC_TRY((enqueue_force<M, EPI_FINISH>(s, a)));
+                VBC_TRY(direct_iteration<M>(s, a, it, nsteps));
+                ++it;
             }
         }
         VBC_TRY(read_status(s));
@@ -443,12 +598,11 @@ int steps_impl(vbc_system* s, int64_t nsteps, double dt, double kT, double gamma
         if (!s->st_host->overflow) break;
         if (attempt >= MAX_RETRIES) return fail(VBC_ERR_NLIST_OVERFLOW, "neighbour list kept overflowing");
         // The build of iteration frozen_iter overflowed: every kernel after it
-        // returned at once.  The position buffer flips only on START
-        // epilogues that ran, so recompute which one is current.
+        // returned at once.  Iterations it0 .. frozen_iter - 1 ran, each
+        // opening a step (one buffer flip) since it < nsteps there.
+        const int64_t done = (int64_t)s->st_host->frozen_iter - it0;
+        s->cur = cur0 ^ (int)(done & 1);
         it0 = s->st_host->frozen_iter;
-        const int64_t flips_enqueued = nsteps;        // iterations 0..nsteps-1 flip
-        const int64_t flips_done = it0;               // iterations 0..it0-1 ran
-        if ((flips_enqueued - flips_done) & 1) s->cur ^= 1;
         VBC_TRY(grow_list(s));
     }
     s->step += nsteps;
@@ -490,7 +644,7 @@ int build_now(vbc_system* s)
 {
     for (int attempt = 0;; ++attempt) {
         VBC_TRY(force_rebuild_flag(s));
-        VBC_TRY(enqueue_rebuild<M>(s, 0));
+        VBC_TRY(enqueue_rebuild<M>(s));
         VBC_TRY(read_status(s));
         VBC_TRY(halt_error(s));
         if (!s->st_host->overflow) return VBC_OK;
@@ -529,6 +683,7 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
         const int u = std::atoi(e);
         if (u == 1 || u == 2 || u == 4 || u == 8) s->unroll = u;
     }
+    if (const char* e = std::getenv("VBC_NO_GRAPHS")) s->use_graphs = std::atoi(e) == 0;
     s->n = cfg->n;
     s->prec = cfg->precision;
     s->prm = cfg->params;
@@ -617,6 +772,8 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     ALLOC(dalloc(s->ppairs, (size_t)s->nblk_energy));
     ALLOC(dalloc(s->red, 2));
     ALLOC(dalloc(s->win, 1));
+    ALLOC(dalloc(s->e_sd, n));
+    ALLOC(dalloc(s->e_A, n));
 #undef ALLOC
     if (cudaMallocHost((void**)&s->st_host, sizeof(Status)) != cudaSuccess ||
         cudaMallocHost((void**)&s->red_host, 2 * sizeof(double)) != cudaSuccess)
@@ -813,6 +970,7 @@ int vbc_set_params(vbc_system* s, const vbc_pair_params* p)
     VBC_CUDA(cudaStreamSynchronize(s->stream));
     s->prm = *p;
     s->coef = c;
+    s->coef_version += 1;
     return VBC_OK;
 }
 
@@ -872,6 +1030,10 @@ int vbc_profile_read(vbc_system* s, int which, double* total_ms, int64_t* launch
     return VBC_OK;
 }
 
-int64_t vbc_kernel_launches(vbc_system* s) { return s ? s->launches : 0; }
+int64_t vbc_kernel_launches(vbc_system* s)
+{
+    if (!s || check_sys(s) != VBC_OK || read_status(s) != VBC_OK) return -1;
+    return s->launches + 8 * s->st_host->graph_rebuild_runs;  // eight kernels per rebuild body run
+}
 
 }  // extern "C"

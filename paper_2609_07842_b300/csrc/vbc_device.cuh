@@ -1,7 +1,7 @@
 // vbc_device.cuh -- device-side types and per-pair arithmetic of the VBC.
 //
 // Positions live on the device as fixed-point fractions of the box edge:
-// a coordinate x in [0, L) is stored as floor(x / L * 2^B) modulo 2^B, with
+// a coordinate x is stored as x / L * 2^B, rounded, modulo 2^B, with
 // B = 32 (FP32-split mode, int4 per particle) or B = 64 (FP64 mode, 32-byte
 // record).  The difference of two such words, read as a signed integer, is
 // the minimum-image separation in units of L / 2^B, so the periodic wrap
@@ -30,6 +30,11 @@ struct Geom {
     int ncell;
 };
 
+// Unevaluated sum hi + lo of two floats (see the two-float helpers below).
+struct f2x {
+    float hi, lo;
+};
+
 // Pair parameters with derived constants (Eqs. softcore, omega, Psidelta).
 struct Coef {
     // FP64 copies
@@ -44,6 +49,7 @@ struct Coef {
     float Ea4hf;   // 4 E_a / h
     // fixed-point radii (units (L/2^32)^2) and threshold for the exact counts
     unsigned long long rl2_fix, rh2_fix;
+    f2x rl_s, w_s;                    // r_l / s and (r_h - r_l) / s as two floats
     long long fd_int;                 // floor(f - delta)
     long long fd_frac_fix;            // (f - delta - fd_int) * 2^31, rounded
 };
@@ -63,6 +69,9 @@ struct Status {
     long long rebuilds; // builds so far
     long long in_window;// particles inside the switching window at the last count
     long long pairs;    // pairs with r < r_c at the last energy evaluation
+    long long iter;     // loop iteration now running (advanced by k_gate)
+    long long step_base;// noise counter of iteration 0 of the current call
+    long long graph_rebuild_runs;  // rebuild bodies a graph conditional executed
 };
 
 // ---------------------------------------------------------------- Philox4x32-10
@@ -152,12 +161,13 @@ struct ModeF32 {
     {
         return (uint32_t)(a == 0 ? p.x : (a == 1 ? p.y : p.z));
     }
-    // fixed-point word of an unwrapped coordinate: floor(x 2^32 / L) mod 2^32
+    // fixed-point word of an unwrapped coordinate: round(x 2^32 / L) mod 2^32
+    // (rounding to nearest halves the quantisation error of a separation)
     __device__ __forceinline__ static int4 from_x(double x, double y, double z, const Geom& g)
     {
-        return make_int4((int)(uint32_t)__double2ll_rd(x * g.inv32[0]),
-                         (int)(uint32_t)__double2ll_rd(y * g.inv32[1]),
-                         (int)(uint32_t)__double2ll_rd(z * g.inv32[2]), 0);
+        return make_int4((int)(uint32_t)__double2ll_rn(x * g.inv32[0]),
+                         (int)(uint32_t)__double2ll_rn(y * g.inv32[1]),
+                         (int)(uint32_t)__double2ll_rn(z * g.inv32[2]), 0);
     }
 };
 
@@ -210,6 +220,83 @@ __device__ __forceinline__ int3 cell_of_pos(const typename M::pos_t& p, const Ge
     return make_int3((int)(((unsigned long long)M::hi32(p, 0) * (unsigned)g.nc[0]) >> 32),
                      (int)(((unsigned long long)M::hi32(p, 1) * (unsigned)g.nc[1]) >> 32),
                      (int)(((unsigned long long)M::hi32(p, 2) * (unsigned)g.nc[2]) >> 32));
+}
+
+// ---------------------------------------------------------------- two-float arithmetic
+// Unevaluated sums hi + lo of two floats (error-free transformations of
+// Dekker and Knuth), about 48 significant bits from the FP32 pipes; B300 runs
+// FP64 at a small fraction of its FP32 rate, so the few operations that need
+// more than FP32 on the per-step path use these instead.
+__device__ __forceinline__ f2x two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ f2x fast_two_sum(float a, float b)  // |a| >= |b|
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ f2x two_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ f2x f2x_add(f2x a, f2x b)
+{
+    f2x s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ f2x f2x_mul(f2x a, f2x b)
+{
+    f2x p = two_prod(a.hi, b.hi);
+    const float c = __fmaf_rn(a.hi, b.lo, __fmul_rn(a.lo, b.hi));
+    return fast_two_sum(p.hi, __fadd_rn(p.lo, c));
+}
+// Exact two-float value of an unsigned integer below 2^62.
+__device__ __forceinline__ f2x f2x_from_u64(unsigned long long v)
+{
+    const float hi = __ull2float_rn(v);
+    const long long rest = (long long)v - (long long)__float2ull_rn(hi);
+    return {hi, __ll2float_rn(rest)};
+}
+
+// omega(r; r_l, r_h) * 2^31, rounded to an integer, for a separation inside
+// the counting window.  Inputs are exact integers in units of s = L / 2^32:
+// r2 = r^2 / s^2 and D = (r^2 - r_l^2) / s^2; rl_s = r_l / s and w_s =
+// (r_h - r_l) / s are two-float constants.  With
+//   t = (r - r_l) / w = (r^2 - r_l^2) / ((r + r_l) w)
+// the cancellation of r - r_l happens in exact integers, and every later
+// step keeps about 48 bits, so the result is the rounded weight of the
+// fixed-point separation.
+__device__ __forceinline__ unsigned long long window_weight_fix31(unsigned long long r2,
+                                                                  unsigned long long D, f2x rl_s, f2x w_s)
+{
+    const f2x R2 = f2x_from_u64(r2);
+    const f2x Dd = f2x_from_u64(D);
+    // r = sqrt(r2): FP32 root plus one correction from the exact residual
+    const float rh = sqrtf(R2.hi);
+    const f2x sq = two_prod(rh, rh);
+    const float res = __fadd_rn(__fsub_rn(__fsub_rn(R2.hi, sq.hi), sq.lo), R2.lo);
+    const f2x r = fast_two_sum(rh, __fdividef(res, __fmul_rn(2.0f, rh)));
+    // den = (r + r_l) w, then t = D / den with one remainder correction
+    const f2x den = f2x_mul(f2x_add(r, rl_s), w_s);
+    const float t0 = __fdividef(Dd.hi, den.hi);
+    const f2x p = two_prod(t0, den.hi);
+    const float rem = __fsub_rn(__fadd_rn(__fsub_rn(__fsub_rn(Dd.hi, p.hi), p.lo), Dd.lo), __fmul_rn(t0, den.lo));
+    const f2x t = fast_two_sum(t0, __fdividef(rem, den.hi));
+    // omega = ((1 - t)(1 + t))^2
+    f2x a = two_sum(1.0f, -t.hi);
+    a.lo = __fsub_rn(a.lo, t.lo);
+    f2x b = two_sum(1.0f, t.hi);
+    b.lo = __fadd_rn(b.lo, t.lo);
+    const f2x q = f2x_mul(a, b);
+    const f2x w = f2x_mul(q, q);
+    long long v = __float2ll_rn(__fmul_rn(w.hi, 2147483648.0f)) + __float2ll_rn(__fmul_rn(w.lo, 2147483648.0f));
+    v = v < 0 ? 0 : (v > 2147483648LL ? 2147483648LL : v);
+    return (unsigned long long)v;
 }
 
 // ---------------------------------------------------------------- pair functions (FP64)

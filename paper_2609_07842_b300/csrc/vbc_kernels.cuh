@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(TPB) k_nlist(int n, Geom g, const typename M::
                                                const int* __restrict__ morton_rank,
                                                const int* __restrict__ cell_start, unsigned long long rl2fix,
                                                double rl2, int cap, int* __restrict__ nbr,
-                                               int* __restrict__ nnb, Status* st, int iter)
+                                               int* __restrict__ nnb, Status* st)
 {
     // k_nlist raises `overflow` itself, so it does not test it
     if (!st->rebuild || st->frozen || st->crowded) return;
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(TPB) k_nlist(int n, Geom g, const typename M::
         nnb[i] = cnt < cap ? cnt : cap;
         if (cnt > cap) {
             st->overflow = 1;
-            st->frozen_iter = iter;
+            st->frozen_iter = (int)st->iter;
         }
     }
     // block maximum and sum of the list lengths
@@ -377,12 +377,7 @@ __global__ void __launch_bounds__(TPB) k_count_f32(int n, Geom g, Coef c, const 
                 if (r2 <= c.rl2_fix) {
                     ++full;
                 } else {
-                    const float D = __ull2float_rn(r2 - c.rl2_fix) * g.s32sq;  // r^2 - r_l^2
-                    const float r = sqrtf(__ull2float_rn(r2) * g.s32sq);
-                    float t = D / ((r + c.rlf) * c.wf);                        // (r - r_l) / w
-                    t = fminf(t, 1.0f);
-                    const float qq = 1.0f - t * t;
-                    q += (unsigned long long)__float2uint_rn(qq * qq * 2147483648.0f);
+                    q += window_weight_fix31(r2, r2 - c.rl2_fix, c.rl_s, c.w_s);
                 }
             }
         });
@@ -476,7 +471,6 @@ struct StepArgs {
     double* F_out;        // forces in caller order [n][3], or null (EPI_FORCE)
     double dt, c1, c2;    // BAOAB constants: c1 = exp(-gamma dt), c2 = sqrt((1 - c1^2) kT)
     unsigned long long seed;
-    long long step;       // noise counter of the step being started
     float half_skin2;     // (skin / 2)^2
 };
 
@@ -557,11 +551,13 @@ __global__ void __launch_bounds__(TPB) k_force(int n, Geom g, Coef c, const type
         }
         if constexpr (EPI == EPI_START || EPI == EPI_FINISH_START) {
             double z[3];
+            // noise counter of the step this iteration starts
+            const unsigned long long nstep = (unsigned long long)(st->step_base + st->iter);
             if constexpr (M::fp64) {
-                const double3 xi = langevin_normals_d(a.seed, (unsigned long long)a.step, (uint32_t)id[i]);
+                const double3 xi = langevin_normals_d(a.seed, nstep, (uint32_t)id[i]);
                 z[0] = xi.x; z[1] = xi.y; z[2] = xi.z;
             } else {
-                const float3 xi = langevin_normals(a.seed, (unsigned long long)a.step, (uint32_t)id[i]);
+                const float3 xi = langevin_normals(a.seed, nstep, (uint32_t)id[i]);
                 z[0] = xi.x; z[1] = xi.y; z[2] = xi.z;
             }
 #pragma unroll
@@ -600,12 +596,63 @@ __global__ void __launch_bounds__(TPB) k_force(int n, Geom g, Coef c, const type
 }
 
 // ================================================================ FP64 energy / virial
+// Requested energies are held to 1e-9 relative, which needs the switching
+// factors to FP64 accuracy: the counts, s, s' and A are recomputed here in
+// FP64 from the exact fixed-point separations (these kernels run only when U
+// or W is asked for, never inside the step loop).
+template <class M>
+__global__ void __launch_bounds__(TPB) k_count_e(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
+                                                 const int* __restrict__ nbr, const int* __restrict__ nnb,
+                                                 double2* __restrict__ sd, const Status* st)
+{
+    if (halted(st)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const typename M::pos_t pi = pos[i];
+    const int m = nnb[i];
+    double acc = 0.0;
+    for (int k = 0; k < m; ++k) {
+        double dx, dy, dz;
+        M::delta64(pi, pos[nbr[(size_t)k * n + i]], g, dx, dy, dz);
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < c.rh2) acc += r2 <= c.rl2 ? 1.0 : omega_d(sqrt(r2), c.r_l, c.r_h);
+    }
+    sd[i] = make_double2(omega_d(acc, c.fd, c.fd + 1.0), domega_d(acc, c.fd, c.fd + 1.0));
+}
+
+template <class M>
+__global__ void __launch_bounds__(TPB) k_chain_e(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
+                                                 const int* __restrict__ nbr, const int* __restrict__ nnb,
+                                                 const double2* __restrict__ sd, double* __restrict__ Ad,
+                                                 const Status* st)
+{
+    if (halted(st)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double dsi = sd[i].y;
+    if (dsi == 0.0) {
+        Ad[i] = 0.0;
+        return;
+    }
+    const typename M::pos_t pi = pos[i];
+    const int m = nnb[i];
+    double acc = 0.0;
+    for (int k = 0; k < m; ++k) {
+        const int j = nbr[(size_t)k * n + i];
+        double dx, dy, dz;
+        M::delta64(pi, pos[j], g, dx, dy, dz);
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 > c.rr2 && r2 < c.ra2) acc += sd[j].x * Va_d(sqrt(r2), c);
+    }
+    Ad[i] = dsi * acc;
+}
+
 // Per-block partial sums of U = sum_{i<j} [V_r + s_i s_j V_a], W = sum_{i<j} -g r and
 // of the number of pairs with r < r_c, each pair seen from both ends (halves).
 template <class M>
 __global__ void __launch_bounds__(RED_TPB) k_energy(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
                                                     const int* __restrict__ nbr, const int* __restrict__ nnb,
-                                                    const typename M::real2* __restrict__ sA,
+                                                    const double2* __restrict__ sd, const double* __restrict__ Ad,
                                                     double* __restrict__ partial, long long* __restrict__ ppairs,
                                                     const Status* st)
 {
@@ -616,7 +663,7 @@ __global__ void __launch_bounds__(RED_TPB) k_energy(int n, Geom g, Coef c, const
     long long pairs = 0;
     if (i < n && !halted(st)) {
         const typename M::pos_t pi = pos[i];
-        const double si = (double)sA[i].x, Ai = (double)sA[i].y;
+        const double si = sd[i].x, Ai = Ad[i];
         const int m = nnb[i];
         for (int k = 0; k < m; ++k) {
             const int j = nbr[(size_t)k * n + i];
@@ -625,7 +672,7 @@ __global__ void __launch_bounds__(RED_TPB) k_energy(int n, Geom g, Coef c, const
             const double r2 = dx * dx + dy * dy + dz * dz;
             if (r2 >= c.rc2) continue;
             ++pairs;
-            const double sj = (double)sA[j].x, Aj = (double)sA[j].y;
+            const double sj = sd[j].x, Aj = Ad[j];
             const double r = sqrt(r2);
             e += 0.5 * (Vr_d(r2, c) + si * sj * Va_d(r, c));
             const double gg = dVr_over_r_d(r2, c) * r + si * sj * dVa_d(r, c) +
@@ -748,6 +795,25 @@ __global__ void __launch_bounds__(TPB) k_store_nlist(int n, int cap_out, const i
         const int mm = m < cap_out ? m : cap_out;
         for (int k = 0; k < mm; ++k) nbr_out[(size_t)o * cap_out + k] = id[nbr[(size_t)k * n + i]];
     }
+}
+
+// Opens one loop iteration: advances the device iteration counter (which
+// keys the Langevin noise) and, inside a CUDA graph, sets the conditional
+// that runs the rebuild body only when a rebuild is due.
+__global__ void k_gate(Status* st, cudaGraphConditionalHandle h, int in_graph)
+{
+    st->iter += 1;
+    if (in_graph) {
+        const bool due = st->rebuild && !halted(st);
+        if (due) st->graph_rebuild_runs += 1;
+        cudaGraphSetConditional(h, due ? 1u : 0u);
+    }
+}
+
+__global__ void k_set_iter(Status* st, long long iter, long long step_base)
+{
+    st->iter = iter;
+    st->step_base = step_base;
 }
 
 __global__ void k_iota(int n, int* __restrict__ id)

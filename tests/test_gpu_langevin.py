@@ -117,8 +117,11 @@ def test_checkpoint_restart_fp64():
 
 
 def test_equipartition():
-    """Langevin at kT = 1.2: <KE>/N -> 3/2 kT (FP32 split, 8000 particles)."""
-    pos, vel, L, p = _system(8000, 0.5, seed=7, E_a=8.0, q=0.5)
+    """Langevin at kT = 1.2: <KE>/N -> 3/2 kT (FP32 split, 8000 particles of the
+    throughput workload: rho = 0.5, E_a = 8, valency 2, which relaxes quickly)."""
+    pos, L = inputs.uniform_positions(8000, 0.5, seed=7)
+    vel = inputs.maxwell_velocities(8000, 1.2, seed=8)
+    p = Params(E_a=8.0, f=2.0)
     kT = 1.2
     with vbc.System(pos, L, _vp(p), vel=vel, seed=2) as s:
         s.step(1000, 0.005, kT, 1.0)
@@ -153,7 +156,34 @@ def test_nve_energy_conservation(prec):
 def test_kernel_launch_accounting():
     pos, vel, L, p = _system(2000, 0.5, seed=9)
     with vbc.System(pos, L, _vp(p), vel=vel) as s:
+        # direct launches (per-kernel timing on): one iteration counter reset, then per
+        # iteration a gate, 8 rebuild kernels (returning at once when no rebuild is due),
+        # count, chain and force
+        s.profile(True)
         before = s.kernel_launches()
         s.step(10, 0.005, 1.0, 1.0)
-        # per iteration: 8 rebuild kernels (early-exit when not due) + count + chain + force
-        assert s.kernel_launches() - before == 11 * 11
+        assert s.kernel_launches() - before == 1 + 11 * 12
+        s.profile(False)
+        # graphs: iterations 1..8 run as four two-step graphs of 8 kernels, plus 8 kernels
+        # for every rebuild the graphs' conditionals executed
+        before = s.kernel_launches()
+        s.step(10, 0.005, 1.0, 1.0)
+        d = s.kernel_launches() - before
+        assert d >= 1 + 3 * 12 + 4 * 8 and (d - (1 + 3 * 12 + 4 * 8)) % 8 == 0
+
+
+@pytest.mark.parametrize("prec", [F32, F64])
+def test_graph_and_direct_launches_agree_bitwise(prec):
+    """The two-step CUDA graphs (conditional rebuild body) and plain launches run the
+    same kernels on the same data: trajectories are bitwise equal, rebuilds included."""
+    pos, vel, L, p = _system(3000, 0.5, seed=10)
+    outs = []
+    for direct in (False, True):
+        with vbc.System(pos, L, _vp(p), vel=vel, seed=4, precision=prec) as s:
+            if direct:
+                s.profile(True, 1 << 14)
+            s.step(61, 0.005, 1.0, 1.0)
+            outs.append(s.get_state())
+            st = s.stats()
+    assert st.rebuilds >= 3
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])

@@ -67,7 +67,8 @@ def compare(pos, L, p: Params, prec, mode=0, min_window=0.0, ref=None, nlist_cap
 def test_uniform_rho05_quantile_valency(prec, q):
     pos, L = inputs.uniform_positions(1000, 0.5, seed=1)
     p = with_quantile_valency(pos, L, Params(E_a=5.0), q)
-    compare(pos, L, p, prec, min_window=0.1)
+    # counts spread with a standard deviation near 3, so a unit window holds ~10%
+    compare(pos, L, p, prec, min_window=0.05)
 
 
 @pytest.mark.parametrize("prec", [F32, F64])
