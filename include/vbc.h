@@ -181,6 +181,38 @@ int vbc_profile_read(vbc_system* sys, int which, double* total_ms, int64_t* laun
 /* Number of kernel launches the library has issued (all kinds) since creation. */
 int64_t vbc_kernel_launches(vbc_system* sys);
 
+/*
+ * Force evaluation that allocates nothing (the paper has no counterpart: this
+ * is a deployment aid).  Some callers cannot call cudaMalloc -- code running
+ * under another framework's allocator or fixed memory budget, real-time loops
+ * that must not pay an allocation's latency or risk its failure, plug-ins that
+ * are handed device buffers but may not create their own.  This call needs no
+ * vbc_system: it evaluates the counts and forces of one small system with the
+ * same FP32-split arithmetic as vbc_compute_forces (all pairs instead of a
+ * neighbour list), keeping the scratch that its passes exchange in one
+ * file-scope device array of VBC_NOALLOC_MAX_N * 28 bytes (448 KiB).  Every
+ * GPU that loads the library holds that array until the process exits.
+ *
+ *   n       1 <= n <= VBC_NOALLOC_MAX_N (larger n returns VBC_ERR_INVALID_ARG)
+ *   box     [3] host array, a cube of edge >= 2 max(r_r, r_a, r_h)
+ *   pos     [n][3] device array of positions (any periodic image)
+ *   params  host pointer to the pair parameters
+ *   F       [n][3] device array, receives the forces
+ *   counts  [n] device array for n_i, or NULL
+ *   stream  cudaStream_t to run on (NULL = default stream); returns after it finishes
+ *
+ * The first call on a device looks up the device address of the scratch array
+ * (once per device, with that device current); make that first call before any
+ * stream capture.  Calls never call cudaMalloc, cudaFree or an allocating
+ * library routine.  All calls share the one array: each call writes every
+ * scratch entry it reads, so nothing carries over from a previous call, but
+ * calls whose work overlaps on the GPU (two streams, two host threads) race
+ * with each other and must be serialised by the caller.
+ */
+#define VBC_NOALLOC_MAX_N 16384
+int vbc_compute_forces_noalloc(int32_t n, const double* box, const double* pos, const vbc_pair_params* params,
+                               double* F, double* counts, void* stream);
+
 /* Release everything the system owns.  NULL is accepted. */
 void vbc_destroy(vbc_system* sys);
 

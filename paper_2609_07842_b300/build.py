@@ -2,8 +2,9 @@
 
     python -m paper_2609_07842_b300.build
 
-The library is a single translation unit (csrc/vbc_api.cu including the
-kernels); the C ABI it exports is declared in include/vbc.h.
+The library is built from csrc/vbc_api.cu (runtime, C ABI and, through its
+includes, the kernels) and csrc/vbc_noalloc.cu (the allocation-free
+evaluation); the C ABI it exports is declared in include/vbc.h.
 """
 from __future__ import annotations
 
@@ -13,8 +14,9 @@ import sys
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
-SRC = os.path.join(PKG, "csrc", "vbc_api.cu")
-DEPS = [os.path.join(PKG, "csrc", f) for f in ("vbc_api.cu", "vbc_kernels.cuh", "vbc_device.cuh")] + [
+SRCS = [os.path.join(PKG, "csrc", f) for f in ("vbc_api.cu", "vbc_noalloc.cu")]
+DEPS = [os.path.join(PKG, "csrc", f) for f in ("vbc_api.cu", "vbc_noalloc.cu", "vbc_kernels.cuh",
+                                               "vbc_device.cuh")] + [
     os.path.join(ROOT, "include", "vbc.h")]
 LIB = os.path.join(PKG, "libvbc.so")
 
@@ -39,7 +41,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         os.path.getmtime(d) > os.path.getmtime(LIB) for d in DEPS)
     if stale:
         tmp = LIB + ".tmp%d" % os.getpid()
-        cmd = [nvcc(), *NVCC_FLAGS, "-I" + os.path.join(ROOT, "include"), "-o", tmp, SRC]
+        cmd = [nvcc(), *NVCC_FLAGS, "-I" + os.path.join(ROOT, "include"), "-o", tmp, *SRCS]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
             print(" ".join(cmd), file=sys.stderr)

@@ -655,6 +655,12 @@ int build_now(vbc_system* s)
 
 }  // namespace
 
+// Lets the other translation unit of the library (vbc_noalloc.cu) report
+// through vbc_last_error(); not exported.
+namespace vbc_detail {
+__attribute__((visibility("hidden"))) int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace vbc_detail
+
 // =================================================================== C ABI
 extern "C" {
 

@@ -31,7 +31,11 @@ K_REBUILD, K_COUNT, K_CHAIN, K_FORCE, K_ENERGY = range(5)
 EXPORTS = ("vbc_create_system", "vbc_build_neighbors", "vbc_compute_forces", "vbc_get_switch",
            "vbc_get_neighbors",
            "vbc_step_langevin", "vbc_get_state", "vbc_set_state", "vbc_set_params", "vbc_get_stats",
-           "vbc_profile", "vbc_profile_read", "vbc_kernel_launches", "vbc_destroy", "vbc_last_error")
+           "vbc_profile", "vbc_profile_read", "vbc_kernel_launches", "vbc_destroy", "vbc_last_error",
+           "vbc_compute_forces_noalloc")
+
+#: largest n accepted by compute_forces_noalloc (size of its static device scratch)
+NOALLOC_MAX_N = 16384
 
 
 class VBCError(RuntimeError):
@@ -87,6 +91,9 @@ def load() -> ctypes.CDLL:
     L.vbc_kernel_launches.restype = i64
     L.vbc_destroy.argtypes = [vp]
     L.vbc_destroy.restype = None
+    L.vbc_compute_forces_noalloc.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double), vp,
+                                             ctypes.POINTER(PairParams), vp, vp, vp]
+    L.vbc_compute_forces_noalloc.restype = i32
     L.vbc_last_error.argtypes = []
     L.vbc_last_error.restype = ctypes.c_char_p
     for name in ("vbc_create_system", "vbc_build_neighbors", "vbc_compute_forces", "vbc_get_switch",
@@ -274,3 +281,21 @@ class System:
 
     def kernel_launches(self) -> int:
         return int(load().vbc_kernel_launches(self._h))
+
+
+def compute_forces_noalloc(pos, box: float, prm: PairParams, F, counts=None, stream=None):
+    """Counts and forces of one small system without any device allocation
+    (vbc_compute_forces_noalloc).  pos [n,3], F [n,3] and counts [n] are CUDA
+    float64 tensors; the library's static scratch holds at most NOALLOC_MAX_N
+    particles.  Meant for callers that cannot allocate device memory."""
+    import torch
+    for t in (pos, F) + ((counts,) if counts is not None else ()):
+        if not (_is_torch(t) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise TypeError("pos, F and counts must be contiguous CUDA float64 tensors")
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    b = (ctypes.c_double * 3)(*np.broadcast_to(np.asarray(box, dtype=np.float64), (3,)))
+    _check(load().vbc_compute_forces_noalloc(int(pos.shape[0]), b, ctypes.c_void_p(pos.data_ptr()),
+                                             ctypes.byref(prm), ctypes.c_void_p(F.data_ptr()),
+                                             ctypes.c_void_p(counts.data_ptr()) if counts is not None else None,
+                                             ctypes.c_void_p(stream) if stream else None))
