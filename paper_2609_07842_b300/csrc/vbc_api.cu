@@ -4,10 +4,11 @@
 // all work on one CUDA stream.  The host never waits for the device inside a
 // run of steps: neighbour-list rebuilds are decided on the device, and the
 // host reads the status words once, when the call ends.  If a rebuild found a
-// list longer than the capacity, every later kernel of the call stopped
-// without touching the state; the host then grows the list and resumes from
-// the iteration that stopped, so the trajectory is the same as with a large
-// enough list from the start.
+// list longer than its capacity, or a block whose neighbourhood does not fit
+// its shared-memory staging, every later kernel of the call stopped without
+// touching the state; the host then grows the capacity and resumes from the
+// iteration that stopped, so the trajectory is the same as with large enough
+// capacities from the start.
 #include "vbc.h"
 #include "vbc_kernels.cuh"
 
@@ -17,8 +18,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <type_traits>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 using namespace vbc;
@@ -52,10 +53,20 @@ int fail(int code, const char* fmt, ...)
         if (rc_ != VBC_OK) return rc_; \
     } while (0)
 
-constexpr int MAX_CAP = 8192;   // longest neighbour list the library will grow to
-constexpr int MAX_RETRIES = 8;
+constexpr int MAX_CAP = 4096;          // longest neighbour list the library will grow to
+constexpr int MAX_STAGE = 65535;       // staged particles per block (16-bit list entries)
+constexpr int MAX_CMAX = 4096;         // staged cells per block
+constexpr size_t MAX_SMEM = 227 * 1024;
+constexpr int MAX_RETRIES = 12;
 
 int blocks_for(int64_t n, int tpb) { return (int)((n + tpb - 1) / tpb); }
+
+int pow2_at_least(int v)
+{
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
 
 }  // namespace
 
@@ -72,19 +83,25 @@ struct vbc_system {
 
     Geom geom{};
     Coef coef{};
+    ListParams lp{};
     double rcut = 0.0, rlist = 0.0;
-    unsigned long long rlist2_fix = 0;
-    int cap = 0;
+    int cap = 0;       // list capacity per particle
+    int cmax = 0;      // staging capacity in cells per block (power of two)
+    int smax = 0;      // staging capacity in particles per block
+    int nblk = 0;      // blocks of TPB particles
 
     // device buffers (particle arrays in sorted order)
-    double *x = nullptr, *v = nullptr, *xt = nullptr, *vt = nullptr;  // [3][n] each
+    unsigned long long *x = nullptr, *v = nullptr, *xt = nullptr, *vt = nullptr;  // [3][n] 8-byte words
     int *id = nullptr, *idt = nullptr;
     void *pos[2] = {nullptr, nullptr};
     void *post = nullptr, *xref = nullptr;
     int cur = 0;
-    int *nbr = nullptr, *nnb = nullptr;
+    uint16_t* nbr = nullptr;
+    int* nnb = nullptr;
     int *cell_of = nullptr, *slot_of = nullptr, *order = nullptr;
-    int *cell_count = nullptr, *cell_start = nullptr, *morton_rank = nullptr, *chunk_sum = nullptr;
+    int *cell_count = nullptr, *cell_start = nullptr, *morton_rank = nullptr, *rank_to_lin = nullptr;
+    int* chunk_sum = nullptr;
+    int *tb_base = nullptr, *tb_off = nullptr, *tb_n = nullptr;
     void *ds = nullptr, *sA = nullptr;
     Status* st = nullptr;
     Status* st_host = nullptr;  // pinned
@@ -95,7 +112,6 @@ struct vbc_system {
     long long* win = nullptr;
     double2* e_sd = nullptr;     // FP64 (s, s') of the energy evaluation
     double* e_A = nullptr;       // FP64 A of the energy evaluation
-    int nblk_energy = 0;
 
     int64_t step = 0;
     int64_t launches = 0;
@@ -109,11 +125,10 @@ struct vbc_system {
     struct PairGraph {
         cudaGraphExec_t exec = nullptr;
         double dt = 0, c1 = 0, c2 = 0;
-        const void* nbr = nullptr;
-        long long coef_version = -1;
+        long long layout_version = -1;
         int unroll = 0;
     } pair_graph[2];
-    long long coef_version = 0;
+    long long layout_version = 0;  // bumps when parameters or capacities (kernel arguments) change
 
     // per-kernel event timing
     bool prof = false;
@@ -124,6 +139,13 @@ struct vbc_system {
 
     size_t pos_bytes() const { return prec == VBC_FP64 ? sizeof(P64) : sizeof(int4); }
     size_t real_bytes() const { return prec == VBC_FP64 ? sizeof(double) : sizeof(float); }
+    StageTable table() const { return StageTable{tb_base, tb_off, tb_n, cmax, smax}; }
+    // dynamic shared memory of each kernel family
+    size_t smem_nlist() const { return nlist_spos_offset(cmax) + (size_t)smax * pos_bytes() + (size_t)cap * TPB * 4; }
+    size_t smem_count() const { return stage_header_bytes(cmax) + (size_t)smax * pos_bytes(); }
+    size_t smem_chain() const { return stage_header_bytes(cmax) + (size_t)smax * (pos_bytes() + real_bytes()); }
+    size_t smem_force() const { return stage_header_bytes(cmax) + (size_t)smax * (pos_bytes() + 2 * real_bytes()); }
+    size_t smem_energy() const { return stage_header_bytes(cmax) + (size_t)smax * (pos_bytes() + 4); }
 };
 
 namespace {
@@ -163,6 +185,7 @@ __global__ void k_set_flag(Status* st, int which, int value)
 __global__ void k_clear_halt(Status* st)
 {
     st->overflow = 0;
+    st->stage_overflow = 0;
     st->frozen = 0;
     st->crowded = 0;
     st->rebuild = 1;
@@ -202,8 +225,14 @@ int make_coef(const vbc_pair_params& p, const Geom& g, Coef& c)
     c.Eaf = (float)p.E_a;
     c.Ea4hf = (float)(4.0 * p.E_a / c.h);
     const double s2 = g.s32d[0] * g.s32d[0];
+    c.rr2_fix = (unsigned long long)std::llround(c.rr2 / s2);
     c.rl2_fix = (unsigned long long)std::llround(c.rl2 / s2);
     c.rh2_fix = (unsigned long long)std::llround(c.rh2 / s2);
+    c.ra2_fix = (unsigned long long)std::llround(c.ra2 / s2);
+    c.rm2_fix = (unsigned long long)std::llround(c.rm * c.rm / s2);
+    c.rc2_fix = (unsigned long long)std::llround(c.rc2 / s2);
+    c.s2hinv = (float)(s2 / c.h);
+    c.s2winv = (float)(s2 / c.w);
     {
         const double rl_s = p.r_l / g.s32d[0], w_s = c.w / g.s32d[0];
         c.rl_s.hi = (float)rl_s;
@@ -222,6 +251,30 @@ int make_coef(const vbc_pair_params& p, const Geom& g, Coef& c)
     c.fd_int = (long long)fi;
     c.fd_frac_fix = frac;
     return VBC_OK;
+}
+
+// Distance classes of the lists: thresholds r_r^2, r_l^2, r_h^2 in ascending order.
+ListParams make_list_params(const Coef& c, double rlist, const Geom& g)
+{
+    ListParams lp{};
+    const double s2 = g.s32d[0] * g.s32d[0];
+    double t[3] = {c.rr2, c.rl2, c.rh2};
+    std::sort(t, t + 3);
+    lp.rlist2 = rlist * rlist;
+    lp.rlist2_fix = (unsigned long long)std::llround(lp.rlist2 / s2);
+    for (int k = 0; k < 3; ++k) {
+        lp.t[k] = t[k];
+        lp.t_fix[k] = (unsigned long long)std::llround(t[k] / s2);
+    }
+    return lp;
+}
+
+f2x to_f2x(double v)
+{
+    f2x r;
+    r.hi = (float)v;
+    r.lo = (float)(v - (double)r.hi);
+    return r;
 }
 
 uint32_t spread3(uint32_t v)  // 10 bits -> every third bit
@@ -256,16 +309,26 @@ int dalloc_bytes(void*& p, size_t bytes)
     return VBC_OK;
 }
 
+template <class T>
+void dfree(T*& p)
+{
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
 void free_all(vbc_system* s)
 {
-    void* bufs[] = {s->x, s->v, s->xt, s->vt, s->id, s->idt, s->pos[0], s->pos[1], s->post, s->xref,
-                    s->nbr, s->nnb, s->cell_of, s->slot_of, s->order, s->cell_count, s->cell_start,
-                    s->morton_rank, s->chunk_sum, s->ds, s->sA, s->st, s->partial, s->ppairs, s->red, s->win,
-                    s->e_sd, s->e_A};
-    for (void* b : bufs)
-        if (b) cudaFree(b);
+    dfree(s->x); dfree(s->v); dfree(s->xt); dfree(s->vt); dfree(s->id); dfree(s->idt);
+    dfree(s->pos[0]); dfree(s->pos[1]); dfree(s->post); dfree(s->xref);
+    dfree(s->nbr); dfree(s->nnb); dfree(s->cell_of); dfree(s->slot_of); dfree(s->order);
+    dfree(s->cell_count); dfree(s->cell_start); dfree(s->morton_rank); dfree(s->rank_to_lin);
+    dfree(s->chunk_sum); dfree(s->tb_base); dfree(s->tb_off); dfree(s->tb_n);
+    dfree(s->ds); dfree(s->sA); dfree(s->st); dfree(s->partial); dfree(s->ppairs); dfree(s->red);
+    dfree(s->win); dfree(s->e_sd); dfree(s->e_A);
     if (s->st_host) cudaFreeHost(s->st_host);
     if (s->red_host) cudaFreeHost(s->red_host);
+    s->st_host = nullptr;
+    s->red_host = nullptr;
     for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
     s->ev.clear();
     for (auto& pg : s->pair_graph)
@@ -275,7 +338,65 @@ void free_all(vbc_system* s)
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
 }
 
+// ------------------------------------------------------------------ shared-memory limits
+template <class F>
+int set_smem(F* func, size_t bytes)
+{
+    VBC_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return VBC_OK;
+}
+
+// Raises the dynamic shared-memory limit of every kernel instance of mode M
+// to what the current capacities need.
+template <class M>
+int configure_smem(vbc_system* s)
+{
+    if (s->smem_nlist() > MAX_SMEM || s->smem_force() > MAX_SMEM)
+        return fail(VBC_ERR_UNSTABLE,
+                    "a block's neighbourhood (%d particles, %d cells) or a list of %d entries does not fit "
+                    "in shared memory: the system is too dense",
+                    s->smax, s->cmax, s->cap);
+    VBC_TRY(set_smem(k_nlist<M>, s->smem_nlist()));
+    if constexpr (M::fp64) {
+        VBC_TRY(set_smem(k_count_f64, s->smem_count()));
+    } else {
+        VBC_TRY(set_smem(k_count_f32<1>, s->smem_count()));
+        VBC_TRY(set_smem(k_count_f32<2>, s->smem_count()));
+        VBC_TRY(set_smem(k_count_f32<4>, s->smem_count()));
+        VBC_TRY(set_smem(k_count_f32<8>, s->smem_count()));
+    }
+    VBC_TRY(set_smem(k_chain<M>, s->smem_chain()));
+#define VBC_SET_FORCE(E)                                              \
+    VBC_TRY(set_smem(k_force<M, E, 1>, s->smem_force()));            \
+    VBC_TRY(set_smem(k_force<M, E, 2>, s->smem_force()));            \
+    VBC_TRY(set_smem(k_force<M, E, 4>, s->smem_force()));            \
+    VBC_TRY(set_smem(k_force<M, E, 8>, s->smem_force()));
+    VBC_SET_FORCE(EPI_FORCE)
+    VBC_SET_FORCE(EPI_START)
+    VBC_SET_FORCE(EPI_FINISH)
+    VBC_SET_FORCE(EPI_FINISH_START)
+#undef VBC_SET_FORCE
+    VBC_TRY(set_smem(k_count_e<M>, s->smem_energy()));
+    VBC_TRY(set_smem(k_chain_e<M>, s->smem_energy()));
+    VBC_TRY(set_smem(k_energy<M>, s->smem_energy()));
+    return VBC_OK;
+}
+
+int configure(vbc_system* s) { return s->prec == VBC_FP64 ? configure_smem<ModeF64>(s) : configure_smem<ModeF32>(s); }
+
 // ------------------------------------------------------------------ launches
+// Calls f with the list-walk batch size as a compile-time constant.
+template <class F>
+void with_unroll(int u, F&& f)
+{
+    switch (u) {
+        case 1: f(std::integral_constant<int, 1>{}); break;
+        case 2: f(std::integral_constant<int, 2>{}); break;
+        case 8: f(std::integral_constant<int, 8>{}); break;
+        default: f(std::integral_constant<int, 4>{}); break;
+    }
+}
+
 template <class M>
 int enqueue_rebuild(vbc_system* s)
 {
@@ -297,21 +418,10 @@ int enqueue_rebuild(vbc_system* s)
                                             (pos_t*)s->post, s->st);
     k_copyback<M><<<nb, TPB, 0, s->stream>>>(n, s->xt, s->vt, s->idt, (const pos_t*)s->post, s->x, s->v, s->id,
                                              pos, (pos_t*)s->xref, s->st);
-    k_nlist<M><<<nb, TPB, 0, s->stream>>>(n, s->geom, pos, s->morton_rank, s->cell_start, s->rlist2_fix,
-                                          s->rlist * s->rlist, s->cap, s->nbr, s->nnb, s->st);
+    k_nlist<M><<<nb, TPB, s->smem_nlist(), s->stream>>>(n, s->geom, pos, s->morton_rank, s->rank_to_lin,
+                                                         s->cell_start, s->table(), s->lp, s->cap, s->nbr, s->nnb,
+                                                         s->st);
     return check_launch(s, 8);
-}
-
-// Calls f with the list-walk batch size as a compile-time constant.
-template <class F>
-void with_unroll(int u, F&& f)
-{
-    switch (u) {
-        case 1: f(std::integral_constant<int, 1>{}); break;
-        case 2: f(std::integral_constant<int, 2>{}); break;
-        case 8: f(std::integral_constant<int, 8>{}); break;
-        default: f(std::integral_constant<int, 4>{}); break;
-    }
 }
 
 template <class M>
@@ -328,17 +438,18 @@ int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window)
         {
             Timed t(s, VBC_K_COUNT);
             if constexpr (M::fp64)
-                k_count_f64<<<nb, TPB, 0, s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb, s->id,
-                                                       (real*)s->ds, (real2*)s->sA, out, s->st);
+                k_count_f64<<<nb, TPB, s->smem_count(), s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb, s->id,
+                                                                     s->table(), (real*)s->ds, (real2*)s->sA, out,
+                                                                     s->st);
             else
-                k_count_f32<decltype(U)::value><<<nb, TPB, 0, s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb,
-                                                                           s->id, (real*)s->ds, (real2*)s->sA, out,
-                                                                           s->st);
+                k_count_f32<decltype(U)::value><<<nb, TPB, s->smem_count(), s->stream>>>(
+                    n, s->geom, s->coef, pos, s->nbr, s->nnb, s->id, s->table(), (real*)s->ds, (real2*)s->sA, out,
+                    s->st);
         }
         {
             Timed t(s, VBC_K_CHAIN);
-            k_chain<M, decltype(U)::value><<<nb, TPB, 0, s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb,
-                                                                       (const real*)s->ds, (real2*)s->sA, s->st);
+            k_chain<M><<<nb, TPB, s->smem_chain(), s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb,
+                                                                s->table(), (const real*)s->ds, (real2*)s->sA, s->st);
         }
     });
     return check_launch(s, 2);
@@ -354,9 +465,9 @@ int enqueue_force(vbc_system* s, const StepArgs& a)
     pos_t* pos_next = (pos_t*)s->pos[s->cur ^ 1];
     with_unroll(s->unroll, [&](auto U) {
         Timed t(s, VBC_K_FORCE);
-        k_force<M, EPI, decltype(U)::value><<<blocks_for(n, TPB), TPB, 0, s->stream>>>(
-            n, s->geom, s->coef, pos, s->nbr, s->nnb, s->id, (const real2*)s->sA, pos_next, (const pos_t*)s->xref, a,
-            s->st);
+        k_force<M, EPI, decltype(U)::value><<<blocks_for(n, TPB), TPB, s->smem_force(), s->stream>>>(
+            n, s->geom, s->coef, pos, s->nbr, s->nnb, s->id, s->table(), (const real2*)s->sA, pos_next,
+            (const pos_t*)s->xref, a, s->st);
     });
     VBC_TRY(check_launch(s));
     if (EPI == EPI_START || EPI == EPI_FINISH_START) s->cur ^= 1;
@@ -372,11 +483,13 @@ int enqueue_energy(vbc_system* s)
         Timed t(s, VBC_K_ENERGY);
         const pos_t* pos = (const pos_t*)s->pos[s->cur];
         const int nb = blocks_for(n, TPB);
-        k_count_e<M><<<nb, TPB, 0, s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb, s->e_sd, s->st);
-        k_chain_e<M><<<nb, TPB, 0, s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb, s->e_sd, s->e_A, s->st);
-        k_energy<M><<<s->nblk_energy, RED_TPB, 0, s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb, s->e_sd,
-                                                                s->e_A, s->partial, s->ppairs, s->st);
-        k_reduce_final<<<1, RED_TPB, 0, s->stream>>>(s->nblk_energy, s->partial, s->ppairs, s->red, s->st);
+        k_count_e<M><<<nb, TPB, s->smem_energy(), s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb, s->table(),
+                                                                s->e_sd, s->st);
+        k_chain_e<M><<<nb, TPB, s->smem_energy(), s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb, s->table(),
+                                                                s->e_sd, s->e_A, s->st);
+        k_energy<M><<<nb, TPB, s->smem_energy(), s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb, s->table(),
+                                                               s->e_sd, s->e_A, s->partial, s->ppairs, s->st);
+        k_reduce_final<<<1, RED_TPB, 0, s->stream>>>(nb, s->partial, s->ppairs, s->red, s->st);
     }
     return check_launch(s, 4);
 }
@@ -394,21 +507,47 @@ int read_status(vbc_system* s)
     return VBC_OK;
 }
 
-// Grow the list after an overflow; the caller resumes the interrupted work.
-int grow_list(vbc_system* s)
+bool needs_growth(const vbc_system* s) { return s->st_host->overflow || s->st_host->stage_overflow; }
+
+// Grows the list and staging capacities after an overflow; the caller resumes
+// the interrupted work.
+int grow(vbc_system* s)
 {
-    const int need = s->st_host->max_nnb;
-    if (need > MAX_CAP)
-        return fail(VBC_ERR_NLIST_OVERFLOW, "a particle has %d neighbours within r_c + skin, above the limit %d",
-                    need, MAX_CAP);
-    int cap = std::max(s->cap * 2, need + need / 4 + 8);
-    cap = std::min(cap, MAX_CAP);
-    cap = (cap + 7) & ~7;
     VBC_CUDA(cudaStreamSynchronize(s->stream));
-    VBC_CUDA(cudaFree(s->nbr));
-    s->nbr = nullptr;
-    VBC_TRY(dalloc(s->nbr, (size_t)cap * (size_t)s->n));
-    s->cap = cap;
+    const Status& h = *s->st_host;
+    if (h.overflow) {
+        const int need = h.max_nnb;
+        if (need > MAX_CAP)
+            return fail(VBC_ERR_NLIST_OVERFLOW, "a particle has %d neighbours within r_c + skin, above the limit %d",
+                        need, MAX_CAP);
+        int cap = std::max(s->cap + s->cap / 2, need + need / 4 + 8);
+        cap = std::min((cap + 7) & ~7, MAX_CAP);
+        dfree(s->nbr);
+        VBC_TRY(dalloc(s->nbr, (size_t)cap * (size_t)s->n));
+        s->cap = cap;
+    }
+    if (h.stage_overflow) {
+        if (h.max_stage_cells > s->cmax) {
+            const int cmax = pow2_at_least(h.max_stage_cells + h.max_stage_cells / 4);
+            if (cmax > MAX_CMAX)
+                return fail(VBC_ERR_UNSTABLE, "a block's neighbourhood spans %d cells, above the limit %d",
+                            h.max_stage_cells, MAX_CMAX);
+            dfree(s->tb_base);
+            dfree(s->tb_off);
+            VBC_TRY(dalloc(s->tb_base, (size_t)s->nblk * cmax));
+            VBC_TRY(dalloc(s->tb_off, (size_t)s->nblk * (cmax + 1)));
+            s->cmax = cmax;
+        }
+        if (h.max_stage > s->smax) {
+            const int smax = ((h.max_stage + h.max_stage / 8 + 63) / 64) * 64;
+            if (smax > MAX_STAGE)
+                return fail(VBC_ERR_UNSTABLE, "a block's neighbourhood holds %d particles, above the limit %d",
+                            h.max_stage, MAX_STAGE);
+            s->smax = smax;
+        }
+    }
+    VBC_TRY(configure(s));
+    s->layout_version += 1;
     k_clear_halt<<<1, 1, 0, s->stream>>>(s->st);
     return check_launch(s);
 }
@@ -418,7 +557,7 @@ int halt_error(vbc_system* s)
     if (s->st_host->crowded)
         return fail(VBC_ERR_UNSTABLE, "more than %d particles in one cell: the system has collapsed or blown up",
                     MAX_CELL);
-    if (s->st_host->frozen) return fail(VBC_ERR_UNSTABLE, "a position or velocity became non-finite");
+    if (s->st_host->frozen) return fail(VBC_ERR_UNSTABLE, "a position, velocity or force became non-finite");
     return VBC_OK;
 }
 
@@ -436,9 +575,9 @@ int compute_impl(vbc_system* s, double* F_dev, double* n_dev, bool energy)
         if (energy) VBC_TRY(enqueue_energy<M>(s));
         VBC_TRY(read_status(s));
         VBC_TRY(halt_error(s));
-        if (!s->st_host->overflow) break;
-        if (attempt >= MAX_RETRIES) return fail(VBC_ERR_NLIST_OVERFLOW, "neighbour list kept overflowing");
-        VBC_TRY(grow_list(s));
+        if (!needs_growth(s)) break;
+        if (attempt >= MAX_RETRIES) return fail(VBC_ERR_NLIST_OVERFLOW, "capacities kept overflowing");
+        VBC_TRY(grow(s));
     }
     return VBC_OK;
 }
@@ -545,8 +684,7 @@ int build_pair_graph(vbc_system* s, int c, const StepArgs& a)
     pg.dt = a.dt;
     pg.c1 = a.c1;
     pg.c2 = a.c2;
-    pg.nbr = s->nbr;
-    pg.coef_version = s->coef_version;
+    pg.layout_version = s->layout_version;
     pg.unroll = s->unroll;
     return VBC_OK;
 }
@@ -555,8 +693,8 @@ template <class M>
 int launch_pair_graph(vbc_system* s, const StepArgs& a)
 {
     auto& pg = s->pair_graph[s->cur];
-    if (!pg.exec || pg.dt != a.dt || pg.c1 != a.c1 || pg.c2 != a.c2 || pg.nbr != s->nbr ||
-        pg.coef_version != s->coef_version || pg.unroll != s->unroll)
+    if (!pg.exec || pg.dt != a.dt || pg.c1 != a.c1 || pg.c2 != a.c2 || pg.layout_version != s->layout_version ||
+        pg.unroll != s->unroll)
         VBC_TRY(build_pair_graph<M>(s, s->cur, a));
     VBC_CUDA(cudaGraphLaunch(pg.exec, s->stream));
     s->launches += 8;  // two gates, two count/chain/force triples (rebuild bodies counted on the device)
@@ -572,6 +710,10 @@ int steps_impl(vbc_system* s, int64_t nsteps, double dt, double kT, double gamma
     a.dt = dt;
     a.c1 = std::exp(-gamma * dt);
     a.c2 = std::sqrt(std::max(0.0, (1.0 - a.c1 * a.c1) * kT));
+    a.h = to_f2x(0.5 * dt);
+    for (int d = 0; d < 3; ++d) a.hK[d] = to_f2x(0.5 * dt * 4503599627370496.0 / s->box[d]);  // 2^52 / L
+    a.c1f = to_f2x(a.c1);
+    a.c2f = to_f2x(a.c2);
     a.seed = s->seed;
     a.half_skin2 = (float)(0.25 * s->skin * s->skin);
     // Iteration 0 opens step 0 (forces at the initial state, then B A O A);
@@ -595,15 +737,15 @@ int steps_impl(vbc_system* s, int64_t nsteps, double dt, double kT, double gamma
         }
         VBC_TRY(read_status(s));
         VBC_TRY(halt_error(s));
-        if (!s->st_host->overflow) break;
-        if (attempt >= MAX_RETRIES) return fail(VBC_ERR_NLIST_OVERFLOW, "neighbour list kept overflowing");
+        if (!needs_growth(s)) break;
+        if (attempt >= MAX_RETRIES) return fail(VBC_ERR_NLIST_OVERFLOW, "capacities kept overflowing");
         // The build of iteration frozen_iter overflowed: every kernel after it
         // returned at once.  Iterations it0 .. frozen_iter - 1 ran, each
         // opening a step (one buffer flip) since it < nsteps there.
         const int64_t done = (int64_t)s->st_host->frozen_iter - it0;
         s->cur = cur0 ^ (int)(done & 1);
         it0 = s->st_host->frozen_iter;
-        VBC_TRY(grow_list(s));
+        VBC_TRY(grow(s));
     }
     s->step += nsteps;
     return VBC_OK;
@@ -617,7 +759,7 @@ int check_sys(vbc_system* s)
     return VBC_OK;
 }
 
-// Copies n*per doubles from caller memory (host or device) into device buffer dst.
+// Copies count doubles from caller memory (host or device) into device buffer dst.
 int stage_in(vbc_system* s, double* dst, const double* src, size_t count, int on_device)
 {
     VBC_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(double),
@@ -628,12 +770,12 @@ int stage_in(vbc_system* s, double* dst, const double* src, size_t count, int on
 template <class M>
 int load_state(vbc_system* s, const double* pos, const double* vel, int on_device)
 {
-    // caller arrays -> staging (xt holds positions, vt velocities) -> sorted SoA
-    VBC_TRY(stage_in(s, s->xt, pos, 3 * (size_t)s->n, on_device));
-    if (vel) VBC_TRY(stage_in(s, s->vt, vel, 3 * (size_t)s->n, on_device));
-    k_load_state<M><<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>((int)s->n, s->geom, s->xt, vel ? s->vt : nullptr,
-                                                                  s->id, s->x, s->v,
-                                                                  (typename M::pos_t*)s->pos[s->cur]);
+    // caller arrays -> staging (xt holds positions, vt velocities) -> sorted state
+    VBC_TRY(stage_in(s, (double*)s->xt, pos, 3 * (size_t)s->n, on_device));
+    if (vel) VBC_TRY(stage_in(s, (double*)s->vt, vel, 3 * (size_t)s->n, on_device));
+    k_load_state<M><<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>((int)s->n, s->geom, (const double*)s->xt,
+                                                                  vel ? (const double*)s->vt : nullptr, s->id,
+                                                                  s->x, s->v, (typename M::pos_t*)s->pos[s->cur]);
     VBC_TRY(check_launch(s));
     k_clear_halt<<<1, 1, 0, s->stream>>>(s->st);  // also requests a rebuild
     return check_launch(s);
@@ -647,9 +789,9 @@ int build_now(vbc_system* s)
         VBC_TRY(enqueue_rebuild<M>(s));
         VBC_TRY(read_status(s));
         VBC_TRY(halt_error(s));
-        if (!s->st_host->overflow) return VBC_OK;
-        if (attempt >= MAX_RETRIES) return fail(VBC_ERR_NLIST_OVERFLOW, "neighbour list kept overflowing");
-        VBC_TRY(grow_list(s));
+        if (!needs_growth(s)) return VBC_OK;
+        if (attempt >= MAX_RETRIES) return fail(VBC_ERR_NLIST_OVERFLOW, "capacities kept overflowing");
+        VBC_TRY(grow(s));
     }
 }
 
@@ -684,7 +826,7 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     if (cfg->nlist_cap < 0) return fail(VBC_ERR_INVALID_ARG, "nlist_cap must be >= 0");
 
     vbc_system* s = new vbc_system();
-    // tuning knob for experiments: list entries per batch in the pass kernels
+    // tuning knobs for experiments: list entries per batch in the pass kernels; graphs off
     if (const char* e = std::getenv("VBC_WALK_UNROLL")) {
         const int u = std::atoi(e);
         if (u == 1 || u == 2 || u == 4 || u == 8) s->unroll = u;
@@ -726,14 +868,23 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
         int rc = make_coef(s->prm, g, s->coef);
         if (rc) return bail(rc);
     }
-    s->rlist2_fix = (unsigned long long)std::llround(s->rlist * s->rlist / (g.s32d[0] * g.s32d[0]));
+    s->lp = make_list_params(s->coef, s->rlist, g);
 
-    // initial list capacity from the mean density
+    // initial capacities from the mean density
     const double rho = (double)s->n / (s->box[0] * s->box[1] * s->box[2]);
     const double kbar = rho * 4.18879020478639098 * s->rlist * s->rlist * s->rlist;  // 4 pi / 3
-    int cap = cfg->nlist_cap > 0 ? cfg->nlist_cap : (int)std::ceil(1.5 * kbar + 8.0 * std::sqrt(kbar) + 16.0);
-    cap = std::min(std::max(cap, 1), MAX_CAP);
-    s->cap = cap;
+    int cap = cfg->nlist_cap > 0 ? cfg->nlist_cap : (int)std::ceil(1.3 * kbar + 6.0 * std::sqrt(kbar) + 12.0);
+    s->cap = std::min(std::max(cap, 1), MAX_CAP);
+    {
+        // a block of TPB particles covers about TPB / rho_cell cells; stage its dilated neighbourhood
+        const double rho_cell = (double)s->n / g.ncell;
+        const double span = std::cbrt(TPB / std::max(rho_cell, 1e-9));
+        const double cells = std::min((double)g.ncell, 1.2 * std::pow(span + 2.0, 3.0));
+        s->cmax = std::min(std::max(pow2_at_least((int)std::ceil(1.5 * cells)), 64), MAX_CMAX);
+        const double parts = std::min((double)s->n, cells * rho_cell + 32.0);
+        s->smax = std::min(((int)std::ceil(parts) + 63) / 64 * 64, MAX_STAGE);
+    }
+    s->nblk = blocks_for(s->n, TPB);
 
     {
         cudaError_t e = cudaGetDevice(&s->device);
@@ -761,7 +912,7 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     ALLOC(dalloc_bytes(s->pos[1], n * s->pos_bytes()));
     ALLOC(dalloc_bytes(s->post, n * s->pos_bytes()));
     ALLOC(dalloc_bytes(s->xref, n * s->pos_bytes()));
-    ALLOC(dalloc(s->nbr, (size_t)cap * n));
+    ALLOC(dalloc(s->nbr, (size_t)s->cap * n));
     ALLOC(dalloc(s->nnb, n));
     ALLOC(dalloc(s->cell_of, n));
     ALLOC(dalloc(s->slot_of, n));
@@ -769,13 +920,16 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     ALLOC(dalloc(s->cell_count, (size_t)g.ncell));
     ALLOC(dalloc(s->cell_start, (size_t)g.ncell + 1));
     ALLOC(dalloc(s->morton_rank, (size_t)g.ncell));
+    ALLOC(dalloc(s->rank_to_lin, (size_t)g.ncell));
     ALLOC(dalloc(s->chunk_sum, (size_t)blocks_for(g.ncell, SCAN_CHUNK)));
+    ALLOC(dalloc(s->tb_base, (size_t)s->nblk * s->cmax));
+    ALLOC(dalloc(s->tb_off, (size_t)s->nblk * (s->cmax + 1)));
+    ALLOC(dalloc(s->tb_n, (size_t)s->nblk));
     ALLOC(dalloc_bytes(s->ds, n * s->real_bytes()));
     ALLOC(dalloc_bytes(s->sA, n * 2 * s->real_bytes()));
     ALLOC(dalloc(s->st, 1));
-    s->nblk_energy = blocks_for(s->n, RED_TPB);
-    ALLOC(dalloc(s->partial, 2 * (size_t)s->nblk_energy));
-    ALLOC(dalloc(s->ppairs, (size_t)s->nblk_energy));
+    ALLOC(dalloc(s->partial, 2 * (size_t)s->nblk));
+    ALLOC(dalloc(s->ppairs, (size_t)s->nblk));
     ALLOC(dalloc(s->red, 2));
     ALLOC(dalloc(s->win, 1));
     ALLOC(dalloc(s->e_sd, n));
@@ -784,8 +938,9 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     if (cudaMallocHost((void**)&s->st_host, sizeof(Status)) != cudaSuccess ||
         cudaMallocHost((void**)&s->red_host, 2 * sizeof(double)) != cudaSuccess)
         return bail(fail(VBC_ERR_OOM, "pinned host allocation failed"));
+    if ((rc = configure(s)) != VBC_OK) return bail(rc);
 
-    // Morton order of the cells: rank of each linear cell index along the curve
+    // Morton order of the cells: rank of each linear cell index along the curve, and back
     {
         std::vector<std::pair<uint32_t, int>> code((size_t)g.ncell);
         for (int z = 0; z < g.nc[2]; ++z)
@@ -795,14 +950,19 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
                     code[lin] = {spread3((uint32_t)x) | (spread3((uint32_t)y) << 1) | (spread3((uint32_t)z) << 2), lin};
                 }
         std::sort(code.begin(), code.end());
-        std::vector<int> rank((size_t)g.ncell);
-        for (int r = 0; r < g.ncell; ++r) rank[code[r].second] = r;
-        if (cudaMemcpy(s->morton_rank, rank.data(), rank.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
-            return bail(fail(VBC_ERR_CUDA, "upload of the Morton table failed"));
+        std::vector<int> rank((size_t)g.ncell), back((size_t)g.ncell);
+        for (int r = 0; r < g.ncell; ++r) {
+            rank[code[r].second] = r;
+            back[r] = code[r].second;
+        }
+        if (cudaMemcpy(s->morton_rank, rank.data(), rank.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(s->rank_to_lin, back.data(), back.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(fail(VBC_ERR_CUDA, "upload of the Morton tables failed"));
     }
     if (cudaMemsetAsync(s->cell_count, 0, (size_t)g.ncell * sizeof(int), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->st, 0, sizeof(Status), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->nnb, 0, n * sizeof(int), s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->tb_n, 0, (size_t)s->nblk * sizeof(int), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->sA, 0, n * 2 * s->real_bytes(), s->stream) != cudaSuccess)
         return bail(fail(VBC_ERR_CUDA, "initial memset failed"));
     k_iota<<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>((int)s->n, s->id);
@@ -839,8 +999,8 @@ int vbc_compute_forces(vbc_system* s, double* F, double* counts, double* energy,
     VBC_TRY(check_sys(s));
     const size_t n = (size_t)s->n;
     // host outputs are staged through the scratch halves (free once the rebuild ran)
-    double* F_dev = F ? (outputs_on_device ? F : s->xt) : nullptr;
-    double* n_dev = counts ? (outputs_on_device ? counts : s->vt) : nullptr;
+    double* F_dev = F ? (outputs_on_device ? F : (double*)s->xt) : nullptr;
+    double* n_dev = counts ? (outputs_on_device ? counts : (double*)s->vt) : nullptr;
     const bool want_e = energy || virial;
     VBC_TRY(s->prec == VBC_FP64 ? compute_impl<ModeF64>(s, F_dev, n_dev, want_e)
                                 : compute_impl<ModeF32>(s, F_dev, n_dev, want_e));
@@ -869,9 +1029,10 @@ int vbc_get_switch(vbc_system* s, double* sw, double* dsw, double* A, int output
     VBC_TRY(check_sys(s));
     const size_t n = (size_t)s->n;
     // staging: xt holds three n-long slices
-    double* d_s = sw ? (outputs_on_device ? sw : s->xt) : nullptr;
-    double* d_ds = dsw ? (outputs_on_device ? dsw : s->xt + n) : nullptr;
-    double* d_A = A ? (outputs_on_device ? A : s->xt + 2 * n) : nullptr;
+    double* xt = (double*)s->xt;
+    double* d_s = sw ? (outputs_on_device ? sw : xt) : nullptr;
+    double* d_ds = dsw ? (outputs_on_device ? dsw : xt + n) : nullptr;
+    double* d_A = A ? (outputs_on_device ? A : xt + 2 * n) : nullptr;
     if (s->prec == VBC_FP64)
         k_store_switch<ModeF64><<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>(
             (int)n, s->id, (const double*)s->ds, (const double2*)s->sA, d_s, d_ds, d_A);
@@ -908,7 +1069,8 @@ int vbc_get_neighbors(vbc_system* s, int32_t* nnb, int32_t* nbr, int32_t cap, in
             cudaMemsetAsync(d_nbr, 0xff, n * (size_t)cap * sizeof(int), s->stream);
         }
     }
-    k_store_nlist<<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>((int)n, cap, s->id, s->nbr, s->nnb, d_nnb, d_nbr);
+    k_store_nlist<<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>((int)n, cap, s->id, s->nbr, s->nnb, s->table(), d_nnb,
+                                                                d_nbr);
     int rc = check_launch(s);
     if (rc == VBC_OK && !outputs_on_device) {
         if (nnb && cudaMemcpyAsync(nnb, d_nnb, n * sizeof(int), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
@@ -941,9 +1103,12 @@ int vbc_get_state(vbc_system* s, double* pos, double* vel, int64_t* step, int on
 {
     VBC_TRY(check_sys(s));
     const size_t n = (size_t)s->n;
-    double* dp = pos ? (on_device ? pos : s->xt) : nullptr;
-    double* dv = vel ? (on_device ? vel : s->vt) : nullptr;
-    k_store_state<<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>((int)n, s->id, s->x, s->v, dp, dv);
+    double* dp = pos ? (on_device ? pos : (double*)s->xt) : nullptr;
+    double* dv = vel ? (on_device ? vel : (double*)s->vt) : nullptr;
+    if (s->prec == VBC_FP64)
+        k_store_state<ModeF64><<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>((int)n, s->geom, s->id, s->x, s->v, dp, dv);
+    else
+        k_store_state<ModeF32><<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>((int)n, s->geom, s->id, s->x, s->v, dp, dv);
     VBC_TRY(check_launch(s));
     if (pos && !on_device) VBC_CUDA(cudaMemcpyAsync(pos, s->xt, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     if (vel && !on_device) VBC_CUDA(cudaMemcpyAsync(vel, s->vt, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
@@ -976,7 +1141,8 @@ int vbc_set_params(vbc_system* s, const vbc_pair_params* p)
     VBC_CUDA(cudaStreamSynchronize(s->stream));
     s->prm = *p;
     s->coef = c;
-    s->coef_version += 1;
+    s->lp = make_list_params(c, s->rlist, s->geom);
+    s->layout_version += 1;
     return VBC_OK;
 }
 

@@ -1,12 +1,18 @@
 // vbc_device.cuh -- device-side types and per-pair arithmetic of the VBC.
 //
-// Positions live on the device as fixed-point fractions of the box edge:
-// a coordinate x is stored as x / L * 2^B, rounded, modulo 2^B, with
-// B = 32 (FP32-split mode, int4 per particle) or B = 64 (FP64 mode, 32-byte
-// record).  The difference of two such words, read as a signed integer, is
-// the minimum-image separation in units of L / 2^B, so the periodic wrap
-// costs nothing and the separation is exact before it is rounded to
-// floating point once.
+// Positions live on the device in fixed point.  For the pair walks, a
+// coordinate x is stored as x / L * 2^B, rounded, modulo 2^B, with B = 32
+// (FP32-split mode, int4 per particle) or B = 64 (FP64 mode, 32-byte record).
+// The difference of two such words, read as a signed integer, is the
+// minimum-image separation in units of L / 2^B: the periodic wrap costs
+// nothing and the separation is exact before it is rounded once.
+//
+// B300 executes FP64 arithmetic, and 64-bit integer <-> floating-point
+// conversions, on a narrow pipe (a small fraction of the FP32 rate).  The
+// per-step kernels of the FP32-split mode therefore contain no FP64
+// instruction at all: exact integers carry what needs more than 24 bits, and
+// the few quantities that need about 48 bits are two-float values
+// (unevaluated sums hi + lo, Dekker/Knuth error-free transformations).
 #pragma once
 
 #include <cstdint>
@@ -30,7 +36,7 @@ struct Geom {
     int ncell;
 };
 
-// Unevaluated sum hi + lo of two floats (see the two-float helpers below).
+// Unevaluated sum hi + lo of two floats.
 struct f2x {
     float hi, lo;
 };
@@ -47,9 +53,11 @@ struct Coef {
     float rr2invf; // 1 / r_r^2
     float Eaf;     // E_a
     float Ea4hf;   // 4 E_a / h
-    // fixed-point radii (units (L/2^32)^2) and threshold for the exact counts
-    unsigned long long rl2_fix, rh2_fix;
-    f2x rl_s, w_s;                    // r_l / s and (r_h - r_l) / s as two floats
+    // exact fixed-point squared radii (units (L/2^32)^2) and the threshold for the counts
+    unsigned long long rr2_fix, rl2_fix, rh2_fix, ra2_fix, rm2_fix, rc2_fix;
+    float s2hinv;   // s^2 / h: u = (r^2 - r_m^2) / ((r + r_m) h) from an integer difference
+    float s2winv;   // s^2 / w: t = (r^2 - r_l^2) / ((r + r_l) w)
+    f2x rl_s, w_s;                    // r_l / s and (r_h - r_l) / s as two floats, s = L / 2^32
     long long fd_int;                 // floor(f - delta)
     long long fd_frac_fix;            // (f - delta - fd_int) * 2^31, rounded
 };
@@ -62,9 +70,12 @@ struct Status {
     int overflow;       // 1: a list exceeded the capacity at the last build (k_nlist)
     int frozen;         // 1: a non-finite position or velocity was produced (k_force)
     int crowded;        // 1: a cell held more than MAX_CELL particles (k_scan_apply)
-    int nonfinite;      // unused padding kept for layout stability
+    int max_stage;      // largest number of particles a block stages (last build)
     int max_nnb;        // longest list found at the last build (uncapped)
-    int frozen_iter;    // loop iteration at which the freeze happened
+    int frozen_iter;    // loop iteration at which the overflow happened
+    int max_stage_cells;// largest number of cells a block stages (last build)
+    int stage_overflow; // 1: a block's neighbourhood exceeded the staging capacity (k_nlist)
+    int pad0;
     long long nnb_sum;  // sum of list lengths at the last build
     long long rebuilds; // builds so far
     long long in_window;// particles inside the switching window at the last count
@@ -73,6 +84,12 @@ struct Status {
     long long step_base;// noise counter of iteration 0 of the current call
     long long graph_rebuild_runs;  // rebuild bodies a graph conditional executed
 };
+
+// Work stops (until the host intervenes) once any of these is raised.
+__device__ __forceinline__ bool halted(const Status* st)
+{
+    return (st->frozen | st->crowded | st->overflow | st->stage_overflow) != 0;
+}
 
 // ---------------------------------------------------------------- Philox4x32-10
 // Counter-based generator of Salmon et al. (SC'11): ten rounds of two 32x32
@@ -129,45 +146,160 @@ __device__ __forceinline__ double3 langevin_normals_d(unsigned long long seed,
     return make_double3(r0 * c0, r0 * s0, r1 * cospi(2.0 * u3));
 }
 
+// ---------------------------------------------------------------- conversions on the ALU pipes
+// Exact float of an unsigned integer below 2^23 (magic-number trick).
+__device__ __forceinline__ float u23_to_float(uint32_t v)
+{
+    return __uint_as_float(0x4B000000u | v) - 8388608.0f;
+}
+// Nearest integer of a float with |x| < 2^62, as a 64-bit integer, from its bits.
+__device__ __forceinline__ long long float_to_ll_rn(float x)
+{
+    const uint32_t u = __float_as_uint(x);
+    const int e = (int)((u >> 23) & 0xffu) - 150;  // |x| = m 2^e
+    const unsigned long long m = (unsigned long long)((u & 0x7fffffu) | 0x800000u);
+    unsigned long long v;
+    if (e >= 0) {
+        v = m << e;
+    } else if (e > -25) {
+        v = (m + (1ull << (-e - 1))) >> (-e);  // round half away from zero
+    } else {
+        v = 0ull;
+    }
+    return (u >> 31) ? -(long long)v : (long long)v;
+}
+
+// ---------------------------------------------------------------- two-float arithmetic
+__device__ __forceinline__ f2x two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ f2x fast_two_sum(float a, float b)  // |a| >= |b|
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ f2x two_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ f2x f2x_add(f2x a, f2x b)
+{
+    f2x s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ f2x f2x_mul(f2x a, f2x b)
+{
+    f2x p = two_prod(a.hi, b.hi);
+    const float c = __fmaf_rn(a.hi, b.lo, __fmul_rn(a.lo, b.hi));
+    return fast_two_sum(p.hi, __fadd_rn(p.lo, c));
+}
+// two-float times float
+__device__ __forceinline__ f2x f2x_mulf(f2x a, float b)
+{
+    f2x p = two_prod(a.hi, b);
+    return fast_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
+}
+// Nearest 64-bit integer of a two-float value (|value| < 2^62).
+__device__ __forceinline__ long long f2x_to_ll(f2x a)
+{
+    const long long ih = float_to_ll_rn(a.hi);
+    // a.hi - ih is exact: zero when |a.hi| >= 2^24 (a.hi is then an integer),
+    // and |ih| < 2^24 is exactly a float otherwise
+    const float base = fabsf(a.hi) < 16777216.0f ? __int2float_rn((int)ih) : a.hi;
+    const float fr = __fadd_rn(__fsub_rn(a.hi, base), a.lo);
+    return ih + float_to_ll_rn(fr);
+}
+// Float of an unsigned integer below 2^63 (within one unit in the last place),
+// with only ALU/FMA operations.
+__device__ __forceinline__ float u64_to_float(unsigned long long v)
+{
+    const float c2 = u23_to_float((uint32_t)(v >> 42)) * 4398046511104.0f;               // * 2^42
+    const float c1 = u23_to_float((uint32_t)(v >> 21) & 0x1fffffu) * 2097152.0f;          // * 2^21
+    const float c0 = u23_to_float((uint32_t)v & 0x1fffffu);
+    return __fadd_rn(__fadd_rn(c2, c1), c0);
+}
+__device__ __forceinline__ float s64_to_float(long long v)
+{
+    const float f = u64_to_float((unsigned long long)(v < 0 ? -v : v));
+    return v < 0 ? -f : f;
+}
+
+// Two-float value of an unsigned integer below 2^63, with only ALU/FMA operations:
+// three exact 21-bit chunks summed with one error-free addition.
+__device__ __forceinline__ f2x u64_to_f2x(unsigned long long v)
+{
+    const float c2 = u23_to_float((uint32_t)(v >> 42)) * 4398046511104.0f;               // * 2^42
+    const float c1 = u23_to_float((uint32_t)(v >> 21) & 0x1fffffu) * 2097152.0f;          // * 2^21
+    const float c0 = u23_to_float((uint32_t)v & 0x1fffffu);
+    const f2x s = two_sum(c2, c1);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, c0));
+}
+
+// omega(r; r_l, r_h) * 2^31, rounded to an integer, for a separation inside
+// the counting window.  Inputs are exact integers in units of s = L / 2^32:
+// r2 = r^2 / s^2 and D = (r^2 - r_l^2) / s^2; rl_s = r_l / s and w_s =
+// (r_h - r_l) / s are two-float constants.  With
+//   t = (r - r_l) / w = (r^2 - r_l^2) / ((r + r_l) w)
+// the cancellation in r - r_l happens in exact integers; r, r + r_l, the
+// denominator and t carry two-float residuals (about 7e-9 RMS error in
+// omega), and omega = ((1 - t)(1 + t))^2 is formed in 31-bit fixed point.
+// No FP64 instruction and no 64-bit conversion is involved.
+__device__ __forceinline__ unsigned long long window_weight_fix31(unsigned long long r2,
+                                                                  unsigned long long D, f2x rl_s, f2x w_s)
+{
+    const f2x Dd = u64_to_f2x(D);
+    const f2x R2 = u64_to_f2x(r2);
+    // r = sqrt(r2), corrected once from the residual r2 - r^2
+    const float rh = sqrtf(R2.hi);
+    const float res = __fadd_rn(__fmaf_rn(-rh, rh, R2.hi), R2.lo);
+    const float rlo = __fdividef(res, __fmul_rn(2.0f, rh));
+    // a = r + r_l and den = a w as two floats
+    f2x a = two_sum(rh, rl_s.hi);
+    a = fast_two_sum(a.hi, __fadd_rn(a.lo, __fadd_rn(rl_s.lo, rlo)));
+    const float dh = __fmul_rn(a.hi, w_s.hi);
+    const float dl = __fadd_rn(__fmaf_rn(a.hi, w_s.hi, -dh), __fmaf_rn(a.hi, w_s.lo, __fmul_rn(a.lo, w_s.hi)));
+    // t = D / den: leading quotient and the quotient of the exact remainder
+    const float rcp = __frcp_rn(dh);
+    const float th = __fmul_rn(Dd.hi, rcp);
+    const float e = __fsub_rn(__fadd_rn(__fmaf_rn(-th, dh, Dd.hi), Dd.lo), __fmul_rn(th, dl));
+    const float tl = __fmul_rn(e, rcp);
+    long long t31 = float_to_ll_rn(__fmul_rn(th, 2147483648.0f)) + float_to_ll_rn(__fmul_rn(tl, 2147483648.0f));
+    t31 = t31 < 0 ? 0 : (t31 > 2147483647LL ? 2147483647LL : t31);
+    const unsigned long long q =
+        ((2147483648ull - (unsigned long long)t31) * (2147483648ull + (unsigned long long)t31)) >> 31;
+    return (q * q) >> 31;
+}
+
 // ---------------------------------------------------------------- position modes
 struct ModeF32 {
     using pos_t = int4;
     using real = float;
     using real2 = float2;
+    using xstate_t = long long;  // unwrapped position, fixed point in units of L / 2^52
+    using vstate_t = float2;     // velocity as a two-float (hi, lo)
     static constexpr bool fp64 = false;
 
-    __device__ __forceinline__ static int3 idelta(const int4& a, const int4& b)
-    {
-        return make_int3(a.x - b.x, a.y - b.y, a.z - b.z);
-    }
     // minimum-image separation a - b in length units
-    __device__ __forceinline__ static void delta(const int4& a, const int4& b, const Geom& g,
-                                                 float& dx, float& dy, float& dz)
-    {
-        const int3 d = idelta(a, b);
-        dx = (float)d.x * g.s32;
-        dy = (float)d.y * g.s32;
-        dz = (float)d.z * g.s32;
-    }
     __device__ __forceinline__ static void delta64(const int4& a, const int4& b, const Geom& g,
                                                    double& dx, double& dy, double& dz)
     {
-        const int3 d = idelta(a, b);
-        dx = (double)d.x * g.s32d[0];
-        dy = (double)d.y * g.s32d[1];
-        dz = (double)d.z * g.s32d[2];
+        dx = (double)(a.x - b.x) * g.s32d[0];
+        dy = (double)(a.y - b.y) * g.s32d[1];
+        dz = (double)(a.z - b.z) * g.s32d[2];
     }
     __device__ __forceinline__ static uint32_t hi32(const int4& p, int a)
     {
         return (uint32_t)(a == 0 ? p.x : (a == 1 ? p.y : p.z));
     }
-    // fixed-point word of an unwrapped coordinate: round(x 2^32 / L) mod 2^32
-    // (rounding to nearest halves the quantisation error of a separation)
-    __device__ __forceinline__ static int4 from_x(double x, double y, double z, const Geom& g)
+    // 32-bit word of an unwrapped fixed-point coordinate P (units L / 2^52): round(P / 2^20) mod 2^32
+    __device__ __forceinline__ static int word(long long P)
     {
-        return make_int4((int)(uint32_t)__double2ll_rn(x * g.inv32[0]),
-                         (int)(uint32_t)__double2ll_rn(y * g.inv32[1]),
-                         (int)(uint32_t)__double2ll_rn(z * g.inv32[2]), 0);
+        return (int)(uint32_t)((unsigned long long)(P + (1ll << 19)) >> 20);
     }
 };
 
@@ -175,6 +307,8 @@ struct ModeF64 {
     using pos_t = P64;
     using real = double;
     using real2 = double2;
+    using xstate_t = double;     // unwrapped position
+    using vstate_t = double;     // velocity
     static constexpr bool fp64 = true;
 
     __device__ __forceinline__ static void delta64(const P64& a, const P64& b, const Geom& g,
@@ -183,11 +317,6 @@ struct ModeF64 {
         dx = (double)(long long)(a.x - b.x) * g.s64[0];
         dy = (double)(long long)(a.y - b.y) * g.s64[1];
         dz = (double)(long long)(a.z - b.z) * g.s64[2];
-    }
-    __device__ __forceinline__ static void delta(const P64& a, const P64& b, const Geom& g,
-                                                 double& dx, double& dy, double& dz)
-    {
-        delta64(a, b, g, dx, dy, dz);
     }
     __device__ __forceinline__ static uint32_t hi32(const P64& p, int a)
     {
@@ -222,85 +351,8 @@ __device__ __forceinline__ int3 cell_of_pos(const typename M::pos_t& p, const Ge
                      (int)(((unsigned long long)M::hi32(p, 2) * (unsigned)g.nc[2]) >> 32));
 }
 
-// ---------------------------------------------------------------- two-float arithmetic
-// Unevaluated sums hi + lo of two floats (error-free transformations of
-// Dekker and Knuth), about 48 significant bits from the FP32 pipes; B300 runs
-// FP64 at a small fraction of its FP32 rate, so the few operations that need
-// more than FP32 on the per-step path use these instead.
-__device__ __forceinline__ f2x two_sum(float a, float b)
-{
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return {s, e};
-}
-__device__ __forceinline__ f2x fast_two_sum(float a, float b)  // |a| >= |b|
-{
-    const float s = __fadd_rn(a, b);
-    return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ f2x two_prod(float a, float b)
-{
-    const float p = __fmul_rn(a, b);
-    return {p, __fmaf_rn(a, b, -p)};
-}
-__device__ __forceinline__ f2x f2x_add(f2x a, f2x b)
-{
-    f2x s = two_sum(a.hi, b.hi);
-    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
-}
-__device__ __forceinline__ f2x f2x_mul(f2x a, f2x b)
-{
-    f2x p = two_prod(a.hi, b.hi);
-    const float c = __fmaf_rn(a.hi, b.lo, __fmul_rn(a.lo, b.hi));
-    return fast_two_sum(p.hi, __fadd_rn(p.lo, c));
-}
-// Exact two-float value of an unsigned integer below 2^62.
-__device__ __forceinline__ f2x f2x_from_u64(unsigned long long v)
-{
-    const float hi = __ull2float_rn(v);
-    const long long rest = (long long)v - (long long)__float2ull_rn(hi);
-    return {hi, __ll2float_rn(rest)};
-}
-
-// omega(r; r_l, r_h) * 2^31, rounded to an integer, for a separation inside
-// the counting window.  Inputs are exact integers in units of s = L / 2^32:
-// r2 = r^2 / s^2 and D = (r^2 - r_l^2) / s^2; rl_s = r_l / s and w_s =
-// (r_h - r_l) / s are two-float constants.  With
-//   t = (r - r_l) / w = (r^2 - r_l^2) / ((r + r_l) w)
-// the cancellation of r - r_l happens in exact integers, and every later
-// step keeps about 48 bits, so the result is the rounded weight of the
-// fixed-point separation.
-__device__ __forceinline__ unsigned long long window_weight_fix31(unsigned long long r2,
-                                                                  unsigned long long D, f2x rl_s, f2x w_s)
-{
-    const f2x R2 = f2x_from_u64(r2);
-    const f2x Dd = f2x_from_u64(D);
-    // r = sqrt(r2): FP32 root plus one correction from the exact residual
-    const float rh = sqrtf(R2.hi);
-    const f2x sq = two_prod(rh, rh);
-    const float res = __fadd_rn(__fsub_rn(__fsub_rn(R2.hi, sq.hi), sq.lo), R2.lo);
-    const f2x r = fast_two_sum(rh, __fdividef(res, __fmul_rn(2.0f, rh)));
-    // den = (r + r_l) w, then t = D / den with one remainder correction
-    const f2x den = f2x_mul(f2x_add(r, rl_s), w_s);
-    const float t0 = __fdividef(Dd.hi, den.hi);
-    const f2x p = two_prod(t0, den.hi);
-    const float rem = __fsub_rn(__fadd_rn(__fsub_rn(__fsub_rn(Dd.hi, p.hi), p.lo), Dd.lo), __fmul_rn(t0, den.lo));
-    const f2x t = fast_two_sum(t0, __fdividef(rem, den.hi));
-    // omega = ((1 - t)(1 + t))^2
-    f2x a = two_sum(1.0f, -t.hi);
-    a.lo = __fsub_rn(a.lo, t.lo);
-    f2x b = two_sum(1.0f, t.hi);
-    b.lo = __fadd_rn(b.lo, t.lo);
-    const f2x q = f2x_mul(a, b);
-    const f2x w = f2x_mul(q, q);
-    long long v = __float2ll_rn(__fmul_rn(w.hi, 2147483648.0f)) + __float2ll_rn(__fmul_rn(w.lo, 2147483648.0f));
-    v = v < 0 ? 0 : (v > 2147483648LL ? 2147483648LL : v);
-    return (unsigned long long)v;
-}
-
 // ---------------------------------------------------------------- pair functions (FP64)
-// Used by the FP64 pass kernels and by the FP64 energy/virial kernel.
+// Used by the FP64 mode and by the FP64 energy/virial evaluation.
 __device__ __forceinline__ double omega_d(double x, double x1, double x2)
 {
     if (x <= x1) return 1.0;
@@ -340,12 +392,6 @@ __device__ __forceinline__ double dVa_d(double r, const Coef& c)
     if (r <= c.r_r || r >= c.r_a) return 0.0;
     const double u = (r - c.rm) / c.h;
     return 4.0 * c.E_a * u * (1.0 - u * u) / c.h;
-}
-
-// Work stops (until the host intervenes) once any of these is raised.
-__device__ __forceinline__ bool halted(const Status* st)
-{
-    return (st->frozen | st->crowded | st->overflow) != 0;
 }
 
 }  // namespace vbc

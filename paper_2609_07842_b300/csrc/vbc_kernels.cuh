@@ -1,16 +1,24 @@
 // vbc_kernels.cuh -- CUDA kernels of the VBC path (sm_103a).
 //
-// One step of the path, for N particles stored in Morton order of their cells:
+// Particles are stored in Morton order of their cells.  Kernels that walk
+// neighbour lists run in blocks of TPB = 128 consecutive particles, and each
+// block first copies the union of its particles' 27-cell neighbourhoods (a
+// set of whole cells, i.e. contiguous runs of the sorted arrays) into shared
+// memory: the staging.  Neighbour lists store 16-bit indices into that
+// staging, so a pass reads 2 bytes per list entry from HBM and serves every
+// neighbour lookup from shared memory.
+//
+// One MD step:
 //   rebuild (only when a particle moved more than skin/2 since the last build):
 //     k_bin -> k_scan_sums -> k_scan_apply -> k_scatter -> k_cellsort ->
-//     k_permute -> k_copyback -> k_nlist
+//     k_permute -> k_copyback -> k_nlist (staging table + lists)
 //   k_count   pass 1: n_i, s_i, s'_i                        (Eqs. counter, Psidelta)
 //   k_chain   A_i = s'_i sum_j s_j V_a(r_ij), window particles only
 //   k_force   pass 2: F_i, fused with the BAOAB update of the state
-//   k_energy  FP64 U, W and pair count (on request only)
+//   k_count_e, k_chain_e, k_energy   FP64 U, W and pair count (on request only)
 // The rebuild kernels read a device flag and return at once when no rebuild
 // is due, so the host never waits on the device between steps.  Every pass
-// walks a full (both-direction) Verlet list, one thread per particle, and
+// walks a full (both-direction) list, one thread per particle, and
 // accumulates without atomics, so results do not depend on scheduling.
 #pragma once
 
@@ -22,11 +30,29 @@ constexpr int TPB = 128;          // threads per block of the per-particle kerne
 constexpr int SCAN_CHUNK = 2048;  // cells per block in the two-pass scan
 constexpr int SCAN_TPB = 256;
 constexpr int MAX_CELL = 512;     // a denser cell means the system has collapsed
-constexpr int RED_TPB = 256;      // energy kernel block size
+constexpr int HASH_SIZE = 4096;   // open-addressing set of a block's neighbour cells
+constexpr int NCLASS = 4;         // distance classes that order each list
 
 enum Epilogue { EPI_FORCE = 0, EPI_START = 1, EPI_FINISH = 2, EPI_FINISH_START = 3 };
 
-// ================================================================ rebuild
+// Per-block staging table in global memory: for block b, cells k < n[b] with
+// first sorted particle base[b*cmax + k] and staging offset off[b*(cmax+1) + k].
+struct StageTable {
+    int* base;
+    int* off;
+    int* n;
+    int cmax;  // capacity in cells
+    int smax;  // capacity in particles
+};
+
+// Distance classes (exact squared separations in the units of each mode):
+// class = number of thresholds t1 <= t2 <= t3 that r^2 reaches.
+struct ListParams {
+    unsigned long long rlist2_fix, t_fix[3];
+    double rlist2, t[3];
+};
+
+// ================================================================ rebuild: sort by cell
 template <class M>
 __global__ void __launch_bounds__(TPB) k_bin(const typename M::pos_t* __restrict__ pos, int n,
                                              Geom g, const int* __restrict__ morton_rank,
@@ -38,6 +64,8 @@ __global__ void __launch_bounds__(TPB) k_bin(const typename M::pos_t* __restrict
     if (i == 0) {
         st->max_nnb = 0;
         st->nnb_sum = 0;
+        st->max_stage = 0;
+        st->max_stage_cells = 0;
     }
     if (i >= n) return;
     const int3 c = cell_of_pos<M>(pos[i], g);
@@ -162,14 +190,17 @@ __global__ void __launch_bounds__(TPB) k_cellsort(int ncell, const int* __restri
     }
 }
 
+// Gathers the state (8-byte words: positions and velocities of either mode),
+// the original index and the fixed-point position into sorted order.
 template <class M>
 __global__ void __launch_bounds__(TPB) k_permute(int n, const int* __restrict__ order,
-                                                 const double* __restrict__ x, const double* __restrict__ v,
+                                                 const unsigned long long* __restrict__ x,
+                                                 const unsigned long long* __restrict__ v,
                                                  const int* __restrict__ id,
                                                  const typename M::pos_t* __restrict__ pos,
-                                                 double* __restrict__ xt, double* __restrict__ vt,
-                                                 int* __restrict__ idt, typename M::pos_t* __restrict__ post,
-                                                 const Status* st)
+                                                 unsigned long long* __restrict__ xt,
+                                                 unsigned long long* __restrict__ vt, int* __restrict__ idt,
+                                                 typename M::pos_t* __restrict__ post, const Status* st)
 {
     if (!st->rebuild || st->frozen || st->crowded) return;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -185,10 +216,11 @@ __global__ void __launch_bounds__(TPB) k_permute(int n, const int* __restrict__ 
 }
 
 template <class M>
-__global__ void __launch_bounds__(TPB) k_copyback(int n, const double* __restrict__ xt,
-                                                  const double* __restrict__ vt, const int* __restrict__ idt,
+__global__ void __launch_bounds__(TPB) k_copyback(int n, const unsigned long long* __restrict__ xt,
+                                                  const unsigned long long* __restrict__ vt,
+                                                  const int* __restrict__ idt,
                                                   const typename M::pos_t* __restrict__ post,
-                                                  double* __restrict__ x, double* __restrict__ v,
+                                                  unsigned long long* __restrict__ x, unsigned long long* __restrict__ v,
                                                   int* __restrict__ id, typename M::pos_t* __restrict__ pos,
                                                   typename M::pos_t* __restrict__ xref, const Status* st)
 {
@@ -206,132 +238,293 @@ __global__ void __launch_bounds__(TPB) k_copyback(int n, const double* __restric
     xref[k] = p;
 }
 
-// Squared separation compared against a squared radius: exact integers in the
-// FP32 mode (cubic box), FP64 in the FP64 mode.
+// ================================================================ staging
+// Index of the last k with off[k] <= m, for a sorted off[0..S] (off[0] = 0).
+__device__ __forceinline__ int stage_find(const int* s_off, int S, int m)
+{
+    int lo = 0, hi = S - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_off[mid] <= m) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Loads block b's staging table into shared memory; returns the number of
+// staged particles.  s_base and s_off must hold cmax and cmax + 1 ints.
+__device__ __forceinline__ int load_stage_table(const StageTable& tb, int b, int* s_base, int* s_off, int& S)
+{
+    S = tb.n[b];
+    for (int k = threadIdx.x; k < S; k += blockDim.x) s_base[k] = tb.base[(size_t)b * tb.cmax + k];
+    for (int k = threadIdx.x; k <= S; k += blockDim.x) s_off[k] = tb.off[(size_t)b * (tb.cmax + 1) + k];
+    __syncthreads();
+    return s_off[S];
+}
+
+// Copies the staged runs of src into dst (every thread of the block takes part).
+template <class T>
+__device__ __forceinline__ void stage_copy(T* dst, const T* __restrict__ src, const int* s_base, const int* s_off,
+                                           int S, int total)
+{
+    for (int m = threadIdx.x; m < total; m += blockDim.x) {
+        const int k = stage_find(s_off, S, m);
+        dst[m] = src[s_base[k] + (m - s_off[k])];
+    }
+}
+
+// Squared separation and its class, exact integers in the FP32 mode.
 template <class M>
 struct ListTest;
 template <>
 struct ListTest<ModeF32> {
-    __device__ __forceinline__ static bool within(const int4& a, const int4& b, const Geom&,
-                                                  unsigned long long r2fix, double)
+    __device__ __forceinline__ static int cls(const int4& a, const int4& b, const Geom&, const ListParams& lp)
     {
         const int dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
         const unsigned long long r2 = (unsigned long long)((long long)dx * dx) +
                                       (unsigned long long)((long long)dy * dy) +
                                       (unsigned long long)((long long)dz * dz);
-        return r2 < r2fix;
+        if (r2 >= lp.rlist2_fix) return -1;
+        return (r2 >= lp.t_fix[0]) + (r2 >= lp.t_fix[1]) + (r2 >= lp.t_fix[2]);
     }
 };
 template <>
 struct ListTest<ModeF64> {
-    __device__ __forceinline__ static bool within(const P64& a, const P64& b, const Geom& g,
-                                                  unsigned long long, double r2)
+    __device__ __forceinline__ static int cls(const P64& a, const P64& b, const Geom& g, const ListParams& lp)
     {
         double dx, dy, dz;
         ModeF64::delta64(a, b, g, dx, dy, dz);
-        return dx * dx + dy * dy + dz * dz < r2;
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 >= lp.rlist2) return -1;
+        return (r2 >= lp.t[0]) + (r2 >= lp.t[1]) + (r2 >= lp.t[2]);
     }
 };
 
-// Verlet list of radius r_list: column-major nbr[k * n + i], k < cap.
+// Shared-memory layout of k_nlist (dynamic): hash | cells | base | off | spos | buf.
+__host__ __device__ inline size_t nlist_spos_offset(int cmax) { return (((size_t)(HASH_SIZE + 3 * cmax + 1) * 4) + 15) & ~(size_t)15; }
+
+// ================================================================ rebuild: staging table and lists
+// For each block of TPB sorted particles:
+//  1. the set of cells in the 27-neighbourhoods of its particles' cells
+//     (open-addressing hash in shared memory), sorted by Morton rank;
+//  2. the staging table (first sorted particle and staging offset of each
+//     cell), written to global memory for the pass kernels;
+//  3. the staged positions in shared memory;
+//  4. each particle's list of staged indices within r_list, ordered by
+//     distance class (so that a warp walks neighbours of similar distance
+//     together), column-major nbr[k * n + i].
 template <class M>
 __global__ void __launch_bounds__(TPB) k_nlist(int n, Geom g, const typename M::pos_t* __restrict__ pos,
                                                const int* __restrict__ morton_rank,
-                                               const int* __restrict__ cell_start, unsigned long long rl2fix,
-                                               double rl2, int cap, int* __restrict__ nbr,
-                                               int* __restrict__ nnb, Status* st)
+                                               const int* __restrict__ rank_to_lin,
+                                               const int* __restrict__ cell_start, StageTable tb, ListParams lp,
+                                               int cap, uint16_t* __restrict__ nbr, int* __restrict__ nnb,
+                                               Status* st)
 {
-    // k_nlist raises `overflow` itself, so it does not test it
+    using pos_t = typename M::pos_t;
+    // raises `overflow` and `stage_overflow` itself, so it does not test them
     if (!st->rebuild || st->frozen || st->crowded) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int cnt = 0;
-    if (i < n) {
-        const typename M::pos_t pi = pos[i];
-        const int3 c = cell_of_pos<M>(pi, g);
-        for (int dz = -1; dz <= 1; ++dz) {
-            int z = c.z + dz;
-            z = z < 0 ? z + g.nc[2] : (z >= g.nc[2] ? z - g.nc[2] : z);
-            for (int dy = -1; dy <= 1; ++dy) {
-                int y = c.y + dy;
-                y = y < 0 ? y + g.nc[1] : (y >= g.nc[1] ? y - g.nc[1] : y);
-                for (int dx = -1; dx <= 1; ++dx) {
-                    int x = c.x + dx;
-                    x = x < 0 ? x + g.nc[0] : (x >= g.nc[0] ? x - g.nc[0] : x);
-                    const int key = morton_rank[(z * g.nc[1] + y) * g.nc[0] + x];
-                    const int b = cell_start[key], e = cell_start[key + 1];
-                    for (int j = b; j < e; ++j) {
-                        if (j == i) continue;
-                        if (ListTest<M>::within(pi, pos[j], g, rl2fix, rl2)) {
-                            if (cnt < cap) nbr[(size_t)cnt * n + i] = j;
-                            ++cnt;
-                        }
+    extern __shared__ __align__(16) unsigned char smem[];
+    int* hash = (int*)smem;
+    int* cells = hash + HASH_SIZE;
+    int* s_base = cells + tb.cmax;
+    int* s_off = s_base + tb.cmax;
+    pos_t* spos = (pos_t*)(smem + nlist_spos_offset(tb.cmax));
+    uint32_t* buf = (uint32_t*)(spos + tb.smax);
+    __shared__ int s_rank[TPB];
+    __shared__ int s_uniq[TPB];
+    __shared__ int s_nu, s_nc;
+    __shared__ int sw[TPB / 32];
+    __shared__ int smx[TPB / 32];
+    __shared__ long long ssm[TPB / 32];
+
+    const int b = blockIdx.x;
+    const int i = b * TPB + threadIdx.x;
+    const bool valid = i < n;
+    pos_t pi{};
+    int rank_i = -1;
+    int3 ci = make_int3(0, 0, 0);
+    if (valid) {
+        pi = pos[i];
+        ci = cell_of_pos<M>(pi, g);
+        rank_i = morton_rank[(ci.z * g.nc[1] + ci.y) * g.nc[0] + ci.x];
+    }
+    s_rank[threadIdx.x] = rank_i;
+    for (int h = threadIdx.x; h < HASH_SIZE; h += TPB) hash[h] = -1;
+    if (threadIdx.x == 0) {
+        s_nu = 0;
+        s_nc = 0;
+    }
+    __syncthreads();
+    // 1. unique cells of the block (ranks ascend along the sorted particles)
+    if (valid && (threadIdx.x == 0 || s_rank[threadIdx.x - 1] != rank_i)) s_uniq[atomicAdd(&s_nu, 1)] = rank_i;
+    __syncthreads();
+    const int U = s_nu;
+    for (int t = threadIdx.x; t < 27 * U; t += TPB) {
+        const int u = t / 27, d = t - 27 * u;
+        const int lin = rank_to_lin[s_uniq[u]];
+        int x = lin % g.nc[0] + (d % 3) - 1;
+        int y = (lin / g.nc[0]) % g.nc[1] + (d / 3) % 3 - 1;
+        int z = lin / (g.nc[0] * g.nc[1]) + d / 9 - 1;
+        x = x < 0 ? x + g.nc[0] : (x >= g.nc[0] ? x - g.nc[0] : x);
+        y = y < 0 ? y + g.nc[1] : (y >= g.nc[1] ? y - g.nc[1] : y);
+        z = z < 0 ? z + g.nc[2] : (z >= g.nc[2] ? z - g.nc[2] : z);
+        const int r = morton_rank[(z * g.nc[1] + y) * g.nc[0] + x];
+        unsigned h = ((unsigned)r * 2654435761u) & (HASH_SIZE - 1);
+        for (int probe = 0; probe < HASH_SIZE; ++probe) {
+            const int old = atomicCAS(&hash[h], -1, r);
+            if (old == -1) {
+                const int idx = atomicAdd(&s_nc, 1);
+                if (idx < tb.cmax) cells[idx] = r;
+                break;
+            }
+            if (old == r) break;
+            h = (h + 1) & (HASH_SIZE - 1);
+        }
+    }
+    __syncthreads();
+    const int S = s_nc;
+    if (S > tb.cmax) {
+        if (threadIdx.x == 0) {
+            atomicMax(&st->max_stage_cells, S);
+            st->stage_overflow = 1;
+            st->frozen_iter = (int)st->iter;
+        }
+        return;
+    }
+    // sort the cells by rank (bitonic over the next power of two, padded)
+    int P = 1;
+    while (P < S) P <<= 1;
+    for (int k = S + threadIdx.x; k < P; k += TPB) cells[k] = 0x7fffffff;
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < P; t += TPB) {
+                const int o = t ^ j;
+                if (o > t) {
+                    const int a = cells[t], c = cells[o];
+                    const bool up = (t & k) == 0;
+                    if ((a > c) == up) {
+                        cells[t] = c;
+                        cells[o] = a;
                     }
                 }
             }
+            __syncthreads();
         }
-        nnb[i] = cnt < cap ? cnt : cap;
-        if (cnt > cap) {
+    }
+    // 2. staging offsets: consecutive cells per thread, then a block scan
+    const int per = (S + TPB - 1) / TPB;
+    const int k0 = min(S, (int)threadIdx.x * per), k1 = min(S, ((int)threadIdx.x + 1) * per);
+    int cnt = 0;
+    for (int k = k0; k < k1; ++k) {
+        s_base[k] = cell_start[cells[k]];
+        cnt += cell_start[cells[k] + 1] - s_base[k];
+    }
+    int total;
+    int run = block_exclusive_scan<TPB>(cnt, sw, total);
+    for (int k = k0; k < k1; ++k) {
+        s_off[k] = run;
+        run += cell_start[cells[k] + 1] - s_base[k];
+    }
+    if (threadIdx.x == 0) {
+        s_off[S] = total;
+        atomicMax(&st->max_stage, total);
+        atomicMax(&st->max_stage_cells, S);
+    }
+    __syncthreads();
+    if (total > tb.smax) {
+        if (threadIdx.x == 0) {
+            st->stage_overflow = 1;
+            st->frozen_iter = (int)st->iter;
+        }
+        return;
+    }
+    for (int k = threadIdx.x; k < S; k += TPB) tb.base[(size_t)b * tb.cmax + k] = s_base[k];
+    for (int k = threadIdx.x; k <= S; k += TPB) tb.off[(size_t)b * (tb.cmax + 1) + k] = s_off[k];
+    if (threadIdx.x == 0) tb.n[b] = S;
+    // 3. staged positions
+    stage_copy<pos_t>(spos, pos, s_base, s_off, S, total);
+    __syncthreads();
+    // 4. lists
+    int count = 0;
+    if (valid) {
+        // staging index of i itself
+        int lo = 0, hi = S - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (cells[mid] < rank_i) lo = mid + 1;
+            else hi = mid;
+        }
+        const int m_self = s_off[lo] + (i - s_base[lo]);
+        int ncls[NCLASS] = {0, 0, 0, 0};
+        for (int d = 0; d < 27; ++d) {
+            int x = ci.x + (d % 3) - 1, y = ci.y + (d / 3) % 3 - 1, z = ci.z + d / 9 - 1;
+            x = x < 0 ? x + g.nc[0] : (x >= g.nc[0] ? x - g.nc[0] : x);
+            y = y < 0 ? y + g.nc[1] : (y >= g.nc[1] ? y - g.nc[1] : y);
+            z = z < 0 ? z + g.nc[2] : (z >= g.nc[2] ? z - g.nc[2] : z);
+            const int r = morton_rank[(z * g.nc[1] + y) * g.nc[0] + x];
+            int a = 0, c = S - 1;
+            while (a < c) {
+                const int mid = (a + c) >> 1;
+                if (cells[mid] < r) a = mid + 1;
+                else c = mid;
+            }
+            for (int m = s_off[a]; m < s_off[a + 1]; ++m) {
+                if (m == m_self) continue;
+                const int cl = ListTest<M>::cls(pi, spos[m], g, lp);
+                if (cl < 0) continue;
+                if (count < cap) buf[(size_t)count * TPB + threadIdx.x] = ((uint32_t)cl << 16) | (uint32_t)m;
+                ++ncls[cl];
+                ++count;
+            }
+        }
+        const int kept = count < cap ? count : cap;
+        int o = 0;
+        for (int cl = 0; cl < NCLASS; ++cl) {
+            if (ncls[cl] == 0) continue;
+            for (int e = 0; e < kept; ++e) {
+                const uint32_t v = buf[(size_t)e * TPB + threadIdx.x];
+                if ((int)(v >> 16) == cl) nbr[(size_t)(o++) * n + i] = (uint16_t)(v & 0xffffu);
+            }
+        }
+        nnb[i] = kept;
+        if (count > cap) {
             st->overflow = 1;
             st->frozen_iter = (int)st->iter;
         }
     }
     // block maximum and sum of the list lengths
-    __shared__ int smax[TPB / 32];
-    __shared__ long long ssum[TPB / 32];
-    int m = cnt;
-    long long s = cnt;
+    int mx = count;
+    long long sm = count;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-        s += __shfl_xor_sync(0xffffffffu, s, o);
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        sm += __shfl_xor_sync(0xffffffffu, sm, o);
     }
     if ((threadIdx.x & 31) == 0) {
-        smax[threadIdx.x >> 5] = m;
-        ssum[threadIdx.x >> 5] = s;
+        smx[threadIdx.x >> 5] = mx;
+        ssm[threadIdx.x >> 5] = sm;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        m = smax[0];
-        s = ssum[0];
+        mx = smx[0];
+        sm = ssm[0];
         for (int w = 1; w < TPB / 32; ++w) {
-            m = max(m, smax[w]);
-            s += ssum[w];
+            mx = max(mx, smx[w]);
+            sm += ssm[w];
         }
-        atomicMax(&st->max_nnb, m);
-        atomicAdd((unsigned long long*)&st->nnb_sum, (unsigned long long)s);
+        atomicMax(&st->max_nnb, mx);
+        atomicAdd((unsigned long long*)&st->nnb_sum, (unsigned long long)sm);
         if (blockIdx.x == 0) st->rebuilds += 1;
-    }
-}
-
-// ================================================================ list walk
-// Visits the list of particle i in batches of U entries: the U indices are
-// loaded first (each a coalesced 128-byte row across the warp), then the U
-// neighbour positions (gathers served by L1/L2), then the U pair bodies run.
-// Batching keeps U independent loads in flight per thread, which the
-// dependent index -> position chain would otherwise serialise.  Padding
-// slots of the last batch point at i itself and are skipped.
-template <class M, int U, class Body>
-__device__ __forceinline__ void walk_list(int i, int n, int m, const int* __restrict__ nbr,
-                                          const typename M::pos_t* __restrict__ pos, Body&& body)
-{
-    for (int k0 = 0; k0 < m; k0 += U) {
-        int jj[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) jj[u] = (k0 + u < m) ? __ldg(nbr + (size_t)(k0 + u) * n + i) : i;
-        typename M::pos_t pj[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) pj[u] = pos[jj[u]];
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (k0 + u < m) body(jj[u], pj[u]);
     }
 }
 
 // ================================================================ pass 1: counts
 // FP32-split: neighbours with r <= r_l add exactly 1 (an integer); window
-// neighbours add omega in 2^-31 fixed point, evaluated from the exact integer
-// r^2 - r_l^2.  The threshold test t = n - (f - delta) is taken in the same
-// fixed point, so s_i and s'_i carry only the error of the window terms.
+// neighbours add omega in 2^-31 fixed point (window_weight_fix31).  The
+// threshold test t = n - (f - delta) is taken in the same fixed point, so
+// s_i and s'_i carry only the error of the window terms.
 struct CountOut {
     double* n_out;          // counts in caller order, or null
     long long* in_window;   // counter of window particles, or null
@@ -353,14 +546,26 @@ __device__ __forceinline__ void switch_from_fix(long long T, float& s, float& ds
     }
 }
 
+// Dynamic shared memory of the pass kernels: base[cmax] | off[cmax+1] | staged arrays.
+__host__ __device__ inline size_t stage_header_bytes(int cmax) { return (((size_t)(2 * cmax + 1) * 4) + 15) & ~(size_t)15; }
+
 template <int U>
 __global__ void __launch_bounds__(TPB) k_count_f32(int n, Geom g, Coef c, const int4* __restrict__ pos,
-                                                   const int* __restrict__ nbr, const int* __restrict__ nnb,
-                                                   const int* __restrict__ id, float* __restrict__ ds_out,
-                                                   float2* __restrict__ sA, CountOut out, Status* st)
+                                                   const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
+                                                   const int* __restrict__ id, StageTable tb,
+                                                   float* __restrict__ ds_out, float2* __restrict__ sA,
+                                                   CountOut out, Status* st)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) st->rebuild = 0;
     if (halted(st)) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    int* s_base = (int*)smem;
+    int* s_off = s_base + tb.cmax;
+    int4* spos = (int4*)(smem + stage_header_bytes(tb.cmax));
+    int S;
+    const int total = load_stage_table(tb, blockIdx.x, s_base, s_off, S);
+    stage_copy<int4>(spos, pos, s_base, s_off, S, total);
+    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool win = false;
     if (i < n) {
@@ -368,19 +573,24 @@ __global__ void __launch_bounds__(TPB) k_count_f32(int n, Geom g, Coef c, const 
         const int m = nnb[i];
         unsigned full = 0;
         unsigned long long q = 0;
-        walk_list<ModeF32, U>(i, n, m, nbr, pos, [&](int, const int4& pj) {
-            const int dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-            const unsigned long long r2 = (unsigned long long)((long long)dx * dx) +
-                                          (unsigned long long)((long long)dy * dy) +
-                                          (unsigned long long)((long long)dz * dz);
-            if (r2 < c.rh2_fix) {
-                if (r2 <= c.rl2_fix) {
-                    ++full;
-                } else {
-                    q += window_weight_fix31(r2, r2 - c.rl2_fix, c.rl_s, c.w_s);
+        for (int k0 = 0; k0 < m; k0 += U) {
+            uint16_t jj[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) jj[u] = (k0 + u < m) ? __ldg(nbr + (size_t)(k0 + u) * n + i) : 0;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (k0 + u >= m) break;
+                const int4 pj = spos[jj[u]];
+                const int dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+                const unsigned long long r2 = (unsigned long long)((long long)dx * dx) +
+                                              (unsigned long long)((long long)dy * dy) +
+                                              (unsigned long long)((long long)dz * dz);
+                if (r2 < c.rh2_fix) {
+                    if (r2 <= c.rl2_fix) ++full;
+                    else q += window_weight_fix31(r2, r2 - c.rl2_fix, c.rl_s, c.w_s);
                 }
             }
-        });
+        }
         const long long T = ((long long)full - c.fd_int) * 2147483648LL + (long long)q - c.fd_frac_fix;
         float s, ds;
         switch_from_fix(T, s, ds);
@@ -390,18 +600,28 @@ __global__ void __launch_bounds__(TPB) k_count_f32(int n, Geom g, Coef c, const 
         if (out.n_out) out.n_out[id[i]] = (double)full + (double)q * 4.656612873077393e-10;
     }
     if (out.in_window) {
-        const unsigned b = __ballot_sync(0xffffffffu, win);
-        if ((threadIdx.x & 31) == 0 && b) atomicAdd((unsigned long long*)out.in_window, (unsigned long long)__popc(b));
+        const unsigned bal = __ballot_sync(0xffffffffu, win);
+        if ((threadIdx.x & 31) == 0 && bal)
+            atomicAdd((unsigned long long*)out.in_window, (unsigned long long)__popc(bal));
     }
 }
 
 __global__ void __launch_bounds__(TPB) k_count_f64(int n, Geom g, Coef c, const P64* __restrict__ pos,
-                                                        const int* __restrict__ nbr, const int* __restrict__ nnb,
-                                                        const int* __restrict__ id, double* __restrict__ ds_out,
-                                                        double2* __restrict__ sA, CountOut out, Status* st)
+                                                   const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
+                                                   const int* __restrict__ id, StageTable tb,
+                                                   double* __restrict__ ds_out, double2* __restrict__ sA,
+                                                   CountOut out, Status* st)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) st->rebuild = 0;
     if (halted(st)) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    int* s_base = (int*)smem;
+    int* s_off = s_base + tb.cmax;
+    P64* spos = (P64*)(smem + stage_header_bytes(tb.cmax));
+    int S;
+    const int total = load_stage_table(tb, blockIdx.x, s_base, s_off, S);
+    stage_copy<P64>(spos, pos, s_base, s_off, S, total);
+    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool win = false;
     if (i < n) {
@@ -409,9 +629,8 @@ __global__ void __launch_bounds__(TPB) k_count_f64(int n, Geom g, Coef c, const 
         const int m = nnb[i];
         double acc = 0.0;
         for (int k = 0; k < m; ++k) {
-            const int j = nbr[(size_t)k * n + i];
             double dx, dy, dz;
-            ModeF64::delta64(pi, pos[j], g, dx, dy, dz);
+            ModeF64::delta64(pi, spos[nbr[(size_t)k * n + i]], g, dx, dy, dz);
             const double r2 = dx * dx + dy * dy + dz * dz;
             if (r2 < c.rh2) acc += r2 <= c.rl2 ? 1.0 : omega_d(sqrt(r2), c.r_l, c.r_h);
         }
@@ -423,111 +642,268 @@ __global__ void __launch_bounds__(TPB) k_count_f64(int n, Geom g, Coef c, const 
         if (out.n_out) out.n_out[id[i]] = acc;
     }
     if (out.in_window) {
-        const unsigned b = __ballot_sync(0xffffffffu, win);
-        if ((threadIdx.x & 31) == 0 && b) atomicAdd((unsigned long long*)out.in_window, (unsigned long long)__popc(b));
+        const unsigned bal = __ballot_sync(0xffffffffu, win);
+        if ((threadIdx.x & 31) == 0 && bal)
+            atomicAdd((unsigned long long*)out.in_window, (unsigned long long)__popc(bal));
     }
 }
 
 // ================================================================ chain-rule pass
-// A_i = s'_i sum_j s_j V_a(r_ij) for particles inside the switching window.
-template <class M, int U>
+// A_i = s'_i sum_j s_j V_a(r_ij) for particles inside the switching window;
+// blocks without such a particle return after one vote.
+template <class M>
 __global__ void __launch_bounds__(TPB) k_chain(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
-                                               const int* __restrict__ nbr, const int* __restrict__ nnb,
-                                               const typename M::real* __restrict__ ds,
+                                               const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
+                                               StageTable tb, const typename M::real* __restrict__ ds,
                                                typename M::real2* __restrict__ sA, const Status* st)
 {
     using real = typename M::real;
+    using pos_t = typename M::pos_t;
     if (halted(st)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const real dsi = ds[i];
-    if (dsi == (real)0) return;
-    const typename M::pos_t pi = pos[i];
-    const int m = nnb[i];
+    const real dsi = i < n ? ds[i] : (real)0;
+    if (!__syncthreads_or(dsi != (real)0)) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    int* s_base = (int*)smem;
+    int* s_off = s_base + tb.cmax;
+    pos_t* spos = (pos_t*)(smem + stage_header_bytes(tb.cmax));
+    real* ss = (real*)(spos + tb.smax);
+    int S;
+    const int total = load_stage_table(tb, blockIdx.x, s_base, s_off, S);
     const real* s_only = reinterpret_cast<const real*>(sA);  // s_j at even offsets
+    for (int mm = threadIdx.x; mm < total; mm += blockDim.x) {
+        const int k = stage_find(s_off, S, mm);
+        const int j = s_base[k] + (mm - s_off[k]);
+        spos[mm] = pos[j];
+        ss[mm] = s_only[2 * j];
+    }
+    __syncthreads();
+    if (dsi == (real)0) return;
+    const pos_t pi = pos[i];
+    const int m = nnb[i];
     real acc = 0;
-    walk_list<M, U>(i, n, m, nbr, pos, [&](int j, const typename M::pos_t& pj) {
-        real dx, dy, dz;
-        M::delta(pi, pj, g, dx, dy, dz);
-        const real r2 = dx * dx + dy * dy + dz * dz;
+    for (int k = 0; k < m; ++k) {
+        const int jj = nbr[(size_t)k * n + i];
         if constexpr (M::fp64) {
-            if (r2 > c.rr2 && r2 < c.ra2) acc += s_only[2 * j] * Va_d(sqrt(r2), c);
+            double dx, dy, dz;
+            M::delta64(pi, spos[jj], g, dx, dy, dz);
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 > c.rr2 && r2 < c.ra2) acc += ss[jj] * Va_d(sqrt(r2), c);
         } else {
+            const int4 pj = spos[jj];
+            const float dx = (float)(pi.x - pj.x) * g.s32, dy = (float)(pi.y - pj.y) * g.s32,
+                        dz = (float)(pi.z - pj.z) * g.s32;
+            const float r2 = dx * dx + dy * dy + dz * dz;
             if (r2 > c.rr2f && r2 < c.ra2f) {
-                const float r = sqrtf(r2);
-                const float u = (r - c.rmf) * c.hinvf;
+                const float u = (sqrtf(r2) - c.rmf) * c.hinvf;
                 const float q = 1.0f - u * u;
-                acc += s_only[2 * j] * (-c.Eaf * q * q);
+                acc += ss[jj] * (-c.Eaf * q * q);
             }
         }
-    });
+    }
     sA[i].y = dsi * acc;
 }
 
 // ================================================================ pass 2: forces + BAOAB
 struct StepArgs {
-    double* x;            // [3][n] unwrapped positions (FP64)
-    double* v;            // [3][n] velocities (FP64)
+    void* x;              // [3][n] unwrapped positions (FP32 mode: int64 in units L / 2^52; FP64: double)
+    void* v;              // [3][n] velocities (FP32 mode: two-float; FP64: double)
     double* F_out;        // forces in caller order [n][3], or null (EPI_FORCE)
-    double dt, c1, c2;    // BAOAB constants: c1 = exp(-gamma dt), c2 = sqrt((1 - c1^2) kT)
+    // FP64 mode constants
+    double dt, c1, c2;    // c1 = exp(-gamma dt), c2 = sqrt((1 - c1^2) kT)
+    // FP32 mode constants as two-floats
+    f2x h;                // dt / 2
+    f2x hK[3];            // dt / 2 * 2^52 / L_a: velocity -> fixed-point displacement of a half drift
+    f2x c1f, c2f;
     unsigned long long seed;
     float half_skin2;     // (skin / 2)^2
 };
 
+// BAOAB update of particle i (unit mass, h = dt / 2) from its force.
+// FP32 mode: the unwrapped position is an int64 in units of L / 2^52 and the
+// velocity a two-float, so the update needs no FP64 instruction; each half
+// drift adds the nearest integer of h v 2^52 / L.  FP64 mode: doubles.
+template <class M, int EPI>
+__device__ __forceinline__ void integrate(int i, int n, const Geom& g, typename M::real fx, typename M::real fy,
+                                          typename M::real fz, const StepArgs& a, uint32_t pid, Status* st,
+                                          typename M::pos_t* __restrict__ pos_next,
+                                          const typename M::pos_t* __restrict__ xref)
+{
+    constexpr bool start = EPI == EPI_START || EPI == EPI_FINISH_START;
+    constexpr bool finish = EPI == EPI_FINISH || EPI == EPI_FINISH_START;
+    bool bad = !isfinite(fx) || !isfinite(fy) || !isfinite(fz);
+    if constexpr (!M::fp64) {
+        long long* X = (long long*)a.x;
+        float2* V = (float2*)a.v;
+        const float f3[3] = {fx, fy, fz};
+        float xi[3] = {0.0f, 0.0f, 0.0f};
+        if constexpr (start) {
+            const float3 z = langevin_normals(a.seed, (unsigned long long)(st->step_base + st->iter), pid);
+            xi[0] = z.x;
+            xi[1] = z.y;
+            xi[2] = z.z;
+        }
+        int w[3] = {0, 0, 0};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float2 vv = V[(size_t)d * n + i];
+            f2x v = {vv.x, vv.y};
+            const f2x hf = f2x_mulf(a.h, f3[d]);
+            if constexpr (finish) v = f2x_add(v, hf);                             // B (closes the step)
+            if constexpr (start) {
+                long long P = X[(size_t)d * n + i];
+                v = f2x_add(v, hf);                                                // B
+                P += f2x_to_ll(f2x_mul(v, a.hK[d]));                               // A
+                v = f2x_add(f2x_mul(v, a.c1f), f2x_mulf(a.c2f, xi[d]));            // O
+                P += f2x_to_ll(f2x_mul(v, a.hK[d]));                               // A
+                X[(size_t)d * n + i] = P;
+                w[d] = ModeF32::word(P);
+            }
+            bad |= !isfinite(v.hi);
+            V[(size_t)d * n + i] = make_float2(v.hi, v.lo);
+        }
+        if constexpr (start) {
+            const int4 pn = make_int4(w[0], w[1], w[2], 0);
+            pos_next[i] = pn;
+            const int4 pr = xref[i];
+            const float ux = (float)(pn.x - pr.x) * g.s32, uy = (float)(pn.y - pr.y) * g.s32,
+                        uz = (float)(pn.z - pr.z) * g.s32;
+            if (ux * ux + uy * uy + uz * uz > a.half_skin2) st->rebuild = 1;
+        }
+    } else {
+        double* X = (double*)a.x;
+        double* V = (double*)a.v;
+        const double h = 0.5 * a.dt;
+        const double f3[3] = {(double)fx, (double)fy, (double)fz};
+        double xs[3], vs[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            xs[d] = X[(size_t)d * n + i];
+            vs[d] = V[(size_t)d * n + i];
+        }
+        if constexpr (finish) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) vs[d] += h * f3[d];
+        }
+        if constexpr (start) {
+            const double3 z = langevin_normals_d(a.seed, (unsigned long long)(st->step_base + st->iter), pid);
+            const double zz[3] = {z.x, z.y, z.z};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                vs[d] += h * f3[d];
+                xs[d] += h * vs[d];
+                vs[d] = a.c1 * vs[d] + a.c2 * zz[d];
+                xs[d] += h * vs[d];
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            bad |= !isfinite(xs[d]) || !isfinite(vs[d]);
+            X[(size_t)d * n + i] = xs[d];
+            V[(size_t)d * n + i] = vs[d];
+        }
+        if constexpr (start) {
+            const P64 pn = ModeF64::from_x(xs[0], xs[1], xs[2], g);
+            pos_next[i] = pn;
+            const P64 pr = xref[i];
+            float d2 = 0.0f;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const float u = (float)(int)(ModeF64::hi32(pn, d) - ModeF64::hi32(pr, d)) * (float)g.s32d[d];
+                d2 += u * u;
+            }
+            if (d2 > a.half_skin2) st->rebuild = 1;
+        }
+    }
+    if (bad) st->frozen = 1;
+}
+
 template <class M, int EPI, int U>
 __global__ void __launch_bounds__(TPB) k_force(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
-                                               const int* __restrict__ nbr, const int* __restrict__ nnb,
-                                               const int* __restrict__ id,
+                                               const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
+                                               const int* __restrict__ id, StageTable tb,
                                                const typename M::real2* __restrict__ sA,
                                                typename M::pos_t* __restrict__ pos_next,
-                                               const typename M::pos_t* __restrict__ xref, StepArgs a,
-                                               Status* st)
+                                               const typename M::pos_t* __restrict__ xref, StepArgs a, Status* st)
 {
     using real = typename M::real;
-    // k_force raises `frozen` itself; a thread that sees it raised by another
-    // thread of the same launch stops early, which only happens on the error path
+    using real2 = typename M::real2;
+    using pos_t = typename M::pos_t;
+    // k_force raises `frozen` and `rebuild` itself; it tests `frozen` only through
+    // halted(), which a thread of this launch changes only on the error path
     if (halted(st)) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    int* s_base = (int*)smem;
+    int* s_off = s_base + tb.cmax;
+    pos_t* spos = (pos_t*)(smem + stage_header_bytes(tb.cmax));
+    real2* ssa = (real2*)(spos + tb.smax);
+    int S;
+    const int total = load_stage_table(tb, blockIdx.x, s_base, s_off, S);
+    for (int mm = threadIdx.x; mm < total; mm += blockDim.x) {
+        const int k = stage_find(s_off, S, mm);
+        const int j = s_base[k] + (mm - s_off[k]);
+        spos[mm] = pos[j];
+        ssa[mm] = sA[j];
+    }
+    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const typename M::pos_t pi = pos[i];
-    const typename M::real2 sai = sA[i];
+    const pos_t pi = pos[i];
+    const real2 sai = sA[i];
     const int m = nnb[i];
     real fx = 0, fy = 0, fz = 0;
-    walk_list<M, U>(i, n, m, nbr, pos, [&](int j, const typename M::pos_t& pj) {
-        real dx, dy, dz;
-        M::delta(pi, pj, g, dx, dy, dz);
-        const real r2 = dx * dx + dy * dy + dz * dz;
-        if constexpr (M::fp64) {
-            if (r2 >= c.rc2) return;
-            const typename M::real2 saj = sA[j];
-            const double r = sqrt(r2);
-            double gr = dVr_over_r_d(r2, c);
-            if (r > 0.0) gr += (sai.x * saj.x * dVa_d(r, c) + (sai.y + saj.y) * domega_d(r, c.r_l, c.r_h)) / r;
-            fx -= gr * dx;
-            fy -= gr * dy;
-            fz -= gr * dz;
-        } else {
-            if (r2 >= c.rc2f) return;
-            const float2 saj = __ldg(sA + j);
-            const float rinv = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
-            const float r = r2 * rinv;
-            float gr = 0.0f;                                   // g / r
-            if (r2 < c.rr2f) gr = c.Er4f * (r2 * c.rr2invf - 1.0f);
-            float gt = 0.0f;                                   // g from the well and the counts
-            if (r2 > c.rr2f && r2 < c.ra2f) {
-                const float u = (r - c.rmf) * c.hinvf;
-                gt = sai.x * saj.x * c.Ea4hf * u * (1.0f - u * u);
+    for (int k0 = 0; k0 < m; k0 += U) {
+        uint16_t jj[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) jj[u] = (k0 + u < m) ? __ldg(nbr + (size_t)(k0 + u) * n + i) : 0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (k0 + u >= m) break;
+            const pos_t pj = spos[jj[u]];
+            const real2 saj = ssa[jj[u]];
+            if constexpr (M::fp64) {
+                double dx, dy, dz;
+                M::delta64(pi, pj, g, dx, dy, dz);
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 >= c.rc2) continue;
+                const double r = sqrt(r2);
+                double gr = dVr_over_r_d(r2, c);
+                if (r > 0.0) gr += (sai.x * saj.x * dVa_d(r, c) + (sai.y + saj.y) * domega_d(r, c.r_l, c.r_h)) / r;
+                fx -= gr * dx;
+                fy -= gr * dy;
+                fz -= gr * dz;
+            } else {
+                // exact integer r^2; the arguments of the steep well and of the
+                // counting window come from exact integer differences r^2 - r_m^2 and
+                // r^2 - r_l^2, so their error is a few FP32 roundings of small numbers
+                const int ix = pi.x - pj.x, iy = pi.y - pj.y, iz = pi.z - pj.z;
+                const unsigned long long r2i = (unsigned long long)((long long)ix * ix) +
+                                               (unsigned long long)((long long)iy * iy) +
+                                               (unsigned long long)((long long)iz * iz);
+                if (r2i >= c.rc2_fix) continue;
+                const float dx = (float)ix * g.s32, dy = (float)iy * g.s32, dz = (float)iz * g.s32;
+                const float r2 = u64_to_float(r2i) * g.s32sq;
+                float rinv = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+                rinv = rinv * __fmaf_rn(-0.5f * r2 * rinv, rinv, 1.5f);   // one Newton step
+                const float r = r2 * rinv;
+                float gr = 0.0f;                                   // g / r
+                if (r2i < c.rr2_fix) gr = c.Er4f * (r2 * c.rr2invf - 1.0f);
+                float gt = 0.0f;                                   // g from the well and the counts
+                if (r2i > c.rr2_fix && r2i < c.ra2_fix) {
+                    const float u2 = s64_to_float((long long)r2i - (long long)c.rm2_fix) * c.s2hinv / (r + c.rmf);
+                    gt = sai.x * saj.x * c.Ea4hf * u2 * (1.0f - u2 * u2);
+                }
+                if (r2i > c.rl2_fix && r2i < c.rh2_fix) {
+                    const float t = u64_to_float(r2i - c.rl2_fix) * c.s2winv / (r + c.rlf);
+                    gt -= (sai.y + saj.y) * 4.0f * t * (1.0f - t * t) * c.winvf;
+                }
+                gr += gt * rinv;
+                fx -= gr * dx;
+                fy -= gr * dy;
+                fz -= gr * dz;
             }
-            if (r2 > c.rl2f && r2 < c.rh2f) {
-                const float t = (r - c.rlf) * c.winvf;
-                gt -= (sai.y + saj.y) * 4.0f * t * (1.0f - t * t) * c.winvf;
-            }
-            gr += gt * rinv;
-            fx -= gr * dx;
-            fy -= gr * dy;
-            fz -= gr * dz;
         }
-    });
+    }
     if constexpr (EPI == EPI_FORCE) {
         if (a.F_out) {
             const int o = id[i];
@@ -536,62 +912,7 @@ __global__ void __launch_bounds__(TPB) k_force(int n, Geom g, Coef c, const type
             a.F_out[3 * (size_t)o + 2] = (double)fz;
         }
     } else {
-        // BAOAB on the FP64 state (unit mass, h = dt / 2)
-        const double h = 0.5 * a.dt;
-        double xs[3], vs[3];
-        const double f3[3] = {(double)fx, (double)fy, (double)fz};
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            xs[d] = a.x[(size_t)d * n + i];
-            vs[d] = a.v[(size_t)d * n + i];
-        }
-        if constexpr (EPI == EPI_FINISH || EPI == EPI_FINISH_START) {
-#pragma unroll
-            for (int d = 0; d < 3; ++d) vs[d] += h * f3[d];      // B: closes the previous step
-        }
-        if constexpr (EPI == EPI_START || EPI == EPI_FINISH_START) {
-            double z[3];
-            // noise counter of the step this iteration starts
-            const unsigned long long nstep = (unsigned long long)(st->step_base + st->iter);
-            if constexpr (M::fp64) {
-                const double3 xi = langevin_normals_d(a.seed, nstep, (uint32_t)id[i]);
-                z[0] = xi.x; z[1] = xi.y; z[2] = xi.z;
-            } else {
-                const float3 xi = langevin_normals(a.seed, nstep, (uint32_t)id[i]);
-                z[0] = xi.x; z[1] = xi.y; z[2] = xi.z;
-            }
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                vs[d] += h * f3[d];                               // B
-                xs[d] += h * vs[d];                               // A
-                vs[d] = a.c1 * vs[d] + a.c2 * z[d];               // O
-                xs[d] += h * vs[d];                               // A
-            }
-        }
-        bool bad = false;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            bad |= !isfinite(xs[d]) || !isfinite(vs[d]);
-            a.x[(size_t)d * n + i] = xs[d];
-            a.v[(size_t)d * n + i] = vs[d];
-        }
-        if constexpr (EPI == EPI_START || EPI == EPI_FINISH_START) {
-            const typename M::pos_t pn = M::from_x(xs[0], xs[1], xs[2], g);
-            pos_next[i] = pn;
-            // displacement since the last build, on the top 32 bits of the words
-            const typename M::pos_t pr = xref[i];
-            float r2 = 0.0f;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const float u = (float)(int)(M::hi32(pn, d) - M::hi32(pr, d)) * (float)g.s32d[d];
-                r2 += u * u;
-            }
-            if (r2 > a.half_skin2) st->rebuild = 1;
-        }
-        if (bad) {
-            st->nonfinite = 1;
-            st->frozen = 1;
-        }
+        integrate<M, EPI>(i, n, g, fx, fy, fz, a, (uint32_t)id[i], st, pos_next, xref);
     }
 }
 
@@ -599,21 +920,31 @@ __global__ void __launch_bounds__(TPB) k_force(int n, Geom g, Coef c, const type
 // Requested energies are held to 1e-9 relative, which needs the switching
 // factors to FP64 accuracy: the counts, s, s' and A are recomputed here in
 // FP64 from the exact fixed-point separations (these kernels run only when U
-// or W is asked for, never inside the step loop).
+// or W is asked for, never inside the step loop).  Neighbour values are read
+// through each block's staging table (staged index -> sorted index).
 template <class M>
 __global__ void __launch_bounds__(TPB) k_count_e(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
-                                                 const int* __restrict__ nbr, const int* __restrict__ nnb,
-                                                 double2* __restrict__ sd, const Status* st)
+                                                 const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
+                                                 StageTable tb, double2* __restrict__ sd, const Status* st)
 {
+    using pos_t = typename M::pos_t;
     if (halted(st)) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    int* s_base = (int*)smem;
+    int* s_off = s_base + tb.cmax;
+    pos_t* spos = (pos_t*)(smem + stage_header_bytes(tb.cmax));
+    int S;
+    const int total = load_stage_table(tb, blockIdx.x, s_base, s_off, S);
+    stage_copy<pos_t>(spos, pos, s_base, s_off, S, total);
+    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const typename M::pos_t pi = pos[i];
+    const pos_t pi = pos[i];
     const int m = nnb[i];
     double acc = 0.0;
     for (int k = 0; k < m; ++k) {
         double dx, dy, dz;
-        M::delta64(pi, pos[nbr[(size_t)k * n + i]], g, dx, dy, dz);
+        M::delta64(pi, spos[nbr[(size_t)k * n + i]], g, dx, dy, dz);
         const double r2 = dx * dx + dy * dy + dz * dz;
         if (r2 < c.rh2) acc += r2 <= c.rl2 ? 1.0 : omega_d(sqrt(r2), c.r_l, c.r_h);
     }
@@ -622,11 +953,26 @@ __global__ void __launch_bounds__(TPB) k_count_e(int n, Geom g, Coef c, const ty
 
 template <class M>
 __global__ void __launch_bounds__(TPB) k_chain_e(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
-                                                 const int* __restrict__ nbr, const int* __restrict__ nnb,
-                                                 const double2* __restrict__ sd, double* __restrict__ Ad,
-                                                 const Status* st)
+                                                 const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
+                                                 StageTable tb, const double2* __restrict__ sd,
+                                                 double* __restrict__ Ad, const Status* st)
 {
+    using pos_t = typename M::pos_t;
     if (halted(st)) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    int* s_base = (int*)smem;
+    int* s_off = s_base + tb.cmax;
+    pos_t* spos = (pos_t*)(smem + stage_header_bytes(tb.cmax));
+    int* sj = (int*)(spos + tb.smax);
+    int S;
+    const int total = load_stage_table(tb, blockIdx.x, s_base, s_off, S);
+    for (int mm = threadIdx.x; mm < total; mm += blockDim.x) {
+        const int k = stage_find(s_off, S, mm);
+        const int j = s_base[k] + (mm - s_off[k]);
+        spos[mm] = pos[j];
+        sj[mm] = j;
+    }
+    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double dsi = sd[i].y;
@@ -634,15 +980,15 @@ __global__ void __launch_bounds__(TPB) k_chain_e(int n, Geom g, Coef c, const ty
         Ad[i] = 0.0;
         return;
     }
-    const typename M::pos_t pi = pos[i];
+    const pos_t pi = pos[i];
     const int m = nnb[i];
     double acc = 0.0;
     for (int k = 0; k < m; ++k) {
-        const int j = nbr[(size_t)k * n + i];
+        const int jj = nbr[(size_t)k * n + i];
         double dx, dy, dz;
-        M::delta64(pi, pos[j], g, dx, dy, dz);
+        M::delta64(pi, spos[jj], g, dx, dy, dz);
         const double r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 > c.rr2 && r2 < c.ra2) acc += sd[j].x * Va_d(sqrt(r2), c);
+        if (r2 > c.rr2 && r2 < c.ra2) acc += sd[sj[jj]].x * Va_d(sqrt(r2), c);
     }
     Ad[i] = dsi * acc;
 }
@@ -650,32 +996,51 @@ __global__ void __launch_bounds__(TPB) k_chain_e(int n, Geom g, Coef c, const ty
 // Per-block partial sums of U = sum_{i<j} [V_r + s_i s_j V_a], W = sum_{i<j} -g r and
 // of the number of pairs with r < r_c, each pair seen from both ends (halves).
 template <class M>
-__global__ void __launch_bounds__(RED_TPB) k_energy(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
-                                                    const int* __restrict__ nbr, const int* __restrict__ nnb,
-                                                    const double2* __restrict__ sd, const double* __restrict__ Ad,
-                                                    double* __restrict__ partial, long long* __restrict__ ppairs,
-                                                    const Status* st)
+__global__ void __launch_bounds__(TPB) k_energy(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
+                                                const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
+                                                StageTable tb, const double2* __restrict__ sd,
+                                                const double* __restrict__ Ad, double* __restrict__ partial,
+                                                long long* __restrict__ ppairs, const Status* st)
 {
-    __shared__ double se[RED_TPB], sw[RED_TPB];
-    __shared__ long long sp[RED_TPB];
+    using pos_t = typename M::pos_t;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double se[TPB], sw[TPB];
+    __shared__ long long sp[TPB];
+    int* s_base = (int*)smem;
+    int* s_off = s_base + tb.cmax;
+    pos_t* spos = (pos_t*)(smem + stage_header_bytes(tb.cmax));
+    int* sj = (int*)(spos + tb.smax);
+    const bool live = !halted(st);
+    int S = 0, total = 0;
+    if (live) {
+        total = load_stage_table(tb, blockIdx.x, s_base, s_off, S);
+        for (int mm = threadIdx.x; mm < total; mm += blockDim.x) {
+            const int k = stage_find(s_off, S, mm);
+            const int j = s_base[k] + (mm - s_off[k]);
+            spos[mm] = pos[j];
+            sj[mm] = j;
+        }
+    }
+    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double e = 0.0, w = 0.0;
     long long pairs = 0;
-    if (i < n && !halted(st)) {
-        const typename M::pos_t pi = pos[i];
+    if (i < n && live) {
+        const pos_t pi = pos[i];
         const double si = sd[i].x, Ai = Ad[i];
         const int m = nnb[i];
         for (int k = 0; k < m; ++k) {
-            const int j = nbr[(size_t)k * n + i];
+            const int jj = nbr[(size_t)k * n + i];
             double dx, dy, dz;
-            M::delta64(pi, pos[j], g, dx, dy, dz);
+            M::delta64(pi, spos[jj], g, dx, dy, dz);
             const double r2 = dx * dx + dy * dy + dz * dz;
             if (r2 >= c.rc2) continue;
             ++pairs;
-            const double sj = sd[j].x, Aj = Ad[j];
+            const int j = sj[jj];
+            const double sjv = sd[j].x, Aj = Ad[j];
             const double r = sqrt(r2);
-            e += 0.5 * (Vr_d(r2, c) + si * sj * Va_d(r, c));
-            const double gg = dVr_over_r_d(r2, c) * r + si * sj * dVa_d(r, c) +
+            e += 0.5 * (Vr_d(r2, c) + si * sjv * Va_d(r, c));
+            const double gg = dVr_over_r_d(r2, c) * r + si * sjv * dVa_d(r, c) +
                               (Ai + Aj) * domega_d(r, c.r_l, c.r_h);
             w += 0.5 * (-gg * r);
         }
@@ -684,7 +1049,7 @@ __global__ void __launch_bounds__(RED_TPB) k_energy(int n, Geom g, Coef c, const
     sw[threadIdx.x] = w;
     sp[threadIdx.x] = pairs;
     __syncthreads();
-    for (int s = RED_TPB / 2; s > 0; s >>= 1) {
+    for (int s = TPB / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) {
             se[threadIdx.x] += se[threadIdx.x + s];
             sw[threadIdx.x] += sw[threadIdx.x + s];
@@ -699,6 +1064,7 @@ __global__ void __launch_bounds__(RED_TPB) k_energy(int n, Geom g, Coef c, const
     }
 }
 
+constexpr int RED_TPB = 256;
 // Fixed-order sum of the block partials: out[0] = U, out[1] = W; pairs / 2 -> Status.
 __global__ void __launch_bounds__(RED_TPB) k_reduce_final(int nb, const double* __restrict__ partial,
                                                           const long long* __restrict__ ppairs,
@@ -733,37 +1099,63 @@ __global__ void __launch_bounds__(RED_TPB) k_reduce_final(int nb, const double* 
 }
 
 // ================================================================ state I/O
-// Caller order [n][3] -> internal SoA in sorted order, and fixed-point words.
+// Caller order [n][3] doubles -> internal state in sorted order, and the
+// fixed-point words.  FP32 mode: X = round(x 2^52 / L) (int64), V = two-float.
 template <class M>
 __global__ void __launch_bounds__(TPB) k_load_state(int n, Geom g, const double* __restrict__ pos_in,
                                                     const double* __restrict__ vel_in, const int* __restrict__ id,
-                                                    double* __restrict__ x, double* __restrict__ v,
+                                                    void* __restrict__ xs, void* __restrict__ vs,
                                                     typename M::pos_t* __restrict__ pos)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int o = id[i];
-    double xs[3];
+    if constexpr (M::fp64) {
+        double xx[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        xs[d] = pos_in[3 * (size_t)o + d];
-        x[(size_t)d * n + i] = xs[d];
-        v[(size_t)d * n + i] = vel_in ? vel_in[3 * (size_t)o + d] : 0.0;
+        for (int d = 0; d < 3; ++d) {
+            xx[d] = pos_in[3 * (size_t)o + d];
+            ((double*)xs)[(size_t)d * n + i] = xx[d];
+            ((double*)vs)[(size_t)d * n + i] = vel_in ? vel_in[3 * (size_t)o + d] : 0.0;
+        }
+        pos[i] = ModeF64::from_x(xx[0], xx[1], xx[2], g);
+    } else {
+        int w[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double x = pos_in[3 * (size_t)o + d];
+            const long long P = __double2ll_rn(x * g.inv32[d] * 1048576.0);  // x 2^52 / L
+            ((long long*)xs)[(size_t)d * n + i] = P;
+            w[d] = ModeF32::word(P);
+            const double v = vel_in ? vel_in[3 * (size_t)o + d] : 0.0;
+            const float vh = (float)v;
+            ((float2*)vs)[(size_t)d * n + i] = make_float2(vh, (float)(v - (double)vh));
+        }
+        pos[i] = make_int4(w[0], w[1], w[2], 0);
     }
-    pos[i] = M::from_x(xs[0], xs[1], xs[2], g);
 }
 
-__global__ void __launch_bounds__(TPB) k_store_state(int n, const int* __restrict__ id, const double* __restrict__ x,
-                                                     const double* __restrict__ v, double* __restrict__ pos_out,
-                                                     double* __restrict__ vel_out)
+template <class M>
+__global__ void __launch_bounds__(TPB) k_store_state(int n, Geom g, const int* __restrict__ id,
+                                                     const void* __restrict__ xs, const void* __restrict__ vs,
+                                                     double* __restrict__ pos_out, double* __restrict__ vel_out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int o = id[i];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        if (pos_out) pos_out[3 * (size_t)o + d] = x[(size_t)d * n + i];
-        if (vel_out) vel_out[3 * (size_t)o + d] = v[(size_t)d * n + i];
+        double x, v;
+        if constexpr (M::fp64) {
+            x = ((const double*)xs)[(size_t)d * n + i];
+            v = ((const double*)vs)[(size_t)d * n + i];
+        } else {
+            x = (double)((const long long*)xs)[(size_t)d * n + i] * (g.s32d[d] * 9.5367431640625e-07);  // L / 2^52
+            const float2 vv = ((const float2*)vs)[(size_t)d * n + i];
+            v = (double)vv.x + (double)vv.y;
+        }
+        if (pos_out) pos_out[3 * (size_t)o + d] = x;
+        if (vel_out) vel_out[3 * (size_t)o + d] = v;
     }
 }
 
@@ -782,18 +1174,32 @@ __global__ void __launch_bounds__(TPB) k_store_switch(int n, const int* __restri
     if (A_out) A_out[o] = (double)sA[i].y;
 }
 
+// Lists in caller indices (diagnostics): staged index -> sorted index -> id.
 __global__ void __launch_bounds__(TPB) k_store_nlist(int n, int cap_out, const int* __restrict__ id,
-                                                     const int* __restrict__ nbr, const int* __restrict__ nnb,
-                                                     int* __restrict__ nnb_out, int* __restrict__ nbr_out)
+                                                     const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
+                                                     StageTable tb, int* __restrict__ nnb_out, int* __restrict__ nbr_out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const int b = i / TPB;
+    const int S = tb.n[b];
+    const int* off = tb.off + (size_t)b * (tb.cmax + 1);
+    const int* base = tb.base + (size_t)b * tb.cmax;
     const int o = id[i];
     const int m = nnb[i];
     if (nnb_out) nnb_out[o] = m;
     if (nbr_out) {
         const int mm = m < cap_out ? m : cap_out;
-        for (int k = 0; k < mm; ++k) nbr_out[(size_t)o * cap_out + k] = id[nbr[(size_t)k * n + i]];
+        for (int k = 0; k < mm; ++k) {
+            const int s = nbr[(size_t)k * n + i];
+            int lo = 0, hi = S - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (off[mid] <= s) lo = mid;
+                else hi = mid - 1;
+            }
+            nbr_out[(size_t)o * cap_out + k] = id[base[lo] + (s - off[lo])];
+        }
     }
 }
 
