@@ -58,6 +58,7 @@ constexpr int MAX_STAGE = 65535;       // staged particles per block (16-bit lis
 constexpr int MAX_CMAX = 4096;         // staged cells per block
 constexpr size_t MAX_SMEM = 227 * 1024;
 constexpr int MAX_RETRIES = 12;
+constexpr int REBUILD_KERNELS = 9;     // kernels of one neighbour-list rebuild
 
 int blocks_for(int64_t n, int tpb) { return (int)((n + tpb - 1) / tpb); }
 
@@ -101,7 +102,7 @@ struct vbc_system {
     int *cell_of = nullptr, *slot_of = nullptr, *order = nullptr;
     int *cell_count = nullptr, *cell_start = nullptr, *morton_rank = nullptr, *rank_to_lin = nullptr;
     int* chunk_sum = nullptr;
-    int *tb_base = nullptr, *tb_off = nullptr, *tb_n = nullptr;
+    int *tb_base = nullptr, *tb_off = nullptr, *tb_rank = nullptr, *tb_n = nullptr;
     void *ds = nullptr, *sA = nullptr;
     Status* st = nullptr;
     Status* st_host = nullptr;  // pinned
@@ -115,7 +116,6 @@ struct vbc_system {
 
     int64_t step = 0;
     int64_t launches = 0;
-    int unroll = 4;  // list entries per batch in the pass kernels (1, 2, 4 or 8)
 
     // CUDA graphs of two FINISH_START iterations, one per parity of the
     // position buffer at the first of the two (see steps_impl)
@@ -126,7 +126,6 @@ struct vbc_system {
         cudaGraphExec_t exec = nullptr;
         double dt = 0, c1 = 0, c2 = 0;
         long long layout_version = -1;
-        int unroll = 0;
     } pair_graph[2];
     long long layout_version = 0;  // bumps when parameters or capacities (kernel arguments) change
 
@@ -139,9 +138,11 @@ struct vbc_system {
 
     size_t pos_bytes() const { return prec == VBC_FP64 ? sizeof(P64) : sizeof(int4); }
     size_t real_bytes() const { return prec == VBC_FP64 ? sizeof(double) : sizeof(float); }
-    StageTable table() const { return StageTable{tb_base, tb_off, tb_n, cmax, smax}; }
+    StageTable table() const { return StageTable{tb_base, tb_off, tb_rank, tb_n, cmax, smax}; }
+    ListRef list() const { return ListRef{nbr, nnb, cap}; }
     // dynamic shared memory of each kernel family
-    size_t smem_nlist() const { return nlist_spos_offset(cmax) + (size_t)smax * pos_bytes() + (size_t)cap * TPB * 4; }
+    size_t smem_table() const { return stage_table_smem(cmax); }
+    size_t smem_nlist() const { return nlist_header_bytes(cmax) + (size_t)smax * pos_bytes(); }
     size_t smem_count() const { return stage_header_bytes(cmax) + (size_t)smax * pos_bytes(); }
     size_t smem_chain() const { return stage_header_bytes(cmax) + (size_t)smax * (pos_bytes() + real_bytes()); }
     size_t smem_force() const { return stage_header_bytes(cmax) + (size_t)smax * (pos_bytes() + 2 * real_bytes()); }
@@ -250,22 +251,19 @@ int make_coef(const vbc_pair_params& p, const Geom& g, Coef& c)
     }
     c.fd_int = (long long)fi;
     c.fd_frac_fix = frac;
+    c.sat_full = c.fd_int + 1 + (frac > 0 ? 1 : 0);
     return VBC_OK;
 }
 
-// Distance classes of the lists: thresholds r_r^2, r_l^2, r_h^2 in ascending order.
+// List radius and the near/far split: near entries are closer than max(r_r, r_l).
 ListParams make_list_params(const Coef& c, double rlist, const Geom& g)
 {
     ListParams lp{};
     const double s2 = g.s32d[0] * g.s32d[0];
-    double t[3] = {c.rr2, c.rl2, c.rh2};
-    std::sort(t, t + 3);
     lp.rlist2 = rlist * rlist;
     lp.rlist2_fix = (unsigned long long)std::llround(lp.rlist2 / s2);
-    for (int k = 0; k < 3; ++k) {
-        lp.t[k] = t[k];
-        lp.t_fix[k] = (unsigned long long)std::llround(t[k] / s2);
-    }
+    lp.near2 = std::max(c.rr2, c.rl2);
+    lp.near2_fix = (unsigned long long)std::llround(lp.near2 / s2);
     return lp;
 }
 
@@ -322,7 +320,7 @@ void free_all(vbc_system* s)
     dfree(s->pos[0]); dfree(s->pos[1]); dfree(s->post); dfree(s->xref);
     dfree(s->nbr); dfree(s->nnb); dfree(s->cell_of); dfree(s->slot_of); dfree(s->order);
     dfree(s->cell_count); dfree(s->cell_start); dfree(s->morton_rank); dfree(s->rank_to_lin);
-    dfree(s->chunk_sum); dfree(s->tb_base); dfree(s->tb_off); dfree(s->tb_n);
+    dfree(s->chunk_sum); dfree(s->tb_base); dfree(s->tb_off); dfree(s->tb_rank); dfree(s->tb_n);
     dfree(s->ds); dfree(s->sA); dfree(s->st); dfree(s->partial); dfree(s->ppairs); dfree(s->red);
     dfree(s->win); dfree(s->e_sd); dfree(s->e_A);
     if (s->st_host) cudaFreeHost(s->st_host);
@@ -351,31 +349,23 @@ int set_smem(F* func, size_t bytes)
 template <class M>
 int configure_smem(vbc_system* s)
 {
-    if (s->smem_nlist() > MAX_SMEM || s->smem_force() > MAX_SMEM)
+    if (s->smem_table() > MAX_SMEM || s->smem_force() > MAX_SMEM || s->smem_nlist() > MAX_SMEM)
         return fail(VBC_ERR_UNSTABLE,
-                    "a block's neighbourhood (%d particles, %d cells) or a list of %d entries does not fit "
-                    "in shared memory: the system is too dense",
-                    s->smax, s->cmax, s->cap);
+                    "a block's neighbourhood (%d particles, %d cells) does not fit in shared memory: "
+                    "the system is too dense",
+                    s->smax, s->cmax);
+    VBC_TRY(set_smem(k_stage_table<M>, s->smem_table()));
     VBC_TRY(set_smem(k_nlist<M>, s->smem_nlist()));
     if constexpr (M::fp64) {
         VBC_TRY(set_smem(k_count_f64, s->smem_count()));
     } else {
-        VBC_TRY(set_smem(k_count_f32<1>, s->smem_count()));
-        VBC_TRY(set_smem(k_count_f32<2>, s->smem_count()));
-        VBC_TRY(set_smem(k_count_f32<4>, s->smem_count()));
-        VBC_TRY(set_smem(k_count_f32<8>, s->smem_count()));
+        VBC_TRY(set_smem(k_count_f32, s->smem_count()));
     }
     VBC_TRY(set_smem(k_chain<M>, s->smem_chain()));
-#define VBC_SET_FORCE(E)                                              \
-    VBC_TRY(set_smem(k_force<M, E, 1>, s->smem_force()));            \
-    VBC_TRY(set_smem(k_force<M, E, 2>, s->smem_force()));            \
-    VBC_TRY(set_smem(k_force<M, E, 4>, s->smem_force()));            \
-    VBC_TRY(set_smem(k_force<M, E, 8>, s->smem_force()));
-    VBC_SET_FORCE(EPI_FORCE)
-    VBC_SET_FORCE(EPI_START)
-    VBC_SET_FORCE(EPI_FINISH)
-    VBC_SET_FORCE(EPI_FINISH_START)
-#undef VBC_SET_FORCE
+    VBC_TRY(set_smem(k_force<M, EPI_FORCE>, s->smem_force()));
+    VBC_TRY(set_smem(k_force<M, EPI_START>, s->smem_force()));
+    VBC_TRY(set_smem(k_force<M, EPI_FINISH>, s->smem_force()));
+    VBC_TRY(set_smem(k_force<M, EPI_FINISH_START>, s->smem_force()));
     VBC_TRY(set_smem(k_count_e<M>, s->smem_energy()));
     VBC_TRY(set_smem(k_chain_e<M>, s->smem_energy()));
     VBC_TRY(set_smem(k_energy<M>, s->smem_energy()));
@@ -385,18 +375,6 @@ int configure_smem(vbc_system* s)
 int configure(vbc_system* s) { return s->prec == VBC_FP64 ? configure_smem<ModeF64>(s) : configure_smem<ModeF32>(s); }
 
 // ------------------------------------------------------------------ launches
-// Calls f with the list-walk batch size as a compile-time constant.
-template <class F>
-void with_unroll(int u, F&& f)
-{
-    switch (u) {
-        case 1: f(std::integral_constant<int, 1>{}); break;
-        case 2: f(std::integral_constant<int, 2>{}); break;
-        case 8: f(std::integral_constant<int, 8>{}); break;
-        default: f(std::integral_constant<int, 4>{}); break;
-    }
-}
-
 template <class M>
 int enqueue_rebuild(vbc_system* s)
 {
@@ -418,10 +396,11 @@ int enqueue_rebuild(vbc_system* s)
                                             (pos_t*)s->post, s->st);
     k_copyback<M><<<nb, TPB, 0, s->stream>>>(n, s->xt, s->vt, s->idt, (const pos_t*)s->post, s->x, s->v, s->id,
                                              pos, (pos_t*)s->xref, s->st);
-    k_nlist<M><<<nb, TPB, s->smem_nlist(), s->stream>>>(n, s->geom, pos, s->morton_rank, s->rank_to_lin,
-                                                         s->cell_start, s->table(), s->lp, s->cap, s->nbr, s->nnb,
-                                                         s->st);
-    return check_launch(s, 8);
+    k_stage_table<M><<<nb, TPB, s->smem_table(), s->stream>>>(n, s->geom, pos, s->morton_rank, s->rank_to_lin,
+                                                               s->cell_start, s->table(), s->st);
+    k_nlist<M><<<nb, TPB, s->smem_nlist(), s->stream>>>(n, s->geom, pos, s->morton_rank, s->cell_start, s->table(),
+                                                         s->lp, s->cap, s->nbr, s->nnb, s->st);
+    return check_launch(s, REBUILD_KERNELS);
 }
 
 template <class M>
@@ -434,24 +413,20 @@ int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window)
     const int nb = blocks_for(n, TPB);
     const pos_t* pos = (const pos_t*)s->pos[s->cur];
     CountOut out{n_out, want_window ? s->win : nullptr};
-    with_unroll(s->unroll, [&](auto U) {
-        {
-            Timed t(s, VBC_K_COUNT);
-            if constexpr (M::fp64)
-                k_count_f64<<<nb, TPB, s->smem_count(), s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb, s->id,
-                                                                     s->table(), (real*)s->ds, (real2*)s->sA, out,
-                                                                     s->st);
-            else
-                k_count_f32<decltype(U)::value><<<nb, TPB, s->smem_count(), s->stream>>>(
-                    n, s->geom, s->coef, pos, s->nbr, s->nnb, s->id, s->table(), (real*)s->ds, (real2*)s->sA, out,
-                    s->st);
-        }
-        {
-            Timed t(s, VBC_K_CHAIN);
-            k_chain<M><<<nb, TPB, s->smem_chain(), s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb,
-                                                                s->table(), (const real*)s->ds, (real2*)s->sA, s->st);
-        }
-    });
+    {
+        Timed t(s, VBC_K_COUNT);
+        if constexpr (M::fp64)
+            k_count_f64<<<nb, TPB, s->smem_count(), s->stream>>>(n, s->geom, s->coef, pos, s->list(), s->id,
+                                                                 s->table(), (real*)s->ds, (real2*)s->sA, out, s->st);
+        else
+            k_count_f32<<<nb, TPB, s->smem_count(), s->stream>>>(n, s->geom, s->coef, pos, s->list(), s->id,
+                                                                 s->table(), (real*)s->ds, (real2*)s->sA, out, s->st);
+    }
+    {
+        Timed t(s, VBC_K_CHAIN);
+        k_chain<M><<<nb, TPB, s->smem_chain(), s->stream>>>(n, s->geom, s->coef, pos, s->list(), s->table(),
+                                                            (const real*)s->ds, (real2*)s->sA, s->st);
+    }
     return check_launch(s, 2);
 }
 
@@ -463,12 +438,12 @@ int enqueue_force(vbc_system* s, const StepArgs& a)
     const int n = (int)s->n;
     const pos_t* pos = (const pos_t*)s->pos[s->cur];
     pos_t* pos_next = (pos_t*)s->pos[s->cur ^ 1];
-    with_unroll(s->unroll, [&](auto U) {
+    {
         Timed t(s, VBC_K_FORCE);
-        k_force<M, EPI, decltype(U)::value><<<blocks_for(n, TPB), TPB, s->smem_force(), s->stream>>>(
-            n, s->geom, s->coef, pos, s->nbr, s->nnb, s->id, s->table(), (const real2*)s->sA, pos_next,
+        k_force<M, EPI><<<blocks_for(n, TPB), TPB, s->smem_force(), s->stream>>>(
+            n, s->geom, s->coef, pos, s->list(), s->id, s->table(), (const real2*)s->sA, pos_next,
             (const pos_t*)s->xref, a, s->st);
-    });
+    }
     VBC_TRY(check_launch(s));
     if (EPI == EPI_START || EPI == EPI_FINISH_START) s->cur ^= 1;
     return VBC_OK;
@@ -483,11 +458,11 @@ int enqueue_energy(vbc_system* s)
         Timed t(s, VBC_K_ENERGY);
         const pos_t* pos = (const pos_t*)s->pos[s->cur];
         const int nb = blocks_for(n, TPB);
-        k_count_e<M><<<nb, TPB, s->smem_energy(), s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb, s->table(),
+        k_count_e<M><<<nb, TPB, s->smem_energy(), s->stream>>>(n, s->geom, s->coef, pos, s->list(), s->table(),
                                                                 s->e_sd, s->st);
-        k_chain_e<M><<<nb, TPB, s->smem_energy(), s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb, s->table(),
+        k_chain_e<M><<<nb, TPB, s->smem_energy(), s->stream>>>(n, s->geom, s->coef, pos, s->list(), s->table(),
                                                                 s->e_sd, s->e_A, s->st);
-        k_energy<M><<<nb, TPB, s->smem_energy(), s->stream>>>(n, s->geom, s->coef, pos, s->nbr, s->nnb, s->table(),
+        k_energy<M><<<nb, TPB, s->smem_energy(), s->stream>>>(n, s->geom, s->coef, pos, s->list(), s->table(),
                                                                s->e_sd, s->e_A, s->partial, s->ppairs, s->st);
         k_reduce_final<<<1, RED_TPB, 0, s->stream>>>(nb, s->partial, s->ppairs, s->red, s->st);
     }
@@ -534,8 +509,10 @@ int grow(vbc_system* s)
                             h.max_stage_cells, MAX_CMAX);
             dfree(s->tb_base);
             dfree(s->tb_off);
+            dfree(s->tb_rank);
             VBC_TRY(dalloc(s->tb_base, (size_t)s->nblk * cmax));
             VBC_TRY(dalloc(s->tb_off, (size_t)s->nblk * (cmax + 1)));
+            VBC_TRY(dalloc(s->tb_rank, (size_t)s->nblk * cmax));
             s->cmax = cmax;
         }
         if (h.max_stage > s->smax) {
@@ -604,7 +581,7 @@ int graph_error(vbc_system* s, const char* what, cudaError_t e)
 
 // Captures two FINISH_START iterations starting on position buffer c into
 // one executable graph.  Each iteration is: k_gate -> IF(rebuild due){the
-// eight rebuild kernels} -> count -> chain -> force, so steps that need no
+// nine rebuild kernels} -> count -> chain -> force, so steps that need no
 // rebuild launch no rebuild kernel at all.
 template <class M>
 int build_pair_graph(vbc_system* s, int c, const StepArgs& a)
@@ -685,7 +662,6 @@ int build_pair_graph(vbc_system* s, int c, const StepArgs& a)
     pg.c1 = a.c1;
     pg.c2 = a.c2;
     pg.layout_version = s->layout_version;
-    pg.unroll = s->unroll;
     return VBC_OK;
 }
 
@@ -693,8 +669,7 @@ template <class M>
 int launch_pair_graph(vbc_system* s, const StepArgs& a)
 {
     auto& pg = s->pair_graph[s->cur];
-    if (!pg.exec || pg.dt != a.dt || pg.c1 != a.c1 || pg.c2 != a.c2 || pg.layout_version != s->layout_version ||
-        pg.unroll != s->unroll)
+    if (!pg.exec || pg.dt != a.dt || pg.c1 != a.c1 || pg.c2 != a.c2 || pg.layout_version != s->layout_version)
         VBC_TRY(build_pair_graph<M>(s, s->cur, a));
     VBC_CUDA(cudaGraphLaunch(pg.exec, s->stream));
     s->launches += 8;  // two gates, two count/chain/force triples (rebuild bodies counted on the device)
@@ -826,11 +801,7 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     if (cfg->nlist_cap < 0) return fail(VBC_ERR_INVALID_ARG, "nlist_cap must be >= 0");
 
     vbc_system* s = new vbc_system();
-    // tuning knobs for experiments: list entries per batch in the pass kernels; graphs off
-    if (const char* e = std::getenv("VBC_WALK_UNROLL")) {
-        const int u = std::atoi(e);
-        if (u == 1 || u == 2 || u == 4 || u == 8) s->unroll = u;
-    }
+    // experiments: plain launches instead of CUDA graphs
     if (const char* e = std::getenv("VBC_NO_GRAPHS")) s->use_graphs = std::atoi(e) == 0;
     s->n = cfg->n;
     s->prec = cfg->precision;
@@ -924,6 +895,7 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     ALLOC(dalloc(s->chunk_sum, (size_t)blocks_for(g.ncell, SCAN_CHUNK)));
     ALLOC(dalloc(s->tb_base, (size_t)s->nblk * s->cmax));
     ALLOC(dalloc(s->tb_off, (size_t)s->nblk * (s->cmax + 1)));
+    ALLOC(dalloc(s->tb_rank, (size_t)s->nblk * s->cmax));
     ALLOC(dalloc(s->tb_n, (size_t)s->nblk));
     ALLOC(dalloc_bytes(s->ds, n * s->real_bytes()));
     ALLOC(dalloc_bytes(s->sA, n * 2 * s->real_bytes()));
@@ -1069,7 +1041,7 @@ int vbc_get_neighbors(vbc_system* s, int32_t* nnb, int32_t* nbr, int32_t cap, in
             cudaMemsetAsync(d_nbr, 0xff, n * (size_t)cap * sizeof(int), s->stream);
         }
     }
-    k_store_nlist<<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>((int)n, cap, s->id, s->nbr, s->nnb, s->table(), d_nnb,
+    k_store_nlist<<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>((int)n, cap, s->id, s->list(), s->table(), d_nnb,
                                                                 d_nbr);
     int rc = check_launch(s);
     if (rc == VBC_OK && !outputs_on_device) {
@@ -1205,7 +1177,7 @@ int vbc_profile_read(vbc_system* s, int which, double* total_ms, int64_t* launch
 int64_t vbc_kernel_launches(vbc_system* s)
 {
     if (!s || check_sys(s) != VBC_OK || read_status(s) != VBC_OK) return -1;
-    return s->launches + 8 * s->st_host->graph_rebuild_runs;  // eight kernels per rebuild body run
+    return s->launches + REBUILD_KERNELS * s->st_host->graph_rebuild_runs;
 }
 
 }  // extern "C"

@@ -60,6 +60,7 @@ struct Coef {
     f2x rl_s, w_s;                    // r_l / s and (r_h - r_l) / s as two floats, s = L / 2^32
     long long fd_int;                 // floor(f - delta)
     long long fd_frac_fix;            // (f - delta - fd_int) * 2^31, rounded
+    long long sat_full;               // ceil(f - delta + 1): this many neighbours inside r_l give s = s' = 0
 };
 
 // Device-side status words shared by all kernels of a system.

@@ -11,7 +11,7 @@
 // One MD step:
 //   rebuild (only when a particle moved more than skin/2 since the last build):
 //     k_bin -> k_scan_sums -> k_scan_apply -> k_scatter -> k_cellsort ->
-//     k_permute -> k_copyback -> k_nlist (staging table + lists)
+//     k_permute -> k_copyback -> k_stage_table -> k_nlist
 //   k_count   pass 1: n_i, s_i, s'_i                        (Eqs. counter, Psidelta)
 //   k_chain   A_i = s'_i sum_j s_j V_a(r_ij), window particles only
 //   k_force   pass 2: F_i, fused with the BAOAB update of the state
@@ -31,26 +31,8 @@ constexpr int SCAN_CHUNK = 2048;  // cells per block in the two-pass scan
 constexpr int SCAN_TPB = 256;
 constexpr int MAX_CELL = 512;     // a denser cell means the system has collapsed
 constexpr int HASH_SIZE = 4096;   // open-addressing set of a block's neighbour cells
-constexpr int NCLASS = 4;         // distance classes that order each list
 
 enum Epilogue { EPI_FORCE = 0, EPI_START = 1, EPI_FINISH = 2, EPI_FINISH_START = 3 };
-
-// Per-block staging table in global memory: for block b, cells k < n[b] with
-// first sorted particle base[b*cmax + k] and staging offset off[b*(cmax+1) + k].
-struct StageTable {
-    int* base;
-    int* off;
-    int* n;
-    int cmax;  // capacity in cells
-    int smax;  // capacity in particles
-};
-
-// Distance classes (exact squared separations in the units of each mode):
-// class = number of thresholds t1 <= t2 <= t3 that r^2 reaches.
-struct ListParams {
-    unsigned long long rlist2_fix, t_fix[3];
-    double rlist2, t[3];
-};
 
 // ================================================================ rebuild: sort by cell
 template <class M>
@@ -239,41 +221,73 @@ __global__ void __launch_bounds__(TPB) k_copyback(int n, const unsigned long lon
 }
 
 // ================================================================ staging
-// Index of the last k with off[k] <= m, for a sorted off[0..S] (off[0] = 0).
-__device__ __forceinline__ int stage_find(const int* s_off, int S, int m)
+// A block's staging is a list of runs: maximal sequences of cells with
+// consecutive Morton ranks, i.e. contiguous ranges of the sorted particle
+// arrays.  Run k of block b starts at sorted particle base[b*cmax + k], holds
+// off[b*(cmax+1) + k + 1] - off[b*(cmax+1) + k] particles at that staging
+// offset, and begins with the cell of rank rank[b*cmax + k].
+struct StageTable {
+    int* base;
+    int* off;
+    int* rank;
+    int* n;    // runs per block
+    int cmax;  // capacity in cells (and runs) per block
+    int smax;  // capacity in staged particles per block
+};
+
+// A list: near entries (closer than max(r_r, r_l) at the build) in rows
+// 0..nn-1 from the front, far entries (up to r_list) in rows cap-1, cap-2, ...
+// from the back, column-major nbr[row * n + i]; nnb[i] = nn | nf << 16.
+struct ListRef {
+    const uint16_t* nbr;
+    const int* nnb;
+    int cap;
+};
+
+template <class F>
+__device__ __forceinline__ void for_entries(const ListRef& L, int n, int i, int nn, int nf, F&& f)
 {
-    int lo = 0, hi = S - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_off[mid] <= m) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
+#pragma unroll 4
+    for (int t = 0; t < nn; ++t) f((int)__ldg(L.nbr + (size_t)t * n + i));
+#pragma unroll 4
+    for (int t = 0; t < nf; ++t) f((int)__ldg(L.nbr + (size_t)(L.cap - 1 - t) * n + i));
 }
 
-// Loads block b's staging table into shared memory; returns the number of
-// staged particles.  s_base and s_off must hold cmax and cmax + 1 ints.
-__device__ __forceinline__ int load_stage_table(const StageTable& tb, int b, int* s_base, int* s_off, int& S)
+// Loads block b's run table (base, off) into shared memory; returns the
+// number of staged particles.  s_base and s_off hold cmax and cmax + 1 ints.
+__device__ __forceinline__ int load_runs(const StageTable& tb, int b, int* s_base, int* s_off, int& R)
 {
-    S = tb.n[b];
-    for (int k = threadIdx.x; k < S; k += blockDim.x) s_base[k] = tb.base[(size_t)b * tb.cmax + k];
-    for (int k = threadIdx.x; k <= S; k += blockDim.x) s_off[k] = tb.off[(size_t)b * (tb.cmax + 1) + k];
+    R = tb.n[b];
+    for (int k = threadIdx.x; k < R; k += blockDim.x) s_base[k] = tb.base[(size_t)b * tb.cmax + k];
+    for (int k = threadIdx.x; k <= R; k += blockDim.x) s_off[k] = tb.off[(size_t)b * (tb.cmax + 1) + k];
     __syncthreads();
-    return s_off[S];
+    return s_off[R];
 }
 
-// Copies the staged runs of src into dst (every thread of the block takes part).
-template <class T>
-__device__ __forceinline__ void stage_copy(T* dst, const T* __restrict__ src, const int* s_base, const int* s_off,
-                                           int S, int total)
+// Copies every staged particle: copy(staging index, sorted index), one warp per run.
+template <class F>
+__device__ __forceinline__ void stage_runs(const int* s_base, const int* s_off, int R, F&& copy)
 {
-    for (int m = threadIdx.x; m < total; m += blockDim.x) {
-        const int k = stage_find(s_off, S, m);
-        dst[m] = src[s_base[k] + (m - s_off[k])];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = warp; k < R; k += (int)(blockDim.x >> 5)) {
+        const int b = s_base[k], o = s_off[k], len = s_off[k + 1] - o;
+        for (int l = lane; l < len; l += 32) copy(o + l, b + l);
     }
 }
 
-// Squared separation and its class, exact integers in the FP32 mode.
+// Dynamic shared memory of the pass kernels: base[cmax] | off[cmax+1] | staged arrays.
+__host__ __device__ inline size_t stage_header_bytes(int cmax) { return (((size_t)(2 * cmax + 1) * 4) + 15) & ~(size_t)15; }
+// ... of k_stage_table: hash[HASH_SIZE] | cells[cmax] | starts[cmax+1]
+__host__ __device__ inline size_t stage_table_smem(int cmax) { return (size_t)(HASH_SIZE + 2 * cmax + 1) * 4; }
+// ... of k_nlist: base[cmax] | off[cmax+1] | rank[cmax] | staged positions
+__host__ __device__ inline size_t nlist_header_bytes(int cmax) { return (((size_t)(3 * cmax + 1) * 4) + 15) & ~(size_t)15; }
+
+// Near (0), far (1) or beyond the list radius (-1), from exact integer squared
+// separations in the FP32 mode.
+struct ListParams {
+    unsigned long long rlist2_fix, near2_fix;
+    double rlist2, near2;
+};
 template <class M>
 struct ListTest;
 template <>
@@ -285,7 +299,7 @@ struct ListTest<ModeF32> {
                                       (unsigned long long)((long long)dy * dy) +
                                       (unsigned long long)((long long)dz * dz);
         if (r2 >= lp.rlist2_fix) return -1;
-        return (r2 >= lp.t_fix[0]) + (r2 >= lp.t_fix[1]) + (r2 >= lp.t_fix[2]);
+        return r2 < lp.near2_fix ? 0 : 1;
     }
 };
 template <>
@@ -296,58 +310,48 @@ struct ListTest<ModeF64> {
         ModeF64::delta64(a, b, g, dx, dy, dz);
         const double r2 = dx * dx + dy * dy + dz * dz;
         if (r2 >= lp.rlist2) return -1;
-        return (r2 >= lp.t[0]) + (r2 >= lp.t[1]) + (r2 >= lp.t[2]);
+        return r2 < lp.near2 ? 0 : 1;
     }
 };
 
-// Shared-memory layout of k_nlist (dynamic): hash | cells | base | off | spos | buf.
-__host__ __device__ inline size_t nlist_spos_offset(int cmax) { return (((size_t)(HASH_SIZE + 3 * cmax + 1) * 4) + 15) & ~(size_t)15; }
-
-// ================================================================ rebuild: staging table and lists
-// For each block of TPB sorted particles:
-//  1. the set of cells in the 27-neighbourhoods of its particles' cells
-//     (open-addressing hash in shared memory), sorted by Morton rank;
-//  2. the staging table (first sorted particle and staging offset of each
-//     cell), written to global memory for the pass kernels;
-//  3. the staged positions in shared memory;
-//  4. each particle's list of staged indices within r_list, ordered by
-//     distance class (so that a warp walks neighbours of similar distance
-//     together), column-major nbr[k * n + i].
-template <class M>
-__global__ void __launch_bounds__(TPB) k_nlist(int n, Geom g, const typename M::pos_t* __restrict__ pos,
-                                               const int* __restrict__ morton_rank,
-                                               const int* __restrict__ rank_to_lin,
-                                               const int* __restrict__ cell_start, StageTable tb, ListParams lp,
-                                               int cap, uint16_t* __restrict__ nbr, int* __restrict__ nnb,
-                                               Status* st)
+// Neighbour cell d (0..26) of cell (x, y, z), periodic.
+__device__ __forceinline__ int neighbour_cell_lin(int x, int y, int z, int d, const Geom& g)
 {
-    using pos_t = typename M::pos_t;
-    // raises `overflow` and `stage_overflow` itself, so it does not test them
+    x += d % 3 - 1;
+    y += (d / 3) % 3 - 1;
+    z += d / 9 - 1;
+    x = x < 0 ? x + g.nc[0] : (x >= g.nc[0] ? x - g.nc[0] : x);
+    y = y < 0 ? y + g.nc[1] : (y >= g.nc[1] ? y - g.nc[1] : y);
+    z = z < 0 ? z + g.nc[2] : (z >= g.nc[2] ? z - g.nc[2] : z);
+    return (z * g.nc[1] + y) * g.nc[0] + x;
+}
+
+// ================================================================ rebuild: staging tables
+// For each block of TPB sorted particles: the set of cells in the
+// 27-neighbourhoods of its particles' cells (open-addressing hash in shared
+// memory), sorted by Morton rank and merged into runs of consecutive ranks,
+// with staging offsets; written to the global run table.
+template <class M>
+__global__ void __launch_bounds__(TPB) k_stage_table(int n, Geom g, const typename M::pos_t* __restrict__ pos,
+                                                     const int* __restrict__ morton_rank,
+                                                     const int* __restrict__ rank_to_lin,
+                                                     const int* __restrict__ cell_start, StageTable tb, Status* st)
+{
     if (!st->rebuild || st->frozen || st->crowded) return;
     extern __shared__ __align__(16) unsigned char smem[];
     int* hash = (int*)smem;
     int* cells = hash + HASH_SIZE;
-    int* s_base = cells + tb.cmax;
-    int* s_off = s_base + tb.cmax;
-    pos_t* spos = (pos_t*)(smem + nlist_spos_offset(tb.cmax));
-    uint32_t* buf = (uint32_t*)(spos + tb.smax);
+    int* starts = cells + tb.cmax;
     __shared__ int s_rank[TPB];
     __shared__ int s_uniq[TPB];
     __shared__ int s_nu, s_nc;
     __shared__ int sw[TPB / 32];
-    __shared__ int smx[TPB / 32];
-    __shared__ long long ssm[TPB / 32];
-
     const int b = blockIdx.x;
     const int i = b * TPB + threadIdx.x;
-    const bool valid = i < n;
-    pos_t pi{};
     int rank_i = -1;
-    int3 ci = make_int3(0, 0, 0);
-    if (valid) {
-        pi = pos[i];
-        ci = cell_of_pos<M>(pi, g);
-        rank_i = morton_rank[(ci.z * g.nc[1] + ci.y) * g.nc[0] + ci.x];
+    if (i < n) {
+        const int3 c = cell_of_pos<M>(pos[i], g);
+        rank_i = morton_rank[(c.z * g.nc[1] + c.y) * g.nc[0] + c.x];
     }
     s_rank[threadIdx.x] = rank_i;
     for (int h = threadIdx.x; h < HASH_SIZE; h += TPB) hash[h] = -1;
@@ -356,20 +360,15 @@ __global__ void __launch_bounds__(TPB) k_nlist(int n, Geom g, const typename M::
         s_nc = 0;
     }
     __syncthreads();
-    // 1. unique cells of the block (ranks ascend along the sorted particles)
-    if (valid && (threadIdx.x == 0 || s_rank[threadIdx.x - 1] != rank_i)) s_uniq[atomicAdd(&s_nu, 1)] = rank_i;
+    // unique cells of the block (ranks ascend along the sorted particles)
+    if (i < n && (threadIdx.x == 0 || s_rank[threadIdx.x - 1] != rank_i)) s_uniq[atomicAdd(&s_nu, 1)] = rank_i;
     __syncthreads();
     const int U = s_nu;
     for (int t = threadIdx.x; t < 27 * U; t += TPB) {
         const int u = t / 27, d = t - 27 * u;
         const int lin = rank_to_lin[s_uniq[u]];
-        int x = lin % g.nc[0] + (d % 3) - 1;
-        int y = (lin / g.nc[0]) % g.nc[1] + (d / 3) % 3 - 1;
-        int z = lin / (g.nc[0] * g.nc[1]) + d / 9 - 1;
-        x = x < 0 ? x + g.nc[0] : (x >= g.nc[0] ? x - g.nc[0] : x);
-        y = y < 0 ? y + g.nc[1] : (y >= g.nc[1] ? y - g.nc[1] : y);
-        z = z < 0 ? z + g.nc[2] : (z >= g.nc[2] ? z - g.nc[2] : z);
-        const int r = morton_rank[(z * g.nc[1] + y) * g.nc[0] + x];
+        const int r = morton_rank[neighbour_cell_lin(lin % g.nc[0], (lin / g.nc[0]) % g.nc[1],
+                                                     lin / (g.nc[0] * g.nc[1]), d, g)];
         unsigned h = ((unsigned)r * 2654435761u) & (HASH_SIZE - 1);
         for (int probe = 0; probe < HASH_SIZE; ++probe) {
             const int old = atomicCAS(&hash[h], -1, r);
@@ -403,8 +402,7 @@ __global__ void __launch_bounds__(TPB) k_nlist(int n, Geom g, const typename M::
                 const int o = t ^ j;
                 if (o > t) {
                     const int a = cells[t], c = cells[o];
-                    const bool up = (t & k) == 0;
-                    if ((a > c) == up) {
+                    if ((a > c) == ((t & k) == 0)) {
                         cells[t] = c;
                         cells[o] = a;
                     }
@@ -413,82 +411,108 @@ __global__ void __launch_bounds__(TPB) k_nlist(int n, Geom g, const typename M::
             __syncthreads();
         }
     }
-    // 2. staging offsets: consecutive cells per thread, then a block scan
+    // runs of consecutive ranks: start positions, consecutive cells per thread
     const int per = (S + TPB - 1) / TPB;
     const int k0 = min(S, (int)threadIdx.x * per), k1 = min(S, ((int)threadIdx.x + 1) * per);
-    int cnt = 0;
-    for (int k = k0; k < k1; ++k) {
-        s_base[k] = cell_start[cells[k]];
-        cnt += cell_start[cells[k] + 1] - s_base[k];
-    }
+    int nstart = 0;
+    for (int k = k0; k < k1; ++k) nstart += (k == 0 || cells[k] != cells[k - 1] + 1);
+    int R;
+    int r = block_exclusive_scan<TPB>(nstart, sw, R);
+    for (int k = k0; k < k1; ++k)
+        if (k == 0 || cells[k] != cells[k - 1] + 1) starts[r++] = k;
+    if (threadIdx.x == 0) starts[R] = S;
+    __syncthreads();
+    // staging offsets of the runs
+    const int rper = (R + TPB - 1) / TPB;
+    const int q0 = min(R, (int)threadIdx.x * rper), q1 = min(R, ((int)threadIdx.x + 1) * rper);
+    int len = 0;
+    for (int q = q0; q < q1; ++q)
+        len += cell_start[cells[starts[q + 1] - 1] + 1] - cell_start[cells[starts[q]]];
     int total;
-    int run = block_exclusive_scan<TPB>(cnt, sw, total);
-    for (int k = k0; k < k1; ++k) {
-        s_off[k] = run;
-        run += cell_start[cells[k] + 1] - s_base[k];
+    int o = block_exclusive_scan<TPB>(len, sw, total);
+    for (int q = q0; q < q1; ++q) {
+        const int first = cells[starts[q]];
+        const int bq = cell_start[first];
+        tb.base[(size_t)b * tb.cmax + q] = bq;
+        tb.rank[(size_t)b * tb.cmax + q] = first;
+        tb.off[(size_t)b * (tb.cmax + 1) + q] = o;
+        o += cell_start[cells[starts[q + 1] - 1] + 1] - bq;
     }
     if (threadIdx.x == 0) {
-        s_off[S] = total;
+        tb.off[(size_t)b * (tb.cmax + 1) + R] = total;
+        tb.n[b] = R;
         atomicMax(&st->max_stage, total);
         atomicMax(&st->max_stage_cells, S);
-    }
-    __syncthreads();
-    if (total > tb.smax) {
-        if (threadIdx.x == 0) {
+        if (total > tb.smax) {
             st->stage_overflow = 1;
             st->frozen_iter = (int)st->iter;
         }
-        return;
     }
-    for (int k = threadIdx.x; k < S; k += TPB) tb.base[(size_t)b * tb.cmax + k] = s_base[k];
-    for (int k = threadIdx.x; k <= S; k += TPB) tb.off[(size_t)b * (tb.cmax + 1) + k] = s_off[k];
-    if (threadIdx.x == 0) tb.n[b] = S;
-    // 3. staged positions
-    stage_copy<pos_t>(spos, pos, s_base, s_off, S, total);
+}
+
+// ================================================================ rebuild: lists
+// Each particle's list of staged indices within r_list, near entries from the
+// front and far entries from the back (so that a pass walks neighbours of
+// similar distance together and the count pass can stop after the near ones).
+template <class M>
+__global__ void __launch_bounds__(TPB) k_nlist(int n, Geom g, const typename M::pos_t* __restrict__ pos,
+                                               const int* __restrict__ morton_rank,
+                                               const int* __restrict__ cell_start, StageTable tb, ListParams lp,
+                                               int cap, uint16_t* __restrict__ nbr, int* __restrict__ nnb,
+                                               Status* st)
+{
+    using pos_t = typename M::pos_t;
+    // raises `overflow` itself, so it does not test it; `stage_overflow` comes from k_stage_table
+    if (!st->rebuild || st->frozen || st->crowded || st->stage_overflow) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    int* s_base = (int*)smem;
+    int* s_off = s_base + tb.cmax;
+    int* s_rk = s_off + tb.cmax + 1;
+    pos_t* spos = (pos_t*)(smem + nlist_header_bytes(tb.cmax));
+    __shared__ int smx[TPB / 32];
+    __shared__ long long ssm[TPB / 32];
+    const int b = blockIdx.x;
+    int R;
+    load_runs(tb, b, s_base, s_off, R);
+    for (int k = threadIdx.x; k < R; k += TPB) s_rk[k] = tb.rank[(size_t)b * tb.cmax + k];
+    stage_runs(s_base, s_off, R, [&](int m, int j) { spos[m] = pos[j]; });
     __syncthreads();
-    // 4. lists
+    const int i = b * TPB + threadIdx.x;
     int count = 0;
-    if (valid) {
-        // staging index of i itself
-        int lo = 0, hi = S - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (cells[mid] < rank_i) lo = mid + 1;
-            else hi = mid;
-        }
-        const int m_self = s_off[lo] + (i - s_base[lo]);
-        int ncls[NCLASS] = {0, 0, 0, 0};
-        for (int d = 0; d < 27; ++d) {
-            int x = ci.x + (d % 3) - 1, y = ci.y + (d / 3) % 3 - 1, z = ci.z + d / 9 - 1;
-            x = x < 0 ? x + g.nc[0] : (x >= g.nc[0] ? x - g.nc[0] : x);
-            y = y < 0 ? y + g.nc[1] : (y >= g.nc[1] ? y - g.nc[1] : y);
-            z = z < 0 ? z + g.nc[2] : (z >= g.nc[2] ? z - g.nc[2] : z);
-            const int r = morton_rank[(z * g.nc[1] + y) * g.nc[0] + x];
-            int a = 0, c = S - 1;
-            while (a < c) {
-                const int mid = (a + c) >> 1;
-                if (cells[mid] < r) a = mid + 1;
-                else c = mid;
+    if (i < n) {
+        const pos_t pi = pos[i];
+        const int3 ci = cell_of_pos<M>(pi, g);
+        // staging position of cell rank r: run with the largest first rank <= r
+        auto locate = [&](int r) {
+            int lo = 0, hi = R - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_rk[mid] <= r) lo = mid;
+                else hi = mid - 1;
             }
-            for (int m = s_off[a]; m < s_off[a + 1]; ++m) {
+            return s_off[lo] + (cell_start[r] - s_base[lo]);
+        };
+        const int m_self = locate(morton_rank[(ci.z * g.nc[1] + ci.y) * g.nc[0] + ci.x]) +
+                           (i - cell_start[morton_rank[(ci.z * g.nc[1] + ci.y) * g.nc[0] + ci.x]]);
+        int nn = 0, nf = 0;
+        for (int d = 0; d < 27; ++d) {
+            const int r = morton_rank[neighbour_cell_lin(ci.x, ci.y, ci.z, d, g)];
+            const int o = locate(r);
+            const int len = cell_start[r + 1] - cell_start[r];
+            for (int m = o; m < o + len; ++m) {
                 if (m == m_self) continue;
                 const int cl = ListTest<M>::cls(pi, spos[m], g, lp);
                 if (cl < 0) continue;
-                if (count < cap) buf[(size_t)count * TPB + threadIdx.x] = ((uint32_t)cl << 16) | (uint32_t)m;
-                ++ncls[cl];
-                ++count;
+                if (nn + nf < cap) {
+                    if (cl == 0) nbr[(size_t)nn * n + i] = (uint16_t)m;
+                    else nbr[(size_t)(cap - 1 - nf) * n + i] = (uint16_t)m;
+                }
+                if (cl == 0) ++nn;
+                else ++nf;
             }
         }
-        const int kept = count < cap ? count : cap;
-        int o = 0;
-        for (int cl = 0; cl < NCLASS; ++cl) {
-            if (ncls[cl] == 0) continue;
-            for (int e = 0; e < kept; ++e) {
-                const uint32_t v = buf[(size_t)e * TPB + threadIdx.x];
-                if ((int)(v >> 16) == cl) nbr[(size_t)(o++) * n + i] = (uint16_t)(v & 0xffffu);
-            }
-        }
-        nnb[i] = kept;
+        count = nn + nf;
+        nnb[i] = nn | (nf << 16);
         if (count > cap) {
             st->overflow = 1;
             st->frozen_iter = (int)st->iter;
@@ -525,6 +549,10 @@ __global__ void __launch_bounds__(TPB) k_nlist(int n, Geom g, const typename M::
 // neighbours add omega in 2^-31 fixed point (window_weight_fix31).  The
 // threshold test t = n - (f - delta) is taken in the same fixed point, so
 // s_i and s'_i carry only the error of the window terms.
+// Saturation: when the near entries alone hold at least ceil(f - delta + 1)
+// neighbours with r <= r_l, then n_i >= f - delta + 1 whatever the other
+// entries add, so s_i = s'_i = 0 exactly and the window terms are not needed
+// (unless the counts themselves are requested).
 struct CountOut {
     double* n_out;          // counts in caller order, or null
     long long* in_window;   // counter of window particles, or null
@@ -546,13 +574,15 @@ __device__ __forceinline__ void switch_from_fix(long long T, float& s, float& ds
     }
 }
 
-// Dynamic shared memory of the pass kernels: base[cmax] | off[cmax+1] | staged arrays.
-__host__ __device__ inline size_t stage_header_bytes(int cmax) { return (((size_t)(2 * cmax + 1) * 4) + 15) & ~(size_t)15; }
+__device__ __forceinline__ unsigned long long r2_fix(const int4& a, const int4& b)
+{
+    const int dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+    return (unsigned long long)((long long)dx * dx) + (unsigned long long)((long long)dy * dy) +
+           (unsigned long long)((long long)dz * dz);
+}
 
-template <int U>
 __global__ void __launch_bounds__(TPB) k_count_f32(int n, Geom g, Coef c, const int4* __restrict__ pos,
-                                                   const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
-                                                   const int* __restrict__ id, StageTable tb,
+                                                   ListRef L, const int* __restrict__ id, StageTable tb,
                                                    float* __restrict__ ds_out, float2* __restrict__ sA,
                                                    CountOut out, Status* st)
 {
@@ -562,42 +592,36 @@ __global__ void __launch_bounds__(TPB) k_count_f32(int n, Geom g, Coef c, const 
     int* s_base = (int*)smem;
     int* s_off = s_base + tb.cmax;
     int4* spos = (int4*)(smem + stage_header_bytes(tb.cmax));
-    int S;
-    const int total = load_stage_table(tb, blockIdx.x, s_base, s_off, S);
-    stage_copy<int4>(spos, pos, s_base, s_off, S, total);
+    int R;
+    load_runs(tb, blockIdx.x, s_base, s_off, R);
+    stage_runs(s_base, s_off, R, [&](int m, int j) { spos[m] = pos[j]; });
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool win = false;
     if (i < n) {
         const int4 pi = pos[i];
-        const int m = nnb[i];
-        unsigned full = 0;
-        unsigned long long q = 0;
-        for (int k0 = 0; k0 < m; k0 += U) {
-            uint16_t jj[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) jj[u] = (k0 + u < m) ? __ldg(nbr + (size_t)(k0 + u) * n + i) : 0;
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (k0 + u >= m) break;
-                const int4 pj = spos[jj[u]];
-                const int dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-                const unsigned long long r2 = (unsigned long long)((long long)dx * dx) +
-                                              (unsigned long long)((long long)dy * dy) +
-                                              (unsigned long long)((long long)dz * dz);
+        const int w = L.nnb[i];
+        const int nn = w & 0xffff, nf = w >> 16;
+        long long full = 0;
+        for_entries(L, n, i, nn, 0, [&](int m) { full += r2_fix(pi, spos[m]) <= c.rl2_fix; });
+        float s = 0.0f, ds = 0.0f;
+        if (full < c.sat_full || out.n_out) {
+            full = 0;
+            unsigned long long q = 0;
+            for_entries(L, n, i, nn, nf, [&](int m) {
+                const unsigned long long r2 = r2_fix(pi, spos[m]);
                 if (r2 < c.rh2_fix) {
                     if (r2 <= c.rl2_fix) ++full;
                     else q += window_weight_fix31(r2, r2 - c.rl2_fix, c.rl_s, c.w_s);
                 }
-            }
+            });
+            const long long T = (full - c.fd_int) * 2147483648LL + (long long)q - c.fd_frac_fix;
+            switch_from_fix(T, s, ds);
+            if (out.n_out) out.n_out[id[i]] = (double)full + (double)q * 4.656612873077393e-10;
         }
-        const long long T = ((long long)full - c.fd_int) * 2147483648LL + (long long)q - c.fd_frac_fix;
-        float s, ds;
-        switch_from_fix(T, s, ds);
         ds_out[i] = ds;
         sA[i] = make_float2(s, 0.0f);
         win = ds != 0.0f;
-        if (out.n_out) out.n_out[id[i]] = (double)full + (double)q * 4.656612873077393e-10;
     }
     if (out.in_window) {
         const unsigned bal = __ballot_sync(0xffffffffu, win);
@@ -606,8 +630,7 @@ __global__ void __launch_bounds__(TPB) k_count_f32(int n, Geom g, Coef c, const 
     }
 }
 
-__global__ void __launch_bounds__(TPB) k_count_f64(int n, Geom g, Coef c, const P64* __restrict__ pos,
-                                                   const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
+__global__ void __launch_bounds__(TPB) k_count_f64(int n, Geom g, Coef c, const P64* __restrict__ pos, ListRef L,
                                                    const int* __restrict__ id, StageTable tb,
                                                    double* __restrict__ ds_out, double2* __restrict__ sA,
                                                    CountOut out, Status* st)
@@ -618,22 +641,22 @@ __global__ void __launch_bounds__(TPB) k_count_f64(int n, Geom g, Coef c, const 
     int* s_base = (int*)smem;
     int* s_off = s_base + tb.cmax;
     P64* spos = (P64*)(smem + stage_header_bytes(tb.cmax));
-    int S;
-    const int total = load_stage_table(tb, blockIdx.x, s_base, s_off, S);
-    stage_copy<P64>(spos, pos, s_base, s_off, S, total);
+    int R;
+    load_runs(tb, blockIdx.x, s_base, s_off, R);
+    stage_runs(s_base, s_off, R, [&](int m, int j) { spos[m] = pos[j]; });
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool win = false;
     if (i < n) {
         const P64 pi = pos[i];
-        const int m = nnb[i];
+        const int w = L.nnb[i];
         double acc = 0.0;
-        for (int k = 0; k < m; ++k) {
+        for_entries(L, n, i, w & 0xffff, w >> 16, [&](int m) {
             double dx, dy, dz;
-            ModeF64::delta64(pi, spos[nbr[(size_t)k * n + i]], g, dx, dy, dz);
+            ModeF64::delta64(pi, spos[m], g, dx, dy, dz);
             const double r2 = dx * dx + dy * dy + dz * dz;
             if (r2 < c.rh2) acc += r2 <= c.rl2 ? 1.0 : omega_d(sqrt(r2), c.r_l, c.r_h);
-        }
+        });
         const double s = omega_d(acc, c.fd, c.fd + 1.0);
         const double ds = domega_d(acc, c.fd, c.fd + 1.0);
         ds_out[i] = ds;
@@ -653,8 +676,7 @@ __global__ void __launch_bounds__(TPB) k_count_f64(int n, Geom g, Coef c, const 
 // blocks without such a particle return after one vote.
 template <class M>
 __global__ void __launch_bounds__(TPB) k_chain(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
-                                               const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
-                                               StageTable tb, const typename M::real* __restrict__ ds,
+                                               ListRef L, StageTable tb, const typename M::real* __restrict__ ds,
                                                typename M::real2* __restrict__ sA, const Status* st)
 {
     using real = typename M::real;
@@ -668,39 +690,35 @@ __global__ void __launch_bounds__(TPB) k_chain(int n, Geom g, Coef c, const type
     int* s_off = s_base + tb.cmax;
     pos_t* spos = (pos_t*)(smem + stage_header_bytes(tb.cmax));
     real* ss = (real*)(spos + tb.smax);
-    int S;
-    const int total = load_stage_table(tb, blockIdx.x, s_base, s_off, S);
+    int R;
+    load_runs(tb, blockIdx.x, s_base, s_off, R);
     const real* s_only = reinterpret_cast<const real*>(sA);  // s_j at even offsets
-    for (int mm = threadIdx.x; mm < total; mm += blockDim.x) {
-        const int k = stage_find(s_off, S, mm);
-        const int j = s_base[k] + (mm - s_off[k]);
-        spos[mm] = pos[j];
-        ss[mm] = s_only[2 * j];
-    }
+    stage_runs(s_base, s_off, R, [&](int m, int j) {
+        spos[m] = pos[j];
+        ss[m] = s_only[2 * (size_t)j];
+    });
     __syncthreads();
     if (dsi == (real)0) return;
     const pos_t pi = pos[i];
-    const int m = nnb[i];
+    const int w = L.nnb[i];
     real acc = 0;
-    for (int k = 0; k < m; ++k) {
-        const int jj = nbr[(size_t)k * n + i];
+    for_entries(L, n, i, w & 0xffff, w >> 16, [&](int m) {
         if constexpr (M::fp64) {
             double dx, dy, dz;
-            M::delta64(pi, spos[jj], g, dx, dy, dz);
+            M::delta64(pi, spos[m], g, dx, dy, dz);
             const double r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 > c.rr2 && r2 < c.ra2) acc += ss[jj] * Va_d(sqrt(r2), c);
+            if (r2 > c.rr2 && r2 < c.ra2) acc += ss[m] * Va_d(sqrt(r2), c);
         } else {
-            const int4 pj = spos[jj];
-            const float dx = (float)(pi.x - pj.x) * g.s32, dy = (float)(pi.y - pj.y) * g.s32,
-                        dz = (float)(pi.z - pj.z) * g.s32;
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 > c.rr2f && r2 < c.ra2f) {
-                const float u = (sqrtf(r2) - c.rmf) * c.hinvf;
+            const unsigned long long r2i = r2_fix(pi, spos[m]);
+            if (r2i > c.rr2_fix && r2i < c.ra2_fix) {
+                const float r2 = u64_to_float(r2i) * g.s32sq;
+                const float r = sqrtf(r2);
+                const float u = s64_to_float((long long)r2i - (long long)c.rm2_fix) * c.s2hinv / (r + c.rmf);
                 const float q = 1.0f - u * u;
-                acc += ss[jj] * (-c.Eaf * q * q);
+                acc += ss[m] * (-c.Eaf * q * q);
             }
         }
-    }
+    });
     sA[i].y = dsi * acc;
 }
 
@@ -818,10 +836,14 @@ __device__ __forceinline__ void integrate(int i, int n, const Geom& g, typename 
     if (bad) st->frozen = 1;
 }
 
-template <class M, int EPI, int U>
+// Pass 2.  FP32 mode, per pair: the exact integer r^2 decides which terms can
+// be nonzero (core overlap r < r_r; the well, only if s_i s_j != 0; the
+// counting window, only if A_i + A_j != 0) and pairs with none of them stop
+// there.  The arguments of the steep well and of the window come from exact
+// integer differences r^2 - r_m^2 and r^2 - r_l^2.
+template <class M, int EPI>
 __global__ void __launch_bounds__(TPB) k_force(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
-                                               const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
-                                               const int* __restrict__ id, StageTable tb,
+                                               ListRef L, const int* __restrict__ id, StageTable tb,
                                                const typename M::real2* __restrict__ sA,
                                                typename M::pos_t* __restrict__ pos_next,
                                                const typename M::pos_t* __restrict__ xref, StepArgs a, Status* st)
@@ -837,73 +859,66 @@ __global__ void __launch_bounds__(TPB) k_force(int n, Geom g, Coef c, const type
     int* s_off = s_base + tb.cmax;
     pos_t* spos = (pos_t*)(smem + stage_header_bytes(tb.cmax));
     real2* ssa = (real2*)(spos + tb.smax);
-    int S;
-    const int total = load_stage_table(tb, blockIdx.x, s_base, s_off, S);
-    for (int mm = threadIdx.x; mm < total; mm += blockDim.x) {
-        const int k = stage_find(s_off, S, mm);
-        const int j = s_base[k] + (mm - s_off[k]);
-        spos[mm] = pos[j];
-        ssa[mm] = sA[j];
-    }
+    int R;
+    load_runs(tb, blockIdx.x, s_base, s_off, R);
+    stage_runs(s_base, s_off, R, [&](int m, int j) {
+        spos[m] = pos[j];
+        ssa[m] = sA[j];
+    });
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const pos_t pi = pos[i];
     const real2 sai = sA[i];
-    const int m = nnb[i];
+    const int w = L.nnb[i];
     real fx = 0, fy = 0, fz = 0;
-    for (int k0 = 0; k0 < m; k0 += U) {
-        uint16_t jj[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) jj[u] = (k0 + u < m) ? __ldg(nbr + (size_t)(k0 + u) * n + i) : 0;
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (k0 + u >= m) break;
-            const pos_t pj = spos[jj[u]];
-            const real2 saj = ssa[jj[u]];
-            if constexpr (M::fp64) {
-                double dx, dy, dz;
-                M::delta64(pi, pj, g, dx, dy, dz);
-                const double r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 >= c.rc2) continue;
-                const double r = sqrt(r2);
-                double gr = dVr_over_r_d(r2, c);
-                if (r > 0.0) gr += (sai.x * saj.x * dVa_d(r, c) + (sai.y + saj.y) * domega_d(r, c.r_l, c.r_h)) / r;
-                fx -= gr * dx;
-                fy -= gr * dy;
-                fz -= gr * dz;
-            } else {
-                // exact integer r^2; the arguments of the steep well and of the
-                // counting window come from exact integer differences r^2 - r_m^2 and
-                // r^2 - r_l^2, so their error is a few FP32 roundings of small numbers
-                const int ix = pi.x - pj.x, iy = pi.y - pj.y, iz = pi.z - pj.z;
-                const unsigned long long r2i = (unsigned long long)((long long)ix * ix) +
-                                               (unsigned long long)((long long)iy * iy) +
-                                               (unsigned long long)((long long)iz * iz);
-                if (r2i >= c.rc2_fix) continue;
-                const float dx = (float)ix * g.s32, dy = (float)iy * g.s32, dz = (float)iz * g.s32;
+    for_entries(L, n, i, w & 0xffff, w >> 16, [&](int m) {
+        const pos_t pj = spos[m];
+        const real2 saj = ssa[m];
+        if constexpr (M::fp64) {
+            double dx, dy, dz;
+            M::delta64(pi, pj, g, dx, dy, dz);
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 >= c.rc2) return;
+            const double r = sqrt(r2);
+            double gr = dVr_over_r_d(r2, c);
+            if (r > 0.0) gr += (sai.x * saj.x * dVa_d(r, c) + (sai.y + saj.y) * domega_d(r, c.r_l, c.r_h)) / r;
+            fx -= gr * dx;
+            fy -= gr * dy;
+            fz -= gr * dz;
+        } else {
+            const int ix = pi.x - pj.x, iy = pi.y - pj.y, iz = pi.z - pj.z;
+            const unsigned long long r2i = (unsigned long long)((long long)ix * ix) +
+                                           (unsigned long long)((long long)iy * iy) +
+                                           (unsigned long long)((long long)iz * iz);
+            const bool core = r2i < c.rr2_fix;
+            const bool well = r2i > c.rr2_fix && r2i < c.ra2_fix && sai.x * saj.x != 0.0f;
+            const bool chain = r2i > c.rl2_fix && r2i < c.rh2_fix && sai.y + saj.y != 0.0f;
+            if (!(core || well || chain)) return;
+            const float dx = (float)ix * g.s32, dy = (float)iy * g.s32, dz = (float)iz * g.s32;
+            float gr = 0.0f;                                   // g / r
+            if (core) gr = c.Er4f * (u64_to_float(r2i) * g.s32sq * c.rr2invf - 1.0f);
+            if (well || chain) {
                 const float r2 = u64_to_float(r2i) * g.s32sq;
-                float rinv = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+                float rinv = rsqrtf(r2);
                 rinv = rinv * __fmaf_rn(-0.5f * r2 * rinv, rinv, 1.5f);   // one Newton step
                 const float r = r2 * rinv;
-                float gr = 0.0f;                                   // g / r
-                if (r2i < c.rr2_fix) gr = c.Er4f * (r2 * c.rr2invf - 1.0f);
-                float gt = 0.0f;                                   // g from the well and the counts
-                if (r2i > c.rr2_fix && r2i < c.ra2_fix) {
-                    const float u2 = s64_to_float((long long)r2i - (long long)c.rm2_fix) * c.s2hinv / (r + c.rmf);
-                    gt = sai.x * saj.x * c.Ea4hf * u2 * (1.0f - u2 * u2);
+                float gt = 0.0f;                               // g from the well and the counts
+                if (well) {
+                    const float u = s64_to_float((long long)r2i - (long long)c.rm2_fix) * c.s2hinv / (r + c.rmf);
+                    gt = sai.x * saj.x * c.Ea4hf * u * (1.0f - u * u);
                 }
-                if (r2i > c.rl2_fix && r2i < c.rh2_fix) {
+                if (chain) {
                     const float t = u64_to_float(r2i - c.rl2_fix) * c.s2winv / (r + c.rlf);
                     gt -= (sai.y + saj.y) * 4.0f * t * (1.0f - t * t) * c.winvf;
                 }
                 gr += gt * rinv;
-                fx -= gr * dx;
-                fy -= gr * dy;
-                fz -= gr * dz;
             }
+            fx -= gr * dx;
+            fy -= gr * dy;
+            fz -= gr * dz;
         }
-    }
+    });
     if constexpr (EPI == EPI_FORCE) {
         if (a.F_out) {
             const int o = id[i];
@@ -921,11 +936,24 @@ __global__ void __launch_bounds__(TPB) k_force(int n, Geom g, Coef c, const type
 // factors to FP64 accuracy: the counts, s, s' and A are recomputed here in
 // FP64 from the exact fixed-point separations (these kernels run only when U
 // or W is asked for, never inside the step loop).  Neighbour values are read
-// through each block's staging table (staged index -> sorted index).
+// through each block's staging (staged index -> sorted index, kept in sj).
+template <class M>
+__device__ __forceinline__ int stage_pos_index(const StageTable& tb, const typename M::pos_t* __restrict__ pos,
+                                               int* s_base, int* s_off, typename M::pos_t* spos, int* sj)
+{
+    int R;
+    const int total = load_runs(tb, blockIdx.x, s_base, s_off, R);
+    stage_runs(s_base, s_off, R, [&](int m, int j) {
+        spos[m] = pos[j];
+        sj[m] = j;
+    });
+    __syncthreads();
+    return total;
+}
+
 template <class M>
 __global__ void __launch_bounds__(TPB) k_count_e(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
-                                                 const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
-                                                 StageTable tb, double2* __restrict__ sd, const Status* st)
+                                                 ListRef L, StageTable tb, double2* __restrict__ sd, const Status* st)
 {
     using pos_t = typename M::pos_t;
     if (halted(st)) return;
@@ -933,28 +961,25 @@ __global__ void __launch_bounds__(TPB) k_count_e(int n, Geom g, Coef c, const ty
     int* s_base = (int*)smem;
     int* s_off = s_base + tb.cmax;
     pos_t* spos = (pos_t*)(smem + stage_header_bytes(tb.cmax));
-    int S;
-    const int total = load_stage_table(tb, blockIdx.x, s_base, s_off, S);
-    stage_copy<pos_t>(spos, pos, s_base, s_off, S, total);
-    __syncthreads();
+    int* sj = (int*)(spos + tb.smax);
+    stage_pos_index<M>(tb, pos, s_base, s_off, spos, sj);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const pos_t pi = pos[i];
-    const int m = nnb[i];
+    const int w = L.nnb[i];
     double acc = 0.0;
-    for (int k = 0; k < m; ++k) {
+    for_entries(L, n, i, w & 0xffff, w >> 16, [&](int m) {
         double dx, dy, dz;
-        M::delta64(pi, spos[nbr[(size_t)k * n + i]], g, dx, dy, dz);
+        M::delta64(pi, spos[m], g, dx, dy, dz);
         const double r2 = dx * dx + dy * dy + dz * dz;
         if (r2 < c.rh2) acc += r2 <= c.rl2 ? 1.0 : omega_d(sqrt(r2), c.r_l, c.r_h);
-    }
+    });
     sd[i] = make_double2(omega_d(acc, c.fd, c.fd + 1.0), domega_d(acc, c.fd, c.fd + 1.0));
 }
 
 template <class M>
 __global__ void __launch_bounds__(TPB) k_chain_e(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
-                                                 const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
-                                                 StageTable tb, const double2* __restrict__ sd,
+                                                 ListRef L, StageTable tb, const double2* __restrict__ sd,
                                                  double* __restrict__ Ad, const Status* st)
 {
     using pos_t = typename M::pos_t;
@@ -964,15 +989,7 @@ __global__ void __launch_bounds__(TPB) k_chain_e(int n, Geom g, Coef c, const ty
     int* s_off = s_base + tb.cmax;
     pos_t* spos = (pos_t*)(smem + stage_header_bytes(tb.cmax));
     int* sj = (int*)(spos + tb.smax);
-    int S;
-    const int total = load_stage_table(tb, blockIdx.x, s_base, s_off, S);
-    for (int mm = threadIdx.x; mm < total; mm += blockDim.x) {
-        const int k = stage_find(s_off, S, mm);
-        const int j = s_base[k] + (mm - s_off[k]);
-        spos[mm] = pos[j];
-        sj[mm] = j;
-    }
-    __syncthreads();
+    stage_pos_index<M>(tb, pos, s_base, s_off, spos, sj);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double dsi = sd[i].y;
@@ -981,15 +998,14 @@ __global__ void __launch_bounds__(TPB) k_chain_e(int n, Geom g, Coef c, const ty
         return;
     }
     const pos_t pi = pos[i];
-    const int m = nnb[i];
+    const int w = L.nnb[i];
     double acc = 0.0;
-    for (int k = 0; k < m; ++k) {
-        const int jj = nbr[(size_t)k * n + i];
+    for_entries(L, n, i, w & 0xffff, w >> 16, [&](int m) {
         double dx, dy, dz;
-        M::delta64(pi, spos[jj], g, dx, dy, dz);
+        M::delta64(pi, spos[m], g, dx, dy, dz);
         const double r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 > c.rr2 && r2 < c.ra2) acc += sd[sj[jj]].x * Va_d(sqrt(r2), c);
-    }
+        if (r2 > c.rr2 && r2 < c.ra2) acc += sd[sj[m]].x * Va_d(sqrt(r2), c);
+    });
     Ad[i] = dsi * acc;
 }
 
@@ -997,8 +1013,7 @@ __global__ void __launch_bounds__(TPB) k_chain_e(int n, Geom g, Coef c, const ty
 // of the number of pairs with r < r_c, each pair seen from both ends (halves).
 template <class M>
 __global__ void __launch_bounds__(TPB) k_energy(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
-                                                const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
-                                                StageTable tb, const double2* __restrict__ sd,
+                                                ListRef L, StageTable tb, const double2* __restrict__ sd,
                                                 const double* __restrict__ Ad, double* __restrict__ partial,
                                                 long long* __restrict__ ppairs, const Status* st)
 {
@@ -1011,39 +1026,28 @@ __global__ void __launch_bounds__(TPB) k_energy(int n, Geom g, Coef c, const typ
     pos_t* spos = (pos_t*)(smem + stage_header_bytes(tb.cmax));
     int* sj = (int*)(spos + tb.smax);
     const bool live = !halted(st);
-    int S = 0, total = 0;
-    if (live) {
-        total = load_stage_table(tb, blockIdx.x, s_base, s_off, S);
-        for (int mm = threadIdx.x; mm < total; mm += blockDim.x) {
-            const int k = stage_find(s_off, S, mm);
-            const int j = s_base[k] + (mm - s_off[k]);
-            spos[mm] = pos[j];
-            sj[mm] = j;
-        }
-    }
-    __syncthreads();
+    if (live) stage_pos_index<M>(tb, pos, s_base, s_off, spos, sj);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double e = 0.0, w = 0.0;
     long long pairs = 0;
     if (i < n && live) {
         const pos_t pi = pos[i];
         const double si = sd[i].x, Ai = Ad[i];
-        const int m = nnb[i];
-        for (int k = 0; k < m; ++k) {
-            const int jj = nbr[(size_t)k * n + i];
+        const int nw = L.nnb[i];
+        for_entries(L, n, i, nw & 0xffff, nw >> 16, [&](int m) {
             double dx, dy, dz;
-            M::delta64(pi, spos[jj], g, dx, dy, dz);
+            M::delta64(pi, spos[m], g, dx, dy, dz);
             const double r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 >= c.rc2) continue;
+            if (r2 >= c.rc2) return;
             ++pairs;
-            const int j = sj[jj];
+            const int j = sj[m];
             const double sjv = sd[j].x, Aj = Ad[j];
             const double r = sqrt(r2);
             e += 0.5 * (Vr_d(r2, c) + si * sjv * Va_d(r, c));
             const double gg = dVr_over_r_d(r2, c) * r + si * sjv * dVa_d(r, c) +
                               (Ai + Aj) * domega_d(r, c.r_l, c.r_h);
             w += 0.5 * (-gg * r);
-        }
+        });
     }
     se[threadIdx.x] = e;
     sw[threadIdx.x] = w;
@@ -1175,32 +1179,31 @@ __global__ void __launch_bounds__(TPB) k_store_switch(int n, const int* __restri
 }
 
 // Lists in caller indices (diagnostics): staged index -> sorted index -> id.
-__global__ void __launch_bounds__(TPB) k_store_nlist(int n, int cap_out, const int* __restrict__ id,
-                                                     const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
+__global__ void __launch_bounds__(TPB) k_store_nlist(int n, int cap_out, const int* __restrict__ id, ListRef L,
                                                      StageTable tb, int* __restrict__ nnb_out, int* __restrict__ nbr_out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int b = i / TPB;
-    const int S = tb.n[b];
+    const int R = tb.n[b];
     const int* off = tb.off + (size_t)b * (tb.cmax + 1);
     const int* base = tb.base + (size_t)b * tb.cmax;
     const int o = id[i];
-    const int m = nnb[i];
-    if (nnb_out) nnb_out[o] = m;
-    if (nbr_out) {
-        const int mm = m < cap_out ? m : cap_out;
-        for (int k = 0; k < mm; ++k) {
-            const int s = nbr[(size_t)k * n + i];
-            int lo = 0, hi = S - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (off[mid] <= s) lo = mid;
-                else hi = mid - 1;
-            }
-            nbr_out[(size_t)o * cap_out + k] = id[base[lo] + (s - off[lo])];
+    const int w = L.nnb[i];
+    const int nn = w & 0xffff, nf = w >> 16;
+    if (nnb_out) nnb_out[o] = nn + nf;
+    if (!nbr_out) return;
+    int k = 0;
+    for_entries(L, n, i, nn, nf, [&](int s) {
+        if (k >= cap_out) return;
+        int lo = 0, hi = R - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= s) lo = mid;
+            else hi = mid - 1;
         }
-    }
+        nbr_out[(size_t)o * cap_out + k++] = id[base[lo] + (s - off[lo])];
+    });
 }
 
 // Opens one loop iteration: advances the device iteration counter (which
