@@ -4,8 +4,8 @@
 // all work on one CUDA stream.  The host never waits for the device inside a
 // run of steps: neighbour-list rebuilds are decided on the device, and the
 // host reads the status words once, when the call ends.  If a rebuild found a
-// list longer than its capacity, or a block whose neighbourhood does not fit
-// its shared-memory staging, every later kernel of the call stopped without
+// list longer than its capacity, or a supercell whose neighbourhood or list
+// segment does not fit its capacity, every later kernel of the call stopped without
 // touching the state; the host then grows the capacity and resumes from the
 // iteration that stopped, so the trajectory is the same as with large enough
 // capacities from the start.
@@ -54,20 +54,13 @@ int fail(int code, const char* fmt, ...)
     } while (0)
 
 constexpr int MAX_CAP = 4096;          // longest neighbour list the library will grow to
-constexpr int MAX_STAGE = 65535;       // staged particles per block (16-bit list entries)
-constexpr int MAX_CMAX = 4096;         // staged cells per block
+constexpr int MAX_STAGE = 65535;       // staged particles per supercell (16-bit list entries)
+constexpr int MAX_OWN = 8 * MAX_CELL;  // particles of one supercell
 constexpr size_t MAX_SMEM = 227 * 1024;
 constexpr int MAX_RETRIES = 12;
-constexpr int REBUILD_KERNELS = 9;     // kernels of one neighbour-list rebuild
+constexpr int REBUILD_KERNELS = 8;     // kernels of one neighbour-list rebuild
 
 int blocks_for(int64_t n, int tpb) { return (int)((n + tpb - 1) / tpb); }
-
-int pow2_at_least(int v)
-{
-    int p = 1;
-    while (p < v) p <<= 1;
-    return p;
-}
 
 }  // namespace
 
@@ -86,10 +79,12 @@ struct vbc_system {
     Coef coef{};
     ListParams lp{};
     double rcut = 0.0, rlist = 0.0;
-    int cap = 0;       // list capacity per particle
-    int cmax = 0;      // staging capacity in cells per block (power of two)
-    int smax = 0;      // staging capacity in particles per block
-    int nblk = 0;      // blocks of TPB particles
+    int cap = 0;       // list capacity per particle (multiple of 8)
+    int smax = 0;      // staging capacity in particles per supercell
+    int omax = 0;      // particles per supercell
+    int seg = 0;       // list entries per supercell (multiple of 64)
+    int npad = 0;      // cells of the grid padded to even extents
+    int nsc = 0;       // supercells (npad / 8)
 
     // device buffers (particle arrays in sorted order)
     unsigned long long *x = nullptr, *v = nullptr, *xt = nullptr, *vt = nullptr;  // [3][n] 8-byte words
@@ -100,9 +95,8 @@ struct vbc_system {
     uint16_t* nbr = nullptr;
     int* nnb = nullptr;
     int *cell_of = nullptr, *slot_of = nullptr, *order = nullptr;
-    int *cell_count = nullptr, *cell_start = nullptr, *morton_rank = nullptr, *rank_to_lin = nullptr;
+    int *cell_count = nullptr, *cell_start = nullptr, *morton_rank = nullptr, *sc_org = nullptr;
     int* chunk_sum = nullptr;
-    int *tb_base = nullptr, *tb_off = nullptr, *tb_rank = nullptr, *tb_n = nullptr;
     void *ds = nullptr, *sA = nullptr;
     Status* st = nullptr;
     Status* st_host = nullptr;  // pinned
@@ -138,15 +132,15 @@ struct vbc_system {
 
     size_t pos_bytes() const { return prec == VBC_FP64 ? sizeof(P64) : sizeof(int4); }
     size_t real_bytes() const { return prec == VBC_FP64 ? sizeof(double) : sizeof(float); }
-    StageTable table() const { return StageTable{tb_base, tb_off, tb_rank, tb_n, cmax, smax}; }
-    ListRef list() const { return ListRef{nbr, nnb, cap}; }
+    SuperGrid grid() const { return SuperGrid{morton_rank, sc_org, cell_start}; }
+    SuperCaps caps() const { return SuperCaps{smax, omax, seg, cap}; }
     // dynamic shared memory of each kernel family
-    size_t smem_table() const { return stage_table_smem(cmax); }
-    size_t smem_nlist() const { return nlist_header_bytes(cmax) + (size_t)smax * pos_bytes(); }
-    size_t smem_count() const { return stage_header_bytes(cmax) + (size_t)smax * pos_bytes(); }
-    size_t smem_chain() const { return stage_header_bytes(cmax) + (size_t)smax * (pos_bytes() + real_bytes()); }
-    size_t smem_force() const { return stage_header_bytes(cmax) + (size_t)smax * (pos_bytes() + 2 * real_bytes()); }
-    size_t smem_energy() const { return stage_header_bytes(cmax) + (size_t)smax * (pos_bytes() + 4); }
+    size_t smem_nlist() const { return nlist_layout(caps(), pos_bytes()).total; }
+    size_t smem_count() const { return pass_layout(caps(), pos_bytes(), 0).total; }
+    size_t smem_chain() const { return pass_layout(caps(), pos_bytes(), real_bytes()).total; }
+    size_t smem_force() const { return force_layout(caps(), pos_bytes(), real_bytes()).total; }
+    size_t smem_energy() const { return pass_layout(caps(), pos_bytes(), sizeof(double2)).total; }
+    size_t smem_store() const { return al16((size_t)(omax + 1) * 4); }
 };
 
 namespace {
@@ -319,8 +313,8 @@ void free_all(vbc_system* s)
     dfree(s->x); dfree(s->v); dfree(s->xt); dfree(s->vt); dfree(s->id); dfree(s->idt);
     dfree(s->pos[0]); dfree(s->pos[1]); dfree(s->post); dfree(s->xref);
     dfree(s->nbr); dfree(s->nnb); dfree(s->cell_of); dfree(s->slot_of); dfree(s->order);
-    dfree(s->cell_count); dfree(s->cell_start); dfree(s->morton_rank); dfree(s->rank_to_lin);
-    dfree(s->chunk_sum); dfree(s->tb_base); dfree(s->tb_off); dfree(s->tb_rank); dfree(s->tb_n);
+    dfree(s->cell_count); dfree(s->cell_start); dfree(s->morton_rank); dfree(s->sc_org);
+    dfree(s->chunk_sum);
     dfree(s->ds); dfree(s->sA); dfree(s->st); dfree(s->partial); dfree(s->ppairs); dfree(s->red);
     dfree(s->win); dfree(s->e_sd); dfree(s->e_A);
     if (s->st_host) cudaFreeHost(s->st_host);
@@ -349,18 +343,13 @@ int set_smem(F* func, size_t bytes)
 template <class M>
 int configure_smem(vbc_system* s)
 {
-    if (s->smem_table() > MAX_SMEM || s->smem_force() > MAX_SMEM || s->smem_nlist() > MAX_SMEM)
+    if (s->smem_force() > MAX_SMEM || s->smem_nlist() > MAX_SMEM || s->smem_energy() > MAX_SMEM)
         return fail(VBC_ERR_UNSTABLE,
-                    "a block's neighbourhood (%d particles, %d cells) does not fit in shared memory: "
-                    "the system is too dense",
-                    s->smax, s->cmax);
-    VBC_TRY(set_smem(k_stage_table<M>, s->smem_table()));
+                    "a supercell's neighbourhood (%d staged, %d own particles, %d list entries) does not fit in "
+                    "shared memory: the system is too dense",
+                    s->smax, s->omax, s->seg);
     VBC_TRY(set_smem(k_nlist<M>, s->smem_nlist()));
-    if constexpr (M::fp64) {
-        VBC_TRY(set_smem(k_count_f64, s->smem_count()));
-    } else {
-        VBC_TRY(set_smem(k_count_f32, s->smem_count()));
-    }
+    VBC_TRY(set_smem(k_count<M>, s->smem_count()));
     VBC_TRY(set_smem(k_chain<M>, s->smem_chain()));
     VBC_TRY(set_smem(k_force<M, EPI_FORCE>, s->smem_force()));
     VBC_TRY(set_smem(k_force<M, EPI_START>, s->smem_force()));
@@ -369,6 +358,7 @@ int configure_smem(vbc_system* s)
     VBC_TRY(set_smem(k_count_e<M>, s->smem_energy()));
     VBC_TRY(set_smem(k_chain_e<M>, s->smem_energy()));
     VBC_TRY(set_smem(k_energy<M>, s->smem_energy()));
+    VBC_TRY(set_smem(k_store_nlist, s->smem_store()));
     return VBC_OK;
 }
 
@@ -385,21 +375,17 @@ int enqueue_rebuild(vbc_system* s)
     pos_t* pos = (pos_t*)s->pos[s->cur];
     k_bin<M><<<nb, TPB, 0, s->stream>>>(pos, n, s->geom, s->morton_rank, s->cell_of, s->slot_of, s->cell_count,
                                         s->st);
-    const int nchunk = blocks_for(s->geom.ncell, SCAN_CHUNK);
-    k_scan_sums<<<nchunk, SCAN_TPB, 0, s->stream>>>(s->cell_count, s->geom.ncell, s->chunk_sum, s->st);
-    k_scan_apply<<<nchunk, SCAN_TPB, 0, s->stream>>>(s->cell_count, s->geom.ncell, s->chunk_sum, s->cell_start,
-                                                      s->st);
+    const int nchunk = blocks_for(s->npad, SCAN_CHUNK);
+    k_scan_sums<<<nchunk, SCAN_TPB, 0, s->stream>>>(s->cell_count, s->npad, s->chunk_sum, s->st);
+    k_scan_apply<<<nchunk, SCAN_TPB, 0, s->stream>>>(s->cell_count, s->npad, s->chunk_sum, s->cell_start, s->st);
     k_scatter<<<nb, TPB, 0, s->stream>>>(n, s->cell_of, s->slot_of, s->cell_start, s->order, s->st);
-    k_cellsort<<<blocks_for(s->geom.ncell, TPB), TPB, 0, s->stream>>>(s->geom.ncell, s->cell_start, s->id,
-                                                                       s->order, s->st);
+    k_cellsort<<<blocks_for(s->npad, TPB), TPB, 0, s->stream>>>(s->npad, s->cell_start, s->id, s->order, s->st);
     k_permute<M><<<nb, TPB, 0, s->stream>>>(n, s->order, s->x, s->v, s->id, pos, s->xt, s->vt, s->idt,
                                             (pos_t*)s->post, s->st);
     k_copyback<M><<<nb, TPB, 0, s->stream>>>(n, s->xt, s->vt, s->idt, (const pos_t*)s->post, s->x, s->v, s->id,
                                              pos, (pos_t*)s->xref, s->st);
-    k_stage_table<M><<<nb, TPB, s->smem_table(), s->stream>>>(n, s->geom, pos, s->morton_rank, s->rank_to_lin,
-                                                               s->cell_start, s->table(), s->st);
-    k_nlist<M><<<nb, TPB, s->smem_nlist(), s->stream>>>(n, s->geom, pos, s->morton_rank, s->cell_start, s->table(),
-                                                         s->lp, s->cap, s->nbr, s->nnb, s->st);
+    k_nlist<M><<<s->nsc, SC_TPB, s->smem_nlist(), s->stream>>>(s->geom, pos, s->grid(), s->caps(), s->lp, s->nbr,
+                                                                s->nnb, s->st);
     return check_launch(s, REBUILD_KERNELS);
 }
 
@@ -409,23 +395,19 @@ int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window)
     using pos_t = typename M::pos_t;
     using real = typename M::real;
     using real2 = typename M::real2;
-    const int n = (int)s->n;
-    const int nb = blocks_for(n, TPB);
     const pos_t* pos = (const pos_t*)s->pos[s->cur];
     CountOut out{n_out, want_window ? s->win : nullptr};
     {
         Timed t(s, VBC_K_COUNT);
-        if constexpr (M::fp64)
-            k_count_f64<<<nb, TPB, s->smem_count(), s->stream>>>(n, s->geom, s->coef, pos, s->list(), s->id,
-                                                                 s->table(), (real*)s->ds, (real2*)s->sA, out, s->st);
-        else
-            k_count_f32<<<nb, TPB, s->smem_count(), s->stream>>>(n, s->geom, s->coef, pos, s->list(), s->id,
-                                                                 s->table(), (real*)s->ds, (real2*)s->sA, out, s->st);
+        k_count<M><<<s->nsc, SC_TPB, s->smem_count(), s->stream>>>(s->geom, s->coef, pos, s->grid(), s->caps(),
+                                                                    s->nbr, s->nnb, s->id, (real*)s->ds,
+                                                                    (real2*)s->sA, out, s->st);
     }
     {
         Timed t(s, VBC_K_CHAIN);
-        k_chain<M><<<nb, TPB, s->smem_chain(), s->stream>>>(n, s->geom, s->coef, pos, s->list(), s->table(),
-                                                            (const real*)s->ds, (real2*)s->sA, s->st);
+        k_chain<M><<<s->nsc, SC_TPB, s->smem_chain(), s->stream>>>(s->geom, s->coef, pos, s->grid(), s->caps(),
+                                                                    s->nbr, s->nnb, (const real*)s->ds,
+                                                                    (real2*)s->sA, s->st);
     }
     return check_launch(s, 2);
 }
@@ -440,8 +422,8 @@ int enqueue_force(vbc_system* s, const StepArgs& a)
     pos_t* pos_next = (pos_t*)s->pos[s->cur ^ 1];
     {
         Timed t(s, VBC_K_FORCE);
-        k_force<M, EPI><<<blocks_for(n, TPB), TPB, s->smem_force(), s->stream>>>(
-            n, s->geom, s->coef, pos, s->list(), s->id, s->table(), (const real2*)s->sA, pos_next,
+        k_force<M, EPI><<<s->nsc, SC_TPB, s->smem_force(), s->stream>>>(
+            n, s->geom, s->coef, pos, s->grid(), s->caps(), s->nbr, s->nnb, s->id, (const real2*)s->sA, pos_next,
             (const pos_t*)s->xref, a, s->st);
     }
     VBC_TRY(check_launch(s));
@@ -453,17 +435,17 @@ template <class M>
 int enqueue_energy(vbc_system* s)
 {
     using pos_t = typename M::pos_t;
-    const int n = (int)s->n;
     {
         Timed t(s, VBC_K_ENERGY);
         const pos_t* pos = (const pos_t*)s->pos[s->cur];
-        const int nb = blocks_for(n, TPB);
-        k_count_e<M><<<nb, TPB, s->smem_energy(), s->stream>>>(n, s->geom, s->coef, pos, s->list(), s->table(),
-                                                                s->e_sd, s->st);
-        k_chain_e<M><<<nb, TPB, s->smem_energy(), s->stream>>>(n, s->geom, s->coef, pos, s->list(), s->table(),
-                                                                s->e_sd, s->e_A, s->st);
-        k_energy<M><<<nb, TPB, s->smem_energy(), s->stream>>>(n, s->geom, s->coef, pos, s->list(), s->table(),
-                                                               s->e_sd, s->e_A, s->partial, s->ppairs, s->st);
+        const int nb = s->nsc;
+        k_count_e<M><<<nb, SC_TPB, s->smem_energy(), s->stream>>>(s->geom, s->coef, pos, s->grid(), s->caps(),
+                                                                   s->nbr, s->nnb, s->e_sd, s->st);
+        k_chain_e<M><<<nb, SC_TPB, s->smem_energy(), s->stream>>>(s->geom, s->coef, pos, s->grid(), s->caps(),
+                                                                   s->nbr, s->nnb, s->e_sd, s->e_A, s->st);
+        k_energy<M><<<nb, SC_TPB, s->smem_energy(), s->stream>>>(s->geom, s->coef, pos, s->grid(), s->caps(),
+                                                                  s->nbr, s->nnb, s->e_sd, s->e_A, s->partial,
+                                                                  s->ppairs, s->st);
         k_reduce_final<<<1, RED_TPB, 0, s->stream>>>(nb, s->partial, s->ppairs, s->red, s->st);
     }
     return check_launch(s, 4);
@@ -496,31 +478,28 @@ int grow(vbc_system* s)
             return fail(VBC_ERR_NLIST_OVERFLOW, "a particle has %d neighbours within r_c + skin, above the limit %d",
                         need, MAX_CAP);
         int cap = std::max(s->cap + s->cap / 2, need + need / 4 + 8);
-        cap = std::min((cap + 7) & ~7, MAX_CAP);
-        dfree(s->nbr);
-        VBC_TRY(dalloc(s->nbr, (size_t)cap * (size_t)s->n));
-        s->cap = cap;
+        s->cap = std::min((cap + 7) & ~7, MAX_CAP);
     }
     if (h.stage_overflow) {
-        if (h.max_stage_cells > s->cmax) {
-            const int cmax = pow2_at_least(h.max_stage_cells + h.max_stage_cells / 4);
-            if (cmax > MAX_CMAX)
-                return fail(VBC_ERR_UNSTABLE, "a block's neighbourhood spans %d cells, above the limit %d",
-                            h.max_stage_cells, MAX_CMAX);
-            dfree(s->tb_base);
-            dfree(s->tb_off);
-            dfree(s->tb_rank);
-            VBC_TRY(dalloc(s->tb_base, (size_t)s->nblk * cmax));
-            VBC_TRY(dalloc(s->tb_off, (size_t)s->nblk * (cmax + 1)));
-            VBC_TRY(dalloc(s->tb_rank, (size_t)s->nblk * cmax));
-            s->cmax = cmax;
-        }
         if (h.max_stage > s->smax) {
             const int smax = ((h.max_stage + h.max_stage / 8 + 63) / 64) * 64;
             if (smax > MAX_STAGE)
-                return fail(VBC_ERR_UNSTABLE, "a block's neighbourhood holds %d particles, above the limit %d",
+                return fail(VBC_ERR_UNSTABLE, "a supercell's neighbourhood holds %d particles, above the limit %d",
                             h.max_stage, MAX_STAGE);
             s->smax = smax;
+        }
+        if (h.max_own > s->omax) {
+            const int omax = ((h.max_own + h.max_own / 4 + 31) / 32) * 32;
+            if (omax > MAX_OWN)
+                return fail(VBC_ERR_UNSTABLE, "a supercell holds %d particles, above the limit %d", h.max_own,
+                            MAX_OWN);
+            s->omax = omax;
+        }
+        if (h.max_seg > s->seg) {
+            const int seg = ((h.max_seg + h.max_seg / 4 + 63) / 64) * 64;
+            dfree(s->nbr);
+            VBC_TRY(dalloc(s->nbr, (size_t)seg * (size_t)s->nsc));
+            s->seg = seg;
         }
     }
     VBC_TRY(configure(s));
@@ -831,8 +810,13 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
                              "box edge %g holds fewer than 3 cells of r_c + skin = %g", s->box[a], s->rlist));
         g.nc[a] = (int)std::min(ncd, 1024.0);
     }
-    if ((double)g.nc[0] * g.nc[1] * g.nc[2] > 2.0e9) return bail(fail(VBC_ERR_INVALID_ARG, "cell grid too large"));
+    if ((double)(g.nc[0] + 1) * (g.nc[1] + 1) * (g.nc[2] + 1) > 2.0e9)
+        return bail(fail(VBC_ERR_INVALID_ARG, "cell grid too large"));
     g.ncell = g.nc[0] * g.nc[1] * g.nc[2];
+    int pc[3];
+    for (int a = 0; a < 3; ++a) pc[a] = g.nc[a] + (g.nc[a] & 1);  // padded to even extents
+    s->npad = pc[0] * pc[1] * pc[2];
+    s->nsc = s->npad / 8;
     g.s32 = (float)g.s32d[0];
     g.s32sq = (float)(g.s32d[0] * g.s32d[0]);
     {
@@ -845,17 +829,15 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     const double rho = (double)s->n / (s->box[0] * s->box[1] * s->box[2]);
     const double kbar = rho * 4.18879020478639098 * s->rlist * s->rlist * s->rlist;  // 4 pi / 3
     int cap = cfg->nlist_cap > 0 ? cfg->nlist_cap : (int)std::ceil(1.3 * kbar + 6.0 * std::sqrt(kbar) + 12.0);
-    s->cap = std::min(std::max(cap, 1), MAX_CAP);
+    s->cap = std::min((std::max(cap, 1) + 7) & ~7, MAX_CAP);
     {
-        // a block of TPB particles covers about TPB / rho_cell cells; stage its dilated neighbourhood
+        // a supercell owns 8 cells and stages 64; lists hold about kbar entries per particle
         const double rho_cell = (double)s->n / g.ncell;
-        const double span = std::cbrt(TPB / std::max(rho_cell, 1e-9));
-        const double cells = std::min((double)g.ncell, 1.2 * std::pow(span + 2.0, 3.0));
-        s->cmax = std::min(std::max(pow2_at_least((int)std::ceil(1.5 * cells)), 64), MAX_CMAX);
-        const double parts = std::min((double)s->n, cells * rho_cell + 32.0);
-        s->smax = std::min(((int)std::ceil(parts) + 63) / 64 * 64, MAX_STAGE);
+        s->smax = std::min((((int)std::ceil(1.5 * 64.0 * rho_cell) + 64) + 63) / 64 * 64, MAX_STAGE);
+        s->omax = std::min(((int)std::ceil(2.0 * 8.0 * rho_cell) + 32 + 31) / 32 * 32, MAX_OWN);
+        const double entries = 8.0 * rho_cell * (std::min(kbar, (double)s->cap) + 4.0);
+        s->seg = (int)std::min(((long long)std::ceil(1.5 * entries) + 256 + 63) / 64 * 64, 1LL << 24);
     }
-    s->nblk = blocks_for(s->n, TPB);
 
     {
         cudaError_t e = cudaGetDevice(&s->device);
@@ -883,25 +865,21 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     ALLOC(dalloc_bytes(s->pos[1], n * s->pos_bytes()));
     ALLOC(dalloc_bytes(s->post, n * s->pos_bytes()));
     ALLOC(dalloc_bytes(s->xref, n * s->pos_bytes()));
-    ALLOC(dalloc(s->nbr, (size_t)s->cap * n));
+    ALLOC(dalloc(s->nbr, (size_t)s->seg * (size_t)s->nsc));
     ALLOC(dalloc(s->nnb, n));
     ALLOC(dalloc(s->cell_of, n));
     ALLOC(dalloc(s->slot_of, n));
     ALLOC(dalloc(s->order, n));
-    ALLOC(dalloc(s->cell_count, (size_t)g.ncell));
-    ALLOC(dalloc(s->cell_start, (size_t)g.ncell + 1));
+    ALLOC(dalloc(s->cell_count, (size_t)s->npad));
+    ALLOC(dalloc(s->cell_start, (size_t)s->npad + 1));
     ALLOC(dalloc(s->morton_rank, (size_t)g.ncell));
-    ALLOC(dalloc(s->rank_to_lin, (size_t)g.ncell));
-    ALLOC(dalloc(s->chunk_sum, (size_t)blocks_for(g.ncell, SCAN_CHUNK)));
-    ALLOC(dalloc(s->tb_base, (size_t)s->nblk * s->cmax));
-    ALLOC(dalloc(s->tb_off, (size_t)s->nblk * (s->cmax + 1)));
-    ALLOC(dalloc(s->tb_rank, (size_t)s->nblk * s->cmax));
-    ALLOC(dalloc(s->tb_n, (size_t)s->nblk));
+    ALLOC(dalloc(s->sc_org, (size_t)s->nsc));
+    ALLOC(dalloc(s->chunk_sum, (size_t)blocks_for(s->npad, SCAN_CHUNK)));
     ALLOC(dalloc_bytes(s->ds, n * s->real_bytes()));
     ALLOC(dalloc_bytes(s->sA, n * 2 * s->real_bytes()));
     ALLOC(dalloc(s->st, 1));
-    ALLOC(dalloc(s->partial, 2 * (size_t)s->nblk));
-    ALLOC(dalloc(s->ppairs, (size_t)s->nblk));
+    ALLOC(dalloc(s->partial, 2 * (size_t)s->nsc));
+    ALLOC(dalloc(s->ppairs, (size_t)s->nsc));
     ALLOC(dalloc(s->red, 2));
     ALLOC(dalloc(s->win, 1));
     ALLOC(dalloc(s->e_sd, n));
@@ -912,29 +890,33 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
         return bail(fail(VBC_ERR_OOM, "pinned host allocation failed"));
     if ((rc = configure(s)) != VBC_OK) return bail(rc);
 
-    // Morton order of the cells: rank of each linear cell index along the curve, and back
+    // Morton order of the padded grid's cells.  Each aligned 2x2x2 block has
+    // eight consecutive codes, so supercell s holds the ranks 8s .. 8s+7; its
+    // rank-8s cell (even coordinates) is its origin.  Phantom cells (beyond
+    // the real grid) are ranked but never hold a particle.
     {
-        std::vector<std::pair<uint32_t, int>> code((size_t)g.ncell);
-        for (int z = 0; z < g.nc[2]; ++z)
-            for (int y = 0; y < g.nc[1]; ++y)
-                for (int x = 0; x < g.nc[0]; ++x) {
-                    const int lin = (z * g.nc[1] + y) * g.nc[0] + x;
+        std::vector<std::pair<uint32_t, int>> code((size_t)s->npad);
+        for (int z = 0; z < pc[2]; ++z)
+            for (int y = 0; y < pc[1]; ++y)
+                for (int x = 0; x < pc[0]; ++x) {
+                    const int lin = (z * pc[1] + y) * pc[0] + x;
                     code[lin] = {spread3((uint32_t)x) | (spread3((uint32_t)y) << 1) | (spread3((uint32_t)z) << 2), lin};
                 }
         std::sort(code.begin(), code.end());
-        std::vector<int> rank((size_t)g.ncell), back((size_t)g.ncell);
-        for (int r = 0; r < g.ncell; ++r) {
-            rank[code[r].second] = r;
-            back[r] = code[r].second;
+        std::vector<int> rank((size_t)g.ncell), org((size_t)s->nsc);
+        for (int r = 0; r < s->npad; ++r) {
+            const int lin = code[r].second;
+            const int x = lin % pc[0], y = (lin / pc[0]) % pc[1], z = lin / (pc[0] * pc[1]);
+            if (r % 8 == 0) org[r / 8] = x | (y << 10) | (z << 20);
+            if (x < g.nc[0] && y < g.nc[1] && z < g.nc[2]) rank[(z * g.nc[1] + y) * g.nc[0] + x] = r;
         }
         if (cudaMemcpy(s->morton_rank, rank.data(), rank.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(s->rank_to_lin, back.data(), back.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+            cudaMemcpy(s->sc_org, org.data(), org.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(fail(VBC_ERR_CUDA, "upload of the Morton tables failed"));
     }
-    if (cudaMemsetAsync(s->cell_count, 0, (size_t)g.ncell * sizeof(int), s->stream) != cudaSuccess ||
+    if (cudaMemsetAsync(s->cell_count, 0, (size_t)s->npad * sizeof(int), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->st, 0, sizeof(Status), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->nnb, 0, n * sizeof(int), s->stream) != cudaSuccess ||
-        cudaMemsetAsync(s->tb_n, 0, (size_t)s->nblk * sizeof(int), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->sA, 0, n * 2 * s->real_bytes(), s->stream) != cudaSuccess)
         return bail(fail(VBC_ERR_CUDA, "initial memset failed"));
     k_iota<<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>((int)s->n, s->id);
@@ -1041,8 +1023,8 @@ int vbc_get_neighbors(vbc_system* s, int32_t* nnb, int32_t* nbr, int32_t cap, in
             cudaMemsetAsync(d_nbr, 0xff, n * (size_t)cap * sizeof(int), s->stream);
         }
     }
-    k_store_nlist<<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>((int)n, cap, s->id, s->list(), s->table(), d_nnb,
-                                                                d_nbr);
+    k_store_nlist<<<s->nsc, SC_TPB, s->smem_store(), s->stream>>>(s->geom, s->grid(), s->caps(), s->nbr, s->nnb,
+                                                                   s->id, cap, d_nnb, d_nbr);
     int rc = check_launch(s);
     if (rc == VBC_OK && !outputs_on_device) {
         if (nnb && cudaMemcpyAsync(nnb, d_nnb, n * sizeof(int), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)

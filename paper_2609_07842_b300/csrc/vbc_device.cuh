@@ -71,12 +71,12 @@ struct Status {
     int overflow;       // 1: a list exceeded the capacity at the last build (k_nlist)
     int frozen;         // 1: a non-finite position or velocity was produced (k_force)
     int crowded;        // 1: a cell held more than MAX_CELL particles (k_scan_apply)
-    int max_stage;      // largest number of particles a block stages (last build)
+    int max_stage;      // largest number of particles a supercell stages (last build)
     int max_nnb;        // longest list found at the last build (uncapped)
     int frozen_iter;    // loop iteration at which the overflow happened
-    int max_stage_cells;// largest number of cells a block stages (last build)
-    int stage_overflow; // 1: a block's neighbourhood exceeded the staging capacity (k_nlist)
-    int pad0;
+    int max_own;        // largest number of particles of one supercell (last build)
+    int stage_overflow; // 1: a supercell exceeded a staging or list-segment capacity (k_nlist)
+    int max_seg;        // largest list segment (entries) of one supercell (last build)
     long long nnb_sum;  // sum of list lengths at the last build
     long long rebuilds; // builds so far
     long long in_window;// particles inside the switching window at the last count

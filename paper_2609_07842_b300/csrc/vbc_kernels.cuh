@@ -1,25 +1,27 @@
 // vbc_kernels.cuh -- CUDA kernels of the VBC path (sm_103a).
 //
-// Particles are stored in Morton order of their cells.  Kernels that walk
-// neighbour lists run in blocks of TPB = 128 consecutive particles, and each
-// block first copies the union of its particles' 27-cell neighbourhoods (a
-// set of whole cells, i.e. contiguous runs of the sorted arrays) into shared
-// memory: the staging.  Neighbour lists store 16-bit indices into that
-// staging, so a pass reads 2 bytes per list entry from HBM and serves every
-// neighbour lookup from shared memory.
+// Particles are stored sorted by cell, the cells ranked along a Morton curve.
+// The cell grid (cells at least r_c + skin wide) is padded to even extents
+// with empty phantom cells, so every aligned 2x2x2 block of cells -- a
+// supercell -- holds eight consecutive ranks and its particles form one
+// contiguous range of the sorted arrays.  Every kernel that walks neighbour
+// lists runs one block per supercell.  The block first copies the 4x4x4 real
+// cells around its supercell into shared memory (the staging), and the lists
+// hold 16-bit indices into that staging, so a pass reads 2 bytes per list
+// entry from HBM and serves every neighbour lookup from shared memory.
 //
 // One MD step:
 //   rebuild (only when a particle moved more than skin/2 since the last build):
 //     k_bin -> k_scan_sums -> k_scan_apply -> k_scatter -> k_cellsort ->
-//     k_permute -> k_copyback -> k_stage_table -> k_nlist
+//     k_permute -> k_copyback -> k_nlist
 //   k_count   pass 1: n_i, s_i, s'_i                        (Eqs. counter, Psidelta)
 //   k_chain   A_i = s'_i sum_j s_j V_a(r_ij), window particles only
 //   k_force   pass 2: F_i, fused with the BAOAB update of the state
 //   k_count_e, k_chain_e, k_energy   FP64 U, W and pair count (on request only)
 // The rebuild kernels read a device flag and return at once when no rebuild
 // is due, so the host never waits on the device between steps.  Every pass
-// walks a full (both-direction) list, one thread per particle, and
-// accumulates without atomics, so results do not depend on scheduling.
+// walks a full (both-direction) list and sums without floating-point
+// atomics, so results do not depend on scheduling.
 #pragma once
 
 #include "vbc_device.cuh"
@@ -27,10 +29,11 @@
 namespace vbc {
 
 constexpr int TPB = 128;          // threads per block of the per-particle kernels
+constexpr int SC_TPB = 128;       // threads per block of the supercell kernels
+constexpr int SC_CELLS = 64;      // staged cells per supercell (4 x 4 x 4)
 constexpr int SCAN_CHUNK = 2048;  // cells per block in the two-pass scan
 constexpr int SCAN_TPB = 256;
 constexpr int MAX_CELL = 512;     // a denser cell means the system has collapsed
-constexpr int HASH_SIZE = 4096;   // open-addressing set of a block's neighbour cells
 
 enum Epilogue { EPI_FORCE = 0, EPI_START = 1, EPI_FINISH = 2, EPI_FINISH_START = 3 };
 
@@ -47,7 +50,8 @@ __global__ void __launch_bounds__(TPB) k_bin(const typename M::pos_t* __restrict
         st->max_nnb = 0;
         st->nnb_sum = 0;
         st->max_stage = 0;
-        st->max_stage_cells = 0;
+        st->max_own = 0;
+        st->max_seg = 0;
     }
     if (i >= n) return;
     const int3 c = cell_of_pos<M>(pos[i], g);
@@ -220,70 +224,160 @@ __global__ void __launch_bounds__(TPB) k_copyback(int n, const unsigned long lon
     xref[k] = p;
 }
 
-// ================================================================ staging
-// A block's staging is a list of runs: maximal sequences of cells with
-// consecutive Morton ranks, i.e. contiguous ranges of the sorted particle
-// arrays.  Run k of block b starts at sorted particle base[b*cmax + k], holds
-// off[b*(cmax+1) + k + 1] - off[b*(cmax+1) + k] particles at that staging
-// offset, and begins with the cell of rank rank[b*cmax + k].
-struct StageTable {
-    int* base;
-    int* off;
-    int* rank;
-    int* n;    // runs per block
-    int cmax;  // capacity in cells (and runs) per block
-    int smax;  // capacity in staged particles per block
+
+// ================================================================ supercells
+// Staged cells are numbered k = 16 lz + 4 ly + lx (l in 0..3 along each axis,
+// the supercell's own cells at l in {1, 2}) and copied in that order, so the
+// three cells of one x row of a particle's 27-cell neighbourhood occupy one
+// contiguous range of the staging.  Neighbour cells wrap on the real grid,
+// which needs at least 3 cells per axis; with exactly 3 a staged cell can
+// appear twice, but the 27 cells around any one particle stay distinct.
+
+struct SuperGrid {
+    const int* morton_rank;  // real linear cell index -> rank on the padded Morton curve
+    const int* sc_org;       // supercell -> coordinates of its first cell, x | y << 10 | z << 20
+    const int* cell_start;   // rank -> sorted index of its first particle; [npad + 1]
 };
 
-// A list: near entries (closer than max(r_r, r_l) at the build) in rows
-// 0..nn-1 from the front, far entries (up to r_list) in rows cap-1, cap-2, ...
-// from the back, column-major nbr[row * n + i]; nnb[i] = nn | nf << 16.
-struct ListRef {
-    const uint16_t* nbr;
-    const int* nnb;
-    int cap;
+// Per-supercell capacities (grown after an overflow).
+struct SuperCaps {
+    int smax;  // staged particles
+    int omax;  // own particles (multiple of 4)
+    int seg;   // list entries of one supercell (multiple of 64)
+    int cap;   // list entries of one particle (multiple of 8)
 };
 
-template <class F>
-__device__ __forceinline__ void for_entries(const ListRef& L, int n, int i, int nn, int nf, F&& f)
-{
-#pragma unroll 4
-    for (int t = 0; t < nn; ++t) f((int)__ldg(L.nbr + (size_t)t * n + i));
-#pragma unroll 4
-    for (int t = 0; t < nf; ++t) f((int)__ldg(L.nbr + (size_t)(L.cap - 1 - t) * n + i));
-}
+struct SuperTab {
+    int base[SC_CELLS];     // sorted index of each staged cell's first particle
+    int off[SC_CELLS + 1];  // staging offset of each staged cell; off[SC_CELLS] = total
+    int own[9];             // cell_start of ranks 8s .. 8s+8
+    int sw[SC_TPB / 32];    // scan scratch
+};
 
-// Loads block b's run table (base, off) into shared memory; returns the
-// number of staged particles.  s_base and s_off hold cmax and cmax + 1 ints.
-__device__ __forceinline__ int load_runs(const StageTable& tb, int b, int* s_base, int* s_off, int& R)
+// Exclusive scan of a[0..n) in shared memory, in place, with a[n] = total.
+// Called by the whole block once a[] is written.
+__device__ __forceinline__ int scan_in_place(int* a, int n, int* sw)
 {
-    R = tb.n[b];
-    for (int k = threadIdx.x; k < R; k += blockDim.x) s_base[k] = tb.base[(size_t)b * tb.cmax + k];
-    for (int k = threadIdx.x; k <= R; k += blockDim.x) s_off[k] = tb.off[(size_t)b * (tb.cmax + 1) + k];
     __syncthreads();
-    return s_off[R];
+    const int per = (n + SC_TPB - 1) / SC_TPB;
+    const int b = min(n, (int)threadIdx.x * per), e = min(n, b + per);
+    int s = 0;
+    for (int k = b; k < e; ++k) s += a[k];
+    int total;
+    int off = block_exclusive_scan<SC_TPB>(s, sw, total);
+    for (int k = b; k < e; ++k) {
+        const int v = a[k];
+        a[k] = off;
+        off += v;
+    }
+    if (threadIdx.x == 0) a[n] = total;
+    __syncthreads();
+    return total;
 }
 
-// Copies every staged particle: copy(staging index, sorted index), one warp per run.
-template <class F>
-__device__ __forceinline__ void stage_runs(const int* s_base, const int* s_off, int R, F&& copy)
+// Reads the staging table of supercell s (whole block).  Returns the first
+// own particle p0, the number of own particles and of staged particles.
+__device__ __forceinline__ void load_supercell(int s, const Geom& g, const SuperGrid& G, SuperTab& T, int& p0,
+                                               int& n_own, int& total)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int k = warp; k < R; k += (int)(blockDim.x >> 5)) {
-        const int b = s_base[k], o = s_off[k], len = s_off[k + 1] - o;
-        for (int l = lane; l < len; l += 32) copy(o + l, b + l);
+    const int t = threadIdx.x;
+    int cnt = 0;
+    if (t < SC_CELLS) {
+        const int org = __ldg(G.sc_org + s);
+        int x = (org & 1023) - 1 + (t & 3);
+        int y = ((org >> 10) & 1023) - 1 + ((t >> 2) & 3);
+        int z = (org >> 20) - 1 + (t >> 4);
+        x += x < 0 ? g.nc[0] : (x >= g.nc[0] ? -g.nc[0] : 0);
+        y += y < 0 ? g.nc[1] : (y >= g.nc[1] ? -g.nc[1] : 0);
+        z += z < 0 ? g.nc[2] : (z >= g.nc[2] ? -g.nc[2] : 0);
+        const int r = __ldg(G.morton_rank + (z * g.nc[1] + y) * g.nc[0] + x);
+        const int b = __ldg(G.cell_start + r);
+        cnt = __ldg(G.cell_start + r + 1) - b;
+        T.base[t] = b;
+    }
+    if (t < 9) T.own[t] = __ldg(G.cell_start + 8 * s + t);
+    int tot;
+    const int o = block_exclusive_scan<SC_TPB>(cnt, T.sw, tot);
+    if (t < SC_CELLS) T.off[t] = o;
+    if (t == 0) T.off[SC_CELLS] = tot;
+    __syncthreads();
+    p0 = T.own[0];
+    n_own = T.own[8] - p0;
+    total = tot;
+}
+
+// Staged cell holding staging index m: the largest k with off[k] <= m.
+__device__ __forceinline__ int staged_cell(const int* off, int m)
+{
+    int k = 0;
+#pragma unroll
+    for (int step = 32; step > 0; step >>= 1)
+        if (off[k + step] <= m) k += step;
+    return k;
+}
+
+// Sorted index of staging index m.
+__device__ __forceinline__ int staged_index(const SuperTab& T, int m)
+{
+    const int k = staged_cell(T.off, m);
+    return T.base[k] + (m - T.off[k]);
+}
+
+// Copies every staged particle: put(m, get(j)) for staging index m and
+// sorted index j, B loads in flight per thread.
+template <class V, int B = 4, class Get, class Put>
+__device__ __forceinline__ void stage(const SuperTab& T, int total, Get&& get, Put&& put)
+{
+    for (int m0 = threadIdx.x; m0 < total; m0 += SC_TPB * B) {
+        int jj[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            const int m = m0 + u * SC_TPB;
+            jj[u] = m < total ? staged_index(T, m) : -1;
+        }
+        V v[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u)
+            if (jj[u] >= 0) v[u] = get(jj[u]);
+#pragma unroll
+        for (int u = 0; u < B; ++u)
+            if (jj[u] >= 0) put(m0 + u * SC_TPB, v[u]);
     }
 }
 
-// Dynamic shared memory of the pass kernels: base[cmax] | off[cmax+1] | staged arrays.
-__host__ __device__ inline size_t stage_header_bytes(int cmax) { return (((size_t)(2 * cmax + 1) * 4) + 15) & ~(size_t)15; }
-// ... of k_stage_table: hash[HASH_SIZE] | cells[cmax] | starts[cmax+1]
-__host__ __device__ inline size_t stage_table_smem(int cmax) { return (size_t)(HASH_SIZE + 2 * cmax + 1) * 4; }
-// ... of k_nlist: base[cmax] | off[cmax+1] | rank[cmax] | staged positions
-__host__ __device__ inline size_t nlist_header_bytes(int cmax) { return (((size_t)(3 * cmax + 1) * 4) + 15) & ~(size_t)15; }
+// Own cell (0..7, Morton low bits x | y << 1 | z << 2) of own particle p.
+__device__ __forceinline__ int own_cell(const SuperTab& T, int p)
+{
+    int b = 0;
+    if (T.own[b + 4] <= p) b += 4;
+    if (T.own[b + 2] <= p) b += 2;
+    if (T.own[b + 1] <= p) b += 1;
+    return b;
+}
 
-// Near (0), far (1) or beyond the list radius (-1), from exact integer squared
-// separations in the FP32 mode.
+// Staged cell number of own cell b.
+__device__ __forceinline__ int own_staged_cell(int b) { return 21 + (b & 1) + ((b >> 1) & 1) * 4 + (b >> 2) * 16; }
+
+// ---------------------------------------------------------------- lists
+// The lists of supercell s occupy nbr[s * seg ...]: the rows of its own
+// particles in sorted order, each padded to a multiple of 4 entries.  A row
+// holds the near entries (closer than max(r_r, r_l) at the build) first,
+// then the far ones (up to r_c + skin); pads repeat the particle's own
+// staging index, which adds exactly nothing to a force (d = 0).
+// nnb[p] = near | far << 16.
+__device__ __forceinline__ int pad4(int v) { return (v + 3) & ~3; }
+__device__ __forceinline__ int row_len(int w) { return (w & 0xffff) + (w >> 16); }
+
+// Row offsets of the own particles (entries from the segment start) in
+// roff[0 .. n_own], computed by the whole block; returns the padded total.
+__device__ __forceinline__ int own_rows(const int* __restrict__ nnb, int p0, int n_own, int* roff, int* sw)
+{
+    for (int j = threadIdx.x; j < n_own; j += SC_TPB) roff[j] = pad4(row_len(__ldg(nnb + p0 + j)));
+    return scan_in_place(roff, n_own, sw);
+}
+
+// Near (0), far (1) or beyond the list radius (-1), from exact integer
+// squared separations in the FP32 mode.
 struct ListParams {
     unsigned long long rlist2_fix, near2_fix;
     double rlist2, near2;
@@ -314,233 +408,178 @@ struct ListTest<ModeF64> {
     }
 };
 
-// Neighbour cell d (0..26) of cell (x, y, z), periodic.
-__device__ __forceinline__ int neighbour_cell_lin(int x, int y, int z, int d, const Geom& g)
+// ---------------------------------------------------------------- shared-memory layouts
+// Dynamic shared memory of each supercell kernel, carved in 16-byte aligned
+// pieces; the host sizes its launches with the same functions.
+__host__ __device__ constexpr size_t al16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+struct NlistLayout {
+    size_t rows, roff, rnn, total;
+};
+__host__ __device__ inline NlistLayout nlist_layout(const SuperCaps& cp, size_t pos_bytes)
 {
-    x += d % 3 - 1;
-    y += (d / 3) % 3 - 1;
-    z += d / 9 - 1;
-    x = x < 0 ? x + g.nc[0] : (x >= g.nc[0] ? x - g.nc[0] : x);
-    y = y < 0 ? y + g.nc[1] : (y >= g.nc[1] ? y - g.nc[1] : y);
-    z = z < 0 ? z + g.nc[2] : (z >= g.nc[2] ? z - g.nc[2] : z);
-    return (z * g.nc[1] + y) * g.nc[0] + x;
+    NlistLayout l{};
+    l.rows = al16((size_t)cp.smax * pos_bytes);
+    l.roff = l.rows + al16((size_t)cp.omax * cp.cap * 2);
+    l.rnn = l.roff + al16((size_t)(cp.omax + 1) * 4);
+    l.total = l.rnn + al16((size_t)cp.omax * 4);
+    return l;
 }
 
-// ================================================================ rebuild: staging tables
-// For each block of TPB sorted particles: the set of cells in the
-// 27-neighbourhoods of its particles' cells (open-addressing hash in shared
-// memory), sorted by Morton rank and merged into runs of consecutive ranks,
-// with staging offsets; written to the global run table.
-template <class M>
-__global__ void __launch_bounds__(TPB) k_stage_table(int n, Geom g, const typename M::pos_t* __restrict__ pos,
-                                                     const int* __restrict__ morton_rank,
-                                                     const int* __restrict__ rank_to_lin,
-                                                     const int* __restrict__ cell_start, StageTable tb, Status* st)
+// k_count, k_chain, the energy kernels and k_store_nlist: staged positions,
+// an optional staged value per particle, row offsets and a particle list.
+struct PassLayout {
+    size_t val, roff, plist, total;
+};
+__host__ __device__ inline PassLayout pass_layout(const SuperCaps& cp, size_t pos_bytes, size_t val_bytes)
 {
+    PassLayout l{};
+    l.val = al16((size_t)cp.smax * pos_bytes);
+    l.roff = l.val + al16((size_t)cp.smax * val_bytes);
+    l.plist = l.roff + al16((size_t)(cp.omax + 1) * 4);
+    l.total = l.plist + al16((size_t)cp.omax * 4);
+    return l;
+}
+
+// k_force: staged positions (with s_j in the spare word) and A_j, row
+// offsets, the owner of each 4-entry chunk and the chunks' partial forces.
+struct ForceLayout {
+    size_t sA, roff, cown, cpart, total;
+};
+__host__ __device__ inline ForceLayout force_layout(const SuperCaps& cp, size_t pos_bytes, size_t real_bytes)
+{
+    ForceLayout l{};
+    const size_t nch = (size_t)cp.seg / 4;
+    l.sA = al16((size_t)cp.smax * pos_bytes);
+    l.roff = l.sA + al16((size_t)cp.smax * real_bytes);
+    l.cown = l.roff + al16((size_t)(cp.omax + 1) * 4);
+    l.cpart = l.cown + al16(nch * 2);
+    l.total = l.cpart + al16(3 * nch * real_bytes);
+    return l;
+}
+
+// ================================================================ rebuild: lists
+// One block per supercell: stage the 4x4x4 cells, then each thread takes own
+// particles and scans the 9 contiguous x rows of their 27-cell neighbourhood,
+// writing a two-ended row (near from the front, far from the back) into
+// shared memory; the rows are then packed into the supercell's segment.
+template <class M>
+__global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_t* __restrict__ pos, SuperGrid G,
+                                                  SuperCaps cp, ListParams lp, uint16_t* __restrict__ nbr,
+                                                  int* __restrict__ nnb, Status* st)
+{
+    using pos_t = typename M::pos_t;
+    // raises `overflow` and `stage_overflow` itself, so it does not test them
     if (!st->rebuild || st->frozen || st->crowded) return;
+    __shared__ SuperTab T;
+    __shared__ int s_mx;
+    __shared__ unsigned long long s_sum;
     extern __shared__ __align__(16) unsigned char smem[];
-    int* hash = (int*)smem;
-    int* cells = hash + HASH_SIZE;
-    int* starts = cells + tb.cmax;
-    __shared__ int s_rank[TPB];
-    __shared__ int s_uniq[TPB];
-    __shared__ int s_nu, s_nc;
-    __shared__ int sw[TPB / 32];
-    const int b = blockIdx.x;
-    const int i = b * TPB + threadIdx.x;
-    int rank_i = -1;
-    if (i < n) {
-        const int3 c = cell_of_pos<M>(pos[i], g);
-        rank_i = morton_rank[(c.z * g.nc[1] + c.y) * g.nc[0] + c.x];
+    const int t = threadIdx.x;
+    int p0, n_own, total;
+    load_supercell(blockIdx.x, g, G, T, p0, n_own, total);
+    if (t == 0) {
+        atomicMax(&st->max_stage, total);
+        atomicMax(&st->max_own, n_own);
+        s_mx = 0;
+        s_sum = 0;
     }
-    s_rank[threadIdx.x] = rank_i;
-    for (int h = threadIdx.x; h < HASH_SIZE; h += TPB) hash[h] = -1;
-    if (threadIdx.x == 0) {
-        s_nu = 0;
-        s_nc = 0;
-    }
-    __syncthreads();
-    // unique cells of the block (ranks ascend along the sorted particles)
-    if (i < n && (threadIdx.x == 0 || s_rank[threadIdx.x - 1] != rank_i)) s_uniq[atomicAdd(&s_nu, 1)] = rank_i;
-    __syncthreads();
-    const int U = s_nu;
-    for (int t = threadIdx.x; t < 27 * U; t += TPB) {
-        const int u = t / 27, d = t - 27 * u;
-        const int lin = rank_to_lin[s_uniq[u]];
-        const int r = morton_rank[neighbour_cell_lin(lin % g.nc[0], (lin / g.nc[0]) % g.nc[1],
-                                                     lin / (g.nc[0] * g.nc[1]), d, g)];
-        unsigned h = ((unsigned)r * 2654435761u) & (HASH_SIZE - 1);
-        for (int probe = 0; probe < HASH_SIZE; ++probe) {
-            const int old = atomicCAS(&hash[h], -1, r);
-            if (old == -1) {
-                const int idx = atomicAdd(&s_nc, 1);
-                if (idx < tb.cmax) cells[idx] = r;
-                break;
-            }
-            if (old == r) break;
-            h = (h + 1) & (HASH_SIZE - 1);
-        }
-    }
-    __syncthreads();
-    const int S = s_nc;
-    if (S > tb.cmax) {
-        if (threadIdx.x == 0) {
-            atomicMax(&st->max_stage_cells, S);
+    if (total > cp.smax || n_own > cp.omax) {
+        if (t == 0) {
             st->stage_overflow = 1;
             st->frozen_iter = (int)st->iter;
         }
         return;
     }
-    // sort the cells by rank (bitonic over the next power of two, padded)
-    int P = 1;
-    while (P < S) P <<= 1;
-    for (int k = S + threadIdx.x; k < P; k += TPB) cells[k] = 0x7fffffff;
+    const NlistLayout ly = nlist_layout(cp, sizeof(pos_t));
+    pos_t* spos = (pos_t*)smem;
+    uint16_t* rows = (uint16_t*)(smem + ly.rows);
+    int* roff = (int*)(smem + ly.roff);
+    int* rnn = (int*)(smem + ly.rnn);
+    stage<pos_t>(T, total, [&](int j) { return pos[j]; }, [&](int m, const pos_t& v) { spos[m] = v; });
     __syncthreads();
-    for (int k = 2; k <= P; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int t = threadIdx.x; t < P; t += TPB) {
-                const int o = t ^ j;
-                if (o > t) {
-                    const int a = cells[t], c = cells[o];
-                    if ((a > c) == ((t & k) == 0)) {
-                        cells[t] = c;
-                        cells[o] = a;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    // runs of consecutive ranks: start positions, consecutive cells per thread
-    const int per = (S + TPB - 1) / TPB;
-    const int k0 = min(S, (int)threadIdx.x * per), k1 = min(S, ((int)threadIdx.x + 1) * per);
-    int nstart = 0;
-    for (int k = k0; k < k1; ++k) nstart += (k == 0 || cells[k] != cells[k - 1] + 1);
-    int R;
-    int r = block_exclusive_scan<TPB>(nstart, sw, R);
-    for (int k = k0; k < k1; ++k)
-        if (k == 0 || cells[k] != cells[k - 1] + 1) starts[r++] = k;
-    if (threadIdx.x == 0) starts[R] = S;
-    __syncthreads();
-    // staging offsets of the runs
-    const int rper = (R + TPB - 1) / TPB;
-    const int q0 = min(R, (int)threadIdx.x * rper), q1 = min(R, ((int)threadIdx.x + 1) * rper);
-    int len = 0;
-    for (int q = q0; q < q1; ++q)
-        len += cell_start[cells[starts[q + 1] - 1] + 1] - cell_start[cells[starts[q]]];
-    int total;
-    int o = block_exclusive_scan<TPB>(len, sw, total);
-    for (int q = q0; q < q1; ++q) {
-        const int first = cells[starts[q]];
-        const int bq = cell_start[first];
-        tb.base[(size_t)b * tb.cmax + q] = bq;
-        tb.rank[(size_t)b * tb.cmax + q] = first;
-        tb.off[(size_t)b * (tb.cmax + 1) + q] = o;
-        o += cell_start[cells[starts[q + 1] - 1] + 1] - bq;
-    }
-    if (threadIdx.x == 0) {
-        tb.off[(size_t)b * (tb.cmax + 1) + R] = total;
-        tb.n[b] = R;
-        atomicMax(&st->max_stage, total);
-        atomicMax(&st->max_stage_cells, S);
-        if (total > tb.smax) {
-            st->stage_overflow = 1;
-            st->frozen_iter = (int)st->iter;
-        }
-    }
-}
-
-// ================================================================ rebuild: lists
-// Each particle's list of staged indices within r_list, near entries from the
-// front and far entries from the back (so that a pass walks neighbours of
-// similar distance together and the count pass can stop after the near ones).
-template <class M>
-__global__ void __launch_bounds__(TPB) k_nlist(int n, Geom g, const typename M::pos_t* __restrict__ pos,
-                                               const int* __restrict__ morton_rank,
-                                               const int* __restrict__ cell_start, StageTable tb, ListParams lp,
-                                               int cap, uint16_t* __restrict__ nbr, int* __restrict__ nnb,
-                                               Status* st)
-{
-    using pos_t = typename M::pos_t;
-    // raises `overflow` itself, so it does not test it; `stage_overflow` comes from k_stage_table
-    if (!st->rebuild || st->frozen || st->crowded || st->stage_overflow) return;
-    extern __shared__ __align__(16) unsigned char smem[];
-    int* s_base = (int*)smem;
-    int* s_off = s_base + tb.cmax;
-    int* s_rk = s_off + tb.cmax + 1;
-    pos_t* spos = (pos_t*)(smem + nlist_header_bytes(tb.cmax));
-    __shared__ int smx[TPB / 32];
-    __shared__ long long ssm[TPB / 32];
-    const int b = blockIdx.x;
-    int R;
-    load_runs(tb, b, s_base, s_off, R);
-    for (int k = threadIdx.x; k < R; k += TPB) s_rk[k] = tb.rank[(size_t)b * tb.cmax + k];
-    stage_runs(s_base, s_off, R, [&](int m, int j) { spos[m] = pos[j]; });
-    __syncthreads();
-    const int i = b * TPB + threadIdx.x;
-    int count = 0;
-    if (i < n) {
-        const pos_t pi = pos[i];
-        const int3 ci = cell_of_pos<M>(pi, g);
-        // staging position of cell rank r: run with the largest first rank <= r
-        auto locate = [&](int r) {
-            int lo = 0, hi = R - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_rk[mid] <= r) lo = mid;
-                else hi = mid - 1;
-            }
-            return s_off[lo] + (cell_start[r] - s_base[lo]);
-        };
-        const int m_self = locate(morton_rank[(ci.z * g.nc[1] + ci.y) * g.nc[0] + ci.x]) +
-                           (i - cell_start[morton_rank[(ci.z * g.nc[1] + ci.y) * g.nc[0] + ci.x]]);
+    int mx = 0;
+    long long sum = 0;
+    bool over = false;
+    for (int j = t; j < n_own; j += SC_TPB) {
+        const int p = p0 + j;
+        const int b = own_cell(T, p);
+        const int kb = own_staged_cell(b);
+        const int mself = T.off[kb] + (p - T.own[b]);
+        const pos_t pi = spos[mself];
+        uint16_t* row = rows + (size_t)j * cp.cap;
         int nn = 0, nf = 0;
-        for (int d = 0; d < 27; ++d) {
-            const int r = morton_rank[neighbour_cell_lin(ci.x, ci.y, ci.z, d, g)];
-            const int o = locate(r);
-            const int len = cell_start[r + 1] - cell_start[r];
-            for (int m = o; m < o + len; ++m) {
-                if (m == m_self) continue;
+        for (int d = 0; d < 9; ++d) {
+            const int k0 = kb + (d / 3 - 1) * 16 + (d % 3 - 1) * 4 - 1;
+            const int e = T.off[k0 + 3];
+            for (int m = T.off[k0]; m < e; ++m) {
+                if (m == mself) continue;
                 const int cl = ListTest<M>::cls(pi, spos[m], g, lp);
                 if (cl < 0) continue;
-                if (nn + nf < cap) {
-                    if (cl == 0) nbr[(size_t)nn * n + i] = (uint16_t)m;
-                    else nbr[(size_t)(cap - 1 - nf) * n + i] = (uint16_t)m;
-                }
+                if (nn + nf < cp.cap) row[cl == 0 ? nn : cp.cap - 1 - nf] = (uint16_t)m;
                 if (cl == 0) ++nn;
                 else ++nf;
             }
         }
-        count = nn + nf;
-        nnb[i] = nn | (nf << 16);
-        if (count > cap) {
+        const int len = nn + nf;
+        nnb[p] = nn | (nf << 16);
+        rnn[j] = (nn | (nf << 16));
+        roff[j] = pad4(len);
+        over |= len > cp.cap;
+        mx = max(mx, len);
+        sum += len;
+    }
+    // list statistics
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    }
+    if ((t & 31) == 0) {
+        atomicMax(&s_mx, mx);
+        atomicAdd(&s_sum, (unsigned long long)sum);
+    }
+    const bool any_over = __syncthreads_or(over);
+    if (t == 0) {
+        atomicMax(&st->max_nnb, s_mx);
+        atomicAdd((unsigned long long*)&st->nnb_sum, s_sum);
+        if (blockIdx.x == 0) st->rebuilds += 1;
+        if (any_over) {
             st->overflow = 1;
             st->frozen_iter = (int)st->iter;
         }
     }
-    // block maximum and sum of the list lengths
-    int mx = count;
-    long long sm = count;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        sm += __shfl_xor_sync(0xffffffffu, sm, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        smx[threadIdx.x >> 5] = mx;
-        ssm[threadIdx.x >> 5] = sm;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        mx = smx[0];
-        sm = ssm[0];
-        for (int w = 1; w < TPB / 32; ++w) {
-            mx = max(mx, smx[w]);
-            sm += ssm[w];
+    if (any_over) return;
+    const int tot = scan_in_place(roff, n_own, T.sw);
+    if (t == 0) atomicMax(&st->max_seg, tot);
+    if (tot > cp.seg) {
+        if (t == 0) {
+            st->stage_overflow = 1;
+            st->frozen_iter = (int)st->iter;
         }
-        atomicMax(&st->max_nnb, mx);
-        atomicAdd((unsigned long long*)&st->nnb_sum, (unsigned long long)sm);
-        if (blockIdx.x == 0) st->rebuilds += 1;
+        return;
+    }
+    // pack: chunk c (4 entries) belongs to the row j with roff[j] <= 4c < roff[j + 1]
+    uint2* out = reinterpret_cast<uint2*>(nbr + (size_t)blockIdx.x * cp.seg);
+    for (int c = t; c < tot / 4; c += SC_TPB) {
+        int lo = 0, hi = n_own - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (roff[mid] <= 4 * c) lo = mid;
+            else hi = mid - 1;
+        }
+        const int j = lo, w = rnn[j], nn = w & 0xffff, len = nn + (w >> 16);
+        const uint16_t* row = rows + (size_t)j * cp.cap;
+        const int p = p0 + j;
+        const int b = own_cell(T, p);
+        const uint32_t self = (uint32_t)(T.off[own_staged_cell(b)] + (p - T.own[b]));
+        uint32_t h[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = 4 * c - roff[j] + u;
+            h[u] = e < nn ? row[e] : (e < len ? row[cp.cap - 1 - (e - nn)] : self);
+        }
+        out[c] = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
     }
 }
 
@@ -548,14 +587,18 @@ __global__ void __launch_bounds__(TPB) k_nlist(int n, Geom g, const typename M::
 // FP32-split: neighbours with r <= r_l add exactly 1 (an integer); window
 // neighbours add omega in 2^-31 fixed point (window_weight_fix31).  The
 // threshold test t = n - (f - delta) is taken in the same fixed point, so
-// s_i and s'_i carry only the error of the window terms.
+// s_i and s'_i carry only the error of the window terms, and the integer sums
+// do not depend on the order of the terms.
 // Saturation: when the near entries alone hold at least ceil(f - delta + 1)
 // neighbours with r <= r_l, then n_i >= f - delta + 1 whatever the other
-// entries add, so s_i = s'_i = 0 exactly and the window terms are not needed
-// (unless the counts themselves are requested).
+// entries add, so s_i = s'_i = 0 exactly and nothing else is needed (unless
+// the counts themselves are requested).  Each thread first tests its own
+// particles for saturation over their near entries; the block then hands the
+// unsaturated ones, one at a time, to whole warps that walk the full row with
+// one lane per entry.
 struct CountOut {
-    double* n_out;          // counts in caller order, or null
-    long long* in_window;   // counter of window particles, or null
+    double* n_out;         // counts in caller order, or null
+    long long* in_window;  // counter of window particles, or null
 };
 
 __device__ __forceinline__ void switch_from_fix(long long T, float& s, float& ds)
@@ -581,147 +624,202 @@ __device__ __forceinline__ unsigned long long r2_fix(const int4& a, const int4& 
            (unsigned long long)((long long)dz * dz);
 }
 
-__global__ void __launch_bounds__(TPB) k_count_f32(int n, Geom g, Coef c, const int4* __restrict__ pos,
-                                                   ListRef L, const int* __restrict__ id, StageTable tb,
-                                                   float* __restrict__ ds_out, float2* __restrict__ sA,
-                                                   CountOut out, Status* st)
+// Squared separation for the FP64 paths.
+template <class M>
+__device__ __forceinline__ double r2_d(const typename M::pos_t& a, const typename M::pos_t& b, const Geom& g)
 {
+    double dx, dy, dz;
+    M::delta64(a, b, g, dx, dy, dz);
+    return dx * dx + dy * dy + dz * dz;
+}
+
+// The 4 entries of one 8-byte chunk.
+__device__ __forceinline__ void unpack4(const uint2 v, int h[4])
+{
+    h[0] = (int)(v.x & 0xffffu);
+    h[1] = (int)(v.x >> 16);
+    h[2] = (int)(v.y & 0xffffu);
+    h[3] = (int)(v.y >> 16);
+}
+
+template <class M>
+__global__ void __launch_bounds__(SC_TPB) k_count(Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
+                                                  SuperGrid G, SuperCaps cp, const uint16_t* __restrict__ nbr,
+                                                  const int* __restrict__ nnb, const int* __restrict__ id,
+                                                  typename M::real* __restrict__ ds_out,
+                                                  typename M::real2* __restrict__ sA, CountOut out, Status* st)
+{
+    using pos_t = typename M::pos_t;
+    using real = typename M::real;
+    using real2 = typename M::real2;
     if (blockIdx.x == 0 && threadIdx.x == 0) st->rebuild = 0;
     if (halted(st)) return;
+    __shared__ SuperTab T;
+    __shared__ int s_nu;
     extern __shared__ __align__(16) unsigned char smem[];
-    int* s_base = (int*)smem;
-    int* s_off = s_base + tb.cmax;
-    int4* spos = (int4*)(smem + stage_header_bytes(tb.cmax));
-    int R;
-    load_runs(tb, blockIdx.x, s_base, s_off, R);
-    stage_runs(s_base, s_off, R, [&](int m, int j) { spos[m] = pos[j]; });
-    __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    bool win = false;
-    if (i < n) {
-        const int4 pi = pos[i];
-        const int w = L.nnb[i];
-        const int nn = w & 0xffff, nf = w >> 16;
+    const int t = threadIdx.x;
+    int p0, n_own, total;
+    load_supercell(blockIdx.x, g, G, T, p0, n_own, total);
+    const PassLayout ly = pass_layout(cp, sizeof(pos_t), 0);
+    pos_t* spos = (pos_t*)smem;
+    int* roff = (int*)(smem + ly.roff);
+    int* ulist = (int*)(smem + ly.plist);
+    if (t == 0) s_nu = 0;
+    stage<pos_t>(T, total, [&](int j) { return pos[j]; }, [&](int m, const pos_t& v) { spos[m] = v; });
+    own_rows(nnb, p0, n_own, roff, T.sw);
+    const uint16_t* seg = nbr + (size_t)blockIdx.x * cp.seg;
+
+    // saturation test over the near entries
+    for (int j = t; j < n_own; j += SC_TPB) {
+        const int p = p0 + j;
+        const int nn = __ldg(nnb + p) & 0xffff;
+        const pos_t pi = pos[p];
+        const uint2* row = reinterpret_cast<const uint2*>(seg + roff[j]);
         long long full = 0;
-        for_entries(L, n, i, nn, 0, [&](int m) { full += r2_fix(pi, spos[m]) <= c.rl2_fix; });
-        float s = 0.0f, ds = 0.0f;
-        if (full < c.sat_full || out.n_out) {
-            full = 0;
+        for (int q = 0; q < nn; q += 4) {
+            int h[4];
+            unpack4(__ldg(row + (q >> 2)), h);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (q + u >= nn) break;
+                if constexpr (M::fp64) full += r2_d<M>(pi, spos[h[u]], g) <= c.rl2;
+                else full += r2_fix(pi, spos[h[u]]) <= c.rl2_fix;
+            }
+        }
+        if (full >= c.sat_full && !out.n_out) {
+            ds_out[p] = (real)0;
+            sA[p] = real2{(real)0, (real)0};
+        } else {
+            ulist[atomicAdd(&s_nu, 1)] = j;
+        }
+    }
+    __syncthreads();
+
+    // unsaturated particles: one warp each, one lane per entry
+    const int nu = s_nu;
+    const int lane = t & 31;
+    for (int u = t >> 5; u < nu; u += SC_TPB / 32) {
+        const int j = ulist[u], p = p0 + j;
+        const int len = row_len(__ldg(nnb + p));
+        const pos_t pi = pos[p];
+        const uint16_t* row = seg + roff[j];
+        real s, ds;
+        double n_val;
+        if constexpr (M::fp64) {
+            double acc = 0.0;
+            for (int e = lane; e < len; e += 32) {
+                const double r2 = r2_d<M>(pi, spos[__ldg(row + e)], g);
+                if (r2 < c.rh2) acc += r2 <= c.rl2 ? 1.0 : omega_d(sqrt(r2), c.r_l, c.r_h);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            s = omega_d(acc, c.fd, c.fd + 1.0);
+            ds = domega_d(acc, c.fd, c.fd + 1.0);
+            n_val = acc;
+        } else {
+            long long full = 0;
             unsigned long long q = 0;
-            for_entries(L, n, i, nn, nf, [&](int m) {
-                const unsigned long long r2 = r2_fix(pi, spos[m]);
+            for (int e = lane; e < len; e += 32) {
+                const unsigned long long r2 = r2_fix(pi, spos[__ldg(row + e)]);
                 if (r2 < c.rh2_fix) {
                     if (r2 <= c.rl2_fix) ++full;
                     else q += window_weight_fix31(r2, r2 - c.rl2_fix, c.rl_s, c.w_s);
                 }
-            });
-            const long long T = (full - c.fd_int) * 2147483648LL + (long long)q - c.fd_frac_fix;
-            switch_from_fix(T, s, ds);
-            if (out.n_out) out.n_out[id[i]] = (double)full + (double)q * 4.656612873077393e-10;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                full += __shfl_xor_sync(0xffffffffu, full, o);
+                q += __shfl_xor_sync(0xffffffffu, q, o);
+            }
+            const long long Tf = (full - c.fd_int) * 2147483648LL + (long long)q - c.fd_frac_fix;
+            switch_from_fix(Tf, s, ds);
+            n_val = (double)full + (double)q * 4.656612873077393e-10;
         }
-        ds_out[i] = ds;
-        sA[i] = make_float2(s, 0.0f);
-        win = ds != 0.0f;
-    }
-    if (out.in_window) {
-        const unsigned bal = __ballot_sync(0xffffffffu, win);
-        if ((threadIdx.x & 31) == 0 && bal)
-            atomicAdd((unsigned long long*)out.in_window, (unsigned long long)__popc(bal));
-    }
-}
-
-__global__ void __launch_bounds__(TPB) k_count_f64(int n, Geom g, Coef c, const P64* __restrict__ pos, ListRef L,
-                                                   const int* __restrict__ id, StageTable tb,
-                                                   double* __restrict__ ds_out, double2* __restrict__ sA,
-                                                   CountOut out, Status* st)
-{
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->rebuild = 0;
-    if (halted(st)) return;
-    extern __shared__ __align__(16) unsigned char smem[];
-    int* s_base = (int*)smem;
-    int* s_off = s_base + tb.cmax;
-    P64* spos = (P64*)(smem + stage_header_bytes(tb.cmax));
-    int R;
-    load_runs(tb, blockIdx.x, s_base, s_off, R);
-    stage_runs(s_base, s_off, R, [&](int m, int j) { spos[m] = pos[j]; });
-    __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    bool win = false;
-    if (i < n) {
-        const P64 pi = pos[i];
-        const int w = L.nnb[i];
-        double acc = 0.0;
-        for_entries(L, n, i, w & 0xffff, w >> 16, [&](int m) {
-            double dx, dy, dz;
-            ModeF64::delta64(pi, spos[m], g, dx, dy, dz);
-            const double r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 < c.rh2) acc += r2 <= c.rl2 ? 1.0 : omega_d(sqrt(r2), c.r_l, c.r_h);
-        });
-        const double s = omega_d(acc, c.fd, c.fd + 1.0);
-        const double ds = domega_d(acc, c.fd, c.fd + 1.0);
-        ds_out[i] = ds;
-        sA[i] = make_double2(s, 0.0);
-        win = ds != 0.0;
-        if (out.n_out) out.n_out[id[i]] = acc;
-    }
-    if (out.in_window) {
-        const unsigned bal = __ballot_sync(0xffffffffu, win);
-        if ((threadIdx.x & 31) == 0 && bal)
-            atomicAdd((unsigned long long*)out.in_window, (unsigned long long)__popc(bal));
+        if (lane == 0) {
+            ds_out[p] = ds;
+            sA[p] = real2{s, (real)0};
+            if (out.n_out) out.n_out[id[p]] = n_val;
+            if (out.in_window && ds != (real)0) atomicAdd((unsigned long long*)out.in_window, 1ull);
+        }
     }
 }
 
 // ================================================================ chain-rule pass
-// A_i = s'_i sum_j s_j V_a(r_ij) for particles inside the switching window;
-// blocks without such a particle return after one vote.
+// A_i = s'_i sum_j s_j V_a(r_ij) for particles inside the switching window
+// (s'_i != 0), one warp per such particle; supercells without one return
+// after one vote.
 template <class M>
-__global__ void __launch_bounds__(TPB) k_chain(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
-                                               ListRef L, StageTable tb, const typename M::real* __restrict__ ds,
-                                               typename M::real2* __restrict__ sA, const Status* st)
+__global__ void __launch_bounds__(SC_TPB) k_chain(Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
+                                                  SuperGrid G, SuperCaps cp, const uint16_t* __restrict__ nbr,
+                                                  const int* __restrict__ nnb, const typename M::real* __restrict__ ds,
+                                                  typename M::real2* __restrict__ sA, const Status* st)
 {
-    using real = typename M::real;
     using pos_t = typename M::pos_t;
+    using real = typename M::real;
     if (halted(st)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const real dsi = i < n ? ds[i] : (real)0;
-    if (!__syncthreads_or(dsi != (real)0)) return;
+    const int t = threadIdx.x;
+    {
+        const int q0 = __ldg(G.cell_start + 8 * blockIdx.x), q1 = __ldg(G.cell_start + 8 * blockIdx.x + 8);
+        bool any = false;
+        for (int p = q0 + t; p < q1; p += SC_TPB) any |= ds[p] != (real)0;
+        if (!__syncthreads_or(any)) return;
+    }
+    __shared__ SuperTab T;
+    __shared__ int s_nw;
     extern __shared__ __align__(16) unsigned char smem[];
-    int* s_base = (int*)smem;
-    int* s_off = s_base + tb.cmax;
-    pos_t* spos = (pos_t*)(smem + stage_header_bytes(tb.cmax));
-    real* ss = (real*)(spos + tb.smax);
-    int R;
-    load_runs(tb, blockIdx.x, s_base, s_off, R);
-    const real* s_only = reinterpret_cast<const real*>(sA);  // s_j at even offsets
-    stage_runs(s_base, s_off, R, [&](int m, int j) {
-        spos[m] = pos[j];
-        ss[m] = s_only[2 * (size_t)j];
-    });
+    int p0, n_own, total;
+    load_supercell(blockIdx.x, g, G, T, p0, n_own, total);
+    const PassLayout ly = pass_layout(cp, sizeof(pos_t), sizeof(real));
+    pos_t* spos = (pos_t*)smem;
+    real* ss = (real*)(smem + ly.val);
+    int* roff = (int*)(smem + ly.roff);
+    int* wlist = (int*)(smem + ly.plist);
+    if (t == 0) s_nw = 0;
+    const real* s_only = reinterpret_cast<const real*>(sA);  // s_j at even offsets (A is written here)
+    struct PS {
+        pos_t p;
+        real s;
+    };
+    stage<PS>(
+        T, total, [&](int j) { return PS{pos[j], s_only[2 * (size_t)j]}; },
+        [&](int m, const PS& v) {
+            spos[m] = v.p;
+            ss[m] = v.s;
+        });
+    own_rows(nnb, p0, n_own, roff, T.sw);
+    for (int j = t; j < n_own; j += SC_TPB)
+        if (ds[p0 + j] != (real)0) wlist[atomicAdd(&s_nw, 1)] = j;
     __syncthreads();
-    if (dsi == (real)0) return;
-    const pos_t pi = pos[i];
-    const int w = L.nnb[i];
-    real acc = 0;
-    for_entries(L, n, i, w & 0xffff, w >> 16, [&](int m) {
-        if constexpr (M::fp64) {
-            double dx, dy, dz;
-            M::delta64(pi, spos[m], g, dx, dy, dz);
-            const double r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 > c.rr2 && r2 < c.ra2) acc += ss[m] * Va_d(sqrt(r2), c);
-        } else {
-            const unsigned long long r2i = r2_fix(pi, spos[m]);
-            if (r2i > c.rr2_fix && r2i < c.ra2_fix) {
-                const float r2 = u64_to_float(r2i) * g.s32sq;
-                const float r = sqrtf(r2);
-                const float u = s64_to_float((long long)r2i - (long long)c.rm2_fix) * c.s2hinv / (r + c.rmf);
-                const float q = 1.0f - u * u;
-                acc += ss[m] * (-c.Eaf * q * q);
+    const int nw = s_nw;
+    const int lane = t & 31;
+    const uint16_t* seg = nbr + (size_t)blockIdx.x * cp.seg;
+    for (int u = t >> 5; u < nw; u += SC_TPB / 32) {
+        const int j = wlist[u], p = p0 + j;
+        const int len = row_len(__ldg(nnb + p));
+        const pos_t pi = pos[p];
+        const uint16_t* row = seg + roff[j];
+        real acc = 0;
+        for (int e = lane; e < len; e += 32) {
+            const int m = __ldg(row + e);
+            if constexpr (M::fp64) {
+                const double r2 = r2_d<M>(pi, spos[m], g);
+                if (r2 > c.rr2 && r2 < c.ra2) acc += ss[m] * Va_d(sqrt(r2), c);
+            } else {
+                const unsigned long long r2i = r2_fix(pi, spos[m]);
+                if (r2i > c.rr2_fix && r2i < c.ra2_fix) {
+                    const float r2 = u64_to_float(r2i) * g.s32sq;
+                    const float r = sqrtf(r2);
+                    const float uu = s64_to_float((long long)r2i - (long long)c.rm2_fix) * c.s2hinv / (r + c.rmf);
+                    const float q = 1.0f - uu * uu;
+                    acc += ss[m] * (-c.Eaf * q * q);
+                }
             }
         }
-    });
-    sA[i].y = dsi * acc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) sA[p].y = ds[p] * acc;
+    }
 }
-
 // ================================================================ pass 2: forces + BAOAB
 struct StepArgs {
     void* x;              // [3][n] unwrapped positions (FP32 mode: int64 in units L / 2^52; FP64: double)
@@ -836,98 +934,204 @@ __device__ __forceinline__ void integrate(int i, int n, const Geom& g, typename 
     if (bad) st->frozen = 1;
 }
 
-// Pass 2.  FP32 mode, per pair: the exact integer r^2 decides which terms can
-// be nonzero (core overlap r < r_r; the well, only if s_i s_j != 0; the
-// counting window, only if A_i + A_j != 0) and pairs with none of them stop
-// there.  The arguments of the steep well and of the window come from exact
-// integer differences r^2 - r_m^2 and r^2 - r_l^2.
-template <class M, int EPI>
-__global__ void __launch_bounds__(TPB) k_force(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
-                                               ListRef L, const int* __restrict__ id, StageTable tb,
-                                               const typename M::real2* __restrict__ sA,
-                                               typename M::pos_t* __restrict__ pos_next,
-                                               const typename M::pos_t* __restrict__ xref, StepArgs a, Status* st)
+
+// Pass 2, one block per supercell.  The block's list entries are cut into
+// 4-entry chunks (rows are padded to a multiple of 4), the threads take
+// chunks in turn, each chunk's partial force goes to shared memory, and each
+// own particle then sums its chunks in order -- deterministic, no atomics.
+// If no staged particle has s_j != 0 or A_j != 0, no pair of the block can
+// have a well or window term and the block runs the soft-core-only loop.
+// Otherwise, per pair in the FP32 mode, the exact integer r^2 decides which
+// terms can be nonzero (core overlap r < r_r; the well, only if s_i s_j != 0;
+// the counting window, only if A_i + A_j != 0), and the arguments of the
+// steep well and of the window come from exact integer differences
+// r^2 - r_m^2 and r^2 - r_l^2.
+
+// Spare word of a staged position, holding s_j.
+__device__ __forceinline__ void put_s(int4& p, float s) { p.w = __float_as_int(s); }
+__device__ __forceinline__ void put_s(P64& p, double s) { p.w = (unsigned long long)__double_as_longlong(s); }
+__device__ __forceinline__ float get_s(const int4& p) { return __int_as_float(p.w); }
+__device__ __forceinline__ double get_s(const P64& p) { return __longlong_as_double((long long)p.w); }
+
+// All terms of one pair in the FP32 mode, added to f (physical units).
+__device__ __forceinline__ void pair_f32(const int4& pi, float si, float Ai, const int4& pj, float sj, float Aj,
+                                         const Coef& c, const Geom& g, float& fx, float& fy, float& fz)
 {
+    const int ix = pi.x - pj.x, iy = pi.y - pj.y, iz = pi.z - pj.z;
+    const unsigned long long r2i = (unsigned long long)((long long)ix * ix) +
+                                   (unsigned long long)((long long)iy * iy) +
+                                   (unsigned long long)((long long)iz * iz);
+    const bool core = r2i < c.rr2_fix;
+    const bool well = r2i > c.rr2_fix && r2i < c.ra2_fix && si * sj != 0.0f;
+    const bool chain = r2i > c.rl2_fix && r2i < c.rh2_fix && Ai + Aj != 0.0f;
+    if (!(core || well || chain)) return;
+    const float dx = (float)ix * g.s32, dy = (float)iy * g.s32, dz = (float)iz * g.s32;
+    float gr = 0.0f;  // g / r
+    if (core) gr = c.Er4f * (u64_to_float(r2i) * g.s32sq * c.rr2invf - 1.0f);
+    if (well || chain) {
+        const float r2 = u64_to_float(r2i) * g.s32sq;
+        float rinv = rsqrtf(r2);
+        rinv = rinv * __fmaf_rn(-0.5f * r2 * rinv, rinv, 1.5f);  // one Newton step
+        const float r = r2 * rinv;
+        float gt = 0.0f;  // g from the well and the counts
+        if (well) {
+            const float u = s64_to_float((long long)r2i - (long long)c.rm2_fix) * c.s2hinv / (r + c.rmf);
+            gt = si * sj * c.Ea4hf * u * (1.0f - u * u);
+        }
+        if (chain) {
+            const float tt = u64_to_float(r2i - c.rl2_fix) * c.s2winv / (r + c.rlf);
+            gt -= (Ai + Aj) * 4.0f * tt * (1.0f - tt * tt) * c.winvf;
+        }
+        gr += gt * rinv;
+    }
+    fx -= gr * dx;
+    fy -= gr * dy;
+    fz -= gr * dz;
+}
+
+// All terms of one pair in the FP64 mode.
+__device__ __forceinline__ void pair_f64(const P64& pi, double si, double Ai, const P64& pj, double sj, double Aj,
+                                         const Coef& c, const Geom& g, double& fx, double& fy, double& fz)
+{
+    double dx, dy, dz;
+    ModeF64::delta64(pi, pj, g, dx, dy, dz);
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 >= c.rc2) return;
+    const double r = sqrt(r2);
+    double gr = dVr_over_r_d(r2, c);
+    if (r > 0.0) gr += (si * sj * dVa_d(r, c) + (Ai + Aj) * domega_d(r, c.r_l, c.r_h)) / r;
+    fx -= gr * dx;
+    fy -= gr * dy;
+    fz -= gr * dz;
+}
+
+template <class M, int EPI>
+__global__ void __launch_bounds__(SC_TPB) k_force(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
+                                                  SuperGrid G, SuperCaps cp, const uint16_t* __restrict__ nbr,
+                                                  const int* __restrict__ nnb, const int* __restrict__ id,
+                                                  const typename M::real2* __restrict__ sA,
+                                                  typename M::pos_t* __restrict__ pos_next,
+                                                  const typename M::pos_t* __restrict__ xref, StepArgs a, Status* st)
+{
+    using pos_t = typename M::pos_t;
     using real = typename M::real;
     using real2 = typename M::real2;
-    using pos_t = typename M::pos_t;
     // k_force raises `frozen` and `rebuild` itself; it tests `frozen` only through
     // halted(), which a thread of this launch changes only on the error path
     if (halted(st)) return;
+    __shared__ SuperTab T;
     extern __shared__ __align__(16) unsigned char smem[];
-    int* s_base = (int*)smem;
-    int* s_off = s_base + tb.cmax;
-    pos_t* spos = (pos_t*)(smem + stage_header_bytes(tb.cmax));
-    real2* ssa = (real2*)(spos + tb.smax);
-    int R;
-    load_runs(tb, blockIdx.x, s_base, s_off, R);
-    stage_runs(s_base, s_off, R, [&](int m, int j) {
-        spos[m] = pos[j];
-        ssa[m] = sA[j];
-    });
+    const int t = threadIdx.x;
+    int p0, n_own, total;
+    load_supercell(blockIdx.x, g, G, T, p0, n_own, total);
+    const ForceLayout ly = force_layout(cp, sizeof(pos_t), sizeof(real));
+    pos_t* spos = (pos_t*)smem;
+    real* sAj = (real*)(smem + ly.sA);
+    int* roff = (int*)(smem + ly.roff);
+    uint16_t* cown = (uint16_t*)(smem + ly.cown);
+    const int nchm = cp.seg / 4;
+    real* cpx = (real*)(smem + ly.cpart);
+    real* cpy = cpx + nchm;
+    real* cpz = cpy + nchm;
+    struct PV {
+        pos_t p;
+        real2 sa;
+    };
+    bool nz = false;
+    stage<PV>(
+        T, total, [&](int j) { return PV{pos[j], sA[j]}; },
+        [&](int m, const PV& v) {
+            pos_t q = v.p;
+            put_s(q, v.sa.x);
+            spos[m] = q;
+            sAj[m] = v.sa.y;
+            nz |= (v.sa.x != (real)0) | (v.sa.y != (real)0);
+        });
+    const bool general = __syncthreads_or(nz);
+    const int nch = own_rows(nnb, p0, n_own, roff, T.sw) >> 2;
+    for (int j = t; j < n_own; j += SC_TPB)
+        for (int q = roff[j] >> 2, qe = roff[j + 1] >> 2; q < qe; ++q) cown[q] = (uint16_t)j;
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const pos_t pi = pos[i];
-    const real2 sai = sA[i];
-    const int w = L.nnb[i];
-    real fx = 0, fy = 0, fz = 0;
-    for_entries(L, n, i, w & 0xffff, w >> 16, [&](int m) {
-        const pos_t pj = spos[m];
-        const real2 saj = ssa[m];
-        if constexpr (M::fp64) {
-            double dx, dy, dz;
-            M::delta64(pi, pj, g, dx, dy, dz);
-            const double r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 >= c.rc2) return;
-            const double r = sqrt(r2);
-            double gr = dVr_over_r_d(r2, c);
-            if (r > 0.0) gr += (sai.x * saj.x * dVa_d(r, c) + (sai.y + saj.y) * domega_d(r, c.r_l, c.r_h)) / r;
-            fx -= gr * dx;
-            fy -= gr * dy;
-            fz -= gr * dz;
-        } else {
-            const int ix = pi.x - pj.x, iy = pi.y - pj.y, iz = pi.z - pj.z;
-            const unsigned long long r2i = (unsigned long long)((long long)ix * ix) +
-                                           (unsigned long long)((long long)iy * iy) +
-                                           (unsigned long long)((long long)iz * iz);
-            const bool core = r2i < c.rr2_fix;
-            const bool well = r2i > c.rr2_fix && r2i < c.ra2_fix && sai.x * saj.x != 0.0f;
-            const bool chain = r2i > c.rl2_fix && r2i < c.rh2_fix && sai.y + saj.y != 0.0f;
-            if (!(core || well || chain)) return;
-            const float dx = (float)ix * g.s32, dy = (float)iy * g.s32, dz = (float)iz * g.s32;
-            float gr = 0.0f;                                   // g / r
-            if (core) gr = c.Er4f * (u64_to_float(r2i) * g.s32sq * c.rr2invf - 1.0f);
-            if (well || chain) {
-                const float r2 = u64_to_float(r2i) * g.s32sq;
-                float rinv = rsqrtf(r2);
-                rinv = rinv * __fmaf_rn(-0.5f * r2 * rinv, rinv, 1.5f);   // one Newton step
-                const float r = r2 * rinv;
-                float gt = 0.0f;                               // g from the well and the counts
-                if (well) {
-                    const float u = s64_to_float((long long)r2i - (long long)c.rm2_fix) * c.s2hinv / (r + c.rmf);
-                    gt = sai.x * saj.x * c.Ea4hf * u * (1.0f - u * u);
+    const uint2* L = reinterpret_cast<const uint2*>(nbr + (size_t)blockIdx.x * cp.seg);
+    if constexpr (!M::fp64) {
+        if (!general) {
+            // soft core only: g / r = K (r^2 - r_r^2), r^2 in units of (L / 2^32)^2
+            const float kc = c.Er4f * c.rr2invf * g.s32sq, bc = c.Er4f, rr2u = (float)c.rr2_fix;
+            for (int q = t; q < nch; q += SC_TPB) {
+                const int j = cown[q];
+                const int4 pi = __ldg(pos + p0 + j);
+                int h[4];
+                unpack4(__ldg(L + q), h);
+                float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int4 pj = spos[h[u]];
+                    const float dx = (float)(pi.x - pj.x), dy = (float)(pi.y - pj.y), dz = (float)(pi.z - pj.z);
+                    const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz));
+                    const float gr = r2 < rr2u ? __fmaf_rn(kc, r2, -bc) : 0.0f;
+                    fx = __fmaf_rn(-gr, dx, fx);
+                    fy = __fmaf_rn(-gr, dy, fy);
+                    fz = __fmaf_rn(-gr, dz, fz);
                 }
-                if (chain) {
-                    const float t = u64_to_float(r2i - c.rl2_fix) * c.s2winv / (r + c.rlf);
-                    gt -= (sai.y + saj.y) * 4.0f * t * (1.0f - t * t) * c.winvf;
-                }
-                gr += gt * rinv;
+                cpx[q] = fx * g.s32;
+                cpy[q] = fy * g.s32;
+                cpz[q] = fz * g.s32;
             }
-            fx -= gr * dx;
-            fy -= gr * dy;
-            fz -= gr * dz;
-        }
-    });
-    if constexpr (EPI == EPI_FORCE) {
-        if (a.F_out) {
-            const int o = id[i];
-            a.F_out[3 * (size_t)o + 0] = (double)fx;
-            a.F_out[3 * (size_t)o + 1] = (double)fy;
-            a.F_out[3 * (size_t)o + 2] = (double)fz;
+        } else {
+            for (int q = t; q < nch; q += SC_TPB) {
+                const int j = cown[q];
+                const int4 pi = __ldg(pos + p0 + j);
+                const float2 sai = __ldg(sA + p0 + j);
+                int h[4];
+                unpack4(__ldg(L + q), h);
+                float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int4 pj = spos[h[u]];
+                    pair_f32(pi, sai.x, sai.y, pj, get_s(pj), sAj[h[u]], c, g, fx, fy, fz);
+                }
+                cpx[q] = fx;
+                cpy[q] = fy;
+                cpz[q] = fz;
+            }
         }
     } else {
-        integrate<M, EPI>(i, n, g, fx, fy, fz, a, (uint32_t)id[i], st, pos_next, xref);
+        for (int q = t; q < nch; q += SC_TPB) {
+            const int j = cown[q];
+            const P64 pi = pos[p0 + j];
+            const double2 sai = sA[p0 + j];
+            int h[4];
+            unpack4(__ldg(L + q), h);
+            double fx = 0.0, fy = 0.0, fz = 0.0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const P64 pj = spos[h[u]];
+                pair_f64(pi, sai.x, sai.y, pj, get_s(pj), sAj[h[u]], c, g, fx, fy, fz);
+            }
+            cpx[q] = fx;
+            cpy[q] = fy;
+            cpz[q] = fz;
+        }
+    }
+    __syncthreads();
+    for (int j = t; j < n_own; j += SC_TPB) {
+        real fx = 0, fy = 0, fz = 0;
+        for (int q = roff[j] >> 2, qe = roff[j + 1] >> 2; q < qe; ++q) {
+            fx += cpx[q];
+            fy += cpy[q];
+            fz += cpz[q];
+        }
+        const int p = p0 + j;
+        if constexpr (EPI == EPI_FORCE) {
+            if (a.F_out) {
+                const int o = id[p];
+                a.F_out[3 * (size_t)o + 0] = (double)fx;
+                a.F_out[3 * (size_t)o + 1] = (double)fy;
+                a.F_out[3 * (size_t)o + 2] = (double)fz;
+            }
+        } else {
+            integrate<M, EPI>(p, n, g, fx, fy, fz, a, (uint32_t)id[p], st, pos_next, xref);
+        }
     }
 }
 
@@ -935,125 +1139,144 @@ __global__ void __launch_bounds__(TPB) k_force(int n, Geom g, Coef c, const type
 // Requested energies are held to 1e-9 relative, which needs the switching
 // factors to FP64 accuracy: the counts, s, s' and A are recomputed here in
 // FP64 from the exact fixed-point separations (these kernels run only when U
-// or W is asked for, never inside the step loop).  Neighbour values are read
-// through each block's staging (staged index -> sorted index, kept in sj).
+// or W is asked for, never inside the step loop).  One block per supercell,
+// one thread per own particle.
 template <class M>
-__device__ __forceinline__ int stage_pos_index(const StageTable& tb, const typename M::pos_t* __restrict__ pos,
-                                               int* s_base, int* s_off, typename M::pos_t* spos, int* sj)
-{
-    int R;
-    const int total = load_runs(tb, blockIdx.x, s_base, s_off, R);
-    stage_runs(s_base, s_off, R, [&](int m, int j) {
-        spos[m] = pos[j];
-        sj[m] = j;
-    });
-    __syncthreads();
-    return total;
-}
-
-template <class M>
-__global__ void __launch_bounds__(TPB) k_count_e(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
-                                                 ListRef L, StageTable tb, double2* __restrict__ sd, const Status* st)
+__global__ void __launch_bounds__(SC_TPB) k_count_e(Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
+                                                    SuperGrid G, SuperCaps cp, const uint16_t* __restrict__ nbr,
+                                                    const int* __restrict__ nnb, double2* __restrict__ sd,
+                                                    const Status* st)
 {
     using pos_t = typename M::pos_t;
     if (halted(st)) return;
+    __shared__ SuperTab T;
     extern __shared__ __align__(16) unsigned char smem[];
-    int* s_base = (int*)smem;
-    int* s_off = s_base + tb.cmax;
-    pos_t* spos = (pos_t*)(smem + stage_header_bytes(tb.cmax));
-    int* sj = (int*)(spos + tb.smax);
-    stage_pos_index<M>(tb, pos, s_base, s_off, spos, sj);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const pos_t pi = pos[i];
-    const int w = L.nnb[i];
-    double acc = 0.0;
-    for_entries(L, n, i, w & 0xffff, w >> 16, [&](int m) {
-        double dx, dy, dz;
-        M::delta64(pi, spos[m], g, dx, dy, dz);
-        const double r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 < c.rh2) acc += r2 <= c.rl2 ? 1.0 : omega_d(sqrt(r2), c.r_l, c.r_h);
-    });
-    sd[i] = make_double2(omega_d(acc, c.fd, c.fd + 1.0), domega_d(acc, c.fd, c.fd + 1.0));
-}
-
-template <class M>
-__global__ void __launch_bounds__(TPB) k_chain_e(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
-                                                 ListRef L, StageTable tb, const double2* __restrict__ sd,
-                                                 double* __restrict__ Ad, const Status* st)
-{
-    using pos_t = typename M::pos_t;
-    if (halted(st)) return;
-    extern __shared__ __align__(16) unsigned char smem[];
-    int* s_base = (int*)smem;
-    int* s_off = s_base + tb.cmax;
-    pos_t* spos = (pos_t*)(smem + stage_header_bytes(tb.cmax));
-    int* sj = (int*)(spos + tb.smax);
-    stage_pos_index<M>(tb, pos, s_base, s_off, spos, sj);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double dsi = sd[i].y;
-    if (dsi == 0.0) {
-        Ad[i] = 0.0;
-        return;
+    int p0, n_own, total;
+    load_supercell(blockIdx.x, g, G, T, p0, n_own, total);
+    const PassLayout ly = pass_layout(cp, sizeof(pos_t), 0);
+    pos_t* spos = (pos_t*)smem;
+    int* roff = (int*)(smem + ly.roff);
+    stage<pos_t>(T, total, [&](int j) { return pos[j]; }, [&](int m, const pos_t& v) { spos[m] = v; });
+    own_rows(nnb, p0, n_own, roff, T.sw);
+    const uint16_t* seg = nbr + (size_t)blockIdx.x * cp.seg;
+    for (int j = threadIdx.x; j < n_own; j += SC_TPB) {
+        const int p = p0 + j;
+        const int len = row_len(nnb[p]);
+        const pos_t pi = pos[p];
+        double acc = 0.0;
+        for (int e = 0; e < len; ++e) {
+            const double r2 = r2_d<M>(pi, spos[seg[roff[j] + e]], g);
+            if (r2 < c.rh2) acc += r2 <= c.rl2 ? 1.0 : omega_d(sqrt(r2), c.r_l, c.r_h);
+        }
+        sd[p] = make_double2(omega_d(acc, c.fd, c.fd + 1.0), domega_d(acc, c.fd, c.fd + 1.0));
     }
-    const pos_t pi = pos[i];
-    const int w = L.nnb[i];
-    double acc = 0.0;
-    for_entries(L, n, i, w & 0xffff, w >> 16, [&](int m) {
-        double dx, dy, dz;
-        M::delta64(pi, spos[m], g, dx, dy, dz);
-        const double r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 > c.rr2 && r2 < c.ra2) acc += sd[sj[m]].x * Va_d(sqrt(r2), c);
-    });
-    Ad[i] = dsi * acc;
 }
 
-// Per-block partial sums of U = sum_{i<j} [V_r + s_i s_j V_a], W = sum_{i<j} -g r and
-// of the number of pairs with r < r_c, each pair seen from both ends (halves).
 template <class M>
-__global__ void __launch_bounds__(TPB) k_energy(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
-                                                ListRef L, StageTable tb, const double2* __restrict__ sd,
-                                                const double* __restrict__ Ad, double* __restrict__ partial,
-                                                long long* __restrict__ ppairs, const Status* st)
+__global__ void __launch_bounds__(SC_TPB) k_chain_e(Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
+                                                    SuperGrid G, SuperCaps cp, const uint16_t* __restrict__ nbr,
+                                                    const int* __restrict__ nnb, const double2* __restrict__ sd,
+                                                    double* __restrict__ Ad, const Status* st)
 {
     using pos_t = typename M::pos_t;
+    if (halted(st)) return;
+    __shared__ SuperTab T;
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double se[TPB], sw[TPB];
-    __shared__ long long sp[TPB];
-    int* s_base = (int*)smem;
-    int* s_off = s_base + tb.cmax;
-    pos_t* spos = (pos_t*)(smem + stage_header_bytes(tb.cmax));
-    int* sj = (int*)(spos + tb.smax);
-    const bool live = !halted(st);
-    if (live) stage_pos_index<M>(tb, pos, s_base, s_off, spos, sj);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int p0, n_own, total;
+    load_supercell(blockIdx.x, g, G, T, p0, n_own, total);
+    const PassLayout ly = pass_layout(cp, sizeof(pos_t), sizeof(double));
+    pos_t* spos = (pos_t*)smem;
+    double* ss = (double*)(smem + ly.val);
+    int* roff = (int*)(smem + ly.roff);
+    struct PS {
+        pos_t p;
+        double s;
+    };
+    stage<PS>(
+        T, total, [&](int j) { return PS{pos[j], sd[j].x}; },
+        [&](int m, const PS& v) {
+            spos[m] = v.p;
+            ss[m] = v.s;
+        });
+    own_rows(nnb, p0, n_own, roff, T.sw);
+    const uint16_t* seg = nbr + (size_t)blockIdx.x * cp.seg;
+    for (int j = threadIdx.x; j < n_own; j += SC_TPB) {
+        const int p = p0 + j;
+        const double dsi = sd[p].y;
+        if (dsi == 0.0) {
+            Ad[p] = 0.0;
+            continue;
+        }
+        const int len = row_len(nnb[p]);
+        const pos_t pi = pos[p];
+        double acc = 0.0;
+        for (int e = 0; e < len; ++e) {
+            const int m = seg[roff[j] + e];
+            const double r2 = r2_d<M>(pi, spos[m], g);
+            if (r2 > c.rr2 && r2 < c.ra2) acc += ss[m] * Va_d(sqrt(r2), c);
+        }
+        Ad[p] = dsi * acc;
+    }
+}
+
+// Per-supercell partial sums of U = sum_{i<j} [V_r + s_i s_j V_a], W = sum_{i<j} -g r
+// and of the number of pairs with r < r_c, each pair seen from both ends (halves).
+template <class M>
+__global__ void __launch_bounds__(SC_TPB) k_energy(Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
+                                                   SuperGrid G, SuperCaps cp, const uint16_t* __restrict__ nbr,
+                                                   const int* __restrict__ nnb, const double2* __restrict__ sd,
+                                                   const double* __restrict__ Ad, double* __restrict__ partial,
+                                                   long long* __restrict__ ppairs, const Status* st)
+{
+    using pos_t = typename M::pos_t;
+    __shared__ SuperTab T;
+    __shared__ double se[SC_TPB], sw[SC_TPB];
+    __shared__ long long sp[SC_TPB];
+    extern __shared__ __align__(16) unsigned char smem[];
+    const PassLayout ly = pass_layout(cp, sizeof(pos_t), sizeof(double2));
+    pos_t* spos = (pos_t*)smem;
+    double2* ssa = (double2*)(smem + ly.val);  // (s_j, A_j)
+    int* roff = (int*)(smem + ly.roff);
     double e = 0.0, w = 0.0;
     long long pairs = 0;
-    if (i < n && live) {
-        const pos_t pi = pos[i];
-        const double si = sd[i].x, Ai = Ad[i];
-        const int nw = L.nnb[i];
-        for_entries(L, n, i, nw & 0xffff, nw >> 16, [&](int m) {
-            double dx, dy, dz;
-            M::delta64(pi, spos[m], g, dx, dy, dz);
-            const double r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 >= c.rc2) return;
-            ++pairs;
-            const int j = sj[m];
-            const double sjv = sd[j].x, Aj = Ad[j];
-            const double r = sqrt(r2);
-            e += 0.5 * (Vr_d(r2, c) + si * sjv * Va_d(r, c));
-            const double gg = dVr_over_r_d(r2, c) * r + si * sjv * dVa_d(r, c) +
-                              (Ai + Aj) * domega_d(r, c.r_l, c.r_h);
-            w += 0.5 * (-gg * r);
-        });
+    if (!halted(st)) {
+        int p0, n_own, total;
+        load_supercell(blockIdx.x, g, G, T, p0, n_own, total);
+        struct PS {
+            pos_t p;
+            double2 sa;
+        };
+        stage<PS>(
+            T, total, [&](int j) { return PS{pos[j], make_double2(sd[j].x, Ad[j])}; },
+            [&](int m, const PS& v) {
+                spos[m] = v.p;
+                ssa[m] = v.sa;
+            });
+        own_rows(nnb, p0, n_own, roff, T.sw);
+        const uint16_t* seg = nbr + (size_t)blockIdx.x * cp.seg;
+        for (int j = threadIdx.x; j < n_own; j += SC_TPB) {
+            const int p = p0 + j;
+            const int len = row_len(nnb[p]);
+            const pos_t pi = pos[p];
+            const double si = sd[p].x, Ai = Ad[p];
+            for (int k = 0; k < len; ++k) {
+                const int m = seg[roff[j] + k];
+                const double r2 = r2_d<M>(pi, spos[m], g);
+                if (r2 >= c.rc2) continue;
+                ++pairs;
+                const double sjv = ssa[m].x, Aj = ssa[m].y;
+                const double r = sqrt(r2);
+                e += 0.5 * (Vr_d(r2, c) + si * sjv * Va_d(r, c));
+                const double gg = dVr_over_r_d(r2, c) * r + si * sjv * dVa_d(r, c) + (Ai + Aj) * domega_d(r, c.r_l, c.r_h);
+                w += 0.5 * (-gg * r);
+            }
+        }
     }
     se[threadIdx.x] = e;
     sw[threadIdx.x] = w;
     sp[threadIdx.x] = pairs;
     __syncthreads();
-    for (int s = TPB / 2; s > 0; s >>= 1) {
+    for (int s = SC_TPB / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) {
             se[threadIdx.x] += se[threadIdx.x + s];
             sw[threadIdx.x] += sw[threadIdx.x + s];
@@ -1178,33 +1401,31 @@ __global__ void __launch_bounds__(TPB) k_store_switch(int n, const int* __restri
     if (A_out) A_out[o] = (double)sA[i].y;
 }
 
-// Lists in caller indices (diagnostics): staged index -> sorted index -> id.
-__global__ void __launch_bounds__(TPB) k_store_nlist(int n, int cap_out, const int* __restrict__ id, ListRef L,
-                                                     StageTable tb, int* __restrict__ nnb_out, int* __restrict__ nbr_out)
+
+// Lists in caller indices (diagnostics): staging index -> sorted index -> id.
+__global__ void __launch_bounds__(SC_TPB) k_store_nlist(Geom g, SuperGrid G, SuperCaps cp,
+                                                        const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
+                                                        const int* __restrict__ id, int cap_out,
+                                                        int* __restrict__ nnb_out, int* __restrict__ nbr_out)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int b = i / TPB;
-    const int R = tb.n[b];
-    const int* off = tb.off + (size_t)b * (tb.cmax + 1);
-    const int* base = tb.base + (size_t)b * tb.cmax;
-    const int o = id[i];
-    const int w = L.nnb[i];
-    const int nn = w & 0xffff, nf = w >> 16;
-    if (nnb_out) nnb_out[o] = nn + nf;
-    if (!nbr_out) return;
-    int k = 0;
-    for_entries(L, n, i, nn, nf, [&](int s) {
-        if (k >= cap_out) return;
-        int lo = 0, hi = R - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (off[mid] <= s) lo = mid;
-            else hi = mid - 1;
-        }
-        nbr_out[(size_t)o * cap_out + k++] = id[base[lo] + (s - off[lo])];
-    });
+    __shared__ SuperTab T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    int* roff = (int*)smem;
+    int p0, n_own, total;
+    load_supercell(blockIdx.x, g, G, T, p0, n_own, total);
+    own_rows(nnb, p0, n_own, roff, T.sw);
+    const uint16_t* seg = nbr + (size_t)blockIdx.x * cp.seg;
+    for (int j = threadIdx.x; j < n_own; j += SC_TPB) {
+        const int p = p0 + j;
+        const int o = id[p];
+        const int len = row_len(nnb[p]);
+        if (nnb_out) nnb_out[o] = len;
+        if (!nbr_out) continue;
+        for (int e = 0; e < len && e < cap_out; ++e)
+            nbr_out[(size_t)o * cap_out + e] = id[staged_index(T, seg[roff[j] + e])];
+    }
 }
+
 
 // Opens one loop iteration: advances the device iteration counter (which
 // keys the Langevin noise) and, inside a CUDA graph, sets the conditional

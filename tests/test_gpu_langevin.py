@@ -157,19 +157,19 @@ def test_kernel_launch_accounting():
     pos, vel, L, p = _system(2000, 0.5, seed=9)
     with vbc.System(pos, L, _vp(p), vel=vel) as s:
         # direct launches (per-kernel timing on): one iteration counter reset, then per
-        # iteration a gate, 9 rebuild kernels (returning at once when no rebuild is due),
+        # iteration a gate, 8 rebuild kernels (returning at once when no rebuild is due),
         # count, chain and force
         s.profile(True)
         before = s.kernel_launches()
         s.step(10, 0.005, 1.0, 1.0)
-        assert s.kernel_launches() - before == 1 + 11 * 13
+        assert s.kernel_launches() - before == 1 + 11 * 12
         s.profile(False)
-        # graphs: iterations 1..8 run as four two-step graphs of 8 kernels, plus 9 kernels
+        # graphs: iterations 1..8 run as four two-step graphs of 8 kernels, plus 8 kernels
         # for every rebuild the graphs' conditionals executed
         before = s.kernel_launches()
         s.step(10, 0.005, 1.0, 1.0)
         d = s.kernel_launches() - before
-        assert d >= 1 + 3 * 13 + 4 * 8 and (d - (1 + 3 * 13 + 4 * 8)) % 9 == 0
+        assert d >= 1 + 3 * 12 + 4 * 8 and (d - (1 + 3 * 12 + 4 * 8)) % 8 == 0
 
 
 @pytest.mark.parametrize("prec", [F32, F64])
