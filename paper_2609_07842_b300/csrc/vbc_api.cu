@@ -4,7 +4,7 @@
 // all work on one CUDA stream.  The host never waits for the device inside a
 // run of steps: neighbour-list rebuilds are decided on the device, and the
 // host reads the status words once, when the call ends.  If a rebuild found a
-// list longer than its capacity, or a supercell whose neighbourhood or list
+// list longer than its capacity, or a cell group whose neighbourhood or list
 // segment does not fit its capacity, every later kernel of the call stopped without
 // touching the state; the host then grows the capacity and resumes from the
 // iteration that stopped, so the trajectory is the same as with large enough
@@ -54,8 +54,8 @@ int fail(int code, const char* fmt, ...)
     } while (0)
 
 constexpr int MAX_CAP = 4096;          // longest neighbour list the library will grow to
-constexpr int MAX_STAGE = 65535;       // staged particles per supercell (16-bit list entries)
-constexpr int MAX_OWN = 8 * MAX_CELL;  // particles of one supercell
+constexpr int MAX_STAGE = 65535;       // staged particles per cell group (16-bit list entries)
+constexpr int MAX_OWN = 4096;          // particles of one cell group
 constexpr size_t MAX_SMEM = 227 * 1024;
 constexpr int MAX_RETRIES = 12;
 constexpr int REBUILD_KERNELS = 8;     // kernels of one neighbour-list rebuild
@@ -80,11 +80,12 @@ struct vbc_system {
     ListParams lp{};
     double rcut = 0.0, rlist = 0.0;
     int cap = 0;       // list capacity per particle (multiple of 8)
-    int smax = 0;      // staging capacity in particles per supercell
-    int omax = 0;      // particles per supercell
-    int seg = 0;       // list entries per supercell (multiple of 64)
-    int npad = 0;      // cells of the grid padded to even extents
-    int nsc = 0;       // supercells (npad / 8)
+    int smax = 0;      // staging capacity in particles per cell group
+    int omax = 0;      // particles per cell group
+    int seg = 0;       // list entries per cell group (multiple of 64)
+    int npad = 0;      // cells of the padded grid
+    int nsc = 0;       // cell groups (npad / OWN_CELLS)
+    bool rel_lists = false;  // list build on block-relative float positions
 
     // device buffers (particle arrays in sorted order)
     unsigned long long *x = nullptr, *v = nullptr, *xt = nullptr, *vt = nullptr;  // [3][n] 8-byte words
@@ -93,6 +94,7 @@ struct vbc_system {
     void *post = nullptr, *xref = nullptr;
     int cur = 0;
     uint16_t* nbr = nullptr;
+    uint16_t* scratch = nullptr;  // [n][cap] rows of the list build
     int* nnb = nullptr;
     int *cell_of = nullptr, *slot_of = nullptr, *order = nullptr;
     int *cell_count = nullptr, *cell_start = nullptr, *morton_rank = nullptr, *sc_org = nullptr;
@@ -136,6 +138,7 @@ struct vbc_system {
     SuperCaps caps() const { return SuperCaps{smax, omax, seg, cap}; }
     // dynamic shared memory of each kernel family
     size_t smem_nlist() const { return nlist_layout(caps(), pos_bytes()).total; }
+    size_t smem_nlist_rel() const { return nlist_layout(caps(), sizeof(float4)).total; }
     size_t smem_count() const { return pass_layout(caps(), pos_bytes(), 0).total; }
     size_t smem_chain() const { return pass_layout(caps(), pos_bytes(), real_bytes()).total; }
     size_t smem_force() const { return force_layout(caps(), pos_bytes(), real_bytes()).total; }
@@ -258,6 +261,9 @@ ListParams make_list_params(const Coef& c, double rlist, const Geom& g)
     lp.rlist2_fix = (unsigned long long)std::llround(lp.rlist2 / s2);
     lp.near2 = std::max(c.rr2, c.rl2);
     lp.near2_fix = (unsigned long long)std::llround(lp.near2 / s2);
+    const double rm = rlist * (1.0 + 1e-5);
+    lp.rlist2_f = (float)(rm * rm);
+    lp.near2_f = (float)lp.near2;
     return lp;
 }
 
@@ -312,7 +318,7 @@ void free_all(vbc_system* s)
 {
     dfree(s->x); dfree(s->v); dfree(s->xt); dfree(s->vt); dfree(s->id); dfree(s->idt);
     dfree(s->pos[0]); dfree(s->pos[1]); dfree(s->post); dfree(s->xref);
-    dfree(s->nbr); dfree(s->nnb); dfree(s->cell_of); dfree(s->slot_of); dfree(s->order);
+    dfree(s->nbr); dfree(s->scratch); dfree(s->nnb); dfree(s->cell_of); dfree(s->slot_of); dfree(s->order);
     dfree(s->cell_count); dfree(s->cell_start); dfree(s->morton_rank); dfree(s->sc_org);
     dfree(s->chunk_sum);
     dfree(s->ds); dfree(s->sA); dfree(s->st); dfree(s->partial); dfree(s->ppairs); dfree(s->red);
@@ -345,10 +351,12 @@ int configure_smem(vbc_system* s)
 {
     if (s->smem_force() > MAX_SMEM || s->smem_nlist() > MAX_SMEM || s->smem_energy() > MAX_SMEM)
         return fail(VBC_ERR_UNSTABLE,
-                    "a supercell's neighbourhood (%d staged, %d own particles, %d list entries) does not fit in "
+                    "a cell group's neighbourhood (%d staged, %d own particles, %d list entries) does not fit in "
                     "shared memory: the system is too dense",
                     s->smax, s->omax, s->seg);
-    VBC_TRY(set_smem(k_nlist<M>, s->smem_nlist()));
+    if (s->smem_nlist_rel() > MAX_SMEM) return fail(VBC_ERR_UNSTABLE, "list build staging too large");
+    VBC_TRY(set_smem(k_nlist<M, false>, s->smem_nlist()));
+    if constexpr (!M::fp64) VBC_TRY(set_smem(k_nlist<M, true>, s->smem_nlist_rel()));
     VBC_TRY(set_smem(k_count<M>, s->smem_count()));
     VBC_TRY(set_smem(k_chain<M>, s->smem_chain()));
     VBC_TRY(set_smem(k_force<M, EPI_FORCE>, s->smem_force()));
@@ -384,8 +392,15 @@ int enqueue_rebuild(vbc_system* s)
                                             (pos_t*)s->post, s->st);
     k_copyback<M><<<nb, TPB, 0, s->stream>>>(n, s->xt, s->vt, s->idt, (const pos_t*)s->post, s->x, s->v, s->id,
                                              pos, (pos_t*)s->xref, s->st);
-    k_nlist<M><<<s->nsc, SC_TPB, s->smem_nlist(), s->stream>>>(s->geom, pos, s->grid(), s->caps(), s->lp, s->nbr,
-                                                                s->nnb, s->st);
+    if constexpr (!M::fp64) {
+        if (s->rel_lists) {
+            k_nlist<M, true><<<s->nsc, SC_TPB, s->smem_nlist_rel(), s->stream>>>(
+                s->geom, pos, s->grid(), s->caps(), s->lp, s->scratch, s->nbr, s->nnb, s->st);
+            return check_launch(s, REBUILD_KERNELS);
+        }
+    }
+    k_nlist<M, false><<<s->nsc, SC_TPB, s->smem_nlist(), s->stream>>>(s->geom, pos, s->grid(), s->caps(), s->lp,
+                                                                       s->scratch, s->nbr, s->nnb, s->st);
     return check_launch(s, REBUILD_KERNELS);
 }
 
@@ -478,20 +493,23 @@ int grow(vbc_system* s)
             return fail(VBC_ERR_NLIST_OVERFLOW, "a particle has %d neighbours within r_c + skin, above the limit %d",
                         need, MAX_CAP);
         int cap = std::max(s->cap + s->cap / 2, need + need / 4 + 8);
-        s->cap = std::min((cap + 7) & ~7, MAX_CAP);
+        cap = std::min((cap + 7) & ~7, MAX_CAP);
+        dfree(s->scratch);
+        VBC_TRY(dalloc(s->scratch, (size_t)cap * (size_t)s->n));
+        s->cap = cap;
     }
     if (h.stage_overflow) {
         if (h.max_stage > s->smax) {
             const int smax = ((h.max_stage + h.max_stage / 8 + 63) / 64) * 64;
             if (smax > MAX_STAGE)
-                return fail(VBC_ERR_UNSTABLE, "a supercell's neighbourhood holds %d particles, above the limit %d",
+                return fail(VBC_ERR_UNSTABLE, "a cell group's neighbourhood holds %d particles, above the limit %d",
                             h.max_stage, MAX_STAGE);
             s->smax = smax;
         }
         if (h.max_own > s->omax) {
             const int omax = ((h.max_own + h.max_own / 4 + 31) / 32) * 32;
             if (omax > MAX_OWN)
-                return fail(VBC_ERR_UNSTABLE, "a supercell holds %d particles, above the limit %d", h.max_own,
+                return fail(VBC_ERR_UNSTABLE, "a cell group holds %d particles, above the limit %d", h.max_own,
                             MAX_OWN);
             s->omax = omax;
         }
@@ -749,6 +767,38 @@ int build_now(vbc_system* s)
     }
 }
 
+// Trims the capacities to what the last build needed, with headroom, so that
+// the kernels' shared memory (and with it their occupancy) follows the
+// system rather than the initial estimate; rebuilds when anything shrank.
+// Growth stays with the overflow path.
+template <class M>
+int trim_capacities(vbc_system* s)
+{
+    VBC_TRY(read_status(s));
+    const Status& h = *s->st_host;
+    const int smax = std::min(s->smax, std::max((h.max_stage + h.max_stage / 8 + 32 + 63) / 64 * 64, 64));
+    const int omax = std::min(s->omax, std::max((h.max_own + h.max_own / 4 + 8 + 31) / 32 * 32, 32));
+    const int seg = std::min(s->seg, std::max((h.max_seg + h.max_seg / 4 + 64 + 63) / 64 * 64, 64));
+    const int cap = std::min(s->cap, std::max((h.max_nnb + h.max_nnb / 4 + 8 + 7) & ~7, 8));
+    if (smax == s->smax && omax == s->omax && seg == s->seg && cap == s->cap) return VBC_OK;
+    VBC_CUDA(cudaStreamSynchronize(s->stream));
+    if (seg != s->seg) {
+        dfree(s->nbr);
+        VBC_TRY(dalloc(s->nbr, (size_t)seg * (size_t)s->nsc));
+    }
+    if (cap != s->cap) {
+        dfree(s->scratch);
+        VBC_TRY(dalloc(s->scratch, (size_t)cap * (size_t)s->n));
+    }
+    s->smax = smax;
+    s->omax = omax;
+    s->seg = seg;
+    s->cap = cap;
+    VBC_TRY(configure(s));
+    s->layout_version += 1;
+    return build_now<M>(s);
+}
+
 }  // namespace
 
 // Lets the other translation unit of the library (vbc_noalloc.cu) report
@@ -813,10 +863,12 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     if ((double)(g.nc[0] + 1) * (g.nc[1] + 1) * (g.nc[2] + 1) > 2.0e9)
         return bail(fail(VBC_ERR_INVALID_ARG, "cell grid too large"));
     g.ncell = g.nc[0] * g.nc[1] * g.nc[2];
-    int pc[3];
-    for (int a = 0; a < 3; ++a) pc[a] = g.nc[a] + (g.nc[a] & 1);  // padded to even extents
+    // padded to multiples of the cell-group extents
+    const int pc[3] = {(g.nc[0] + BXC - 1) / BXC * BXC, (g.nc[1] + BYC - 1) / BYC * BYC,
+                       (g.nc[2] + BZC - 1) / BZC * BZC};
     s->npad = pc[0] * pc[1] * pc[2];
-    s->nsc = s->npad / 8;
+    s->nsc = s->npad / OWN_CELLS;
+    s->rel_lists = s->prec == VBC_FP32_SPLIT && g.nc[0] >= 8 && g.nc[1] >= 8 && g.nc[2] >= 8;
     g.s32 = (float)g.s32d[0];
     g.s32sq = (float)(g.s32d[0] * g.s32d[0]);
     {
@@ -831,11 +883,12 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     int cap = cfg->nlist_cap > 0 ? cfg->nlist_cap : (int)std::ceil(1.3 * kbar + 6.0 * std::sqrt(kbar) + 12.0);
     s->cap = std::min((std::max(cap, 1) + 7) & ~7, MAX_CAP);
     {
-        // a supercell owns 8 cells and stages 64; lists hold about kbar entries per particle
+        // a group owns OWN_CELLS cells and stages SCELLS; lists hold about kbar entries per
+        // particle (trimmed to the first build's needs once it ran)
         const double rho_cell = (double)s->n / g.ncell;
-        s->smax = std::min((((int)std::ceil(1.5 * 64.0 * rho_cell) + 64) + 63) / 64 * 64, MAX_STAGE);
-        s->omax = std::min(((int)std::ceil(2.0 * 8.0 * rho_cell) + 32 + 31) / 32 * 32, MAX_OWN);
-        const double entries = 8.0 * rho_cell * (std::min(kbar, (double)s->cap) + 4.0);
+        s->smax = std::min((((int)std::ceil(1.5 * SCELLS * rho_cell) + 64) + 63) / 64 * 64, MAX_STAGE);
+        s->omax = std::min(((int)std::ceil(2.0 * OWN_CELLS * rho_cell) + 32 + 31) / 32 * 32, MAX_OWN);
+        const double entries = OWN_CELLS * rho_cell * (std::min(kbar, (double)s->cap) + 4.0);
         s->seg = (int)std::min(((long long)std::ceil(1.5 * entries) + 256 + 63) / 64 * 64, 1LL << 24);
     }
 
@@ -866,6 +919,7 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     ALLOC(dalloc_bytes(s->post, n * s->pos_bytes()));
     ALLOC(dalloc_bytes(s->xref, n * s->pos_bytes()));
     ALLOC(dalloc(s->nbr, (size_t)s->seg * (size_t)s->nsc));
+    ALLOC(dalloc(s->scratch, (size_t)s->cap * n));
     ALLOC(dalloc(s->nnb, n));
     ALLOC(dalloc(s->cell_of, n));
     ALLOC(dalloc(s->slot_of, n));
@@ -890,10 +944,11 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
         return bail(fail(VBC_ERR_OOM, "pinned host allocation failed"));
     if ((rc = configure(s)) != VBC_OK) return bail(rc);
 
-    // Morton order of the padded grid's cells.  Each aligned 2x2x2 block has
-    // eight consecutive codes, so supercell s holds the ranks 8s .. 8s+7; its
-    // rank-8s cell (even coordinates) is its origin.  Phantom cells (beyond
-    // the real grid) are ranked but never hold a particle.
+    // Morton order of the padded grid's cells.  Each aligned BXC x BYC x BZC
+    // group has OWN_CELLS consecutive codes, so group s holds the ranks
+    // OWN_CELLS s .. OWN_CELLS (s+1) - 1; its lowest-ranked cell is its
+    // origin.  Phantom cells (beyond the real grid) are ranked but never hold
+    // a particle.
     {
         std::vector<std::pair<uint32_t, int>> code((size_t)s->npad);
         for (int z = 0; z < pc[2]; ++z)
@@ -907,7 +962,7 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
         for (int r = 0; r < s->npad; ++r) {
             const int lin = code[r].second;
             const int x = lin % pc[0], y = (lin / pc[0]) % pc[1], z = lin / (pc[0] * pc[1]);
-            if (r % 8 == 0) org[r / 8] = x | (y << 10) | (z << 20);
+            if (r % OWN_CELLS == 0) org[r / OWN_CELLS] = x | (y << 10) | (z << 20);
             if (x < g.nc[0] && y < g.nc[1] && z < g.nc[2]) rank[(z * g.nc[1] + y) * g.nc[0] + x] = r;
         }
         if (cudaMemcpy(s->morton_rank, rank.data(), rank.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -924,9 +979,11 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     if (s->prec == VBC_FP64) {
         if ((rc = load_state<ModeF64>(s, cfg->pos, cfg->vel, cfg->inputs_on_device)) != VBC_OK) return bail(rc);
         if ((rc = build_now<ModeF64>(s)) != VBC_OK) return bail(rc);
+        if ((rc = trim_capacities<ModeF64>(s)) != VBC_OK) return bail(rc);
     } else {
         if ((rc = load_state<ModeF32>(s, cfg->pos, cfg->vel, cfg->inputs_on_device)) != VBC_OK) return bail(rc);
         if ((rc = build_now<ModeF32>(s)) != VBC_OK) return bail(rc);
+        if ((rc = trim_capacities<ModeF32>(s)) != VBC_OK) return bail(rc);
     }
     *out = s;
     return VBC_OK;

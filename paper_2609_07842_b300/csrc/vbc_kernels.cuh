@@ -1,14 +1,14 @@
 // vbc_kernels.cuh -- CUDA kernels of the VBC path (sm_103a).
 //
 // Particles are stored sorted by cell, the cells ranked along a Morton curve.
-// The cell grid (cells at least r_c + skin wide) is padded to even extents
-// with empty phantom cells, so every aligned 2x2x2 block of cells -- a
-// supercell -- holds eight consecutive ranks and its particles form one
-// contiguous range of the sorted arrays.  Every kernel that walks neighbour
-// lists runs one block per supercell.  The block first copies the 4x4x4 real
-// cells around its supercell into shared memory (the staging), and the lists
-// hold 16-bit indices into that staging, so a pass reads 2 bytes per list
-// entry from HBM and serves every neighbour lookup from shared memory.
+// The cell grid (cells at least r_c + skin wide) is padded with empty
+// phantom cells so that every aligned 4x2x2 group of cells holds consecutive
+// ranks and its particles form one contiguous range of the sorted arrays.
+// Every kernel that walks neighbour lists runs one thread block per group.
+// The block first copies the 6x4x4 real cells around its group into shared
+// memory (the staging), and the lists hold 16-bit indices into that staging,
+// so a pass reads 2 bytes per list entry from HBM and serves every neighbour
+// lookup from shared memory.
 //
 // One MD step:
 //   rebuild (only when a particle moved more than skin/2 since the last build):
@@ -24,13 +24,14 @@
 // atomics, so results do not depend on scheduling.
 #pragma once
 
+#include <type_traits>
+
 #include "vbc_device.cuh"
 
 namespace vbc {
 
 constexpr int TPB = 128;          // threads per block of the per-particle kernels
-constexpr int SC_TPB = 128;       // threads per block of the supercell kernels
-constexpr int SC_CELLS = 64;      // staged cells per supercell (4 x 4 x 4)
+constexpr int SC_TPB = 128;       // threads per block of the cell-group kernels
 constexpr int SCAN_CHUNK = 2048;  // cells per block in the two-pass scan
 constexpr int SCAN_TPB = 256;
 constexpr int MAX_CELL = 512;     // a denser cell means the system has collapsed
@@ -225,33 +226,48 @@ __global__ void __launch_bounds__(TPB) k_copyback(int n, const unsigned long lon
 }
 
 
-// ================================================================ supercells
-// Staged cells are numbered k = 16 lz + 4 ly + lx (l in 0..3 along each axis,
-// the supercell's own cells at l in {1, 2}) and copied in that order, so the
+// ================================================================ blocks of cells
+// The cell grid is padded with empty phantom cells to extents that are
+// multiples of (BXC, BYC, BZC), and cells are ranked along the Morton curve
+// of the padded grid (code bits x0 y0 z0 x1 y1 z1 ... from the lowest).  An
+// aligned BXC x BYC x BZC group of cells is then 2^BLOCK_BITS consecutive
+// ranks, so its particles form one contiguous range of the sorted arrays.
+// Every kernel that walks neighbour lists runs one thread block per such
+// group.  The block first copies the (BXC+2) x (BYC+2) x (BZC+2) real cells
+// around its group (periodic wrap on the real grid) into shared memory --
+// the staging -- cell by cell in the order k = (lz SY + ly) SX + lx, so the
 // three cells of one x row of a particle's 27-cell neighbourhood occupy one
-// contiguous range of the staging.  Neighbour cells wrap on the real grid,
-// which needs at least 3 cells per axis; with exactly 3 a staged cell can
-// appear twice, but the 27 cells around any one particle stay distinct.
+// contiguous range of the staging.  List entries are 16-bit staging indices.
+// The wrap needs at least 3 real cells per axis; with few cells a staged
+// cell can appear twice, but the 27 cells around any one particle are
+// distinct.
+constexpr int BLOCK_BITS = 4;                    // Morton bits x0 y0 z0 x1
+constexpr int BXC = 4, BYC = 2, BZC = 2;         // own cells per axis
+constexpr int OWN_CELLS = BXC * BYC * BZC;       // 16
+constexpr int SX = BXC + 2, SY = BYC + 2, SZ = BZC + 2;
+constexpr int SCELLS = SX * SY * SZ;             // 96 staged cells
+constexpr int SCELLS_P2 = 128;                   // offset table size (binary search)
+static_assert(SCELLS <= SC_TPB && SCELLS <= SCELLS_P2, "one thread per staged cell");
 
 struct SuperGrid {
     const int* morton_rank;  // real linear cell index -> rank on the padded Morton curve
-    const int* sc_org;       // supercell -> coordinates of its first cell, x | y << 10 | z << 20
+    const int* sc_org;       // block -> coordinates of its first cell, x | y << 10 | z << 20
     const int* cell_start;   // rank -> sorted index of its first particle; [npad + 1]
 };
 
-// Per-supercell capacities (grown after an overflow).
+// Per-block capacities (grown after an overflow).
 struct SuperCaps {
     int smax;  // staged particles
-    int omax;  // own particles (multiple of 4)
-    int seg;   // list entries of one supercell (multiple of 64)
+    int omax;  // own particles (multiple of 32)
+    int seg;   // list entries of one block (multiple of 64)
     int cap;   // list entries of one particle (multiple of 8)
 };
 
 struct SuperTab {
-    int base[SC_CELLS];     // sorted index of each staged cell's first particle
-    int off[SC_CELLS + 1];  // staging offset of each staged cell; off[SC_CELLS] = total
-    int own[9];             // cell_start of ranks 8s .. 8s+8
-    int sw[SC_TPB / 32];    // scan scratch
+    int base[SCELLS];             // sorted index of each staged cell's first particle
+    int off[SCELLS_P2 + 1];       // staging offset of each staged cell; total from SCELLS on
+    int own[OWN_CELLS + 1];       // cell_start of the block's ranks
+    int sw[SC_TPB / 32];          // scan scratch
 };
 
 // Exclusive scan of a[0..n) in shared memory, in place, with a[n] = total.
@@ -275,34 +291,35 @@ __device__ __forceinline__ int scan_in_place(int* a, int n, int* sw)
     return total;
 }
 
-// Reads the staging table of supercell s (whole block).  Returns the first
-// own particle p0, the number of own particles and of staged particles.
-__device__ __forceinline__ void load_supercell(int s, const Geom& g, const SuperGrid& G, SuperTab& T, int& p0,
+// Reads the staging table of block s (whole block).  Returns the first own
+// particle p0, the number of own particles and of staged particles.
+__device__ __forceinline__ void load_group(int s, const Geom& g, const SuperGrid& G, SuperTab& T, int& p0,
                                                int& n_own, int& total)
 {
     const int t = threadIdx.x;
     int cnt = 0;
-    if (t < SC_CELLS) {
+    if (t < SCELLS) {
         const int org = __ldg(G.sc_org + s);
-        int x = (org & 1023) - 1 + (t & 3);
-        int y = ((org >> 10) & 1023) - 1 + ((t >> 2) & 3);
-        int z = (org >> 20) - 1 + (t >> 4);
-        x += x < 0 ? g.nc[0] : (x >= g.nc[0] ? -g.nc[0] : 0);
-        y += y < 0 ? g.nc[1] : (y >= g.nc[1] ? -g.nc[1] : 0);
-        z += z < 0 ? g.nc[2] : (z >= g.nc[2] ? -g.nc[2] : 0);
+        int x = (org & 1023) - 1 + t % SX;
+        int y = ((org >> 10) & 1023) - 1 + (t / SX) % SY;
+        int z = (org >> 20) - 1 + t / (SX * SY);
+        x = x < 0 ? x + g.nc[0] : (x >= g.nc[0] ? x - g.nc[0] : x);
+        y = y < 0 ? y + g.nc[1] : (y >= g.nc[1] ? y - g.nc[1] : y);
+        z = z < 0 ? z + g.nc[2] : (z >= g.nc[2] ? z - g.nc[2] : z);
         const int r = __ldg(G.morton_rank + (z * g.nc[1] + y) * g.nc[0] + x);
         const int b = __ldg(G.cell_start + r);
         cnt = __ldg(G.cell_start + r + 1) - b;
         T.base[t] = b;
     }
-    if (t < 9) T.own[t] = __ldg(G.cell_start + 8 * s + t);
+    if (t <= OWN_CELLS) T.own[t] = __ldg(G.cell_start + OWN_CELLS * s + t);
     int tot;
     const int o = block_exclusive_scan<SC_TPB>(cnt, T.sw, tot);
-    if (t < SC_CELLS) T.off[t] = o;
-    if (t == 0) T.off[SC_CELLS] = tot;
+    if (t < SCELLS) T.off[t] = o;
+    else if (t < SCELLS_P2) T.off[t] = tot;
+    if (t == 0) T.off[SCELLS_P2] = tot;
     __syncthreads();
     p0 = T.own[0];
-    n_own = T.own[8] - p0;
+    n_own = T.own[OWN_CELLS] - p0;
     total = tot;
 }
 
@@ -311,7 +328,7 @@ __device__ __forceinline__ int staged_cell(const int* off, int m)
 {
     int k = 0;
 #pragma unroll
-    for (int step = 32; step > 0; step >>= 1)
+    for (int step = SCELLS_P2 / 2; step > 0; step >>= 1)
         if (off[k + step] <= m) k += step;
     return k;
 }
@@ -345,21 +362,26 @@ __device__ __forceinline__ void stage(const SuperTab& T, int total, Get&& get, P
     }
 }
 
-// Own cell (0..7, Morton low bits x | y << 1 | z << 2) of own particle p.
+// Own cell b (Morton low bits of its rank) of own particle p: the largest b
+// with own[b] <= p.
 __device__ __forceinline__ int own_cell(const SuperTab& T, int p)
 {
     int b = 0;
-    if (T.own[b + 4] <= p) b += 4;
-    if (T.own[b + 2] <= p) b += 2;
-    if (T.own[b + 1] <= p) b += 1;
+#pragma unroll
+    for (int step = OWN_CELLS / 2; step > 0; step >>= 1)
+        if (T.own[b + step] <= p) b += step;
     return b;
 }
 
-// Staged cell number of own cell b.
-__device__ __forceinline__ int own_staged_cell(int b) { return 21 + (b & 1) + ((b >> 1) & 1) * 4 + (b >> 2) * 16; }
+// Staged cell number of own cell b (bits x0 y0 z0 x1).
+__device__ __forceinline__ int own_staged_cell(int b)
+{
+    const int bx = (b & 1) | ((b >> 2) & 2), by = (b >> 1) & 1, bz = (b >> 2) & 1;
+    return ((1 + bz) * SY + (1 + by)) * SX + (1 + bx);
+}
 
 // ---------------------------------------------------------------- lists
-// The lists of supercell s occupy nbr[s * seg ...]: the rows of its own
+// The lists of block s occupy nbr[s * seg ...]: the rows of its own
 // particles in sorted order, each padded to a multiple of 4 entries.  A row
 // holds the near entries (closer than max(r_r, r_l) at the build) first,
 // then the far ones (up to r_c + skin); pads repeat the particle's own
@@ -376,11 +398,20 @@ __device__ __forceinline__ int own_rows(const int* __restrict__ nnb, int p0, int
     return scan_in_place(roff, n_own, sw);
 }
 
-// Near (0), far (1) or beyond the list radius (-1), from exact integer
-// squared separations in the FP32 mode.
+// The 4 entries of one 8-byte chunk.
+__device__ __forceinline__ void unpack4(const uint2 v, int h[4])
+{
+    h[0] = (int)(v.x & 0xffffu);
+    h[1] = (int)(v.x >> 16);
+    h[2] = (int)(v.y & 0xffffu);
+    h[3] = (int)(v.y >> 16);
+}
+
+// Near (0), far (1) or beyond the list radius (-1).
 struct ListParams {
     unsigned long long rlist2_fix, near2_fix;
     double rlist2, near2;
+    float rlist2_f, near2_f;  // float tests on block-relative coordinates (with a margin)
 };
 template <class M>
 struct ListTest;
@@ -407,27 +438,39 @@ struct ListTest<ModeF64> {
         return r2 < lp.near2 ? 0 : 1;
     }
 };
+// Float positions relative to the block's centre (FP32 mode, at least 8
+// cells per axis so that the staging spans less than half the box): the
+// classification only has to keep every pair within r_c + skin, so it tests
+// against a radius enlarged by a relative 1e-5, far above the float error.
+struct ListTestRel {
+    __device__ __forceinline__ static int cls(const float4& a, const float4& b, const ListParams& lp)
+    {
+        const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+        const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz));
+        if (r2 >= lp.rlist2_f) return -1;
+        return r2 < lp.near2_f ? 0 : 1;
+    }
+};
 
 // ---------------------------------------------------------------- shared-memory layouts
-// Dynamic shared memory of each supercell kernel, carved in 16-byte aligned
+// Dynamic shared memory of each block kernel, carved in 16-byte aligned
 // pieces; the host sizes its launches with the same functions.
 __host__ __device__ constexpr size_t al16(size_t v) { return (v + 15) & ~(size_t)15; }
 
 struct NlistLayout {
-    size_t rows, roff, rnn, total;
+    size_t roff, rnn, total;
 };
 __host__ __device__ inline NlistLayout nlist_layout(const SuperCaps& cp, size_t pos_bytes)
 {
     NlistLayout l{};
-    l.rows = al16((size_t)cp.smax * pos_bytes);
-    l.roff = l.rows + al16((size_t)cp.omax * cp.cap * 2);
+    l.roff = al16((size_t)cp.smax * pos_bytes);
     l.rnn = l.roff + al16((size_t)(cp.omax + 1) * 4);
     l.total = l.rnn + al16((size_t)cp.omax * 4);
     return l;
 }
 
-// k_count, k_chain, the energy kernels and k_store_nlist: staged positions,
-// an optional staged value per particle, row offsets and a particle list.
+// k_count, k_chain, the energy kernels: staged positions, an optional staged
+// value per particle, row offsets and a particle list.
 struct PassLayout {
     size_t val, roff, plist, total;
 };
@@ -442,33 +485,37 @@ __host__ __device__ inline PassLayout pass_layout(const SuperCaps& cp, size_t po
 }
 
 // k_force: staged positions (with s_j in the spare word) and A_j, row
-// offsets, the owner of each 4-entry chunk and the chunks' partial forces.
+// offsets, the owner of each 4-entry chunk, the own particles' positions and
+// A, and the forces of owners whose chunks one thread covered completely.
 struct ForceLayout {
-    size_t sA, roff, cown, cpart, total;
+    size_t sA, roff, cown, opos, oA, oF, total;
 };
 __host__ __device__ inline ForceLayout force_layout(const SuperCaps& cp, size_t pos_bytes, size_t real_bytes)
 {
     ForceLayout l{};
-    const size_t nch = (size_t)cp.seg / 4;
     l.sA = al16((size_t)cp.smax * pos_bytes);
     l.roff = l.sA + al16((size_t)cp.smax * real_bytes);
     l.cown = l.roff + al16((size_t)(cp.omax + 1) * 4);
-    l.cpart = l.cown + al16(nch * 2);
-    l.total = l.cpart + al16(3 * nch * real_bytes);
+    l.opos = l.cown + al16((size_t)cp.seg / 4 * 2);
+    l.oA = l.opos + al16((size_t)cp.omax * pos_bytes);
+    l.oF = l.oA + al16((size_t)cp.omax * real_bytes);
+    l.total = l.oF + al16((size_t)3 * cp.omax * real_bytes);
     return l;
 }
 
 // ================================================================ rebuild: lists
-// One block per supercell: stage the 4x4x4 cells, then each thread takes own
-// particles and scans the 9 contiguous x rows of their 27-cell neighbourhood,
-// writing a two-ended row (near from the front, far from the back) into
-// shared memory; the rows are then packed into the supercell's segment.
-template <class M>
+// One block per cell group: stage the surrounding cells, then each thread
+// takes own particles and scans the 9 contiguous x rows of their 27-cell
+// neighbourhood, writing a two-ended row (near from the front, far from the
+// back) into a per-particle scratch row in global memory; the rows are then
+// packed into the block's segment.
+template <class M, bool REL>
 __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_t* __restrict__ pos, SuperGrid G,
-                                                  SuperCaps cp, ListParams lp, uint16_t* __restrict__ nbr,
-                                                  int* __restrict__ nnb, Status* st)
+                                                  SuperCaps cp, ListParams lp, uint16_t* __restrict__ scratch,
+                                                  uint16_t* __restrict__ nbr, int* __restrict__ nnb, Status* st)
 {
     using pos_t = typename M::pos_t;
+    using spos_t = typename std::conditional<REL, float4, pos_t>::type;
     // raises `overflow` and `stage_overflow` itself, so it does not test them
     if (!st->rebuild || st->frozen || st->crowded) return;
     __shared__ SuperTab T;
@@ -477,7 +524,7 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
     extern __shared__ __align__(16) unsigned char smem[];
     const int t = threadIdx.x;
     int p0, n_own, total;
-    load_supercell(blockIdx.x, g, G, T, p0, n_own, total);
+    load_group(blockIdx.x, g, G, T, p0, n_own, total);
     if (t == 0) {
         atomicMax(&st->max_stage, total);
         atomicMax(&st->max_own, n_own);
@@ -491,12 +538,27 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
         }
         return;
     }
-    const NlistLayout ly = nlist_layout(cp, sizeof(pos_t));
-    pos_t* spos = (pos_t*)smem;
-    uint16_t* rows = (uint16_t*)(smem + ly.rows);
+    const NlistLayout ly = nlist_layout(cp, sizeof(spos_t));
+    spos_t* spos = (spos_t*)smem;
     int* roff = (int*)(smem + ly.roff);
     int* rnn = (int*)(smem + ly.rnn);
-    stage<pos_t>(T, total, [&](int j) { return pos[j]; }, [&](int m, const pos_t& v) { spos[m] = v; });
+    if constexpr (REL) {
+        // reference: the centre of the block's own cells (a cell boundary)
+        const int org = __ldg(G.sc_org + blockIdx.x);
+        const int cx[3] = {(org & 1023) + BXC / 2, ((org >> 10) & 1023) + BYC / 2, (org >> 20) + BZC / 2};
+        uint32_t ref[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) ref[a] = (uint32_t)(((unsigned long long)cx[a] << 32) / (unsigned)g.nc[a]);
+        stage<int4>(
+            T, total, [&](int j) { return pos[j]; },
+            [&](int m, const int4& v) {
+                spos[m] = make_float4((float)(int)((uint32_t)v.x - ref[0]) * g.s32,
+                                      (float)(int)((uint32_t)v.y - ref[1]) * g.s32,
+                                      (float)(int)((uint32_t)v.z - ref[2]) * g.s32, 0.0f);
+            });
+    } else {
+        stage<pos_t>(T, total, [&](int j) { return pos[j]; }, [&](int m, const pos_t& v) { spos[m] = v; });
+    }
     __syncthreads();
     int mx = 0;
     long long sum = 0;
@@ -506,16 +568,19 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
         const int b = own_cell(T, p);
         const int kb = own_staged_cell(b);
         const int mself = T.off[kb] + (p - T.own[b]);
-        const pos_t pi = spos[mself];
-        uint16_t* row = rows + (size_t)j * cp.cap;
+        const spos_t pi = spos[mself];
+        uint16_t* row = scratch + (size_t)p * cp.cap;
         int nn = 0, nf = 0;
+#pragma unroll 1
         for (int d = 0; d < 9; ++d) {
-            const int k0 = kb + (d / 3 - 1) * 16 + (d % 3 - 1) * 4 - 1;
+            const int k0 = kb + (d / 3 - 1) * (SX * SY) + (d % 3 - 1) * SX - 1;
             const int e = T.off[k0 + 3];
+#pragma unroll 4
             for (int m = T.off[k0]; m < e; ++m) {
-                if (m == mself) continue;
-                const int cl = ListTest<M>::cls(pi, spos[m], g, lp);
-                if (cl < 0) continue;
+                int cl;
+                if constexpr (REL) cl = ListTestRel::cls(pi, spos[m], lp);
+                else cl = ListTest<M>::cls(pi, spos[m], g, lp);
+                if (cl < 0 || m == mself) continue;
                 if (nn + nf < cp.cap) row[cl == 0 ? nn : cp.cap - 1 - nf] = (uint16_t)m;
                 if (cl == 0) ++nn;
                 else ++nf;
@@ -523,7 +588,7 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
         }
         const int len = nn + nf;
         nnb[p] = nn | (nf << 16);
-        rnn[j] = (nn | (nf << 16));
+        rnn[j] = nn | (nf << 16);
         roff[j] = pad4(len);
         over |= len > cp.cap;
         mx = max(mx, len);
@@ -569,8 +634,8 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
             else hi = mid - 1;
         }
         const int j = lo, w = rnn[j], nn = w & 0xffff, len = nn + (w >> 16);
-        const uint16_t* row = rows + (size_t)j * cp.cap;
         const int p = p0 + j;
+        const uint16_t* row = scratch + (size_t)p * cp.cap;
         const int b = own_cell(T, p);
         const uint32_t self = (uint32_t)(T.off[own_staged_cell(b)] + (p - T.own[b]));
         uint32_t h[4];
@@ -633,15 +698,6 @@ __device__ __forceinline__ double r2_d(const typename M::pos_t& a, const typenam
     return dx * dx + dy * dy + dz * dz;
 }
 
-// The 4 entries of one 8-byte chunk.
-__device__ __forceinline__ void unpack4(const uint2 v, int h[4])
-{
-    h[0] = (int)(v.x & 0xffffu);
-    h[1] = (int)(v.x >> 16);
-    h[2] = (int)(v.y & 0xffffu);
-    h[3] = (int)(v.y >> 16);
-}
-
 template <class M>
 __global__ void __launch_bounds__(SC_TPB) k_count(Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
                                                   SuperGrid G, SuperCaps cp, const uint16_t* __restrict__ nbr,
@@ -659,7 +715,7 @@ __global__ void __launch_bounds__(SC_TPB) k_count(Geom g, Coef c, const typename
     extern __shared__ __align__(16) unsigned char smem[];
     const int t = threadIdx.x;
     int p0, n_own, total;
-    load_supercell(blockIdx.x, g, G, T, p0, n_own, total);
+    load_group(blockIdx.x, g, G, T, p0, n_own, total);
     const PassLayout ly = pass_layout(cp, sizeof(pos_t), 0);
     pos_t* spos = (pos_t*)smem;
     int* roff = (int*)(smem + ly.roff);
@@ -746,7 +802,7 @@ __global__ void __launch_bounds__(SC_TPB) k_count(Geom g, Coef c, const typename
 
 // ================================================================ chain-rule pass
 // A_i = s'_i sum_j s_j V_a(r_ij) for particles inside the switching window
-// (s'_i != 0), one warp per such particle; supercells without one return
+// (s'_i != 0), one warp per such particle; blocks without one return
 // after one vote.
 template <class M>
 __global__ void __launch_bounds__(SC_TPB) k_chain(Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
@@ -759,7 +815,8 @@ __global__ void __launch_bounds__(SC_TPB) k_chain(Geom g, Coef c, const typename
     if (halted(st)) return;
     const int t = threadIdx.x;
     {
-        const int q0 = __ldg(G.cell_start + 8 * blockIdx.x), q1 = __ldg(G.cell_start + 8 * blockIdx.x + 8);
+        const int q0 = __ldg(G.cell_start + OWN_CELLS * blockIdx.x),
+                  q1 = __ldg(G.cell_start + OWN_CELLS * blockIdx.x + OWN_CELLS);
         bool any = false;
         for (int p = q0 + t; p < q1; p += SC_TPB) any |= ds[p] != (real)0;
         if (!__syncthreads_or(any)) return;
@@ -768,7 +825,7 @@ __global__ void __launch_bounds__(SC_TPB) k_chain(Geom g, Coef c, const typename
     __shared__ int s_nw;
     extern __shared__ __align__(16) unsigned char smem[];
     int p0, n_own, total;
-    load_supercell(blockIdx.x, g, G, T, p0, n_own, total);
+    load_group(blockIdx.x, g, G, T, p0, n_own, total);
     const PassLayout ly = pass_layout(cp, sizeof(pos_t), sizeof(real));
     pos_t* spos = (pos_t*)smem;
     real* ss = (real*)(smem + ly.val);
@@ -820,6 +877,7 @@ __global__ void __launch_bounds__(SC_TPB) k_chain(Geom g, Coef c, const typename
         if (lane == 0) sA[p].y = ds[p] * acc;
     }
 }
+
 // ================================================================ pass 2: forces + BAOAB
 struct StepArgs {
     void* x;              // [3][n] unwrapped positions (FP32 mode: int64 in units L / 2^52; FP64: double)
@@ -835,15 +893,56 @@ struct StepArgs {
     float half_skin2;     // (skin / 2)^2
 };
 
+// State of one particle for its BAOAB update, loaded before the force loop
+// so that the loads overlap it.
+template <class M>
+struct PState;
+template <>
+struct PState<ModeF32> {
+    long long X[3];
+    float2 V[3];
+    int4 xr;
+    uint32_t id;
+};
+template <>
+struct PState<ModeF64> {
+    double X[3];
+    double V[3];
+    P64 xr;
+    uint32_t id;
+};
+
+template <class M, int EPI>
+__device__ __forceinline__ void load_pstate(int i, int n, const StepArgs& a, const int* __restrict__ id,
+                                            const typename M::pos_t* __restrict__ xref, PState<M>& ps)
+{
+    constexpr bool start = EPI == EPI_START || EPI == EPI_FINISH_START;
+    ps.id = (uint32_t)__ldg(id + i);
+    if constexpr (EPI == EPI_FORCE) return;
+    if constexpr (!M::fp64) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            ps.V[d] = ((const float2*)a.v)[(size_t)d * n + i];
+            if constexpr (start) ps.X[d] = ((const long long*)a.x)[(size_t)d * n + i];
+        }
+    } else {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            ps.V[d] = ((const double*)a.v)[(size_t)d * n + i];
+            ps.X[d] = ((const double*)a.x)[(size_t)d * n + i];
+        }
+    }
+    if constexpr (start) ps.xr = xref[i];
+}
+
 // BAOAB update of particle i (unit mass, h = dt / 2) from its force.
 // FP32 mode: the unwrapped position is an int64 in units of L / 2^52 and the
 // velocity a two-float, so the update needs no FP64 instruction; each half
 // drift adds the nearest integer of h v 2^52 / L.  FP64 mode: doubles.
 template <class M, int EPI>
 __device__ __forceinline__ void integrate(int i, int n, const Geom& g, typename M::real fx, typename M::real fy,
-                                          typename M::real fz, const StepArgs& a, uint32_t pid, Status* st,
-                                          typename M::pos_t* __restrict__ pos_next,
-                                          const typename M::pos_t* __restrict__ xref)
+                                          typename M::real fz, const StepArgs& a, const PState<M>& ps, Status* st,
+                                          typename M::pos_t* __restrict__ pos_next)
 {
     constexpr bool start = EPI == EPI_START || EPI == EPI_FINISH_START;
     constexpr bool finish = EPI == EPI_FINISH || EPI == EPI_FINISH_START;
@@ -854,7 +953,7 @@ __device__ __forceinline__ void integrate(int i, int n, const Geom& g, typename 
         const float f3[3] = {fx, fy, fz};
         float xi[3] = {0.0f, 0.0f, 0.0f};
         if constexpr (start) {
-            const float3 z = langevin_normals(a.seed, (unsigned long long)(st->step_base + st->iter), pid);
+            const float3 z = langevin_normals(a.seed, (unsigned long long)(st->step_base + st->iter), ps.id);
             xi[0] = z.x;
             xi[1] = z.y;
             xi[2] = z.z;
@@ -862,12 +961,11 @@ __device__ __forceinline__ void integrate(int i, int n, const Geom& g, typename 
         int w[3] = {0, 0, 0};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const float2 vv = V[(size_t)d * n + i];
-            f2x v = {vv.x, vv.y};
+            f2x v = {ps.V[d].x, ps.V[d].y};
             const f2x hf = f2x_mulf(a.h, f3[d]);
             if constexpr (finish) v = f2x_add(v, hf);                             // B (closes the step)
             if constexpr (start) {
-                long long P = X[(size_t)d * n + i];
+                long long P = ps.X[d];
                 v = f2x_add(v, hf);                                                // B
                 P += f2x_to_ll(f2x_mul(v, a.hK[d]));                               // A
                 v = f2x_add(f2x_mul(v, a.c1f), f2x_mulf(a.c2f, xi[d]));            // O
@@ -881,9 +979,8 @@ __device__ __forceinline__ void integrate(int i, int n, const Geom& g, typename 
         if constexpr (start) {
             const int4 pn = make_int4(w[0], w[1], w[2], 0);
             pos_next[i] = pn;
-            const int4 pr = xref[i];
-            const float ux = (float)(pn.x - pr.x) * g.s32, uy = (float)(pn.y - pr.y) * g.s32,
-                        uz = (float)(pn.z - pr.z) * g.s32;
+            const float ux = (float)(pn.x - ps.xr.x) * g.s32, uy = (float)(pn.y - ps.xr.y) * g.s32,
+                        uz = (float)(pn.z - ps.xr.z) * g.s32;
             if (ux * ux + uy * uy + uz * uz > a.half_skin2) st->rebuild = 1;
         }
     } else {
@@ -894,15 +991,15 @@ __device__ __forceinline__ void integrate(int i, int n, const Geom& g, typename 
         double xs[3], vs[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            xs[d] = X[(size_t)d * n + i];
-            vs[d] = V[(size_t)d * n + i];
+            xs[d] = ps.X[d];
+            vs[d] = ps.V[d];
         }
         if constexpr (finish) {
 #pragma unroll
             for (int d = 0; d < 3; ++d) vs[d] += h * f3[d];
         }
         if constexpr (start) {
-            const double3 z = langevin_normals_d(a.seed, (unsigned long long)(st->step_base + st->iter), pid);
+            const double3 z = langevin_normals_d(a.seed, (unsigned long long)(st->step_base + st->iter), ps.id);
             const double zz[3] = {z.x, z.y, z.z};
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
@@ -921,11 +1018,10 @@ __device__ __forceinline__ void integrate(int i, int n, const Geom& g, typename 
         if constexpr (start) {
             const P64 pn = ModeF64::from_x(xs[0], xs[1], xs[2], g);
             pos_next[i] = pn;
-            const P64 pr = xref[i];
             float d2 = 0.0f;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                const float u = (float)(int)(ModeF64::hi32(pn, d) - ModeF64::hi32(pr, d)) * (float)g.s32d[d];
+                const float u = (float)(int)(ModeF64::hi32(pn, d) - ModeF64::hi32(ps.xr, d)) * (float)g.s32d[d];
                 d2 += u * u;
             }
             if (d2 > a.half_skin2) st->rebuild = 1;
@@ -933,20 +1029,6 @@ __device__ __forceinline__ void integrate(int i, int n, const Geom& g, typename 
     }
     if (bad) st->frozen = 1;
 }
-
-
-// Pass 2, one block per supercell.  The block's list entries are cut into
-// 4-entry chunks (rows are padded to a multiple of 4), the threads take
-// chunks in turn, each chunk's partial force goes to shared memory, and each
-// own particle then sums its chunks in order -- deterministic, no atomics.
-// If no staged particle has s_j != 0 or A_j != 0, no pair of the block can
-// have a well or window term and the block runs the soft-core-only loop.
-// Otherwise, per pair in the FP32 mode, the exact integer r^2 decides which
-// terms can be nonzero (core overlap r < r_r; the well, only if s_i s_j != 0;
-// the counting window, only if A_i + A_j != 0), and the arguments of the
-// steep well and of the window come from exact integer differences
-// r^2 - r_m^2 and r^2 - r_l^2.
-
 // Spare word of a staged position, holding s_j.
 __device__ __forceinline__ void put_s(int4& p, float s) { p.w = __float_as_int(s); }
 __device__ __forceinline__ void put_s(P64& p, double s) { p.w = (unsigned long long)__double_as_longlong(s); }
@@ -1005,6 +1087,21 @@ __device__ __forceinline__ void pair_f64(const P64& pi, double si, double Ai, co
     fz -= gr * dz;
 }
 
+
+// Pass 2, one block per cell group.  The block's list entries are cut into
+// 4-entry chunks (rows are padded to a multiple of 4); each thread takes an
+// equal contiguous run of chunks, so it meets few owners and adds its chunks
+// in registers.  A run's first and last owners may continue in the
+// neighbouring runs: their partial forces go to per-thread head and tail
+// slots, owners wholly inside a run are written directly, and each own
+// particle then adds its pieces in thread order -- deterministic, no atomics.
+// A chunk whose owner has s_i = 0, in a block where no staged particle has
+// A_j != 0, can have no well or window term and takes the soft-core-only
+// path.  Otherwise, per pair in the FP32 mode, the exact integer r^2 decides
+// which terms can be nonzero (core overlap r < r_r; the well, only if
+// s_i s_j != 0; the counting window, only if A_i + A_j != 0), and the
+// arguments of the steep well and of the window come from exact integer
+// differences r^2 - r_m^2 and r^2 - r_l^2.
 template <class M, int EPI>
 __global__ void __launch_bounds__(SC_TPB) k_force(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
                                                   SuperGrid G, SuperCaps cp, const uint16_t* __restrict__ nbr,
@@ -1020,24 +1117,26 @@ __global__ void __launch_bounds__(SC_TPB) k_force(int n, Geom g, Coef c, const t
     // halted(), which a thread of this launch changes only on the error path
     if (halted(st)) return;
     __shared__ SuperTab T;
+    __shared__ real hF[3][SC_TPB], tF[3][SC_TPB];
+    __shared__ int jf[SC_TPB], jl[SC_TPB];
     extern __shared__ __align__(16) unsigned char smem[];
     const int t = threadIdx.x;
     int p0, n_own, total;
-    load_supercell(blockIdx.x, g, G, T, p0, n_own, total);
+    load_group(blockIdx.x, g, G, T, p0, n_own, total);
+    PState<M> ps;
+    if (t < n_own) load_pstate<M, EPI>(p0 + t, n, a, id, xref, ps);
     const ForceLayout ly = force_layout(cp, sizeof(pos_t), sizeof(real));
     pos_t* spos = (pos_t*)smem;
     real* sAj = (real*)(smem + ly.sA);
     int* roff = (int*)(smem + ly.roff);
-    uint16_t* cown = (uint16_t*)(smem + ly.cown);
-    const int nchm = cp.seg / 4;
-    real* cpx = (real*)(smem + ly.cpart);
-    real* cpy = cpx + nchm;
-    real* cpz = cpy + nchm;
+    pos_t* opos = (pos_t*)(smem + ly.opos);
+    real* oA = (real*)(smem + ly.oA);
+    real* oF = (real*)(smem + ly.oF);  // [3][omax]
     struct PV {
         pos_t p;
         real2 sa;
     };
-    bool nz = false;
+    bool anyA = false;
     stage<PV>(
         T, total, [&](int j) { return PV{pos[j], sA[j]}; },
         [&](int m, const PV& v) {
@@ -1045,92 +1144,139 @@ __global__ void __launch_bounds__(SC_TPB) k_force(int n, Geom g, Coef c, const t
             put_s(q, v.sa.x);
             spos[m] = q;
             sAj[m] = v.sa.y;
-            nz |= (v.sa.x != (real)0) | (v.sa.y != (real)0);
+            anyA |= v.sa.y != (real)0;
         });
-    const bool general = __syncthreads_or(nz);
-    const int nch = own_rows(nnb, p0, n_own, roff, T.sw) >> 2;
-    for (int j = t; j < n_own; j += SC_TPB)
-        for (int q = roff[j] >> 2, qe = roff[j + 1] >> 2; q < qe; ++q) cown[q] = (uint16_t)j;
-    __syncthreads();
-    const uint2* L = reinterpret_cast<const uint2*>(nbr + (size_t)blockIdx.x * cp.seg);
-    if constexpr (!M::fp64) {
-        if (!general) {
-            // soft core only: g / r = K (r^2 - r_r^2), r^2 in units of (L / 2^32)^2
-            const float kc = c.Er4f * c.rr2invf * g.s32sq, bc = c.Er4f, rr2u = (float)c.rr2_fix;
-            for (int q = t; q < nch; q += SC_TPB) {
-                const int j = cown[q];
-                const int4 pi = __ldg(pos + p0 + j);
-                int h[4];
-                unpack4(__ldg(L + q), h);
-                float fx = 0.0f, fy = 0.0f, fz = 0.0f;
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int4 pj = spos[h[u]];
-                    const float dx = (float)(pi.x - pj.x), dy = (float)(pi.y - pj.y), dz = (float)(pi.z - pj.z);
-                    const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz));
-                    const float gr = r2 < rr2u ? __fmaf_rn(kc, r2, -bc) : 0.0f;
-                    fx = __fmaf_rn(-gr, dx, fx);
-                    fy = __fmaf_rn(-gr, dy, fy);
-                    fz = __fmaf_rn(-gr, dz, fz);
-                }
-                cpx[q] = fx * g.s32;
-                cpy[q] = fy * g.s32;
-                cpz[q] = fz * g.s32;
-            }
-        } else {
-            for (int q = t; q < nch; q += SC_TPB) {
-                const int j = cown[q];
-                const int4 pi = __ldg(pos + p0 + j);
-                const float2 sai = __ldg(sA + p0 + j);
-                int h[4];
-                unpack4(__ldg(L + q), h);
-                float fx = 0.0f, fy = 0.0f, fz = 0.0f;
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int4 pj = spos[h[u]];
-                    pair_f32(pi, sai.x, sai.y, pj, get_s(pj), sAj[h[u]], c, g, fx, fy, fz);
-                }
-                cpx[q] = fx;
-                cpy[q] = fy;
-                cpz[q] = fz;
-            }
-        }
-    } else {
-        for (int q = t; q < nch; q += SC_TPB) {
-            const int j = cown[q];
-            const P64 pi = pos[p0 + j];
-            const double2 sai = sA[p0 + j];
-            int h[4];
-            unpack4(__ldg(L + q), h);
-            double fx = 0.0, fy = 0.0, fz = 0.0;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const P64 pj = spos[h[u]];
-                pair_f64(pi, sai.x, sai.y, pj, get_s(pj), sAj[h[u]], c, g, fx, fy, fz);
-            }
-            cpx[q] = fx;
-            cpy[q] = fy;
-            cpz[q] = fz;
-        }
+    for (int j = t; j < n_own; j += SC_TPB) {
+        pos_t q = pos[p0 + j];
+        const real2 sa = sA[p0 + j];
+        put_s(q, sa.x);
+        opos[j] = q;
+        oA[j] = sa.y;
     }
+    anyA = __syncthreads_or(anyA);
+    const int nch = own_rows(nnb, p0, n_own, roff, T.sw) >> 2;
+    const uint2* L = reinterpret_cast<const uint2*>(nbr + (size_t)blockIdx.x * cp.seg);
+    const int per = (nch + SC_TPB - 1) / SC_TPB;
+    const int c0 = min(nch, t * per), c1 = min(nch, c0 + per);
+    int jfirst = -1, jlast = -1;
+    if (c0 < c1) {
+        // owner of chunk c0: the largest j with roff[j] <= 4 c0
+        int j = 0;
+        {
+            int hi = n_own - 1;
+            while (j < hi) {
+                const int mid = (j + hi + 1) >> 1;
+                if (roff[mid] <= 4 * c0) j = mid;
+                else hi = mid - 1;
+            }
+        }
+        jfirst = j;
+        int jend = roff[j + 1] >> 2;
+        pos_t pi = opos[j];
+        real si = get_s(pi), Ai = oA[j];
+        real fx = 0, fy = 0, fz = 0;
+#pragma unroll 4
+        for (int cc = c0; cc < c1; ++cc) {
+            const uint2 v = __ldg(L + cc);
+            if (cc >= jend) {
+                if (j == jfirst) {
+                    hF[0][t] = fx;
+                    hF[1][t] = fy;
+                    hF[2][t] = fz;
+                } else {
+                    oF[j] = fx;
+                    oF[cp.omax + j] = fy;
+                    oF[2 * cp.omax + j] = fz;
+                }
+                do {
+                    ++j;
+                    jend = roff[j + 1] >> 2;
+                } while (cc >= jend);
+                pi = opos[j];
+                si = get_s(pi);
+                Ai = oA[j];
+                fx = fy = fz = 0;
+            }
+            int h[4];
+            unpack4(v, h);
+            if constexpr (!M::fp64) {
+                if (!anyA && si == 0.0f) {
+                    // soft core only: g / r = K (r^2 - r_r^2), r^2 in units of (L / 2^32)^2
+                    const float kc = c.Er4f * c.rr2invf * g.s32sq, rr2u = (float)c.rr2_fix;
+                    float gx = 0.0f, gy = 0.0f, gz = 0.0f;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int4 pj = spos[h[u]];
+                        const float dx = (float)(pi.x - pj.x), dy = (float)(pi.y - pj.y), dz = (float)(pi.z - pj.z);
+                        const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz));
+                        const float gr = r2 < rr2u ? __fmaf_rn(kc, r2, -c.Er4f) : 0.0f;
+                        gx = __fmaf_rn(-gr, dx, gx);
+                        gy = __fmaf_rn(-gr, dy, gy);
+                        gz = __fmaf_rn(-gr, dz, gz);
+                    }
+                    fx = __fmaf_rn(gx, g.s32, fx);
+                    fy = __fmaf_rn(gy, g.s32, fy);
+                    fz = __fmaf_rn(gz, g.s32, fz);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int4 pj = spos[h[u]];
+                        pair_f32(pi, si, Ai, pj, get_s(pj), sAj[h[u]], c, g, fx, fy, fz);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const P64 pj = spos[h[u]];
+                    pair_f64(pi, si, Ai, pj, get_s(pj), sAj[h[u]], c, g, fx, fy, fz);
+                }
+            }
+        }
+        if (j == jfirst) {
+            hF[0][t] = fx;
+            hF[1][t] = fy;
+            hF[2][t] = fz;
+        } else {
+            tF[0][t] = fx;
+            tF[1][t] = fy;
+            tF[2][t] = fz;
+        }
+        jlast = j;
+    }
+    jf[t] = jfirst;
+    jl[t] = jlast;
     __syncthreads();
     for (int j = t; j < n_own; j += SC_TPB) {
-        real fx = 0, fy = 0, fz = 0;
-        for (int q = roff[j] >> 2, qe = roff[j + 1] >> 2; q < qe; ++q) {
-            fx += cpx[q];
-            fy += cpy[q];
-            fz += cpz[q];
+        const int cs = roff[j] >> 2, ce = roff[j + 1] >> 2;
+        real f[3] = {0, 0, 0};
+        if (cs < ce) {
+            const int ta = cs / per, tb = (ce - 1) / per;
+            if (ta == tb && jf[ta] != j && jl[ta] != j) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) f[d] = oF[d * cp.omax + j];
+            } else {
+                const bool head = jf[ta] == j;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) f[d] = head ? hF[d][ta] : tF[d][ta];
+                for (int k = ta + 1; k <= tb; ++k) {
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) f[d] += hF[d][k];
+                }
+            }
         }
         const int p = p0 + j;
+        PState<M> q;
+        if (j == t) q = ps;
+        else load_pstate<M, EPI>(p, n, a, id, xref, q);
         if constexpr (EPI == EPI_FORCE) {
             if (a.F_out) {
-                const int o = id[p];
-                a.F_out[3 * (size_t)o + 0] = (double)fx;
-                a.F_out[3 * (size_t)o + 1] = (double)fy;
-                a.F_out[3 * (size_t)o + 2] = (double)fz;
+                const size_t o = 3 * (size_t)q.id;
+                a.F_out[o + 0] = (double)f[0];
+                a.F_out[o + 1] = (double)f[1];
+                a.F_out[o + 2] = (double)f[2];
             }
         } else {
-            integrate<M, EPI>(p, n, g, fx, fy, fz, a, (uint32_t)id[p], st, pos_next, xref);
+            integrate<M, EPI>(p, n, g, f[0], f[1], f[2], a, q, st, pos_next);
         }
     }
 }
@@ -1139,7 +1285,7 @@ __global__ void __launch_bounds__(SC_TPB) k_force(int n, Geom g, Coef c, const t
 // Requested energies are held to 1e-9 relative, which needs the switching
 // factors to FP64 accuracy: the counts, s, s' and A are recomputed here in
 // FP64 from the exact fixed-point separations (these kernels run only when U
-// or W is asked for, never inside the step loop).  One block per supercell,
+// or W is asked for, never inside the step loop).  One block per cell group,
 // one thread per own particle.
 template <class M>
 __global__ void __launch_bounds__(SC_TPB) k_count_e(Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
@@ -1152,7 +1298,7 @@ __global__ void __launch_bounds__(SC_TPB) k_count_e(Geom g, Coef c, const typena
     __shared__ SuperTab T;
     extern __shared__ __align__(16) unsigned char smem[];
     int p0, n_own, total;
-    load_supercell(blockIdx.x, g, G, T, p0, n_own, total);
+    load_group(blockIdx.x, g, G, T, p0, n_own, total);
     const PassLayout ly = pass_layout(cp, sizeof(pos_t), 0);
     pos_t* spos = (pos_t*)smem;
     int* roff = (int*)(smem + ly.roff);
@@ -1183,7 +1329,7 @@ __global__ void __launch_bounds__(SC_TPB) k_chain_e(Geom g, Coef c, const typena
     __shared__ SuperTab T;
     extern __shared__ __align__(16) unsigned char smem[];
     int p0, n_own, total;
-    load_supercell(blockIdx.x, g, G, T, p0, n_own, total);
+    load_group(blockIdx.x, g, G, T, p0, n_own, total);
     const PassLayout ly = pass_layout(cp, sizeof(pos_t), sizeof(double));
     pos_t* spos = (pos_t*)smem;
     double* ss = (double*)(smem + ly.val);
@@ -1219,7 +1365,7 @@ __global__ void __launch_bounds__(SC_TPB) k_chain_e(Geom g, Coef c, const typena
     }
 }
 
-// Per-supercell partial sums of U = sum_{i<j} [V_r + s_i s_j V_a], W = sum_{i<j} -g r
+// Per-block partial sums of U = sum_{i<j} [V_r + s_i s_j V_a], W = sum_{i<j} -g r
 // and of the number of pairs with r < r_c, each pair seen from both ends (halves).
 template <class M>
 __global__ void __launch_bounds__(SC_TPB) k_energy(Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
@@ -1241,7 +1387,7 @@ __global__ void __launch_bounds__(SC_TPB) k_energy(Geom g, Coef c, const typenam
     long long pairs = 0;
     if (!halted(st)) {
         int p0, n_own, total;
-        load_supercell(blockIdx.x, g, G, T, p0, n_own, total);
+        load_group(blockIdx.x, g, G, T, p0, n_own, total);
         struct PS {
             pos_t p;
             double2 sa;
@@ -1412,7 +1558,7 @@ __global__ void __launch_bounds__(SC_TPB) k_store_nlist(Geom g, SuperGrid G, Sup
     extern __shared__ __align__(16) unsigned char smem[];
     int* roff = (int*)smem;
     int p0, n_own, total;
-    load_supercell(blockIdx.x, g, G, T, p0, n_own, total);
+    load_group(blockIdx.x, g, G, T, p0, n_own, total);
     own_rows(nnb, p0, n_own, roff, T.sw);
     const uint16_t* seg = nbr + (size_t)blockIdx.x * cp.seg;
     for (int j = threadIdx.x; j < n_own; j += SC_TPB) {
