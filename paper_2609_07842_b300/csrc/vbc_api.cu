@@ -99,6 +99,8 @@ struct vbc_system {
     int *cell_of = nullptr, *slot_of = nullptr, *order = nullptr;
     int *cell_count = nullptr, *cell_start = nullptr, *morton_rank = nullptr, *sc_org = nullptr;
     int* chunk_sum = nullptr;
+    int* wblk = nullptr;        // cell groups with window particles (k_count -> k_chain)
+    int chain_grid = 0;         // blocks of the chain-rule pass
     void *ds = nullptr, *sA = nullptr;
     Status* st = nullptr;
     Status* st_host = nullptr;  // pinned
@@ -320,7 +322,7 @@ void free_all(vbc_system* s)
     dfree(s->pos[0]); dfree(s->pos[1]); dfree(s->post); dfree(s->xref);
     dfree(s->nbr); dfree(s->scratch); dfree(s->nnb); dfree(s->cell_of); dfree(s->slot_of); dfree(s->order);
     dfree(s->cell_count); dfree(s->cell_start); dfree(s->morton_rank); dfree(s->sc_org);
-    dfree(s->chunk_sum);
+    dfree(s->chunk_sum); dfree(s->wblk);
     dfree(s->ds); dfree(s->sA); dfree(s->st); dfree(s->partial); dfree(s->ppairs); dfree(s->red);
     dfree(s->win); dfree(s->e_sd); dfree(s->e_A);
     if (s->st_host) cudaFreeHost(s->st_host);
@@ -416,13 +418,13 @@ int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window)
         Timed t(s, VBC_K_COUNT);
         k_count<M><<<s->nsc, SC_TPB, s->smem_count(), s->stream>>>(s->geom, s->coef, pos, s->grid(), s->caps(),
                                                                     s->nbr, s->nnb, s->id, (real*)s->ds,
-                                                                    (real2*)s->sA, out, s->st);
+                                                                    (real2*)s->sA, out, s->wblk, s->st);
     }
     {
         Timed t(s, VBC_K_CHAIN);
-        k_chain<M><<<s->nsc, SC_TPB, s->smem_chain(), s->stream>>>(s->geom, s->coef, pos, s->grid(), s->caps(),
-                                                                    s->nbr, s->nnb, (const real*)s->ds,
-                                                                    (real2*)s->sA, s->st);
+        k_chain<M><<<s->chain_grid, SC_TPB, s->smem_chain(), s->stream>>>(
+            s->geom, s->coef, pos, s->grid(), s->caps(), s->nbr, s->nnb, (const real*)s->ds, (real2*)s->sA, s->wblk,
+            s->nsc, s->st);
     }
     return check_launch(s, 2);
 }
@@ -541,6 +543,7 @@ int compute_impl(vbc_system* s, double* F_dev, double* n_dev, bool energy)
 {
     for (int attempt = 0;; ++attempt) {
         VBC_CUDA(cudaMemsetAsync(s->win, 0, sizeof(long long), s->stream));
+        VBC_CUDA(cudaMemsetAsync(&s->st->nwin_blocks, 0, sizeof(int), s->stream));
         VBC_TRY(enqueue_rebuild<M>(s));
         VBC_TRY(enqueue_count_chain<M>(s, n_dev, true));
         StepArgs a{};
@@ -896,6 +899,12 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
         cudaError_t e = cudaGetDevice(&s->device);
         if (e != cudaSuccess) return bail(fail(VBC_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e)));
     }
+    {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess || sms < 1)
+            sms = 148;
+        s->chain_grid = std::max(1, std::min(2 * sms, s->nsc));
+    }
     if (cfg->stream) {
         s->stream = (cudaStream_t)cfg->stream;
     } else {
@@ -929,6 +938,7 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     ALLOC(dalloc(s->morton_rank, (size_t)g.ncell));
     ALLOC(dalloc(s->sc_org, (size_t)s->nsc));
     ALLOC(dalloc(s->chunk_sum, (size_t)blocks_for(s->npad, SCAN_CHUNK)));
+    ALLOC(dalloc(s->wblk, (size_t)s->nsc));
     ALLOC(dalloc_bytes(s->ds, n * s->real_bytes()));
     ALLOC(dalloc_bytes(s->sA, n * 2 * s->real_bytes()));
     ALLOC(dalloc(s->st, 1));

@@ -703,7 +703,8 @@ __global__ void __launch_bounds__(SC_TPB) k_count(Geom g, Coef c, const typename
                                                   SuperGrid G, SuperCaps cp, const uint16_t* __restrict__ nbr,
                                                   const int* __restrict__ nnb, const int* __restrict__ id,
                                                   typename M::real* __restrict__ ds_out,
-                                                  typename M::real2* __restrict__ sA, CountOut out, Status* st)
+                                                  typename M::real2* __restrict__ sA, CountOut out,
+                                                  int* __restrict__ wblk, Status* st)
 {
     using pos_t = typename M::pos_t;
     using real = typename M::real;
@@ -711,7 +712,7 @@ __global__ void __launch_bounds__(SC_TPB) k_count(Geom g, Coef c, const typename
     if (blockIdx.x == 0 && threadIdx.x == 0) st->rebuild = 0;
     if (halted(st)) return;
     __shared__ SuperTab T;
-    __shared__ int s_nu;
+    __shared__ int s_nu, s_win;
     extern __shared__ __align__(16) unsigned char smem[];
     const int t = threadIdx.x;
     int p0, n_own, total;
@@ -720,7 +721,10 @@ __global__ void __launch_bounds__(SC_TPB) k_count(Geom g, Coef c, const typename
     pos_t* spos = (pos_t*)smem;
     int* roff = (int*)(smem + ly.roff);
     int* ulist = (int*)(smem + ly.plist);
-    if (t == 0) s_nu = 0;
+    if (t == 0) {
+        s_nu = 0;
+        s_win = 0;
+    }
     stage<pos_t>(T, total, [&](int j) { return pos[j]; }, [&](int m, const pos_t& v) { spos[m] = v; });
     own_rows(nnb, p0, n_own, roff, T.sw);
     const uint16_t* seg = nbr + (size_t)blockIdx.x * cp.seg;
@@ -795,86 +799,96 @@ __global__ void __launch_bounds__(SC_TPB) k_count(Geom g, Coef c, const typename
             ds_out[p] = ds;
             sA[p] = real2{s, (real)0};
             if (out.n_out) out.n_out[id[p]] = n_val;
-            if (out.in_window && ds != (real)0) atomicAdd((unsigned long long*)out.in_window, 1ull);
+            if (ds != (real)0) {
+                s_win = 1;
+                if (out.in_window) atomicAdd((unsigned long long*)out.in_window, 1ull);
+            }
         }
+    }
+    // groups with a window particle go on the list of the chain-rule pass
+    __syncthreads();
+    if (t == 0 && s_win) {
+        const int k = atomicAdd(&st->nwin_blocks, 1);
+        if (k < (int)gridDim.x) wblk[k] = blockIdx.x;
     }
 }
 
 // ================================================================ chain-rule pass
 // A_i = s'_i sum_j s_j V_a(r_ij) for particles inside the switching window
-// (s'_i != 0), one warp per such particle; blocks without one return
-// after one vote.
+// (s'_i != 0), one warp per such particle.  Only the cell groups that k_count
+// listed are visited; a fixed grid walks the list, so a step without window
+// particles costs one launch that reads one counter.
 template <class M>
 __global__ void __launch_bounds__(SC_TPB) k_chain(Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
                                                   SuperGrid G, SuperCaps cp, const uint16_t* __restrict__ nbr,
                                                   const int* __restrict__ nnb, const typename M::real* __restrict__ ds,
-                                                  typename M::real2* __restrict__ sA, const Status* st)
+                                                  typename M::real2* __restrict__ sA, const int* __restrict__ wblk,
+                                                  int nsc, const Status* st)
 {
     using pos_t = typename M::pos_t;
     using real = typename M::real;
     if (halted(st)) return;
+    const int nlist = min(st->nwin_blocks, nsc);
+    if ((int)blockIdx.x >= nlist) return;
     const int t = threadIdx.x;
-    {
-        const int q0 = __ldg(G.cell_start + OWN_CELLS * blockIdx.x),
-                  q1 = __ldg(G.cell_start + OWN_CELLS * blockIdx.x + OWN_CELLS);
-        bool any = false;
-        for (int p = q0 + t; p < q1; p += SC_TPB) any |= ds[p] != (real)0;
-        if (!__syncthreads_or(any)) return;
-    }
     __shared__ SuperTab T;
     __shared__ int s_nw;
     extern __shared__ __align__(16) unsigned char smem[];
-    int p0, n_own, total;
-    load_group(blockIdx.x, g, G, T, p0, n_own, total);
     const PassLayout ly = pass_layout(cp, sizeof(pos_t), sizeof(real));
     pos_t* spos = (pos_t*)smem;
     real* ss = (real*)(smem + ly.val);
     int* roff = (int*)(smem + ly.roff);
     int* wlist = (int*)(smem + ly.plist);
-    if (t == 0) s_nw = 0;
     const real* s_only = reinterpret_cast<const real*>(sA);  // s_j at even offsets (A is written here)
     struct PS {
         pos_t p;
         real s;
     };
-    stage<PS>(
-        T, total, [&](int j) { return PS{pos[j], s_only[2 * (size_t)j]}; },
-        [&](int m, const PS& v) {
-            spos[m] = v.p;
-            ss[m] = v.s;
-        });
-    own_rows(nnb, p0, n_own, roff, T.sw);
-    for (int j = t; j < n_own; j += SC_TPB)
-        if (ds[p0 + j] != (real)0) wlist[atomicAdd(&s_nw, 1)] = j;
-    __syncthreads();
-    const int nw = s_nw;
-    const int lane = t & 31;
-    const uint16_t* seg = nbr + (size_t)blockIdx.x * cp.seg;
-    for (int u = t >> 5; u < nw; u += SC_TPB / 32) {
-        const int j = wlist[u], p = p0 + j;
-        const int len = row_len(__ldg(nnb + p));
-        const pos_t pi = pos[p];
-        const uint16_t* row = seg + roff[j];
-        real acc = 0;
-        for (int e = lane; e < len; e += 32) {
-            const int m = __ldg(row + e);
-            if constexpr (M::fp64) {
-                const double r2 = r2_d<M>(pi, spos[m], g);
-                if (r2 > c.rr2 && r2 < c.ra2) acc += ss[m] * Va_d(sqrt(r2), c);
-            } else {
-                const unsigned long long r2i = r2_fix(pi, spos[m]);
-                if (r2i > c.rr2_fix && r2i < c.ra2_fix) {
-                    const float r2 = u64_to_float(r2i) * g.s32sq;
-                    const float r = sqrtf(r2);
-                    const float uu = s64_to_float((long long)r2i - (long long)c.rm2_fix) * c.s2hinv / (r + c.rmf);
-                    const float q = 1.0f - uu * uu;
-                    acc += ss[m] * (-c.Eaf * q * q);
+    for (int i = blockIdx.x; i < nlist; i += gridDim.x) {
+        const int b = wblk[i];
+        int p0, n_own, total;
+        load_group(b, g, G, T, p0, n_own, total);
+        if (t == 0) s_nw = 0;
+        stage<PS>(
+            T, total, [&](int j) { return PS{pos[j], s_only[2 * (size_t)j]}; },
+            [&](int m, const PS& v) {
+                spos[m] = v.p;
+                ss[m] = v.s;
+            });
+        own_rows(nnb, p0, n_own, roff, T.sw);
+        for (int j = t; j < n_own; j += SC_TPB)
+            if (ds[p0 + j] != (real)0) wlist[atomicAdd(&s_nw, 1)] = j;
+        __syncthreads();
+        const int nw = s_nw;
+        const int lane = t & 31;
+        const uint16_t* seg = nbr + (size_t)b * cp.seg;
+        for (int u = t >> 5; u < nw; u += SC_TPB / 32) {
+            const int j = wlist[u], p = p0 + j;
+            const int len = row_len(__ldg(nnb + p));
+            const pos_t pi = pos[p];
+            const uint16_t* row = seg + roff[j];
+            real acc = 0;
+            for (int e = lane; e < len; e += 32) {
+                const int m = __ldg(row + e);
+                if constexpr (M::fp64) {
+                    const double r2 = r2_d<M>(pi, spos[m], g);
+                    if (r2 > c.rr2 && r2 < c.ra2) acc += ss[m] * Va_d(sqrt(r2), c);
+                } else {
+                    const unsigned long long r2i = r2_fix(pi, spos[m]);
+                    if (r2i > c.rr2_fix && r2i < c.ra2_fix) {
+                        const float r2 = u64_to_float(r2i) * g.s32sq;
+                        const float r = sqrtf(r2);
+                        const float uu = s64_to_float((long long)r2i - (long long)c.rm2_fix) * c.s2hinv / (r + c.rmf);
+                        const float q = 1.0f - uu * uu;
+                        acc += ss[m] * (-c.Eaf * q * q);
+                    }
                 }
             }
-        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) sA[p].y = ds[p] * acc;
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) sA[p].y = ds[p] * acc;
+        }
+        __syncthreads();  // shared memory is reused by the next group
     }
 }
 
@@ -1575,10 +1589,12 @@ __global__ void __launch_bounds__(SC_TPB) k_store_nlist(Geom g, SuperGrid G, Sup
 
 // Opens one loop iteration: advances the device iteration counter (which
 // keys the Langevin noise) and, inside a CUDA graph, sets the conditional
-// that runs the rebuild body only when a rebuild is due.
+// that runs the rebuild body only when a rebuild is due; clears the list of
+// cell groups with window particles that the iteration's count fills.
 __global__ void k_gate(Status* st, cudaGraphConditionalHandle h, int in_graph)
 {
     st->iter += 1;
+    st->nwin_blocks = 0;
     if (in_graph) {
         const bool due = st->rebuild && !halted(st);
         if (due) st->graph_rebuild_runs += 1;
