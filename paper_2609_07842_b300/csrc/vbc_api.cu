@@ -99,7 +99,11 @@ struct vbc_system {
     int *cell_of = nullptr, *slot_of = nullptr, *order = nullptr;
     int *cell_count = nullptr, *cell_start = nullptr, *morton_rank = nullptr, *sc_org = nullptr;
     int* chunk_sum = nullptr;
-    int* wblk = nullptr;        // cell groups with window particles (k_count -> k_chain)
+    int* wpart = nullptr;       // [n][2] window particles and their groups (k_count -> k_chain)
+    int* stage_idx = nullptr;   // [nsc][smax] sorted index of each staged particle (list build)
+    int2* gmeta = nullptr;      // [nsc] staged particles and padded list entries per group
+    int* roff_g = nullptr;      // [n] row offset of each particle in its group's segment
+    int* near_k = nullptr;      // [n][NEAR_K] near neighbours kept for the saturation test
     int chain_grid = 0;         // blocks of the chain-rule pass
     void *ds = nullptr, *sA = nullptr;
     Status* st = nullptr;
@@ -138,11 +142,11 @@ struct vbc_system {
     size_t real_bytes() const { return prec == VBC_FP64 ? sizeof(double) : sizeof(float); }
     SuperGrid grid() const { return SuperGrid{morton_rank, sc_org, cell_start}; }
     SuperCaps caps() const { return SuperCaps{smax, omax, seg, cap}; }
+    GroupAux aux() const { return GroupAux{stage_idx, gmeta, roff_g, near_k}; }
     // dynamic shared memory of each kernel family
     size_t smem_nlist() const { return nlist_layout(caps(), pos_bytes()).total; }
     size_t smem_nlist_rel() const { return nlist_layout(caps(), sizeof(float4)).total; }
-    size_t smem_count() const { return pass_layout(caps(), pos_bytes(), 0).total; }
-    size_t smem_chain() const { return pass_layout(caps(), pos_bytes(), real_bytes()).total; }
+    size_t smem_count() const { return al16((size_t)omax * 4); }
     size_t smem_force() const { return force_layout(caps(), pos_bytes(), real_bytes()).total; }
     size_t smem_energy() const { return pass_layout(caps(), pos_bytes(), sizeof(double2)).total; }
     size_t smem_store() const { return al16((size_t)(omax + 1) * 4); }
@@ -322,7 +326,8 @@ void free_all(vbc_system* s)
     dfree(s->pos[0]); dfree(s->pos[1]); dfree(s->post); dfree(s->xref);
     dfree(s->nbr); dfree(s->scratch); dfree(s->nnb); dfree(s->cell_of); dfree(s->slot_of); dfree(s->order);
     dfree(s->cell_count); dfree(s->cell_start); dfree(s->morton_rank); dfree(s->sc_org);
-    dfree(s->chunk_sum); dfree(s->wblk);
+    dfree(s->chunk_sum); dfree(s->wpart); dfree(s->stage_idx); dfree(s->gmeta); dfree(s->roff_g);
+    dfree(s->near_k);
     dfree(s->ds); dfree(s->sA); dfree(s->st); dfree(s->partial); dfree(s->ppairs); dfree(s->red);
     dfree(s->win); dfree(s->e_sd); dfree(s->e_A);
     if (s->st_host) cudaFreeHost(s->st_host);
@@ -360,7 +365,6 @@ int configure_smem(vbc_system* s)
     VBC_TRY(set_smem(k_nlist<M, false>, s->smem_nlist()));
     if constexpr (!M::fp64) VBC_TRY(set_smem(k_nlist<M, true>, s->smem_nlist_rel()));
     VBC_TRY(set_smem(k_count<M>, s->smem_count()));
-    VBC_TRY(set_smem(k_chain<M>, s->smem_chain()));
     VBC_TRY(set_smem(k_force<M, EPI_FORCE>, s->smem_force()));
     VBC_TRY(set_smem(k_force<M, EPI_START>, s->smem_force()));
     VBC_TRY(set_smem(k_force<M, EPI_FINISH>, s->smem_force()));
@@ -397,12 +401,12 @@ int enqueue_rebuild(vbc_system* s)
     if constexpr (!M::fp64) {
         if (s->rel_lists) {
             k_nlist<M, true><<<s->nsc, SC_TPB, s->smem_nlist_rel(), s->stream>>>(
-                s->geom, pos, s->grid(), s->caps(), s->lp, s->scratch, s->nbr, s->nnb, s->st);
+                s->geom, pos, s->grid(), s->caps(), s->lp, s->scratch, s->nbr, s->nnb, s->aux(), s->st);
             return check_launch(s, REBUILD_KERNELS);
         }
     }
     k_nlist<M, false><<<s->nsc, SC_TPB, s->smem_nlist(), s->stream>>>(s->geom, pos, s->grid(), s->caps(), s->lp,
-                                                                       s->scratch, s->nbr, s->nnb, s->st);
+                                                                       s->scratch, s->nbr, s->nnb, s->aux(), s->st);
     return check_launch(s, REBUILD_KERNELS);
 }
 
@@ -417,14 +421,14 @@ int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window)
     {
         Timed t(s, VBC_K_COUNT);
         k_count<M><<<s->nsc, SC_TPB, s->smem_count(), s->stream>>>(s->geom, s->coef, pos, s->grid(), s->caps(),
-                                                                    s->nbr, s->nnb, s->id, (real*)s->ds,
-                                                                    (real2*)s->sA, out, s->wblk, s->st);
+                                                                    s->aux(), s->nbr, s->nnb, s->id, (real*)s->ds,
+                                                                    (real2*)s->sA, out, s->wpart, s->st);
     }
     {
         Timed t(s, VBC_K_CHAIN);
-        k_chain<M><<<s->chain_grid, SC_TPB, s->smem_chain(), s->stream>>>(
-            s->geom, s->coef, pos, s->grid(), s->caps(), s->nbr, s->nnb, (const real*)s->ds, (real2*)s->sA, s->wblk,
-            s->nsc, s->st);
+        k_chain<M><<<s->chain_grid, SC_TPB, 0, s->stream>>>(s->geom, s->coef, pos, s->caps(), s->aux(), s->nbr,
+                                                            s->nnb, (const real*)s->ds, (real2*)s->sA, s->wpart,
+                                                            s->st);
     }
     return check_launch(s, 2);
 }
@@ -441,7 +445,7 @@ int enqueue_force(vbc_system* s, const StepArgs& a)
         Timed t(s, VBC_K_FORCE);
         k_force<M, EPI><<<s->nsc, SC_TPB, s->smem_force(), s->stream>>>(
             n, s->geom, s->coef, pos, s->grid(), s->caps(), s->nbr, s->nnb, s->id, (const real2*)s->sA, pos_next,
-            (const pos_t*)s->xref, a, s->st);
+            (const pos_t*)s->xref, s->aux(), a, s->st);
     }
     VBC_TRY(check_launch(s));
     if (EPI == EPI_START || EPI == EPI_FINISH_START) s->cur ^= 1;
@@ -506,6 +510,8 @@ int grow(vbc_system* s)
             if (smax > MAX_STAGE)
                 return fail(VBC_ERR_UNSTABLE, "a cell group's neighbourhood holds %d particles, above the limit %d",
                             h.max_stage, MAX_STAGE);
+            dfree(s->stage_idx);
+            VBC_TRY(dalloc(s->stage_idx, (size_t)s->nsc * smax));
             s->smax = smax;
         }
         if (h.max_own > s->omax) {
@@ -543,7 +549,7 @@ int compute_impl(vbc_system* s, double* F_dev, double* n_dev, bool energy)
 {
     for (int attempt = 0;; ++attempt) {
         VBC_CUDA(cudaMemsetAsync(s->win, 0, sizeof(long long), s->stream));
-        VBC_CUDA(cudaMemsetAsync(&s->st->nwin_blocks, 0, sizeof(int), s->stream));
+        VBC_CUDA(cudaMemsetAsync(&s->st->nwin, 0, sizeof(int), s->stream));
         VBC_TRY(enqueue_rebuild<M>(s));
         VBC_TRY(enqueue_count_chain<M>(s, n_dev, true));
         StepArgs a{};
@@ -793,6 +799,10 @@ int trim_capacities(vbc_system* s)
         dfree(s->scratch);
         VBC_TRY(dalloc(s->scratch, (size_t)cap * (size_t)s->n));
     }
+    if (smax != s->smax) {
+        dfree(s->stage_idx);
+        VBC_TRY(dalloc(s->stage_idx, (size_t)s->nsc * smax));
+    }
     s->smax = smax;
     s->omax = omax;
     s->seg = seg;
@@ -938,7 +948,11 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     ALLOC(dalloc(s->morton_rank, (size_t)g.ncell));
     ALLOC(dalloc(s->sc_org, (size_t)s->nsc));
     ALLOC(dalloc(s->chunk_sum, (size_t)blocks_for(s->npad, SCAN_CHUNK)));
-    ALLOC(dalloc(s->wblk, (size_t)s->nsc));
+    ALLOC(dalloc(s->wpart, 2 * n));
+    ALLOC(dalloc(s->stage_idx, (size_t)s->nsc * s->smax));
+    ALLOC(dalloc(s->gmeta, (size_t)s->nsc));
+    ALLOC(dalloc(s->roff_g, n));
+    ALLOC(dalloc(s->near_k, (size_t)NEAR_K * n));
     ALLOC(dalloc_bytes(s->ds, n * s->real_bytes()));
     ALLOC(dalloc_bytes(s->sA, n * 2 * s->real_bytes()));
     ALLOC(dalloc(s->st, 1));

@@ -84,7 +84,7 @@ struct Status {
     long long iter;     // loop iteration now running (advanced by k_gate)
     long long step_base;// noise counter of iteration 0 of the current call
     long long graph_rebuild_runs;  // rebuild bodies a graph conditional executed
-    int nwin_blocks;    // cell groups with a window particle at the last count (k_count)
+    int nwin;           // window particles listed by the last count (k_count)
     int pad1;
 };
 

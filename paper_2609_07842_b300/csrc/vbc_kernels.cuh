@@ -263,6 +263,15 @@ struct SuperCaps {
     int cap;   // list entries of one particle (multiple of 8)
 };
 
+// Tables the list build leaves for the passes.
+constexpr int NEAR_K = 8;  // near neighbours kept per particle for the saturation test
+struct GroupAux {
+    int* stage_idx;  // [groups][smax] sorted index of each staged particle
+    int2* meta;      // [groups] (staged particles, padded list entries)
+    int* roff;       // [n] row offset of each particle in its group's list segment
+    int* near;       // [n][NEAR_K] sorted indices of up to NEAR_K near neighbours, -1 for none
+};
+
 struct SuperTab {
     int base[SCELLS];             // sorted index of each staged cell's first particle
     int off[SCELLS_P2 + 1];       // staging offset of each staged cell; total from SCELLS on
@@ -485,20 +494,18 @@ __host__ __device__ inline PassLayout pass_layout(const SuperCaps& cp, size_t po
 }
 
 // k_force: staged positions (with s_j in the spare word) and A_j, row
-// offsets, the owner of each 4-entry chunk, the own particles' positions and
-// A, and the forces of owners whose chunks one thread covered completely.
+// offsets, the staging index of each own particle, and the forces of owners
+// whose chunks one thread covered completely.
 struct ForceLayout {
-    size_t sA, roff, cown, opos, oA, oF, total;
+    size_t sA, roff, ownm, oF, total;
 };
 __host__ __device__ inline ForceLayout force_layout(const SuperCaps& cp, size_t pos_bytes, size_t real_bytes)
 {
     ForceLayout l{};
     l.sA = al16((size_t)cp.smax * pos_bytes);
     l.roff = l.sA + al16((size_t)cp.smax * real_bytes);
-    l.cown = l.roff + al16((size_t)(cp.omax + 1) * 4);
-    l.opos = l.cown + al16((size_t)cp.seg / 4 * 2);
-    l.oA = l.opos + al16((size_t)cp.omax * pos_bytes);
-    l.oF = l.oA + al16((size_t)cp.omax * real_bytes);
+    l.ownm = l.roff + al16((size_t)(cp.omax + 1) * 4);
+    l.oF = l.ownm + al16((size_t)cp.omax * 2);
     l.total = l.oF + al16((size_t)3 * cp.omax * real_bytes);
     return l;
 }
@@ -512,7 +519,8 @@ __host__ __device__ inline ForceLayout force_layout(const SuperCaps& cp, size_t 
 template <class M, bool REL>
 __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_t* __restrict__ pos, SuperGrid G,
                                                   SuperCaps cp, ListParams lp, uint16_t* __restrict__ scratch,
-                                                  uint16_t* __restrict__ nbr, int* __restrict__ nnb, Status* st)
+                                                  uint16_t* __restrict__ nbr, int* __restrict__ nnb, GroupAux aux,
+                                                  Status* st)
 {
     using pos_t = typename M::pos_t;
     using spos_t = typename std::conditional<REL, float4, pos_t>::type;
@@ -559,6 +567,10 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
     } else {
         stage<pos_t>(T, total, [&](int j) { return pos[j]; }, [&](int m, const pos_t& v) { spos[m] = v; });
     }
+    {
+        int* sidx = aux.stage_idx + (size_t)blockIdx.x * cp.smax;
+        for (int m = t; m < total; m += SC_TPB) sidx[m] = staged_index(T, m);
+    }
     __syncthreads();
     int mx = 0;
     long long sum = 0;
@@ -589,6 +601,15 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
         const int len = nn + nf;
         nnb[p] = nn | (nf << 16);
         rnn[j] = nn | (nf << 16);
+        {
+            // up to NEAR_K near neighbours as sorted indices, for the saturation test
+            int q[NEAR_K];
+#pragma unroll
+            for (int k = 0; k < NEAR_K; ++k) q[k] = k < nn && k < cp.cap ? staged_index(T, row[k]) : -1;
+            int4* nv = reinterpret_cast<int4*>(aux.near) + 2 * (size_t)p;
+            nv[0] = make_int4(q[0], q[1], q[2], q[3]);
+            nv[1] = make_int4(q[4], q[5], q[6], q[7]);
+        }
         roff[j] = pad4(len);
         over |= len > cp.cap;
         mx = max(mx, len);
@@ -616,7 +637,11 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
     }
     if (any_over) return;
     const int tot = scan_in_place(roff, n_own, T.sw);
-    if (t == 0) atomicMax(&st->max_seg, tot);
+    for (int j = t; j < n_own; j += SC_TPB) aux.roff[p0 + j] = roff[j];
+    if (t == 0) {
+        atomicMax(&st->max_seg, tot);
+        aux.meta[blockIdx.x] = make_int2(total, tot);
+    }
     if (tot > cp.seg) {
         if (t == 0) {
             st->stage_overflow = 1;
@@ -654,13 +679,15 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
 // threshold test t = n - (f - delta) is taken in the same fixed point, so
 // s_i and s'_i carry only the error of the window terms, and the integer sums
 // do not depend on the order of the terms.
-// Saturation: when the near entries alone hold at least ceil(f - delta + 1)
-// neighbours with r <= r_l, then n_i >= f - delta + 1 whatever the other
-// entries add, so s_i = s'_i = 0 exactly and nothing else is needed (unless
-// the counts themselves are requested).  Each thread first tests its own
-// particles for saturation over their near entries; the block then hands the
-// unsaturated ones, one at a time, to whole warps that walk the full row with
-// one lane per entry.
+// Saturation: when up to NEAR_K near neighbours kept by the list build
+// already hold at least ceil(f - delta + 1) neighbours with r <= r_l, then
+// n_i >= f - delta + 1 whatever the other entries add, so s_i = s'_i = 0
+// exactly and nothing else is needed (unless the counts themselves are
+// requested).  One block per cell group: each thread tests its own particles
+// for saturation with direct loads of those few neighbours; the block then
+// hands the unsaturated ones, one at a time, to whole warps that walk the
+// full row with one lane per entry, reading neighbours through the group's
+// staged-index table.  No shared-memory staging is needed.
 struct CountOut {
     double* n_out;         // counts in caller order, or null
     long long* in_window;  // counter of window particles, or null
@@ -700,53 +727,47 @@ __device__ __forceinline__ double r2_d(const typename M::pos_t& a, const typenam
 
 template <class M>
 __global__ void __launch_bounds__(SC_TPB) k_count(Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
-                                                  SuperGrid G, SuperCaps cp, const uint16_t* __restrict__ nbr,
-                                                  const int* __restrict__ nnb, const int* __restrict__ id,
-                                                  typename M::real* __restrict__ ds_out,
+                                                  SuperGrid G, SuperCaps cp, GroupAux aux,
+                                                  const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
+                                                  const int* __restrict__ id, typename M::real* __restrict__ ds_out,
                                                   typename M::real2* __restrict__ sA, CountOut out,
-                                                  int* __restrict__ wblk, Status* st)
+                                                  int* __restrict__ wpart, Status* st)
 {
     using pos_t = typename M::pos_t;
     using real = typename M::real;
     using real2 = typename M::real2;
     if (blockIdx.x == 0 && threadIdx.x == 0) st->rebuild = 0;
     if (halted(st)) return;
-    __shared__ SuperTab T;
-    __shared__ int s_nu, s_win;
+    __shared__ int s_nu;
     extern __shared__ __align__(16) unsigned char smem[];
-    const int t = threadIdx.x;
-    int p0, n_own, total;
-    load_group(blockIdx.x, g, G, T, p0, n_own, total);
-    const PassLayout ly = pass_layout(cp, sizeof(pos_t), 0);
-    pos_t* spos = (pos_t*)smem;
-    int* roff = (int*)(smem + ly.roff);
-    int* ulist = (int*)(smem + ly.plist);
-    if (t == 0) {
-        s_nu = 0;
-        s_win = 0;
-    }
-    stage<pos_t>(T, total, [&](int j) { return pos[j]; }, [&](int m, const pos_t& v) { spos[m] = v; });
-    own_rows(nnb, p0, n_own, roff, T.sw);
-    const uint16_t* seg = nbr + (size_t)blockIdx.x * cp.seg;
+    int* ulist = (int*)smem;  // [omax] unsaturated own particles
+    const int t = threadIdx.x, b = blockIdx.x;
+    const int p0 = __ldg(G.cell_start + OWN_CELLS * b);
+    const int n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
+    if (t == 0) s_nu = 0;
+    __syncthreads();
 
-    // saturation test over the near entries
+    // saturation test over the kept near neighbours
     for (int j = t; j < n_own; j += SC_TPB) {
         const int p = p0 + j;
-        const int nn = __ldg(nnb + p) & 0xffff;
-        const pos_t pi = pos[p];
-        const uint2* row = reinterpret_cast<const uint2*>(seg + roff[j]);
         long long full = 0;
-        for (int q = 0; q < nn; q += 4) {
-            int h[4];
-            unpack4(__ldg(row + (q >> 2)), h);
+        if (!out.n_out) {
+            const pos_t pi = pos[p];
+            const int4* nv = reinterpret_cast<const int4*>(aux.near) + 2 * (size_t)p;
+            const int4 a0 = __ldg(nv), a1 = __ldg(nv + 1);
+            const int q[NEAR_K] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            pos_t pj[NEAR_K];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (q + u >= nn) break;
-                if constexpr (M::fp64) full += r2_d<M>(pi, spos[h[u]], g) <= c.rl2;
-                else full += r2_fix(pi, spos[h[u]]) <= c.rl2_fix;
+            for (int k = 0; k < NEAR_K; ++k)
+                if (q[k] >= 0) pj[k] = pos[q[k]];
+#pragma unroll
+            for (int k = 0; k < NEAR_K; ++k) {
+                if (q[k] < 0) continue;
+                if constexpr (M::fp64) full += r2_d<M>(pi, pj[k], g) <= c.rl2;
+                else full += r2_fix(pi, pj[k]) <= c.rl2_fix;
             }
         }
-        if (full >= c.sat_full && !out.n_out) {
+        if (!out.n_out && full >= c.sat_full) {
             ds_out[p] = (real)0;
             sA[p] = real2{(real)0, (real)0};
         } else {
@@ -758,17 +779,19 @@ __global__ void __launch_bounds__(SC_TPB) k_count(Geom g, Coef c, const typename
     // unsaturated particles: one warp each, one lane per entry
     const int nu = s_nu;
     const int lane = t & 31;
+    const uint16_t* seg = nbr + (size_t)b * cp.seg;
+    const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
     for (int u = t >> 5; u < nu; u += SC_TPB / 32) {
         const int j = ulist[u], p = p0 + j;
         const int len = row_len(__ldg(nnb + p));
         const pos_t pi = pos[p];
-        const uint16_t* row = seg + roff[j];
+        const uint16_t* row = seg + __ldg(aux.roff + p);
         real s, ds;
         double n_val;
         if constexpr (M::fp64) {
             double acc = 0.0;
             for (int e = lane; e < len; e += 32) {
-                const double r2 = r2_d<M>(pi, spos[__ldg(row + e)], g);
+                const double r2 = r2_d<M>(pi, pos[__ldg(sidx + __ldg(row + e))], g);
                 if (r2 < c.rh2) acc += r2 <= c.rl2 ? 1.0 : omega_d(sqrt(r2), c.r_l, c.r_h);
             }
 #pragma unroll
@@ -780,7 +803,7 @@ __global__ void __launch_bounds__(SC_TPB) k_count(Geom g, Coef c, const typename
             long long full = 0;
             unsigned long long q = 0;
             for (int e = lane; e < len; e += 32) {
-                const unsigned long long r2 = r2_fix(pi, spos[__ldg(row + e)]);
+                const unsigned long long r2 = r2_fix(pi, pos[__ldg(sidx + __ldg(row + e))]);
                 if (r2 < c.rh2_fix) {
                     if (r2 <= c.rl2_fix) ++full;
                     else q += window_weight_fix31(r2, r2 - c.rl2_fix, c.rl_s, c.w_s);
@@ -793,102 +816,69 @@ __global__ void __launch_bounds__(SC_TPB) k_count(Geom g, Coef c, const typename
             }
             const long long Tf = (full - c.fd_int) * 2147483648LL + (long long)q - c.fd_frac_fix;
             switch_from_fix(Tf, s, ds);
-            n_val = (double)full + (double)q * 4.656612873077393e-10;
+            n_val = 0.0;
+            if (out.n_out) n_val = (double)full + (double)q * 4.656612873077393e-10;
         }
         if (lane == 0) {
             ds_out[p] = ds;
             sA[p] = real2{s, (real)0};
             if (out.n_out) out.n_out[id[p]] = n_val;
             if (ds != (real)0) {
-                s_win = 1;
+                // the chain-rule pass visits the window particles listed here
+                const int k = atomicAdd(&st->nwin, 1);
+                wpart[2 * k] = p;
+                wpart[2 * k + 1] = b;
                 if (out.in_window) atomicAdd((unsigned long long*)out.in_window, 1ull);
             }
         }
     }
-    // groups with a window particle go on the list of the chain-rule pass
-    __syncthreads();
-    if (t == 0 && s_win) {
-        const int k = atomicAdd(&st->nwin_blocks, 1);
-        if (k < (int)gridDim.x) wblk[k] = blockIdx.x;
-    }
 }
 
 // ================================================================ chain-rule pass
-// A_i = s'_i sum_j s_j V_a(r_ij) for particles inside the switching window
-// (s'_i != 0), one warp per such particle.  Only the cell groups that k_count
-// listed are visited; a fixed grid walks the list, so a step without window
-// particles costs one launch that reads one counter.
+// A_i = s'_i sum_j s_j V_a(r_ij) for the particles inside the switching
+// window (s'_i != 0) that k_count listed, one warp per particle, neighbours
+// read through their group's staged-index table.  A fixed grid walks the
+// list, so a step without window particles costs one launch that reads one
+// counter.
 template <class M>
 __global__ void __launch_bounds__(SC_TPB) k_chain(Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
-                                                  SuperGrid G, SuperCaps cp, const uint16_t* __restrict__ nbr,
+                                                  SuperCaps cp, GroupAux aux, const uint16_t* __restrict__ nbr,
                                                   const int* __restrict__ nnb, const typename M::real* __restrict__ ds,
-                                                  typename M::real2* __restrict__ sA, const int* __restrict__ wblk,
-                                                  int nsc, const Status* st)
+                                                  typename M::real2* __restrict__ sA, const int* __restrict__ wpart,
+                                                  const Status* st)
 {
     using pos_t = typename M::pos_t;
     using real = typename M::real;
     if (halted(st)) return;
-    const int nlist = min(st->nwin_blocks, nsc);
-    if ((int)blockIdx.x >= nlist) return;
-    const int t = threadIdx.x;
-    __shared__ SuperTab T;
-    __shared__ int s_nw;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const PassLayout ly = pass_layout(cp, sizeof(pos_t), sizeof(real));
-    pos_t* spos = (pos_t*)smem;
-    real* ss = (real*)(smem + ly.val);
-    int* roff = (int*)(smem + ly.roff);
-    int* wlist = (int*)(smem + ly.plist);
+    const int nw = st->nwin;
+    const int lane = threadIdx.x & 31;
     const real* s_only = reinterpret_cast<const real*>(sA);  // s_j at even offsets (A is written here)
-    struct PS {
-        pos_t p;
-        real s;
-    };
-    for (int i = blockIdx.x; i < nlist; i += gridDim.x) {
-        const int b = wblk[i];
-        int p0, n_own, total;
-        load_group(b, g, G, T, p0, n_own, total);
-        if (t == 0) s_nw = 0;
-        stage<PS>(
-            T, total, [&](int j) { return PS{pos[j], s_only[2 * (size_t)j]}; },
-            [&](int m, const PS& v) {
-                spos[m] = v.p;
-                ss[m] = v.s;
-            });
-        own_rows(nnb, p0, n_own, roff, T.sw);
-        for (int j = t; j < n_own; j += SC_TPB)
-            if (ds[p0 + j] != (real)0) wlist[atomicAdd(&s_nw, 1)] = j;
-        __syncthreads();
-        const int nw = s_nw;
-        const int lane = t & 31;
-        const uint16_t* seg = nbr + (size_t)b * cp.seg;
-        for (int u = t >> 5; u < nw; u += SC_TPB / 32) {
-            const int j = wlist[u], p = p0 + j;
-            const int len = row_len(__ldg(nnb + p));
-            const pos_t pi = pos[p];
-            const uint16_t* row = seg + roff[j];
-            real acc = 0;
-            for (int e = lane; e < len; e += 32) {
-                const int m = __ldg(row + e);
-                if constexpr (M::fp64) {
-                    const double r2 = r2_d<M>(pi, spos[m], g);
-                    if (r2 > c.rr2 && r2 < c.ra2) acc += ss[m] * Va_d(sqrt(r2), c);
-                } else {
-                    const unsigned long long r2i = r2_fix(pi, spos[m]);
-                    if (r2i > c.rr2_fix && r2i < c.ra2_fix) {
-                        const float r2 = u64_to_float(r2i) * g.s32sq;
-                        const float r = sqrtf(r2);
-                        const float uu = s64_to_float((long long)r2i - (long long)c.rm2_fix) * c.s2hinv / (r + c.rmf);
-                        const float q = 1.0f - uu * uu;
-                        acc += ss[m] * (-c.Eaf * q * q);
-                    }
+    for (int k = (int)((blockIdx.x * SC_TPB + threadIdx.x) >> 5); k < nw; k += (int)((gridDim.x * SC_TPB) >> 5)) {
+        const int p = wpart[2 * k], b = wpart[2 * k + 1];
+        const int len = row_len(__ldg(nnb + p));
+        const pos_t pi = pos[p];
+        const uint16_t* row = nbr + (size_t)b * cp.seg + __ldg(aux.roff + p);
+        const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
+        real acc = 0;
+        for (int e = lane; e < len; e += 32) {
+            const int jj = __ldg(sidx + __ldg(row + e));
+            if constexpr (M::fp64) {
+                const double r2 = r2_d<M>(pi, pos[jj], g);
+                if (r2 > c.rr2 && r2 < c.ra2) acc += s_only[2 * (size_t)jj] * Va_d(sqrt(r2), c);
+            } else {
+                const unsigned long long r2i = r2_fix(pi, pos[jj]);
+                if (r2i > c.rr2_fix && r2i < c.ra2_fix) {
+                    const float r2 = u64_to_float(r2i) * g.s32sq;
+                    const float r = sqrtf(r2);
+                    const float uu = s64_to_float((long long)r2i - (long long)c.rm2_fix) * c.s2hinv / (r + c.rmf);
+                    const float q = 1.0f - uu * uu;
+                    acc += s_only[2 * (size_t)jj] * (-c.Eaf * q * q);
                 }
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) sA[p].y = ds[p] * acc;
         }
-        __syncthreads();  // shared memory is reused by the next group
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) sA[p].y = ds[p] * acc;
     }
 }
 
@@ -1102,7 +1092,8 @@ __device__ __forceinline__ void pair_f64(const P64& pi, double si, double Ai, co
 }
 
 
-// Pass 2, one block per cell group.  The block's list entries are cut into
+// Pass 2, one block per cell group.  The block stages its neighbourhood
+// through the table of sorted indices the list build left.  Its list entries are cut into
 // 4-entry chunks (rows are padded to a multiple of 4); each thread takes an
 // equal contiguous run of chunks, so it meets few owners and adds its chunks
 // in registers.  A run's first and last owners may continue in the
@@ -1122,7 +1113,8 @@ __global__ void __launch_bounds__(SC_TPB) k_force(int n, Geom g, Coef c, const t
                                                   const int* __restrict__ nnb, const int* __restrict__ id,
                                                   const typename M::real2* __restrict__ sA,
                                                   typename M::pos_t* __restrict__ pos_next,
-                                                  const typename M::pos_t* __restrict__ xref, StepArgs a, Status* st)
+                                                  const typename M::pos_t* __restrict__ xref, GroupAux aux, StepArgs a,
+                                                  Status* st)
 {
     using pos_t = typename M::pos_t;
     using real = typename M::real;
@@ -1130,46 +1122,58 @@ __global__ void __launch_bounds__(SC_TPB) k_force(int n, Geom g, Coef c, const t
     // k_force raises `frozen` and `rebuild` itself; it tests `frozen` only through
     // halted(), which a thread of this launch changes only on the error path
     if (halted(st)) return;
-    __shared__ SuperTab T;
     __shared__ real hF[3][SC_TPB], tF[3][SC_TPB];
     __shared__ int jf[SC_TPB], jl[SC_TPB];
     extern __shared__ __align__(16) unsigned char smem[];
-    const int t = threadIdx.x;
-    int p0, n_own, total;
-    load_group(blockIdx.x, g, G, T, p0, n_own, total);
+    const int t = threadIdx.x, b = blockIdx.x;
+    const int p0 = __ldg(G.cell_start + OWN_CELLS * b);
+    const int n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
+    const int2 meta = __ldg(aux.meta + b);
+    const int total = meta.x;
     PState<M> ps;
     if (t < n_own) load_pstate<M, EPI>(p0 + t, n, a, id, xref, ps);
     const ForceLayout ly = force_layout(cp, sizeof(pos_t), sizeof(real));
     pos_t* spos = (pos_t*)smem;
     real* sAj = (real*)(smem + ly.sA);
     int* roff = (int*)(smem + ly.roff);
-    pos_t* opos = (pos_t*)(smem + ly.opos);
-    real* oA = (real*)(smem + ly.oA);
+    uint16_t* ownm = (uint16_t*)(smem + ly.ownm);
     real* oF = (real*)(smem + ly.oF);  // [3][omax]
     struct PV {
         pos_t p;
         real2 sa;
     };
     bool anyA = false;
-    stage<PV>(
-        T, total, [&](int j) { return PV{pos[j], sA[j]}; },
-        [&](int m, const PV& v) {
-            pos_t q = v.p;
-            put_s(q, v.sa.x);
-            spos[m] = q;
-            sAj[m] = v.sa.y;
-            anyA |= v.sa.y != (real)0;
-        });
-    for (int j = t; j < n_own; j += SC_TPB) {
-        pos_t q = pos[p0 + j];
-        const real2 sa = sA[p0 + j];
-        put_s(q, sa.x);
-        opos[j] = q;
-        oA[j] = sa.y;
+    {
+        // staging through the group's table of sorted indices, B loads in flight
+        constexpr int B = 4;
+        const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
+        for (int m0 = t; m0 < total; m0 += SC_TPB * B) {
+            int jj[B];
+#pragma unroll
+            for (int u = 0; u < B; ++u) jj[u] = m0 + u * SC_TPB < total ? __ldg(sidx + m0 + u * SC_TPB) : -1;
+            PV v[B];
+#pragma unroll
+            for (int u = 0; u < B; ++u)
+                if (jj[u] >= 0) v[u] = PV{pos[jj[u]], sA[jj[u]]};
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                if (jj[u] < 0) continue;
+                const int m = m0 + u * SC_TPB;
+                pos_t q = v[u].p;
+                put_s(q, v[u].sa.x);
+                spos[m] = q;
+                sAj[m] = v[u].sa.y;
+                anyA |= v[u].sa.y != (real)0;
+                // own particles are staged too (twice on very small grids: either copy will do)
+                if (jj[u] >= p0 && jj[u] < p0 + n_own) ownm[jj[u] - p0] = (uint16_t)m;
+            }
+        }
     }
+    for (int j = t; j < n_own; j += SC_TPB) roff[j] = __ldg(aux.roff + p0 + j);
+    if (t == 0) roff[n_own] = meta.y;
     anyA = __syncthreads_or(anyA);
-    const int nch = own_rows(nnb, p0, n_own, roff, T.sw) >> 2;
-    const uint2* L = reinterpret_cast<const uint2*>(nbr + (size_t)blockIdx.x * cp.seg);
+    const int nch = meta.y >> 2;
+    const uint2* L = reinterpret_cast<const uint2*>(nbr + (size_t)b * cp.seg);
     const int per = (nch + SC_TPB - 1) / SC_TPB;
     const int c0 = min(nch, t * per), c1 = min(nch, c0 + per);
     int jfirst = -1, jlast = -1;
@@ -1186,8 +1190,8 @@ __global__ void __launch_bounds__(SC_TPB) k_force(int n, Geom g, Coef c, const t
         }
         jfirst = j;
         int jend = roff[j + 1] >> 2;
-        pos_t pi = opos[j];
-        real si = get_s(pi), Ai = oA[j];
+        pos_t pi = spos[ownm[j]];
+        real si = get_s(pi), Ai = sAj[ownm[j]];
         real fx = 0, fy = 0, fz = 0;
 #pragma unroll 4
         for (int cc = c0; cc < c1; ++cc) {
@@ -1206,9 +1210,9 @@ __global__ void __launch_bounds__(SC_TPB) k_force(int n, Geom g, Coef c, const t
                     ++j;
                     jend = roff[j + 1] >> 2;
                 } while (cc >= jend);
-                pi = opos[j];
+                pi = spos[ownm[j]];
                 si = get_s(pi);
-                Ai = oA[j];
+                Ai = sAj[ownm[j]];
                 fx = fy = fz = 0;
             }
             int h[4];
@@ -1590,11 +1594,11 @@ __global__ void __launch_bounds__(SC_TPB) k_store_nlist(Geom g, SuperGrid G, Sup
 // Opens one loop iteration: advances the device iteration counter (which
 // keys the Langevin noise) and, inside a CUDA graph, sets the conditional
 // that runs the rebuild body only when a rebuild is due; clears the list of
-// cell groups with window particles that the iteration's count fills.
+// window particles that the iteration's count fills.
 __global__ void k_gate(Status* st, cudaGraphConditionalHandle h, int in_graph)
 {
     st->iter += 1;
-    st->nwin_blocks = 0;
+    st->nwin = 0;
     if (in_graph) {
         const bool due = st->rebuild && !halted(st);
         if (due) st->graph_rebuild_runs += 1;
