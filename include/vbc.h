@@ -97,6 +97,12 @@ typedef struct {
     double nlist_mean;         /* mean list length at the last build */
     int64_t pairs_within_rc;   /* unordered pairs with r < r_c at the last energy evaluation */
     int64_t in_window;         /* particles with f - delta < n_i < f - delta + 1 (last count pass) */
+    int64_t unsaturated;       /* particles the last count pass had to walk in full: fewer than
+                                  ceil(f - delta + 1) of their kept near neighbours within r_l */
+    int32_t stage_cap;         /* staged particles per cell group (current capacity) */
+    int32_t group_cap;         /* particles per cell group (current capacity) */
+    int32_t segment_cap;       /* list entries per cell group (current capacity) */
+    int32_t groups;            /* cell groups (thread blocks of the list-walking kernels) */
 } vbc_stats;
 
 /*

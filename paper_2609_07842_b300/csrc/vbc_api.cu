@@ -99,12 +99,15 @@ struct vbc_system {
     int *cell_of = nullptr, *slot_of = nullptr, *order = nullptr;
     int *cell_count = nullptr, *cell_start = nullptr, *morton_rank = nullptr, *sc_org = nullptr;
     int* chunk_sum = nullptr;
-    int* wpart = nullptr;       // [n][2] window particles and their groups (k_count -> k_chain)
+    int* wpart = nullptr;       // [n] window particles (k_count_rows -> k_chain)
+    int* ulist = nullptr;       // [n] particles the count walks in full (k_count_near -> k_count_rows)
     int* stage_idx = nullptr;   // [nsc][smax] sorted index of each staged particle (list build)
     int2* gmeta = nullptr;      // [nsc] staged particles and padded list entries per group
     int* roff_g = nullptr;      // [n] row offset of each particle in its group's segment
     int* near_k = nullptr;      // [n][NEAR_K] near neighbours kept for the saturation test
-    int chain_grid = 0;         // blocks of the chain-rule pass
+    int* hasA = nullptr;        // [nsc] groups that stage a window particle (k_chain -> k_force)
+    int rows_grid = 0;          // blocks of the count's full-row walk
+    int chain_grid = 0;         // blocks of the list-walking grids (count rows, chain-rule pass)
     void *ds = nullptr, *sA = nullptr;
     Status* st = nullptr;
     Status* st_host = nullptr;  // pinned
@@ -142,11 +145,10 @@ struct vbc_system {
     size_t real_bytes() const { return prec == VBC_FP64 ? sizeof(double) : sizeof(float); }
     SuperGrid grid() const { return SuperGrid{morton_rank, sc_org, cell_start}; }
     SuperCaps caps() const { return SuperCaps{smax, omax, seg, cap}; }
-    GroupAux aux() const { return GroupAux{stage_idx, gmeta, roff_g, near_k}; }
+    GroupAux aux() const { return GroupAux{stage_idx, gmeta, roff_g, near_k, hasA}; }
     // dynamic shared memory of each kernel family
     size_t smem_nlist() const { return nlist_layout(caps(), pos_bytes()).total; }
     size_t smem_nlist_rel() const { return nlist_layout(caps(), sizeof(float4)).total; }
-    size_t smem_count() const { return al16((size_t)omax * 4); }
     size_t smem_force() const { return force_layout(caps(), pos_bytes(), real_bytes()).total; }
     size_t smem_energy() const { return pass_layout(caps(), pos_bytes(), sizeof(double2)).total; }
     size_t smem_store() const { return al16((size_t)(omax + 1) * 4); }
@@ -326,8 +328,8 @@ void free_all(vbc_system* s)
     dfree(s->pos[0]); dfree(s->pos[1]); dfree(s->post); dfree(s->xref);
     dfree(s->nbr); dfree(s->scratch); dfree(s->nnb); dfree(s->cell_of); dfree(s->slot_of); dfree(s->order);
     dfree(s->cell_count); dfree(s->cell_start); dfree(s->morton_rank); dfree(s->sc_org);
-    dfree(s->chunk_sum); dfree(s->wpart); dfree(s->stage_idx); dfree(s->gmeta); dfree(s->roff_g);
-    dfree(s->near_k);
+    dfree(s->chunk_sum); dfree(s->wpart); dfree(s->ulist); dfree(s->stage_idx); dfree(s->gmeta); dfree(s->roff_g);
+    dfree(s->near_k); dfree(s->hasA);
     dfree(s->ds); dfree(s->sA); dfree(s->st); dfree(s->partial); dfree(s->ppairs); dfree(s->red);
     dfree(s->win); dfree(s->e_sd); dfree(s->e_A);
     if (s->st_host) cudaFreeHost(s->st_host);
@@ -364,7 +366,6 @@ int configure_smem(vbc_system* s)
     if (s->smem_nlist_rel() > MAX_SMEM) return fail(VBC_ERR_UNSTABLE, "list build staging too large");
     VBC_TRY(set_smem(k_nlist<M, false>, s->smem_nlist()));
     if constexpr (!M::fp64) VBC_TRY(set_smem(k_nlist<M, true>, s->smem_nlist_rel()));
-    VBC_TRY(set_smem(k_count<M>, s->smem_count()));
     VBC_TRY(set_smem(k_force<M, EPI_FORCE>, s->smem_force()));
     VBC_TRY(set_smem(k_force<M, EPI_START>, s->smem_force()));
     VBC_TRY(set_smem(k_force<M, EPI_FINISH>, s->smem_force()));
@@ -416,21 +417,24 @@ int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window)
     using pos_t = typename M::pos_t;
     using real = typename M::real;
     using real2 = typename M::real2;
-    const pos_t* pos = (const pos_t*)s->pos[s->cur];
+    pos_t* pos = (pos_t*)s->pos[s->cur];  // the count writes s_i into the positions' spare word
     CountOut out{n_out, want_window ? s->win : nullptr};
     {
         Timed t(s, VBC_K_COUNT);
-        k_count<M><<<s->nsc, SC_TPB, s->smem_count(), s->stream>>>(s->geom, s->coef, pos, s->grid(), s->caps(),
-                                                                    s->aux(), s->nbr, s->nnb, s->id, (real*)s->ds,
-                                                                    (real2*)s->sA, out, s->wpart, s->st);
+        k_count_near<M><<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>((int)s->n, s->geom, s->coef, pos, s->aux(),
+                                                                       (real*)s->ds, (real2*)s->sA, out, s->ulist,
+                                                                       s->st);
+        k_count_rows<M><<<s->rows_grid, TPB, 0, s->stream>>>(s->geom, s->coef, pos, s->caps(), s->aux(), s->nbr,
+                                                               s->nnb, s->id, (real*)s->ds, (real2*)s->sA, out,
+                                                               s->ulist, s->wpart, s->st);
     }
     {
         Timed t(s, VBC_K_CHAIN);
         k_chain<M><<<s->chain_grid, SC_TPB, 0, s->stream>>>(s->geom, s->coef, pos, s->caps(), s->aux(), s->nbr,
                                                             s->nnb, (const real*)s->ds, (real2*)s->sA, s->wpart,
-                                                            s->st);
+                                                            s->morton_rank, s->st);
     }
-    return check_launch(s, 2);
+    return check_launch(s, 3);
 }
 
 template <class M, int EPI>
@@ -549,7 +553,7 @@ int compute_impl(vbc_system* s, double* F_dev, double* n_dev, bool energy)
 {
     for (int attempt = 0;; ++attempt) {
         VBC_CUDA(cudaMemsetAsync(s->win, 0, sizeof(long long), s->stream));
-        VBC_CUDA(cudaMemsetAsync(&s->st->nwin, 0, sizeof(int), s->stream));
+        VBC_CUDA(cudaMemsetAsync(&s->st->nwin, 0, 2 * sizeof(int), s->stream));  // nwin and nu
         VBC_TRY(enqueue_rebuild<M>(s));
         VBC_TRY(enqueue_count_chain<M>(s, n_dev, true));
         StepArgs a{};
@@ -678,7 +682,7 @@ int launch_pair_graph(vbc_system* s, const StepArgs& a)
     if (!pg.exec || pg.dt != a.dt || pg.c1 != a.c1 || pg.c2 != a.c2 || pg.layout_version != s->layout_version)
         VBC_TRY(build_pair_graph<M>(s, s->cur, a));
     VBC_CUDA(cudaGraphLaunch(pg.exec, s->stream));
-    s->launches += 8;  // two gates, two count/chain/force triples (rebuild bodies counted on the device)
+    s->launches += 10;  // two gates, two count/count/chain/force sets (rebuild bodies counted on the device)
     return VBC_OK;
 }
 
@@ -914,6 +918,8 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess || sms < 1)
             sms = 148;
         s->chain_grid = std::max(1, std::min(2 * sms, s->nsc));
+        // one warp per particle the count walks in full: about 1 % of them at high counts
+        s->rows_grid = std::max(s->chain_grid, blocks_for(s->n, 256));
     }
     if (cfg->stream) {
         s->stream = (cudaStream_t)cfg->stream;
@@ -948,11 +954,13 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     ALLOC(dalloc(s->morton_rank, (size_t)g.ncell));
     ALLOC(dalloc(s->sc_org, (size_t)s->nsc));
     ALLOC(dalloc(s->chunk_sum, (size_t)blocks_for(s->npad, SCAN_CHUNK)));
-    ALLOC(dalloc(s->wpart, 2 * n));
+    ALLOC(dalloc(s->wpart, n));
+    ALLOC(dalloc(s->ulist, n));
     ALLOC(dalloc(s->stage_idx, (size_t)s->nsc * s->smax));
     ALLOC(dalloc(s->gmeta, (size_t)s->nsc));
     ALLOC(dalloc(s->roff_g, n));
     ALLOC(dalloc(s->near_k, (size_t)NEAR_K * n));
+    ALLOC(dalloc(s->hasA, (size_t)s->nsc));
     ALLOC(dalloc_bytes(s->ds, n * s->real_bytes()));
     ALLOC(dalloc_bytes(s->sA, n * 2 * s->real_bytes()));
     ALLOC(dalloc(s->st, 1));
@@ -995,6 +1003,7 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     }
     if (cudaMemsetAsync(s->cell_count, 0, (size_t)s->npad * sizeof(int), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->st, 0, sizeof(Status), s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->hasA, 0, (size_t)s->nsc * sizeof(int), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->nnb, 0, n * sizeof(int), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->sA, 0, n * 2 * s->real_bytes(), s->stream) != cudaSuccess)
         return bail(fail(VBC_ERR_CUDA, "initial memset failed"));
@@ -1196,6 +1205,11 @@ int vbc_get_stats(vbc_system* s, vbc_stats* out)
     long long w = 0;
     VBC_CUDA(cudaMemcpy(&w, s->win, sizeof(long long), cudaMemcpyDeviceToHost));
     out->in_window = w;
+    out->unsaturated = s->st_host->nu;
+    out->stage_cap = s->smax;
+    out->group_cap = s->omax;
+    out->segment_cap = s->seg;
+    out->groups = s->nsc;
     return VBC_OK;
 }
 

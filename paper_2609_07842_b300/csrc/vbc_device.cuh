@@ -84,8 +84,9 @@ struct Status {
     long long iter;     // loop iteration now running (advanced by k_gate)
     long long step_base;// noise counter of iteration 0 of the current call
     long long graph_rebuild_runs;  // rebuild bodies a graph conditional executed
-    int nwin;           // window particles listed by the last count (k_count)
-    int pad1;
+    int nwin;           // window particles listed by the last count (k_count_rows)
+    int nu;             // particles the last count walked in full: not saturated by their kept near
+                        // neighbours (k_count_near)
 };
 
 // Work stops (until the host intervenes) once any of these is raised.

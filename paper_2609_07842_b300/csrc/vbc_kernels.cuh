@@ -268,8 +268,9 @@ constexpr int NEAR_K = 8;  // near neighbours kept per particle for the saturati
 struct GroupAux {
     int* stage_idx;  // [groups][smax] sorted index of each staged particle
     int2* meta;      // [groups] (staged particles, padded list entries)
-    int* roff;       // [n] row offset of each particle in its group's list segment
+    int* roff;       // [n] start of each particle's row in nbr (group * seg + offset in its segment)
     int* near;       // [n][NEAR_K] sorted indices of up to NEAR_K near neighbours, -1 for none
+    int* hasA;       // [groups] 1: the group stages a window particle (set by k_chain, cleared by k_force)
 };
 
 struct SuperTab {
@@ -637,7 +638,7 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
     }
     if (any_over) return;
     const int tot = scan_in_place(roff, n_own, T.sw);
-    for (int j = t; j < n_own; j += SC_TPB) aux.roff[p0 + j] = roff[j];
+    for (int j = t; j < n_own; j += SC_TPB) aux.roff[p0 + j] = (int)blockIdx.x * cp.seg + roff[j];
     if (t == 0) {
         atomicMax(&st->max_seg, tot);
         aux.meta[blockIdx.x] = make_int2(total, tot);
@@ -683,11 +684,12 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
 // already hold at least ceil(f - delta + 1) neighbours with r <= r_l, then
 // n_i >= f - delta + 1 whatever the other entries add, so s_i = s'_i = 0
 // exactly and nothing else is needed (unless the counts themselves are
-// requested).  One block per cell group: each thread tests its own particles
-// for saturation with direct loads of those few neighbours; the block then
-// hands the unsaturated ones, one at a time, to whole warps that walk the
-// full row with one lane per entry, reading neighbours through the group's
-// staged-index table.  No shared-memory staging is needed.
+// requested).  k_count_near tests that, one thread per particle, with direct
+// loads of those few neighbours, and lists the particles it cannot settle;
+// k_count_rows then walks their full rows, one warp per particle and one lane
+// per entry, reading neighbours through the group's staged-index table.
+// Both write s_i also into the spare word of the particle's position, where
+// the force pass stages it.
 struct CountOut {
     double* n_out;         // counts in caller order, or null
     long long* in_window;  // counter of window particles, or null
@@ -725,67 +727,74 @@ __device__ __forceinline__ double r2_d(const typename M::pos_t& a, const typenam
     return dx * dx + dy * dy + dz * dz;
 }
 
+// s_i into the spare word of a position.
+__device__ __forceinline__ void put_w(int4* p, float s) { reinterpret_cast<int*>(p)[3] = __float_as_int(s); }
+__device__ __forceinline__ void put_w(P64* p, double s)
+{
+    reinterpret_cast<unsigned long long*>(p)[3] = (unsigned long long)__double_as_longlong(s);
+}
+
 template <class M>
-__global__ void __launch_bounds__(SC_TPB) k_count(Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
-                                                  SuperGrid G, SuperCaps cp, GroupAux aux,
-                                                  const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
-                                                  const int* __restrict__ id, typename M::real* __restrict__ ds_out,
-                                                  typename M::real2* __restrict__ sA, CountOut out,
-                                                  int* __restrict__ wpart, Status* st)
+__global__ void __launch_bounds__(TPB) k_count_near(int n, Geom g, Coef c, typename M::pos_t* __restrict__ pos,
+                                                    GroupAux aux, typename M::real* __restrict__ ds_out,
+                                                    typename M::real2* __restrict__ sA, CountOut out,
+                                                    int* __restrict__ ulist, Status* st)
 {
     using pos_t = typename M::pos_t;
     using real = typename M::real;
     using real2 = typename M::real2;
     if (blockIdx.x == 0 && threadIdx.x == 0) st->rebuild = 0;
     if (halted(st)) return;
-    __shared__ int s_nu;
-    extern __shared__ __align__(16) unsigned char smem[];
-    int* ulist = (int*)smem;  // [omax] unsaturated own particles
-    const int t = threadIdx.x, b = blockIdx.x;
-    const int p0 = __ldg(G.cell_start + OWN_CELLS * b);
-    const int n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
-    if (t == 0) s_nu = 0;
-    __syncthreads();
-
-    // saturation test over the kept near neighbours
-    for (int j = t; j < n_own; j += SC_TPB) {
-        const int p = p0 + j;
-        long long full = 0;
-        if (!out.n_out) {
-            const pos_t pi = pos[p];
-            const int4* nv = reinterpret_cast<const int4*>(aux.near) + 2 * (size_t)p;
-            const int4 a0 = __ldg(nv), a1 = __ldg(nv + 1);
-            const int q[NEAR_K] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            pos_t pj[NEAR_K];
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    long long full = 0;
+    if (!out.n_out) {
+        const pos_t pi = pos[p];
+        const int4* nv = reinterpret_cast<const int4*>(aux.near) + 2 * (size_t)p;
+        const int4 a0 = __ldg(nv), a1 = __ldg(nv + 1);
+        const int q[NEAR_K] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        pos_t pj[NEAR_K];
 #pragma unroll
-            for (int k = 0; k < NEAR_K; ++k)
-                if (q[k] >= 0) pj[k] = pos[q[k]];
+        for (int k = 0; k < NEAR_K; ++k)
+            if (q[k] >= 0) pj[k] = pos[q[k]];
 #pragma unroll
-            for (int k = 0; k < NEAR_K; ++k) {
-                if (q[k] < 0) continue;
-                if constexpr (M::fp64) full += r2_d<M>(pi, pj[k], g) <= c.rl2;
-                else full += r2_fix(pi, pj[k]) <= c.rl2_fix;
-            }
-        }
-        if (!out.n_out && full >= c.sat_full) {
-            ds_out[p] = (real)0;
-            sA[p] = real2{(real)0, (real)0};
-        } else {
-            ulist[atomicAdd(&s_nu, 1)] = j;
+        for (int k = 0; k < NEAR_K; ++k) {
+            if (q[k] < 0) continue;
+            if constexpr (M::fp64) full += r2_d<M>(pi, pj[k], g) <= c.rl2;
+            else full += r2_fix(pi, pj[k]) <= c.rl2_fix;
         }
     }
-    __syncthreads();
+    if (!out.n_out && full >= c.sat_full) {
+        ds_out[p] = (real)0;
+        sA[p] = real2{(real)0, (real)0};
+        put_w(pos + p, (real)0);
+    } else {
+        ulist[atomicAdd(&st->nu, 1)] = p;
+    }
+}
 
-    // unsaturated particles: one warp each, one lane per entry
-    const int nu = s_nu;
-    const int lane = t & 31;
-    const uint16_t* seg = nbr + (size_t)b * cp.seg;
-    const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
-    for (int u = t >> 5; u < nu; u += SC_TPB / 32) {
-        const int j = ulist[u], p = p0 + j;
+template <class M>
+__global__ void __launch_bounds__(TPB) k_count_rows(Geom g, Coef c, typename M::pos_t* __restrict__ pos,
+                                                    SuperCaps cp, GroupAux aux, const uint16_t* __restrict__ nbr,
+                                                    const int* __restrict__ nnb, const int* __restrict__ id,
+                                                    typename M::real* __restrict__ ds_out,
+                                                    typename M::real2* __restrict__ sA, CountOut out,
+                                                    const int* __restrict__ ulist, int* __restrict__ wpart,
+                                                    Status* st)
+{
+    using pos_t = typename M::pos_t;
+    using real = typename M::real;
+    using real2 = typename M::real2;
+    if (halted(st)) return;
+    const int nu = st->nu;
+    const int lane = threadIdx.x & 31;
+    for (int k = (int)((blockIdx.x * TPB + threadIdx.x) >> 5); k < nu; k += (int)((gridDim.x * TPB) >> 5)) {
+        const int p = ulist[k];
+        const int ra = __ldg(aux.roff + p), b = ra / cp.seg;
         const int len = row_len(__ldg(nnb + p));
         const pos_t pi = pos[p];
-        const uint16_t* row = seg + __ldg(aux.roff + p);
+        const uint16_t* row = nbr + ra;
+        const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
         real s, ds;
         double n_val;
         if constexpr (M::fp64) {
@@ -822,12 +831,11 @@ __global__ void __launch_bounds__(SC_TPB) k_count(Geom g, Coef c, const typename
         if (lane == 0) {
             ds_out[p] = ds;
             sA[p] = real2{s, (real)0};
+            put_w(pos + p, s);
             if (out.n_out) out.n_out[id[p]] = n_val;
             if (ds != (real)0) {
                 // the chain-rule pass visits the window particles listed here
-                const int k = atomicAdd(&st->nwin, 1);
-                wpart[2 * k] = p;
-                wpart[2 * k + 1] = b;
+                wpart[atomicAdd(&st->nwin, 1)] = p;
                 if (out.in_window) atomicAdd((unsigned long long*)out.in_window, 1ull);
             }
         }
@@ -840,12 +848,44 @@ __global__ void __launch_bounds__(SC_TPB) k_count(Geom g, Coef c, const typename
 // read through their group's staged-index table.  A fixed grid walks the
 // list, so a step without window particles costs one launch that reads one
 // counter.
+// Marks every cell group whose staging holds the cell (cx, cy, cz): the groups
+// with origin x0 in [cx - BXC, cx + 1] (multiples of BXC, modulo the padded
+// grid), and likewise in y and z.
+__device__ __forceinline__ void mark_groups(int cx, int cy, int cz, const Geom& g, const int* __restrict__ morton_rank,
+                                            int* __restrict__ hasA)
+{
+    const int pc[3] = {(g.nc[0] + BXC - 1) / BXC * BXC, (g.nc[1] + BYC - 1) / BYC * BYC,
+                       (g.nc[2] + BZC - 1) / BZC * BZC};
+    const int bc[3] = {BXC, BYC, BZC}, cc[3] = {cx, cy, cz};
+    int o[3][2], no[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        // staged columns of a group at x0 are x0 - 1 .. x0 + bc, wrapped on the real grid
+        no[a] = 0;
+        for (int x0 = 0; x0 < pc[a] && no[a] < 2; x0 += bc[a]) {
+            bool hit = false;
+            for (int l = -1; l <= bc[a]; ++l) {
+                int x = x0 + l;
+                x = x < 0 ? x + g.nc[a] : (x >= g.nc[a] ? x - g.nc[a] : x);
+                hit |= x == cc[a];
+            }
+            if (hit) o[a][no[a]++] = x0;
+        }
+    }
+    for (int i = 0; i < no[0]; ++i)
+        for (int j = 0; j < no[1]; ++j)
+            for (int k = 0; k < no[2]; ++k) {
+                const int lin = (o[2][k] * g.nc[1] + o[1][j]) * g.nc[0] + o[0][i];
+                hasA[__ldg(morton_rank + lin) / OWN_CELLS] = 1;
+            }
+}
+
 template <class M>
 __global__ void __launch_bounds__(SC_TPB) k_chain(Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
                                                   SuperCaps cp, GroupAux aux, const uint16_t* __restrict__ nbr,
                                                   const int* __restrict__ nnb, const typename M::real* __restrict__ ds,
                                                   typename M::real2* __restrict__ sA, const int* __restrict__ wpart,
-                                                  const Status* st)
+                                                  const int* __restrict__ morton_rank, const Status* st)
 {
     using pos_t = typename M::pos_t;
     using real = typename M::real;
@@ -854,10 +894,11 @@ __global__ void __launch_bounds__(SC_TPB) k_chain(Geom g, Coef c, const typename
     const int lane = threadIdx.x & 31;
     const real* s_only = reinterpret_cast<const real*>(sA);  // s_j at even offsets (A is written here)
     for (int k = (int)((blockIdx.x * SC_TPB + threadIdx.x) >> 5); k < nw; k += (int)((gridDim.x * SC_TPB) >> 5)) {
-        const int p = wpart[2 * k], b = wpart[2 * k + 1];
+        const int p = wpart[k];
+        const int ra = __ldg(aux.roff + p), b = ra / cp.seg;
         const int len = row_len(__ldg(nnb + p));
         const pos_t pi = pos[p];
-        const uint16_t* row = nbr + (size_t)b * cp.seg + __ldg(aux.roff + p);
+        const uint16_t* row = nbr + ra;
         const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
         real acc = 0;
         for (int e = lane; e < len; e += 32) {
@@ -878,7 +919,11 @@ __global__ void __launch_bounds__(SC_TPB) k_chain(Geom g, Coef c, const typename
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) sA[p].y = ds[p] * acc;
+        if (lane == 0) {
+            sA[p].y = ds[p] * acc;
+            const int3 cl = cell_of_pos<M>(pi, g);
+            mark_groups(cl.x, cl.y, cl.z, g, morton_rank, aux.hasA);
+        }
     }
 }
 
@@ -1138,10 +1183,8 @@ __global__ void __launch_bounds__(SC_TPB) k_force(int n, Geom g, Coef c, const t
     int* roff = (int*)(smem + ly.roff);
     uint16_t* ownm = (uint16_t*)(smem + ly.ownm);
     real* oF = (real*)(smem + ly.oF);  // [3][omax]
-    struct PV {
-        pos_t p;
-        real2 sa;
-    };
+    // A_j can be nonzero only if the chain-rule pass flagged this group
+    const bool useA = __ldg(aux.hasA + b) != 0;
     bool anyA = false;
     {
         // staging through the group's table of sorted indices, B loads in flight
@@ -1151,27 +1194,30 @@ __global__ void __launch_bounds__(SC_TPB) k_force(int n, Geom g, Coef c, const t
             int jj[B];
 #pragma unroll
             for (int u = 0; u < B; ++u) jj[u] = m0 + u * SC_TPB < total ? __ldg(sidx + m0 + u * SC_TPB) : -1;
-            PV v[B];
+            pos_t v[B];
+            real A[B];
 #pragma unroll
-            for (int u = 0; u < B; ++u)
-                if (jj[u] >= 0) v[u] = PV{pos[jj[u]], sA[jj[u]]};
+            for (int u = 0; u < B; ++u) {
+                if (jj[u] < 0) continue;
+                v[u] = pos[jj[u]];  // s_j is in the spare word
+                A[u] = useA ? sA[jj[u]].y : (real)0;
+            }
 #pragma unroll
             for (int u = 0; u < B; ++u) {
                 if (jj[u] < 0) continue;
                 const int m = m0 + u * SC_TPB;
-                pos_t q = v[u].p;
-                put_s(q, v[u].sa.x);
-                spos[m] = q;
-                sAj[m] = v[u].sa.y;
-                anyA |= v[u].sa.y != (real)0;
+                spos[m] = v[u];
+                sAj[m] = A[u];
+                anyA |= A[u] != (real)0;
                 // own particles are staged too (twice on very small grids: either copy will do)
                 if (jj[u] >= p0 && jj[u] < p0 + n_own) ownm[jj[u] - p0] = (uint16_t)m;
             }
         }
     }
-    for (int j = t; j < n_own; j += SC_TPB) roff[j] = __ldg(aux.roff + p0 + j);
+    for (int j = t; j < n_own; j += SC_TPB) roff[j] = __ldg(aux.roff + p0 + j) - b * cp.seg;
     if (t == 0) roff[n_own] = meta.y;
     anyA = __syncthreads_or(anyA);
+    if (t == 0 && useA) aux.hasA[b] = 0;  // ready for the next step
     const int nch = meta.y >> 2;
     const uint2* L = reinterpret_cast<const uint2*>(nbr + (size_t)b * cp.seg);
     const int per = (nch + SC_TPB - 1) / SC_TPB;
@@ -1599,6 +1645,7 @@ __global__ void k_gate(Status* st, cudaGraphConditionalHandle h, int in_graph)
 {
     st->iter += 1;
     st->nwin = 0;
+    st->nu = 0;
     if (in_graph) {
         const bool due = st->rebuild && !halted(st);
         if (due) st->graph_rebuild_runs += 1;

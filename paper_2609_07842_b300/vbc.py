@@ -59,7 +59,9 @@ class _Config(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("step", ctypes.c_int64), ("rebuilds", ctypes.c_int64),
                 ("nlist_cap", ctypes.c_int32), ("nlist_max", ctypes.c_int32), ("nlist_mean", ctypes.c_double),
-                ("pairs_within_rc", ctypes.c_int64), ("in_window", ctypes.c_int64)]
+                ("pairs_within_rc", ctypes.c_int64), ("in_window", ctypes.c_int64),
+                ("unsaturated", ctypes.c_int64), ("stage_cap", ctypes.c_int32), ("group_cap", ctypes.c_int32),
+                ("segment_cap", ctypes.c_int32), ("groups", ctypes.c_int32)]
 
 
 _lib = None
