@@ -166,7 +166,8 @@ int vbc_set_state(vbc_system* sys, const double* pos, const double* vel, int64_t
                   int on_device);
 
 /* Change the pair parameters of an existing system (same cut-off or smaller:
- * r_c + skin must still fit the cell grid built at creation). */
+ * r_c + skin must still fit the cell grid built at creation).  The neighbour
+ * list is rebuilt before the next pass. */
 int vbc_set_params(vbc_system* sys, const vbc_pair_params* params);
 
 int vbc_get_stats(vbc_system* sys, vbc_stats* out);

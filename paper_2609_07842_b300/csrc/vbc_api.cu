@@ -260,27 +260,39 @@ int make_coef(const vbc_pair_params& p, const Geom& g, Coef& c)
     return VBC_OK;
 }
 
-// List radius and the near/far split: near entries are closer than max(r_r, r_l).
-ListParams make_list_params(const Coef& c, double rlist, const Geom& g)
+// List radius and the near/far split.  Near entries are closer than
+// r_r + skin at the build: no particle moves more than skin / 2 before the
+// next build, so every pair inside the soft core at any step until then is a
+// near entry, and the soft-core-only force path scans the near prefix of a
+// row only.  The radius carries a relative margin of 1e-5 (above the float
+// error of the build's block-relative classification).
+ListParams make_list_params(const Coef& c, double rlist, double skin, const Geom& g)
 {
     ListParams lp{};
     const double s2 = g.s32d[0] * g.s32d[0];
     lp.rlist2 = rlist * rlist;
     lp.rlist2_fix = (unsigned long long)std::llround(lp.rlist2 / s2);
-    lp.near2 = std::max(c.rr2, c.rl2);
-    lp.near2_fix = (unsigned long long)std::llround(lp.near2 / s2);
+    const double rn = (c.r_r + skin) * (1.0 + 1e-5);
+    lp.near2 = rn * rn;
+    lp.near2_fix = (unsigned long long)std::ceil(lp.near2 / s2);
     const double rm = rlist * (1.0 + 1e-5);
     lp.rlist2_f = (float)(rm * rm);
     lp.near2_f = (float)lp.near2;
+    lp.rl2 = c.rl2;
+    lp.rl2_fix = (unsigned long long)std::llround(c.rl2 / s2);
+    lp.rl2_f = (float)c.rl2;
     return lp;
 }
 
-f2x to_f2x(double v)
+// Integer part and 2^-64 fraction of a non-negative factor (the fraction to
+// double precision, which bounds the error of a fixed-point product by a
+// relative 2^-53 of it).
+void split_fix(double v, unsigned long long& hi, unsigned long long& lo)
 {
-    f2x r;
-    r.hi = (float)v;
-    r.lo = (float)(v - (double)r.hi);
-    return r;
+    const double ip = std::floor(v);
+    hi = (unsigned long long)ip;
+    const double fr = std::ldexp(v - ip, 64);
+    lo = fr >= 18446744073709551615.0 ? ~0ull : (unsigned long long)fr;
 }
 
 uint32_t spread3(uint32_t v)  // 10 bits -> every third bit
@@ -695,10 +707,10 @@ int steps_impl(vbc_system* s, int64_t nsteps, double dt, double kT, double gamma
     a.dt = dt;
     a.c1 = std::exp(-gamma * dt);
     a.c2 = std::sqrt(std::max(0.0, (1.0 - a.c1 * a.c1) * kT));
-    a.h = to_f2x(0.5 * dt);
-    for (int d = 0; d < 3; ++d) a.hK[d] = to_f2x(0.5 * dt * 4503599627370496.0 / s->box[d]);  // 2^52 / L
-    a.c1f = to_f2x(a.c1);
-    a.c2f = to_f2x(a.c2);
+    a.kick40 = (float)(0.5 * dt * 1099511627776.0);  // 2^40
+    a.c2_40 = (float)(a.c2 * 1099511627776.0);
+    for (int d = 0; d < 3; ++d) split_fix(0.5 * dt * 4096.0 / s->box[d], a.dk_hi[d], a.dk_lo[d]);  // 2^12 / L
+    split_fix(a.c1, a.c1_hi, a.c1_lo);
     a.seed = s->seed;
     a.half_skin2 = (float)(0.25 * s->skin * s->skin);
     // Iteration 0 opens step 0 (forces at the initial state, then B A O A);
@@ -892,7 +904,7 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
         int rc = make_coef(s->prm, g, s->coef);
         if (rc) return bail(rc);
     }
-    s->lp = make_list_params(s->coef, s->rlist, g);
+    s->lp = make_list_params(s->coef, s->rlist, s->skin, g);
 
     // initial capacities from the mean density
     const double rho = (double)s->n / (s->box[0] * s->box[1] * s->box[2]);
@@ -1185,9 +1197,10 @@ int vbc_set_params(vbc_system* s, const vbc_pair_params* p)
     VBC_CUDA(cudaStreamSynchronize(s->stream));
     s->prm = *p;
     s->coef = c;
-    s->lp = make_list_params(c, s->rlist, s->geom);
+    s->lp = make_list_params(c, s->rlist, s->skin, s->geom);
     s->layout_version += 1;
-    return VBC_OK;
+    // the near/far split of the lists depends on r_r: rebuild before the next pass
+    return force_rebuild_flag(s);
 }
 
 int vbc_get_stats(vbc_system* s, vbc_stats* out)

@@ -120,16 +120,31 @@ __device__ __forceinline__ float3 langevin_normals(unsigned long long seed,
 {
     const uint4 x = philox4x32_10(make_uint4((uint32_t)step, (uint32_t)(step >> 32), pid, 0u),
                                   make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
-    const float k = 1.0f / 8388608.0f;
-    const float u0 = ((float)(x.x >> 9) + 0.5f) * k;
-    const float u1 = ((float)(x.y >> 9) + 0.5f) * k;
-    const float u2 = ((float)(x.z >> 9) + 0.5f) * k;
-    const float u3 = ((float)(x.w >> 9) + 0.5f) * k;
+    // u = ((x >> 9) + 1/2) 2^-23, exactly, from the bits of 1 + (x >> 9) 2^-23
+    const float half_ulp = 5.9604644775390625e-8f;  // 2^-24
+    const float u0 = (__uint_as_float(0x3F800000u | (x.x >> 9)) - 1.0f) + half_ulp;
+    const float u1 = (__uint_as_float(0x3F800000u | (x.y >> 9)) - 1.0f) + half_ulp;
+    const float u2 = (__uint_as_float(0x3F800000u | (x.z >> 9)) - 1.0f) + half_ulp;
+    const float u3 = (__uint_as_float(0x3F800000u | (x.w >> 9)) - 1.0f) + half_ulp;
     const float r0 = sqrtf(-2.0f * logf(u0));
     const float r1 = sqrtf(-2.0f * logf(u2));
+    // angles 2 pi u taken as pi + 2 pi (u - 1/2): the hardware sine and cosine
+    // are accurate to 2^-21.4 on [-pi, pi], and u - 1/2 is exact
+    const float k2pi = 6.2831853071795864769f;
     float s0, c0;
-    sincospif(2.0f * u1, &s0, &c0);
-    return make_float3(r0 * c0, r0 * s0, r1 * cospif(2.0f * u3));
+    __sincosf(k2pi * (u1 - 0.5f), &s0, &c0);
+    const float c3 = __cosf(k2pi * (u3 - 0.5f));
+    return make_float3(-r0 * c0, -r0 * s0, -r1 * c3);
+}
+
+// Fixed-point product: nearest integer of v (hi + lo 2^-64), for |v| < 2^62
+// and a non-negative factor with integer part hi and fraction lo 2^-64.
+__device__ __forceinline__ long long mul_fix(long long v, unsigned long long hi, unsigned long long lo)
+{
+    const unsigned long long av = (unsigned long long)(v < 0 ? -v : v);
+    const unsigned long long frac_lo = av * lo;
+    unsigned long long r = av * hi + __umul64hi(av, lo) + (frac_lo >> 63);
+    return v < 0 ? -(long long)r : (long long)r;
 }
 
 // The same three normals with the Box-Muller transform in FP64 (FP64 mode).
@@ -285,7 +300,7 @@ struct ModeF32 {
     using real = float;
     using real2 = float2;
     using xstate_t = long long;  // unwrapped position, fixed point in units of L / 2^52
-    using vstate_t = float2;     // velocity as a two-float (hi, lo)
+    using vstate_t = long long;  // velocity, fixed point in units of 2^-40
     static constexpr bool fp64 = false;
 
     // minimum-image separation a - b in length units

@@ -393,7 +393,7 @@ __device__ __forceinline__ int own_staged_cell(int b)
 // ---------------------------------------------------------------- lists
 // The lists of block s occupy nbr[s * seg ...]: the rows of its own
 // particles in sorted order, each padded to a multiple of 4 entries.  A row
-// holds the near entries (closer than max(r_r, r_l) at the build) first,
+// holds the near entries (closer than r_r + skin at the build) first,
 // then the far ones (up to r_c + skin); pads repeat the particle's own
 // staging index, which adds exactly nothing to a force (d = 0).
 // nnb[p] = near | far << 16.
@@ -419,9 +419,9 @@ __device__ __forceinline__ void unpack4(const uint2 v, int h[4])
 
 // Near (0), far (1) or beyond the list radius (-1).
 struct ListParams {
-    unsigned long long rlist2_fix, near2_fix;
-    double rlist2, near2;
-    float rlist2_f, near2_f;  // float tests on block-relative coordinates (with a margin)
+    unsigned long long rlist2_fix, near2_fix, rl2_fix;
+    double rlist2, near2, rl2;
+    float rlist2_f, near2_f, rl2_f;  // float tests on block-relative coordinates (with a margin)
 };
 template <class M>
 struct ListTest;
@@ -494,18 +494,20 @@ __host__ __device__ inline PassLayout pass_layout(const SuperCaps& cp, size_t po
     return l;
 }
 
-// k_force: staged positions (with s_j in the spare word) and A_j, row
-// offsets, the staging index of each own particle, and the forces of owners
-// whose chunks one thread covered completely.
+// k_force: staged positions (with s_j in the spare word) and A_j, the first
+// chunk of each own row and of each owner's visited chunks, the staging index
+// of each own particle, and the forces of owners whose chunks one thread
+// covered completely.
 struct ForceLayout {
-    size_t sA, roff, ownm, oF, total;
+    size_t sA, roff, vpre, ownm, oF, total;
 };
 __host__ __device__ inline ForceLayout force_layout(const SuperCaps& cp, size_t pos_bytes, size_t real_bytes)
 {
     ForceLayout l{};
     l.sA = al16((size_t)cp.smax * pos_bytes);
     l.roff = l.sA + al16((size_t)cp.smax * real_bytes);
-    l.ownm = l.roff + al16((size_t)(cp.omax + 1) * 4);
+    l.vpre = l.roff + al16((size_t)(cp.omax + 1) * 4);
+    l.ownm = l.vpre + al16((size_t)(cp.omax + 1) * 4);
     l.oF = l.ownm + al16((size_t)cp.omax * 2);
     l.total = l.oF + al16((size_t)3 * cp.omax * real_bytes);
     return l;
@@ -603,13 +605,30 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
         nnb[p] = nn | (nf << 16);
         rnn[j] = nn | (nf << 16);
         {
-            // up to NEAR_K near neighbours as sorted indices, for the saturation test
-            int q[NEAR_K];
-#pragma unroll
-            for (int k = 0; k < NEAR_K; ++k) q[k] = k < nn && k < cp.cap ? staged_index(T, row[k]) : -1;
-            int4* nv = reinterpret_cast<int4*>(aux.near) + 2 * (size_t)p;
-            nv[0] = make_int4(q[0], q[1], q[2], q[3]);
-            nv[1] = make_int4(q[4], q[5], q[6], q[7]);
+            // up to NEAR_K neighbours within r_l at the build (near entries first), as sorted
+            // indices, for the saturation test of the count
+            int* nv = aux.near + (size_t)NEAR_K * p;
+            int cnt = 0;
+            for (int e = 0; e < len && e < cp.cap && cnt < NEAR_K; ++e) {
+                const int m = e < nn ? row[e] : row[cp.cap - 1 - (e - nn)];
+                bool in;
+                if constexpr (REL) {
+                    const float4 q = spos[m];
+                    const float dx = pi.x - q.x, dy = pi.y - q.y, dz = pi.z - q.z;
+                    in = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz)) <= lp.rl2_f;
+                } else if constexpr (M::fp64) {
+                    double dx, dy, dz;
+                    ModeF64::delta64(pi, spos[m], g, dx, dy, dz);
+                    in = dx * dx + dy * dy + dz * dz <= lp.rl2;
+                } else {
+                    const int dx = pi.x - spos[m].x, dy = pi.y - spos[m].y, dz = pi.z - spos[m].z;
+                    in = (unsigned long long)((long long)dx * dx) + (unsigned long long)((long long)dy * dy) +
+                             (unsigned long long)((long long)dz * dz) <=
+                         lp.rl2_fix;
+                }
+                if (in) nv[cnt++] = staged_index(T, m);
+            }
+            for (int k = cnt; k < NEAR_K; ++k) nv[k] = -1;
         }
         roff[j] = pad4(len);
         over |= len > cp.cap;
@@ -930,14 +949,15 @@ __global__ void __launch_bounds__(SC_TPB) k_chain(Geom g, Coef c, const typename
 // ================================================================ pass 2: forces + BAOAB
 struct StepArgs {
     void* x;              // [3][n] unwrapped positions (FP32 mode: int64 in units L / 2^52; FP64: double)
-    void* v;              // [3][n] velocities (FP32 mode: two-float; FP64: double)
+    void* v;              // [3][n] velocities (FP32 mode: int64 in units 2^-40; FP64: double)
     double* F_out;        // forces in caller order [n][3], or null (EPI_FORCE)
     // FP64 mode constants
     double dt, c1, c2;    // c1 = exp(-gamma dt), c2 = sqrt((1 - c1^2) kT)
-    // FP32 mode constants as two-floats
-    f2x h;                // dt / 2
-    f2x hK[3];            // dt / 2 * 2^52 / L_a: velocity -> fixed-point displacement of a half drift
-    f2x c1f, c2f;
+    // FP32 mode constants (fixed point)
+    float kick40;                        // (dt / 2) 2^40: force -> velocity units of a half kick
+    float c2_40;                         // c2 2^40: normal -> velocity units
+    unsigned long long dk_hi[3], dk_lo[3];  // (dt / 2) 2^12 / L_a: velocity units -> position units of a half drift
+    unsigned long long c1_hi, c1_lo;        // c1 as integer part and 2^-64 fraction
     unsigned long long seed;
     float half_skin2;     // (skin / 2)^2
 };
@@ -949,7 +969,7 @@ struct PState;
 template <>
 struct PState<ModeF32> {
     long long X[3];
-    float2 V[3];
+    long long V[3];
     int4 xr;
     uint32_t id;
 };
@@ -971,7 +991,7 @@ __device__ __forceinline__ void load_pstate(int i, int n, const StepArgs& a, con
     if constexpr (!M::fp64) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            ps.V[d] = ((const float2*)a.v)[(size_t)d * n + i];
+            ps.V[d] = ((const long long*)a.v)[(size_t)d * n + i];
             if constexpr (start) ps.X[d] = ((const long long*)a.x)[(size_t)d * n + i];
         }
     } else {
@@ -985,9 +1005,11 @@ __device__ __forceinline__ void load_pstate(int i, int n, const StepArgs& a, con
 }
 
 // BAOAB update of particle i (unit mass, h = dt / 2) from its force.
-// FP32 mode: the unwrapped position is an int64 in units of L / 2^52 and the
-// velocity a two-float, so the update needs no FP64 instruction; each half
-// drift adds the nearest integer of h v 2^52 / L.  FP64 mode: doubles.
+// FP32 mode: positions are int64 in units of L / 2^52 and velocities int64
+// in units of 2^-40, so the update needs no FP64 instruction: a kick adds
+// the nearest integer of h F 2^40 (F from the FP32 force), a drift the exact
+// fixed-point product v h 2^12 / L, and the friction a fixed-point product
+// with c1.  FP64 mode: doubles.
 template <class M, int EPI>
 __device__ __forceinline__ void integrate(int i, int n, const Geom& g, typename M::real fx, typename M::real fy,
                                           typename M::real fz, const StepArgs& a, const PState<M>& ps, Status* st,
@@ -998,7 +1020,7 @@ __device__ __forceinline__ void integrate(int i, int n, const Geom& g, typename 
     bool bad = !isfinite(fx) || !isfinite(fy) || !isfinite(fz);
     if constexpr (!M::fp64) {
         long long* X = (long long*)a.x;
-        float2* V = (float2*)a.v;
+        long long* V = (long long*)a.v;
         const float f3[3] = {fx, fy, fz};
         float xi[3] = {0.0f, 0.0f, 0.0f};
         if constexpr (start) {
@@ -1010,20 +1032,19 @@ __device__ __forceinline__ void integrate(int i, int n, const Geom& g, typename 
         int w[3] = {0, 0, 0};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            f2x v = {ps.V[d].x, ps.V[d].y};
-            const f2x hf = f2x_mulf(a.h, f3[d]);
-            if constexpr (finish) v = f2x_add(v, hf);                             // B (closes the step)
+            long long v = ps.V[d];
+            const long long kick = float_to_ll_rn(f3[d] * a.kick40);
+            if constexpr (finish) v += kick;                                       // B (closes the step)
             if constexpr (start) {
                 long long P = ps.X[d];
-                v = f2x_add(v, hf);                                                // B
-                P += f2x_to_ll(f2x_mul(v, a.hK[d]));                               // A
-                v = f2x_add(f2x_mul(v, a.c1f), f2x_mulf(a.c2f, xi[d]));            // O
-                P += f2x_to_ll(f2x_mul(v, a.hK[d]));                               // A
+                v += kick;                                                         // B
+                P += mul_fix(v, a.dk_hi[d], a.dk_lo[d]);                           // A
+                v = mul_fix(v, a.c1_hi, a.c1_lo) + float_to_ll_rn(a.c2_40 * xi[d]);  // O
+                P += mul_fix(v, a.dk_hi[d], a.dk_lo[d]);                           // A
                 X[(size_t)d * n + i] = P;
                 w[d] = ModeF32::word(P);
             }
-            bad |= !isfinite(v.hi);
-            V[(size_t)d * n + i] = make_float2(v.hi, v.lo);
+            V[(size_t)d * n + i] = v;
         }
         if constexpr (start) {
             const int4 pn = make_int4(w[0], w[1], w[2], 0);
@@ -1138,20 +1159,23 @@ __device__ __forceinline__ void pair_f64(const P64& pi, double si, double Ai, co
 
 
 // Pass 2, one block per cell group.  The block stages its neighbourhood
-// through the table of sorted indices the list build left.  Its list entries are cut into
-// 4-entry chunks (rows are padded to a multiple of 4); each thread takes an
-// equal contiguous run of chunks, so it meets few owners and adds its chunks
-// in registers.  A run's first and last owners may continue in the
-// neighbouring runs: their partial forces go to per-thread head and tail
-// slots, owners wholly inside a run are written directly, and each own
-// particle then adds its pieces in thread order -- deterministic, no atomics.
-// A chunk whose owner has s_i = 0, in a block where no staged particle has
-// A_j != 0, can have no well or window term and takes the soft-core-only
-// path.  Otherwise, per pair in the FP32 mode, the exact integer r^2 decides
-// which terms can be nonzero (core overlap r < r_r; the well, only if
-// s_i s_j != 0; the counting window, only if A_i + A_j != 0), and the
-// arguments of the steep well and of the window come from exact integer
-// differences r^2 - r_m^2 and r^2 - r_l^2.
+// through the table of sorted indices the list build left.  Its list entries
+// are cut into 4-entry chunks (rows are padded to a multiple of 4).  An owner
+// with s_i = 0, in a block where no staged particle has A_j != 0, can have no
+// well or window term: only soft-core pairs, all of them near entries (see
+// the near/far split of the lists), so only the chunks holding its near
+// prefix are visited, with the soft-core-only arithmetic.  Other owners visit
+// all their chunks with every term.  The visited chunks of the block are
+// numbered consecutively (owner by owner) and each thread takes an equal
+// contiguous run of them, so it meets few owners and adds its chunks in
+// registers.  A run's first and last owners may continue in the neighbouring
+// runs: their partial forces go to per-thread head and tail slots, owners
+// wholly inside a run are written directly, and each own particle then adds
+// its pieces in thread order -- deterministic, no atomics.  Per pair in the
+// general FP32 path, the exact integer r^2 decides which terms can be nonzero
+// (core overlap r < r_r; the well, only if s_i s_j != 0; the counting window,
+// only if A_i + A_j != 0), and the arguments of the steep well and of the
+// window come from exact integer differences r^2 - r_m^2 and r^2 - r_l^2.
 template <class M, int EPI>
 __global__ void __launch_bounds__(SC_TPB) k_force(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
                                                   SuperGrid G, SuperCaps cp, const uint16_t* __restrict__ nbr,
@@ -1163,12 +1187,11 @@ __global__ void __launch_bounds__(SC_TPB) k_force(int n, Geom g, Coef c, const t
 {
     using pos_t = typename M::pos_t;
     using real = typename M::real;
-    using real2 = typename M::real2;
     // k_force raises `frozen` and `rebuild` itself; it tests `frozen` only through
     // halted(), which a thread of this launch changes only on the error path
     if (halted(st)) return;
     __shared__ real hF[3][SC_TPB], tF[3][SC_TPB];
-    __shared__ int jf[SC_TPB], jl[SC_TPB];
+    __shared__ int jf[SC_TPB], jl[SC_TPB], sw[SC_TPB / 32];
     extern __shared__ __align__(16) unsigned char smem[];
     const int t = threadIdx.x, b = blockIdx.x;
     const int p0 = __ldg(G.cell_start + OWN_CELLS * b);
@@ -1180,7 +1203,8 @@ __global__ void __launch_bounds__(SC_TPB) k_force(int n, Geom g, Coef c, const t
     const ForceLayout ly = force_layout(cp, sizeof(pos_t), sizeof(real));
     pos_t* spos = (pos_t*)smem;
     real* sAj = (real*)(smem + ly.sA);
-    int* roff = (int*)(smem + ly.roff);
+    int* roff = (int*)(smem + ly.roff);   // first chunk of each own row
+    int* vpre = (int*)(smem + ly.vpre);   // first visited chunk of each owner (block numbering)
     uint16_t* ownm = (uint16_t*)(smem + ly.ownm);
     real* oF = (real*)(smem + ly.oF);  // [3][omax]
     // A_j can be nonzero only if the chain-rule pass flagged this group
@@ -1214,34 +1238,47 @@ __global__ void __launch_bounds__(SC_TPB) k_force(int n, Geom g, Coef c, const t
             }
         }
     }
-    for (int j = t; j < n_own; j += SC_TPB) roff[j] = __ldg(aux.roff + p0 + j) - b * cp.seg;
-    if (t == 0) roff[n_own] = meta.y;
+    for (int j = t; j < n_own; j += SC_TPB) {
+        const int r0 = __ldg(aux.roff + p0 + j) - b * cp.seg;
+        const int w = __ldg(nnb + p0 + j);
+        roff[j] = r0 >> 2;
+        const int all = pad4(row_len(w)) >> 2, nearc = ((w & 0xffff) + 3) >> 2;
+        // chunks visited: the near prefix (soft-core-only owners, decided below) or all
+        vpre[j] = (all << 16) | nearc;
+    }
+    if (t == 0) roff[n_own] = meta.y >> 2;
     anyA = __syncthreads_or(anyA);
     if (t == 0 && useA) aux.hasA[b] = 0;  // ready for the next step
-    const int nch = meta.y >> 2;
+    for (int j = t; j < n_own; j += SC_TPB) {
+        const int v = vpre[j];
+        const bool fast = !M::fp64 && !anyA && get_s(spos[ownm[j]]) == (real)0;
+        vpre[j] = fast ? (v & 0xffff) : (v >> 16);
+    }
+    const int nch = scan_in_place(vpre, n_own, sw);
     const uint2* L = reinterpret_cast<const uint2*>(nbr + (size_t)b * cp.seg);
     const int per = (nch + SC_TPB - 1) / SC_TPB;
     const int c0 = min(nch, t * per), c1 = min(nch, c0 + per);
     int jfirst = -1, jlast = -1;
     if (c0 < c1) {
-        // owner of chunk c0: the largest j with roff[j] <= 4 c0
+        // owner of visited chunk c0: the largest j with vpre[j] <= c0
         int j = 0;
         {
             int hi = n_own - 1;
             while (j < hi) {
                 const int mid = (j + hi + 1) >> 1;
-                if (roff[mid] <= 4 * c0) j = mid;
+                if (vpre[mid] <= c0) j = mid;
                 else hi = mid - 1;
             }
         }
         jfirst = j;
-        int jend = roff[j + 1] >> 2;
+        int jend = vpre[j + 1];
+        int cbase = roff[j] - vpre[j];  // physical chunk = visited chunk + cbase
         pos_t pi = spos[ownm[j]];
         real si = get_s(pi), Ai = sAj[ownm[j]];
+        bool fast = !M::fp64 && !anyA && si == (real)0;
         real fx = 0, fy = 0, fz = 0;
 #pragma unroll 4
         for (int cc = c0; cc < c1; ++cc) {
-            const uint2 v = __ldg(L + cc);
             if (cc >= jend) {
                 if (j == jfirst) {
                     hF[0][t] = fx;
@@ -1254,17 +1291,20 @@ __global__ void __launch_bounds__(SC_TPB) k_force(int n, Geom g, Coef c, const t
                 }
                 do {
                     ++j;
-                    jend = roff[j + 1] >> 2;
+                    jend = vpre[j + 1];
                 } while (cc >= jend);
+                cbase = roff[j] - vpre[j];
                 pi = spos[ownm[j]];
                 si = get_s(pi);
                 Ai = sAj[ownm[j]];
+                fast = !M::fp64 && !anyA && si == (real)0;
                 fx = fy = fz = 0;
             }
+            const uint2 v = __ldg(L + cc + cbase);
             int h[4];
             unpack4(v, h);
             if constexpr (!M::fp64) {
-                if (!anyA && si == 0.0f) {
+                if (fast) {
                     // soft core only: g / r = K (r^2 - r_r^2), r^2 in units of (L / 2^32)^2
                     const float kc = c.Er4f * c.rr2invf * g.s32sq, rr2u = (float)c.rr2_fix;
                     float gx = 0.0f, gy = 0.0f, gz = 0.0f;
@@ -1311,7 +1351,7 @@ __global__ void __launch_bounds__(SC_TPB) k_force(int n, Geom g, Coef c, const t
     jl[t] = jlast;
     __syncthreads();
     for (int j = t; j < n_own; j += SC_TPB) {
-        const int cs = roff[j] >> 2, ce = roff[j + 1] >> 2;
+        const int cs = vpre[j], ce = vpre[j + 1];
         real f[3] = {0, 0, 0};
         if (cs < ce) {
             const int ta = cs / per, tb = (ce - 1) / per;
@@ -1537,7 +1577,7 @@ __global__ void __launch_bounds__(RED_TPB) k_reduce_final(int nb, const double* 
 
 // ================================================================ state I/O
 // Caller order [n][3] doubles -> internal state in sorted order, and the
-// fixed-point words.  FP32 mode: X = round(x 2^52 / L) (int64), V = two-float.
+// fixed-point words.  FP32 mode: X = round(x 2^52 / L) and V = round(v 2^40) (int64).
 template <class M>
 __global__ void __launch_bounds__(TPB) k_load_state(int n, Geom g, const double* __restrict__ pos_in,
                                                     const double* __restrict__ vel_in, const int* __restrict__ id,
@@ -1565,8 +1605,7 @@ __global__ void __launch_bounds__(TPB) k_load_state(int n, Geom g, const double*
             ((long long*)xs)[(size_t)d * n + i] = P;
             w[d] = ModeF32::word(P);
             const double v = vel_in ? vel_in[3 * (size_t)o + d] : 0.0;
-            const float vh = (float)v;
-            ((float2*)vs)[(size_t)d * n + i] = make_float2(vh, (float)(v - (double)vh));
+            ((long long*)vs)[(size_t)d * n + i] = __double2ll_rn(v * 1099511627776.0);  // 2^40
         }
         pos[i] = make_int4(w[0], w[1], w[2], 0);
     }
@@ -1588,8 +1627,7 @@ __global__ void __launch_bounds__(TPB) k_store_state(int n, Geom g, const int* _
             v = ((const double*)vs)[(size_t)d * n + i];
         } else {
             x = (double)((const long long*)xs)[(size_t)d * n + i] * (g.s32d[d] * 9.5367431640625e-07);  // L / 2^52
-            const float2 vv = ((const float2*)vs)[(size_t)d * n + i];
-            v = (double)vv.x + (double)vv.y;
+            v = (double)((const long long*)vs)[(size_t)d * n + i] * 9.094947017729282e-13;  // 2^-40
         }
         if (pos_out) pos_out[3 * (size_t)o + d] = x;
         if (vel_out) vel_out[3 * (size_t)o + d] = v;
