@@ -104,8 +104,9 @@ struct vbc_system {
     int* stage_idx = nullptr;   // [nsc][smax] sorted index of each staged particle (list build)
     int2* gmeta = nullptr;      // [nsc] staged particles and padded list entries per group
     int* roff_g = nullptr;      // [n] row offset of each particle in its group's segment
-    int* near_k = nullptr;      // [n][NEAR_K] near neighbours kept for the saturation test
-    int* hasA = nullptr;        // [nsc] groups that stage a window particle (k_chain -> k_force)
+    int* close_k = nullptr;     // [n][CLOSE_K] near entries as sorted indices (count, soft-core force)
+    void* fcore = nullptr;      // [n] forces and tags, float4 or F64x4 (k_count_near, k_force_rows -> k_step)
+    int* glist = nullptr;       // [n] particles whose force k_force_rows forms
     int rows_grid = 0;          // blocks of the count's full-row walk
     int chain_grid = 0;         // blocks of the list-walking grids (count rows, chain-rule pass)
     void *ds = nullptr, *sA = nullptr;
@@ -145,11 +146,10 @@ struct vbc_system {
     size_t real_bytes() const { return prec == VBC_FP64 ? sizeof(double) : sizeof(float); }
     SuperGrid grid() const { return SuperGrid{morton_rank, sc_org, cell_start}; }
     SuperCaps caps() const { return SuperCaps{smax, omax, seg, cap}; }
-    GroupAux aux() const { return GroupAux{stage_idx, gmeta, roff_g, near_k, hasA}; }
+    GroupAux aux() const { return GroupAux{stage_idx, gmeta, roff_g, close_k, fcore, glist}; }
     // dynamic shared memory of each kernel family
     size_t smem_nlist() const { return nlist_layout(caps(), pos_bytes()).total; }
     size_t smem_nlist_rel() const { return nlist_layout(caps(), sizeof(float4)).total; }
-    size_t smem_force() const { return force_layout(caps(), pos_bytes(), real_bytes()).total; }
     size_t smem_energy() const { return pass_layout(caps(), pos_bytes(), sizeof(double2)).total; }
     size_t smem_store() const { return al16((size_t)(omax + 1) * 4); }
 };
@@ -341,7 +341,7 @@ void free_all(vbc_system* s)
     dfree(s->nbr); dfree(s->scratch); dfree(s->nnb); dfree(s->cell_of); dfree(s->slot_of); dfree(s->order);
     dfree(s->cell_count); dfree(s->cell_start); dfree(s->morton_rank); dfree(s->sc_org);
     dfree(s->chunk_sum); dfree(s->wpart); dfree(s->ulist); dfree(s->stage_idx); dfree(s->gmeta); dfree(s->roff_g);
-    dfree(s->near_k); dfree(s->hasA);
+    dfree(s->close_k); dfree(s->fcore); dfree(s->glist);
     dfree(s->ds); dfree(s->sA); dfree(s->st); dfree(s->partial); dfree(s->ppairs); dfree(s->red);
     dfree(s->win); dfree(s->e_sd); dfree(s->e_A);
     if (s->st_host) cudaFreeHost(s->st_host);
@@ -370,7 +370,7 @@ int set_smem(F* func, size_t bytes)
 template <class M>
 int configure_smem(vbc_system* s)
 {
-    if (s->smem_force() > MAX_SMEM || s->smem_nlist() > MAX_SMEM || s->smem_energy() > MAX_SMEM)
+    if (s->smem_nlist() > MAX_SMEM || s->smem_energy() > MAX_SMEM)
         return fail(VBC_ERR_UNSTABLE,
                     "a cell group's neighbourhood (%d staged, %d own particles, %d list entries) does not fit in "
                     "shared memory: the system is too dense",
@@ -378,10 +378,6 @@ int configure_smem(vbc_system* s)
     if (s->smem_nlist_rel() > MAX_SMEM) return fail(VBC_ERR_UNSTABLE, "list build staging too large");
     VBC_TRY(set_smem(k_nlist<M, false>, s->smem_nlist()));
     if constexpr (!M::fp64) VBC_TRY(set_smem(k_nlist<M, true>, s->smem_nlist_rel()));
-    VBC_TRY(set_smem(k_force<M, EPI_FORCE>, s->smem_force()));
-    VBC_TRY(set_smem(k_force<M, EPI_START>, s->smem_force()));
-    VBC_TRY(set_smem(k_force<M, EPI_FINISH>, s->smem_force()));
-    VBC_TRY(set_smem(k_force<M, EPI_FINISH_START>, s->smem_force()));
     VBC_TRY(set_smem(k_count_e<M>, s->smem_energy()));
     VBC_TRY(set_smem(k_chain_e<M>, s->smem_energy()));
     VBC_TRY(set_smem(k_energy<M>, s->smem_energy()));
@@ -434,8 +430,8 @@ int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window)
     {
         Timed t(s, VBC_K_COUNT);
         k_count_near<M><<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>((int)s->n, s->geom, s->coef, pos, s->aux(),
-                                                                       (real*)s->ds, (real2*)s->sA, out, s->ulist,
-                                                                       s->st);
+                                                                       s->nnb, (real*)s->ds, (real2*)s->sA, out,
+                                                                       s->ulist, s->st);
         k_count_rows<M><<<s->rows_grid, TPB, 0, s->stream>>>(s->geom, s->coef, pos, s->caps(), s->aux(), s->nbr,
                                                                s->nnb, s->id, (real*)s->ds, (real2*)s->sA, out,
                                                                s->ulist, s->wpart, s->st);
@@ -444,7 +440,7 @@ int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window)
         Timed t(s, VBC_K_CHAIN);
         k_chain<M><<<s->chain_grid, SC_TPB, 0, s->stream>>>(s->geom, s->coef, pos, s->caps(), s->aux(), s->nbr,
                                                             s->nnb, (const real*)s->ds, (real2*)s->sA, s->wpart,
-                                                            s->morton_rank, s->st);
+                                                            s->st);
     }
     return check_launch(s, 3);
 }
@@ -459,11 +455,12 @@ int enqueue_force(vbc_system* s, const StepArgs& a)
     pos_t* pos_next = (pos_t*)s->pos[s->cur ^ 1];
     {
         Timed t(s, VBC_K_FORCE);
-        k_force<M, EPI><<<s->nsc, SC_TPB, s->smem_force(), s->stream>>>(
-            n, s->geom, s->coef, pos, s->grid(), s->caps(), s->nbr, s->nnb, s->id, (const real2*)s->sA, pos_next,
-            (const pos_t*)s->xref, s->aux(), a, s->st);
+        k_force_rows<M><<<s->rows_grid, TPB, 0, s->stream>>>(s->geom, s->coef, pos, s->caps(), s->aux(), s->nbr,
+                                                              s->nnb, (const real2*)s->sA, s->st);
+        k_step<M, EPI><<<blocks_for(n, TPB), TPB, 0, s->stream>>>(n, s->geom, s->aux(), s->id, pos_next,
+                                                                  (const pos_t*)s->xref, a, s->st);
     }
-    VBC_TRY(check_launch(s));
+    VBC_TRY(check_launch(s, 2));
     if (EPI == EPI_START || EPI == EPI_FINISH_START) s->cur ^= 1;
     return VBC_OK;
 }
@@ -565,7 +562,7 @@ int compute_impl(vbc_system* s, double* F_dev, double* n_dev, bool energy)
 {
     for (int attempt = 0;; ++attempt) {
         VBC_CUDA(cudaMemsetAsync(s->win, 0, sizeof(long long), s->stream));
-        VBC_CUDA(cudaMemsetAsync(&s->st->nwin, 0, 2 * sizeof(int), s->stream));  // nwin and nu
+        VBC_CUDA(cudaMemsetAsync(&s->st->nwin, 0, 3 * sizeof(int), s->stream));  // nwin, nu, ngen
         VBC_TRY(enqueue_rebuild<M>(s));
         VBC_TRY(enqueue_count_chain<M>(s, n_dev, true));
         StepArgs a{};
@@ -694,7 +691,8 @@ int launch_pair_graph(vbc_system* s, const StepArgs& a)
     if (!pg.exec || pg.dt != a.dt || pg.c1 != a.c1 || pg.c2 != a.c2 || pg.layout_version != s->layout_version)
         VBC_TRY(build_pair_graph<M>(s, s->cur, a));
     VBC_CUDA(cudaGraphLaunch(pg.exec, s->stream));
-    s->launches += 10;  // two gates, two count/count/chain/force sets (rebuild bodies counted on the device)
+    s->launches += 12;  // two gates, two sets of count, count rows, chain, force rows, step (rebuild bodies
+                        // counted on the device)
     return VBC_OK;
 }
 
@@ -971,8 +969,9 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     ALLOC(dalloc(s->stage_idx, (size_t)s->nsc * s->smax));
     ALLOC(dalloc(s->gmeta, (size_t)s->nsc));
     ALLOC(dalloc(s->roff_g, n));
-    ALLOC(dalloc(s->near_k, (size_t)NEAR_K * n));
-    ALLOC(dalloc(s->hasA, (size_t)s->nsc));
+    ALLOC(dalloc(s->close_k, (size_t)CLOSE_K * n));
+    ALLOC(dalloc_bytes(s->fcore, n * (s->prec == VBC_FP64 ? sizeof(F64x4) : sizeof(float4))));
+    ALLOC(dalloc(s->glist, n));
     ALLOC(dalloc_bytes(s->ds, n * s->real_bytes()));
     ALLOC(dalloc_bytes(s->sA, n * 2 * s->real_bytes()));
     ALLOC(dalloc(s->st, 1));
@@ -1015,7 +1014,6 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     }
     if (cudaMemsetAsync(s->cell_count, 0, (size_t)s->npad * sizeof(int), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->st, 0, sizeof(Status), s->stream) != cudaSuccess ||
-        cudaMemsetAsync(s->hasA, 0, (size_t)s->nsc * sizeof(int), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->nnb, 0, n * sizeof(int), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->sA, 0, n * 2 * s->real_bytes(), s->stream) != cudaSuccess)
         return bail(fail(VBC_ERR_CUDA, "initial memset failed"));

@@ -85,8 +85,10 @@ struct Status {
     long long step_base;// noise counter of iteration 0 of the current call
     long long graph_rebuild_runs;  // rebuild bodies a graph conditional executed
     int nwin;           // window particles listed by the last count (k_count_rows)
-    int nu;             // particles the last count walked in full: not saturated by their kept near
+    int nu;             // particles the last count walked in full: not saturated by their kept close
                         // neighbours (k_count_near)
+    int ngen;           // particles whose force k_force_rows forms (k_count_near, k_chain)
+    int pad2;
 };
 
 // Work stops (until the host intervenes) once any of these is raised.

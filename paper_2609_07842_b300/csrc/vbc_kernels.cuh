@@ -264,13 +264,14 @@ struct SuperCaps {
 };
 
 // Tables the list build leaves for the passes.
-constexpr int NEAR_K = 8;  // near neighbours kept per particle for the saturation test
+constexpr int CLOSE_K = 12;  // close entries kept per particle as sorted indices
 struct GroupAux {
     int* stage_idx;  // [groups][smax] sorted index of each staged particle
     int2* meta;      // [groups] (staged particles, padded list entries)
     int* roff;       // [n] start of each particle's row in nbr (group * seg + offset in its segment)
-    int* near;       // [n][NEAR_K] sorted indices of up to NEAR_K near neighbours, -1 for none
-    int* hasA;       // [groups] 1: the group stages a window particle (set by k_chain, cleared by k_force)
+    int* close;      // [n][CLOSE_K] sorted indices of close entries (near, then far within r_l), -1 for none
+    void* fcore;     // [n] force and tag, float4 (FP32 mode) or F64x4 (w = 1: the particle's whole force)
+    int* glist;      // [n] particles whose force the list-walking pass forms (k_count_near, k_chain)
 };
 
 struct SuperTab {
@@ -605,30 +606,33 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
         nnb[p] = nn | (nf << 16);
         rnn[j] = nn | (nf << 16);
         {
-            // up to NEAR_K neighbours within r_l at the build (near entries first), as sorted
-            // indices, for the saturation test of the count
-            int* nv = aux.near + (size_t)NEAR_K * p;
+            // up to CLOSE_K close entries as sorted indices: the near entries, then far entries
+            // within r_l at the build (for the per-particle count and soft-core force; a row
+            // with more near entries takes the list-walking force path)
+            int* cv = aux.close + (size_t)CLOSE_K * p;
             int cnt = 0;
-            for (int e = 0; e < len && e < cp.cap && cnt < NEAR_K; ++e) {
+            for (int e = 0; e < len && e < cp.cap && cnt < CLOSE_K; ++e) {
                 const int m = e < nn ? row[e] : row[cp.cap - 1 - (e - nn)];
-                bool in;
-                if constexpr (REL) {
-                    const float4 q = spos[m];
-                    const float dx = pi.x - q.x, dy = pi.y - q.y, dz = pi.z - q.z;
-                    in = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz)) <= lp.rl2_f;
-                } else if constexpr (M::fp64) {
-                    double dx, dy, dz;
-                    ModeF64::delta64(pi, spos[m], g, dx, dy, dz);
-                    in = dx * dx + dy * dy + dz * dz <= lp.rl2;
-                } else {
-                    const int dx = pi.x - spos[m].x, dy = pi.y - spos[m].y, dz = pi.z - spos[m].z;
-                    in = (unsigned long long)((long long)dx * dx) + (unsigned long long)((long long)dy * dy) +
-                             (unsigned long long)((long long)dz * dz) <=
-                         lp.rl2_fix;
+                bool in = e < nn;
+                if (!in) {
+                    if constexpr (REL) {
+                        const float4 q = spos[m];
+                        const float dx = pi.x - q.x, dy = pi.y - q.y, dz = pi.z - q.z;
+                        in = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz)) <= lp.rl2_f;
+                    } else if constexpr (M::fp64) {
+                        double dx, dy, dz;
+                        ModeF64::delta64(pi, spos[m], g, dx, dy, dz);
+                        in = dx * dx + dy * dy + dz * dz <= lp.rl2;
+                    } else {
+                        const int dx = pi.x - spos[m].x, dy = pi.y - spos[m].y, dz = pi.z - spos[m].z;
+                        in = (unsigned long long)((long long)dx * dx) + (unsigned long long)((long long)dy * dy) +
+                                 (unsigned long long)((long long)dz * dz) <=
+                             lp.rl2_fix;
+                    }
                 }
-                if (in) nv[cnt++] = staged_index(T, m);
+                if (in) cv[cnt++] = staged_index(T, m);
             }
-            for (int k = cnt; k < NEAR_K; ++k) nv[k] = -1;
+            for (int k = cnt; k < CLOSE_K; ++k) cv[k] = -1;
         }
         roff[j] = pad4(len);
         over |= len > cp.cap;
@@ -690,259 +694,6 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
             h[u] = e < nn ? row[e] : (e < len ? row[cp.cap - 1 - (e - nn)] : self);
         }
         out[c] = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
-    }
-}
-
-// ================================================================ pass 1: counts
-// FP32-split: neighbours with r <= r_l add exactly 1 (an integer); window
-// neighbours add omega in 2^-31 fixed point (window_weight_fix31).  The
-// threshold test t = n - (f - delta) is taken in the same fixed point, so
-// s_i and s'_i carry only the error of the window terms, and the integer sums
-// do not depend on the order of the terms.
-// Saturation: when up to NEAR_K near neighbours kept by the list build
-// already hold at least ceil(f - delta + 1) neighbours with r <= r_l, then
-// n_i >= f - delta + 1 whatever the other entries add, so s_i = s'_i = 0
-// exactly and nothing else is needed (unless the counts themselves are
-// requested).  k_count_near tests that, one thread per particle, with direct
-// loads of those few neighbours, and lists the particles it cannot settle;
-// k_count_rows then walks their full rows, one warp per particle and one lane
-// per entry, reading neighbours through the group's staged-index table.
-// Both write s_i also into the spare word of the particle's position, where
-// the force pass stages it.
-struct CountOut {
-    double* n_out;         // counts in caller order, or null
-    long long* in_window;  // counter of window particles, or null
-};
-
-__device__ __forceinline__ void switch_from_fix(long long T, float& s, float& ds)
-{
-    if (T <= 0) {
-        s = 1.0f;
-        ds = 0.0f;
-    } else if (T >= 2147483648LL) {
-        s = 0.0f;
-        ds = 0.0f;
-    } else {
-        const float t = (float)T * 4.656612873077393e-10f;  // 2^-31
-        const float q = 1.0f - t * t;
-        s = q * q;
-        ds = -4.0f * t * q;
-    }
-}
-
-__device__ __forceinline__ unsigned long long r2_fix(const int4& a, const int4& b)
-{
-    const int dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
-    return (unsigned long long)((long long)dx * dx) + (unsigned long long)((long long)dy * dy) +
-           (unsigned long long)((long long)dz * dz);
-}
-
-// Squared separation for the FP64 paths.
-template <class M>
-__device__ __forceinline__ double r2_d(const typename M::pos_t& a, const typename M::pos_t& b, const Geom& g)
-{
-    double dx, dy, dz;
-    M::delta64(a, b, g, dx, dy, dz);
-    return dx * dx + dy * dy + dz * dz;
-}
-
-// s_i into the spare word of a position.
-__device__ __forceinline__ void put_w(int4* p, float s) { reinterpret_cast<int*>(p)[3] = __float_as_int(s); }
-__device__ __forceinline__ void put_w(P64* p, double s)
-{
-    reinterpret_cast<unsigned long long*>(p)[3] = (unsigned long long)__double_as_longlong(s);
-}
-
-template <class M>
-__global__ void __launch_bounds__(TPB) k_count_near(int n, Geom g, Coef c, typename M::pos_t* __restrict__ pos,
-                                                    GroupAux aux, typename M::real* __restrict__ ds_out,
-                                                    typename M::real2* __restrict__ sA, CountOut out,
-                                                    int* __restrict__ ulist, Status* st)
-{
-    using pos_t = typename M::pos_t;
-    using real = typename M::real;
-    using real2 = typename M::real2;
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->rebuild = 0;
-    if (halted(st)) return;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    long long full = 0;
-    if (!out.n_out) {
-        const pos_t pi = pos[p];
-        const int4* nv = reinterpret_cast<const int4*>(aux.near) + 2 * (size_t)p;
-        const int4 a0 = __ldg(nv), a1 = __ldg(nv + 1);
-        const int q[NEAR_K] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        pos_t pj[NEAR_K];
-#pragma unroll
-        for (int k = 0; k < NEAR_K; ++k)
-            if (q[k] >= 0) pj[k] = pos[q[k]];
-#pragma unroll
-        for (int k = 0; k < NEAR_K; ++k) {
-            if (q[k] < 0) continue;
-            if constexpr (M::fp64) full += r2_d<M>(pi, pj[k], g) <= c.rl2;
-            else full += r2_fix(pi, pj[k]) <= c.rl2_fix;
-        }
-    }
-    if (!out.n_out && full >= c.sat_full) {
-        ds_out[p] = (real)0;
-        sA[p] = real2{(real)0, (real)0};
-        put_w(pos + p, (real)0);
-    } else {
-        ulist[atomicAdd(&st->nu, 1)] = p;
-    }
-}
-
-template <class M>
-__global__ void __launch_bounds__(TPB) k_count_rows(Geom g, Coef c, typename M::pos_t* __restrict__ pos,
-                                                    SuperCaps cp, GroupAux aux, const uint16_t* __restrict__ nbr,
-                                                    const int* __restrict__ nnb, const int* __restrict__ id,
-                                                    typename M::real* __restrict__ ds_out,
-                                                    typename M::real2* __restrict__ sA, CountOut out,
-                                                    const int* __restrict__ ulist, int* __restrict__ wpart,
-                                                    Status* st)
-{
-    using pos_t = typename M::pos_t;
-    using real = typename M::real;
-    using real2 = typename M::real2;
-    if (halted(st)) return;
-    const int nu = st->nu;
-    const int lane = threadIdx.x & 31;
-    for (int k = (int)((blockIdx.x * TPB + threadIdx.x) >> 5); k < nu; k += (int)((gridDim.x * TPB) >> 5)) {
-        const int p = ulist[k];
-        const int ra = __ldg(aux.roff + p), b = ra / cp.seg;
-        const int len = row_len(__ldg(nnb + p));
-        const pos_t pi = pos[p];
-        const uint16_t* row = nbr + ra;
-        const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
-        real s, ds;
-        double n_val;
-        if constexpr (M::fp64) {
-            double acc = 0.0;
-            for (int e = lane; e < len; e += 32) {
-                const double r2 = r2_d<M>(pi, pos[__ldg(sidx + __ldg(row + e))], g);
-                if (r2 < c.rh2) acc += r2 <= c.rl2 ? 1.0 : omega_d(sqrt(r2), c.r_l, c.r_h);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            s = omega_d(acc, c.fd, c.fd + 1.0);
-            ds = domega_d(acc, c.fd, c.fd + 1.0);
-            n_val = acc;
-        } else {
-            long long full = 0;
-            unsigned long long q = 0;
-            for (int e = lane; e < len; e += 32) {
-                const unsigned long long r2 = r2_fix(pi, pos[__ldg(sidx + __ldg(row + e))]);
-                if (r2 < c.rh2_fix) {
-                    if (r2 <= c.rl2_fix) ++full;
-                    else q += window_weight_fix31(r2, r2 - c.rl2_fix, c.rl_s, c.w_s);
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                full += __shfl_xor_sync(0xffffffffu, full, o);
-                q += __shfl_xor_sync(0xffffffffu, q, o);
-            }
-            const long long Tf = (full - c.fd_int) * 2147483648LL + (long long)q - c.fd_frac_fix;
-            switch_from_fix(Tf, s, ds);
-            n_val = 0.0;
-            if (out.n_out) n_val = (double)full + (double)q * 4.656612873077393e-10;
-        }
-        if (lane == 0) {
-            ds_out[p] = ds;
-            sA[p] = real2{s, (real)0};
-            put_w(pos + p, s);
-            if (out.n_out) out.n_out[id[p]] = n_val;
-            if (ds != (real)0) {
-                // the chain-rule pass visits the window particles listed here
-                wpart[atomicAdd(&st->nwin, 1)] = p;
-                if (out.in_window) atomicAdd((unsigned long long*)out.in_window, 1ull);
-            }
-        }
-    }
-}
-
-// ================================================================ chain-rule pass
-// A_i = s'_i sum_j s_j V_a(r_ij) for the particles inside the switching
-// window (s'_i != 0) that k_count listed, one warp per particle, neighbours
-// read through their group's staged-index table.  A fixed grid walks the
-// list, so a step without window particles costs one launch that reads one
-// counter.
-// Marks every cell group whose staging holds the cell (cx, cy, cz): the groups
-// with origin x0 in [cx - BXC, cx + 1] (multiples of BXC, modulo the padded
-// grid), and likewise in y and z.
-__device__ __forceinline__ void mark_groups(int cx, int cy, int cz, const Geom& g, const int* __restrict__ morton_rank,
-                                            int* __restrict__ hasA)
-{
-    const int pc[3] = {(g.nc[0] + BXC - 1) / BXC * BXC, (g.nc[1] + BYC - 1) / BYC * BYC,
-                       (g.nc[2] + BZC - 1) / BZC * BZC};
-    const int bc[3] = {BXC, BYC, BZC}, cc[3] = {cx, cy, cz};
-    int o[3][2], no[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        // staged columns of a group at x0 are x0 - 1 .. x0 + bc, wrapped on the real grid
-        no[a] = 0;
-        for (int x0 = 0; x0 < pc[a] && no[a] < 2; x0 += bc[a]) {
-            bool hit = false;
-            for (int l = -1; l <= bc[a]; ++l) {
-                int x = x0 + l;
-                x = x < 0 ? x + g.nc[a] : (x >= g.nc[a] ? x - g.nc[a] : x);
-                hit |= x == cc[a];
-            }
-            if (hit) o[a][no[a]++] = x0;
-        }
-    }
-    for (int i = 0; i < no[0]; ++i)
-        for (int j = 0; j < no[1]; ++j)
-            for (int k = 0; k < no[2]; ++k) {
-                const int lin = (o[2][k] * g.nc[1] + o[1][j]) * g.nc[0] + o[0][i];
-                hasA[__ldg(morton_rank + lin) / OWN_CELLS] = 1;
-            }
-}
-
-template <class M>
-__global__ void __launch_bounds__(SC_TPB) k_chain(Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
-                                                  SuperCaps cp, GroupAux aux, const uint16_t* __restrict__ nbr,
-                                                  const int* __restrict__ nnb, const typename M::real* __restrict__ ds,
-                                                  typename M::real2* __restrict__ sA, const int* __restrict__ wpart,
-                                                  const int* __restrict__ morton_rank, const Status* st)
-{
-    using pos_t = typename M::pos_t;
-    using real = typename M::real;
-    if (halted(st)) return;
-    const int nw = st->nwin;
-    const int lane = threadIdx.x & 31;
-    const real* s_only = reinterpret_cast<const real*>(sA);  // s_j at even offsets (A is written here)
-    for (int k = (int)((blockIdx.x * SC_TPB + threadIdx.x) >> 5); k < nw; k += (int)((gridDim.x * SC_TPB) >> 5)) {
-        const int p = wpart[k];
-        const int ra = __ldg(aux.roff + p), b = ra / cp.seg;
-        const int len = row_len(__ldg(nnb + p));
-        const pos_t pi = pos[p];
-        const uint16_t* row = nbr + ra;
-        const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
-        real acc = 0;
-        for (int e = lane; e < len; e += 32) {
-            const int jj = __ldg(sidx + __ldg(row + e));
-            if constexpr (M::fp64) {
-                const double r2 = r2_d<M>(pi, pos[jj], g);
-                if (r2 > c.rr2 && r2 < c.ra2) acc += s_only[2 * (size_t)jj] * Va_d(sqrt(r2), c);
-            } else {
-                const unsigned long long r2i = r2_fix(pi, pos[jj]);
-                if (r2i > c.rr2_fix && r2i < c.ra2_fix) {
-                    const float r2 = u64_to_float(r2i) * g.s32sq;
-                    const float r = sqrtf(r2);
-                    const float uu = s64_to_float((long long)r2i - (long long)c.rm2_fix) * c.s2hinv / (r + c.rmf);
-                    const float q = 1.0f - uu * uu;
-                    acc += s_only[2 * (size_t)jj] * (-c.Eaf * q * q);
-                }
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) {
-            sA[p].y = ds[p] * acc;
-            const int3 cl = cell_of_pos<M>(pi, g);
-            mark_groups(cl.x, cl.y, cl.z, g, morton_rank, aux.hasA);
-        }
     }
 }
 
@@ -1158,230 +909,356 @@ __device__ __forceinline__ void pair_f64(const P64& pi, double si, double Ai, co
 }
 
 
-// Pass 2, one block per cell group.  The block stages its neighbourhood
-// through the table of sorted indices the list build left.  Its list entries
-// are cut into 4-entry chunks (rows are padded to a multiple of 4).  An owner
-// with s_i = 0, in a block where no staged particle has A_j != 0, can have no
-// well or window term: only soft-core pairs, all of them near entries (see
-// the near/far split of the lists), so only the chunks holding its near
-// prefix are visited, with the soft-core-only arithmetic.  Other owners visit
-// all their chunks with every term.  The visited chunks of the block are
-// numbered consecutively (owner by owner) and each thread takes an equal
-// contiguous run of them, so it meets few owners and adds its chunks in
-// registers.  A run's first and last owners may continue in the neighbouring
-// runs: their partial forces go to per-thread head and tail slots, owners
-// wholly inside a run are written directly, and each own particle then adds
-// its pieces in thread order -- deterministic, no atomics.  Per pair in the
-// general FP32 path, the exact integer r^2 decides which terms can be nonzero
-// (core overlap r < r_r; the well, only if s_i s_j != 0; the counting window,
-// only if A_i + A_j != 0), and the arguments of the steep well and of the
-// window come from exact integer differences r^2 - r_m^2 and r^2 - r_l^2.
-template <class M, int EPI>
-__global__ void __launch_bounds__(SC_TPB) k_force(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
-                                                  SuperGrid G, SuperCaps cp, const uint16_t* __restrict__ nbr,
-                                                  const int* __restrict__ nnb, const int* __restrict__ id,
-                                                  const typename M::real2* __restrict__ sA,
-                                                  typename M::pos_t* __restrict__ pos_next,
-                                                  const typename M::pos_t* __restrict__ xref, GroupAux aux, StepArgs a,
+// ================================================================ pass 1: counts
+// FP32-split: neighbours with r <= r_l add exactly 1 (an integer); window
+// neighbours add omega in 2^-31 fixed point (window_weight_fix31).  The
+// threshold test t = n - (f - delta) is taken in the same fixed point, so
+// s_i and s'_i carry only the error of the window terms, and the integer sums
+// do not depend on the order of the terms.
+// Saturation: when the close neighbours kept by the list build (up to
+// CLOSE_K near entries) hold at least ceil(f - delta + 1) neighbours with r <= r_l, then
+// n_i >= f - delta + 1 whatever the other entries add, so s_i = s'_i = 0
+// exactly and nothing else is needed (unless the counts themselves are
+// requested).  k_count_near tests that, one thread per particle, with direct
+// loads of those few neighbours, and lists the particles it cannot settle;
+// k_count_rows then walks their full rows, one warp per particle and one lane
+// per entry, reading neighbours through the group's staged-index table.
+// Both write s_i also into the spare word of the particle's position, where
+// the force pass stages it.
+struct CountOut {
+    double* n_out;         // counts in caller order, or null
+    long long* in_window;  // counter of window particles, or null
+};
+
+__device__ __forceinline__ void switch_from_fix(long long T, float& s, float& ds)
+{
+    if (T <= 0) {
+        s = 1.0f;
+        ds = 0.0f;
+    } else if (T >= 2147483648LL) {
+        s = 0.0f;
+        ds = 0.0f;
+    } else {
+        const float t = (float)T * 4.656612873077393e-10f;  // 2^-31
+        const float q = 1.0f - t * t;
+        s = q * q;
+        ds = -4.0f * t * q;
+    }
+}
+
+__device__ __forceinline__ unsigned long long r2_fix(const int4& a, const int4& b)
+{
+    const int dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+    return (unsigned long long)((long long)dx * dx) + (unsigned long long)((long long)dy * dy) +
+           (unsigned long long)((long long)dz * dz);
+}
+
+// Squared separation for the FP64 paths.
+template <class M>
+__device__ __forceinline__ double r2_d(const typename M::pos_t& a, const typename M::pos_t& b, const Geom& g)
+{
+    double dx, dy, dz;
+    M::delta64(a, b, g, dx, dy, dz);
+    return dx * dx + dy * dy + dz * dz;
+}
+
+// s_i into the spare word of a position.
+__device__ __forceinline__ void put_w(int4* p, float s) { reinterpret_cast<int*>(p)[3] = __float_as_int(s); }
+__device__ __forceinline__ void put_w(P64* p, double s)
+{
+    reinterpret_cast<unsigned long long*>(p)[3] = (unsigned long long)__double_as_longlong(s);
+}
+
+// Force and tag of a particle: float4 in the FP32 mode, F64x4 in FP64.
+struct __align__(32) F64x4 {
+    double x, y, z, w;
+};
+
+// k_count_near also forms, in the FP32 mode, the soft-core force of its
+// particle from the same close neighbours.  Every pair inside the soft core
+// is a near entry, so for a particle whose near entries all fit the close
+// list the sum is its whole soft-core force; if the particle is saturated
+// too (s_i = s'_i = 0, hence A_i = 0), it has no well term and its window
+// terms need A_j != 0 of a neighbour -- which k_chain rules out by clearing
+// the tag of every list neighbour of a window particle.  Every other particle
+// goes on the list of k_force_rows.
+template <class M>
+__global__ void __launch_bounds__(TPB) k_count_near(int n, Geom g, Coef c, typename M::pos_t* __restrict__ pos,
+                                                    GroupAux aux, const int* __restrict__ nnb,
+                                                    typename M::real* __restrict__ ds_out,
+                                                    typename M::real2* __restrict__ sA, CountOut out,
+                                                    int* __restrict__ ulist, Status* st)
+{
+    using pos_t = typename M::pos_t;
+    using real = typename M::real;
+    using real2 = typename M::real2;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->rebuild = 0;
+    if (halted(st)) return;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    long long full = 0;
+    float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+    const int nn = __ldg(nnb + p) & 0xffff;
+    if (!out.n_out) {
+        const pos_t pi = pos[p];
+        const int4* cv = reinterpret_cast<const int4*>(aux.close) + (CLOSE_K / 4) * (size_t)p;
+        int q[CLOSE_K];
+#pragma unroll
+        for (int k = 0; k < CLOSE_K / 4; ++k) {
+            const int4 v = __ldg(cv + k);
+            q[4 * k] = v.x;
+            q[4 * k + 1] = v.y;
+            q[4 * k + 2] = v.z;
+            q[4 * k + 3] = v.w;
+        }
+        pos_t pj[CLOSE_K];
+#pragma unroll
+        for (int k = 0; k < CLOSE_K; ++k)
+            if (q[k] >= 0) pj[k] = pos[q[k]];
+        // soft core: g / r = K (r^2 - r_r^2), r^2 in units of (L / 2^32)^2
+        const float kc = c.Er4f * c.rr2invf * g.s32sq;
+#pragma unroll
+        for (int k = 0; k < CLOSE_K; ++k) {
+            if (q[k] < 0) continue;
+            if constexpr (M::fp64) {
+                full += r2_d<M>(pi, pj[k], g) <= c.rl2;
+            } else {
+                const unsigned long long r2i = r2_fix(pi, pj[k]);
+                full += r2i <= c.rl2_fix;
+                if (r2i < c.rr2_fix) {
+                    const float dx = (float)(pi.x - pj[k].x), dy = (float)(pi.y - pj[k].y),
+                                dz = (float)(pi.z - pj[k].z);
+                    const float gr = __fmaf_rn(kc, __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz)), -c.Er4f);
+                    fx = __fmaf_rn(-gr, dx, fx);
+                    fy = __fmaf_rn(-gr, dy, fy);
+                    fz = __fmaf_rn(-gr, dz, fz);
+                }
+            }
+        }
+    }
+    const bool sat = !out.n_out && full >= c.sat_full;
+    if (sat) {
+        ds_out[p] = (real)0;
+        sA[p] = real2{(real)0, (real)0};
+        put_w(pos + p, (real)0);
+    } else {
+        ulist[atomicAdd(&st->nu, 1)] = p;
+    }
+    const bool whole = !M::fp64 && sat && nn <= CLOSE_K;
+    if constexpr (M::fp64) {
+        static_cast<F64x4*>(aux.fcore)[p] = F64x4{0.0, 0.0, 0.0, 0.0};
+    } else {
+        static_cast<float4*>(aux.fcore)[p] = make_float4(fx * g.s32, fy * g.s32, fz * g.s32, whole ? 1.0f : 0.0f);
+    }
+    if (!whole) aux.glist[atomicAdd(&st->ngen, 1)] = p;
+}
+
+template <class M>
+__global__ void __launch_bounds__(TPB) k_count_rows(Geom g, Coef c, typename M::pos_t* __restrict__ pos,
+                                                    SuperCaps cp, GroupAux aux, const uint16_t* __restrict__ nbr,
+                                                    const int* __restrict__ nnb, const int* __restrict__ id,
+                                                    typename M::real* __restrict__ ds_out,
+                                                    typename M::real2* __restrict__ sA, CountOut out,
+                                                    const int* __restrict__ ulist, int* __restrict__ wpart,
+                                                    Status* st)
+{
+    using pos_t = typename M::pos_t;
+    using real = typename M::real;
+    using real2 = typename M::real2;
+    if (halted(st)) return;
+    const int nu = st->nu;
+    const int lane = threadIdx.x & 31;
+    for (int k = (int)((blockIdx.x * TPB + threadIdx.x) >> 5); k < nu; k += (int)((gridDim.x * TPB) >> 5)) {
+        const int p = ulist[k];
+        const int ra = __ldg(aux.roff + p), b = ra / cp.seg;
+        const int len = row_len(__ldg(nnb + p));
+        const pos_t pi = pos[p];
+        const uint16_t* row = nbr + ra;
+        const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
+        real s, ds;
+        double n_val;
+        if constexpr (M::fp64) {
+            double acc = 0.0;
+            for (int e = lane; e < len; e += 32) {
+                const double r2 = r2_d<M>(pi, pos[__ldg(sidx + __ldg(row + e))], g);
+                if (r2 < c.rh2) acc += r2 <= c.rl2 ? 1.0 : omega_d(sqrt(r2), c.r_l, c.r_h);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            s = omega_d(acc, c.fd, c.fd + 1.0);
+            ds = domega_d(acc, c.fd, c.fd + 1.0);
+            n_val = acc;
+        } else {
+            long long full = 0;
+            unsigned long long q = 0;
+            for (int e = lane; e < len; e += 32) {
+                const unsigned long long r2 = r2_fix(pi, pos[__ldg(sidx + __ldg(row + e))]);
+                if (r2 < c.rh2_fix) {
+                    if (r2 <= c.rl2_fix) ++full;
+                    else q += window_weight_fix31(r2, r2 - c.rl2_fix, c.rl_s, c.w_s);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                full += __shfl_xor_sync(0xffffffffu, full, o);
+                q += __shfl_xor_sync(0xffffffffu, q, o);
+            }
+            const long long Tf = (full - c.fd_int) * 2147483648LL + (long long)q - c.fd_frac_fix;
+            switch_from_fix(Tf, s, ds);
+            n_val = 0.0;
+            if (out.n_out) n_val = (double)full + (double)q * 4.656612873077393e-10;
+        }
+        if (lane == 0) {
+            ds_out[p] = ds;
+            sA[p] = real2{s, (real)0};
+            put_w(pos + p, s);
+            if (out.n_out) out.n_out[id[p]] = n_val;
+            if (ds != (real)0) {
+                // the chain-rule pass visits the window particles listed here
+                wpart[atomicAdd(&st->nwin, 1)] = p;
+                if (out.in_window) atomicAdd((unsigned long long*)out.in_window, 1ull);
+            }
+        }
+    }
+}
+
+// ================================================================ chain-rule pass
+// A_i = s'_i sum_j s_j V_a(r_ij) for the particles inside the switching
+// window (s'_i != 0) that k_count_rows listed, one warp per particle,
+// neighbours read through their group's staged-index table.  A fixed grid
+// walks the list, so a step without window particles costs one launch that
+// reads one counter.  Every list neighbour of a window particle loses its
+// whole-force tag (its window term needs A_i) and joins the general list.
+template <class M>
+__global__ void __launch_bounds__(SC_TPB) k_chain(Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
+                                                  SuperCaps cp, GroupAux aux, const uint16_t* __restrict__ nbr,
+                                                  const int* __restrict__ nnb, const typename M::real* __restrict__ ds,
+                                                  typename M::real2* __restrict__ sA, const int* __restrict__ wpart,
                                                   Status* st)
 {
     using pos_t = typename M::pos_t;
     using real = typename M::real;
-    // k_force raises `frozen` and `rebuild` itself; it tests `frozen` only through
-    // halted(), which a thread of this launch changes only on the error path
     if (halted(st)) return;
-    __shared__ real hF[3][SC_TPB], tF[3][SC_TPB];
-    __shared__ int jf[SC_TPB], jl[SC_TPB], sw[SC_TPB / 32];
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int t = threadIdx.x, b = blockIdx.x;
-    const int p0 = __ldg(G.cell_start + OWN_CELLS * b);
-    const int n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
-    const int2 meta = __ldg(aux.meta + b);
-    const int total = meta.x;
-    PState<M> ps;
-    if (t < n_own) load_pstate<M, EPI>(p0 + t, n, a, id, xref, ps);
-    const ForceLayout ly = force_layout(cp, sizeof(pos_t), sizeof(real));
-    pos_t* spos = (pos_t*)smem;
-    real* sAj = (real*)(smem + ly.sA);
-    int* roff = (int*)(smem + ly.roff);   // first chunk of each own row
-    int* vpre = (int*)(smem + ly.vpre);   // first visited chunk of each owner (block numbering)
-    uint16_t* ownm = (uint16_t*)(smem + ly.ownm);
-    real* oF = (real*)(smem + ly.oF);  // [3][omax]
-    // A_j can be nonzero only if the chain-rule pass flagged this group
-    const bool useA = __ldg(aux.hasA + b) != 0;
-    bool anyA = false;
-    {
-        // staging through the group's table of sorted indices, B loads in flight
-        constexpr int B = 4;
+    const int nw = st->nwin;
+    const int lane = threadIdx.x & 31;
+    const real* s_only = reinterpret_cast<const real*>(sA);  // s_j at even offsets (A is written here)
+    for (int k = (int)((blockIdx.x * SC_TPB + threadIdx.x) >> 5); k < nw; k += (int)((gridDim.x * SC_TPB) >> 5)) {
+        const int p = wpart[k];
+        const int ra = __ldg(aux.roff + p), b = ra / cp.seg;
+        const int len = row_len(__ldg(nnb + p));
+        const pos_t pi = pos[p];
+        const uint16_t* row = nbr + ra;
         const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
-        for (int m0 = t; m0 < total; m0 += SC_TPB * B) {
-            int jj[B];
-#pragma unroll
-            for (int u = 0; u < B; ++u) jj[u] = m0 + u * SC_TPB < total ? __ldg(sidx + m0 + u * SC_TPB) : -1;
-            pos_t v[B];
-            real A[B];
-#pragma unroll
-            for (int u = 0; u < B; ++u) {
-                if (jj[u] < 0) continue;
-                v[u] = pos[jj[u]];  // s_j is in the spare word
-                A[u] = useA ? sA[jj[u]].y : (real)0;
-            }
-#pragma unroll
-            for (int u = 0; u < B; ++u) {
-                if (jj[u] < 0) continue;
-                const int m = m0 + u * SC_TPB;
-                spos[m] = v[u];
-                sAj[m] = A[u];
-                anyA |= A[u] != (real)0;
-                // own particles are staged too (twice on very small grids: either copy will do)
-                if (jj[u] >= p0 && jj[u] < p0 + n_own) ownm[jj[u] - p0] = (uint16_t)m;
-            }
-        }
-    }
-    for (int j = t; j < n_own; j += SC_TPB) {
-        const int r0 = __ldg(aux.roff + p0 + j) - b * cp.seg;
-        const int w = __ldg(nnb + p0 + j);
-        roff[j] = r0 >> 2;
-        const int all = pad4(row_len(w)) >> 2, nearc = ((w & 0xffff) + 3) >> 2;
-        // chunks visited: the near prefix (soft-core-only owners, decided below) or all
-        vpre[j] = (all << 16) | nearc;
-    }
-    if (t == 0) roff[n_own] = meta.y >> 2;
-    anyA = __syncthreads_or(anyA);
-    if (t == 0 && useA) aux.hasA[b] = 0;  // ready for the next step
-    for (int j = t; j < n_own; j += SC_TPB) {
-        const int v = vpre[j];
-        const bool fast = !M::fp64 && !anyA && get_s(spos[ownm[j]]) == (real)0;
-        vpre[j] = fast ? (v & 0xffff) : (v >> 16);
-    }
-    const int nch = scan_in_place(vpre, n_own, sw);
-    const uint2* L = reinterpret_cast<const uint2*>(nbr + (size_t)b * cp.seg);
-    const int per = (nch + SC_TPB - 1) / SC_TPB;
-    const int c0 = min(nch, t * per), c1 = min(nch, c0 + per);
-    int jfirst = -1, jlast = -1;
-    if (c0 < c1) {
-        // owner of visited chunk c0: the largest j with vpre[j] <= c0
-        int j = 0;
-        {
-            int hi = n_own - 1;
-            while (j < hi) {
-                const int mid = (j + hi + 1) >> 1;
-                if (vpre[mid] <= c0) j = mid;
-                else hi = mid - 1;
-            }
-        }
-        jfirst = j;
-        int jend = vpre[j + 1];
-        int cbase = roff[j] - vpre[j];  // physical chunk = visited chunk + cbase
-        pos_t pi = spos[ownm[j]];
-        real si = get_s(pi), Ai = sAj[ownm[j]];
-        bool fast = !M::fp64 && !anyA && si == (real)0;
-        real fx = 0, fy = 0, fz = 0;
-#pragma unroll 4
-        for (int cc = c0; cc < c1; ++cc) {
-            if (cc >= jend) {
-                if (j == jfirst) {
-                    hF[0][t] = fx;
-                    hF[1][t] = fy;
-                    hF[2][t] = fz;
-                } else {
-                    oF[j] = fx;
-                    oF[cp.omax + j] = fy;
-                    oF[2 * cp.omax + j] = fz;
-                }
-                do {
-                    ++j;
-                    jend = vpre[j + 1];
-                } while (cc >= jend);
-                cbase = roff[j] - vpre[j];
-                pi = spos[ownm[j]];
-                si = get_s(pi);
-                Ai = sAj[ownm[j]];
-                fast = !M::fp64 && !anyA && si == (real)0;
-                fx = fy = fz = 0;
-            }
-            const uint2 v = __ldg(L + cc + cbase);
-            int h[4];
-            unpack4(v, h);
+        real acc = 0;
+        for (int e = lane; e < len; e += 32) {
+            const int jj = __ldg(sidx + __ldg(row + e));
+            // the force of jj needs A_p: if it was tagged whole, it now goes on the general list
             if constexpr (!M::fp64) {
-                if (fast) {
-                    // soft core only: g / r = K (r^2 - r_r^2), r^2 in units of (L / 2^32)^2
-                    const float kc = c.Er4f * c.rr2invf * g.s32sq, rr2u = (float)c.rr2_fix;
-                    float gx = 0.0f, gy = 0.0f, gz = 0.0f;
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int4 pj = spos[h[u]];
-                        const float dx = (float)(pi.x - pj.x), dy = (float)(pi.y - pj.y), dz = (float)(pi.z - pj.z);
-                        const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz));
-                        const float gr = r2 < rr2u ? __fmaf_rn(kc, r2, -c.Er4f) : 0.0f;
-                        gx = __fmaf_rn(-gr, dx, gx);
-                        gy = __fmaf_rn(-gr, dy, gy);
-                        gz = __fmaf_rn(-gr, dz, gz);
-                    }
-                    fx = __fmaf_rn(gx, g.s32, fx);
-                    fy = __fmaf_rn(gy, g.s32, fy);
-                    fz = __fmaf_rn(gz, g.s32, fz);
-                } else {
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int4 pj = spos[h[u]];
-                        pair_f32(pi, si, Ai, pj, get_s(pj), sAj[h[u]], c, g, fx, fy, fz);
-                    }
-                }
+                if (atomicExch(reinterpret_cast<float*>(static_cast<float4*>(aux.fcore) + jj) + 3, 0.0f) != 0.0f)
+                    aux.glist[atomicAdd(&st->ngen, 1)] = jj;
+            }
+            if constexpr (M::fp64) {
+                const double r2 = r2_d<M>(pi, pos[jj], g);
+                if (r2 > c.rr2 && r2 < c.ra2) acc += s_only[2 * (size_t)jj] * Va_d(sqrt(r2), c);
             } else {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const P64 pj = spos[h[u]];
-                    pair_f64(pi, si, Ai, pj, get_s(pj), sAj[h[u]], c, g, fx, fy, fz);
+                const unsigned long long r2i = r2_fix(pi, pos[jj]);
+                if (r2i > c.rr2_fix && r2i < c.ra2_fix) {
+                    const float r2 = u64_to_float(r2i) * g.s32sq;
+                    const float r = sqrtf(r2);
+                    const float uu = s64_to_float((long long)r2i - (long long)c.rm2_fix) * c.s2hinv / (r + c.rmf);
+                    const float q = 1.0f - uu * uu;
+                    acc += s_only[2 * (size_t)jj] * (-c.Eaf * q * q);
                 }
             }
         }
-        if (j == jfirst) {
-            hF[0][t] = fx;
-            hF[1][t] = fy;
-            hF[2][t] = fz;
-        } else {
-            tF[0][t] = fx;
-            tF[1][t] = fy;
-            tF[2][t] = fz;
-        }
-        jlast = j;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) sA[p].y = ds[p] * acc;
     }
-    jf[t] = jfirst;
-    jl[t] = jlast;
-    __syncthreads();
-    for (int j = t; j < n_own; j += SC_TPB) {
-        const int cs = vpre[j], ce = vpre[j + 1];
-        real f[3] = {0, 0, 0};
-        if (cs < ce) {
-            const int ta = cs / per, tb = (ce - 1) / per;
-            if (ta == tb && jf[ta] != j && jl[ta] != j) {
-#pragma unroll
-                for (int d = 0; d < 3; ++d) f[d] = oF[d * cp.omax + j];
-            } else {
-                const bool head = jf[ta] == j;
-#pragma unroll
-                for (int d = 0; d < 3; ++d) f[d] = head ? hF[d][ta] : tF[d][ta];
-                for (int k = ta + 1; k <= tb; ++k) {
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) f[d] += hF[d][k];
-                }
-            }
+}
+
+// ================================================================ pass 2: forces + BAOAB
+// k_force_rows: the whole force of every particle on the general list (not
+// saturated, a neighbour of a window particle, more near entries than the
+// close list holds, or any particle in the FP64 mode): one warp per particle,
+// one lane per entry of its full row, neighbours and their s_j (in the
+// positions' spare word) and A_j read through the group's staged-index
+// table, lane sums reduced in a fixed tree.  The result overwrites the
+// particle's force slot with the tag set.
+template <class M>
+__global__ void __launch_bounds__(TPB) k_force_rows(Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
+                                                    SuperCaps cp, GroupAux aux, const uint16_t* __restrict__ nbr,
+                                                    const int* __restrict__ nnb,
+                                                    const typename M::real2* __restrict__ sA, const Status* st)
+{
+    using pos_t = typename M::pos_t;
+    using real = typename M::real;
+    if (halted(st)) return;
+    const int ng = st->ngen;
+    const bool useA = st->nwin > 0;  // A_j != 0 only for window particles
+    const int lane = threadIdx.x & 31;
+    for (int k = (int)((blockIdx.x * TPB + threadIdx.x) >> 5); k < ng; k += (int)((gridDim.x * TPB) >> 5)) {
+        const int p = aux.glist[k];
+        const int ra = __ldg(aux.roff + p), b = ra / cp.seg;
+        const int len = row_len(__ldg(nnb + p));
+        const pos_t pi = pos[p];
+        const real si = get_s(pi), Ai = useA ? sA[p].y : (real)0;
+        const uint16_t* row = nbr + ra;
+        const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
+        real fx = 0, fy = 0, fz = 0;
+        for (int e = lane; e < len; e += 32) {
+            const int jj = __ldg(sidx + __ldg(row + e));
+            const pos_t pj = pos[jj];
+            const real Aj = useA ? sA[jj].y : (real)0;
+            if constexpr (M::fp64) pair_f64(pi, si, Ai, pj, get_s(pj), Aj, c, g, fx, fy, fz);
+            else pair_f32(pi, si, Ai, pj, get_s(pj), Aj, c, g, fx, fy, fz);
         }
-        const int p = p0 + j;
-        PState<M> q;
-        if (j == t) q = ps;
-        else load_pstate<M, EPI>(p, n, a, id, xref, q);
-        if constexpr (EPI == EPI_FORCE) {
-            if (a.F_out) {
-                const size_t o = 3 * (size_t)q.id;
-                a.F_out[o + 0] = (double)f[0];
-                a.F_out[o + 1] = (double)f[1];
-                a.F_out[o + 2] = (double)f[2];
-            }
-        } else {
-            integrate<M, EPI>(p, n, g, f[0], f[1], f[2], a, q, st, pos_next);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            fx += __shfl_xor_sync(0xffffffffu, fx, o);
+            fy += __shfl_xor_sync(0xffffffffu, fy, o);
+            fz += __shfl_xor_sync(0xffffffffu, fz, o);
         }
+        if (lane == 0) {
+            if constexpr (M::fp64) static_cast<F64x4*>(aux.fcore)[p] = F64x4{fx, fy, fz, 1.0};
+            else static_cast<float4*>(aux.fcore)[p] = make_float4(fx, fy, fz, 1.0f);
+        }
+    }
+}
+
+// k_step: the BAOAB update of every particle from its force slot (or, for a
+// force evaluation, the forces in caller order).  A streaming kernel.
+template <class M, int EPI>
+__global__ void __launch_bounds__(TPB) k_step(int n, Geom g, GroupAux aux, const int* __restrict__ id,
+                                              typename M::pos_t* __restrict__ pos_next,
+                                              const typename M::pos_t* __restrict__ xref, StepArgs a, Status* st)
+{
+    if (halted(st)) return;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    typename M::real f[3];
+    if constexpr (M::fp64) {
+        const F64x4 fc = static_cast<const F64x4*>(aux.fcore)[p];
+        f[0] = fc.x;
+        f[1] = fc.y;
+        f[2] = fc.z;
+    } else {
+        const float4 fc = static_cast<const float4*>(aux.fcore)[p];
+        f[0] = fc.x;
+        f[1] = fc.y;
+        f[2] = fc.z;
+    }
+    PState<M> q;
+    load_pstate<M, EPI>(p, n, a, id, xref, q);
+    if constexpr (EPI == EPI_FORCE) {
+        if (a.F_out) {
+            const size_t o = 3 * (size_t)q.id;
+            a.F_out[o + 0] = (double)f[0];
+            a.F_out[o + 1] = (double)f[1];
+            a.F_out[o + 2] = (double)f[2];
+        }
+    } else {
+        integrate<M, EPI>(p, n, g, f[0], f[1], f[2], a, q, st, pos_next);
     }
 }
 
@@ -1684,6 +1561,7 @@ __global__ void k_gate(Status* st, cudaGraphConditionalHandle h, int in_graph)
     st->iter += 1;
     st->nwin = 0;
     st->nu = 0;
+    st->ngen = 0;
     if (in_graph) {
         const bool due = st->rebuild && !halted(st);
         if (due) st->graph_rebuild_runs += 1;

@@ -158,18 +158,18 @@ def test_kernel_launch_accounting():
     with vbc.System(pos, L, _vp(p), vel=vel) as s:
         # direct launches (per-kernel timing on): one iteration counter reset, then per
         # iteration a gate, 8 rebuild kernels (returning at once when no rebuild is due),
-        # the two count kernels, chain and force
+        # the two count kernels, chain, force rows and the update
         s.profile(True)
         before = s.kernel_launches()
         s.step(10, 0.005, 1.0, 1.0)
-        assert s.kernel_launches() - before == 1 + 11 * 13
+        assert s.kernel_launches() - before == 1 + 11 * 14
         s.profile(False)
-        # graphs: iterations 1..8 run as four two-step graphs of 10 kernels, plus 8 kernels
+        # graphs: iterations 1..8 run as four two-step graphs of 12 kernels, plus 8 kernels
         # for every rebuild the graphs' conditionals executed
         before = s.kernel_launches()
         s.step(10, 0.005, 1.0, 1.0)
         d = s.kernel_launches() - before
-        assert d >= 1 + 3 * 13 + 4 * 10 and (d - (1 + 3 * 13 + 4 * 10)) % 8 == 0
+        assert d >= 1 + 3 * 14 + 4 * 12 and (d - (1 + 3 * 14 + 4 * 12)) % 8 == 0
 
 
 @pytest.mark.parametrize("prec", [F32, F64])
