@@ -402,7 +402,7 @@ int enqueue_rebuild(vbc_system* s)
     k_scan_sums<<<nchunk, SCAN_TPB, 0, s->stream>>>(s->cell_count, s->npad, s->chunk_sum, s->st);
     k_scan_apply<<<nchunk, SCAN_TPB, 0, s->stream>>>(s->cell_count, s->npad, s->chunk_sum, s->cell_start, s->st);
     k_scatter<<<nb, TPB, 0, s->stream>>>(n, s->cell_of, s->slot_of, s->cell_start, s->order, s->st);
-    k_cellsort<<<blocks_for(s->npad, TPB), TPB, 0, s->stream>>>(s->npad, s->cell_start, s->id, s->order, s->st);
+    k_cellsort<<<blocks_for(s->npad, TPB), TPB, 0, s->stream>>>(s->npad, s->cell_start, s->order, s->st);
     k_permute<M><<<nb, TPB, 0, s->stream>>>(n, s->order, s->x, s->v, s->id, pos, s->xt, s->vt, s->idt,
                                             (pos_t*)s->post, s->st);
     k_copyback<M><<<nb, TPB, 0, s->stream>>>(n, s->xt, s->vt, s->idt, (const pos_t*)s->post, s->x, s->v, s->id,

@@ -155,21 +155,41 @@ __global__ void __launch_bounds__(TPB) k_scatter(int n, const int* __restrict__ 
     order[cell_start[cell_of[i]] + slot_of[i]] = i;
 }
 
-// Within each cell, order particles by their original index so that the
-// layout (and every summation order) is independent of atomic scheduling.
+// Within each cell, order particles by their index in the previous sorted
+// order, so that the layout (and every summation order) is a function of the
+// previous layout and the positions only, not of atomic scheduling.  Cells of
+// up to 16 particles are sorted in registers (odd-even transposition), larger
+// ones by insertion in memory.
 __global__ void __launch_bounds__(TPB) k_cellsort(int ncell, const int* __restrict__ cell_start,
-                                                  const int* __restrict__ id, int* __restrict__ order,
-                                                  const Status* st)
+                                                  int* __restrict__ order, const Status* st)
 {
     if (!st->rebuild || st->frozen || st->crowded) return;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
-    const int b = cell_start[c], e = cell_start[c + 1];
+    const int b = cell_start[c], e = cell_start[c + 1], cnt = e - b;
+    if (cnt <= 1) return;
+    if (cnt <= 16) {
+        int v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = k < cnt ? order[b + k] : 0x7fffffff;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+#pragma unroll
+            for (int k = r & 1; k + 1 < 16; k += 2) {
+                const int lo = min(v[k], v[k + 1]), hi = max(v[k], v[k + 1]);
+                v[k] = lo;
+                v[k + 1] = hi;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (k < cnt) order[b + k] = v[k];
+        return;
+    }
     for (int k = b + 1; k < e; ++k) {
         const int o = order[k];
-        const int key = id[o];
         int m = k - 1;
-        while (m >= b && id[order[m]] > key) {
+        while (m >= b && order[m] > o) {
             order[m + 1] = order[m];
             --m;
         }
@@ -974,6 +994,14 @@ struct __align__(32) F64x4 {
     double x, y, z, w;
 };
 
+// k_count_near also forms, in the FP32 mode, the soft-core force of its
+// particle from the same close neighbours.  Every pair inside the soft core
+// is a near entry, so for a particle whose near entries all fit the close
+// list the sum is its whole soft-core force; if the particle is saturated
+// too (s_i = s'_i = 0, hence A_i = 0), it has no well term and its window
+// terms need A_j != 0 of a neighbour -- which k_chain rules out by clearing
+// the tag of every list neighbour of a window particle.  Every other particle
+// goes on the list of k_force_rows.
 // k_count_near also forms, in the FP32 mode, the soft-core force of its
 // particle from the same close neighbours.  Every pair inside the soft core
 // is a near entry, so for a particle whose near entries all fit the close
