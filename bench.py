@@ -34,8 +34,10 @@ sys.path.insert(0, ROOT)
 METRIC = "VBC pair-interactions/s and MD timesteps/s at N=1M on 1 B300, % HBM roofline; p50/p99 served"
 UNIT = "timesteps/s"
 FALLBACK_HBM_GBS = 6400.0
+KERNELS_OF = {"count": "k_count_near + k_count_rows", "chain": "k_chain", "force": "k_force_rows + k_step",
+              "rebuild": "k_bin, k_scan_sums, k_scan_apply, k_scatter, k_cellsort, k_permute, k_copyback, k_nlist"}
 KERNEL_SOURCES = ("paper_2609_07842_b300/csrc/vbc_kernels.cuh", "paper_2609_07842_b300/csrc/vbc_device.cuh")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_kernel_traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "kernel_traffic.json")
 
 
 def parse():
@@ -139,9 +141,11 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(n):
-    """DRAM bytes per launch of the fused force kernel from the committed ncu summary,
-    scaled to n particles; None when the kernel changed since the capture."""
+def ncu_traffic(kernel_class, n):
+    """DRAM bytes per launch of one kernel class (ncu dram__bytes_read.sum +
+    dram__bytes_write.sum, summed over the class's kernels) from the committed
+    summary, scaled to n particles; None when the kernels changed since the
+    capture."""
     try:
         with open(TRAFFIC_FILE) as fh:
             t = json.load(fh)
@@ -149,21 +153,23 @@ def ncu_traffic(n):
         return None
     if t.get("kernel_sources_sha256_16") != kernel_hash():
         return None
-    return t["dram_bytes_per_particle"] * n
+    per = t.get("dram_bytes_per_particle", {}).get(kernel_class)
+    return None if per is None else per * n
 
 
-def force_bytes_per_particle(k):
-    """Algorithmic HBM bytes per particle of one fused force + BAOAB launch: list 4k, list
-    length 4, own fixed-point position 16, own (s, A) 8, id 4, FP64 x and v read + write 96,
-    next fixed-point position 16, position at the last build 16."""
-    return 4.0 * k + 160.0
-
-
-def step_bytes_per_particle(k, phi, rebuild_every):
-    """Algorithmic bytes per particle-step of the whole path: count (4k + 32), chain
-    (4 + phi (4k + 24)), force (4k + 160), amortised rebuild (~(4k + 220) / R)."""
-    rb = (4.0 * k + 220.0) / rebuild_every if rebuild_every > 0 else 0.0
-    return (4.0 * k + 32.0) + (4.0 + phi * (4.0 * k + 24.0)) + force_bytes_per_particle(k) + rb
+# Algorithmic HBM bytes per particle of each kernel class, with the per-unit
+# figures of the hot-path scope table (4-byte list entries, k = mean list
+# length, phi = in-window fraction).  This design moves fewer bytes than these
+# figures (2-byte entries, and saturated particles read a 12-entry close list
+# instead of their full row); the measured DRAM bytes are in "traffic".
+def class_bytes_per_particle(k, phi):
+    return {
+        "count": 4.0 * k + 16.0 + 8.0,                                   # list, own position, n
+        "chain": phi * (4.0 * k + 32.0),                                 # window particles only
+        "force": (4.0 * k + 16.0 + 8.0 + 4.0 + 16.0)                     # pass 2: list, pos, s/n, A, F
+                 + (24.0 + 24.0 + 24.0 + 24.0 + 16.0 + 16.0),            # BAOAB: x, v r/w, F read, pos write
+        "rebuild": 4.0 * k + 48.0,                                       # per build
+    }
 
 
 # ------------------------------------------------------------------ reference arm (the oracle)
@@ -268,6 +274,15 @@ def main():
     sys_.profile(False)
     st_d = sys_.stats()
 
+    # ---- timed region 3: forced neighbour-list builds, one event pair each
+    nb = 5
+    sys_.profile(True, max_launches=4 * nb + 4)
+    for _ in range(nb):
+        sys_.build_neighbors()
+    b_ms, b_n = sys_.profile_read(vbc.K_REBUILD)
+    sys_.profile(False)
+    build_ms = b_ms / max(b_n, 1)
+
     if world > 1:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -285,11 +300,24 @@ def main():
 
     steps_per_s = args.steps / (ms / 1e3) * world
     peak, peak_kind = hbm_peak()
-    fb = force_bytes_per_particle(k_mean) * args.n
-    force_avg_s = force_ms / 1e3 / max(force_n, 1)
-    achieved = fb / force_avg_s / 1e9
-    traffic = ncu_traffic(args.n)
-    step_b = step_bytes_per_particle(k_mean, phi, rebuild_every if rebuilds else 0) * args.n
+    cb = class_bytes_per_particle(k_mean, phi)
+    # per-launch duration of each class; the rebuild class from forced builds
+    # (timed region 3), the others from timed region 2
+    per_launch_ms = {"count": count_ms / max(args.steps + 1, 1), "chain": chain_ms / max(args.steps + 1, 1),
+                     "force": force_ms / max(args.steps + 1, 1), "rebuild": build_ms}
+    share_ms = dict(per_launch_ms)
+    share_ms["rebuild"] = build_ms / rebuild_every if rebuilds else 0.0  # amortised per step
+    classes = {}
+    for c_, ms_ in per_launch_ms.items():
+        b_ = cb[c_] * args.n
+        ach = b_ / (ms_ / 1e3) / 1e9 if ms_ > 0 else 0.0
+        classes[c_] = {"achieved": ach, "frac": ach / peak, "algorithmic_bytes_per_launch": b_,
+                       "avg_launch_ms": ms_, "ms_per_step": share_ms[c_],
+                       "traffic": ncu_traffic(c_, args.n)}
+    dominant = max(share_ms, key=lambda c_: share_ms[c_])
+    step_b = sum(cb[c_] for c_ in ("count", "chain", "force")) * args.n
+    if rebuilds:
+        step_b += cb["rebuild"] * args.n / rebuild_every
     step_gbs = step_b * (args.steps / (ms / 1e3)) / 1e9
 
     # ---- e2e: the same steps through the public API with host buffers
@@ -336,18 +364,24 @@ def main():
             "config": workload(args),
             "pair_interactions_per_s": pairs * steps_per_s,
             "pairs_within_rc": pairs,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_force (pass 2 fused with BAOAB)", "peak_source": peak_kind,
-                         "timing": "CUDA events around each k_force launch, timed region 2",
-                         "algorithmic_bytes_per_launch": fb, "avg_launch_ms": force_avg_s * 1e3,
-                         "launches": force_n},
+            "roofline": {"bound": "hbm", "achieved": classes[dominant]["achieved"], "peak": peak,
+                         "unit": "GB/s", "frac": classes[dominant]["frac"],
+                         "traffic": classes[dominant]["traffic"], "kernel": dominant,
+                         "kernels": KERNELS_OF[dominant], "peak_source": peak_kind,
+                         "timing": ("CUDA events around every launch on the library stream (forced builds for "
+                                    "the rebuild class)"),
+                         "algorithmic_bytes_per_launch": classes[dominant]["algorithmic_bytes_per_launch"],
+                         "avg_launch_ms": classes[dominant]["avg_launch_ms"],
+                         "dominant_by": "device time per step (rebuilds amortised)",
+                         "classes": classes},
             "step_roofline": {"achieved": step_gbs, "frac": step_gbs / peak,
                               "algorithmic_bytes_per_step": step_b,
                               "bytes_per_particle_step": step_b / args.n},
             "kernel_ms_per_step": {"rebuild": reb_ms / args.steps, "count": count_ms / args.steps,
                                    "chain": chain_ms / args.steps, "force": force_ms / args.steps,
-                                   "source": "timed region 2 (direct launches, CUDA events per kernel)",
+                                   "build_ms": build_ms,
+                                   "source": "timed region 2 (direct launches, CUDA events per kernel); "
+                                             "build_ms: forced builds (region 3)",
                                    "ms_per_step_direct": ms_direct / args.steps,
                                    "rebuilds": rebuilds_direct},
             "rebuilds": rebuilds,

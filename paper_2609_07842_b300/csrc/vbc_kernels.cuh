@@ -607,20 +607,76 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
         const spos_t pi = spos[mself];
         uint16_t* row = scratch + (size_t)p * cp.cap;
         int nn = 0, nf = 0;
+        // far entries within r_l, in scan order, go to the close list's slots for now
+        int* cv = aux.close + (size_t)CLOSE_K * p;
+        int nfc = 0;
+        unsigned long long bufn = 0ull, buff = 0ull;  // up to 4 pending near / far entries
 #pragma unroll 1
         for (int d = 0; d < 9; ++d) {
             const int k0 = kb + (d / 3 - 1) * (SX * SY) + (d % 3 - 1) * SX - 1;
             const int e = T.off[k0 + 3];
+            for (int base = T.off[k0]; base < e; base += 32) {
+                // test up to 32 candidates into bit masks, then write the accepted ones
+                const int cnt = min(32, e - base);
+                uint32_t mnear = 0u, mfar = 0u, mfc = 0u;
 #pragma unroll 4
-            for (int m = T.off[k0]; m < e; ++m) {
-                int cl;
-                if constexpr (REL) cl = ListTestRel::cls(pi, spos[m], lp);
-                else cl = ListTest<M>::cls(pi, spos[m], g, lp);
-                if (cl < 0 || m == mself) continue;
-                if (nn + nf < cp.cap) row[cl == 0 ? nn : cp.cap - 1 - nf] = (uint16_t)m;
-                if (cl == 0) ++nn;
-                else ++nf;
+                for (int u = 0; u < cnt; ++u) {
+                    const int m = base + u;
+                    int cl;
+                    bool rl;
+                    if constexpr (REL) {
+                        const float4 q = spos[m];
+                        const float dx = pi.x - q.x, dy = pi.y - q.y, dz = pi.z - q.z;
+                        const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz));
+                        cl = r2 >= lp.rlist2_f ? -1 : (r2 < lp.near2_f ? 0 : 1);
+                        rl = r2 <= lp.rl2_f;
+                    } else if constexpr (M::fp64) {
+                        double dx, dy, dz;
+                        ModeF64::delta64(pi, spos[m], g, dx, dy, dz);
+                        const double r2 = dx * dx + dy * dy + dz * dz;
+                        cl = r2 >= lp.rlist2 ? -1 : (r2 < lp.near2 ? 0 : 1);
+                        rl = r2 <= lp.rl2;
+                    } else {
+                        const int dx = pi.x - spos[m].x, dy = pi.y - spos[m].y, dz = pi.z - spos[m].z;
+                        const unsigned long long r2 = (unsigned long long)((long long)dx * dx) +
+                                                      (unsigned long long)((long long)dy * dy) +
+                                                      (unsigned long long)((long long)dz * dz);
+                        cl = r2 >= lp.rlist2_fix ? -1 : (r2 < lp.near2_fix ? 0 : 1);
+                        rl = r2 <= lp.rl2_fix;
+                    }
+                    const uint32_t bit = m != mself ? 1u << u : 0u;
+                    mnear |= cl == 0 ? bit : 0u;
+                    mfar |= cl == 1 ? bit : 0u;
+                    mfc |= cl == 1 && rl ? bit : 0u;
+                }
+                // accepted entries go out four at a time: near ones fill 8-byte words from the
+                // front of the scratch row, far ones from the back (in reverse order)
+                while (mnear) {
+                    const int u = __ffs(mnear) - 1;
+                    mnear &= mnear - 1u;
+                    bufn = (bufn >> 16) | ((unsigned long long)(base + u) << 48);
+                    if ((++nn & 3) == 0 && nn + nf <= cp.cap) *reinterpret_cast<unsigned long long*>(row + nn - 4) = bufn;
+                }
+                while (mfar) {
+                    const int u = __ffs(mfar) - 1;
+                    mfar &= mfar - 1u;
+                    buff = (buff << 16) | (unsigned long long)(base + u);
+                    if ((++nf & 3) == 0 && nn + nf <= cp.cap)
+                        *reinterpret_cast<unsigned long long*>(row + cp.cap - nf) = buff;
+                }
+                while (mfc && nfc < CLOSE_K) {
+                    const int u = __ffs(mfc) - 1;
+                    mfc &= mfc - 1u;
+                    cv[nfc++] = base + u;
+                }
             }
+        }
+        if (nn + nf <= cp.cap) {
+            // the last 1..3 entries of each kind
+            for (int k = 0; k < (nn & 3); ++k)
+                row[(nn & ~3) + k] = (uint16_t)(bufn >> (16 * (4 - (nn & 3) + k)));
+            for (int k = 0; k < (nf & 3); ++k)
+                row[cp.cap - 1 - ((nf & ~3) + k)] = (uint16_t)(buff >> (16 * ((nf & 3) - 1 - k)));
         }
         const int len = nn + nf;
         nnb[p] = nn | (nf << 16);
@@ -629,30 +685,11 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
             // up to CLOSE_K close entries as sorted indices: the near entries, then far entries
             // within r_l at the build (for the per-particle count and soft-core force; a row
             // with more near entries takes the list-walking force path)
-            int* cv = aux.close + (size_t)CLOSE_K * p;
-            int cnt = 0;
-            for (int e = 0; e < len && e < cp.cap && cnt < CLOSE_K; ++e) {
-                const int m = e < nn ? row[e] : row[cp.cap - 1 - (e - nn)];
-                bool in = e < nn;
-                if (!in) {
-                    if constexpr (REL) {
-                        const float4 q = spos[m];
-                        const float dx = pi.x - q.x, dy = pi.y - q.y, dz = pi.z - q.z;
-                        in = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz)) <= lp.rl2_f;
-                    } else if constexpr (M::fp64) {
-                        double dx, dy, dz;
-                        ModeF64::delta64(pi, spos[m], g, dx, dy, dz);
-                        in = dx * dx + dy * dy + dz * dz <= lp.rl2;
-                    } else {
-                        const int dx = pi.x - spos[m].x, dy = pi.y - spos[m].y, dz = pi.z - spos[m].z;
-                        in = (unsigned long long)((long long)dx * dx) + (unsigned long long)((long long)dy * dy) +
-                                 (unsigned long long)((long long)dz * dz) <=
-                             lp.rl2_fix;
-                    }
-                }
-                if (in) cv[cnt++] = staged_index(T, m);
-            }
-            for (int k = cnt; k < CLOSE_K; ++k) cv[k] = -1;
+            const int kn = min(nn, min(CLOSE_K, cp.cap));
+            const int kf = min(nfc, CLOSE_K - kn);
+            for (int k = kf - 1; k >= 0; --k) cv[kn + k] = staged_index(T, cv[k]);
+            for (int k = 0; k < kn; ++k) cv[k] = staged_index(T, row[k]);
+            for (int k = kn + kf; k < CLOSE_K; ++k) cv[k] = -1;
         }
         roff[j] = pad4(len);
         over |= len > cp.cap;
