@@ -489,14 +489,16 @@ struct ListTestRel {
 __host__ __device__ constexpr size_t al16(size_t v) { return (v + 15) & ~(size_t)15; }
 
 struct NlistLayout {
-    size_t roff, rnn, total;
+    size_t sidx, roff, rnn, rself, total;
 };
 __host__ __device__ inline NlistLayout nlist_layout(const SuperCaps& cp, size_t pos_bytes)
 {
     NlistLayout l{};
-    l.roff = al16((size_t)cp.smax * pos_bytes);
+    l.sidx = al16((size_t)cp.smax * pos_bytes);
+    l.roff = l.sidx + al16((size_t)cp.smax * 4);
     l.rnn = l.roff + al16((size_t)(cp.omax + 1) * 4);
-    l.total = l.rnn + al16((size_t)cp.omax * 4);
+    l.rself = l.rnn + al16((size_t)cp.omax * 4);
+    l.total = l.rself + al16((size_t)cp.omax * 4);
     return l;
 }
 
@@ -572,8 +574,10 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
     }
     const NlistLayout ly = nlist_layout(cp, sizeof(spos_t));
     spos_t* spos = (spos_t*)smem;
+    int* ssidx = (int*)(smem + ly.sidx);  // sorted index of each staged particle
     int* roff = (int*)(smem + ly.roff);
     int* rnn = (int*)(smem + ly.rnn);
+    int* rself = (int*)(smem + ly.rself);  // own staging index of each own particle
     if constexpr (REL) {
         // reference: the centre of the block's own cells (a cell boundary)
         const int org = __ldg(G.sc_org + blockIdx.x);
@@ -593,7 +597,11 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
     }
     {
         int* sidx = aux.stage_idx + (size_t)blockIdx.x * cp.smax;
-        for (int m = t; m < total; m += SC_TPB) sidx[m] = staged_index(T, m);
+        for (int m = t; m < total; m += SC_TPB) {
+            const int jj = staged_index(T, m);
+            sidx[m] = jj;
+            ssidx[m] = jj;
+        }
     }
     __syncthreads();
     int mx = 0;
@@ -687,11 +695,12 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
             // with more near entries takes the list-walking force path)
             const int kn = min(nn, min(CLOSE_K, cp.cap));
             const int kf = min(nfc, CLOSE_K - kn);
-            for (int k = kf - 1; k >= 0; --k) cv[kn + k] = staged_index(T, cv[k]);
-            for (int k = 0; k < kn; ++k) cv[k] = staged_index(T, row[k]);
+            for (int k = kf - 1; k >= 0; --k) cv[kn + k] = ssidx[cv[k]];
+            for (int k = 0; k < kn; ++k) cv[k] = ssidx[row[k]];
             for (int k = kn + kf; k < CLOSE_K; ++k) cv[k] = -1;
         }
         roff[j] = pad4(len);
+        rself[j] = mself;
         over |= len > cp.cap;
         mx = max(mx, len);
         sum += len;
@@ -730,27 +739,34 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
         }
         return;
     }
-    // pack: chunk c (4 entries) belongs to the row j with roff[j] <= 4c < roff[j + 1]
+    // pack: each thread takes an equal contiguous run of the group's 4-entry chunks;
+    // chunk c belongs to the row j with roff[j] <= 4c < roff[j + 1]
     uint2* out = reinterpret_cast<uint2*>(nbr + (size_t)blockIdx.x * cp.seg);
-    for (int c = t; c < tot / 4; c += SC_TPB) {
-        int lo = 0, hi = n_own - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (roff[mid] <= 4 * c) lo = mid;
-            else hi = mid - 1;
+    const int nch = tot / 4, per = (nch + SC_TPB - 1) / SC_TPB;
+    const int c0 = min(nch, t * per), c1 = min(nch, c0 + per);
+    if (c0 < c1) {
+        int j = 0;
+        {
+            int hi = n_own - 1;
+            while (j < hi) {
+                const int mid = (j + hi + 1) >> 1;
+                if (roff[mid] <= 4 * c0) j = mid;
+                else hi = mid - 1;
+            }
         }
-        const int j = lo, w = rnn[j], nn = w & 0xffff, len = nn + (w >> 16);
-        const int p = p0 + j;
-        const uint16_t* row = scratch + (size_t)p * cp.cap;
-        const int b = own_cell(T, p);
-        const uint32_t self = (uint32_t)(T.off[own_staged_cell(b)] + (p - T.own[b]));
-        uint32_t h[4];
+        for (int c = c0; c < c1; ++c) {
+            while (4 * c >= roff[j + 1]) ++j;
+            const int w = rnn[j], nn = w & 0xffff, len = nn + (w >> 16);
+            const uint16_t* row = scratch + (size_t)(p0 + j) * cp.cap;
+            const uint32_t self = (uint32_t)rself[j];
+            uint32_t h[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int e = 4 * c - roff[j] + u;
-            h[u] = e < nn ? row[e] : (e < len ? row[cp.cap - 1 - (e - nn)] : self);
+            for (int u = 0; u < 4; ++u) {
+                const int e = 4 * c - roff[j] + u;
+                h[u] = e < nn ? row[e] : (e < len ? row[cp.cap - 1 - (e - nn)] : self);
+            }
+            out[c] = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
         }
-        out[c] = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
     }
 }
 
