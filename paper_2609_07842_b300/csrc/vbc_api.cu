@@ -152,6 +152,7 @@ struct vbc_system {
     size_t smem_nlist_rel() const { return nlist_layout(caps(), sizeof(float4)).total; }
     size_t smem_energy() const { return pass_layout(caps(), pos_bytes(), sizeof(double2)).total; }
     size_t smem_store() const { return al16((size_t)(omax + 1) * 4); }
+    size_t smem_rows(size_t extra) const { return dense_layout(caps(), pos_bytes(), extra).total; }
 };
 
 namespace {
@@ -382,6 +383,9 @@ int configure_smem(vbc_system* s)
     VBC_TRY(set_smem(k_chain_e<M>, s->smem_energy()));
     VBC_TRY(set_smem(k_energy<M>, s->smem_energy()));
     VBC_TRY(set_smem(k_store_nlist, s->smem_store()));
+    VBC_TRY(set_smem(k_count_rows<M>, s->smem_rows(0)));
+    VBC_TRY(set_smem(k_chain<M>, s->smem_rows(4)));
+    VBC_TRY(set_smem(k_force_rows<M>, s->smem_rows(s->real_bytes())));
     return VBC_OK;
 }
 
@@ -432,15 +436,16 @@ int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window)
         k_count_near<M><<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>((int)s->n, s->geom, s->coef, pos, s->aux(),
                                                                        s->nnb, (real*)s->ds, (real2*)s->sA, out,
                                                                        s->ulist, s->st);
-        k_count_rows<M><<<s->rows_grid, TPB, 0, s->stream>>>(s->geom, s->coef, pos, s->caps(), s->aux(), s->nbr,
-                                                               s->nnb, s->id, (real*)s->ds, (real2*)s->sA, out,
-                                                               s->ulist, s->wpart, s->st);
+        k_count_rows<M><<<s->nsc, SC_TPB, s->smem_rows(0), s->stream>>>(
+            (int)s->n, s->geom, s->coef, pos, s->grid(), s->caps(), s->aux(), s->nbr, s->nnb, s->id, (real*)s->ds,
+            (real2*)s->sA, out, s->ulist, s->wpart, s->st);
     }
     {
         Timed t(s, VBC_K_CHAIN);
-        k_chain<M><<<s->chain_grid, SC_TPB, 0, s->stream>>>(s->geom, s->coef, pos, s->caps(), s->aux(), s->nbr,
-                                                            s->nnb, (const real*)s->ds, (real2*)s->sA, s->wpart,
-                                                            s->st);
+        k_chain<M><<<s->nsc, SC_TPB, s->smem_rows(4), s->stream>>>((int)s->n, s->geom, s->coef, pos, s->grid(),
+                                                                    s->caps(), s->aux(), s->nbr, s->nnb,
+                                                                    (const real*)s->ds, (real2*)s->sA, s->wpart,
+                                                                    s->st);
     }
     return check_launch(s, 3);
 }
@@ -455,8 +460,8 @@ int enqueue_force(vbc_system* s, const StepArgs& a)
     pos_t* pos_next = (pos_t*)s->pos[s->cur ^ 1];
     {
         Timed t(s, VBC_K_FORCE);
-        k_force_rows<M><<<s->rows_grid, TPB, 0, s->stream>>>(s->geom, s->coef, pos, s->caps(), s->aux(), s->nbr,
-                                                              s->nnb, (const real2*)s->sA, s->st);
+        k_force_rows<M><<<s->nsc, SC_TPB, s->smem_rows(s->real_bytes()), s->stream>>>(
+            n, s->geom, s->coef, pos, s->grid(), s->caps(), s->aux(), s->nbr, s->nnb, (const real2*)s->sA, s->st);
         k_step<M, EPI><<<blocks_for(n, TPB), TPB, 0, s->stream>>>(n, s->geom, s->aux(), s->id, pos_next,
                                                                   (const pos_t*)s->xref, a, s->st);
     }

@@ -1055,14 +1055,6 @@ struct __align__(32) F64x4 {
 // terms need A_j != 0 of a neighbour -- which k_chain rules out by clearing
 // the tag of every list neighbour of a window particle.  Every other particle
 // goes on the list of k_force_rows.
-// k_count_near also forms, in the FP32 mode, the soft-core force of its
-// particle from the same close neighbours.  Every pair inside the soft core
-// is a near entry, so for a particle whose near entries all fit the close
-// list the sum is its whole soft-core force; if the particle is saturated
-// too (s_i = s'_i = 0, hence A_i = 0), it has no well term and its window
-// terms need A_j != 0 of a neighbour -- which k_chain rules out by clearing
-// the tag of every list neighbour of a window particle.  Every other particle
-// goes on the list of k_force_rows.
 template <class M>
 __global__ void __launch_bounds__(TPB) k_count_near(int n, Geom g, Coef c, typename M::pos_t* __restrict__ pos,
                                                     GroupAux aux, const int* __restrict__ nnb,
@@ -1123,6 +1115,7 @@ __global__ void __launch_bounds__(TPB) k_count_near(int n, Geom g, Coef c, typen
         sA[p] = real2{(real)0, (real)0};
         put_w(pos + p, (real)0);
     } else {
+        ds_out[p] = (real)NAN;  // marks the particle for k_count_rows
         ulist[atomicAdd(&st->nu, 1)] = p;
     }
     const bool whole = !M::fp64 && sat && nn <= CLOSE_K;
@@ -1134,86 +1127,212 @@ __global__ void __launch_bounds__(TPB) k_count_near(int n, Geom g, Coef c, typen
     if (!whole) aux.glist[atomicAdd(&st->ngen, 1)] = p;
 }
 
+// ================================================================ row walks
+// k_count_rows, k_chain and k_force_rows walk full list rows, one warp per
+// particle and one lane per entry, for the particles on their work lists.
+// Each picks its mode on the device from the list length: sparse (a warp per
+// listed particle, neighbours read through the group's staged-index table)
+// while the list holds at most n / DENSE_DIV particles, dense otherwise (one
+// block per cell group: the group stages its neighbourhood in shared memory
+// and its warps walk the rows of its listed particles from there).  A row is
+// walked in the same order and reduced in the same fixed tree either way, so
+// the mode does not change a bit of the result.  The grid is one block per
+// cell group in both modes.
+constexpr int DENSE_DIV = 16;
+constexpr int ROW_WARPS = SC_TPB / 32;
+
+// Shared memory of a dense row walk: staged positions, one extra value per
+// staged particle, and a list of own particles.
+struct DenseLayout {
+    size_t extra, plist, total;
+};
+__host__ __device__ inline DenseLayout dense_layout(const SuperCaps& cp, size_t pos_bytes, size_t extra_bytes)
+{
+    DenseLayout l{};
+    l.extra = al16((size_t)cp.smax * pos_bytes);
+    l.plist = l.extra + al16((size_t)cp.smax * extra_bytes);
+    l.total = l.plist + al16((size_t)cp.omax * 4);
+    return l;
+}
+
+// Copies a group's staged particles: put(m, j) for staging index m and sorted
+// index j, four loads of the index table in flight per thread.
+template <class Put>
+__device__ __forceinline__ void stage_by_table(const int* __restrict__ sidx, int total, Put&& put)
+{
+    constexpr int B = 4;
+    for (int m0 = threadIdx.x; m0 < total; m0 += SC_TPB * B) {
+        int jj[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) jj[u] = m0 + u * SC_TPB < total ? __ldg(sidx + m0 + u * SC_TPB) : -1;
+#pragma unroll
+        for (int u = 0; u < B; ++u)
+            if (jj[u] >= 0) put(m0 + u * SC_TPB, jj[u]);
+    }
+}
+
+// Count of one row, on every lane of the warp: s_i, s'_i and (if wanted) n_i.
+template <class M, class Fetch>
+__device__ __forceinline__ void count_row(const typename M::pos_t& pi, const uint16_t* __restrict__ row, int len,
+                                          Fetch&& fetch, const Coef& c, const Geom& g, bool want_n,
+                                          typename M::real& s, typename M::real& ds, double& n_val)
+{
+    const int lane = threadIdx.x & 31;
+    if constexpr (M::fp64) {
+        double acc = 0.0;
+        for (int e = lane; e < len; e += 32) {
+            const double r2 = r2_d<M>(pi, fetch(__ldg(row + e)), g);
+            if (r2 < c.rh2) acc += r2 <= c.rl2 ? 1.0 : omega_d(sqrt(r2), c.r_l, c.r_h);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        s = omega_d(acc, c.fd, c.fd + 1.0);
+        ds = domega_d(acc, c.fd, c.fd + 1.0);
+        n_val = acc;
+    } else {
+        long long full = 0;
+        unsigned long long q = 0;
+        for (int e = lane; e < len; e += 32) {
+            const unsigned long long r2 = r2_fix(pi, fetch(__ldg(row + e)));
+            if (r2 < c.rh2_fix) {
+                if (r2 <= c.rl2_fix) ++full;
+                else q += window_weight_fix31(r2, r2 - c.rl2_fix, c.rl_s, c.w_s);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            full += __shfl_xor_sync(0xffffffffu, full, o);
+            q += __shfl_xor_sync(0xffffffffu, q, o);
+        }
+        const long long Tf = (full - c.fd_int) * 2147483648LL + (long long)q - c.fd_frac_fix;
+        switch_from_fix(Tf, s, ds);
+        n_val = 0.0;
+        if (want_n) n_val = (double)full + (double)q * 4.656612873077393e-10;
+    }
+}
+
+// Results of one counted row (lane 0 of the warp).
 template <class M>
-__global__ void __launch_bounds__(TPB) k_count_rows(Geom g, Coef c, typename M::pos_t* __restrict__ pos,
-                                                    SuperCaps cp, GroupAux aux, const uint16_t* __restrict__ nbr,
-                                                    const int* __restrict__ nnb, const int* __restrict__ id,
-                                                    typename M::real* __restrict__ ds_out,
-                                                    typename M::real2* __restrict__ sA, CountOut out,
-                                                    const int* __restrict__ ulist, int* __restrict__ wpart,
-                                                    Status* st)
+__device__ __forceinline__ void count_row_out(int p, typename M::real s, typename M::real ds, double n_val,
+                                              typename M::pos_t* __restrict__ pos, typename M::real* __restrict__ ds_out,
+                                              typename M::real2* __restrict__ sA, const int* __restrict__ id,
+                                              const CountOut& out, int* __restrict__ wpart, Status* st)
+{
+    using real = typename M::real;
+    using real2 = typename M::real2;
+    ds_out[p] = ds;
+    sA[p] = real2{s, (real)0};
+    put_w(pos + p, s);
+    if (out.n_out) out.n_out[id[p]] = n_val;
+    if (ds != (real)0) {
+        // the chain-rule pass visits the window particles listed here
+        wpart[atomicAdd(&st->nwin, 1)] = p;
+        if (out.in_window) atomicAdd((unsigned long long*)out.in_window, 1ull);
+    }
+}
+
+template <class M>
+__global__ void __launch_bounds__(SC_TPB) k_count_rows(int n, Geom g, Coef c, typename M::pos_t* __restrict__ pos,
+                                                       SuperGrid G, SuperCaps cp, GroupAux aux,
+                                                       const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
+                                                       const int* __restrict__ id, typename M::real* __restrict__ ds_out,
+                                                       typename M::real2* __restrict__ sA, CountOut out,
+                                                       const int* __restrict__ ulist, int* __restrict__ wpart,
+                                                       Status* st)
 {
     using pos_t = typename M::pos_t;
     using real = typename M::real;
-    using real2 = typename M::real2;
     if (halted(st)) return;
     const int nu = st->nu;
-    const int lane = threadIdx.x & 31;
-    for (int k = (int)((blockIdx.x * TPB + threadIdx.x) >> 5); k < nu; k += (int)((gridDim.x * TPB) >> 5)) {
-        const int p = ulist[k];
-        const int ra = __ldg(aux.roff + p), b = ra / cp.seg;
-        const int len = row_len(__ldg(nnb + p));
-        const pos_t pi = pos[p];
-        const uint16_t* row = nbr + ra;
-        const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
+    const int warp = threadIdx.x >> 5;
+    if (nu <= n / DENSE_DIV) {
+        for (int k = blockIdx.x * ROW_WARPS + warp; k < nu; k += gridDim.x * ROW_WARPS) {
+            const int p = ulist[k];
+            const int ra = __ldg(aux.roff + p), b = ra / cp.seg;
+            const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
+            real s, ds;
+            double n_val;
+            count_row<M>(pos[p], nbr + ra, row_len(__ldg(nnb + p)), [&](int m) { return pos[__ldg(sidx + m)]; }, c, g,
+                         out.n_out != nullptr, s, ds, n_val);
+            if ((threadIdx.x & 31) == 0) count_row_out<M>(p, s, ds, n_val, pos, ds_out, sA, id, out, wpart, st);
+        }
+        return;
+    }
+    // dense: the group's own particles that k_count_near marked (s'_i = NaN)
+    const int b = blockIdx.x, t = threadIdx.x;
+    const int p0 = __ldg(G.cell_start + OWN_CELLS * b);
+    const int n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
+    __shared__ int s_n;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const DenseLayout ly = dense_layout(cp, sizeof(pos_t), 0);
+    pos_t* spos = (pos_t*)smem;
+    int* plist = (int*)(smem + ly.plist);
+    if (t == 0) s_n = 0;
+    __syncthreads();
+    for (int j = t; j < n_own; j += SC_TPB)
+        if (isnan(ds_out[p0 + j])) plist[atomicAdd(&s_n, 1)] = j;
+    __syncthreads();
+    const int nl = s_n;
+    if (nl == 0) return;
+    stage_by_table(aux.stage_idx + (size_t)b * cp.smax, __ldg(aux.meta + b).x,
+                   [&](int m, int jj) { spos[m] = pos[jj]; });
+    __syncthreads();
+    for (int u = warp; u < nl; u += ROW_WARPS) {
+        const int p = p0 + plist[u];
         real s, ds;
         double n_val;
-        if constexpr (M::fp64) {
-            double acc = 0.0;
-            for (int e = lane; e < len; e += 32) {
-                const double r2 = r2_d<M>(pi, pos[__ldg(sidx + __ldg(row + e))], g);
-                if (r2 < c.rh2) acc += r2 <= c.rl2 ? 1.0 : omega_d(sqrt(r2), c.r_l, c.r_h);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            s = omega_d(acc, c.fd, c.fd + 1.0);
-            ds = domega_d(acc, c.fd, c.fd + 1.0);
-            n_val = acc;
-        } else {
-            long long full = 0;
-            unsigned long long q = 0;
-            for (int e = lane; e < len; e += 32) {
-                const unsigned long long r2 = r2_fix(pi, pos[__ldg(sidx + __ldg(row + e))]);
-                if (r2 < c.rh2_fix) {
-                    if (r2 <= c.rl2_fix) ++full;
-                    else q += window_weight_fix31(r2, r2 - c.rl2_fix, c.rl_s, c.w_s);
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                full += __shfl_xor_sync(0xffffffffu, full, o);
-                q += __shfl_xor_sync(0xffffffffu, q, o);
-            }
-            const long long Tf = (full - c.fd_int) * 2147483648LL + (long long)q - c.fd_frac_fix;
-            switch_from_fix(Tf, s, ds);
-            n_val = 0.0;
-            if (out.n_out) n_val = (double)full + (double)q * 4.656612873077393e-10;
-        }
-        if (lane == 0) {
-            ds_out[p] = ds;
-            sA[p] = real2{s, (real)0};
-            put_w(pos + p, s);
-            if (out.n_out) out.n_out[id[p]] = n_val;
-            if (ds != (real)0) {
-                // the chain-rule pass visits the window particles listed here
-                wpart[atomicAdd(&st->nwin, 1)] = p;
-                if (out.in_window) atomicAdd((unsigned long long*)out.in_window, 1ull);
-            }
-        }
+        count_row<M>(pos[p], nbr + __ldg(aux.roff + p), row_len(__ldg(nnb + p)), [&](int m) { return spos[m]; }, c, g,
+                     out.n_out != nullptr, s, ds, n_val);
+        if ((t & 31) == 0) count_row_out<M>(p, s, ds, n_val, pos, ds_out, sA, id, out, wpart, st);
     }
 }
 
 // ================================================================ chain-rule pass
 // A_i = s'_i sum_j s_j V_a(r_ij) for the particles inside the switching
-// window (s'_i != 0) that k_count_rows listed, one warp per particle,
-// neighbours read through their group's staged-index table.  A fixed grid
-// walks the list, so a step without window particles costs one launch that
-// reads one counter.  Every list neighbour of a window particle loses its
-// whole-force tag (its window term needs A_i) and joins the general list.
+// window (s'_i != 0), which k_count_rows listed.  Every list neighbour of a
+// window particle loses its whole-force tag (its window term needs A_i) and
+// joins the general list of k_force_rows.
+template <class M, class Fetch>
+__device__ __forceinline__ typename M::real chain_row(const typename M::pos_t& pi, const uint16_t* __restrict__ row,
+                                                      int len, Fetch&& fetch, const Coef& c, const Geom& g,
+                                                      GroupAux& aux, Status* st)
+{
+    using pos_t = typename M::pos_t;
+    using real = typename M::real;
+    const int lane = threadIdx.x & 31;
+    real acc = 0;
+    for (int e = lane; e < len; e += 32) {
+        int jj;
+        const pos_t pj = fetch(__ldg(row + e), jj);
+        // the force of jj needs A_i: if it was tagged whole, it now goes on the general list
+        if constexpr (!M::fp64) {
+            if (atomicExch(reinterpret_cast<float*>(static_cast<float4*>(aux.fcore) + jj) + 3, 0.0f) != 0.0f)
+                aux.glist[atomicAdd(&st->ngen, 1)] = jj;
+        }
+        if constexpr (M::fp64) {
+            const double r2 = r2_d<M>(pi, pj, g);
+            if (r2 > c.rr2 && r2 < c.ra2) acc += get_s(pj) * Va_d(sqrt(r2), c);
+        } else {
+            const unsigned long long r2i = r2_fix(pi, pj);
+            if (r2i > c.rr2_fix && r2i < c.ra2_fix) {
+                const float r2 = u64_to_float(r2i) * g.s32sq;
+                const float r = sqrtf(r2);
+                const float uu = s64_to_float((long long)r2i - (long long)c.rm2_fix) * c.s2hinv / (r + c.rmf);
+                const float q = 1.0f - uu * uu;
+                acc += get_s(pj) * (-c.Eaf * q * q);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
 template <class M>
-__global__ void __launch_bounds__(SC_TPB) k_chain(Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
-                                                  SuperCaps cp, GroupAux aux, const uint16_t* __restrict__ nbr,
-                                                  const int* __restrict__ nnb, const typename M::real* __restrict__ ds,
+__global__ void __launch_bounds__(SC_TPB) k_chain(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
+                                                  SuperGrid G, SuperCaps cp, GroupAux aux,
+                                                  const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
+                                                  const typename M::real* __restrict__ ds,
                                                   typename M::real2* __restrict__ sA, const int* __restrict__ wpart,
                                                   Status* st)
 {
@@ -1221,89 +1340,162 @@ __global__ void __launch_bounds__(SC_TPB) k_chain(Geom g, Coef c, const typename
     using real = typename M::real;
     if (halted(st)) return;
     const int nw = st->nwin;
-    const int lane = threadIdx.x & 31;
-    const real* s_only = reinterpret_cast<const real*>(sA);  // s_j at even offsets (A is written here)
-    for (int k = (int)((blockIdx.x * SC_TPB + threadIdx.x) >> 5); k < nw; k += (int)((gridDim.x * SC_TPB) >> 5)) {
-        const int p = wpart[k];
-        const int ra = __ldg(aux.roff + p), b = ra / cp.seg;
-        const int len = row_len(__ldg(nnb + p));
-        const pos_t pi = pos[p];
-        const uint16_t* row = nbr + ra;
-        const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
-        real acc = 0;
-        for (int e = lane; e < len; e += 32) {
-            const int jj = __ldg(sidx + __ldg(row + e));
-            // the force of jj needs A_p: if it was tagged whole, it now goes on the general list
-            if constexpr (!M::fp64) {
-                if (atomicExch(reinterpret_cast<float*>(static_cast<float4*>(aux.fcore) + jj) + 3, 0.0f) != 0.0f)
-                    aux.glist[atomicAdd(&st->ngen, 1)] = jj;
-            }
-            if constexpr (M::fp64) {
-                const double r2 = r2_d<M>(pi, pos[jj], g);
-                if (r2 > c.rr2 && r2 < c.ra2) acc += s_only[2 * (size_t)jj] * Va_d(sqrt(r2), c);
-            } else {
-                const unsigned long long r2i = r2_fix(pi, pos[jj]);
-                if (r2i > c.rr2_fix && r2i < c.ra2_fix) {
-                    const float r2 = u64_to_float(r2i) * g.s32sq;
-                    const float r = sqrtf(r2);
-                    const float uu = s64_to_float((long long)r2i - (long long)c.rm2_fix) * c.s2hinv / (r + c.rmf);
-                    const float q = 1.0f - uu * uu;
-                    acc += s_only[2 * (size_t)jj] * (-c.Eaf * q * q);
-                }
-            }
+    const int warp = threadIdx.x >> 5;
+    if (nw <= n / DENSE_DIV) {
+        for (int k = blockIdx.x * ROW_WARPS + warp; k < nw; k += gridDim.x * ROW_WARPS) {
+            const int p = wpart[k];
+            const int ra = __ldg(aux.roff + p), b = ra / cp.seg;
+            const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
+            const real acc = chain_row<M>(pos[p], nbr + ra, row_len(__ldg(nnb + p)), [&](int m, int& jj) {
+                jj = __ldg(sidx + m);
+                return pos[jj];
+            }, c, g, aux, st);
+            if ((threadIdx.x & 31) == 0) sA[p].y = ds[p] * acc;
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) sA[p].y = ds[p] * acc;
+        return;
+    }
+    // dense: the group's own window particles
+    const int b = blockIdx.x, t = threadIdx.x;
+    const int p0 = __ldg(G.cell_start + OWN_CELLS * b);
+    const int n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
+    __shared__ int s_n;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const DenseLayout ly = dense_layout(cp, sizeof(pos_t), 4);
+    pos_t* spos = (pos_t*)smem;
+    int* ssidx = (int*)(smem + ly.extra);
+    int* plist = (int*)(smem + ly.plist);
+    if (t == 0) s_n = 0;
+    __syncthreads();
+    for (int j = t; j < n_own; j += SC_TPB)
+        if (ds[p0 + j] != (real)0) plist[atomicAdd(&s_n, 1)] = j;
+    __syncthreads();
+    const int nl = s_n;
+    if (nl == 0) return;
+    stage_by_table(aux.stage_idx + (size_t)b * cp.smax, __ldg(aux.meta + b).x, [&](int m, int jj) {
+        spos[m] = pos[jj];
+        ssidx[m] = jj;
+    });
+    __syncthreads();
+    for (int u = warp; u < nl; u += ROW_WARPS) {
+        const int p = p0 + plist[u];
+        const real acc = chain_row<M>(pos[p], nbr + __ldg(aux.roff + p), row_len(__ldg(nnb + p)), [&](int m, int& jj) {
+            jj = ssidx[m];
+            return spos[m];
+        }, c, g, aux, st);
+        if ((t & 31) == 0) sA[p].y = ds[p] * acc;
     }
 }
 
 // ================================================================ pass 2: forces + BAOAB
-// k_force_rows: the whole force of every particle on the general list (not
-// saturated, a neighbour of a window particle, more near entries than the
-// close list holds, or any particle in the FP64 mode): one warp per particle,
-// one lane per entry of its full row, neighbours and their s_j (in the
-// positions' spare word) and A_j read through the group's staged-index
-// table, lane sums reduced in a fixed tree.  The result overwrites the
-// particle's force slot with the tag set.
+// k_force_rows: the whole force of every particle without a tagged whole
+// force (not saturated, a neighbour of a window particle, more near entries
+// than the close list holds, or any particle in the FP64 mode), every term
+// of its full row; neighbours carry s_j in the positions' spare word.  The
+// result overwrites the particle's force slot with the tag set.
+template <class M, class Fetch>
+__device__ __forceinline__ void force_row(const typename M::pos_t& pi, typename M::real si, typename M::real Ai,
+                                          const uint16_t* __restrict__ row, int len, Fetch&& fetch, const Coef& c,
+                                          const Geom& g, typename M::real f[3])
+{
+    using pos_t = typename M::pos_t;
+    using real = typename M::real;
+    const int lane = threadIdx.x & 31;
+    real fx = 0, fy = 0, fz = 0;
+    for (int e = lane; e < len; e += 32) {
+        real Aj;
+        const pos_t pj = fetch(__ldg(row + e), Aj);
+        if constexpr (M::fp64) pair_f64(pi, si, Ai, pj, get_s(pj), Aj, c, g, fx, fy, fz);
+        else pair_f32(pi, si, Ai, pj, get_s(pj), Aj, c, g, fx, fy, fz);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        fx += __shfl_xor_sync(0xffffffffu, fx, o);
+        fy += __shfl_xor_sync(0xffffffffu, fy, o);
+        fz += __shfl_xor_sync(0xffffffffu, fz, o);
+    }
+    f[0] = fx;
+    f[1] = fy;
+    f[2] = fz;
+}
+
 template <class M>
-__global__ void __launch_bounds__(TPB) k_force_rows(Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
-                                                    SuperCaps cp, GroupAux aux, const uint16_t* __restrict__ nbr,
-                                                    const int* __restrict__ nnb,
-                                                    const typename M::real2* __restrict__ sA, const Status* st)
+__device__ __forceinline__ void force_out(void* fcore, int p, const typename M::real f[3])
+{
+    if constexpr (M::fp64) static_cast<F64x4*>(fcore)[p] = F64x4{f[0], f[1], f[2], 1.0};
+    else static_cast<float4*>(fcore)[p] = make_float4(f[0], f[1], f[2], 1.0f);
+}
+
+template <class M>
+__device__ __forceinline__ bool tagged_whole(const void* fcore, int p)
+{
+    if constexpr (M::fp64) return static_cast<const F64x4*>(fcore)[p].w != 0.0;
+    else return static_cast<const float4*>(fcore)[p].w != 0.0f;
+}
+
+template <class M>
+__global__ void __launch_bounds__(SC_TPB) k_force_rows(int n, Geom g, Coef c,
+                                                       const typename M::pos_t* __restrict__ pos, SuperGrid G,
+                                                       SuperCaps cp, GroupAux aux, const uint16_t* __restrict__ nbr,
+                                                       const int* __restrict__ nnb,
+                                                       const typename M::real2* __restrict__ sA, const Status* st)
 {
     using pos_t = typename M::pos_t;
     using real = typename M::real;
     if (halted(st)) return;
     const int ng = st->ngen;
     const bool useA = st->nwin > 0;  // A_j != 0 only for window particles
-    const int lane = threadIdx.x & 31;
-    for (int k = (int)((blockIdx.x * TPB + threadIdx.x) >> 5); k < ng; k += (int)((gridDim.x * TPB) >> 5)) {
-        const int p = aux.glist[k];
-        const int ra = __ldg(aux.roff + p), b = ra / cp.seg;
-        const int len = row_len(__ldg(nnb + p));
+    const int warp = threadIdx.x >> 5;
+    if (ng <= n / DENSE_DIV) {
+        for (int k = blockIdx.x * ROW_WARPS + warp; k < ng; k += gridDim.x * ROW_WARPS) {
+            const int p = aux.glist[k];
+            const int ra = __ldg(aux.roff + p), b = ra / cp.seg;
+            const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
+            const pos_t pi = pos[p];
+            real f[3];
+            force_row<M>(pi, get_s(pi), useA ? sA[p].y : (real)0, nbr + ra, row_len(__ldg(nnb + p)),
+                         [&](int m, real& Aj) {
+                             const int jj = __ldg(sidx + m);
+                             Aj = useA ? sA[jj].y : (real)0;
+                             return pos[jj];
+                         },
+                         c, g, f);
+            if ((threadIdx.x & 31) == 0) force_out<M>(aux.fcore, p, f);
+        }
+        return;
+    }
+    // dense: the group's own particles without a whole-force tag
+    const int b = blockIdx.x, t = threadIdx.x;
+    const int p0 = __ldg(G.cell_start + OWN_CELLS * b);
+    const int n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
+    __shared__ int s_n;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const DenseLayout ly = dense_layout(cp, sizeof(pos_t), sizeof(real));
+    pos_t* spos = (pos_t*)smem;
+    real* sAj = (real*)(smem + ly.extra);
+    int* plist = (int*)(smem + ly.plist);
+    if (t == 0) s_n = 0;
+    __syncthreads();
+    for (int j = t; j < n_own; j += SC_TPB)
+        if (!tagged_whole<M>(aux.fcore, p0 + j)) plist[atomicAdd(&s_n, 1)] = j;
+    __syncthreads();
+    const int nl = s_n;
+    if (nl == 0) return;
+    stage_by_table(aux.stage_idx + (size_t)b * cp.smax, __ldg(aux.meta + b).x, [&](int m, int jj) {
+        spos[m] = pos[jj];
+        sAj[m] = useA ? sA[jj].y : (real)0;
+    });
+    __syncthreads();
+    for (int u = warp; u < nl; u += ROW_WARPS) {
+        const int p = p0 + plist[u];
         const pos_t pi = pos[p];
-        const real si = get_s(pi), Ai = useA ? sA[p].y : (real)0;
-        const uint16_t* row = nbr + ra;
-        const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
-        real fx = 0, fy = 0, fz = 0;
-        for (int e = lane; e < len; e += 32) {
-            const int jj = __ldg(sidx + __ldg(row + e));
-            const pos_t pj = pos[jj];
-            const real Aj = useA ? sA[jj].y : (real)0;
-            if constexpr (M::fp64) pair_f64(pi, si, Ai, pj, get_s(pj), Aj, c, g, fx, fy, fz);
-            else pair_f32(pi, si, Ai, pj, get_s(pj), Aj, c, g, fx, fy, fz);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            fx += __shfl_xor_sync(0xffffffffu, fx, o);
-            fy += __shfl_xor_sync(0xffffffffu, fy, o);
-            fz += __shfl_xor_sync(0xffffffffu, fz, o);
-        }
-        if (lane == 0) {
-            if constexpr (M::fp64) static_cast<F64x4*>(aux.fcore)[p] = F64x4{fx, fy, fz, 1.0};
-            else static_cast<float4*>(aux.fcore)[p] = make_float4(fx, fy, fz, 1.0f);
-        }
+        real f[3];
+        force_row<M>(pi, get_s(pi), useA ? sA[p].y : (real)0, nbr + __ldg(aux.roff + p), row_len(__ldg(nnb + p)),
+                     [&](int m, real& Aj) {
+                         Aj = sAj[m];
+                         return spos[m];
+                     },
+                     c, g, f);
+        if ((t & 31) == 0) force_out<M>(aux.fcore, p, f);
     }
 }
 
