@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="short run for profilers: the equilibrated workload (cached under /tmp), one forced "
+                         "list build, one force evaluation and 6 steps; prints no JSON line")
     return ap.parse_args()
 
 
@@ -211,10 +214,36 @@ def reference_main(args):
 
 
 # ------------------------------------------------------------------ B300 arm
+def profile_run(args):
+    """A few launches of every kernel on the bench workload, for a profiler: the
+    state after args.equil steps (cached between runs), one forced list build, one
+    force evaluation and 6 steps."""
+    from paper_2609_07842_b300 import inputs, vbc
+    prm = vbc.params(E_a=args.E_a, f=args.valency)
+    cache = f"/tmp/vbc_bench_state_n{args.n}_rho{args.rho}_v{args.valency:g}_e{args.equil}.npz"
+    if not os.path.exists(cache):
+        pos, L = inputs.uniform_positions(args.n, args.rho, seed=SEED)
+        vel = inputs.maxwell_velocities(args.n, KT, seed=SEED + 1)
+        with vbc.System(pos, L, prm, vel=vel, skin=SKIN, seed=SEED) as s:
+            s.step(args.equil, DT, KT, GAMMA)
+            p, v, _ = s.get_state()
+        np.savez(cache, pos=p, vel=v, L=L)
+    d = np.load(cache)
+    with vbc.System(d["pos"], float(d["L"]), prm, vel=d["vel"], skin=SKIN, seed=SEED) as s:
+        s.build_neighbors()
+        s.compute(F=np.zeros((args.n, 3)))
+        s.step(6, DT, KT, GAMMA)
+        st = s.stats()
+    print(f"profile run: n={args.n} list mean {st.nlist_mean:.2f} unsaturated {st.unsaturated}", file=sys.stderr)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_main(args)
+    if args.profile_run:
+        return profile_run(args)
 
     import torch
     import torch.distributed as dist
