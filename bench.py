@@ -417,7 +417,8 @@ def main():
             "nlist_mean": k_mean, "in_window_fraction": phi, "steps_per_rebuild": rebuild_every,
             "unsaturated_fraction": st2.unsaturated / args.n,
             "capacities": {"stage": st2.stage_cap, "group": st2.group_cap, "segment": st2.segment_cap,
-                           "list": st2.nlist_cap, "groups": st2.groups},
+                           "list": st2.nlist_cap, "groups": st2.groups,
+                           "grows_in_timed_region": st1.capacity_grows - st0.capacity_grows},
             "energy_per_particle": r.energy / args.n,
             "gpu_launches": launches,
             "clocks": clk,

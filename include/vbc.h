@@ -102,7 +102,9 @@ typedef struct {
     int32_t stage_cap;         /* staged particles per cell group (current capacity) */
     int32_t group_cap;         /* particles per cell group (current capacity) */
     int32_t segment_cap;       /* list entries per cell group (current capacity) */
-    int32_t groups;            /* cell groups (thread blocks of the list-walking kernels) */
+    int32_t groups;            /* cell groups (units of the list build and of the dense row walks) */
+    int64_t capacity_grows;    /* capacity growths after an overflow since creation (each resumes the
+                                  interrupted call from the overflowing build) */
 } vbc_stats;
 
 /*

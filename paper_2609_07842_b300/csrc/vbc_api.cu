@@ -107,8 +107,9 @@ struct vbc_system {
     int* close_k = nullptr;     // [n][CLOSE_K] near entries as sorted indices (count, soft-core force)
     void* fcore = nullptr;      // [n] forces and tags, float4 or F64x4 (k_count_near, k_force_rows -> k_step)
     int* glist = nullptr;       // [n] particles whose force k_force_rows forms
-    int rows_grid = 0;          // blocks of the count's full-row walk
-    int chain_grid = 0;         // blocks of the list-walking grids (count rows, chain-rule pass)
+    int sms = 148;              // SMs of the device
+    int row_grid = 1;           // blocks of the row walks (count rows, chain-rule pass, force rows)
+    long long grows = 0;        // capacity growths after an overflow
     void *ds = nullptr, *sA = nullptr;
     Status* st = nullptr;
     Status* st_host = nullptr;  // pinned
@@ -384,8 +385,19 @@ int configure_smem(vbc_system* s)
     VBC_TRY(set_smem(k_energy<M>, s->smem_energy()));
     VBC_TRY(set_smem(k_store_nlist, s->smem_store()));
     VBC_TRY(set_smem(k_count_rows<M>, s->smem_rows(0)));
-    VBC_TRY(set_smem(k_chain<M>, s->smem_rows(4)));
+    VBC_TRY(set_smem(k_chain<M>, s->smem_rows(0)));
     VBC_TRY(set_smem(k_force_rows<M>, s->smem_rows(s->real_bytes())));
+    // the row walks run as many blocks as stay resident together
+    int occ = 1 << 30;
+    const auto resident = [&](const void* kern, size_t smem) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, SC_TPB, smem) != cudaSuccess || b < 1) b = 1;
+        occ = std::min(occ, b);
+    };
+    resident((const void*)k_count_rows<M>, s->smem_rows(0));
+    resident((const void*)k_chain<M>, s->smem_rows(0));
+    resident((const void*)k_force_rows<M>, s->smem_rows(s->real_bytes()));
+    s->row_grid = std::max(1, std::min(s->nsc, occ * s->sms));
     return VBC_OK;
 }
 
@@ -436,13 +448,13 @@ int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window)
         k_count_near<M><<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>((int)s->n, s->geom, s->coef, pos, s->aux(),
                                                                        s->nnb, (real*)s->ds, (real2*)s->sA, out,
                                                                        s->ulist, s->st);
-        k_count_rows<M><<<s->nsc, SC_TPB, s->smem_rows(0), s->stream>>>(
-            (int)s->n, s->geom, s->coef, pos, s->grid(), s->caps(), s->aux(), s->nbr, s->nnb, s->id, (real*)s->ds,
+        k_count_rows<M><<<s->row_grid, SC_TPB, s->smem_rows(0), s->stream>>>(
+            (int)s->n, s->nsc, s->geom, s->coef, pos, s->grid(), s->caps(), s->aux(), s->nbr, s->nnb, s->id, (real*)s->ds,
             (real2*)s->sA, out, s->ulist, s->wpart, s->st);
     }
     {
         Timed t(s, VBC_K_CHAIN);
-        k_chain<M><<<s->nsc, SC_TPB, s->smem_rows(4), s->stream>>>((int)s->n, s->geom, s->coef, pos, s->grid(),
+        k_chain<M><<<s->row_grid, SC_TPB, s->smem_rows(0), s->stream>>>((int)s->n, s->nsc, s->geom, s->coef, pos, s->grid(),
                                                                     s->caps(), s->aux(), s->nbr, s->nnb,
                                                                     (const real*)s->ds, (real2*)s->sA, s->wpart,
                                                                     s->st);
@@ -460,8 +472,8 @@ int enqueue_force(vbc_system* s, const StepArgs& a)
     pos_t* pos_next = (pos_t*)s->pos[s->cur ^ 1];
     {
         Timed t(s, VBC_K_FORCE);
-        k_force_rows<M><<<s->nsc, SC_TPB, s->smem_rows(s->real_bytes()), s->stream>>>(
-            n, s->geom, s->coef, pos, s->grid(), s->caps(), s->aux(), s->nbr, s->nnb, (const real2*)s->sA, s->st);
+        k_force_rows<M><<<s->row_grid, SC_TPB, s->smem_rows(s->real_bytes()), s->stream>>>(
+            n, s->nsc, s->geom, s->coef, pos, s->grid(), s->caps(), s->aux(), s->nbr, s->nnb, (const real2*)s->sA, s->st);
         k_step<M, EPI><<<blocks_for(n, TPB), TPB, 0, s->stream>>>(n, s->geom, s->aux(), s->id, pos_next,
                                                                   (const pos_t*)s->xref, a, s->st);
     }
@@ -510,6 +522,7 @@ bool needs_growth(const vbc_system* s) { return s->st_host->overflow || s->st_ho
 int grow(vbc_system* s)
 {
     VBC_CUDA(cudaStreamSynchronize(s->stream));
+    s->grows += 1;
     const Status& h = *s->st_host;
     if (h.overflow) {
         const int need = h.max_nnb;
@@ -932,9 +945,7 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess || sms < 1)
             sms = 148;
-        s->chain_grid = std::max(1, std::min(2 * sms, s->nsc));
-        // one warp per particle the count walks in full: about 1 % of them at high counts
-        s->rows_grid = std::max(s->chain_grid, blocks_for(s->n, 256));
+        s->sms = sms;
     }
     if (cfg->stream) {
         s->stream = (cudaStream_t)cfg->stream;
@@ -1226,6 +1237,7 @@ int vbc_get_stats(vbc_system* s, vbc_stats* out)
     out->group_cap = s->omax;
     out->segment_cap = s->seg;
     out->groups = s->nsc;
+    out->capacity_grows = s->grows;
     return VBC_OK;
 }
 

@@ -624,58 +624,68 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
             const int k0 = kb + (d / 3 - 1) * (SX * SY) + (d % 3 - 1) * SX - 1;
             const int e = T.off[k0 + 3];
             for (int base = T.off[k0]; base < e; base += 32) {
-                // test up to 32 candidates into bit masks, then write the accepted ones
+                // test up to 32 candidates into bit masks, then write the accepted ones.  Each
+                // mask takes one bit per candidate, shifted in from the bottom, so candidate u
+                // ends at bit cnt - 1 - u; in the FP32 mode the bit is the sign of r^2 minus
+                // the threshold, moved in by a funnel shift (the sign of a float difference
+                // is that of the exact one).
                 const int cnt = min(32, e - base);
-                uint32_t mnear = 0u, mfar = 0u, mfc = 0u;
+                uint32_t mnear = 0u, mlist = 0u, mrl = 0u;
 #pragma unroll 4
                 for (int u = 0; u < cnt; ++u) {
                     const int m = base + u;
-                    int cl;
-                    bool rl;
                     if constexpr (REL) {
                         const float4 q = spos[m];
                         const float dx = pi.x - q.x, dy = pi.y - q.y, dz = pi.z - q.z;
                         const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz));
-                        cl = r2 >= lp.rlist2_f ? -1 : (r2 < lp.near2_f ? 0 : 1);
-                        rl = r2 <= lp.rl2_f;
+                        mnear = __funnelshift_l(__float_as_uint(r2 - lp.near2_f), mnear, 1);
+                        mlist = __funnelshift_l(__float_as_uint(r2 - lp.rlist2_f), mlist, 1);
+                        mrl = __funnelshift_l(__float_as_uint(r2 - lp.rl2_f), mrl, 1);
                     } else if constexpr (M::fp64) {
                         double dx, dy, dz;
                         ModeF64::delta64(pi, spos[m], g, dx, dy, dz);
                         const double r2 = dx * dx + dy * dy + dz * dz;
-                        cl = r2 >= lp.rlist2 ? -1 : (r2 < lp.near2 ? 0 : 1);
-                        rl = r2 <= lp.rl2;
+                        mnear = (mnear << 1) | (r2 < lp.near2 ? 1u : 0u);
+                        mlist = (mlist << 1) | (r2 < lp.rlist2 ? 1u : 0u);
+                        mrl = (mrl << 1) | (r2 <= lp.rl2 ? 1u : 0u);
                     } else {
                         const int dx = pi.x - spos[m].x, dy = pi.y - spos[m].y, dz = pi.z - spos[m].z;
                         const unsigned long long r2 = (unsigned long long)((long long)dx * dx) +
                                                       (unsigned long long)((long long)dy * dy) +
                                                       (unsigned long long)((long long)dz * dz);
-                        cl = r2 >= lp.rlist2_fix ? -1 : (r2 < lp.near2_fix ? 0 : 1);
-                        rl = r2 <= lp.rl2_fix;
+                        mnear = (mnear << 1) | (r2 < lp.near2_fix ? 1u : 0u);
+                        mlist = (mlist << 1) | (r2 < lp.rlist2_fix ? 1u : 0u);
+                        mrl = (mrl << 1) | (r2 <= lp.rl2_fix ? 1u : 0u);
                     }
-                    const uint32_t bit = m != mself ? 1u << u : 0u;
-                    mnear |= cl == 0 ? bit : 0u;
-                    mfar |= cl == 1 ? bit : 0u;
-                    mfc |= cl == 1 && rl ? bit : 0u;
                 }
-                // accepted entries go out four at a time: near ones fill 8-byte words from the
-                // front of the scratch row, far ones from the back (in reverse order)
+                // the particle itself (r = 0) is a candidate of its own cell
+                if ((unsigned)(mself - base) < (unsigned)cnt) {
+                    const uint32_t sb = ~(1u << (cnt - 1 - (mself - base)));
+                    mnear &= sb;
+                    mlist &= sb;
+                }
+                uint32_t mfar = mlist & ~mnear, mfc = mfar & mrl;
+                const int top = base + cnt - 1;  // the candidate at bit 0
+                // accepted entries go out four at a time, in candidate order (highest bit
+                // first): near ones fill 8-byte words from the front of the scratch row, far
+                // ones from the back (in reverse order)
                 while (mnear) {
-                    const int u = __ffs(mnear) - 1;
-                    mnear &= mnear - 1u;
-                    bufn = (bufn >> 16) | ((unsigned long long)(base + u) << 48);
+                    const int hb = 31 - __clz(mnear);
+                    mnear ^= 1u << hb;
+                    bufn = (bufn >> 16) | ((unsigned long long)(top - hb) << 48);
                     if ((++nn & 3) == 0 && nn + nf <= cp.cap) *reinterpret_cast<unsigned long long*>(row + nn - 4) = bufn;
                 }
                 while (mfar) {
-                    const int u = __ffs(mfar) - 1;
-                    mfar &= mfar - 1u;
-                    buff = (buff << 16) | (unsigned long long)(base + u);
+                    const int hb = 31 - __clz(mfar);
+                    mfar ^= 1u << hb;
+                    buff = (buff << 16) | (unsigned long long)(top - hb);
                     if ((++nf & 3) == 0 && nn + nf <= cp.cap)
                         *reinterpret_cast<unsigned long long*>(row + cp.cap - nf) = buff;
                 }
                 while (mfc && nfc < CLOSE_K) {
-                    const int u = __ffs(mfc) - 1;
-                    mfc &= mfc - 1u;
-                    cv[nfc++] = base + u;
+                    const int hb = 31 - __clz(mfc);
+                    mfc ^= 1u << hb;
+                    cv[nfc++] = top - hb;
                 }
             }
         }
@@ -1128,18 +1138,57 @@ __global__ void __launch_bounds__(TPB) k_count_near(int n, Geom g, Coef c, typen
 }
 
 // ================================================================ row walks
-// k_count_rows, k_chain and k_force_rows walk full list rows, one warp per
-// particle and one lane per entry, for the particles on their work lists.
-// Each picks its mode on the device from the list length: sparse (a warp per
-// listed particle, neighbours read through the group's staged-index table)
-// while the list holds at most n / DENSE_DIV particles, dense otherwise (one
-// block per cell group: the group stages its neighbourhood in shared memory
-// and its warps walk the rows of its listed particles from there).  A row is
-// walked in the same order and reduced in the same fixed tree either way, so
-// the mode does not change a bit of the result.  The grid is one block per
-// cell group in both modes.
+// k_count_rows, k_chain and k_force_rows walk the full list rows of the
+// particles on their work lists.  Each picks its mode on the device from the
+// list length.  Sparse, while the list holds at most n / DENSE_DIV particles:
+// one warp per listed particle, one lane per entry, neighbours read through
+// the group's staged-index table.  Dense otherwise: one block per cell group,
+// which stages its neighbourhood in shared memory; a lane group of tpp
+// threads walks each listed own particle's row, tpp the largest power of two
+// (at most 32) with (listed particles) * tpp <= SC_TPB, each thread taking
+// every tpp-th 4-entry chunk.  The order of the terms depends only on the row
+// and the mode, so every result is a function of the state alone.  Both modes
+// run a grid that stays resident (a few blocks per SM), the dense one taking
+// the cell groups in a grid-stride loop.
 constexpr int DENSE_DIV = 16;
 constexpr int ROW_WARPS = SC_TPB / 32;
+
+__device__ __forceinline__ int dense_tpp(int nl)
+{
+    int t = 32;
+    while (t > 1 && nl * t > SC_TPB) t >>= 1;
+    return t;
+}
+
+// Sparse walk: entry e on lane e mod 32.
+template <class Visit>
+__device__ __forceinline__ void walk_lanes(const uint16_t* __restrict__ row, int len, Visit&& visit)
+{
+    for (int e = threadIdx.x & 31; e < len; e += 32) visit((int)__ldg(row + e));
+}
+
+// Dense walk: 4-entry chunk k on thread k mod tpp of the lane group.  Rows
+// start on 4-entry boundaries; the pads after the last entry are skipped.
+template <class Visit>
+__device__ __forceinline__ void walk_chunks(const uint16_t* __restrict__ row, int len, int sub, int tpp, Visit&& visit)
+{
+    for (int e0 = 4 * sub; e0 < len; e0 += 4 * tpp) {
+        int h[4];
+        unpack4(__ldg(reinterpret_cast<const uint2*>(row + e0)), h);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (e0 + k < len) visit(h[k]);
+    }
+}
+
+// Sum over an aligned lane group of w lanes (a power of two); every lane of
+// the warp takes part.
+template <class T>
+__device__ __forceinline__ T group_sum(T v, int w)
+{
+    for (int o = w >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 
 // Shared memory of a dense row walk: staged positions, one extra value per
 // staged particle, and a list of own particles.
@@ -1171,39 +1220,61 @@ __device__ __forceinline__ void stage_by_table(const int* __restrict__ sidx, int
     }
 }
 
-// Count of one row, on every lane of the warp: s_i, s'_i and (if wanted) n_i.
-template <class M, class Fetch>
-__device__ __forceinline__ void count_row(const typename M::pos_t& pi, const uint16_t* __restrict__ row, int len,
-                                          Fetch&& fetch, const Coef& c, const Geom& g, bool want_n,
-                                          typename M::real& s, typename M::real& ds, double& n_val)
+// Lists the own particles of group b that pick(j) selects (j from 0); the
+// whole block calls it.  Returns their number.
+template <class Pick>
+__device__ __forceinline__ int list_own(int n_own, int* plist, int* s_n, Pick&& pick)
 {
-    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) *s_n = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < n_own; j += SC_TPB)
+        if (pick(j)) plist[atomicAdd(s_n, 1)] = j;
+    __syncthreads();
+    return *s_n;
+}
+
+// Runs body(u, sub, tpp) for the listed particles of a dense walk: slot u of
+// the list (u >= nl on idle lanes, which must still take part in the lane
+// group's sums), thread sub of its lane group.
+template <class Body>
+__device__ __forceinline__ void dense_rounds(int nl, Body&& body)
+{
+    const int tpp = dense_tpp(nl), per_warp = 32 / tpp;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int base = warp * per_warp; base < nl; base += ROW_WARPS * per_warp)
+        body(base + lane / tpp, lane & (tpp - 1), tpp);
+}
+
+// Count of one row over a lane group of `width` lanes, the result on every
+// lane of it: s_i, s'_i and (if wanted) n_i.  walk(visit) calls visit(m)
+// for this lane's entries.
+template <class M, class Walk, class Fetch>
+__device__ __forceinline__ void count_row(const typename M::pos_t& pi, Walk&& walk, int width, Fetch&& fetch,
+                                          const Coef& c, const Geom& g, bool want_n, typename M::real& s,
+                                          typename M::real& ds, double& n_val)
+{
     if constexpr (M::fp64) {
         double acc = 0.0;
-        for (int e = lane; e < len; e += 32) {
-            const double r2 = r2_d<M>(pi, fetch(__ldg(row + e)), g);
+        walk([&](int m) {
+            const double r2 = r2_d<M>(pi, fetch(m), g);
             if (r2 < c.rh2) acc += r2 <= c.rl2 ? 1.0 : omega_d(sqrt(r2), c.r_l, c.r_h);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        });
+        acc = group_sum(acc, width);
         s = omega_d(acc, c.fd, c.fd + 1.0);
         ds = domega_d(acc, c.fd, c.fd + 1.0);
         n_val = acc;
     } else {
         long long full = 0;
         unsigned long long q = 0;
-        for (int e = lane; e < len; e += 32) {
-            const unsigned long long r2 = r2_fix(pi, fetch(__ldg(row + e)));
+        walk([&](int m) {
+            const unsigned long long r2 = r2_fix(pi, fetch(m));
             if (r2 < c.rh2_fix) {
                 if (r2 <= c.rl2_fix) ++full;
                 else q += window_weight_fix31(r2, r2 - c.rl2_fix, c.rl_s, c.w_s);
             }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            full += __shfl_xor_sync(0xffffffffu, full, o);
-            q += __shfl_xor_sync(0xffffffffu, q, o);
-        }
+        });
+        full = group_sum(full, width);
+        q = group_sum(q, width);
         const long long Tf = (full - c.fd_int) * 2147483648LL + (long long)q - c.fd_frac_fix;
         switch_from_fix(Tf, s, ds);
         n_val = 0.0;
@@ -1211,7 +1282,7 @@ __device__ __forceinline__ void count_row(const typename M::pos_t& pi, const uin
     }
 }
 
-// Results of one counted row (lane 0 of the warp).
+// Results of one counted row (one lane of the group).
 template <class M>
 __device__ __forceinline__ void count_row_out(int p, typename M::real s, typename M::real ds, double n_val,
                                               typename M::pos_t* __restrict__ pos, typename M::real* __restrict__ ds_out,
@@ -1232,7 +1303,7 @@ __device__ __forceinline__ void count_row_out(int p, typename M::real s, typenam
 }
 
 template <class M>
-__global__ void __launch_bounds__(SC_TPB) k_count_rows(int n, Geom g, Coef c, typename M::pos_t* __restrict__ pos,
+__global__ void __launch_bounds__(SC_TPB) k_count_rows(int n, int ngroups, Geom g, Coef c, typename M::pos_t* __restrict__ pos,
                                                        SuperGrid G, SuperCaps cp, GroupAux aux,
                                                        const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
                                                        const int* __restrict__ id, typename M::real* __restrict__ ds_out,
@@ -1244,71 +1315,67 @@ __global__ void __launch_bounds__(SC_TPB) k_count_rows(int n, Geom g, Coef c, ty
     using real = typename M::real;
     if (halted(st)) return;
     const int nu = st->nu;
-    const int warp = threadIdx.x >> 5;
+    const bool want_n = out.n_out != nullptr;
     if (nu <= n / DENSE_DIV) {
-        for (int k = blockIdx.x * ROW_WARPS + warp; k < nu; k += gridDim.x * ROW_WARPS) {
+        for (int k = blockIdx.x * ROW_WARPS + (threadIdx.x >> 5); k < nu; k += gridDim.x * ROW_WARPS) {
             const int p = ulist[k];
             const int ra = __ldg(aux.roff + p), b = ra / cp.seg;
             const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
+            const uint16_t* row = nbr + ra;
+            const int len = row_len(__ldg(nnb + p));
             real s, ds;
             double n_val;
-            count_row<M>(pos[p], nbr + ra, row_len(__ldg(nnb + p)), [&](int m) { return pos[__ldg(sidx + m)]; }, c, g,
-                         out.n_out != nullptr, s, ds, n_val);
+            count_row<M>(pos[p], [&](auto&& v) { walk_lanes(row, len, v); }, 32,
+                         [&](int m) { return pos[__ldg(sidx + m)]; }, c, g, want_n, s, ds, n_val);
             if ((threadIdx.x & 31) == 0) count_row_out<M>(p, s, ds, n_val, pos, ds_out, sA, id, out, wpart, st);
         }
         return;
     }
-    // dense: the group's own particles that k_count_near marked (s'_i = NaN)
-    const int b = blockIdx.x, t = threadIdx.x;
-    const int p0 = __ldg(G.cell_start + OWN_CELLS * b);
-    const int n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
+    // dense: the own particles that k_count_near marked (s'_i = NaN), group by group
     __shared__ int s_n;
     extern __shared__ __align__(16) unsigned char smem[];
     const DenseLayout ly = dense_layout(cp, sizeof(pos_t), 0);
     pos_t* spos = (pos_t*)smem;
     int* plist = (int*)(smem + ly.plist);
-    if (t == 0) s_n = 0;
-    __syncthreads();
-    for (int j = t; j < n_own; j += SC_TPB)
-        if (isnan(ds_out[p0 + j])) plist[atomicAdd(&s_n, 1)] = j;
-    __syncthreads();
-    const int nl = s_n;
-    if (nl == 0) return;
-    stage_by_table(aux.stage_idx + (size_t)b * cp.smax, __ldg(aux.meta + b).x,
-                   [&](int m, int jj) { spos[m] = pos[jj]; });
-    __syncthreads();
-    for (int u = warp; u < nl; u += ROW_WARPS) {
-        const int p = p0 + plist[u];
-        real s, ds;
-        double n_val;
-        count_row<M>(pos[p], nbr + __ldg(aux.roff + p), row_len(__ldg(nnb + p)), [&](int m) { return spos[m]; }, c, g,
-                     out.n_out != nullptr, s, ds, n_val);
-        if ((t & 31) == 0) count_row_out<M>(p, s, ds, n_val, pos, ds_out, sA, id, out, wpart, st);
+    for (int b = blockIdx.x; b < ngroups; b += gridDim.x) {
+        __syncthreads();  // the previous group is done with the shared arrays
+        const int p0 = __ldg(G.cell_start + OWN_CELLS * b);
+        const int n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
+        const int nl = list_own(n_own, plist, &s_n, [&](int j) { return isnan(ds_out[p0 + j]); });
+        if (nl == 0) continue;
+        stage_by_table(aux.stage_idx + (size_t)b * cp.smax, __ldg(aux.meta + b).x,
+                       [&](int m, int jj) { spos[m] = pos[jj]; });
+        __syncthreads();
+        dense_rounds(nl, [&](int u, int sub, int tpp) {
+            const bool act = u < nl;
+            const int p = p0 + (act ? plist[u] : 0);
+            const uint16_t* row = nbr + __ldg(aux.roff + p);
+            const int len = act ? row_len(__ldg(nnb + p)) : 0;
+            real s, ds;
+            double n_val;
+            count_row<M>(pos[p], [&](auto&& v) { walk_chunks(row, len, sub, tpp, v); }, tpp,
+                         [&](int m) { return spos[m]; }, c, g, want_n, s, ds, n_val);
+            if (act && sub == 0) count_row_out<M>(p, s, ds, n_val, pos, ds_out, sA, id, out, wpart, st);
+        });
     }
 }
 
 // ================================================================ chain-rule pass
 // A_i = s'_i sum_j s_j V_a(r_ij) for the particles inside the switching
-// window (s'_i != 0), which k_count_rows listed.  Every list neighbour of a
-// window particle loses its whole-force tag (its window term needs A_i) and
-// joins the general list of k_force_rows.
-template <class M, class Fetch>
-__device__ __forceinline__ typename M::real chain_row(const typename M::pos_t& pi, const uint16_t* __restrict__ row,
-                                                      int len, Fetch&& fetch, const Coef& c, const Geom& g,
-                                                      GroupAux& aux, Status* st)
+// window (s'_i != 0), which k_count_rows listed.  In the sparse mode every
+// list neighbour of a window particle loses its whole-force tag (its window
+// term needs A_i) and joins the general list of k_force_rows.  In the dense
+// mode nearly every particle neighbours a window particle, so no tag is
+// cleared: k_force_rows, which makes the same mode test, then takes every
+// particle.
+template <class M, class Walk, class Fetch>
+__device__ __forceinline__ typename M::real chain_row(const typename M::pos_t& pi, Walk&& walk, int width,
+                                                      Fetch&& fetch, const Coef& c, const Geom& g)
 {
-    using pos_t = typename M::pos_t;
     using real = typename M::real;
-    const int lane = threadIdx.x & 31;
     real acc = 0;
-    for (int e = lane; e < len; e += 32) {
-        int jj;
-        const pos_t pj = fetch(__ldg(row + e), jj);
-        // the force of jj needs A_i: if it was tagged whole, it now goes on the general list
-        if constexpr (!M::fp64) {
-            if (atomicExch(reinterpret_cast<float*>(static_cast<float4*>(aux.fcore) + jj) + 3, 0.0f) != 0.0f)
-                aux.glist[atomicAdd(&st->ngen, 1)] = jj;
-        }
+    walk([&](int m) {
+        const auto pj = fetch(m);
         if constexpr (M::fp64) {
             const double r2 = r2_d<M>(pi, pj, g);
             if (r2 > c.rr2 && r2 < c.ra2) acc += get_s(pj) * Va_d(sqrt(r2), c);
@@ -1322,14 +1389,12 @@ __device__ __forceinline__ typename M::real chain_row(const typename M::pos_t& p
                 acc += get_s(pj) * (-c.Eaf * q * q);
             }
         }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    return acc;
+    });
+    return group_sum(acc, width);
 }
 
 template <class M>
-__global__ void __launch_bounds__(SC_TPB) k_chain(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
+__global__ void __launch_bounds__(SC_TPB) k_chain(int n, int ngroups, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
                                                   SuperGrid G, SuperCaps cp, GroupAux aux,
                                                   const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
                                                   const typename M::real* __restrict__ ds,
@@ -1340,49 +1405,50 @@ __global__ void __launch_bounds__(SC_TPB) k_chain(int n, Geom g, Coef c, const t
     using real = typename M::real;
     if (halted(st)) return;
     const int nw = st->nwin;
-    const int warp = threadIdx.x >> 5;
     if (nw <= n / DENSE_DIV) {
-        for (int k = blockIdx.x * ROW_WARPS + warp; k < nw; k += gridDim.x * ROW_WARPS) {
+        for (int k = blockIdx.x * ROW_WARPS + (threadIdx.x >> 5); k < nw; k += gridDim.x * ROW_WARPS) {
             const int p = wpart[k];
             const int ra = __ldg(aux.roff + p), b = ra / cp.seg;
             const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
-            const real acc = chain_row<M>(pos[p], nbr + ra, row_len(__ldg(nnb + p)), [&](int m, int& jj) {
-                jj = __ldg(sidx + m);
+            const uint16_t* row = nbr + ra;
+            const int len = row_len(__ldg(nnb + p));
+            const real acc = chain_row<M>(pos[p], [&](auto&& v) { walk_lanes(row, len, v); }, 32, [&](int m) {
+                const int jj = __ldg(sidx + m);
+                // the force of jj needs A_i: if it was tagged whole, it now goes on the general list
+                if constexpr (!M::fp64) {
+                    if (atomicExch(reinterpret_cast<float*>(static_cast<float4*>(aux.fcore) + jj) + 3, 0.0f) != 0.0f)
+                        aux.glist[atomicAdd(&st->ngen, 1)] = jj;
+                }
                 return pos[jj];
-            }, c, g, aux, st);
+            }, c, g);
             if ((threadIdx.x & 31) == 0) sA[p].y = ds[p] * acc;
         }
         return;
     }
-    // dense: the group's own window particles
-    const int b = blockIdx.x, t = threadIdx.x;
-    const int p0 = __ldg(G.cell_start + OWN_CELLS * b);
-    const int n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
+    // dense: the own window particles, group by group
     __shared__ int s_n;
     extern __shared__ __align__(16) unsigned char smem[];
-    const DenseLayout ly = dense_layout(cp, sizeof(pos_t), 4);
+    const DenseLayout ly = dense_layout(cp, sizeof(pos_t), 0);
     pos_t* spos = (pos_t*)smem;
-    int* ssidx = (int*)(smem + ly.extra);
     int* plist = (int*)(smem + ly.plist);
-    if (t == 0) s_n = 0;
-    __syncthreads();
-    for (int j = t; j < n_own; j += SC_TPB)
-        if (ds[p0 + j] != (real)0) plist[atomicAdd(&s_n, 1)] = j;
-    __syncthreads();
-    const int nl = s_n;
-    if (nl == 0) return;
-    stage_by_table(aux.stage_idx + (size_t)b * cp.smax, __ldg(aux.meta + b).x, [&](int m, int jj) {
-        spos[m] = pos[jj];
-        ssidx[m] = jj;
-    });
-    __syncthreads();
-    for (int u = warp; u < nl; u += ROW_WARPS) {
-        const int p = p0 + plist[u];
-        const real acc = chain_row<M>(pos[p], nbr + __ldg(aux.roff + p), row_len(__ldg(nnb + p)), [&](int m, int& jj) {
-            jj = ssidx[m];
-            return spos[m];
-        }, c, g, aux, st);
-        if ((t & 31) == 0) sA[p].y = ds[p] * acc;
+    for (int b = blockIdx.x; b < ngroups; b += gridDim.x) {
+        __syncthreads();  // the previous group is done with the shared arrays
+        const int p0 = __ldg(G.cell_start + OWN_CELLS * b);
+        const int n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
+        const int nl = list_own(n_own, plist, &s_n, [&](int j) { return ds[p0 + j] != (real)0; });
+        if (nl == 0) continue;
+        stage_by_table(aux.stage_idx + (size_t)b * cp.smax, __ldg(aux.meta + b).x,
+                       [&](int m, int jj) { spos[m] = pos[jj]; });
+        __syncthreads();
+        dense_rounds(nl, [&](int u, int sub, int tpp) {
+            const bool act = u < nl;
+            const int p = p0 + (act ? plist[u] : 0);
+            const uint16_t* row = nbr + __ldg(aux.roff + p);
+            const int len = act ? row_len(__ldg(nnb + p)) : 0;
+            const real acc = chain_row<M>(pos[p], [&](auto&& v) { walk_chunks(row, len, sub, tpp, v); }, tpp,
+                                          [&](int m) { return spos[m]; }, c, g);
+            if (act && sub == 0) sA[p].y = ds[p] * acc;
+        });
     }
 }
 
@@ -1390,32 +1456,25 @@ __global__ void __launch_bounds__(SC_TPB) k_chain(int n, Geom g, Coef c, const t
 // k_force_rows: the whole force of every particle without a tagged whole
 // force (not saturated, a neighbour of a window particle, more near entries
 // than the close list holds, or any particle in the FP64 mode), every term
-// of its full row; neighbours carry s_j in the positions' spare word.  The
+// of its full row; neighbours carry s_j in the positions' spare word.  When
+// k_chain ran dense (it cleared no tags) every particle is taken.  The
 // result overwrites the particle's force slot with the tag set.
-template <class M, class Fetch>
+template <class M, class Walk, class Fetch>
 __device__ __forceinline__ void force_row(const typename M::pos_t& pi, typename M::real si, typename M::real Ai,
-                                          const uint16_t* __restrict__ row, int len, Fetch&& fetch, const Coef& c,
-                                          const Geom& g, typename M::real f[3])
+                                          Walk&& walk, int width, Fetch&& fetch, const Coef& c, const Geom& g,
+                                          typename M::real f[3])
 {
-    using pos_t = typename M::pos_t;
     using real = typename M::real;
-    const int lane = threadIdx.x & 31;
     real fx = 0, fy = 0, fz = 0;
-    for (int e = lane; e < len; e += 32) {
+    walk([&](int m) {
         real Aj;
-        const pos_t pj = fetch(__ldg(row + e), Aj);
+        const auto pj = fetch(m, Aj);
         if constexpr (M::fp64) pair_f64(pi, si, Ai, pj, get_s(pj), Aj, c, g, fx, fy, fz);
         else pair_f32(pi, si, Ai, pj, get_s(pj), Aj, c, g, fx, fy, fz);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        fx += __shfl_xor_sync(0xffffffffu, fx, o);
-        fy += __shfl_xor_sync(0xffffffffu, fy, o);
-        fz += __shfl_xor_sync(0xffffffffu, fz, o);
-    }
-    f[0] = fx;
-    f[1] = fy;
-    f[2] = fz;
+    });
+    f[0] = group_sum(fx, width);
+    f[1] = group_sum(fy, width);
+    f[2] = group_sum(fz, width);
 }
 
 template <class M>
@@ -1433,7 +1492,7 @@ __device__ __forceinline__ bool tagged_whole(const void* fcore, int p)
 }
 
 template <class M>
-__global__ void __launch_bounds__(SC_TPB) k_force_rows(int n, Geom g, Coef c,
+__global__ void __launch_bounds__(SC_TPB) k_force_rows(int n, int ngroups, Geom g, Coef c,
                                                        const typename M::pos_t* __restrict__ pos, SuperGrid G,
                                                        SuperCaps cp, GroupAux aux, const uint16_t* __restrict__ nbr,
                                                        const int* __restrict__ nnb,
@@ -1442,17 +1501,19 @@ __global__ void __launch_bounds__(SC_TPB) k_force_rows(int n, Geom g, Coef c,
     using pos_t = typename M::pos_t;
     using real = typename M::real;
     if (halted(st)) return;
-    const int ng = st->ngen;
-    const bool useA = st->nwin > 0;  // A_j != 0 only for window particles
-    const int warp = threadIdx.x >> 5;
-    if (ng <= n / DENSE_DIV) {
-        for (int k = blockIdx.x * ROW_WARPS + warp; k < ng; k += gridDim.x * ROW_WARPS) {
+    const int ng = st->ngen, nw = st->nwin;
+    const bool useA = nw > 0;                  // A_j != 0 only for window particles
+    const bool all = nw > n / DENSE_DIV;       // k_chain ran dense and cleared no tag
+    if (!all && ng <= n / DENSE_DIV) {
+        for (int k = blockIdx.x * ROW_WARPS + (threadIdx.x >> 5); k < ng; k += gridDim.x * ROW_WARPS) {
             const int p = aux.glist[k];
             const int ra = __ldg(aux.roff + p), b = ra / cp.seg;
             const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
+            const uint16_t* row = nbr + ra;
+            const int len = row_len(__ldg(nnb + p));
             const pos_t pi = pos[p];
             real f[3];
-            force_row<M>(pi, get_s(pi), useA ? sA[p].y : (real)0, nbr + ra, row_len(__ldg(nnb + p)),
+            force_row<M>(pi, get_s(pi), useA ? sA[p].y : (real)0, [&](auto&& v) { walk_lanes(row, len, v); }, 32,
                          [&](int m, real& Aj) {
                              const int jj = __ldg(sidx + m);
                              Aj = useA ? sA[jj].y : (real)0;
@@ -1463,39 +1524,46 @@ __global__ void __launch_bounds__(SC_TPB) k_force_rows(int n, Geom g, Coef c,
         }
         return;
     }
-    // dense: the group's own particles without a whole-force tag
-    const int b = blockIdx.x, t = threadIdx.x;
-    const int p0 = __ldg(G.cell_start + OWN_CELLS * b);
-    const int n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
+    // dense: the own particles without a whole-force tag (all of them after a dense k_chain), group by group
     __shared__ int s_n;
     extern __shared__ __align__(16) unsigned char smem[];
     const DenseLayout ly = dense_layout(cp, sizeof(pos_t), sizeof(real));
     pos_t* spos = (pos_t*)smem;
     real* sAj = (real*)(smem + ly.extra);
     int* plist = (int*)(smem + ly.plist);
-    if (t == 0) s_n = 0;
-    __syncthreads();
-    for (int j = t; j < n_own; j += SC_TPB)
-        if (!tagged_whole<M>(aux.fcore, p0 + j)) plist[atomicAdd(&s_n, 1)] = j;
-    __syncthreads();
-    const int nl = s_n;
-    if (nl == 0) return;
-    stage_by_table(aux.stage_idx + (size_t)b * cp.smax, __ldg(aux.meta + b).x, [&](int m, int jj) {
-        spos[m] = pos[jj];
-        sAj[m] = useA ? sA[jj].y : (real)0;
-    });
-    __syncthreads();
-    for (int u = warp; u < nl; u += ROW_WARPS) {
-        const int p = p0 + plist[u];
-        const pos_t pi = pos[p];
-        real f[3];
-        force_row<M>(pi, get_s(pi), useA ? sA[p].y : (real)0, nbr + __ldg(aux.roff + p), row_len(__ldg(nnb + p)),
-                     [&](int m, real& Aj) {
-                         Aj = sAj[m];
-                         return spos[m];
-                     },
-                     c, g, f);
-        if ((t & 31) == 0) force_out<M>(aux.fcore, p, f);
+    for (int b = blockIdx.x; b < ngroups; b += gridDim.x) {
+        __syncthreads();  // the previous group is done with the shared arrays
+        const int p0 = __ldg(G.cell_start + OWN_CELLS * b);
+        const int n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
+        int nl;
+        if (all) {
+            for (int j = threadIdx.x; j < n_own; j += SC_TPB) plist[j] = j;
+            nl = n_own;
+        } else {
+            nl = list_own(n_own, plist, &s_n, [&](int j) { return !tagged_whole<M>(aux.fcore, p0 + j); });
+        }
+        if (nl == 0) continue;
+        stage_by_table(aux.stage_idx + (size_t)b * cp.smax, __ldg(aux.meta + b).x, [&](int m, int jj) {
+            spos[m] = pos[jj];
+            sAj[m] = useA ? sA[jj].y : (real)0;
+        });
+        __syncthreads();
+        dense_rounds(nl, [&](int u, int sub, int tpp) {
+            const bool act = u < nl;
+            const int p = p0 + (act ? plist[u] : 0);
+            const uint16_t* row = nbr + __ldg(aux.roff + p);
+            const int len = act ? row_len(__ldg(nnb + p)) : 0;
+            const pos_t pi = pos[p];
+            real f[3];
+            force_row<M>(pi, get_s(pi), useA ? sA[p].y : (real)0,
+                         [&](auto&& v) { walk_chunks(row, len, sub, tpp, v); }, tpp,
+                         [&](int m, real& Aj) {
+                             Aj = sAj[m];
+                             return spos[m];
+                         },
+                         c, g, f);
+            if (act && sub == 0) force_out<M>(aux.fcore, p, f);
+        });
     }
 }
 

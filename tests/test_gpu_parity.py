@@ -250,6 +250,58 @@ def test_bad_step_arguments_rejected():
             assert e.value.code == vbc.VBC_ERR_INVALID_ARG
 
 
+# ----------------------------------------------------------------- row-walk modes
+def _window_valency(n0: np.ndarray, lo: float, hi: float) -> float:
+    """A valency f (delta = 0) whose window (f, f + 1) holds a fraction of the
+    particles between lo and hi, taken from the oracle's counts."""
+    for q in (0.01, 0.005, 0.02, 0.002, 0.04):
+        f = float(np.quantile(n0, q))
+        frac = np.mean((n0 > f) & (n0 < f + 1.0))
+        if lo <= frac <= hi:
+            return f
+    raise AssertionError("no valency gives the wanted window fraction")
+
+
+@pytest.mark.parametrize("prec", [F32, F64])
+@pytest.mark.parametrize("case", ["saturated", "few_in_window", "many_in_window"])
+def test_forces_only_row_walk_modes(prec, case):
+    """A force evaluation without counts takes the saturation split: the close
+    lists settle saturated particles, and the row walks pick their sparse or dense
+    mode from their list lengths (threshold n/16).  Three valencies on a 30k
+    uniform fluid cover sparse counts and forces with nearly every particle
+    saturated, a sparse chain pass that clears whole-force tags, and the dense
+    passes."""
+    n = 30_000
+    pos, L = inputs.uniform_positions(n, 0.5, seed=11)
+    base = Params(E_a=8.0)
+    n0 = oracle.evaluate(pos, L, base, 1).counts
+    if case == "saturated":
+        f = 2.0
+    elif case == "few_in_window":
+        f = _window_valency(n0, 0.005, 0.05)
+    else:
+        f = inputs.quantile_valency(n0, 0.5)
+    p = Params(**{**base.__dict__, "f": f})
+    ref = oracle.evaluate(pos, L, p, 1)
+    tol = TOL[prec]
+    with vbc.System(pos, L, to_vbc(p), precision=prec) as s:
+        r = s.compute(F=True)
+        sw, dsw, A = s.switch()
+        st = s.stats()
+    rms = np.sqrt(np.mean(np.sum(ref.F ** 2, axis=1)))
+    assert np.max(np.abs(r.F - ref.F)) <= tol["F"] * rms
+    assert np.max(np.abs(sw - ref.s)) <= tol["s"]
+    assert np.max(np.abs(dsw - ref.ds)) <= 4 * tol["s"]
+    assert np.max(np.abs(A - ref.A)) <= tol["A"] * max(np.max(np.abs(ref.A)), 1e-12)
+    assert st.in_window == int(np.sum(dsw != 0.0))
+    if case == "saturated":
+        assert st.in_window <= n // 16 and st.unsaturated <= n // 16
+    elif case == "few_in_window":
+        assert 0 < st.in_window <= n // 16
+    else:
+        assert st.in_window > n // 16 and st.unsaturated > n // 16
+
+
 # ----------------------------------------------------------------- full sizes
 @pytest.mark.parametrize("n", [100_000, 1_000_000])
 def test_full_size_uniform_rho05(n):
