@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-served", action="store_true", help="skip the served leg (p50/p99 latency)")
+    ap.add_argument("--served-requests", type=int, default=24)
+    ap.add_argument("--served-steps", type=int, default=50_000, help="Langevin steps per served request")
+    ap.add_argument("--served-slots", type=int, default=16)
     ap.add_argument("--profile-run", action="store_true",
                     help="short run for profilers: the equilibrated workload (cached under /tmp), one forced "
                          "list build, one force evaluation and 6 steps; prints no JSON line")
@@ -238,6 +242,45 @@ def profile_run(args):
     return 0
 
 
+def served_requests(args):
+    """A Poisson arrival stream of simulation requests: arrival rate 20 per
+    second, N log-uniform in [1k, 200k], valency uniform in {1, ..., 8}, the
+    bench's pair form at density 0.5, args.served_steps steps each (seeded)."""
+    rng = np.random.default_rng(20260)
+    t = np.cumsum(rng.exponential(1.0 / 20.0, args.served_requests))
+    n = np.exp(rng.uniform(np.log(1000), np.log(200_000), args.served_requests)).astype(int)
+    v = rng.integers(1, 9, args.served_requests)
+    return [(float(t[k] - t[0]), int(n[k]), float(v[k]), 100 + k) for k in range(args.served_requests)]
+
+
+def run_served(args, slots):
+    """Submits the request stream at its arrival times to a server with the given
+    slots (150 GB budget, 1000-step chunks, state resident on the device) and
+    returns latency percentiles and aggregate throughput."""
+    from paper_2609_07842_b300 import inputs, vbc
+    reqs = served_requests(args)
+    made = [(t, inputs.uniform_positions(n, args.rho, seed=seed), v, seed) for t, n, v, seed in reqs]
+    with vbc.Server(hbm_budget=150e9, slots=slots, chunk_steps=1000) as srv:
+        t0 = time.perf_counter()
+        ids = []
+        for t, (pos, L), v, seed in made:
+            dt_wait = t - (time.perf_counter() - t0)
+            if dt_wait > 0:
+                time.sleep(dt_wait)
+            ids.append(srv.submit(pos, L, vbc.params(E_a=args.E_a, f=v), nsteps=args.served_steps, dt=DT,
+                                  kT=KT, gamma=GAMMA, seed=seed))
+        srv.wait()
+        infos = [srv.result(i)[2] for i in ids]
+    lat = np.array([x.t_done - x.t_submit for x in infos])
+    span = max(x.t_done for x in infos) - min(x.t_submit for x in infos)
+    steps = sum(args.served_steps for _ in infos)
+    psteps = sum(args.served_steps * x.n for x in infos)
+    return {"slots": slots, "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)), "timesteps_per_s": steps / span,
+            "particle_steps_per_s": psteps / span, "makespan_s": span,
+            "ok": all(x.status == 0 for x in infos)}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -289,7 +332,8 @@ def main():
 
     # ---- timed region 2: the same K steps with direct launches and a CUDA event
     # pair around every kernel on the library's stream, for per-kernel times
-    sys_.profile(True, max_launches=4 * (args.steps + 2) + 16)
+    # (room for the records of iterations an overflow halts and the retry re-runs)
+    sys_.profile(True, max_launches=12 * (args.steps + 2) + 64)
     barrier()
     ev0.record(stream)
     sys_.step(args.steps, DT, KT, GAMMA)
@@ -377,6 +421,18 @@ def main():
                "d2h_bytes_per_step": int(48 * args.n * nchunks / args.steps),
                "chunk_steps": chunk}
 
+    # ---- served: a Poisson stream of uneven requests through the serving loop,
+    # and the same stream one system at a time (rank 0, N = 1 only)
+    served = None
+    if rank == 0 and world == 1 and not args.no_served:
+        mix = run_served(args, args.served_slots)
+        one = run_served(args, 1)
+        served = {"workload": (f"{args.served_requests} requests, Poisson arrivals at 20/s, N log-uniform in "
+                               f"[1k, 200k], valency uniform in 1..8, rho {args.rho}, E_a {args.E_a}, "
+                               f"{args.served_steps} steps each in 1000-step chunks, 150 GB admission budget"),
+                  **mix, "one_at_a_time": one,
+                  "speedup_vs_one_at_a_time": mix["timesteps_per_s"] / one["timesteps_per_s"]}
+
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -423,6 +479,7 @@ def main():
             "gpu_launches": launches,
             "clocks": clk,
             "e2e": e2e,
+            "served": served,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

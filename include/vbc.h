@@ -47,7 +47,8 @@ enum {
     VBC_ERR_CUDA = -2,          /* a CUDA runtime call failed (message has the detail) */
     VBC_ERR_OOM = -3,           /* device allocation failed */
     VBC_ERR_NLIST_OVERFLOW = -4,/* neighbour list still overflows after growing to its limit */
-    VBC_ERR_UNSTABLE = -5       /* non-finite position or velocity produced */
+    VBC_ERR_UNSTABLE = -5,      /* non-finite position or velocity produced */
+    VBC_ERR_TIMEOUT = -6        /* a wait ended before the awaited work (serving) */
 };
 
 /* Precision of the pair arithmetic. */
@@ -105,6 +106,7 @@ typedef struct {
     int32_t groups;            /* cell groups (units of the list build and of the dense row walks) */
     int64_t capacity_grows;    /* capacity growths after an overflow since creation (each resumes the
                                   interrupted call from the overflowing build) */
+    int64_t device_bytes;      /* device memory the system holds at its current capacities */
 } vbc_stats;
 
 /*
@@ -114,6 +116,12 @@ typedef struct {
  * non-cubic box with VBC_FP32_SPLIT, bad parameters, NULL pos/out), OOM, CUDA.
  */
 int vbc_create_system(const vbc_config* cfg, vbc_system** out);
+
+/* Device memory, in bytes, that vbc_create_system would allocate for cfg (the
+ * initial capacities; the first list build trims them, an overflow grows
+ * them).  No device is touched.  Errors: INVALID_ARG (NULL pointers, n, box or
+ * skin out of range, box too small for the cell list). */
+int vbc_estimate_device_bytes(const vbc_config* cfg, int64_t* bytes);
 
 /* Force a neighbour-list rebuild now (Morton sort of the particles, cell list,
  * Verlet list of radius r_c + skin).  Rebuilds also happen automatically when a
@@ -227,6 +235,83 @@ void vbc_destroy(vbc_system* sys);
 
 /* Message describing the last error of the calling thread ("" if none). */
 const char* vbc_last_error(void);
+
+/* ------------------------------------------------------------------ serving
+ * Many independent simulations (valency and temperature sweeps, Sec. 5: one
+ * system per parameter set) on one GPU.  A server admits submitted requests
+ * in arrival order whenever a slot is free and the device memory of the
+ * admitted systems, estimated by vbc_estimate_device_bytes and then taken
+ * from each live system, stays within the budget.  Each slot is a host thread
+ * with its own CUDA stream: it creates the request's system there, advances
+ * it in chunks of chunk_steps Langevin steps with the state resident on the
+ * device, copies the final state to host memory the server owns and
+ * releases the system.  Requests that arrive while others run are admitted
+ * as slots and memory free up, and the slots' kernels overlap on the device.
+ * A system's result does not depend on what else runs: every kernel of the
+ * library is deterministic and a system shares no device memory with
+ * another, so a request alone and in a mix gives bitwise the same state. */
+typedef struct vbc_server vbc_server;
+
+typedef struct {
+    int64_t hbm_budget;   /* device bytes the admitted systems may hold together (> 0) */
+    int32_t slots;        /* systems advanced at the same time, 1 <= slots <= 256 */
+    int64_t chunk_steps;  /* Langevin steps per chunk (> 0) */
+} vbc_server_config;
+
+typedef struct {
+    vbc_config system;    /* as for vbc_create_system, host input only: stream and
+                             inputs_on_device are ignored; pos and vel are copied at submit */
+    int64_t nsteps;       /* Langevin steps to run (>= 0) */
+    double dt, kT, gamma; /* as for vbc_step_langevin */
+} vbc_request;
+
+enum { VBC_REQ_QUEUED = 1, VBC_REQ_RUNNING = 2 };
+
+typedef struct {
+    int32_t status;       /* VBC_REQ_QUEUED, VBC_REQ_RUNNING, then VBC_OK or the error code */
+    int64_t n;            /* particles */
+    int64_t steps_done;   /* Langevin steps completed so far */
+    double t_submit;      /* seconds on the server's clock (steady, from its creation) */
+    double t_admit;       /* when a slot took it (0 while queued) */
+    double t_done;        /* when its state was on the host (0 until then) */
+    int64_t device_bytes; /* device memory reserved for it (estimate, then the live figure) */
+} vbc_request_info;
+
+/* Start a server: its slot threads wait for work.  Errors: INVALID_ARG, CUDA
+ * (no device). */
+int vbc_server_create(const vbc_server_config* cfg, vbc_server** out);
+
+/* Queue a request; *id names it from here on.  The inputs are validated and
+ * copied before the call returns; the work runs later on a slot.  Errors:
+ * INVALID_ARG (as vbc_create_system, or a step argument out of range), OOM
+ * (the estimate alone exceeds the budget). */
+int vbc_server_submit(vbc_server* srv, const vbc_request* req, int64_t* id);
+
+/* Wait up to timeout_s seconds (< 0: without limit) for request id to finish;
+ * id = -1 waits for every request submitted so far.  Fills *info (may be
+ * NULL; not for id = -1).  Returns VBC_OK when finished (the request's own
+ * outcome is info->status), VBC_ERR_TIMEOUT if not finished in time,
+ * INVALID_ARG for an unknown id. */
+int vbc_server_wait(vbc_server* srv, int64_t id, double timeout_s, vbc_request_info* info);
+
+/* Status of request id without waiting.  Errors: INVALID_ARG (unknown id). */
+int vbc_server_info(vbc_server* srv, int64_t id, vbc_request_info* info);
+
+/* Copy a finished request's final state ([n][3] positions, unwrapped, and
+ * velocities, in the submitted particle order; either may be NULL) to host
+ * memory and forget the request.  Errors: INVALID_ARG (unknown id, or not
+ * finished yet), or the request's own error code (its state is then not
+ * copied, and the request is forgotten all the same). */
+int vbc_server_result(vbc_server* srv, int64_t id, double* pos, double* vel, vbc_request_info* info);
+
+/* Stop the server: queued requests are dropped, running ones finish their
+ * current chunk and stop, the slot threads end, and everything is released.
+ * NULL-safe. */
+void vbc_server_destroy(vbc_server* srv);
+
+/* Message of the last failed vbc_server_* call on this thread (a request's own
+ * failure reads back through vbc_server_result). */
+const char* vbc_server_last_error(void);
 
 #ifdef __cplusplus
 }

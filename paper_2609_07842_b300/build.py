@@ -14,8 +14,8 @@ import sys
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
-SRCS = [os.path.join(PKG, "csrc", f) for f in ("vbc_api.cu", "vbc_noalloc.cu")]
-DEPS = [os.path.join(PKG, "csrc", f) for f in ("vbc_api.cu", "vbc_noalloc.cu", "vbc_kernels.cuh",
+SRCS = [os.path.join(PKG, "csrc", f) for f in ("vbc_api.cu", "vbc_noalloc.cu", "vbc_serve.cpp")]
+DEPS = [os.path.join(PKG, "csrc", f) for f in ("vbc_api.cu", "vbc_noalloc.cu", "vbc_serve.cpp", "vbc_kernels.cuh",
                                                "vbc_device.cuh")] + [
     os.path.join(ROOT, "include", "vbc.h")]
 LIB = os.path.join(PKG, "libvbc.so")

@@ -18,6 +18,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -59,8 +61,23 @@ constexpr int MAX_OWN = 4096;          // particles of one cell group
 constexpr size_t MAX_SMEM = 227 * 1024;
 constexpr int MAX_RETRIES = 12;
 constexpr int REBUILD_KERNELS = 8;     // kernels of one neighbour-list rebuild
+constexpr int WTAB_PIECES = 1024;      // pieces of the window-weight table (at most)
 
 int blocks_for(int64_t n, int tpb) { return (int)((n + tpb - 1) / tpb); }
+
+uint32_t float_bits(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, sizeof u);
+    return u;
+}
+
+// Cell grid and capacities of a system.
+struct Sizes {
+    int nc[3] = {0, 0, 0}, pc[3] = {0, 0, 0};  // real and padded cells per edge
+    int ncell = 0, npad = 0, nsc = 0;
+    int cap = 0, smax = 0, omax = 0, seg = 0;
+};
 
 }  // namespace
 
@@ -110,6 +127,7 @@ struct vbc_system {
     int sms = 148;              // SMs of the device
     int row_grid = 1;           // blocks of the row walks (count rows, chain-rule pass, force rows)
     long long grows = 0;        // capacity growths after an overflow
+    uint4* wtab = nullptr;      // [WTAB_PIECES + 1] window-weight pieces of the counts (window_weight_tab)
     void *ds = nullptr, *sA = nullptr;
     Status* st = nullptr;
     Status* st_host = nullptr;  // pinned
@@ -286,6 +304,50 @@ ListParams make_list_params(const Coef& c, double rlist, double skin, const Geom
     return lp;
 }
 
+// Window-weight pieces of the FP32-split counts (window_weight_tab): omega of
+// Eq. (omega) as a function of D = r^2 - r_l^2 in fixed-point units, on
+// pieces of 2^sh units, each a cubic Hermite interpolant of omega and its
+// derivative at the piece's ends (FP64 here, once per parameter set).
+void make_window_table(const Coef& c, const Geom& g, std::vector<uint4>& tab, int& sh)
+{
+    const unsigned long long range = c.rh2_fix > c.rl2_fix ? c.rh2_fix - c.rl2_fix : 1ull;
+    int bits = 0;
+    while (bits < 64 && (range >> bits) != 0) ++bits;
+    sh = std::max(0, bits - 10);  // (range >> sh) < 2^10 = WTAB_PIECES
+    const int pieces = (int)(range >> sh) + 1;
+    const double s2 = g.s32d[0] * g.s32d[0];
+    const auto omega = [&](double D, double& dw_dD) {
+        const double r2 = (double)c.rl2_fix * s2 + D * s2, r = std::sqrt(r2);
+        double t = (r - c.r_l) / c.w;
+        if (t <= 0.0 || t >= 1.0) {
+            dw_dD = 0.0;
+            return t <= 0.0 ? 1.0 : 0.0;
+        }
+        const double q = 1.0 - t * t;
+        dw_dD = -4.0 * t * q / c.w * s2 / (2.0 * r);  // d omega/dt * dt/dr * dr/d(r^2) * d(r^2)/dD
+        return q * q;
+    };
+    tab.assign((size_t)pieces, make_uint4(0u, 0u, 0u, 0u));
+    const double hD = std::ldexp(1.0, sh);
+    for (int k = 0; k < pieces; ++k) {
+        // the last piece ends at the window's edge, where omega's curvature jumps: it
+        // interpolates on [k hD, range] only (rho < 1 of the piece), rescaled to u
+        const double D0 = k * hD, D1 = std::min((k + 1) * hD, (double)range);
+        const double rho = (D1 - D0) / hD;
+        double m0, m1;
+        const double p0 = omega(D0, m0), p1 = omega(D1, m1);
+        m0 *= D1 - D0;
+        m1 *= D1 - D0;
+        const double c2 = 3.0 * (p1 - p0) - 2.0 * m0 - m1, c3 = 2.0 * (p0 - p1) + m0 + m1;
+        uint4 e;
+        e.x = (unsigned)std::llround(p0 * 2147483648.0);
+        e.y = float_bits((float)(m0 / rho));
+        e.z = float_bits((float)(c2 / (rho * rho)));
+        e.w = float_bits((float)(c3 / (rho * rho * rho)));
+        tab[(size_t)k] = e;
+    }
+}
+
 // Integer part and 2^-64 fraction of a non-negative factor (the fraction to
 // double precision, which bounds the error of a fixed-point product by a
 // relative 2^-53 of it).
@@ -336,6 +398,21 @@ void dfree(T*& p)
     p = nullptr;
 }
 
+// Builds the window-weight table of the system's parameters and points its
+// coefficients at it (host copy; the stream holds no work that reads it).
+int upload_window_table(vbc_system* s)
+{
+    std::vector<uint4> tab;
+    int sh = 0;
+    make_window_table(s->coef, s->geom, tab, sh);
+    if (!s->wtab) VBC_TRY(dalloc(s->wtab, (size_t)WTAB_PIECES + 2));
+    VBC_CUDA(cudaMemcpy(s->wtab, tab.data(), tab.size() * sizeof(uint4), cudaMemcpyHostToDevice));
+    s->coef.wtab = s->wtab;
+    s->coef.wsh = sh;
+    return VBC_OK;
+}
+
+
 void free_all(vbc_system* s)
 {
     dfree(s->x); dfree(s->v); dfree(s->xt); dfree(s->vt); dfree(s->id); dfree(s->idt);
@@ -345,7 +422,7 @@ void free_all(vbc_system* s)
     dfree(s->chunk_sum); dfree(s->wpart); dfree(s->ulist); dfree(s->stage_idx); dfree(s->gmeta); dfree(s->roff_g);
     dfree(s->close_k); dfree(s->fcore); dfree(s->glist);
     dfree(s->ds); dfree(s->sA); dfree(s->st); dfree(s->partial); dfree(s->ppairs); dfree(s->red);
-    dfree(s->win); dfree(s->e_sd); dfree(s->e_A);
+    dfree(s->win); dfree(s->e_sd); dfree(s->e_A); dfree(s->wtab);
     if (s->st_host) cudaFreeHost(s->st_host);
     if (s->red_host) cudaFreeHost(s->red_host);
     s->st_host = nullptr;
@@ -363,7 +440,18 @@ void free_all(vbc_system* s)
 template <class F>
 int set_smem(F* func, size_t bytes)
 {
+    // The limit belongs to the kernel, not to a system: it only ever rises,
+    // so that configuring one system never lowers it below what another
+    // (possibly on another host thread) launches with.
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, int> limit;
+    int dev = 0;
+    VBC_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    int& cur = limit[{dev, (const void*)func}];
+    if ((int)bytes <= cur) return VBC_OK;
     VBC_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cur = (int)bytes;
     return VBC_OK;
 }
 
@@ -418,7 +506,7 @@ int enqueue_rebuild(vbc_system* s)
     k_scan_sums<<<nchunk, SCAN_TPB, 0, s->stream>>>(s->cell_count, s->npad, s->chunk_sum, s->st);
     k_scan_apply<<<nchunk, SCAN_TPB, 0, s->stream>>>(s->cell_count, s->npad, s->chunk_sum, s->cell_start, s->st);
     k_scatter<<<nb, TPB, 0, s->stream>>>(n, s->cell_of, s->slot_of, s->cell_start, s->order, s->st);
-    k_cellsort<<<blocks_for(s->npad, TPB), TPB, 0, s->stream>>>(s->npad, s->cell_start, s->order, s->st);
+    k_cellsort<M><<<blocks_for(s->npad, TPB), TPB, 0, s->stream>>>(s->npad, s->cell_start, s->order, pos, s->st);
     k_permute<M><<<nb, TPB, 0, s->stream>>>(n, s->order, s->x, s->v, s->id, pos, s->xt, s->vt, s->idt,
                                             (pos_t*)s->post, s->st);
     k_copyback<M><<<nb, TPB, 0, s->stream>>>(n, s->xt, s->vt, s->idt, (const pos_t*)s->post, s->x, s->v, s->id,
@@ -513,6 +601,82 @@ int read_status(vbc_system* s)
     VBC_CUDA(cudaMemcpyAsync(s->st_host, s->st, sizeof(Status), cudaMemcpyDeviceToHost, s->stream));
     VBC_CUDA(cudaStreamSynchronize(s->stream));
     return VBC_OK;
+}
+
+// Cell grid and initial capacities of a system (create_system; the device
+// memory estimate of the serving admission).  Cells are at least r_c + skin
+// wide, at least 3 per edge; the grid is padded to whole cell groups.
+int plan_sizes(const vbc_config* cfg, Sizes& z)
+{
+    const vbc_pair_params& p = cfg->params;
+    const double rlist = std::max(p.r_r, std::max(p.r_a, p.r_h)) + cfg->skin;
+    for (int a = 0; a < 3; ++a) {
+        const double ncd = std::floor(cfg->box[a] / rlist);
+        if (!(ncd >= 3.0))
+            return fail(VBC_ERR_INVALID_ARG, "box edge %g holds fewer than 3 cells of r_c + skin = %g", cfg->box[a],
+                        rlist);
+        z.nc[a] = (int)std::min(ncd, 1024.0);
+    }
+    if ((double)(z.nc[0] + 1) * (z.nc[1] + 1) * (z.nc[2] + 1) > 2.0e9)
+        return fail(VBC_ERR_INVALID_ARG, "cell grid too large");
+    z.ncell = z.nc[0] * z.nc[1] * z.nc[2];
+    z.pc[0] = (z.nc[0] + BXC - 1) / BXC * BXC;
+    z.pc[1] = (z.nc[1] + BYC - 1) / BYC * BYC;
+    z.pc[2] = (z.nc[2] + BZC - 1) / BZC * BZC;
+    z.npad = z.pc[0] * z.pc[1] * z.pc[2];
+    z.nsc = z.npad / OWN_CELLS;
+    // initial capacities from the mean density: a group owns OWN_CELLS cells and
+    // stages SCELLS; lists hold about kbar entries per particle (trimmed to the
+    // first build's needs once it ran)
+    const double rho = (double)cfg->n / (cfg->box[0] * cfg->box[1] * cfg->box[2]);
+    const double kbar = rho * 4.18879020478639098 * rlist * rlist * rlist;  // 4 pi / 3
+    const int cap = cfg->nlist_cap > 0 ? cfg->nlist_cap : (int)std::ceil(1.3 * kbar + 6.0 * std::sqrt(kbar) + 12.0);
+    z.cap = std::min((std::max(cap, 1) + 7) & ~7, MAX_CAP);
+    const double rho_cell = (double)cfg->n / z.ncell;
+    z.smax = std::min((((int)std::ceil(1.5 * SCELLS * rho_cell) + 64) + 63) / 64 * 64, MAX_STAGE);
+    z.omax = std::min(((int)std::ceil(2.0 * OWN_CELLS * rho_cell) + 32 + 31) / 32 * 32, MAX_OWN);
+    const double entries = OWN_CELLS * rho_cell * (std::min(kbar, (double)z.cap) + 4.0);
+    z.seg = (int)std::min(((long long)std::ceil(1.5 * entries) + 256 + 63) / 64 * 64, 1LL << 24);
+    return VBC_OK;
+}
+
+// Device bytes of a system of n particles at the given sizes: the arrays
+// that create_system and grow allocate.
+long long device_bytes_of(long long n, int prec, const Sizes& z)
+{
+    const long long pb = prec == VBC_FP64 ? (long long)sizeof(P64) : 16, rb = prec == VBC_FP64 ? 8 : 4;
+    struct {
+        int seg, nsc, cap, npad, ncell, smax;
+    } sz{z.seg, z.nsc, z.cap, z.npad, z.ncell, z.smax};
+    const auto* s = &sz;
+    long long b = 0;
+    b += 4 * 3 * n * 8;                                   // x, v, xt, vt
+    b += 2 * n * 4;                                       // id, idt
+    b += 4 * n * pb;                                      // pos[2], post, xref
+    b += (long long)s->seg * s->nsc * 2;                  // nbr
+    b += (long long)s->cap * n * 2;                       // scratch
+    b += 8 * n * 4;                                       // nnb, cell_of, slot_of, order, wpart, ulist, roff_g, glist
+    b += ((long long)s->npad * 2 + 1 + s->ncell + s->nsc) * 4;  // cell tables
+    b += (long long)blocks_for(s->npad, SCAN_CHUNK) * 4;
+    b += (long long)s->nsc * s->smax * 4;                 // stage_idx
+    b += (long long)s->nsc * (8 + 16 + 8);                // gmeta, partial, ppairs
+    b += (long long)CLOSE_K * n * 4;                      // close_k
+    b += n * (prec == VBC_FP64 ? 32 : 16);                // fcore
+    b += 3 * n * rb;                                      // ds, sA
+    b += n * (8 + 16);                                    // e_sd, e_A
+    return b + 4096;                                      // status words and reductions
+}
+
+long long device_bytes(const vbc_system* s)
+{
+    Sizes z{};
+    z.seg = s->seg;
+    z.nsc = s->nsc;
+    z.cap = s->cap;
+    z.npad = s->npad;
+    z.ncell = s->geom.ncell;
+    z.smax = s->smax;
+    return device_bytes_of(s->n, s->prec, z);
 }
 
 bool needs_growth(const vbc_system* s) { return s->st_host->overflow || s->st_host->stage_overflow; }
@@ -857,6 +1021,21 @@ extern "C" {
 
 const char* vbc_last_error(void) { return g_err.c_str(); }
 
+int vbc_estimate_device_bytes(const vbc_config* cfg, int64_t* bytes)
+{
+    g_err.clear();
+    if (!cfg || !bytes) return fail(VBC_ERR_INVALID_ARG, "cfg and bytes must not be NULL");
+    if (cfg->n < 1 || cfg->n > 0x7fffffffLL) return fail(VBC_ERR_INVALID_ARG, "n must be in [1, 2^31 - 1]");
+    if (!(cfg->skin > 0) || !std::isfinite(cfg->skin)) return fail(VBC_ERR_INVALID_ARG, "skin must be > 0");
+    for (int a = 0; a < 3; ++a)
+        if (!(cfg->box[a] > 0) || !std::isfinite(cfg->box[a]))
+            return fail(VBC_ERR_INVALID_ARG, "box edges must be positive and finite");
+    Sizes z;
+    VBC_TRY(plan_sizes(cfg, z));
+    *bytes = device_bytes_of(cfg->n, cfg->precision, z);
+    return VBC_OK;
+}
+
 int vbc_create_system(const vbc_config* cfg, vbc_system** out)
 {
     g_err.clear();
@@ -894,25 +1073,22 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     Geom& g = s->geom;
     s->rcut = std::max(s->prm.r_r, std::max(s->prm.r_a, s->prm.r_h));
     s->rlist = s->rcut + s->skin;
+    Sizes z;
+    {
+        int rc = plan_sizes(cfg, z);
+        if (rc) return bail(rc);
+    }
     for (int a = 0; a < 3; ++a) {
         g.L[a] = s->box[a];
         g.inv32[a] = 4294967296.0 / s->box[a];
         g.s32d[a] = s->box[a] / 4294967296.0;
         g.s64[a] = s->box[a] / 18446744073709551616.0;
-        const double ncd = std::floor(s->box[a] / s->rlist);
-        if (!(ncd >= 3.0))
-            return bail(fail(VBC_ERR_INVALID_ARG,
-                             "box edge %g holds fewer than 3 cells of r_c + skin = %g", s->box[a], s->rlist));
-        g.nc[a] = (int)std::min(ncd, 1024.0);
+        g.nc[a] = z.nc[a];
     }
-    if ((double)(g.nc[0] + 1) * (g.nc[1] + 1) * (g.nc[2] + 1) > 2.0e9)
-        return bail(fail(VBC_ERR_INVALID_ARG, "cell grid too large"));
-    g.ncell = g.nc[0] * g.nc[1] * g.nc[2];
-    // padded to multiples of the cell-group extents
-    const int pc[3] = {(g.nc[0] + BXC - 1) / BXC * BXC, (g.nc[1] + BYC - 1) / BYC * BYC,
-                       (g.nc[2] + BZC - 1) / BZC * BZC};
-    s->npad = pc[0] * pc[1] * pc[2];
-    s->nsc = s->npad / OWN_CELLS;
+    g.ncell = z.ncell;
+    const int* pc = z.pc;
+    s->npad = z.npad;
+    s->nsc = z.nsc;
     s->rel_lists = s->prec == VBC_FP32_SPLIT && g.nc[0] >= 8 && g.nc[1] >= 8 && g.nc[2] >= 8;
     g.s32 = (float)g.s32d[0];
     g.s32sq = (float)(g.s32d[0] * g.s32d[0]);
@@ -922,20 +1098,10 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     }
     s->lp = make_list_params(s->coef, s->rlist, s->skin, g);
 
-    // initial capacities from the mean density
-    const double rho = (double)s->n / (s->box[0] * s->box[1] * s->box[2]);
-    const double kbar = rho * 4.18879020478639098 * s->rlist * s->rlist * s->rlist;  // 4 pi / 3
-    int cap = cfg->nlist_cap > 0 ? cfg->nlist_cap : (int)std::ceil(1.3 * kbar + 6.0 * std::sqrt(kbar) + 12.0);
-    s->cap = std::min((std::max(cap, 1) + 7) & ~7, MAX_CAP);
-    {
-        // a group owns OWN_CELLS cells and stages SCELLS; lists hold about kbar entries per
-        // particle (trimmed to the first build's needs once it ran)
-        const double rho_cell = (double)s->n / g.ncell;
-        s->smax = std::min((((int)std::ceil(1.5 * SCELLS * rho_cell) + 64) + 63) / 64 * 64, MAX_STAGE);
-        s->omax = std::min(((int)std::ceil(2.0 * OWN_CELLS * rho_cell) + 32 + 31) / 32 * 32, MAX_OWN);
-        const double entries = OWN_CELLS * rho_cell * (std::min(kbar, (double)s->cap) + 4.0);
-        s->seg = (int)std::min(((long long)std::ceil(1.5 * entries) + 256 + 63) / 64 * 64, 1LL << 24);
-    }
+    s->cap = z.cap;
+    s->smax = z.smax;
+    s->omax = z.omax;
+    s->seg = z.seg;
 
     {
         cudaError_t e = cudaGetDevice(&s->device);
@@ -997,6 +1163,7 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     ALLOC(dalloc(s->win, 1));
     ALLOC(dalloc(s->e_sd, n));
     ALLOC(dalloc(s->e_A, n));
+    ALLOC(upload_window_table(s));
 #undef ALLOC
     if (cudaMallocHost((void**)&s->st_host, sizeof(Status)) != cudaSuccess ||
         cudaMallocHost((void**)&s->red_host, 2 * sizeof(double)) != cudaSuccess)
@@ -1211,6 +1378,7 @@ int vbc_set_params(vbc_system* s, const vbc_pair_params* p)
     VBC_CUDA(cudaStreamSynchronize(s->stream));
     s->prm = *p;
     s->coef = c;
+    VBC_TRY(upload_window_table(s));
     s->lp = make_list_params(c, s->rlist, s->skin, s->geom);
     s->layout_version += 1;
     // the near/far split of the lists depends on r_r: rebuild before the next pass
@@ -1238,6 +1406,7 @@ int vbc_get_stats(vbc_system* s, vbc_stats* out)
     out->segment_cap = s->seg;
     out->groups = s->nsc;
     out->capacity_grows = s->grows;
+    out->device_bytes = device_bytes(s);
     return VBC_OK;
 }
 

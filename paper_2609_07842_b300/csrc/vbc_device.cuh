@@ -58,6 +58,8 @@ struct Coef {
     float s2hinv;   // s^2 / h: u = (r^2 - r_m^2) / ((r + r_m) h) from an integer difference
     float s2winv;   // s^2 / w: t = (r^2 - r_l^2) / ((r + r_l) w)
     f2x rl_s, w_s;                    // r_l / s and (r_h - r_l) / s as two floats, s = L / 2^32
+    const uint4* wtab;                // window weights as cubic pieces in r^2 (window_weight_tab), or null
+    int wsh;                          // log2 of the r^2 extent of one piece (fixed-point units)
     long long fd_int;                 // floor(f - delta)
     long long fd_frac_fix;            // (f - delta - fd_int) * 2^31, rounded
     long long sat_full;               // ceil(f - delta + 1): this many neighbours inside r_l give s = s' = 0
@@ -294,6 +296,27 @@ __device__ __forceinline__ unsigned long long window_weight_fix31(unsigned long 
     const unsigned long long q =
         ((2147483648ull - (unsigned long long)t31) * (2147483648ull + (unsigned long long)t31)) >> 31;
     return (q * q) >> 31;
+}
+
+// The same weight from a table of cubic pieces in r^2, for the list walks of
+// the FP32-split counts.  Piece k covers D = r^2 - r_l^2 in [k 2^sh,
+// (k + 1) 2^sh) (fixed-point units, exact integers); its entry holds omega at
+// the piece's start in 2^-31 fixed point and the float coefficients of its
+// cubic Hermite interpolant in the local coordinate u in [0, 1):
+// omega = c0 + u (c1 + u (c2 + u c3)).  With 1024 pieces over the window the
+// interpolation error is ~1e-13; the float part is at most the change of
+// omega over one piece (~1e-3), so its rounding adds ~1e-10, and u keeps 23
+// bits.  About 15 instructions against ~55 for window_weight_fix31.
+__device__ __forceinline__ unsigned long long window_weight_tab(unsigned long long D, const uint4* __restrict__ tab,
+                                                                int sh)
+{
+    const uint4 e = __ldg(tab + (int)(D >> sh));
+    const unsigned long long low = D & ((1ull << sh) - 1ull);
+    const uint32_t m = sh >= 23 ? (uint32_t)(low >> (sh - 23)) : (uint32_t)(low << (23 - sh));
+    const float u = u23_to_float(m) * 1.1920928955078125e-7f;  // 2^-23
+    const float d = u * __fmaf_rn(u, __fmaf_rn(u, __uint_as_float(e.w), __uint_as_float(e.z)), __uint_as_float(e.y));
+    const long long q = (long long)e.x + float_to_ll_rn(d * 2147483648.0f);
+    return (unsigned long long)(q < 0 ? 0 : q);
 }
 
 // ---------------------------------------------------------------- position modes

@@ -23,6 +23,9 @@ VBC_ERR_CUDA = -2
 VBC_ERR_OOM = -3
 VBC_ERR_NLIST_OVERFLOW = -4
 VBC_ERR_UNSTABLE = -5
+VBC_ERR_TIMEOUT = -6
+VBC_REQ_QUEUED = 1
+VBC_REQ_RUNNING = 2
 VBC_FP32_SPLIT = 0
 VBC_FP64 = 1
 K_REBUILD, K_COUNT, K_CHAIN, K_FORCE, K_ENERGY = range(5)
@@ -32,7 +35,9 @@ EXPORTS = ("vbc_create_system", "vbc_build_neighbors", "vbc_compute_forces", "vb
            "vbc_get_neighbors",
            "vbc_step_langevin", "vbc_get_state", "vbc_set_state", "vbc_set_params", "vbc_get_stats",
            "vbc_profile", "vbc_profile_read", "vbc_kernel_launches", "vbc_destroy", "vbc_last_error",
-           "vbc_compute_forces_noalloc")
+           "vbc_compute_forces_noalloc", "vbc_estimate_device_bytes",
+           "vbc_server_create", "vbc_server_submit", "vbc_server_wait", "vbc_server_info",
+           "vbc_server_result", "vbc_server_destroy", "vbc_server_last_error")
 
 #: largest n accepted by compute_forces_noalloc (size of its static device scratch)
 NOALLOC_MAX_N = 16384
@@ -56,13 +61,29 @@ class _Config(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("inputs_on_device", ctypes.c_int32)]
 
 
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_int64), ("slots", ctypes.c_int32), ("chunk_steps", ctypes.c_int64)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("system", _Config), ("nsteps", ctypes.c_int64), ("dt", ctypes.c_double),
+                ("kT", ctypes.c_double), ("gamma", ctypes.c_double)]
+
+
+class RequestInfo(ctypes.Structure):
+    """Status and timeline of one served request (seconds on the server's clock)."""
+    _fields_ = [("status", ctypes.c_int32), ("n", ctypes.c_int64), ("steps_done", ctypes.c_int64),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("device_bytes", ctypes.c_int64)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("step", ctypes.c_int64), ("rebuilds", ctypes.c_int64),
                 ("nlist_cap", ctypes.c_int32), ("nlist_max", ctypes.c_int32), ("nlist_mean", ctypes.c_double),
                 ("pairs_within_rc", ctypes.c_int64), ("in_window", ctypes.c_int64),
                 ("unsaturated", ctypes.c_int64), ("stage_cap", ctypes.c_int32), ("group_cap", ctypes.c_int32),
                 ("segment_cap", ctypes.c_int32), ("groups", ctypes.c_int32),
-                ("capacity_grows", ctypes.c_int64)]
+                ("capacity_grows", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
 
 
 _lib = None
@@ -99,6 +120,19 @@ def load() -> ctypes.CDLL:
     L.vbc_compute_forces_noalloc.restype = i32
     L.vbc_last_error.argtypes = []
     L.vbc_last_error.restype = ctypes.c_char_p
+    L.vbc_estimate_device_bytes.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(i64)]
+    L.vbc_server_create.argtypes = [ctypes.POINTER(_ServerConfig), ctypes.POINTER(vp)]
+    L.vbc_server_submit.argtypes = [vp, ctypes.POINTER(_Request), ctypes.POINTER(i64)]
+    L.vbc_server_wait.argtypes = [vp, i64, dp, ctypes.POINTER(RequestInfo)]
+    L.vbc_server_info.argtypes = [vp, i64, ctypes.POINTER(RequestInfo)]
+    L.vbc_server_result.argtypes = [vp, i64, vp, vp, ctypes.POINTER(RequestInfo)]
+    L.vbc_server_destroy.argtypes = [vp]
+    L.vbc_server_destroy.restype = None
+    L.vbc_server_last_error.argtypes = []
+    L.vbc_server_last_error.restype = ctypes.c_char_p
+    for name in ("vbc_estimate_device_bytes", "vbc_server_create", "vbc_server_submit", "vbc_server_wait",
+                 "vbc_server_info", "vbc_server_result"):
+        getattr(L, name).restype = i32
     for name in ("vbc_create_system", "vbc_build_neighbors", "vbc_compute_forces", "vbc_get_switch",
                  "vbc_get_neighbors", "vbc_step_langevin", "vbc_get_state", "vbc_set_state", "vbc_set_params", "vbc_get_stats",
                  "vbc_profile", "vbc_profile_read"):
@@ -302,3 +336,96 @@ def compute_forces_noalloc(pos, box: float, prm: PairParams, F, counts=None, str
                                              ctypes.byref(prm), ctypes.c_void_p(F.data_ptr()),
                                              ctypes.c_void_p(counts.data_ptr()) if counts is not None else None,
                                              ctypes.c_void_p(stream) if stream else None))
+
+
+def _host_config(pos, box, prm: PairParams | None, vel, skin: float, seed: int, precision: int,
+                 nlist_cap: int = 0):
+    """A vbc_config over host float64 arrays (kept alive by the caller)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    n = pos.shape[0]
+    if vel is not None:
+        vel = np.ascontiguousarray(vel, dtype=np.float64)
+    b = np.broadcast_to(np.asarray(box, dtype=np.float64), (3,))
+    cfg = _Config(n=n, box=(ctypes.c_double * 3)(*b), pos=ctypes.c_void_p(pos.ctypes.data),
+                  vel=ctypes.c_void_p(vel.ctypes.data) if vel is not None else None,
+                  params=prm if prm is not None else params(), skin=skin, seed=seed, precision=precision,
+                  nlist_cap=nlist_cap, stream=None, inputs_on_device=0)
+    return cfg, pos, vel
+
+
+def estimate_device_bytes(n: int, box, prm: PairParams | None = None, skin: float = 0.4,
+                          precision: int = VBC_FP32_SPLIT) -> int:
+    """Device bytes vbc_create_system would allocate for n particles in this box
+    (vbc_estimate_device_bytes; touches no device)."""
+    pos = np.zeros((max(int(n), 1), 3))
+    cfg, _, _ = _host_config(pos, box, prm, None, skin, 0, precision)
+    cfg.n = int(n)
+    out = ctypes.c_int64(0)
+    _check(load().vbc_estimate_device_bytes(ctypes.byref(cfg), ctypes.byref(out)))
+    return int(out.value)
+
+
+def _check_server(rc: int):
+    if rc != VBC_OK:
+        raise VBCError(rc, load().vbc_server_last_error().decode())
+
+
+class Server:
+    """Serving loop (vbc_server_*): requests admitted in arrival order by free
+    slots and a device-memory budget, advanced in chunks on their own streams,
+    state resident on the device until a request finishes."""
+
+    def __init__(self, hbm_budget: float = 150e9, slots: int = 8, chunk_steps: int = 1000):
+        L = load()
+        h = ctypes.c_void_p()
+        cfg = _ServerConfig(hbm_budget=int(hbm_budget), slots=int(slots), chunk_steps=int(chunk_steps))
+        _check_server(L.vbc_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, pos, box, prm: PairParams | None = None, nsteps: int = 1000, dt: float = 0.005,
+               kT: float = 1.0, gamma: float = 1.0, vel=None, skin: float = 0.4, seed: int = 0,
+               precision: int = VBC_FP32_SPLIT) -> int:
+        """Queue one simulation; returns its request id.  The inputs are copied."""
+        cfg, _p, _v = _host_config(pos, box, prm, vel, skin, seed, precision)
+        req = _Request(system=cfg, nsteps=int(nsteps), dt=dt, kT=kT, gamma=gamma)
+        rid = ctypes.c_int64(0)
+        _check_server(load().vbc_server_submit(self._h, ctypes.byref(req), ctypes.byref(rid)))
+        return int(rid.value)
+
+    def wait(self, rid: int = -1, timeout: float = -1.0) -> RequestInfo | None:
+        """Wait for one request (or, rid = -1, for all); raises VBCError(VBC_ERR_TIMEOUT) on timeout."""
+        info = RequestInfo()
+        _check_server(load().vbc_server_wait(self._h, int(rid), float(timeout),
+                                             ctypes.byref(info) if rid != -1 else None))
+        return info if rid != -1 else None
+
+    def info(self, rid: int) -> RequestInfo:
+        info = RequestInfo()
+        _check_server(load().vbc_server_info(self._h, int(rid), ctypes.byref(info)))
+        return info
+
+    def result(self, rid: int):
+        """(positions [n,3] unwrapped, velocities [n,3], RequestInfo) of a finished request."""
+        info = self.info(rid)
+        pos = np.zeros((info.n, 3))
+        vel = np.zeros((info.n, 3))
+        _check_server(load().vbc_server_result(self._h, int(rid), ctypes.c_void_p(pos.ctypes.data),
+                                               ctypes.c_void_p(vel.ctypes.data), ctypes.byref(info)))
+        return pos, vel, info
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().vbc_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

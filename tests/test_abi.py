@@ -94,3 +94,31 @@ def test_orthorhombic_box_allowed_in_fp64_until_device_needed(lib):
     else:
         assert rc in (vbc.VBC_ERR_CUDA, vbc.VBC_ERR_OOM)
         assert not h.value
+
+
+# ----------------------------------------------------------------- serving admission estimate
+def test_device_bytes_estimate_scales_with_n(lib):
+    """vbc_estimate_device_bytes touches no device: it sizes the arrays of a
+    system from n, the box and the list radius.  Per particle it must cover at
+    least the resident state (unwrapped positions and velocities, both FP64
+    copies, positions, force slots, close lists), and grow linearly with n at a
+    fixed density."""
+    prm = vbc.params(E_a=8.0, f=2.0)
+    b1 = vbc.estimate_device_bytes(100_000, (100_000 / 0.5) ** (1 / 3), prm)
+    b2 = vbc.estimate_device_bytes(800_000, (800_000 / 0.5) ** (1 / 3), prm)
+    assert b1 >= 100_000 * (4 * 24 + 4 * 16 + 48 + 16)
+    assert 7.0 < b2 / b1 < 9.0
+    assert vbc.estimate_device_bytes(100_000, (100_000 / 0.5) ** (1 / 3), prm, precision=vbc.VBC_FP64) > b1
+
+
+@pytest.mark.parametrize("kw,needle", [
+    (dict(n=0), "n must be"),
+    (dict(box=(6.0, 6.0, 6.0)), "fewer than 3 cells"),
+    (dict(skin=0.0), "skin"),
+])
+def test_device_bytes_estimate_rejects_bad_configs(lib, kw, needle):
+    c, _pos = _cfg(**kw)
+    out = ctypes.c_int64(0)
+    rc = lib.vbc_estimate_device_bytes(ctypes.byref(c), ctypes.byref(out))
+    assert rc == vbc.VBC_ERR_INVALID_ARG
+    assert needle in lib.vbc_last_error().decode()
