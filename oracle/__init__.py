@@ -182,6 +182,28 @@ def pairs_within(pos: np.ndarray, box, rcut: float) -> np.ndarray:
         cap = int(m)
 
 
+@dataclass
+class Observables:
+    z: np.ndarray       # [n] neighbours within the attraction range, r_ij < r_a (strict)
+    mean_z: float       # <z>
+    p_err: float        # fraction of particles with z_i > f
+    z_hist: np.ndarray  # [nbins] particles with z_i = k (last bin: z_i >= nbins - 1)
+
+
+def observables(pos: np.ndarray, box, p: Params, nbins: int = 32) -> Observables:
+    """Valency observables of Sec. 3: the neighbour number z_i = #{j != i : r_ij < r_a}
+    (an instantaneous distance criterion, strict), its mean <z>, and the
+    over-coordination probability P_err = fraction of particles with z_i > f.
+    All pairs, minimum image, FP64."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    n = pos.shape[0]
+    pr = pairs_within(pos, box, p.r_a)
+    z = (np.bincount(pr[:, 0], minlength=n) + np.bincount(pr[:, 1], minlength=n)).astype(np.int64)
+    hist = np.bincount(np.minimum(z, nbins - 1), minlength=nbins).astype(np.int64)
+    return Observables(z=z, mean_z=float(z.mean()) if n else 0.0, p_err=float(np.mean(z > p.f)) if n else 0.0,
+                       z_hist=hist)
+
+
 def philox4x32_10(ctr, key) -> tuple:
     """Philox4x32 with 10 rounds (Salmon et al., SC'11)."""
     c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])

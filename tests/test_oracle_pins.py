@@ -332,6 +332,49 @@ def test_pairs_within_brute_force():
     assert set(map(tuple, pairs.tolist())) == expect
 
 
+# ------------------------------------------------------------ valency observables (Sec. 3)
+def test_observables_line_by_hand():
+    """Four particles on a line at x = 0, 1.2, 2.5, 10 (r_a = 1.5): neighbours are
+    the pairs closer than r_a, so z = (1, 2, 1, 0), <z> = 1 and, at f = 1, only the
+    middle particle is over-coordinated."""
+    pos = np.array([[0.0, 0, 0], [1.2, 0, 0], [2.5, 0, 0], [10.0, 0, 0]]) + 5.0
+    ob = oracle.observables(pos, 40.0, Params(f=1.0), nbins=4)
+    assert ob.z.tolist() == [1, 2, 1, 0]
+    assert ob.mean_z == 1.0 and ob.p_err == 0.25
+    assert ob.z_hist.tolist() == [1, 2, 1, 0]
+
+
+def test_observables_strict_at_r_a():
+    """The criterion is strict: a pair exactly r_a apart is not a neighbour."""
+    pos = np.array([[5.0, 5.0, 5.0], [6.5, 5.0, 5.0]])
+    assert oracle.observables(pos, 20.0, Params()).z.tolist() == [0, 0]
+    pos[1, 0] = np.nextafter(6.5, 0.0)
+    assert oracle.observables(pos, 20.0, Params()).z.tolist() == [1, 1]
+
+
+def test_observables_paper_shell_occupancy(golden_dir):
+    """Sec. 3 at rho = 0.05: about 0.5 shell occupants (r_r < r < r_a) per
+    particle and about 9% of particles with two or more, as the difference of
+    the neighbour numbers at r_a and at r_r; the full neighbour number of an
+    ideal fluid has mean rho 4 pi r_a^3 / 3."""
+    vals = {}
+    with open(os.path.join(golden_dir, "paper_shell_occupancy.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                t = line.split()
+                vals[t[0]] = [float(x) for x in t[1:]]
+    rho = vals["rho"][0]
+    pos, L = inputs.uniform_positions(20000, rho, seed=22)
+    za = oracle.observables(pos, L, Params(r_a=1.5)).z
+    zr = oracle.observables(pos, L, Params(r_a=1.0)).z
+    shell = za - zr
+    mean, tol = vals["mean_shell_occupants"]
+    assert abs(shell.mean() - mean) < tol + 0.015
+    p2, tol2 = vals["p_two_or_more"]
+    assert abs(np.mean(shell >= 2) - p2) < tol2 + 0.008
+    assert abs(za.mean() - rho * 4.0 * np.pi / 3.0 * 1.5 ** 3) < 0.035
+
+
 # ------------------------------------------------------------ BAOAB Langevin
 def test_free_flight_is_exact():
     """No forces, no friction: x advances by dt v, v is unchanged."""
