@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--served-requests", type=int, default=24)
     ap.add_argument("--served-steps", type=int, default=50_000, help="Langevin steps per served request")
     ap.add_argument("--served-slots", type=int, default=16)
+    ap.add_argument("--sweep", action="store_true",
+                    help="cost-vs-valency curve (N=100k, rho 0.5, E_a 8, v in 1,2,4,6,8) and the paper-shape "
+                         "point (N=10k, rho 0.05, E_a 2, dt 0.01, gamma 0.1, f = 1..6); one JSON line each")
     ap.add_argument("--profile-run", action="store_true",
                     help="short run for profilers: the equilibrated workload (cached under /tmp), one forced "
                          "list build, one force evaluation and 6 steps; prints no JSON line")
@@ -281,12 +284,59 @@ def run_served(args, slots):
             "ok": all(x.status == 0 for x in infos)}
 
 
+def timed_steps(sys_, steps, dt, kT, gamma):
+    """ms per step of `steps` Langevin steps (CUDA events on the library's stream)."""
+    import torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    sys_.step(steps, dt, kT, gamma)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / steps
+
+
+def sweep(args):
+    """The single-system valency sweep (N = 100k, density 0.5, E_a = 8, FP32
+    split; the cost-vs-valency curve of the paper's performance table) and the
+    paper-shape point (N = 10k, density 0.05, E_a = 2, dt = 0.01, gamma = 0.1,
+    f = 1..6), each after an untimed equilibration.  Prints one JSON line per
+    configuration."""
+    import torch
+    from paper_2609_07842_b300 import inputs, vbc
+    stream = torch.cuda.current_stream()
+    cases = [("valency sweep", 100_000, 0.5, 8.0, float(v), DT, GAMMA, 2000, 1000) for v in (1, 2, 4, 6, 8)]
+    cases += [("paper shape", 10_000, 0.05, 2.0, float(f), 0.01, 0.1, 5000, 2000) for f in range(1, 7)]
+    for name, n, rho, ea, f, dt, gamma, steps, equil in cases:
+        pos, L = inputs.uniform_positions(n, rho, seed=SEED)
+        vel = inputs.maxwell_velocities(n, KT, seed=SEED + 1)
+        with vbc.System(pos, L, vbc.params(E_a=ea, f=f), vel=vel, skin=SKIN, seed=SEED,
+                        stream=stream.cuda_stream) as s:
+            s.step(equil, dt, KT, gamma)
+            st0 = s.stats()
+            ms = timed_steps(s, steps, dt, KT, gamma)
+            st1 = s.stats()
+            s.compute(energy=True)  # counts the pairs within r_c
+            st2 = s.stats()
+        sps = 1e3 / ms
+        print(json.dumps({"sweep": name, "n": n, "rho": rho, "E_a": ea, "valency": f, "dt": dt, "gamma": gamma,
+                          "steps": steps, "equilibration_steps": equil, "timesteps_per_s": sps,
+                          "seconds_per_1e6_steps": 1e6 / sps,
+                          "pair_interactions_per_s": st2.pairs_within_rc * sps,
+                          "in_window_fraction": st2.in_window / n, "unsaturated_fraction": st2.unsaturated / n,
+                          "steps_per_rebuild": steps / max(st1.rebuilds - st0.rebuilds, 1),
+                          "precision": "FP32 split", "data": "synthetic"}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_main(args)
     if args.profile_run:
         return profile_run(args)
+    if args.sweep:
+        return sweep(args)
 
     import torch
     import torch.distributed as dist

@@ -236,6 +236,26 @@ void vbc_destroy(vbc_system* sys);
 /* Message describing the last error of the calling thread ("" if none). */
 const char* vbc_last_error(void);
 
+/* ------------------------------------------------------------------ observables
+ * Valency observables of Sec. 3 on the current state: two particles are
+ * neighbours when r_ij < r_a (strict; an instantaneous distance criterion, so
+ * transient contacts count as well as bonds).  z_i is the number of
+ * neighbours of particle i, <z> its mean, and P_err the fraction of particles
+ * with z_i > f (over-coordination).  Integer sums on the device, so the
+ * figures do not depend on the launch. */
+#define VBC_ZHIST 32
+typedef struct {
+    double mean_z;                /* <z> */
+    double p_err;                 /* fraction of particles with z_i > f */
+    int64_t z_hist[VBC_ZHIST];    /* particles with z_i = k; the last bin holds z_i >= VBC_ZHIST - 1 */
+} vbc_observables;
+
+/* Fill *out; if z is not NULL, also z_i per particle ([n] int32, caller's
+ * particle order; a device pointer if on_device).  Rebuilds the neighbour
+ * list first if it is due.  Errors: INVALID_ARG (NULL out), CUDA, OOM,
+ * NLIST_OVERFLOW. */
+int vbc_get_observables(vbc_system* s, vbc_observables* out, int32_t* z, int on_device);
+
 /* ------------------------------------------------------------------ serving
  * Many independent simulations (valency and temperature sweeps, Sec. 5: one
  * system per parameter set) on one GPU.  A server admits submitted requests

@@ -128,6 +128,8 @@ struct vbc_system {
     int row_grid = 1;           // blocks of the row walks (count rows, chain-rule pass, force rows)
     long long grows = 0;        // capacity growths after an overflow
     uint4* wtab = nullptr;      // [WTAB_PIECES + 1] window-weight pieces of the counts (window_weight_tab)
+    unsigned long long* obs = nullptr;  // [2 + ZHIST] sums of k_observe
+    int* zbuf = nullptr;                // [n] z per particle for host output of k_observe
     void *ds = nullptr, *sA = nullptr;
     Status* st = nullptr;
     Status* st_host = nullptr;  // pinned
@@ -422,7 +424,7 @@ void free_all(vbc_system* s)
     dfree(s->chunk_sum); dfree(s->wpart); dfree(s->ulist); dfree(s->stage_idx); dfree(s->gmeta); dfree(s->roff_g);
     dfree(s->close_k); dfree(s->fcore); dfree(s->glist);
     dfree(s->ds); dfree(s->sA); dfree(s->st); dfree(s->partial); dfree(s->ppairs); dfree(s->red);
-    dfree(s->win); dfree(s->e_sd); dfree(s->e_A); dfree(s->wtab);
+    dfree(s->win); dfree(s->e_sd); dfree(s->e_A); dfree(s->wtab); dfree(s->obs); dfree(s->zbuf);
     if (s->st_host) cudaFreeHost(s->st_host);
     if (s->red_host) cudaFreeHost(s->red_host);
     s->st_host = nullptr;
@@ -506,7 +508,7 @@ int enqueue_rebuild(vbc_system* s)
     k_scan_sums<<<nchunk, SCAN_TPB, 0, s->stream>>>(s->cell_count, s->npad, s->chunk_sum, s->st);
     k_scan_apply<<<nchunk, SCAN_TPB, 0, s->stream>>>(s->cell_count, s->npad, s->chunk_sum, s->cell_start, s->st);
     k_scatter<<<nb, TPB, 0, s->stream>>>(n, s->cell_of, s->slot_of, s->cell_start, s->order, s->st);
-    k_cellsort<M><<<blocks_for(s->npad, TPB), TPB, 0, s->stream>>>(s->npad, s->cell_start, s->order, pos, s->st);
+    k_cellsort<<<blocks_for(s->npad, TPB), TPB, 0, s->stream>>>(s->npad, s->cell_start, s->order, s->st);
     k_permute<M><<<nb, TPB, 0, s->stream>>>(n, s->order, s->x, s->v, s->id, pos, s->xt, s->vt, s->idt,
                                             (pos_t*)s->post, s->st);
     k_copyback<M><<<nb, TPB, 0, s->stream>>>(n, s->xt, s->vt, s->idt, (const pos_t*)s->post, s->x, s->v, s->id,
@@ -757,6 +759,33 @@ int compute_impl(vbc_system* s, double* F_dev, double* n_dev, bool energy)
         if (attempt >= MAX_RETRIES) return fail(VBC_ERR_NLIST_OVERFLOW, "capacities kept overflowing");
         VBC_TRY(grow(s));
     }
+    return VBC_OK;
+}
+
+// Valency observables of the current state: the list is rebuilt first if due
+// (with the overflow retry of compute_impl), then k_observe walks every row.
+template <class M>
+int observables_impl(vbc_system* s, vbc_observables* out, int* z_dev)
+{
+    if (!s->obs) VBC_TRY(dalloc(s->obs, 2 + ZHIST));
+    for (int attempt = 0;; ++attempt) {
+        VBC_CUDA(cudaMemsetAsync(s->obs, 0, (2 + ZHIST) * sizeof(unsigned long long), s->stream));
+        VBC_TRY(enqueue_rebuild<M>(s));
+        k_observe<M><<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>(
+            (int)s->n, s->geom, s->coef, (const typename M::pos_t*)s->pos[s->cur], s->caps(), s->aux(), s->nbr,
+            s->nnb, s->id, z_dev, s->obs, s->st);
+        VBC_TRY(check_launch(s));
+        VBC_TRY(read_status(s));
+        VBC_TRY(halt_error(s));
+        if (!needs_growth(s)) break;
+        if (attempt >= MAX_RETRIES) return fail(VBC_ERR_NLIST_OVERFLOW, "capacities kept overflowing");
+        VBC_TRY(grow(s));
+    }
+    unsigned long long h[2 + ZHIST];
+    VBC_CUDA(cudaMemcpy(h, s->obs, sizeof h, cudaMemcpyDeviceToHost));
+    out->mean_z = (double)h[0] / (double)s->n;
+    out->p_err = (double)h[1] / (double)s->n;
+    for (int k = 0; k < ZHIST; ++k) out->z_hist[k] = (int64_t)h[2 + k];
     return VBC_OK;
 }
 
@@ -1383,6 +1412,28 @@ int vbc_set_params(vbc_system* s, const vbc_pair_params* p)
     s->layout_version += 1;
     // the near/far split of the lists depends on r_r: rebuild before the next pass
     return force_rebuild_flag(s);
+}
+
+int vbc_get_observables(vbc_system* s, vbc_observables* out, int32_t* z, int on_device)
+{
+    VBC_TRY(check_sys(s));
+    if (!out) return fail(VBC_ERR_INVALID_ARG, "out must not be NULL");
+    static_assert(VBC_ZHIST == ZHIST, "histogram bins of the header and the kernel differ");
+    int* z_dev = nullptr;
+    if (z) {
+        if (on_device) {
+            z_dev = z;
+        } else {
+            if (!s->zbuf) VBC_TRY(dalloc(s->zbuf, (size_t)s->n));
+            z_dev = s->zbuf;
+        }
+    }
+    VBC_TRY(s->prec == VBC_FP64 ? observables_impl<ModeF64>(s, out, z_dev) : observables_impl<ModeF32>(s, out, z_dev));
+    if (z && !on_device) {
+        VBC_CUDA(cudaMemcpyAsync(z, s->zbuf, (size_t)s->n * sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+        VBC_CUDA(cudaStreamSynchronize(s->stream));
+    }
+    return VBC_OK;
 }
 
 int vbc_get_stats(vbc_system* s, vbc_stats* out)

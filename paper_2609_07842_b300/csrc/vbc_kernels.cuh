@@ -155,52 +155,41 @@ __global__ void __launch_bounds__(TPB) k_scatter(int n, const int* __restrict__ 
     order[cell_start[cell_of[i]] + slot_of[i]] = i;
 }
 
-// Within each cell the particles are ordered by x (the high 32 bits of the
-// fixed-point coordinate), ties by their index in the previous sorted order,
-// so that the layout (and every summation order) is a function of the
-// previous layout and the positions only, not of atomic scheduling.  Cells
-// adjacent in x are adjacent in the list build's staging, so each 3-cell row
-// of candidates is sorted by x and the build tests only the x-range a
-// particle can reach.  Key = x << 32 | previous index; cells of up to 16
-// particles are sorted in registers (odd-even transposition), larger ones by
-// insertion in memory.
-__device__ __forceinline__ uint32_t sort_x(const int4& p) { return (uint32_t)p.x; }
-__device__ __forceinline__ uint32_t sort_x(const P64& p) { return (uint32_t)(p.x >> 32); }
-
-template <class M>
+// Within each cell, order particles by their index in the previous sorted
+// order, so that the layout (and every summation order) is a function of the
+// previous layout and the positions only, not of atomic scheduling.  Cells of
+// up to 16 particles are sorted in registers (odd-even transposition), larger
+// ones by insertion in memory.
 __global__ void __launch_bounds__(TPB) k_cellsort(int ncell, const int* __restrict__ cell_start,
-                                                  int* __restrict__ order, const typename M::pos_t* __restrict__ pos,
-                                                  const Status* st)
+                                                  int* __restrict__ order, const Status* st)
 {
     if (!st->rebuild || st->frozen || st->crowded) return;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
     const int b = cell_start[c], e = cell_start[c + 1], cnt = e - b;
     if (cnt <= 1) return;
-    const auto key = [&](int o) { return ((unsigned long long)sort_x(pos[o]) << 32) | (unsigned)o; };
     if (cnt <= 16) {
-        unsigned long long v[16];
+        int v[16];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) v[k] = k < cnt ? key(order[b + k]) : ~0ull;
+        for (int k = 0; k < 16; ++k) v[k] = k < cnt ? order[b + k] : 0x7fffffff;
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
 #pragma unroll
             for (int k = r & 1; k + 1 < 16; k += 2) {
-                const unsigned long long lo = min(v[k], v[k + 1]), hi = max(v[k], v[k + 1]);
+                const int lo = min(v[k], v[k + 1]), hi = max(v[k], v[k + 1]);
                 v[k] = lo;
                 v[k + 1] = hi;
             }
         }
 #pragma unroll
         for (int k = 0; k < 16; ++k)
-            if (k < cnt) order[b + k] = (int)(unsigned)v[k];
+            if (k < cnt) order[b + k] = v[k];
         return;
     }
     for (int k = b + 1; k < e; ++k) {
         const int o = order[k];
-        const unsigned long long ko = key(o);
         int m = k - 1;
-        while (m >= b && key(order[m]) > ko) {
+        while (m >= b && order[m] > o) {
             order[m + 1] = order[m];
             --m;
         }
@@ -547,31 +536,6 @@ __host__ __device__ inline ForceLayout force_layout(const SuperCaps& cp, size_t 
     return l;
 }
 
-// Binary searches over staged candidates sorted by x (block-relative floats):
-// the first m in [lo, hi) with x >= v, and with x > v.
-__device__ __forceinline__ int first_x_at_least(const float4* spos, int lo, int hi, float v)
-{
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (spos[mid].x < v) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-__device__ __forceinline__ int first_x_above(const float4* spos, int lo, int hi, float v)
-{
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (spos[mid].x <= v) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-// Margin of the x-range trim (length units): far above the rounding of the
-// block-relative float coordinates (~1e-6), so that no candidate within the
-// list radius is ever trimmed.
-constexpr float XTRIM_EPS = 1e-3f;
-
 // ================================================================ rebuild: lists
 // One block per cell group: stage the surrounding cells, then each thread
 // takes own particles and scans the 9 contiguous x rows of their 27-cell
@@ -643,17 +607,12 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
     int mx = 0;
     long long sum = 0;
     bool over = false;
-    const float cw[3] = {(float)(g.L[0] / g.nc[0]), (float)(g.L[1] / g.nc[1]), (float)(g.L[2] / g.nc[2])};
     for (int j = t; j < n_own; j += SC_TPB) {
         const int p = p0 + j;
         const int b = own_cell(T, p);
         const int kb = own_staged_cell(b);
         const int mself = T.off[kb] + (p - T.own[b]);
         const spos_t pi = spos[mself];
-        // y and z bounds of the particle's cell, relative to the group's reference
-        // (staged cell (sx, sy, sz) spans [sx - 3, sx - 2) x [sy - 2, sy - 1) x [sz - 2, sz - 1) cells)
-        const float cy0 = (float)((kb / SX) % SY - 2) * cw[1], cy1 = cy0 + cw[1];
-        const float cz0 = (float)(kb / (SX * SY) - 2) * cw[2], cz1 = cz0 + cw[2];
         uint16_t* row = scratch + (size_t)p * cp.cap;
         int nn = 0, nf = 0;
         // far entries within r_l, in scan order, go to the close list's slots for now
@@ -663,20 +622,8 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
 #pragma unroll 1
         for (int d = 0; d < 9; ++d) {
             const int k0 = kb + (d / 3 - 1) * (SX * SY) + (d % 3 - 1) * SX - 1;
-            int b0 = T.off[k0], e = T.off[k0 + 3];
-            if constexpr (REL) {
-                // the row's candidates are sorted by x: keep those within the x-reach left
-                // by the particle's distance to the row's cells across y and z
-                const int oy = d % 3 - 1, oz = d / 3 - 1;
-                const float dy = oy == 0 ? 0.0f : fmaxf(0.0f, (oy > 0 ? cy1 - pi.y : pi.y - cy0) - XTRIM_EPS);
-                const float dz = oz == 0 ? 0.0f : fmaxf(0.0f, (oz > 0 ? cz1 - pi.z : pi.z - cz0) - XTRIM_EPS);
-                const float reach2 = lp.rlist2_f - __fmaf_rn(dy, dy, dz * dz);
-                if (reach2 < 0.0f) continue;
-                const float reach = sqrtf(reach2) + XTRIM_EPS;
-                b0 = first_x_at_least(spos, b0, e, pi.x - reach);
-                e = first_x_above(spos, b0, e, pi.x + reach);
-            }
-            for (int base = b0; base < e; base += 32) {
+            const int e = T.off[k0 + 3];
+            for (int base = T.off[k0]; base < e; base += 32) {
                 // test up to 32 candidates into bit masks, then write the accepted ones.  Each
                 // mask takes one bit per candidate, shifted in from the bottom, so candidate u
                 // ends at bit cnt - 1 - u; in the FP32 mode the bit is the sign of r^2 minus
@@ -1812,6 +1759,46 @@ __global__ void __launch_bounds__(SC_TPB) k_energy(Geom g, Coef c, const typenam
     }
 }
 
+
+// ================================================================ valency observables
+// z_i = #{j != i : r_ij < r_a} (Sec. 3: neighbours within the attraction
+// range, an instantaneous and strict distance criterion), walked over the
+// particle's list row (radius r_c + skin >= r_a).  Integer sums only: acc[0]
+// = sum of z, acc[1] = particles with z > f, acc[2 + k] = particles with
+// z = k (last bin: z >= ZHIST - 1), each formed per block in shared memory
+// and added once per block.  Optional z per particle in caller order.
+constexpr int ZHIST = 32;
+template <class M>
+__global__ void __launch_bounds__(TPB) k_observe(int n, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
+                                                 SuperCaps cp, GroupAux aux, const uint16_t* __restrict__ nbr,
+                                                 const int* __restrict__ nnb, const int* __restrict__ id,
+                                                 int* __restrict__ z_out, unsigned long long* __restrict__ acc,
+                                                 const Status* st)
+{
+    __shared__ unsigned long long s_acc[2 + ZHIST];
+    for (int k = threadIdx.x; k < 2 + ZHIST; k += blockDim.x) s_acc[k] = 0ull;
+    __syncthreads();
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n && !halted(st)) {
+        const int ra = __ldg(aux.roff + p), b = ra / cp.seg;
+        const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
+        const int len = row_len(__ldg(nnb + p));
+        const typename M::pos_t pi = pos[p];
+        int z = 0;
+        for (int e = 0; e < len; ++e) {
+            const typename M::pos_t pj = pos[__ldg(sidx + __ldg(nbr + ra + e))];
+            if constexpr (M::fp64) z += r2_d<M>(pi, pj, g) < c.ra2;
+            else z += r2_fix(pi, pj) < c.ra2_fix;
+        }
+        if (z_out) z_out[id[p]] = z;
+        atomicAdd(&s_acc[0], (unsigned long long)z);
+        if ((double)z > c.f) atomicAdd(&s_acc[1], 1ull);
+        atomicAdd(&s_acc[2 + min(z, ZHIST - 1)], 1ull);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 2 + ZHIST; k += blockDim.x)
+        if (s_acc[k]) atomicAdd(acc + k, s_acc[k]);
+}
 constexpr int RED_TPB = 256;
 // Fixed-order sum of the block partials: out[0] = U, out[1] = W; pairs / 2 -> Status.
 __global__ void __launch_bounds__(RED_TPB) k_reduce_final(int nb, const double* __restrict__ partial,

@@ -35,7 +35,7 @@ EXPORTS = ("vbc_create_system", "vbc_build_neighbors", "vbc_compute_forces", "vb
            "vbc_get_neighbors",
            "vbc_step_langevin", "vbc_get_state", "vbc_set_state", "vbc_set_params", "vbc_get_stats",
            "vbc_profile", "vbc_profile_read", "vbc_kernel_launches", "vbc_destroy", "vbc_last_error",
-           "vbc_compute_forces_noalloc", "vbc_estimate_device_bytes",
+           "vbc_compute_forces_noalloc", "vbc_estimate_device_bytes", "vbc_get_observables",
            "vbc_server_create", "vbc_server_submit", "vbc_server_wait", "vbc_server_info",
            "vbc_server_result", "vbc_server_destroy", "vbc_server_last_error")
 
@@ -59,6 +59,14 @@ class _Config(ctypes.Structure):
                 ("vel", ctypes.c_void_p), ("params", PairParams), ("skin", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32), ("nlist_cap", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("inputs_on_device", ctypes.c_int32)]
+
+
+ZHIST = 32
+
+
+class Observables(ctypes.Structure):
+    """Valency observables (Sec. 3): <z>, P_err and the histogram of z_i."""
+    _fields_ = [("mean_z", ctypes.c_double), ("p_err", ctypes.c_double), ("z_hist", ctypes.c_int64 * ZHIST)]
 
 
 class _ServerConfig(ctypes.Structure):
@@ -121,6 +129,8 @@ def load() -> ctypes.CDLL:
     L.vbc_last_error.argtypes = []
     L.vbc_last_error.restype = ctypes.c_char_p
     L.vbc_estimate_device_bytes.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(i64)]
+    L.vbc_get_observables.argtypes = [vp, ctypes.POINTER(Observables), vp, i32]
+    L.vbc_get_observables.restype = i32
     L.vbc_server_create.argtypes = [ctypes.POINTER(_ServerConfig), ctypes.POINTER(vp)]
     L.vbc_server_submit.argtypes = [vp, ctypes.POINTER(_Request), ctypes.POINTER(i64)]
     L.vbc_server_wait.argtypes = [vp, i64, dp, ctypes.POINTER(RequestInfo)]
@@ -301,6 +311,14 @@ class System:
 
     def set_params(self, prm: PairParams):
         _check(load().vbc_set_params(self._h, ctypes.byref(prm)))
+
+    def observables(self, z: bool = False):
+        """(Observables, z_i per particle [n] int32 or None) of the current state."""
+        out = Observables()
+        zz = np.zeros(self.n, dtype=np.int32) if z else None
+        _check(load().vbc_get_observables(self._h, ctypes.byref(out),
+                                          ctypes.c_void_p(zz.ctypes.data) if z else None, 0))
+        return out, zz
 
     def stats(self) -> Stats:
         s = Stats()

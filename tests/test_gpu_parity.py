@@ -302,6 +302,41 @@ def test_forces_only_row_walk_modes(prec, case):
         assert st.in_window > n // 16 and st.unsaturated > n // 16
 
 
+# ----------------------------------------------------------------- valency observables
+def _borderline(pos, L, i, r_a, eps=1e-6):
+    """Particle i has a pair within eps of r_a, where the two sides' position
+    representations (FP64 here, fixed point on the device) may decide r < r_a
+    differently."""
+    d = pos - pos[i]
+    d -= L * np.round(d / L)
+    r = np.sqrt((d * d).sum(1))
+    return bool(np.any(np.abs(r - r_a) < eps))
+
+
+@pytest.mark.parametrize("prec", [F32, F64])
+@pytest.mark.parametrize("rho,n", [(0.05, 20000), (0.5, 30000)])
+def test_valency_observables(prec, rho, n):
+    """z_i, <z>, P_err and the z histogram (Sec. 3) against the oracle, element by
+    element (integers: equal except for particles with a pair within 1e-6 of r_a),
+    on a fresh state and after 50 Langevin steps with rebuilds."""
+    pos, L = inputs.uniform_positions(n, rho, seed=17)
+    p = Params(E_a=8.0, f=2.0)
+    with vbc.System(pos, L, to_vbc(p), precision=prec) as s:
+        for nsteps in (0, 50):
+            if nsteps:
+                s.step(nsteps, 0.005, 1.0, 1.0)
+            cur, _, _ = s.get_state()
+            ob, z = s.observables(z=True)
+            ref = oracle.observables(cur, L, p)
+            bad = np.nonzero(z != ref.z)[0]
+            assert len(bad) <= 4
+            assert all(_borderline(cur, L, i, p.r_a) for i in bad)
+            assert ob.mean_z == pytest.approx(z.mean(), abs=1e-12)
+            assert ob.p_err == pytest.approx(np.mean(z > p.f), abs=1e-12)
+            assert list(ob.z_hist) == np.bincount(np.minimum(z, vbc.ZHIST - 1), minlength=vbc.ZHIST).tolist()
+            assert abs(ob.mean_z - ref.mean_z) <= 2.0 * len(bad) / n
+
+
 # ----------------------------------------------------------------- full sizes
 @pytest.mark.parametrize("n", [100_000, 1_000_000])
 def test_full_size_uniform_rho05(n):
