@@ -315,7 +315,8 @@ __device__ __forceinline__ unsigned long long window_weight_tab(unsigned long lo
     const uint32_t m = sh >= 23 ? (uint32_t)(low >> (sh - 23)) : (uint32_t)(low << (23 - sh));
     const float u = u23_to_float(m) * 1.1920928955078125e-7f;  // 2^-23
     const float d = u * __fmaf_rn(u, __fmaf_rn(u, __uint_as_float(e.w), __uint_as_float(e.z)), __uint_as_float(e.y));
-    const long long q = (long long)e.x + float_to_ll_rn(d * 2147483648.0f);
+    // |d| 2^31 < 2^22 (the change of omega over one piece), so a 32-bit conversion holds it
+    const long long q = (long long)e.x + (long long)__float2int_rn(d * 2147483648.0f);
     return (unsigned long long)(q < 0 ? 0 : q);
 }
 

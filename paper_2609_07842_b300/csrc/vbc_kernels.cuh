@@ -961,11 +961,11 @@ __device__ __forceinline__ void pair_f32(const int4& pi, float si, float Ai, con
         const float r = r2 * rinv;
         float gt = 0.0f;  // g from the well and the counts
         if (well) {
-            const float u = s64_to_float((long long)r2i - (long long)c.rm2_fix) * c.s2hinv / (r + c.rmf);
+            const float u = __fdividef(s64_to_float((long long)r2i - (long long)c.rm2_fix) * c.s2hinv, r + c.rmf);
             gt = si * sj * c.Ea4hf * u * (1.0f - u * u);
         }
         if (chain) {
-            const float tt = u64_to_float(r2i - c.rl2_fix) * c.s2winv / (r + c.rlf);
+            const float tt = __fdividef(u64_to_float(r2i - c.rl2_fix) * c.s2winv, r + c.rlf);
             gt -= (Ai + Aj) * 4.0f * tt * (1.0f - tt * tt) * c.winvf;
         }
         gr += gt * rinv;
@@ -1264,7 +1264,7 @@ __device__ __forceinline__ void count_row(const typename M::pos_t& pi, Walk&& wa
         ds = domega_d(acc, c.fd, c.fd + 1.0);
         n_val = acc;
     } else {
-        long long full = 0;
+        int full = 0;  // a row holds at most MAX_CAP (4096) entries
         unsigned long long q = 0;
         walk([&](int m) {
             const unsigned long long r2 = r2_fix(pi, fetch(m));
@@ -1275,7 +1275,7 @@ __device__ __forceinline__ void count_row(const typename M::pos_t& pi, Walk&& wa
         });
         full = group_sum(full, width);
         q = group_sum(q, width);
-        const long long Tf = (full - c.fd_int) * 2147483648LL + (long long)q - c.fd_frac_fix;
+        const long long Tf = ((long long)full - c.fd_int) * 2147483648LL + (long long)q - c.fd_frac_fix;
         switch_from_fix(Tf, s, ds);
         n_val = 0.0;
         if (want_n) n_val = (double)full + (double)q * 4.656612873077393e-10;
@@ -1383,8 +1383,8 @@ __device__ __forceinline__ typename M::real chain_row(const typename M::pos_t& p
             const unsigned long long r2i = r2_fix(pi, pj);
             if (r2i > c.rr2_fix && r2i < c.ra2_fix) {
                 const float r2 = u64_to_float(r2i) * g.s32sq;
-                const float r = sqrtf(r2);
-                const float uu = s64_to_float((long long)r2i - (long long)c.rm2_fix) * c.s2hinv / (r + c.rmf);
+                const float r = r2 * rsqrtf(r2);
+                const float uu = __fdividef(s64_to_float((long long)r2i - (long long)c.rm2_fix) * c.s2hinv, r + c.rmf);
                 const float q = 1.0f - uu * uu;
                 acc += get_s(pj) * (-c.Eaf * q * q);
             }
