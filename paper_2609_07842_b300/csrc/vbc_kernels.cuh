@@ -536,6 +536,39 @@ __host__ __device__ inline ForceLayout force_layout(const SuperCaps& cp, size_t 
     return l;
 }
 
+// Shifts the 192-bit value (a2:a1:a0) right by s bits (left by -s when s < 0),
+// |s| < 192; the close-list assembly of k_nlist.
+__device__ __forceinline__ void shift192(unsigned long long& a0, unsigned long long& a1, unsigned long long& a2,
+                                         int s)
+{
+    if (s >= 0) {
+        while (s >= 64) {
+            a0 = a1;
+            a1 = a2;
+            a2 = 0ull;
+            s -= 64;
+        }
+        if (s) {
+            a0 = (a0 >> s) | (a1 << (64 - s));
+            a1 = (a1 >> s) | (a2 << (64 - s));
+            a2 >>= s;
+        }
+    } else {
+        s = -s;
+        while (s >= 64) {
+            a2 = a1;
+            a1 = a0;
+            a0 = 0ull;
+            s -= 64;
+        }
+        if (s) {
+            a2 = (a2 << s) | (a1 >> (64 - s));
+            a1 = (a1 << s) | (a0 >> (64 - s));
+            a0 <<= s;
+        }
+    }
+}
+
 // ================================================================ rebuild: lists
 // One block per cell group: stage the surrounding cells, then each thread
 // takes own particles and scans the 9 contiguous x rows of their 27-cell
@@ -615,8 +648,11 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
         const spos_t pi = spos[mself];
         uint16_t* row = scratch + (size_t)p * cp.cap;
         int nn = 0, nf = 0;
-        // far entries within r_l, in scan order, go to the close list's slots for now
-        int* cv = aux.close + (size_t)CLOSE_K * p;
+        // close entries, as staging indices in registers until the end: the first
+        // CLOSE_K near ones (the row's first three 4-entry words) and, in scan order,
+        // up to CLOSE_K far ones within r_l (shifted in from the top of a 192-bit value)
+        unsigned long long nw0 = 0ull, nw1 = 0ull, nw2 = 0ull;
+        unsigned long long fw0 = 0ull, fw1 = 0ull, fw2 = 0ull;
         int nfc = 0;
         unsigned long long bufn = 0ull, buff = 0ull;  // up to 4 pending near / far entries
 #pragma unroll 1
@@ -673,7 +709,12 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
                     const int hb = 31 - __clz(mnear);
                     mnear ^= 1u << hb;
                     bufn = (bufn >> 16) | ((unsigned long long)(top - hb) << 48);
-                    if ((++nn & 3) == 0 && nn + nf <= cp.cap) *reinterpret_cast<unsigned long long*>(row + nn - 4) = bufn;
+                    if ((++nn & 3) == 0) {
+                        if (nn + nf <= cp.cap) *reinterpret_cast<unsigned long long*>(row + nn - 4) = bufn;
+                        nw0 = nn == 4 ? bufn : nw0;
+                        nw1 = nn == 8 ? bufn : nw1;
+                        nw2 = nn == 12 ? bufn : nw2;
+                    }
                 }
                 while (mfar) {
                     const int hb = 31 - __clz(mfar);
@@ -685,7 +726,10 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
                 while (mfc && nfc < CLOSE_K) {
                     const int hb = 31 - __clz(mfc);
                     mfc ^= 1u << hb;
-                    cv[nfc++] = top - hb;
+                    fw0 = (fw0 >> 16) | (fw1 << 48);
+                    fw1 = (fw1 >> 16) | (fw2 << 48);
+                    fw2 = (fw2 >> 16) | ((unsigned long long)(top - hb) << 48);
+                    ++nfc;
                 }
             }
         }
@@ -705,9 +749,23 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
             // with more near entries takes the list-walking force path)
             const int kn = min(nn, min(CLOSE_K, cp.cap));
             const int kf = min(nfc, CLOSE_K - kn);
-            for (int k = kf - 1; k >= 0; --k) cv[kn + k] = ssidx[cv[k]];
-            for (int k = 0; k < kn; ++k) cv[k] = ssidx[row[k]];
-            for (int k = kn + kf; k < CLOSE_K; ++k) cv[k] = -1;
+            if (nn < CLOSE_K) {
+                // the near word in progress: its (nn & 3) entries sit at the top of bufn
+                const unsigned long long part = (nn & 3) ? bufn >> (16 * (4 - (nn & 3))) : 0ull;
+                nw0 = (nn >> 2) == 0 ? part : nw0;
+                nw1 = (nn >> 2) == 1 ? part : nw1;
+                nw2 = (nn >> 2) == 2 ? part : nw2;
+            }
+            // far entry i sits at bit 192 - 16 nfc + 16 i; move it to slot kn + i
+            shift192(fw0, fw1, fw2, 16 * (CLOSE_K - nfc - kn));
+            const unsigned long long w[3] = {nw0 | fw0, nw1 | fw1, nw2 | fw2};
+            int o[CLOSE_K];
+#pragma unroll
+            for (int k = 0; k < CLOSE_K; ++k)
+                o[k] = k < kn + kf ? ssidx[(int)((w[k >> 2] >> (16 * (k & 3))) & 0xffffull)] : -1;
+            int4* cvo = reinterpret_cast<int4*>(aux.close) + (CLOSE_K / 4) * (size_t)p;
+#pragma unroll
+            for (int k = 0; k < CLOSE_K / 4; ++k) cvo[k] = make_int4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
         }
         roff[j] = pad4(len);
         rself[j] = mself;
@@ -764,18 +822,29 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
                 else hi = mid - 1;
             }
         }
-        for (int c = c0; c < c1; ++c) {
-            while (4 * c >= roff[j + 1]) ++j;
-            const int w = rnn[j], nn = w & 0xffff, len = nn + (w >> 16);
-            const uint16_t* row = scratch + (size_t)(p0 + j) * cp.cap;
-            const uint32_t self = (uint32_t)rself[j];
-            uint32_t h[4];
+        // two chunks per round, so that their eight scratch loads are in flight together
+        const auto fetch = [&](int c, int jc, uint32_t h[4]) {
+            const int w = rnn[jc], nn = w & 0xffff, len = nn + (w >> 16);
+            const uint16_t* row = scratch + (size_t)(p0 + jc) * cp.cap;
+            const uint32_t self = (uint32_t)rself[jc];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int e = 4 * c - roff[j] + u;
+                const int e = 4 * c - roff[jc] + u;
                 h[u] = e < nn ? row[e] : (e < len ? row[cp.cap - 1 - (e - nn)] : self);
             }
+        };
+        for (int c = c0; c < c1; c += 2) {
+            while (4 * c >= roff[j + 1]) ++j;
+            const bool two = c + 1 < c1;
+            int j2 = j;
+            if (two)
+                while (4 * (c + 1) >= roff[j2 + 1]) ++j2;
+            uint32_t h[4], h2[4];
+            fetch(c, j, h);
+            if (two) fetch(c + 1, j2, h2);
             out[c] = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+            if (two) out[c + 1] = make_uint2(h2[0] | (h2[1] << 16), h2[2] | (h2[3] << 16));
+            j = j2;
         }
     }
 }
