@@ -121,11 +121,12 @@ struct vbc_system {
     int* stage_idx = nullptr;   // [nsc][smax] sorted index of each staged particle (list build)
     int2* gmeta = nullptr;      // [nsc] staged particles and padded list entries per group
     int* roff_g = nullptr;      // [n] row offset of each particle in its group's segment
-    int* close_k = nullptr;     // [n][CLOSE_K] near entries as sorted indices (count, soft-core force)
+    uint16_t* close_k = nullptr;  // [n][CLOSE_K] close entries as staging indices (count, soft-core force)
     void* fcore = nullptr;      // [n] forces and tags, float4 or F64x4 (k_count_near, k_force_rows -> k_step)
     int* glist = nullptr;       // [n] particles whose force k_force_rows forms
     int sms = 148;              // SMs of the device
     int row_grid = 1;           // blocks of the row walks (count rows, chain-rule pass, force rows)
+    int near_grid = 1;          // blocks of k_count_near
     long long grows = 0;        // capacity growths after an overflow
     uint4* wtab = nullptr;      // [WTAB_PIECES + 1] window-weight pieces of the counts (window_weight_tab)
     unsigned long long* obs = nullptr;  // [2 + ZHIST] sums of k_observe
@@ -174,6 +175,7 @@ struct vbc_system {
     size_t smem_energy() const { return pass_layout(caps(), pos_bytes(), sizeof(double2)).total; }
     size_t smem_store() const { return al16((size_t)(omax + 1) * 4); }
     size_t smem_rows(size_t extra) const { return dense_layout(caps(), pos_bytes(), extra).total; }
+    size_t smem_near() const { return (size_t)smax * pos_bytes(); }
 };
 
 namespace {
@@ -488,6 +490,10 @@ int configure_smem(vbc_system* s)
     resident((const void*)k_chain<M>, s->smem_rows(0));
     resident((const void*)k_force_rows<M>, s->smem_rows(s->real_bytes()));
     s->row_grid = std::max(1, std::min(s->nsc, occ * s->sms));
+    VBC_TRY(set_smem(k_count_near<M>, s->smem_near()));
+    occ = 1 << 30;
+    resident((const void*)k_count_near<M>, s->smem_near());
+    s->near_grid = std::max(1, std::min(s->nsc, occ * s->sms));
     return VBC_OK;
 }
 
@@ -535,9 +541,9 @@ int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window)
     CountOut out{n_out, want_window ? s->win : nullptr};
     {
         Timed t(s, VBC_K_COUNT);
-        k_count_near<M><<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>((int)s->n, s->geom, s->coef, pos, s->aux(),
-                                                                       s->nnb, (real*)s->ds, (real2*)s->sA, out,
-                                                                       s->ulist, s->st);
+        k_count_near<M><<<s->near_grid, SC_TPB, s->smem_near(), s->stream>>>(
+            s->nsc, s->geom, s->coef, pos, s->grid(), s->caps(), s->aux(), s->nnb, (real*)s->ds, (real2*)s->sA, out,
+            s->ulist, s->st);
         k_count_rows<M><<<s->row_grid, SC_TPB, s->smem_rows(0), s->stream>>>(
             (int)s->n, s->nsc, s->geom, s->coef, pos, s->grid(), s->caps(), s->aux(), s->nbr, s->nnb, s->id, (real*)s->ds,
             (real2*)s->sA, out, s->ulist, s->wpart, s->st);
@@ -662,7 +668,7 @@ long long device_bytes_of(long long n, int prec, const Sizes& z)
     b += (long long)blocks_for(s->npad, SCAN_CHUNK) * 4;
     b += (long long)s->nsc * s->smax * 4;                 // stage_idx
     b += (long long)s->nsc * (8 + 16 + 8);                // gmeta, partial, ppairs
-    b += (long long)CLOSE_K * n * 4;                      // close_k
+    b += (long long)CLOSE_K * n * 2;                      // close_k
     b += n * (prec == VBC_FP64 ? 32 : 16);                // fcore
     b += 3 * n * rb;                                      // ds, sA
     b += n * (8 + 16);                                    // e_sd, e_A

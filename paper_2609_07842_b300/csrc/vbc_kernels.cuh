@@ -284,12 +284,13 @@ struct SuperCaps {
 };
 
 // Tables the list build leaves for the passes.
-constexpr int CLOSE_K = 12;  // close entries kept per particle as sorted indices
+constexpr int CLOSE_K = 12;          // close entries kept per particle, as staging indices of its group
+constexpr int CLOSE_NONE = 0xffff;   // an empty close-list slot
 struct GroupAux {
     int* stage_idx;  // [groups][smax] sorted index of each staged particle
     int2* meta;      // [groups] (staged particles, padded list entries)
     int* roff;       // [n] start of each particle's row in nbr (group * seg + offset in its segment)
-    int* close;      // [n][CLOSE_K] sorted indices of close entries (near, then far within r_l), -1 for none
+    uint16_t* close; // [n][CLOSE_K] staging indices of close entries (near, then far within r_l), CLOSE_NONE for none
     void* fcore;     // [n] force and tag, float4 (FP32 mode) or F64x4 (w = 1: the particle's whole force)
     int* glist;      // [n] particles whose force the list-walking pass forms (k_count_near, k_chain)
 };
@@ -489,13 +490,12 @@ struct ListTestRel {
 __host__ __device__ constexpr size_t al16(size_t v) { return (v + 15) & ~(size_t)15; }
 
 struct NlistLayout {
-    size_t sidx, roff, rnn, rself, total;
+    size_t roff, rnn, rself, total;
 };
 __host__ __device__ inline NlistLayout nlist_layout(const SuperCaps& cp, size_t pos_bytes)
 {
     NlistLayout l{};
-    l.sidx = al16((size_t)cp.smax * pos_bytes);
-    l.roff = l.sidx + al16((size_t)cp.smax * 4);
+    l.roff = al16((size_t)cp.smax * pos_bytes);
     l.rnn = l.roff + al16((size_t)(cp.omax + 1) * 4);
     l.rself = l.rnn + al16((size_t)cp.omax * 4);
     l.total = l.rself + al16((size_t)cp.omax * 4);
@@ -607,7 +607,6 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
     }
     const NlistLayout ly = nlist_layout(cp, sizeof(spos_t));
     spos_t* spos = (spos_t*)smem;
-    int* ssidx = (int*)(smem + ly.sidx);  // sorted index of each staged particle
     int* roff = (int*)(smem + ly.roff);
     int* rnn = (int*)(smem + ly.rnn);
     int* rself = (int*)(smem + ly.rself);  // own staging index of each own particle
@@ -631,9 +630,7 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
     {
         int* sidx = aux.stage_idx + (size_t)blockIdx.x * cp.smax;
         for (int m = t; m < total; m += SC_TPB) {
-            const int jj = staged_index(T, m);
-            sidx[m] = jj;
-            ssidx[m] = jj;
+            sidx[m] = staged_index(T, m);
         }
     }
     __syncthreads();
@@ -758,14 +755,14 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
             }
             // far entry i sits at bit 192 - 16 nfc + 16 i; move it to slot kn + i
             shift192(fw0, fw1, fw2, 16 * (CLOSE_K - nfc - kn));
-            const unsigned long long w[3] = {nw0 | fw0, nw1 | fw1, nw2 | fw2};
-            int o[CLOSE_K];
+            // slots from kn + kf on hold CLOSE_NONE
+            const int used = 16 * (kn + kf);
+            unsigned long long m0 = ~0ull, m1 = ~0ull, m2 = ~0ull;  // ones over the empty slots
+            shift192(m0, m1, m2, -used);
+            uint2* cvo = reinterpret_cast<uint2*>(aux.close) + (CLOSE_K / 4) * (size_t)p;
+            const unsigned long long w[3] = {nw0 | fw0 | m0, nw1 | fw1 | m1, nw2 | fw2 | m2};
 #pragma unroll
-            for (int k = 0; k < CLOSE_K; ++k)
-                o[k] = k < kn + kf ? ssidx[(int)((w[k >> 2] >> (16 * (k & 3))) & 0xffffull)] : -1;
-            int4* cvo = reinterpret_cast<int4*>(aux.close) + (CLOSE_K / 4) * (size_t)p;
-#pragma unroll
-            for (int k = 0; k < CLOSE_K / 4; ++k) cvo[k] = make_int4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
+            for (int k = 0; k < CLOSE_K / 4; ++k) cvo[k] = make_uint2((uint32_t)w[k], (uint32_t)(w[k] >> 32));
         }
         roff[j] = pad4(len);
         rself[j] = mself;
@@ -1126,6 +1123,22 @@ struct __align__(32) F64x4 {
     double x, y, z, w;
 };
 
+// Copies a group's staged particles: put(m, j) for staging index m and sorted
+// index j, four loads of the index table in flight per thread.
+template <class Put>
+__device__ __forceinline__ void stage_by_table(const int* __restrict__ sidx, int total, Put&& put)
+{
+    constexpr int B = 4;
+    for (int m0 = threadIdx.x; m0 < total; m0 += SC_TPB * B) {
+        int jj[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) jj[u] = m0 + u * SC_TPB < total ? __ldg(sidx + m0 + u * SC_TPB) : -1;
+#pragma unroll
+        for (int u = 0; u < B; ++u)
+            if (jj[u] >= 0) put(m0 + u * SC_TPB, jj[u]);
+    }
+}
+
 // k_count_near also forms, in the FP32 mode, the soft-core force of its
 // particle from the same close neighbours.  Every pair inside the soft core
 // is a near entry, so for a particle whose near entries all fit the close
@@ -1135,75 +1148,79 @@ struct __align__(32) F64x4 {
 // the tag of every list neighbour of a window particle.  Every other particle
 // goes on the list of k_force_rows.
 template <class M>
-__global__ void __launch_bounds__(TPB) k_count_near(int n, Geom g, Coef c, typename M::pos_t* __restrict__ pos,
-                                                    GroupAux aux, const int* __restrict__ nnb,
-                                                    typename M::real* __restrict__ ds_out,
-                                                    typename M::real2* __restrict__ sA, CountOut out,
-                                                    int* __restrict__ ulist, Status* st)
+__global__ void __launch_bounds__(SC_TPB) k_count_near(int ngroups, Geom g, Coef c, typename M::pos_t* __restrict__ pos,
+                                                       SuperGrid G, SuperCaps cp, GroupAux aux,
+                                                       const int* __restrict__ nnb, typename M::real* __restrict__ ds_out,
+                                                       typename M::real2* __restrict__ sA, CountOut out,
+                                                       int* __restrict__ ulist, Status* st)
 {
     using pos_t = typename M::pos_t;
     using real = typename M::real;
     using real2 = typename M::real2;
     if (blockIdx.x == 0 && threadIdx.x == 0) st->rebuild = 0;
     if (halted(st)) return;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    long long full = 0;
-    float fx = 0.0f, fy = 0.0f, fz = 0.0f;
-    const int nn = __ldg(nnb + p) & 0xffff;
-    if (!out.n_out) {
-        const pos_t pi = pos[p];
-        const int4* cv = reinterpret_cast<const int4*>(aux.close) + (CLOSE_K / 4) * (size_t)p;
-        int q[CLOSE_K];
+    // the group's neighbourhood, staged once for the close-list gathers of its own particles
+    extern __shared__ __align__(16) unsigned char smem[];
+    pos_t* spos = (pos_t*)smem;
+    for (int b = blockIdx.x; b < ngroups; b += gridDim.x) {
+        __syncthreads();  // the previous group is done with the shared positions
+        const int p0 = __ldg(G.cell_start + OWN_CELLS * b);
+        const int n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
+        if (!out.n_out)
+            stage_by_table(aux.stage_idx + (size_t)b * cp.smax, __ldg(aux.meta + b).x,
+                           [&](int m, int jj) { spos[m] = pos[jj]; });
+        __syncthreads();
+        for (int j = threadIdx.x; j < n_own; j += SC_TPB) {
+            const int p = p0 + j;
+            int full = 0;
+            float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+            const int nn = __ldg(nnb + p) & 0xffff;
+            if (!out.n_out) {
+                const pos_t pi = pos[p];
+                const uint2* cv = reinterpret_cast<const uint2*>(aux.close) + (CLOSE_K / 4) * (size_t)p;
+                int q[CLOSE_K];
 #pragma unroll
-        for (int k = 0; k < CLOSE_K / 4; ++k) {
-            const int4 v = __ldg(cv + k);
-            q[4 * k] = v.x;
-            q[4 * k + 1] = v.y;
-            q[4 * k + 2] = v.z;
-            q[4 * k + 3] = v.w;
-        }
-        pos_t pj[CLOSE_K];
+                for (int k = 0; k < CLOSE_K / 4; ++k) unpack4(__ldg(cv + k), q + 4 * k);
+                // soft core: g / r = K (r^2 - r_r^2), r^2 in units of (L / 2^32)^2
+                const float kc = c.Er4f * c.rr2invf * g.s32sq;
 #pragma unroll
-        for (int k = 0; k < CLOSE_K; ++k)
-            if (q[k] >= 0) pj[k] = pos[q[k]];
-        // soft core: g / r = K (r^2 - r_r^2), r^2 in units of (L / 2^32)^2
-        const float kc = c.Er4f * c.rr2invf * g.s32sq;
-#pragma unroll
-        for (int k = 0; k < CLOSE_K; ++k) {
-            if (q[k] < 0) continue;
-            if constexpr (M::fp64) {
-                full += r2_d<M>(pi, pj[k], g) <= c.rl2;
-            } else {
-                const unsigned long long r2i = r2_fix(pi, pj[k]);
-                full += r2i <= c.rl2_fix;
-                if (r2i < c.rr2_fix) {
-                    const float dx = (float)(pi.x - pj[k].x), dy = (float)(pi.y - pj[k].y),
-                                dz = (float)(pi.z - pj[k].z);
-                    const float gr = __fmaf_rn(kc, __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz)), -c.Er4f);
-                    fx = __fmaf_rn(-gr, dx, fx);
-                    fy = __fmaf_rn(-gr, dy, fy);
-                    fz = __fmaf_rn(-gr, dz, fz);
+                for (int k = 0; k < CLOSE_K; ++k) {
+                    if (q[k] == CLOSE_NONE) continue;
+                    const pos_t pj = spos[q[k]];
+                    if constexpr (M::fp64) {
+                        full += r2_d<M>(pi, pj, g) <= c.rl2;
+                    } else {
+                        const unsigned long long r2i = r2_fix(pi, pj);
+                        full += r2i <= c.rl2_fix;
+                        if (r2i < c.rr2_fix) {
+                            const float dx = (float)(pi.x - pj.x), dy = (float)(pi.y - pj.y), dz = (float)(pi.z - pj.z);
+                            const float gr = __fmaf_rn(kc, __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz)), -c.Er4f);
+                            fx = __fmaf_rn(-gr, dx, fx);
+                            fy = __fmaf_rn(-gr, dy, fy);
+                            fz = __fmaf_rn(-gr, dz, fz);
+                        }
+                    }
                 }
             }
+            const bool sat = !out.n_out && full >= c.sat_full;
+            if (sat) {
+                ds_out[p] = (real)0;
+                sA[p] = real2{(real)0, (real)0};
+                put_w(pos + p, (real)0);
+            } else {
+                ds_out[p] = (real)NAN;  // marks the particle for k_count_rows
+                ulist[atomicAdd(&st->nu, 1)] = p;
+            }
+            const bool whole = !M::fp64 && sat && nn <= CLOSE_K;
+            if constexpr (M::fp64) {
+                static_cast<F64x4*>(aux.fcore)[p] = F64x4{0.0, 0.0, 0.0, 0.0};
+            } else {
+                static_cast<float4*>(aux.fcore)[p] =
+                    make_float4(fx * g.s32, fy * g.s32, fz * g.s32, whole ? 1.0f : 0.0f);
+            }
+            if (!whole) aux.glist[atomicAdd(&st->ngen, 1)] = p;
         }
     }
-    const bool sat = !out.n_out && full >= c.sat_full;
-    if (sat) {
-        ds_out[p] = (real)0;
-        sA[p] = real2{(real)0, (real)0};
-        put_w(pos + p, (real)0);
-    } else {
-        ds_out[p] = (real)NAN;  // marks the particle for k_count_rows
-        ulist[atomicAdd(&st->nu, 1)] = p;
-    }
-    const bool whole = !M::fp64 && sat && nn <= CLOSE_K;
-    if constexpr (M::fp64) {
-        static_cast<F64x4*>(aux.fcore)[p] = F64x4{0.0, 0.0, 0.0, 0.0};
-    } else {
-        static_cast<float4*>(aux.fcore)[p] = make_float4(fx * g.s32, fy * g.s32, fz * g.s32, whole ? 1.0f : 0.0f);
-    }
-    if (!whole) aux.glist[atomicAdd(&st->ngen, 1)] = p;
 }
 
 // ================================================================ row walks
@@ -1273,21 +1290,6 @@ __host__ __device__ inline DenseLayout dense_layout(const SuperCaps& cp, size_t 
     return l;
 }
 
-// Copies a group's staged particles: put(m, j) for staging index m and sorted
-// index j, four loads of the index table in flight per thread.
-template <class Put>
-__device__ __forceinline__ void stage_by_table(const int* __restrict__ sidx, int total, Put&& put)
-{
-    constexpr int B = 4;
-    for (int m0 = threadIdx.x; m0 < total; m0 += SC_TPB * B) {
-        int jj[B];
-#pragma unroll
-        for (int u = 0; u < B; ++u) jj[u] = m0 + u * SC_TPB < total ? __ldg(sidx + m0 + u * SC_TPB) : -1;
-#pragma unroll
-        for (int u = 0; u < B; ++u)
-            if (jj[u] >= 0) put(m0 + u * SC_TPB, jj[u]);
-    }
-}
 
 // Lists the own particles of group b that pick(j) selects (j from 0); the
 // whole block calls it.  Returns their number.
