@@ -83,6 +83,24 @@ def workload(args):
     }
 
 
+def max_over_ranks(v, world, device="cuda"):
+    """The largest v over the ranks (the slowest rank's time): an all-reduce MAX,
+    over NCCL on the GPU machine or gloo on the CPU.  v itself when world is 1."""
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(steps, seconds, world):
+    """Timesteps per second of all replicas together: every rank advances its own
+    system (weak scaling), timed by the slowest rank."""
+    return steps * world / seconds
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -407,10 +425,7 @@ def main():
     sys_.profile(False)
     build_ms = b_ms / max(b_n, 1)
 
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
 
     # pair interactions (unordered pairs with r < r_c) at the end configuration
     r = sys_.compute(energy=True)
@@ -422,7 +437,7 @@ def main():
     rebuild_every = args.steps / rebuilds if rebuilds > 0 else float("inf")
     phi = st2.in_window / args.n
 
-    steps_per_s = args.steps / (ms / 1e3) * world
+    steps_per_s = whole_job_rate(args.steps, ms / 1e3, world)
     peak, peak_kind = hbm_peak()
     cb = class_bytes_per_particle(k_mean, phi)
     # per-launch duration of each class; the rebuild class from forced builds
@@ -462,12 +477,9 @@ def main():
             done += c
         barrier()
         e2e_s = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, world)
         nchunks = -(-args.steps // chunk)
-        e2e = {"value": args.steps / e2e_s * world, "unit": UNIT,
+        e2e = {"value": whole_job_rate(args.steps, e2e_s, world), "unit": UNIT,
                "h2d_bytes_per_step": int(48 * args.n * nchunks / args.steps),
                "d2h_bytes_per_step": int(48 * args.n * nchunks / args.steps),
                "chunk_steps": chunk}

@@ -48,7 +48,8 @@ enum {
     VBC_ERR_OOM = -3,           /* device allocation failed */
     VBC_ERR_NLIST_OVERFLOW = -4,/* neighbour list still overflows after growing to its limit */
     VBC_ERR_UNSTABLE = -5,      /* non-finite position or velocity produced */
-    VBC_ERR_TIMEOUT = -6        /* a wait ended before the awaited work (serving) */
+    VBC_ERR_TIMEOUT = -6,       /* a wait ended before the awaited work (serving) */
+    VBC_ERR_CANCELLED = -7      /* a served request was dropped or stopped by vbc_server_destroy */
 };
 
 /* Precision of the pair arithmetic. */
@@ -324,9 +325,9 @@ int vbc_server_info(vbc_server* srv, int64_t id, vbc_request_info* info);
  * copied, and the request is forgotten all the same). */
 int vbc_server_result(vbc_server* srv, int64_t id, double* pos, double* vel, vbc_request_info* info);
 
-/* Stop the server: queued requests are dropped, running ones finish their
- * current chunk and stop, the slot threads end, and everything is released.
- * NULL-safe. */
+/* Stop the server: queued requests are dropped and running ones stop after
+ * their current chunk (both end with status VBC_ERR_CANCELLED), the slot
+ * threads end, and everything is released.  NULL-safe. */
 void vbc_server_destroy(vbc_server* srv);
 
 /* Message of the last failed vbc_server_* call on this thread (a request's own

@@ -148,7 +148,10 @@ void vbc_server::slot_main()
         {
             std::lock_guard<std::mutex> lock(mu);
             reserved -= r->info.device_bytes;
-            if (rc == VBC_OK && r->info.steps_done < r->nsteps) rc = VBC_ERR_INVALID_ARG;  // stopped early
+            if (rc == VBC_OK && r->info.steps_done < r->nsteps) {  // stopped by vbc_server_destroy
+                rc = VBC_ERR_CANCELLED;
+                r->error = "stopped: the server was destroyed";
+            }
             r->info.t_done = now();
             r->info.status = rc;
         }
@@ -280,8 +283,8 @@ void vbc_server_destroy(vbc_server* srv)
         std::lock_guard<std::mutex> lock(srv->mu);
         srv->stop = true;
         for (auto& r : srv->queue) {
-            r->info.status = VBC_ERR_INVALID_ARG;
-            r->error = "dropped: the server stopped";
+            r->info.status = VBC_ERR_CANCELLED;
+            r->error = "dropped: the server was destroyed";
         }
         srv->queue.clear();
     }

@@ -24,6 +24,7 @@ VBC_ERR_OOM = -3
 VBC_ERR_NLIST_OVERFLOW = -4
 VBC_ERR_UNSTABLE = -5
 VBC_ERR_TIMEOUT = -6
+VBC_ERR_CANCELLED = -7
 VBC_REQ_QUEUED = 1
 VBC_REQ_RUNNING = 2
 VBC_FP32_SPLIT = 0
