@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--served-requests", type=int, default=24)
     ap.add_argument("--served-steps", type=int, default=50_000, help="Langevin steps per served request")
     ap.add_argument("--served-slots", type=int, default=16)
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched leg (many uneven systems)")
+    ap.add_argument("--batched-systems", type=int, default=256)
+    ap.add_argument("--batched-steps", type=int, default=1000)
     ap.add_argument("--sweep", action="store_true",
                     help="cost-vs-valency curve (N=100k, rho 0.5, E_a 8, v in 1,2,4,6,8) and the paper-shape "
                          "point (N=10k, rho 0.05, E_a 2, dt 0.01, gamma 0.1, f = 1..6); one JSON line each")
@@ -347,6 +350,59 @@ def sweep(args):
                           "precision": "FP32 split", "data": "synthetic"}), flush=True)
 
 
+def batched_systems(args):
+    """Uneven independent systems: N log-uniform in [2k, 64k], valency uniform in
+    {1, ..., 6}, kT uniform in [0.8, 1.5], density uniform in [0.2, 0.6] (seeded)."""
+    rng = np.random.default_rng(40960)
+    k = args.batched_systems
+    n = np.exp(rng.uniform(np.log(2000), np.log(64_000), k)).astype(int)
+    v = rng.integers(1, 7, k)
+    kt = rng.uniform(0.8, 1.5, k)
+    rho = rng.uniform(0.2, 0.6, k)
+    return [(int(n[i]), float(rho[i]), float(v[i]), float(kt[i]), 500 + i) for i in range(k)]
+
+
+def run_batched(args):
+    """The uneven systems advanced by args.batched_steps steps, once with one
+    vbc_batch_step (one graph launch per two steps for all of them) and once one
+    system after another (vbc_step_langevin each, its own graphs), after an
+    untimed equilibration; aggregate timesteps/s of each (CUDA events)."""
+    import torch
+    from paper_2609_07842_b300 import inputs, vbc
+    cfg = batched_systems(args)
+    systems = []
+    for n, rho, v, kt, seed in cfg:
+        pos, L = inputs.uniform_positions(n, rho, seed=seed)
+        vel = inputs.maxwell_velocities(n, kt, seed=seed + 1)
+        systems.append(vbc.System(pos, L, vbc.params(E_a=args.E_a, f=v), vel=vel, skin=SKIN, seed=seed))
+    kts = [c[3] for c in cfg]
+    out = {}
+    try:
+        with vbc.Batch(systems) as b:
+            b.step(200, DT, kts, GAMMA)                  # equilibration, untimed
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            b.step(args.batched_steps, DT, kts, GAMMA)
+            torch.cuda.synchronize()
+            t_batch = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for s, kt in zip(systems, kts):
+            s.step(args.batched_steps, DT, kt, GAMMA)
+        torch.cuda.synchronize()
+        t_one = time.perf_counter() - t0
+        nsys, ntot = len(systems), sum(c[0] for c in cfg)
+        for name, t in (("batched", t_batch), ("one_at_a_time", t_one)):
+            out[name] = {"seconds": t, "timesteps_per_s": nsys * args.batched_steps / t,
+                         "particle_steps_per_s": ntot * args.batched_steps / t}
+        out["speedup"] = t_one / t_batch
+        out["workload"] = (f"{nsys} systems, N log-uniform in [2k, 64k] ({ntot:,} particles), valency 1..6, "
+                           f"kT 0.8..1.5, rho 0.2..0.6, E_a {args.E_a}, {args.batched_steps} steps each after 200")
+    finally:
+        for s in systems:
+            s.close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -496,6 +552,11 @@ def main():
                   **mix, "one_at_a_time": one,
                   "speedup_vs_one_at_a_time": mix["timesteps_per_s"] / one["timesteps_per_s"]}
 
+    # ---- batched: many uneven systems in one graph against one at a time (rank 0, N = 1 only)
+    batched = None
+    if rank == 0 and world == 1 and not args.no_batched:
+        batched = run_batched(args)
+
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -543,6 +604,7 @@ def main():
             "clocks": clk,
             "e2e": e2e,
             "served": served,
+            "batched": batched,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -237,6 +237,32 @@ void vbc_destroy(vbc_system* sys);
 /* Message describing the last error of the calling thread ("" if none). */
 const char* vbc_last_error(void);
 
+/* ------------------------------------------------------------------ batched stepping
+ * Many independent systems of uneven size (parameter sweeps, Sec. 5) advanced
+ * together on one GPU.  vbc_batch_step runs each system's Langevin iterations
+ * exactly as vbc_step_langevin does; the systems' two-step graphs are
+ * captured side by side into one CUDA graph, so that one graph launch
+ * advances every system by two steps and the small systems' kernels fill the
+ * GPU together.  The first and last iterations run on each system's own
+ * stream, and a system whose neighbour list overflows is grown and finishes
+ * its iterations on its own.  The results are bitwise those of stepping each
+ * system alone.  The systems stay owned by the caller and must outlive the
+ * batch; they must share one device and appear once each. */
+typedef struct vbc_batch vbc_batch;
+
+/* Errors: INVALID_ARG (NULL or repeated systems, count < 1, systems on
+ * different devices), CUDA. */
+int vbc_batch_create(vbc_system* const* systems, int32_t count, vbc_batch** out);
+
+/* Advance every system of the batch by nsteps steps, as vbc_step_langevin
+ * does, system k at temperature kT[k] ([count] host array); dt and gamma are
+ * shared.  Returns the first error of any system; the others are advanced all
+ * the same. */
+int vbc_batch_step(vbc_batch* batch, int64_t nsteps, double dt, const double* kT, double gamma);
+
+/* Release the batch (not its systems).  NULL-safe. */
+void vbc_batch_destroy(vbc_batch* batch);
+
 /* ------------------------------------------------------------------ observables
  * Valency observables of Sec. 3 on the current state: two particles are
  * neighbours when r_ij < r_a (strict; an instantaneous distance criterion, so

@@ -178,6 +178,20 @@ struct vbc_system {
     size_t smem_near() const { return (size_t)smax * pos_bytes(); }
 };
 
+// Systems stepped together: their pair iterations captured side by side
+// into one graph (vbc_batch_step).
+struct vbc_batch {
+    std::vector<vbc_system*> sys;
+    int device = 0;
+    cudaStream_t stream = nullptr;       // the batch graph's launches
+    cudaEvent_t join = nullptr;          // end of the batch graph's launches
+    std::vector<cudaEvent_t> ready;      // each system's iteration 0 done
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int> cur;                // position buffer of each system the graph was captured for
+    std::vector<long long> layout;
+    std::vector<double> dt, c1, c2;      // the step coefficients it was captured with
+};
+
 namespace {
 
 // ------------------------------------------------------------------ timing helpers
@@ -819,25 +833,18 @@ int graph_error(vbc_system* s, const char* what, cudaError_t e)
 // one executable graph.  Each iteration is: k_gate -> IF(rebuild due){the
 // nine rebuild kernels} -> count -> chain -> force, so steps that need no
 // rebuild launch no rebuild kernel at all.
+// Captures the two iterations into graph g, as nodes that depend on no
+// other node of g (so the iterations of several systems captured into one
+// graph run side by side).
 template <class M>
-int build_pair_graph(vbc_system* s, int c, const StepArgs& a)
+int capture_pair(vbc_system* s, int c, const StepArgs& a, cudaGraph_t g)
 {
-    auto& pg = s->pair_graph[c];
-    if (pg.exec) {
-        cudaGraphExecDestroy(pg.exec);
-        pg.exec = nullptr;
-    }
     if (!s->cap_stream) VBC_CUDA(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
     if (!s->body_stream) VBC_CUDA(cudaStreamCreateWithFlags(&s->body_stream, cudaStreamNonBlocking));
-    cudaGraph_t g = nullptr;
-    VBC_CUDA(cudaGraphCreate(&g, 0));
     cudaGraphConditionalHandle h[2];
     for (int k = 0; k < 2; ++k) {
         cudaError_t e = cudaGraphConditionalHandleCreate(&h[k], g, 0, cudaGraphCondAssignDefault);
-        if (e != cudaSuccess) {
-            cudaGraphDestroy(g);
-            return graph_error(s, "cudaGraphConditionalHandleCreate", e);
-        }
+        if (e != cudaSuccess) return graph_error(s, "cudaGraphConditionalHandleCreate", e);
     }
     const int saved_cur = s->cur;
     cudaStream_t saved_stream = s->stream;
@@ -885,8 +892,22 @@ int build_pair_graph(vbc_system* s, int c, const StepArgs& a)
     s->capturing = false;
     s->stream = saved_stream;
     s->cur = saved_cur;
+    return rc;
+}
+
+template <class M>
+int build_pair_graph(vbc_system* s, int c, const StepArgs& a)
+{
+    auto& pg = s->pair_graph[c];
+    if (pg.exec) {
+        cudaGraphExecDestroy(pg.exec);
+        pg.exec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    VBC_CUDA(cudaGraphCreate(&g, 0));
+    int rc = capture_pair<M>(s, c, a, g);
     if (rc == VBC_OK) {
-        e = cudaGraphInstantiate(&pg.exec, g, 0);
+        const cudaError_t e = cudaGraphInstantiate(&pg.exec, g, 0);
         if (e != cudaSuccess) rc = graph_error(s, "cudaGraphInstantiate", e);
     }
     cudaGraphDestroy(g);
@@ -913,8 +934,8 @@ int launch_pair_graph(vbc_system* s, const StepArgs& a)
     return VBC_OK;
 }
 
-template <class M>
-int steps_impl(vbc_system* s, int64_t nsteps, double dt, double kT, double gamma)
+// Coefficients of the Langevin iterations of one call.
+StepArgs step_args(const vbc_system* s, double dt, double kT, double gamma)
 {
     StepArgs a{};
     a.x = s->x;
@@ -928,11 +949,18 @@ int steps_impl(vbc_system* s, int64_t nsteps, double dt, double kT, double gamma
     split_fix(a.c1, a.c1_hi, a.c1_lo);
     a.seed = s->seed;
     a.half_skin2 = (float)(0.25 * s->skin * s->skin);
-    // Iteration 0 opens step 0 (forces at the initial state, then B A O A);
-    // iteration it in [1, nsteps) closes step it-1 and opens step it;
-    // iteration nsteps closes the last step.  Iterations 1..nsteps-1 run in
-    // pairs through a CUDA graph unless per-kernel timing is on.
-    int64_t it0 = 0;
+    return a;
+}
+
+// Iteration 0 opens step 0 (forces at the initial state, then B A O A);
+// iteration it in [1, nsteps) closes step it-1 and opens step it;
+// iteration nsteps closes the last step.  Iterations 1..nsteps-1 run in
+// pairs through a CUDA graph unless per-kernel timing is on.  Runs
+// iterations it0..nsteps; when a list build overflows it grows the
+// capacities and resumes from the overflowing iteration.
+template <class M>
+int run_iterations(vbc_system* s, const StepArgs& a, int64_t it0, int64_t nsteps)
+{
     for (int attempt = 0;; ++attempt) {
         k_set_iter<<<1, 1, 0, s->stream>>>(s->st, it0 - 1, s->step);
         VBC_TRY(check_launch(s));
@@ -949,7 +977,7 @@ int steps_impl(vbc_system* s, int64_t nsteps, double dt, double kT, double gamma
         }
         VBC_TRY(read_status(s));
         VBC_TRY(halt_error(s));
-        if (!needs_growth(s)) break;
+        if (!needs_growth(s)) return VBC_OK;
         if (attempt >= MAX_RETRIES) return fail(VBC_ERR_NLIST_OVERFLOW, "capacities kept overflowing");
         // The build of iteration frozen_iter overflowed: every kernel after it
         // returned at once.  Iterations it0 .. frozen_iter - 1 ran, each
@@ -958,6 +986,44 @@ int steps_impl(vbc_system* s, int64_t nsteps, double dt, double kT, double gamma
         s->cur = cur0 ^ (int)(done & 1);
         it0 = s->st_host->frozen_iter;
         VBC_TRY(grow(s));
+    }
+}
+
+template <class M>
+int steps_impl(vbc_system* s, int64_t nsteps, double dt, double kT, double gamma)
+{
+    VBC_TRY(run_iterations<M>(s, step_args(s, dt, kT, gamma), 0, nsteps));
+    s->step += nsteps;
+    return VBC_OK;
+}
+
+template <class M>
+int batch_iteration0(vbc_system* s, const StepArgs& a, int64_t nsteps)
+{
+    k_set_iter<<<1, 1, 0, s->stream>>>(s->st, -1, s->step);
+    VBC_TRY(check_launch(s));
+    return direct_iteration<M>(s, a, 0, nsteps);
+}
+
+template <class M>
+int batch_tail(vbc_system* s, const StepArgs& a, int64_t it0, int64_t nsteps)
+{
+    for (int64_t it = it0; it <= nsteps; ++it) VBC_TRY(direct_iteration<M>(s, a, it, nsteps));
+    return VBC_OK;
+}
+
+// Status of one system after a batched run; an overflow is grown and the
+// system's remaining iterations rerun on its own, as vbc_step_langevin does.
+template <class M>
+int batch_settle(vbc_system* s, const StepArgs& a, int cur0, int64_t nsteps)
+{
+    VBC_TRY(read_status(s));
+    VBC_TRY(halt_error(s));
+    if (needs_growth(s)) {
+        const int64_t it0 = s->st_host->frozen_iter;
+        s->cur = cur0 ^ (int)(it0 & 1);
+        VBC_TRY(grow(s));
+        VBC_TRY(run_iterations<M>(s, a, it0, nsteps));
     }
     s->step += nsteps;
     return VBC_OK;
@@ -1509,6 +1575,150 @@ int64_t vbc_kernel_launches(vbc_system* s)
 {
     if (!s || check_sys(s) != VBC_OK || read_status(s) != VBC_OK) return -1;
     return s->launches + REBUILD_KERNELS * s->st_host->graph_rebuild_runs;
+}
+
+int vbc_batch_create(vbc_system* const* systems, int32_t count, vbc_batch** out)
+{
+    g_err.clear();
+    if (!systems || !out || count < 1) return fail(VBC_ERR_INVALID_ARG, "need systems, out and count >= 1");
+    *out = nullptr;
+    auto* b = new vbc_batch();
+    for (int32_t k = 0; k < count; ++k) {
+        vbc_system* s = systems[k];
+        if (!s) {
+            delete b;
+            return fail(VBC_ERR_INVALID_ARG, "system %d is NULL", (int)k);
+        }
+        if (std::find(b->sys.begin(), b->sys.end(), s) != b->sys.end()) {
+            delete b;
+            return fail(VBC_ERR_INVALID_ARG, "system %d appears twice", (int)k);
+        }
+        if (k > 0 && s->device != b->device) {
+            delete b;
+            return fail(VBC_ERR_INVALID_ARG, "the systems of a batch must share one device");
+        }
+        b->device = s->device;
+        b->sys.push_back(s);
+    }
+    const auto bail = [&](const char* what, cudaError_t e) {
+        vbc_batch_destroy(b);
+        return fail(VBC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    };
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e != cudaSuccess) return bail("cudaSetDevice", e);
+    if ((e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking)) != cudaSuccess) return bail("cudaStreamCreate", e);
+    if ((e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming)) != cudaSuccess) return bail("cudaEventCreate", e);
+    b->ready.assign(b->sys.size(), nullptr);
+    for (auto& ev : b->ready)
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return bail("cudaEventCreate", e);
+    *out = b;
+    return VBC_OK;
+}
+
+int vbc_batch_step(vbc_batch* b, int64_t nsteps, double dt, const double* kT, double gamma)
+{
+    g_err.clear();
+    if (!b || !kT) return fail(VBC_ERR_INVALID_ARG, "batch handle and kT must not be NULL");
+    if (nsteps < 0) return fail(VBC_ERR_INVALID_ARG, "nsteps must be >= 0");
+    const size_t K = b->sys.size();
+    bool bad = !(dt > 0) || !std::isfinite(dt) || !(gamma >= 0) || !std::isfinite(gamma);
+    for (size_t k = 0; k < K; ++k) bad = bad || !(kT[k] >= 0) || !std::isfinite(kT[k]);
+    if (bad) return fail(VBC_ERR_INVALID_ARG, "need dt > 0, kT >= 0, gamma >= 0 (finite)");
+    if (nsteps == 0) return VBC_OK;
+    bool plain = nsteps < 3;
+    for (vbc_system* s : b->sys) plain = plain || s->prof || !s->use_graphs;
+    if (plain) {
+        for (size_t k = 0; k < K; ++k) VBC_TRY(vbc_step_langevin(b->sys[k], nsteps, dt, kT[k], gamma));
+        return VBC_OK;
+    }
+    VBC_CUDA(cudaSetDevice(b->device));
+    std::vector<StepArgs> args(K);
+    std::vector<int> cur0(K);
+    // iteration 0 of every system on its own stream; the batch stream waits for all
+    for (size_t k = 0; k < K; ++k) {
+        vbc_system* s = b->sys[k];
+        args[k] = step_args(s, dt, kT[k], gamma);
+        cur0[k] = s->cur;
+        VBC_TRY(s->prec == VBC_FP64 ? batch_iteration0<ModeF64>(s, args[k], nsteps)
+                                    : batch_iteration0<ModeF32>(s, args[k], nsteps));
+        VBC_CUDA(cudaEventRecord(b->ready[k], s->stream));
+        VBC_CUDA(cudaStreamWaitEvent(b->stream, b->ready[k], 0));
+    }
+    // iterations 1 .. 2 npairs: one graph launch advances every system by two
+    const int64_t npairs = (nsteps - 1) / 2;
+    if (npairs > 0) {
+        bool stale = !b->exec;
+        for (size_t k = 0; k < K && !stale; ++k)
+            stale = b->cur[k] != b->sys[k]->cur || b->layout[k] != b->sys[k]->layout_version ||
+                    b->dt[k] != args[k].dt || b->c1[k] != args[k].c1 || b->c2[k] != args[k].c2;
+        if (stale) {
+            if (b->exec) {
+                cudaGraphExecDestroy(b->exec);
+                b->exec = nullptr;
+            }
+            cudaGraph_t g = nullptr;
+            VBC_CUDA(cudaGraphCreate(&g, 0));
+            int rc = VBC_OK;
+            for (size_t k = 0; k < K && rc == VBC_OK; ++k) {
+                vbc_system* s = b->sys[k];
+                rc = s->prec == VBC_FP64 ? capture_pair<ModeF64>(s, s->cur, args[k], g)
+                                         : capture_pair<ModeF32>(s, s->cur, args[k], g);
+            }
+            if (rc == VBC_OK) {
+                const cudaError_t e = cudaGraphInstantiate(&b->exec, g, 0);
+                if (e != cudaSuccess) rc = fail(VBC_ERR_CUDA, "cudaGraphInstantiate (batch): %s", cudaGetErrorString(e));
+            }
+            cudaGraphDestroy(g);
+            if (rc != VBC_OK) {
+                b->exec = nullptr;
+                return rc;
+            }
+            b->cur.assign(K, 0);
+            b->layout.assign(K, 0);
+            b->dt.assign(K, 0.0);
+            b->c1.assign(K, 0.0);
+            b->c2.assign(K, 0.0);
+            for (size_t k = 0; k < K; ++k) {
+                b->cur[k] = b->sys[k]->cur;
+                b->layout[k] = b->sys[k]->layout_version;
+                b->dt[k] = args[k].dt;
+                b->c1[k] = args[k].c1;
+                b->c2[k] = args[k].c2;
+            }
+        }
+        for (int64_t q = 0; q < npairs; ++q) VBC_CUDA(cudaGraphLaunch(b->exec, b->stream));
+        for (vbc_system* s : b->sys) s->launches += 12 * npairs;
+    }
+    // the remaining iterations of every system on its own stream, after the graph
+    VBC_CUDA(cudaEventRecord(b->join, b->stream));
+    for (size_t k = 0; k < K; ++k) {
+        vbc_system* s = b->sys[k];
+        VBC_CUDA(cudaStreamWaitEvent(s->stream, b->join, 0));
+        VBC_TRY(s->prec == VBC_FP64 ? batch_tail<ModeF64>(s, args[k], 1 + 2 * npairs, nsteps)
+                                    : batch_tail<ModeF32>(s, args[k], 1 + 2 * npairs, nsteps));
+    }
+    // statuses; a system whose list overflowed finishes on its own
+    int rc = VBC_OK;
+    for (size_t k = 0; k < K; ++k) {
+        vbc_system* s = b->sys[k];
+        const int r = s->prec == VBC_FP64 ? batch_settle<ModeF64>(s, args[k], cur0[k], nsteps)
+                                          : batch_settle<ModeF32>(s, args[k], cur0[k], nsteps);
+        if (rc == VBC_OK) rc = r;
+    }
+    return rc;
+}
+
+void vbc_batch_destroy(vbc_batch* b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (cudaEvent_t ev : b->ready)
+        if (ev) cudaEventDestroy(ev);
+    if (b->join) cudaEventDestroy(b->join);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
 }
 
 }  // extern "C"

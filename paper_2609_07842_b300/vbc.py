@@ -37,6 +37,7 @@ EXPORTS = ("vbc_create_system", "vbc_build_neighbors", "vbc_compute_forces", "vb
            "vbc_step_langevin", "vbc_get_state", "vbc_set_state", "vbc_set_params", "vbc_get_stats",
            "vbc_profile", "vbc_profile_read", "vbc_kernel_launches", "vbc_destroy", "vbc_last_error",
            "vbc_compute_forces_noalloc", "vbc_estimate_device_bytes", "vbc_get_observables",
+           "vbc_batch_create", "vbc_batch_step", "vbc_batch_destroy",
            "vbc_server_create", "vbc_server_submit", "vbc_server_wait", "vbc_server_info",
            "vbc_server_result", "vbc_server_destroy", "vbc_server_last_error")
 
@@ -132,6 +133,12 @@ def load() -> ctypes.CDLL:
     L.vbc_estimate_device_bytes.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(i64)]
     L.vbc_get_observables.argtypes = [vp, ctypes.POINTER(Observables), vp, i32]
     L.vbc_get_observables.restype = i32
+    L.vbc_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, ctypes.POINTER(vp)]
+    L.vbc_batch_create.restype = i32
+    L.vbc_batch_step.argtypes = [vp, i64, dp, ctypes.POINTER(dp), dp]
+    L.vbc_batch_step.restype = i32
+    L.vbc_batch_destroy.argtypes = [vp]
+    L.vbc_batch_destroy.restype = None
     L.vbc_server_create.argtypes = [ctypes.POINTER(_ServerConfig), ctypes.POINTER(vp)]
     L.vbc_server_submit.argtypes = [vp, ctypes.POINTER(_Request), ctypes.POINTER(i64)]
     L.vbc_server_wait.argtypes = [vp, i64, dp, ctypes.POINTER(RequestInfo)]
@@ -435,6 +442,43 @@ class Server:
     def close(self):
         if getattr(self, "_h", None):
             load().vbc_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Systems advanced together (vbc_batch_*): their two-step graphs captured
+    side by side into one CUDA graph; bitwise the same as stepping each alone.
+    The systems must outlive the batch."""
+
+    def __init__(self, systems):
+        self._systems = list(systems)
+        arr = (ctypes.c_void_p * len(self._systems))(*[s._h.value if isinstance(s._h, ctypes.c_void_p) else s._h
+                                                       for s in self._systems])
+        h = ctypes.c_void_p()
+        _check(load().vbc_batch_create(arr, len(self._systems), ctypes.byref(h)))
+        self._h = h
+
+    def step(self, nsteps: int, dt: float, kT, gamma: float):
+        """kT: one temperature for all systems, or one per system."""
+        t = np.broadcast_to(np.asarray(kT, dtype=np.float64), (len(self._systems),)).copy()
+        _check(load().vbc_batch_step(self._h, int(nsteps), dt, t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     gamma))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().vbc_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

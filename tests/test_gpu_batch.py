@@ -1,0 +1,62 @@
+"""Batched stepping (vbc_batch_*): systems of uneven size, valency and
+temperature advanced together, their two-step graphs captured side by side
+into one CUDA graph.  Every system must end bitwise where it ends when stepped
+alone, over runs long enough to rebuild the neighbour lists, for odd and even
+step counts (the last iteration runs outside the graph)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from paper_2609_07842_b300 import inputs, vbc
+
+pytestmark = pytest.mark.gpu
+
+# (n, rho, valency f, kT, seed)
+SYS = [(3000, 0.5, 2.0, 1.0, 21), (12000, 0.3, 4.0, 1.2, 22), (25000, 0.6, 1.0, 0.9, 23), (7000, 0.5, 6.0, 1.1, 24)]
+
+
+def _make(n, rho, f, kT, seed, prec):
+    pos, L = inputs.uniform_positions(n, rho, seed=seed)
+    vel = inputs.maxwell_velocities(n, kT, seed=seed + 1)
+    return vbc.System(pos, L, vbc.params(E_a=8.0, f=f), vel=vel, seed=seed, precision=prec)
+
+
+@pytest.mark.parametrize("prec", [vbc.VBC_FP32_SPLIT, vbc.VBC_FP64])
+def test_batch_equals_each_system_alone(prec):
+    kts = [c[3] for c in SYS]
+    alone = []
+    for c in SYS:
+        with _make(*c, prec) as s:
+            s.step(151, 0.005, c[3], 1.0)
+            s.step(40, 0.005, c[3], 1.0)
+            alone.append(s.get_state()[:2])
+    systems = [_make(*c, prec) for c in SYS]
+    try:
+        with vbc.Batch(systems) as b:
+            b.step(151, 0.005, kts, 1.0)
+            b.step(40, 0.005, kts, 1.0)
+        for s, (pos, vel) in zip(systems, alone):
+            p2, v2, step = s.get_state()
+            assert step == 191
+            np.testing.assert_array_equal(p2, pos)
+            np.testing.assert_array_equal(v2, vel)
+            assert s.stats().rebuilds > 1
+    finally:
+        for s in systems:
+            s.close()
+
+
+def test_batch_rejects_bad_arguments():
+    a = _make(*SYS[0], vbc.VBC_FP32_SPLIT)
+    try:
+        with pytest.raises(vbc.VBCError) as e:
+            vbc.Batch([a, a])
+        assert e.value.code == vbc.VBC_ERR_INVALID_ARG
+        with vbc.Batch([a]) as b:
+            with pytest.raises(vbc.VBCError) as e:
+                b.step(10, -0.1, 1.0, 1.0)
+            assert e.value.code == vbc.VBC_ERR_INVALID_ARG
+            b.step(0, 0.005, 1.0, 1.0)
+    finally:
+        a.close()
