@@ -435,6 +435,8 @@ def main():
 
     # untimed equilibration + warm-up
     sys_.step(args.equil, DT, KT, GAMMA)
+    # grid settings picked by timed trials (changes no result; the trials are further equilibration)
+    tuning = sys_.autotune(trial_steps=100, dt=DT, kT=KT, gamma=GAMMA)
     sys_.step(max(args.warmup, 3), DT, KT, GAMMA)
     st0 = sys_.stats()
 
@@ -603,6 +605,9 @@ def main():
             "gpu_launches": launches,
             "clocks": clk,
             "e2e": e2e,
+            "tuning": {"rows_blocks_per_sm": tuning.rows_blocks_per_sm,
+                       "count_blocks_per_sm": tuning.count_blocks_per_sm,
+                       "trial_ms_per_step": tuning.ms_per_step, "note": "0 = as many blocks as fit"},
             "served": served,
             "batched": batched,
             "cpu_baseline": cpu,

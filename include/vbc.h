@@ -263,6 +263,31 @@ int vbc_batch_step(vbc_batch* batch, int64_t nsteps, double dt, const double* kT
 /* Release the batch (not its systems).  NULL-safe. */
 void vbc_batch_destroy(vbc_batch* batch);
 
+/* ------------------------------------------------------------------ autotuning
+ * The close-neighbour count and the row walks run resident grids, as many
+ * blocks per SM as fit by default.  For small systems (and many systems side
+ * by side, as in batches and serving) fewer blocks can be faster.  These
+ * settings do not change any result: every row and every cell group is
+ * computed the same way whichever block takes it. */
+typedef struct {
+    int32_t rows_blocks_per_sm;   /* the row walks' grid, 0 = as many as fit */
+    int32_t count_blocks_per_sm;  /* the close-neighbour count's grid, 0 = as many as fit */
+    double ms_per_step;           /* the best trial's time per step (vbc_autotune's output) */
+} vbc_tuning;
+
+/* Apply grid settings (for example the result of an earlier vbc_autotune on a
+ * system of the same shape).  ms_per_step is ignored.  Errors: INVALID_ARG. */
+int vbc_set_tuning(vbc_system* s, const vbc_tuning* t);
+
+/* Time trial_steps Langevin steps (dt, kT, gamma as vbc_step_langevin) for
+ * each candidate setting, one knob at a time, keep the fastest and return it
+ * (the default stays unless a setting beats it by 2%).
+ * The trials advance the system (about 10 (trial_steps + 2) steps); since the
+ * settings change no result, its trajectory is bitwise the one it would have
+ * had untuned.  Errors: INVALID_ARG (NULL out, trial_steps < 4), as
+ * vbc_step_langevin otherwise. */
+int vbc_autotune(vbc_system* s, int64_t trial_steps, double dt, double kT, double gamma, vbc_tuning* out);
+
 /* ------------------------------------------------------------------ observables
  * Valency observables of Sec. 3 on the current state: two particles are
  * neighbours when r_ij < r_a (strict; an instantaneous distance criterion, so

@@ -127,6 +127,7 @@ struct vbc_system {
     int sms = 148;              // SMs of the device
     int row_grid = 1;           // blocks of the row walks (count rows, chain-rule pass, force rows)
     int near_grid = 1;          // blocks of k_count_near
+    int rows_bps = 0, near_bps = 0;  // blocks per SM of those grids, 0 = as many as fit (vbc_autotune)
     long long grows = 0;        // capacity growths after an overflow
     uint4* wtab = nullptr;      // [WTAB_PIECES + 1] window-weight pieces of the counts (window_weight_tab)
     unsigned long long* obs = nullptr;  // [2 + ZHIST] sums of k_observe
@@ -503,11 +504,11 @@ int configure_smem(vbc_system* s)
     resident((const void*)k_count_rows<M>, s->smem_rows(0));
     resident((const void*)k_chain<M>, s->smem_rows(0));
     resident((const void*)k_force_rows<M>, s->smem_rows(s->real_bytes()));
-    s->row_grid = std::max(1, std::min(s->nsc, occ * s->sms));
+    s->row_grid = std::max(1, std::min(s->nsc, (s->rows_bps > 0 ? std::min(occ, s->rows_bps) : occ) * s->sms));
     VBC_TRY(set_smem(k_count_near<M>, s->smem_near()));
     occ = 1 << 30;
     resident((const void*)k_count_near<M>, s->smem_near());
-    s->near_grid = std::max(1, std::min(s->nsc, occ * s->sms));
+    s->near_grid = std::max(1, std::min(s->nsc, (s->near_bps > 0 ? std::min(occ, s->near_bps) : occ) * s->sms));
     return VBC_OK;
 }
 
@@ -1719,6 +1720,67 @@ void vbc_batch_destroy(vbc_batch* b)
     if (b->join) cudaEventDestroy(b->join);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;
+}
+
+int vbc_set_tuning(vbc_system* s, const vbc_tuning* t)
+{
+    VBC_TRY(check_sys(s));
+    if (!t || t->rows_blocks_per_sm < 0 || t->count_blocks_per_sm < 0)
+        return fail(VBC_ERR_INVALID_ARG, "tuning must not be NULL and its block counts must be >= 0");
+    VBC_CUDA(cudaStreamSynchronize(s->stream));
+    s->rows_bps = t->rows_blocks_per_sm;
+    s->near_bps = t->count_blocks_per_sm;
+    VBC_TRY(configure(s));
+    s->layout_version += 1;  // the graphs are captured again with the new grids
+    return VBC_OK;
+}
+
+int vbc_autotune(vbc_system* s, int64_t trial_steps, double dt, double kT, double gamma, vbc_tuning* out)
+{
+    VBC_TRY(check_sys(s));
+    if (!out || trial_steps < 4) return fail(VBC_ERR_INVALID_ARG, "need out and trial_steps >= 4");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    VBC_CUDA(cudaEventCreate(&e0));
+    VBC_CUDA(cudaEventCreate(&e1));
+    const auto trial = [&](vbc_tuning t, double& ms) -> int {
+        VBC_TRY(vbc_set_tuning(s, &t));
+        VBC_TRY(vbc_step_langevin(s, 2, dt, kT, gamma));  // captures the graphs for these grids
+        VBC_CUDA(cudaEventRecord(e0, s->stream));
+        VBC_TRY(vbc_step_langevin(s, trial_steps, dt, kT, gamma));
+        VBC_CUDA(cudaEventRecord(e1, s->stream));
+        VBC_CUDA(cudaEventSynchronize(e1));
+        float f = 0.0f;
+        VBC_CUDA(cudaEventElapsedTime(&f, e0, e1));
+        ms = (double)f / (double)trial_steps;
+        return VBC_OK;
+    };
+    // one knob at a time: the row walks' grid, then the close count's
+    static const int cand[] = {0, 8, 4, 2, 1};
+    vbc_tuning best{0, 0, 0.0};
+    double best_ms = 1e300;
+    int rc = VBC_OK;
+    for (int knob = 0; knob < 2 && rc == VBC_OK; ++knob) {
+        for (int c : cand) {
+            vbc_tuning t = best;
+            if (knob == 0) t.rows_blocks_per_sm = c;
+            else t.count_blocks_per_sm = c;
+            double ms = 0.0;
+            if ((rc = trial(t, ms)) != VBC_OK) break;
+            // the default (tried first) is kept unless a setting beats it by 2%: trials that
+            // straddle different numbers of list builds differ by a few percent themselves
+            if (ms < (best_ms == 1e300 ? best_ms : 0.98 * best_ms)) {
+                best_ms = ms;
+                best = t;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    VBC_TRY(rc);
+    best.ms_per_step = best_ms;
+    VBC_TRY(vbc_set_tuning(s, &best));
+    *out = best;
+    return VBC_OK;
 }
 
 }  // extern "C"

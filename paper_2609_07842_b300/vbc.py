@@ -37,7 +37,7 @@ EXPORTS = ("vbc_create_system", "vbc_build_neighbors", "vbc_compute_forces", "vb
            "vbc_step_langevin", "vbc_get_state", "vbc_set_state", "vbc_set_params", "vbc_get_stats",
            "vbc_profile", "vbc_profile_read", "vbc_kernel_launches", "vbc_destroy", "vbc_last_error",
            "vbc_compute_forces_noalloc", "vbc_estimate_device_bytes", "vbc_get_observables",
-           "vbc_batch_create", "vbc_batch_step", "vbc_batch_destroy",
+           "vbc_batch_create", "vbc_batch_step", "vbc_batch_destroy", "vbc_set_tuning", "vbc_autotune",
            "vbc_server_create", "vbc_server_submit", "vbc_server_wait", "vbc_server_info",
            "vbc_server_result", "vbc_server_destroy", "vbc_server_last_error")
 
@@ -64,6 +64,12 @@ class _Config(ctypes.Structure):
 
 
 ZHIST = 32
+
+
+class Tuning(ctypes.Structure):
+    """Grid settings of the close count and the row walks (vbc_autotune)."""
+    _fields_ = [("rows_blocks_per_sm", ctypes.c_int32), ("count_blocks_per_sm", ctypes.c_int32),
+                ("ms_per_step", ctypes.c_double)]
 
 
 class Observables(ctypes.Structure):
@@ -137,6 +143,10 @@ def load() -> ctypes.CDLL:
     L.vbc_batch_create.restype = i32
     L.vbc_batch_step.argtypes = [vp, i64, dp, ctypes.POINTER(dp), dp]
     L.vbc_batch_step.restype = i32
+    L.vbc_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+    L.vbc_set_tuning.restype = i32
+    L.vbc_autotune.argtypes = [vp, i64, dp, dp, dp, ctypes.POINTER(Tuning)]
+    L.vbc_autotune.restype = i32
     L.vbc_batch_destroy.argtypes = [vp]
     L.vbc_batch_destroy.restype = None
     L.vbc_server_create.argtypes = [ctypes.POINTER(_ServerConfig), ctypes.POINTER(vp)]
@@ -319,6 +329,16 @@ class System:
 
     def set_params(self, prm: PairParams):
         _check(load().vbc_set_params(self._h, ctypes.byref(prm)))
+
+    def autotune(self, trial_steps: int = 50, dt: float = 0.005, kT: float = 1.0, gamma: float = 1.0) -> Tuning:
+        """Pick the fastest grid settings by timed trials (vbc_autotune); advances the system."""
+        t = Tuning()
+        _check(load().vbc_autotune(self._h, int(trial_steps), dt, kT, gamma, ctypes.byref(t)))
+        return t
+
+    def set_tuning(self, rows_blocks_per_sm: int = 0, count_blocks_per_sm: int = 0):
+        t = Tuning(rows_blocks_per_sm=rows_blocks_per_sm, count_blocks_per_sm=count_blocks_per_sm)
+        _check(load().vbc_set_tuning(self._h, ctypes.byref(t)))
 
     def observables(self, z: bool = False):
         """(Observables, z_i per particle [n] int32 or None) of the current state."""

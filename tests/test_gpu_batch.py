@@ -60,3 +60,34 @@ def test_batch_rejects_bad_arguments():
             b.step(0, 0.005, 1.0, 1.0)
     finally:
         a.close()
+
+
+# ----------------------------------------------------------------- autotuning
+@pytest.mark.parametrize("prec", [vbc.VBC_FP32_SPLIT, vbc.VBC_FP64])
+def test_grid_settings_change_no_result(prec):
+    """The tunable grids (blocks per SM of the close count and of the row walks)
+    decide only which block takes which cell group or row: a system on the
+    smallest grids ends bitwise where its twin on the default grids ends."""
+    c = SYS[2]
+    a, b = _make(*c, prec), _make(*c, prec)
+    try:
+        b.set_tuning(rows_blocks_per_sm=1, count_blocks_per_sm=1)
+        for s in (a, b):
+            s.step(120, 0.005, c[3], 1.0)
+        pa, va, _ = a.get_state()
+        pb, vb, _ = b.get_state()
+        np.testing.assert_array_equal(pa, pb)
+        np.testing.assert_array_equal(va, vb)
+    finally:
+        a.close()
+        b.close()
+
+
+def test_autotune_picks_a_setting_and_keeps_stepping():
+    c = SYS[1]
+    with _make(*c, vbc.VBC_FP32_SPLIT) as s:
+        t = s.autotune(trial_steps=8, kT=c[3])
+        assert t.rows_blocks_per_sm in (0, 1, 2, 4, 8) and t.count_blocks_per_sm in (0, 1, 2, 4, 8)
+        assert 0.0 < t.ms_per_step < 100.0
+        s.step(20, 0.005, c[3], 1.0)
+        assert s.get_state()[2] > 20
