@@ -346,3 +346,30 @@ def test_full_size_uniform_rho05(n):
     pos, L = inputs.uniform_positions(n, 0.5, seed=3)
     p = with_quantile_valency(pos, L, Params(E_a=8.0), 0.5, mode=1)
     compare(pos, L, p, F32, mode=1, min_window=0.1)
+
+
+@pytest.mark.parametrize("valency", [2.0, 8.0])
+def test_full_size_forces_only_as_benchmarked(valency):
+    """The throughput workload as the benchmark runs it: N = 1M, density 0.5,
+    E_a = 8, forces without counts, so that the close lists settle the saturated
+    particles and the row walks run sparse (valency 2: under 1% unsettled) or dense
+    (valency 8: most particles unsettled or beside a window particle).  Forces,
+    s, s' and A of every particle against the oracle's cell-list mode."""
+    n = 1_000_000
+    pos, L = inputs.uniform_positions(n, 0.5, seed=3)
+    p = Params(E_a=8.0, f=valency)
+    ref = oracle.evaluate(pos, L, p, 1)
+    tol = TOL[F32]
+    with vbc.System(pos, L, to_vbc(p), precision=F32) as s:
+        r = s.compute(F=True)
+        sw, dsw, A = s.switch()
+        st = s.stats()
+    rms = np.sqrt(np.mean(np.sum(ref.F ** 2, axis=1)))
+    assert np.max(np.abs(r.F - ref.F)) <= tol["F"] * rms
+    assert np.max(np.abs(sw - ref.s)) <= tol["s"]
+    assert np.max(np.abs(dsw - ref.ds)) <= 4 * tol["s"]
+    assert np.max(np.abs(A - ref.A)) <= tol["A"] * max(np.max(np.abs(ref.A)), 1e-12)
+    if valency == 2.0:
+        assert st.unsaturated <= n // 16
+    else:
+        assert st.unsaturated > n // 16
