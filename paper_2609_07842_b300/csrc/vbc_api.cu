@@ -561,7 +561,7 @@ int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window)
             s->ulist, s->st);
         k_count_rows<M><<<s->row_grid, SC_TPB, s->smem_rows(0), s->stream>>>(
             (int)s->n, s->nsc, s->geom, s->coef, pos, s->grid(), s->caps(), s->aux(), s->nbr, s->nnb, s->id, (real*)s->ds,
-            (real2*)s->sA, out, s->ulist, s->wpart, s->st);
+            (real2*)s->sA, out, s->ulist, s->wpart, (const long long*)s->x, s->st);
     }
     {
         Timed t(s, VBC_K_CHAIN);
@@ -758,6 +758,7 @@ int halt_error(vbc_system* s)
         return fail(VBC_ERR_UNSTABLE, "more than %d particles in one cell: the system has collapsed or blown up",
                     MAX_CELL);
     if (s->st_host->frozen) return fail(VBC_ERR_UNSTABLE, "a position, velocity or force became non-finite");
+    if (s->st_host->bad_index) return fail(VBC_ERR_CUDA, "internal error: a count met a particle index out of range");
     return VBC_OK;
 }
 

@@ -90,7 +90,7 @@ struct Status {
     int nu;             // particles the last count walked in full: not saturated by their kept close
                         // neighbours (k_count_near)
     int ngen;           // particles whose force k_force_rows forms (k_count_near, k_chain)
-    int pad2;
+    int bad_index;      // 1: a count was handed a particle index outside [0, n) (k_count_rows; an internal error)
 };
 
 // Work stops (until the host intervenes) once any of these is raised.

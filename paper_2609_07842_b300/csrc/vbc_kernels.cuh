@@ -1088,8 +1088,12 @@ __device__ __forceinline__ void switch_from_fix(long long T, float& s, float& ds
         s = 0.0f;
         ds = 0.0f;
     } else {
-        const float t = (float)T * 4.656612873077393e-10f;  // 2^-31
-        const float q = 1.0f - t * t;
+        // q = 1 - t^2 = (1 - t)(1 + t), with 1 - t taken from the exact fixed-point
+        // difference: near the top of the window (t -> 1) the float 1 - t*t would lose
+        // ~1e-6 of q to cancellation, and s' = -4 t q carries that into A_i
+        const float t = (float)T * 4.656612873077393e-10f;                      // 2^-31
+        const float omt = (float)(2147483648LL - T) * 4.656612873077393e-10f;  // 1 - t
+        const float q = omt * (1.0f + t);
         s = q * q;
         ds = -4.0f * t * q;
     }
@@ -1100,6 +1104,42 @@ __device__ __forceinline__ unsigned long long r2_fix(const int4& a, const int4& 
     const int dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
     return (unsigned long long)((long long)dx * dx) + (unsigned long long)((long long)dy * dy) +
            (unsigned long long)((long long)dz * dz);
+}
+
+// Window pairs of the FP32-split counts are measured finer than the 32-bit
+// words.  A count error dn moves s'_i by s''_i dn, and A_i = s'_i sum_j s_j V_a
+// multiplies that by the well sum, so a window particle of large A_i turns
+// the ~1e-7 count error of the 32-bit position grid (L / 2^32 per axis) into
+// a force error of order 1e-5 rms|F|.  The 64-bit state carries 20 more bits
+// below each word; the top ten of them (P - word(P) 2^20, in [-2^19, 2^19),
+// floored to a multiple of 2^10) are packed three to an int and added to the
+// separation of window pairs only, which puts the count error near 1e-10.
+__device__ __forceinline__ int resid10(long long P)
+{
+    return (int)(((P + (1ll << 19)) & ((1ll << 20) - 1)) - (1ll << 19)) >> 10;
+}
+// Packed residuals of sorted particle j from the state X ([3][n], units L / 2^52).
+__device__ __forceinline__ int pack_resid(const long long* __restrict__ X, size_t n, int j)
+{
+    return (resid10(__ldg(X + j)) & 1023) | (resid10(__ldg(X + n + j)) & 1023) << 10 |
+           (resid10(__ldg(X + 2 * n + j)) & 1023) << 20;
+}
+// Field k (0, 1, 2) of a packed residual, sign-extended.
+__device__ __forceinline__ long long resid_field(int r, int k)
+{
+    return (long long)((int)((unsigned)r << (22 - 10 * k)) >> 22);
+}
+// r^2 of a window pair in units of (L / 2^32)^2 with the residuals ra, rb
+// added: with d the word difference and e the residual difference (units of
+// 2^-10 word), (d + e / 2^10)^2 = d^2 + 2 d e / 2^10 + e^2 / 2^20 per axis.
+__device__ __forceinline__ unsigned long long r2_fine(const int4& a, int ra, const int4& b, int rb,
+                                                      unsigned long long r2)
+{
+    const long long dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+    const long long ex = resid_field(ra, 0) - resid_field(rb, 0), ey = resid_field(ra, 1) - resid_field(rb, 1),
+                    ez = resid_field(ra, 2) - resid_field(rb, 2);
+    const long long cross = 2 * (dx * ex + dy * ey + dz * ez), sq = ex * ex + ey * ey + ez * ez;
+    return (unsigned long long)((long long)r2 + ((cross + (sq >> 10)) >> 10));
 }
 
 // Squared separation for the FP64 paths.
@@ -1319,10 +1359,12 @@ __device__ __forceinline__ void dense_rounds(int nl, Body&& body)
 // Count of one row over a lane group of `width` lanes, the result on every
 // lane of it: s_i, s'_i and (if wanted) n_i.  walk(visit) calls visit(m)
 // for this lane's entries.
-template <class M, class Walk, class Fetch>
-__device__ __forceinline__ void count_row(const typename M::pos_t& pi, Walk&& walk, int width, Fetch&& fetch,
-                                          const Coef& c, const Geom& g, bool want_n, typename M::real& s,
-                                          typename M::real& ds, double& n_val)
+// In the FP32 mode ri is the packed residual of i and resid(m) that of entry m
+// (unused in FP64).
+template <class M, class Walk, class Fetch, class Resid>
+__device__ __forceinline__ void count_row(const typename M::pos_t& pi, int ri, Walk&& walk, int width, Fetch&& fetch,
+                                          Resid&& resid, const Coef& c, const Geom& g, bool want_n,
+                                          typename M::real& s, typename M::real& ds, double& n_val)
 {
     if constexpr (M::fp64) {
         double acc = 0.0;
@@ -1338,10 +1380,18 @@ __device__ __forceinline__ void count_row(const typename M::pos_t& pi, Walk&& wa
         int full = 0;  // a row holds at most MAX_CAP (4096) entries
         unsigned long long q = 0;
         walk([&](int m) {
-            const unsigned long long r2 = r2_fix(pi, fetch(m));
+            const typename M::pos_t pj = fetch(m);
+            const unsigned long long r2 = r2_fix(pi, pj);
             if (r2 < c.rh2_fix) {
-                if (r2 <= c.rl2_fix) ++full;
-                else q += window_weight_tab(r2 - c.rl2_fix, c.wtab, c.wsh);
+                if (r2 <= c.rl2_fix) {
+                    ++full;
+                } else {
+                    // omega has zero slope at both ends of the window, so a pair that the
+                    // finer separation moves across r_l or r_h changes n_i by O(dr^2)
+                    const unsigned long long rf = r2_fine(pi, ri, pj, resid(m), r2);
+                    if (rf <= c.rl2_fix) q += 2147483648ull;
+                    else if (rf < c.rh2_fix) q += window_weight_tab(rf - c.rl2_fix, c.wtab, c.wsh);
+                }
             }
         });
         full = group_sum(full, width);
@@ -1380,12 +1430,22 @@ __global__ void __launch_bounds__(SC_TPB) k_count_rows(int n, int ngroups, Geom 
                                                        const int* __restrict__ id, typename M::real* __restrict__ ds_out,
                                                        typename M::real2* __restrict__ sA, CountOut out,
                                                        const int* __restrict__ ulist, int* __restrict__ wpart,
-                                                       Status* st)
+                                                       const long long* __restrict__ X, Status* st)
 {
     using pos_t = typename M::pos_t;
     using real = typename M::real;
     if (halted(st)) return;
     const int nu = st->nu;
+    // packed residuals of sorted particle j (FP32 mode; X is the state [3][n]); an index
+    // outside [0, n) is refused and reported rather than read
+    auto resid_of = [&](int j) {
+        if (M::fp64) return 0;
+        if ((unsigned)j >= (unsigned)n) {
+            st->bad_index = 1;
+            return 0;
+        }
+        return pack_resid(X, (size_t)n, j);
+    };
     const bool want_n = out.n_out != nullptr;
     if (nu <= n / DENSE_DIV) {
         for (int k = blockIdx.x * ROW_WARPS + (threadIdx.x >> 5); k < nu; k += gridDim.x * ROW_WARPS) {
@@ -1396,8 +1456,9 @@ __global__ void __launch_bounds__(SC_TPB) k_count_rows(int n, int ngroups, Geom 
             const int len = row_len(__ldg(nnb + p));
             real s, ds;
             double n_val;
-            count_row<M>(pos[p], [&](auto&& v) { walk_lanes(row, len, v); }, 32,
-                         [&](int m) { return pos[__ldg(sidx + m)]; }, c, g, want_n, s, ds, n_val);
+            count_row<M>(pos[p], resid_of(p), [&](auto&& v) { walk_lanes(row, len, v); }, 32,
+                         [&](int m) { return pos[__ldg(sidx + m)]; }, [&](int m) { return resid_of(__ldg(sidx + m)); },
+                         c, g, want_n, s, ds, n_val);
             if ((threadIdx.x & 31) == 0) count_row_out<M>(p, s, ds, n_val, pos, ds_out, sA, id, out, wpart, st);
         }
         return;
@@ -1414,8 +1475,12 @@ __global__ void __launch_bounds__(SC_TPB) k_count_rows(int n, int ngroups, Geom 
         const int n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
         const int nl = list_own(n_own, plist, &s_n, [&](int j) { return isnan(ds_out[p0 + j]); });
         if (nl == 0) continue;
-        stage_by_table(aux.stage_idx + (size_t)b * cp.smax, __ldg(aux.meta + b).x,
-                       [&](int m, int jj) { spos[m] = pos[jj]; });
+        // the count reads no s_j, so the spare word of a staged position holds its residuals
+        stage_by_table(aux.stage_idx + (size_t)b * cp.smax, __ldg(aux.meta + b).x, [&](int m, int jj) {
+            pos_t pj = pos[jj];
+            if constexpr (!M::fp64) pj.w = resid_of(jj);
+            spos[m] = pj;
+        });
         __syncthreads();
         dense_rounds(nl, [&](int u, int sub, int tpp) {
             const bool act = u < nl;
@@ -1424,8 +1489,9 @@ __global__ void __launch_bounds__(SC_TPB) k_count_rows(int n, int ngroups, Geom 
             const int len = act ? row_len(__ldg(nnb + p)) : 0;
             real s, ds;
             double n_val;
-            count_row<M>(pos[p], [&](auto&& v) { walk_chunks(row, len, sub, tpp, v); }, tpp,
-                         [&](int m) { return spos[m]; }, c, g, want_n, s, ds, n_val);
+            count_row<M>(pos[p], act ? resid_of(p) : 0, [&](auto&& v) { walk_chunks(row, len, sub, tpp, v); }, tpp,
+                         [&](int m) { return spos[m]; }, [&](int m) { return (int)spos[m].w; }, c, g, want_n, s,
+                         ds, n_val);
             if (act && sub == 0) count_row_out<M>(p, s, ds, n_val, pos, ds_out, sA, id, out, wpart, st);
         });
     }

@@ -348,6 +348,20 @@ def test_full_size_uniform_rho05(n):
     compare(pos, L, p, F32, mode=1, min_window=0.1)
 
 
+@pytest.mark.parametrize("n", [20_000, 1_000_000])
+def test_counts_finer_than_the_position_words(n):
+    """FP32 split: window pairs of the counts (Sec. 2, Eq. n_i) are measured
+    with the residual bits of the 64-bit state below the 32-bit position words,
+    so n_i carries only the 2^-32 rounding of each window term -- far below the
+    ~5e-7 (at N = 1M, L = 126) that the L / 2^32 grid alone would leave."""
+    pos, L = inputs.uniform_positions(n, 0.5, seed=3)
+    p = Params(E_a=8.0, f=8.0)
+    ref = oracle.evaluate(pos, L, p, 1)
+    with vbc.System(pos, L, to_vbc(p), precision=F32) as s:
+        r = s.compute(counts=True)
+    assert np.max(np.abs(r.counts - ref.counts)) <= 1e-8
+
+
 @pytest.mark.parametrize("valency", [2.0, 8.0])
 def test_full_size_forces_only_as_benchmarked(valency):
     """The throughput workload as the benchmark runs it: N = 1M, density 0.5,
