@@ -89,6 +89,11 @@ def lib():
         L.orc_baoab.argtypes = [ctypes.c_int64, dp, dp, dp, ctypes.POINTER(_Params), ctypes.c_int,
                                 ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                 ctypes.c_uint64, ctypes.POINTER(ctypes.c_int64)]
+        L.orc_eval_typed.restype = ctypes.c_int
+        L.orc_eval_typed.argtypes = ([ctypes.c_int64, dp, dp, ctypes.POINTER(ctypes.c_int32), ctypes.c_int,
+                                      ctypes.POINTER(_Params), ctypes.POINTER(ctypes.c_int), ctypes.c_int64,
+                                      ctypes.POINTER(ctypes.c_int64), ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_int] + [dp] * 8)
         L.orc_num_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -159,6 +164,37 @@ def evaluate(pos: np.ndarray, box, p: Params, mode: int = 0) -> EvalResult:
                         *[_dp(a) for a in out], ctypes.byref(U), ctypes.byref(W))
     if rc != 0:
         raise ValueError("oracle: cell-list mode needs at least 3 cells per axis")
+    return EvalResult(*out, U=U.value, W=W.value)
+
+
+def evaluate_typed(pos: np.ndarray, box, types, P, cmask, bonds=None, k_b: float = 0.0, r_0: float = 1.0,
+                   mode: int = 0) -> EvalResult:
+    """Multi-type VBC with harmonic bonds (Sec. 2: counts restricted to selected
+    neighbour types; Sec. 4: bead-spring sticker chains).  types [n] in
+    [0, T); P a T x T nested list of Params (symmetric; a type's valency and
+    shift from its diagonal entry); cmask T x T of 0/1 (cmask[a][b]: a
+    particle of type a counts neighbours of type b); bonds [m, 2] particle
+    indices, each bond once, with energy k_b/2 (r - r_0)^2.  mode 0 = all
+    pairs, 1 = cell list."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    n = pos.shape[0]
+    b = _box3(box)
+    t = np.ascontiguousarray(types, dtype=np.int32).reshape(-1)
+    T = len(P)
+    Pc = (_Params * (T * T))(*[P[a][c].c() for a in range(T) for c in range(T)])
+    m = np.ascontiguousarray(np.asarray(cmask, dtype=np.int32).reshape(T * T))
+    bd = np.ascontiguousarray(np.zeros((0, 2)) if bonds is None else bonds, dtype=np.int64).reshape(-1, 2)
+    out = [np.zeros(n) for _ in range(4)] + [np.zeros((n, 3)), np.zeros(n)]
+    U = ctypes.c_double(0.0)
+    W = ctypes.c_double(0.0)
+    rc = lib().orc_eval_typed(n, _dp(b), _dp(pos), t.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), T, Pc,
+                              m.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), bd.shape[0],
+                              bd.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), k_b, r_0, mode,
+                              *[_dp(a) for a in out], ctypes.byref(U), ctypes.byref(W))
+    if rc == -1:
+        raise ValueError("oracle: cell-list mode needs at least 3 cells per axis")
+    if rc != 0:
+        raise ValueError("oracle: a type or bond index is out of range")
     return EvalResult(*out, U=U.value, W=W.value)
 
 

@@ -34,7 +34,8 @@
  * mode 1 against mode 0.
  *
  * Parity status: every function here is pinned by the CPU tests (closed
- * forms, finite differences, invariants, published Philox test vectors).
+ * forms, finite differences, invariants, published Philox test vectors);
+ * the multi-type evaluation also by its reduction to the single-type one.
  */
 #include <math.h>
 #include <stdint.h>
@@ -317,6 +318,179 @@ int orc_eval(int64_t n, const double* box, const double* pos, const orc_params* 
     if (U) *U = Usum;
     if (W) *W = Wsum;
     free(nn); free(s); free(ds); free(A); free(e); free(w);
+    if (cp) orc_cells_free(cp);
+    return 0;
+}
+
+/* ------------------------------------------ several particle types and bonds */
+/*
+ * Multi-type VBC with harmonic bonds: the count of a particle restricted to
+ * selected neighbour types (Sec. 2, where the counter may run over chosen
+ * types only) and the bead-spring sticker chains of Sec. 4.  Type t_i is in
+ * [0, ntypes).  The pair (i, j) uses the potential parameters
+ * P[t_i][t_j] (r_r, r_a, r_l, r_h, E_r, E_a; P symmetric), a type's
+ * valency and threshold shift are P[t][t].f and P[t][t].delta, and the
+ * count of i takes the pair only if cmask[t_i][t_j] != 0:
+ *   n_i  = sum_{j != i, cmask[t_i][t_j]} omega(r_ij; r_l^{ij}, r_h^{ij})
+ *   s_i  = omega(n_i; f_{t_i} - delta_{t_i}, f_{t_i} - delta_{t_i} + 1)
+ *   U    = sum_{i<j} [V_r^{ij} + s_i s_j V_a^{ij}] + sum_bonds k_b/2 (r - r_0)^2
+ *   A_i  = dU/dn_i = s'_i sum_{j != i} s_j V_a^{ij}
+ *   g_ij = V_r' + s_i s_j V_a' + (cmask[t_i][t_j] A_i + cmask[t_j][t_i] A_j) omega'^{ij}
+ * (A_i enters through n_i, which holds the pair only when cmask[t_i][t_j]
+ * is set.)  A bond (i, j) adds k_b (r - r_0) to g_ij; bonded pairs keep
+ * their non-bonded terms.  With one type, cmask = 1 and no bonds this is
+ * orc_eval.
+ */
+typedef struct {
+    const orc_params* P; /* [ntypes][ntypes] */
+    const int* cmask;    /* [ntypes][ntypes] */
+    const int32_t* type;
+    int ntypes;
+    const double* s;
+    const double* A;
+    double acc;
+    double vec[3];
+    double e, w;
+} orc_tctx;
+
+static const orc_params* orc_pair(const orc_tctx* c, int64_t i, int64_t j)
+{
+    return c->P + (size_t)c->type[i] * c->ntypes + c->type[j];
+}
+
+static int orc_counts_pair(const orc_tctx* c, int64_t i, int64_t j)
+{
+    return c->cmask[(size_t)c->type[i] * c->ntypes + c->type[j]] != 0;
+}
+
+static void tvisit_count(int64_t i, int64_t j, const double d[3], double r, void* vctx)
+{
+    (void)d;
+    orc_tctx* c = (orc_tctx*)vctx;
+    if (!orc_counts_pair(c, i, j)) return;
+    const orc_params* p = orc_pair(c, i, j);
+    c->acc += orc_omega(r, p->r_l, p->r_h);
+}
+
+static void tvisit_chain(int64_t i, int64_t j, const double d[3], double r, void* vctx)
+{
+    (void)d;
+    orc_tctx* c = (orc_tctx*)vctx;
+    c->acc += c->s[j] * orc_Va(r, orc_pair(c, i, j));
+}
+
+static void tvisit_force(int64_t i, int64_t j, const double d[3], double r, void* vctx)
+{
+    orc_tctx* c = (orc_tctx*)vctx;
+    const orc_params* p = orc_pair(c, i, j);
+    double chain = (orc_counts_pair(c, i, j) ? c->A[i] : 0.0) + (orc_counts_pair(c, j, i) ? c->A[j] : 0.0);
+    double g = orc_dVr(r, p) + c->s[i] * c->s[j] * orc_dVa(r, p) + chain * orc_domega(r, p->r_l, p->r_h);
+    if (r > 0.0) {
+        for (int a = 0; a < 3; ++a) c->vec[a] -= g * d[a] / r;
+    }
+    c->e += 0.5 * (orc_Vr(r, p) + c->s[i] * c->s[j] * orc_Va(r, p));
+    c->w += 0.5 * (-g * r);
+}
+
+/*
+ * Full typed evaluation.  type [n], P and cmask [ntypes * ntypes] row-major,
+ * bonds [nbonds][2] particle indices (each bond once), k_b and r_0 the
+ * harmonic bond constants.  Outputs as in orc_eval (each may be NULL).
+ * Returns 0, -1 if the cell list does not fit the box (mode 1), -2 for a type
+ * or bond index out of range.
+ */
+int orc_eval_typed(int64_t n, const double* box, const double* pos, const int32_t* type, int ntypes,
+                   const orc_params* P, const int* cmask, int64_t nbonds, const int64_t* bonds,
+                   double k_b, double r_0, int mode, double* counts, double* s_out, double* ds_out,
+                   double* A_out, double* F, double* e_out, double* U, double* W)
+{
+    if (ntypes < 1) return -2;
+    for (int64_t i = 0; i < n; ++i)
+        if (type[i] < 0 || type[i] >= ntypes) return -2;
+    for (int64_t b = 0; b < 2 * nbonds; ++b)
+        if (bonds[b] < 0 || bonds[b] >= n) return -2;
+    double rc = 0.0;
+    for (int k = 0; k < ntypes * ntypes; ++k) {
+        double c = orc_rcut(P + k);
+        if (c > rc) rc = c;
+    }
+    orc_cells cells;
+    orc_cells* cp = NULL;
+    if (mode == 1) {
+        if (orc_cells_build(n, box, pos, rc, &cells) != 0) return -1;
+        cp = &cells;
+    }
+    size_t sz = sizeof(double) * (size_t)(n > 0 ? n : 1);
+    double* nn = (double*)malloc(sz);
+    double* s = (double*)malloc(sz);
+    double* ds = (double*)malloc(sz);
+    double* A = (double*)malloc(sz);
+    double* e = (double*)malloc(sz);
+    double* w = (double*)malloc(sz);
+    double* Fl = (double*)calloc(3 * (size_t)(n > 0 ? n : 1), sizeof(double));
+
+    /* counts over the selected neighbour types, then each particle's own switch */
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) {
+        orc_tctx c = {P, cmask, type, ntypes, NULL, NULL, 0.0, {0, 0, 0}, 0, 0};
+        orc_for_neighbours(i, n, box, pos, rc, cp, tvisit_count, &c);
+        const orc_params* own = P + (size_t)type[i] * ntypes + type[i];
+        double lo = own->f - own->delta;
+        nn[i] = c.acc;
+        s[i] = orc_omega(nn[i], lo, lo + 1.0);
+        ds[i] = orc_domega(nn[i], lo, lo + 1.0);
+    }
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) {
+        if (ds[i] == 0.0) {
+            A[i] = 0.0;
+            continue;
+        }
+        orc_tctx c = {P, cmask, type, ntypes, s, NULL, 0.0, {0, 0, 0}, 0, 0};
+        orc_for_neighbours(i, n, box, pos, rc, cp, tvisit_chain, &c);
+        A[i] = ds[i] * c.acc;
+    }
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) {
+        orc_tctx c = {P, cmask, type, ntypes, s, A, 0.0, {0, 0, 0}, 0, 0};
+        orc_for_neighbours(i, n, box, pos, rc, cp, tvisit_force, &c);
+        for (int a = 0; a < 3; ++a) Fl[3 * i + a] = c.vec[a];
+        e[i] = c.e;
+        w[i] = c.w;
+    }
+    /* harmonic bonds, one after another: each gives -k_b (r - r_0) d / r to i and the opposite to j */
+    for (int64_t b = 0; b < nbonds; ++b) {
+        int64_t i = bonds[2 * b], j = bonds[2 * b + 1];
+        double d[3];
+        orc_sep(pos + 3 * i, pos + 3 * j, box, d);
+        double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        double g = k_b * (r - r_0);
+        if (r > 0.0) {
+            for (int a = 0; a < 3; ++a) {
+                Fl[3 * i + a] -= g * d[a] / r;
+                Fl[3 * j + a] += g * d[a] / r;
+            }
+        }
+        double eb = 0.5 * k_b * (r - r_0) * (r - r_0);
+        e[i] += 0.5 * eb;
+        e[j] += 0.5 * eb;
+        w[i] += 0.5 * (-g * r);
+        w[j] += 0.5 * (-g * r);
+    }
+    double Usum = 0.0, Wsum = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        Usum += e[i];
+        Wsum += w[i];
+    }
+    if (F) memcpy(F, Fl, 3 * sizeof(double) * (size_t)n);
+    if (counts) memcpy(counts, nn, sizeof(double) * (size_t)n);
+    if (s_out) memcpy(s_out, s, sizeof(double) * (size_t)n);
+    if (ds_out) memcpy(ds_out, ds, sizeof(double) * (size_t)n);
+    if (A_out) memcpy(A_out, A, sizeof(double) * (size_t)n);
+    if (e_out) memcpy(e_out, e, sizeof(double) * (size_t)n);
+    if (U) *U = Usum;
+    if (W) *W = Wsum;
+    free(nn); free(s); free(ds); free(A); free(e); free(w); free(Fl);
     if (cp) orc_cells_free(cp);
     return 0;
 }

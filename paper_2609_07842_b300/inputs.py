@@ -51,3 +51,26 @@ def quantile_valency(counts: np.ndarray, q: float) -> float:
     window [f, f + 1]: f = quantile - 0.5.  Used by tests so that the chain-rule
     terms are exercised on uniform fluids, whose counts sit far above small f."""
     return float(np.quantile(counts, q) - 0.5)
+
+
+def sticker_chains(nchains: int, beads: int, rho: float, seed: int, bond: float = 1.0,
+                   every: int = 4) -> tuple[np.ndarray, float, np.ndarray, np.ndarray]:
+    """Linear bead-spring chains for the sticker model of Sec. 4: each chain a
+    random walk of `beads` beads with steps of length `bond` in uniformly random
+    directions, from a uniform random start in a cubic box at bead density rho.
+    Beads whose index along the chain is a multiple of `every` are stickers
+    (type 1), the others spacers (type 0).  Returns (pos[n,3] wrapped into the
+    box, L, types[n] int32, bonds[m,2] int64 with consecutive beads of a chain)."""
+    n = nchains * beads
+    L = box_length(n, rho)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    start = rng.uniform(0.0, L, size=(nchains, 1, 3))
+    step = rng.normal(size=(nchains, beads - 1, 3))
+    step *= bond / np.linalg.norm(step, axis=2, keepdims=True)
+    walk = np.concatenate([np.zeros((nchains, 1, 3)), np.cumsum(step, axis=1)], axis=1)
+    pos = np.mod((start + walk).reshape(n, 3), L)
+    k = np.arange(n) % beads
+    types = (k % every == 0).astype(np.int32)
+    first = np.arange(n)[k < beads - 1]
+    bonds = np.stack([first, first + 1], axis=1).astype(np.int64)
+    return np.ascontiguousarray(pos), L, types, np.ascontiguousarray(bonds)
