@@ -65,6 +65,10 @@ def parse():
     ap.add_argument("--sweep", action="store_true",
                     help="cost-vs-valency curve (N=100k, rho 0.5, E_a 8, v in 1,2,4,6,8) and the paper-shape "
                          "point (N=10k, rho 0.05, E_a 2, dt 0.01, gamma 0.1, f = 1..6); one JSON line each")
+    ap.add_argument("--leg", choices=("served", "batched"), default=None,
+                    help="run only this optional leg and print its JSON object (the main run starts each "
+                         "optional leg this way, in a process of its own)")
+    ap.add_argument("--leg-timeout", type=float, default=900.0, help="seconds allowed to one optional leg")
     ap.add_argument("--profile-run", action="store_true",
                     help="short run for profilers: the equilibrated workload (cached under /tmp), one forced "
                          "list build, one force evaluation and 6 steps; prints no JSON line")
@@ -403,10 +407,46 @@ def run_batched(args):
     return out
 
 
+def served_leg(args):
+    """The served stream through the serving loop, and the same stream one system
+    at a time."""
+    mix = run_served(args, args.served_slots)
+    one = run_served(args, 1)
+    return {"workload": (f"{args.served_requests} requests, Poisson arrivals at 20/s, N log-uniform in "
+                         f"[1k, 200k], valency uniform in 1..8, rho {args.rho}, E_a {args.E_a}, "
+                         f"{args.served_steps} steps each in 1000-step chunks, 150 GB admission budget"),
+            **mix, "one_at_a_time": one,
+            "speedup_vs_one_at_a_time": mix["timesteps_per_s"] / one["timesteps_per_s"]}
+
+
+def leg_in_child(leg, argv, timeout, python=sys.executable):
+    """Runs one optional leg (`bench.py --leg <leg>`) in a fresh Python process and
+    returns its JSON object.  A leg that fails, faults or overruns gives
+    {"error": ...} instead, so that it cannot take the main measurement with it."""
+    cmd = [python, os.path.abspath(__file__), *argv, "--leg", leg]
+    try:
+        p = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout)
+    except subprocess.TimeoutExpired:
+        return {"error": f"the {leg} leg did not finish within {timeout:g} s"}
+    objs = [ln for ln in p.stdout.splitlines() if ln.startswith("{")]
+    if p.returncode != 0 or not objs:
+        return {"error": f"the {leg} leg exited with status {p.returncode}",
+                "stderr_tail": p.stderr[-800:]}
+    return json.loads(objs[-1])
+
+
+def leg_main(args):
+    out = served_leg(args) if args.leg == "served" else run_batched(args)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_main(args)
+    if args.leg:
+        return leg_main(args)
     if args.profile_run:
         return profile_run(args)
     if args.sweep:
@@ -544,20 +584,15 @@ def main():
 
     # ---- served: a Poisson stream of uneven requests through the serving loop,
     # and the same stream one system at a time (rank 0, N = 1 only)
+    # (each optional leg runs in a process of its own, while this one waits)
     served = None
     if rank == 0 and world == 1 and not args.no_served:
-        mix = run_served(args, args.served_slots)
-        one = run_served(args, 1)
-        served = {"workload": (f"{args.served_requests} requests, Poisson arrivals at 20/s, N log-uniform in "
-                               f"[1k, 200k], valency uniform in 1..8, rho {args.rho}, E_a {args.E_a}, "
-                               f"{args.served_steps} steps each in 1000-step chunks, 150 GB admission budget"),
-                  **mix, "one_at_a_time": one,
-                  "speedup_vs_one_at_a_time": mix["timesteps_per_s"] / one["timesteps_per_s"]}
+        served = leg_in_child("served", sys.argv[1:], args.leg_timeout)
 
     # ---- batched: many uneven systems in one graph against one at a time (rank 0, N = 1 only)
     batched = None
     if rank == 0 and world == 1 and not args.no_batched:
-        batched = run_batched(args)
+        batched = leg_in_child("batched", sys.argv[1:], args.leg_timeout)
 
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
     cpu = None
