@@ -118,6 +118,38 @@ typedef struct {
  */
 int vbc_create_system(const vbc_config* cfg, vbc_system** out);
 
+/* ---------------------------------------------------------------- several types and bonds
+ * Multi-type VBC (Sec. 2: the counter may run over chosen neighbour types
+ * only) with harmonic bonds (the bead-spring sticker chains of Sec. 4).  The
+ * pair (i, j) takes its potential and counting radii from pair[t_i][t_j]; a
+ * type's valency f and shift delta come from its diagonal entry.  Particle i
+ * counts neighbour j only if count_mask[t_i][t_j] is 1, so
+ *   n_i = sum_{j: mask[t_i][t_j]} omega(r_ij; r_l^{ij}, r_h^{ij}),
+ *   s_i = omega(n_i; f_{t_i} - delta_{t_i}, f_{t_i} - delta_{t_i} + 1),
+ *   U   = sum_{i<j} [V_r^{ij} + s_i s_j V_a^{ij}] + sum_bonds k_bond/2 (r - r0_bond)^2.
+ * Bonded pairs keep their non-bonded terms.  All arrays are host memory in
+ * the caller's particle order, copied at creation; row-major tables. */
+#define VBC_MAX_TYPES 8
+typedef struct {
+    int32_t ntypes;                /* 1 <= ntypes <= VBC_MAX_TYPES */
+    const int32_t* type;           /* [n] type of each particle, in [0, ntypes) */
+    const vbc_pair_params* pair;   /* [ntypes][ntypes], symmetric in r_r, r_a, r_l, r_h, E_r, E_a */
+    const int32_t* count_mask;     /* [ntypes][ntypes] of 0 or 1: row type counts column type */
+    int64_t nbonds;                /* bonds, >= 0 */
+    const int64_t* bonds;          /* [nbonds][2] particle indices, i != j, each bond once (NULL if none) */
+    double k_bond, r0_bond;        /* harmonic constant (>= 0) and rest length (>= 0) */
+} vbc_types;
+
+/*
+ * Create a multi-type system.  cfg is as for vbc_create_system except that
+ * cfg->params is ignored (the neighbour list reaches the largest
+ * max(r_r, r_a, r_h) of the table plus the skin) and cfg->precision must be
+ * VBC_FP64.  Every other call then works on it as on any system, except
+ * vbc_set_params and vbc_get_observables (INVALID_ARG).  Errors as
+ * vbc_create_system, and INVALID_ARG for a bad type, table, mask or bond.
+ */
+int vbc_create_typed_system(const vbc_config* cfg, const vbc_types* types, vbc_system** out);
+
 /* Device memory, in bytes, that vbc_create_system would allocate for cfg (the
  * initial capacities; the first list build trims them, an overflow grows
  * them).  No device is touched.  Errors: INVALID_ARG (NULL pointers, n, box or

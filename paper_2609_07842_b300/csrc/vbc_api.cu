@@ -11,6 +11,7 @@
 // capacities from the start.
 #include "vbc.h"
 #include "vbc_kernels.cuh"
+#include "vbc_typed.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -108,6 +109,12 @@ struct vbc_system {
     unsigned long long *x = nullptr, *v = nullptr, *xt = nullptr, *vt = nullptr;  // [3][n] 8-byte words
     int *id = nullptr, *idt = nullptr;
     void *pos[2] = {nullptr, nullptr};
+    // several types and bonds (vbc_create_typed_system, FP64 mode); the arrays of tdev
+    bool typed = false;
+    TypedDev tdev{};
+    Coef* t_pc = nullptr;
+    int *t_mask = nullptr, *t_type = nullptr, *t_tsort = nullptr, *t_inv = nullptr, *t_bto = nullptr;
+    long long* t_bptr = nullptr;
     void *post = nullptr, *xref = nullptr;
     int cur = 0;
     uint16_t* nbr = nullptr;
@@ -435,6 +442,8 @@ int upload_window_table(vbc_system* s)
 void free_all(vbc_system* s)
 {
     dfree(s->x); dfree(s->v); dfree(s->xt); dfree(s->vt); dfree(s->id); dfree(s->idt);
+    dfree(s->t_pc); dfree(s->t_mask); dfree(s->t_type); dfree(s->t_tsort); dfree(s->t_inv); dfree(s->t_bptr);
+    dfree(s->t_bto);
     dfree(s->pos[0]); dfree(s->pos[1]); dfree(s->post); dfree(s->xref);
     dfree(s->nbr); dfree(s->scratch); dfree(s->nnb); dfree(s->cell_of); dfree(s->slot_of); dfree(s->order);
     dfree(s->cell_count); dfree(s->cell_start); dfree(s->morton_rank); dfree(s->sc_org);
@@ -534,6 +543,12 @@ int enqueue_rebuild(vbc_system* s)
                                             (pos_t*)s->post, s->st);
     k_copyback<M><<<nb, TPB, 0, s->stream>>>(n, s->xt, s->vt, s->idt, (const pos_t*)s->post, s->x, s->v, s->id,
                                              pos, (pos_t*)s->xref, s->st);
+    if constexpr (M::fp64) {
+        if (s->typed) {
+            k_tmaps<<<nb, TPB, 0, s->stream>>>(n, s->id, s->tdev);
+            VBC_TRY(check_launch(s));
+        }
+    }
     if constexpr (!M::fp64) {
         if (s->rel_lists) {
             k_nlist<M, true><<<s->nsc, SC_TPB, s->smem_nlist_rel(), s->stream>>>(
@@ -546,9 +561,37 @@ int enqueue_rebuild(vbc_system* s)
     return check_launch(s, REBUILD_KERNELS);
 }
 
+// Resident grid of the typed walks (one warp per particle, grid-stride).
+int typed_grid(const vbc_system* s)
+{
+    const long long want = (s->n * 32 + SC_TPB - 1) / SC_TPB;
+    return (int)std::max<long long>(1, std::min<long long>(want, (long long)s->sms * 16));
+}
+
+int enqueue_typed_count_chain(vbc_system* s, double* n_out, bool want_window)
+{
+    P64* pos = (P64*)s->pos[s->cur];
+    CountOut out{n_out, want_window ? s->win : nullptr};
+    const int n = (int)s->n, gb = typed_grid(s);
+    {
+        Timed t(s, VBC_K_COUNT);
+        k_tcount<<<gb, SC_TPB, 0, s->stream>>>(n, s->geom, pos, s->caps(), s->aux(), s->nbr, s->nnb, s->id, s->tdev,
+                                               (double*)s->ds, (double2*)s->sA, out, s->st);
+    }
+    {
+        Timed t(s, VBC_K_CHAIN);
+        k_tchain<<<gb, SC_TPB, 0, s->stream>>>(n, s->geom, pos, s->caps(), s->aux(), s->nbr, s->nnb, s->tdev,
+                                               (const double*)s->ds, (double2*)s->sA, s->st);
+    }
+    return check_launch(s, 2);
+}
+
 template <class M>
 int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window)
 {
+    if constexpr (M::fp64) {
+        if (s->typed) return enqueue_typed_count_chain(s, n_out, want_window);
+    }
     using pos_t = typename M::pos_t;
     using real = typename M::real;
     using real2 = typename M::real2;
@@ -583,8 +626,19 @@ int enqueue_force(vbc_system* s, const StepArgs& a)
     pos_t* pos_next = (pos_t*)s->pos[s->cur ^ 1];
     {
         Timed t(s, VBC_K_FORCE);
-        k_force_rows<M><<<s->row_grid, SC_TPB, s->smem_rows(s->real_bytes()), s->stream>>>(
-            n, s->nsc, s->geom, s->coef, pos, s->grid(), s->caps(), s->aux(), s->nbr, s->nnb, (const real2*)s->sA, s->st);
+        bool done = false;
+        if constexpr (M::fp64) {
+            if (s->typed) {
+                k_tforce<<<typed_grid(s), SC_TPB, 0, s->stream>>>(n, s->geom, pos, s->caps(), s->aux(), s->nbr,
+                                                                   s->nnb, s->id, s->tdev, (const double2*)s->sA,
+                                                                   s->st);
+                done = true;
+            }
+        }
+        if (!done)
+            k_force_rows<M><<<s->row_grid, SC_TPB, s->smem_rows(s->real_bytes()), s->stream>>>(
+                n, s->nsc, s->geom, s->coef, pos, s->grid(), s->caps(), s->aux(), s->nbr, s->nnb,
+                (const real2*)s->sA, s->st);
         k_step<M, EPI><<<blocks_for(n, TPB), TPB, 0, s->stream>>>(n, s->geom, s->aux(), s->id, pos_next,
                                                                   (const pos_t*)s->xref, a, s->st);
     }
@@ -600,6 +654,16 @@ int enqueue_energy(vbc_system* s)
     {
         Timed t(s, VBC_K_ENERGY);
         const pos_t* pos = (const pos_t*)s->pos[s->cur];
+        if constexpr (M::fp64) {
+            if (s->typed) {
+                const int gb = std::min(typed_grid(s), s->nsc);  // one partial sum per block
+                k_tenergy<<<gb, SC_TPB, 0, s->stream>>>((int)s->n, s->geom, pos, s->caps(), s->aux(), s->nbr,
+                                                         s->nnb, s->id, s->tdev, (const double2*)s->sA, s->partial,
+                                                         s->ppairs, s->st);
+                k_reduce_final<<<1, RED_TPB, 0, s->stream>>>(gb, s->partial, s->ppairs, s->red, s->st);
+                return check_launch(s, 2);
+            }
+        }
         const int nb = s->nsc;
         k_count_e<M><<<nb, SC_TPB, s->smem_energy(), s->stream>>>(s->geom, s->coef, pos, s->grid(), s->caps(),
                                                                    s->nbr, s->nnb, s->e_sd, s->st);
@@ -1318,6 +1382,99 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     return VBC_OK;
 }
 
+int vbc_create_typed_system(const vbc_config* cfg, const vbc_types* ty, vbc_system** out)
+{
+    g_err.clear();
+    if (!cfg || !ty || !out) return fail(VBC_ERR_INVALID_ARG, "cfg, types and out must not be NULL");
+    *out = nullptr;
+    if (cfg->precision != VBC_FP64) return fail(VBC_ERR_INVALID_ARG, "multi-type systems need VBC_FP64");
+    const int T = ty->ntypes;
+    if (T < 1 || T > MAX_TYPES) return fail(VBC_ERR_INVALID_ARG, "ntypes must be in [1, %d]", MAX_TYPES);
+    if (!ty->type || !ty->pair || !ty->count_mask)
+        return fail(VBC_ERR_INVALID_ARG, "type, pair and count_mask must not be NULL");
+    if (cfg->n < 1 || cfg->n > 0x7fffffffLL) return fail(VBC_ERR_INVALID_ARG, "n must be in [1, 2^31 - 1]");
+    const int64_t n = cfg->n;
+    for (int64_t i = 0; i < n; ++i)
+        if (ty->type[i] < 0 || ty->type[i] >= T) return fail(VBC_ERR_INVALID_ARG, "type of particle %lld out of range", (long long)i);
+    Geom g0{};  // only the FP64 fields of the pair coefficients are used; the box scale keeps the rest finite
+    for (int a = 0; a < 3; ++a)
+        g0.s32d[a] = cfg->box[a] > 0 && std::isfinite(cfg->box[a]) ? cfg->box[a] / 4294967296.0 : 1.0;
+    std::vector<Coef> pc((size_t)T * T);
+    double rc = 0.0;
+    for (int a = 0; a < T; ++a)
+        for (int b = 0; b < T; ++b) {
+            const vbc_pair_params &p = ty->pair[a * T + b], &q = ty->pair[b * T + a];
+            if (p.r_r != q.r_r || p.r_a != q.r_a || p.r_l != q.r_l || p.r_h != q.r_h || p.E_r != q.E_r ||
+                p.E_a != q.E_a)
+                return fail(VBC_ERR_INVALID_ARG, "the pair table must be symmetric (types %d and %d)", a, b);
+            const int m = ty->count_mask[a * T + b];
+            if (m != 0 && m != 1) return fail(VBC_ERR_INVALID_ARG, "count_mask entries must be 0 or 1");
+            VBC_TRY(make_coef(p, g0, pc[(size_t)a * T + b]));
+            rc = std::max(rc, std::max(p.r_r, std::max(p.r_a, p.r_h)));
+        }
+    if (ty->nbonds < 0 || (ty->nbonds > 0 && !ty->bonds)) return fail(VBC_ERR_INVALID_ARG, "bad bond list");
+    if (!(ty->k_bond >= 0) || !std::isfinite(ty->k_bond) || !(ty->r0_bond >= 0) || !std::isfinite(ty->r0_bond))
+        return fail(VBC_ERR_INVALID_ARG, "k_bond and r0_bond must be finite and >= 0");
+    // bond partners by original index, each bond from both ends (CSR)
+    std::vector<long long> bptr((size_t)n + 1, 0);
+    for (int64_t b = 0; b < ty->nbonds; ++b) {
+        const int64_t i = ty->bonds[2 * b], j = ty->bonds[2 * b + 1];
+        if (i < 0 || i >= n || j < 0 || j >= n || i == j)
+            return fail(VBC_ERR_INVALID_ARG, "bond %lld joins invalid particles", (long long)b);
+        ++bptr[(size_t)i + 1];
+        ++bptr[(size_t)j + 1];
+    }
+    for (size_t i = 0; i < (size_t)n; ++i) bptr[i + 1] += bptr[i];
+    std::vector<int> bto((size_t)std::max<long long>(bptr[(size_t)n], 1));
+    {
+        std::vector<long long> fill(bptr.begin(), bptr.end() - 1);
+        for (int64_t b = 0; b < ty->nbonds; ++b) {
+            const int64_t i = ty->bonds[2 * b], j = ty->bonds[2 * b + 1];
+            bto[(size_t)fill[(size_t)i]++] = (int)j;
+            bto[(size_t)fill[(size_t)j]++] = (int)i;
+        }
+    }
+    // the single-type machinery (cells, list, state) with a list radius that covers every pair
+    vbc_config c = *cfg;
+    c.params = ty->pair[0];
+    c.params.r_h = std::max(c.params.r_h, rc);
+    vbc_system* s = nullptr;
+    VBC_TRY(vbc_create_system(&c, &s));
+    auto bail = [&](int rc2) {
+        vbc_destroy(s);
+        return rc2;
+    };
+    int rc2 = VBC_OK;
+#define TALLOC(expr) \
+    if ((rc2 = (expr)) != VBC_OK) return bail(rc2)
+    TALLOC(dalloc(s->t_pc, (size_t)T * T));
+    TALLOC(dalloc(s->t_mask, (size_t)T * T));
+    TALLOC(dalloc(s->t_type, (size_t)n));
+    TALLOC(dalloc(s->t_tsort, (size_t)n));
+    TALLOC(dalloc(s->t_inv, (size_t)n));
+    TALLOC(dalloc(s->t_bptr, (size_t)n + 1));
+    TALLOC(dalloc(s->t_bto, bto.size()));
+#undef TALLOC
+    std::vector<int> mask((size_t)T * T), type((size_t)n);
+    for (int k = 0; k < T * T; ++k) mask[(size_t)k] = ty->count_mask[k];
+    for (int64_t i = 0; i < n; ++i) type[(size_t)i] = ty->type[i];
+    if (cudaMemcpy(s->t_pc, pc.data(), pc.size() * sizeof(Coef), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(s->t_mask, mask.data(), mask.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(s->t_type, type.data(), type.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(s->t_bptr, bptr.data(), bptr.size() * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(s->t_bto, bto.data(), bto.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(fail(VBC_ERR_CUDA, "upload of the type tables failed"));
+    s->tdev = TypedDev{s->t_pc, s->t_mask, T, s->t_type, s->t_tsort, s->t_inv, s->t_bptr, s->t_bto, ty->k_bond,
+                       ty->r0_bond};
+    s->typed = true;
+    s->layout_version += 1;  // no graph captured so far holds the typed kernels
+    k_tmaps<<<blocks_for(n, TPB), TPB, 0, s->stream>>>((int)n, s->id, s->tdev);
+    if ((rc2 = check_launch(s)) != VBC_OK) return bail(rc2);
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return bail(fail(VBC_ERR_CUDA, "typed setup failed"));
+    *out = s;
+    return VBC_OK;
+}
+
 void vbc_destroy(vbc_system* s)
 {
     if (!s) return;
@@ -1472,6 +1629,7 @@ int vbc_set_state(vbc_system* s, const double* pos, const double* vel, int64_t s
 int vbc_set_params(vbc_system* s, const vbc_pair_params* p)
 {
     VBC_TRY(check_sys(s));
+    if (s->typed) return fail(VBC_ERR_INVALID_ARG, "a multi-type system takes its parameters at creation");
     if (!p) return fail(VBC_ERR_INVALID_ARG, "params must not be NULL");
     const double rc = std::max(p->r_r, std::max(p->r_a, p->r_h));
     if (!(rc + s->skin <= s->rlist + 1e-12))
@@ -1491,6 +1649,7 @@ int vbc_set_params(vbc_system* s, const vbc_pair_params* p)
 int vbc_get_observables(vbc_system* s, vbc_observables* out, int32_t* z, int on_device)
 {
     VBC_TRY(check_sys(s));
+    if (s->typed) return fail(VBC_ERR_INVALID_ARG, "observables are defined for single-type systems only");
     if (!out) return fail(VBC_ERR_INVALID_ARG, "out must not be NULL");
     static_assert(VBC_ZHIST == ZHIST, "histogram bins of the header and the kernel differ");
     int* z_dev = nullptr;

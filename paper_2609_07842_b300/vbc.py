@@ -32,7 +32,7 @@ VBC_FP64 = 1
 K_REBUILD, K_COUNT, K_CHAIN, K_FORCE, K_ENERGY = range(5)
 
 #: every function the header declares
-EXPORTS = ("vbc_create_system", "vbc_build_neighbors", "vbc_compute_forces", "vbc_get_switch",
+EXPORTS = ("vbc_create_system", "vbc_create_typed_system", "vbc_build_neighbors", "vbc_compute_forces", "vbc_get_switch",
            "vbc_get_neighbors",
            "vbc_step_langevin", "vbc_get_state", "vbc_set_state", "vbc_set_params", "vbc_get_stats",
            "vbc_profile", "vbc_profile_read", "vbc_kernel_launches", "vbc_destroy", "vbc_last_error",
@@ -62,6 +62,15 @@ class _Config(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32), ("nlist_cap", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("inputs_on_device", ctypes.c_int32)]
 
+
+class _Types(ctypes.Structure):
+    _fields_ = [("ntypes", ctypes.c_int32), ("type", ctypes.c_void_p), ("pair", ctypes.c_void_p),
+                ("count_mask", ctypes.c_void_p), ("nbonds", ctypes.c_int64), ("bonds", ctypes.c_void_p),
+                ("k_bond", ctypes.c_double), ("r0_bond", ctypes.c_double)]
+
+
+#: largest number of particle types of a multi-type system
+MAX_TYPES = 8
 
 ZHIST = 32
 
@@ -116,6 +125,7 @@ def load() -> ctypes.CDLL:
     L = ctypes.CDLL(LIB_PATH)
     vp, dp, i64, i32 = ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_int
     L.vbc_create_system.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(vp)]
+    L.vbc_create_typed_system.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_Types), ctypes.POINTER(vp)]
     L.vbc_build_neighbors.argtypes = [vp]
     L.vbc_compute_forces.argtypes = [vp, vp, vp, vp, vp, i32]
     L.vbc_get_switch.argtypes = [vp, vp, vp, vp, i32]
@@ -241,6 +251,41 @@ class System:
         self.n = n
         self.box = b.copy()
         self.precision = precision
+
+    @classmethod
+    def typed(cls, pos, box, types, pair, count_mask, bonds=None, k_bond: float = 0.0, r0_bond: float = 1.0,
+              vel=None, skin: float = 0.4, seed: int = 1, nlist_cap: int = 0):
+        """A multi-type system (vbc_create_typed_system; FP64): types [n] in [0, T),
+        pair a T x T nested list of PairParams (symmetric; a type's f and delta from
+        its diagonal entry), count_mask T x T of 0/1 (row type counts column type),
+        bonds [m, 2] particle indices with energy k_bond/2 (r - r0_bond)^2.  Host
+        arrays; pos and vel as for System."""
+        L = load()
+        pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+        n = int(pos.shape[0])
+        vel = None if vel is None else np.ascontiguousarray(vel, dtype=np.float64).reshape(-1, 3)
+        t = np.ascontiguousarray(types, dtype=np.int32).reshape(-1)
+        T = len(pair)
+        tab = (PairParams * (T * T))(*[pair[a][b] for a in range(T) for b in range(T)])
+        m = np.ascontiguousarray(np.asarray(count_mask, dtype=np.int32).reshape(T * T))
+        bd = np.ascontiguousarray(np.zeros((0, 2)) if bonds is None else bonds, dtype=np.int64).reshape(-1, 2)
+        b = np.broadcast_to(np.asarray(box, dtype=np.float64), (3,))
+        cfg = _Config(n=n, box=(ctypes.c_double * 3)(*b), pos=ctypes.c_void_p(pos.ctypes.data),
+                      vel=ctypes.c_void_p(vel.ctypes.data) if vel is not None else None, params=params(),
+                      skin=skin, seed=seed, precision=VBC_FP64, nlist_cap=nlist_cap, stream=None,
+                      inputs_on_device=0)
+        ty = _Types(ntypes=T, type=ctypes.c_void_p(t.ctypes.data), pair=ctypes.cast(tab, ctypes.c_void_p),
+                    count_mask=ctypes.c_void_p(m.ctypes.data), nbonds=bd.shape[0],
+                    bonds=ctypes.c_void_p(bd.ctypes.data) if bd.shape[0] else None, k_bond=k_bond,
+                    r0_bond=r0_bond)
+        h = ctypes.c_void_p()
+        _check(L.vbc_create_typed_system(ctypes.byref(cfg), ctypes.byref(ty), ctypes.byref(h)))
+        self = cls.__new__(cls)
+        self._h = h
+        self.n = n
+        self.box = b.copy()
+        self.precision = VBC_FP64
+        return self
 
     # -- lifetime
     def close(self):
