@@ -65,6 +65,10 @@ def parse():
     ap.add_argument("--sweep", action="store_true",
                     help="cost-vs-valency curve (N=100k, rho 0.5, E_a 8, v in 1,2,4,6,8) and the paper-shape "
                          "point (N=10k, rho 0.05, E_a 2, dt 0.01, gamma 0.1, f = 1..6); one JSON line each")
+    ap.add_argument("--stickers", action="store_true",
+                    help="the multi-type sticker-chain workload (31,250 chains of 64 beads at bead density 0.3, "
+                         "stickers every 4th bead, FP64 typed path); one JSON line")
+    ap.add_argument("--sticker-chains", type=int, default=31_250)
     ap.add_argument("--leg", choices=("served", "batched"), default=None,
                     help="run only this optional leg and print its JSON object (the main run starts each "
                          "optional leg this way, in a process of its own)")
@@ -407,6 +411,38 @@ def run_batched(args):
     return out
 
 
+def stickers(args):
+    """Timesteps/s of bead-spring sticker chains (Sec. 4): spacers and stickers,
+    stickers attracting and counting stickers only at valency 1 (E_a 10), every
+    pair with the soft core, harmonic bonds k = 100, r0 = 1; FP64 typed path,
+    after an untimed equilibration."""
+    import torch
+    from paper_2609_07842_b300 import inputs, vbc
+    pos, L, t, bonds = inputs.sticker_chains(args.sticker_chains, 64, 0.3, seed=SEED)
+    vel = inputs.maxwell_velocities(pos.shape[0], KT, seed=SEED + 1)
+    spacer, mixed, sticker = vbc.params(E_a=0.0, f=2.0), vbc.params(E_a=0.0), vbc.params(E_a=10.0, f=1.0)
+    with vbc.System.typed(pos, L, t, [[spacer, mixed], [mixed, sticker]], [[0, 0], [0, 1]], bonds=bonds,
+                          k_bond=100.0, r0_bond=1.0, vel=vel, skin=SKIN, seed=SEED) as s:
+        s.step(args.equil, DT, KT, GAMMA)
+        torch.cuda.synchronize()
+        r0 = s.stats().rebuilds
+        t0 = time.perf_counter()
+        s.step(args.steps, DT, KT, GAMMA)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        st = s.stats()
+    n = pos.shape[0]
+    print(json.dumps({"metric": "sticker-chain timesteps/s", "value": args.steps / sec, "unit": "timesteps/s",
+                      "ms_per_step": 1e3 * sec / args.steps, "particle_steps_per_s": n * args.steps / sec,
+                      "steps": args.steps, "steps_per_rebuild": args.steps / max(st.rebuilds - r0, 1),
+                      "dtype": "f64", "timing": "host clock around the steps, device synchronised on both sides",
+                      "config": {"workload": (f"{args.sticker_chains:,} chains x 64 beads ({n:,} beads), bead "
+                                              f"density 0.3, stickers every 4th bead (valency 1, E_a 10, count "
+                                              f"stickers only), harmonic bonds k 100 r0 1, BAOAB dt {DT}"),
+                                 "equilibration_steps": args.equil}}), flush=True)
+    return 0
+
+
 def served_leg(args):
     """The served stream through the serving loop, and the same stream one system
     at a time."""
@@ -447,6 +483,8 @@ def main():
         return reference_main(args)
     if args.leg:
         return leg_main(args)
+    if args.stickers:
+        return stickers(args)
     if args.profile_run:
         return profile_run(args)
     if args.sweep:
