@@ -96,6 +96,62 @@ def test_orthorhombic_box_allowed_in_fp64_until_device_needed(lib):
         assert not h.value
 
 
+# ----------------------------------------------------------------- multi-type creation (host checks)
+def _typed(n=100, T=2, types=None, pair=None, mask=None, bonds=None, k_bond=100.0, r0=1.0,
+           prec=vbc.VBC_FP64):
+    c, keep = _cfg(n=n, prec=prec)
+    t = np.ascontiguousarray(np.zeros(n) if types is None else types, dtype=np.int32)
+    P = pair if pair is not None else [[vbc.params(E_a=0.0), vbc.params(E_a=0.0)],
+                                       [vbc.params(E_a=0.0), vbc.params(E_a=10.0, f=1.0)]][:T]
+    tab = (vbc.PairParams * (T * T))(*[P[a][b] for a in range(T) for b in range(T)])
+    m = np.ascontiguousarray(np.asarray([[0, 0], [0, 1]] if mask is None else mask, dtype=np.int32).reshape(-1))
+    bd = np.ascontiguousarray(np.zeros((0, 2)) if bonds is None else bonds, dtype=np.int64).reshape(-1, 2)
+    ty = vbc._Types(ntypes=T, type=ctypes.c_void_p(t.ctypes.data), pair=ctypes.cast(tab, ctypes.c_void_p),
+                    count_mask=ctypes.c_void_p(m.ctypes.data), nbonds=bd.shape[0],
+                    bonds=ctypes.c_void_p(bd.ctypes.data) if bd.shape[0] else None, k_bond=k_bond, r0_bond=r0)
+    return c, ty, (keep, t, tab, m, bd)
+
+
+@pytest.mark.parametrize("kw,needle", [
+    (dict(prec=vbc.VBC_FP32_SPLIT), "VBC_FP64"),
+    (dict(T=0), "ntypes"),
+    (dict(types=np.full(100, 2)), "type of particle"),
+    (dict(types=np.full(100, -1)), "type of particle"),
+    (dict(mask=[[0, 0], [0, 3]]), "0 or 1"),
+    (dict(pair=[[vbc.params(E_a=0.0), vbc.params(E_a=1.0)], [vbc.params(E_a=0.0), vbc.params()]]), "symmetric"),
+    (dict(pair=[[vbc.params(r_a=0.5), vbc.params()], [vbc.params(), vbc.params()]]), "pair parameters"),
+    (dict(bonds=[[0, 100]]), "bond 0"),
+    (dict(bonds=[[0, 1], [5, 5]]), "bond 1"),
+    (dict(k_bond=-1.0), "k_bond"),
+    (dict(r0=float("inf")), "k_bond"),
+])
+def test_typed_create_rejects_bad_arguments(lib, kw, needle):
+    if kw.get("T") == 0:
+        c, ty, _keep = _typed()
+        ty.ntypes = 0
+    else:
+        c, ty, _keep = _typed(**kw)
+    h = ctypes.c_void_p()
+    rc = lib.vbc_create_typed_system(ctypes.byref(c), ctypes.byref(ty), ctypes.byref(h))
+    assert rc == vbc.VBC_ERR_INVALID_ARG
+    assert needle in lib.vbc_last_error().decode()
+    assert not h.value
+
+
+def test_typed_create_valid_until_device_needed(lib):
+    """A valid two-type description with bonds passes every host check; without a
+    GPU the call then fails with a CUDA error."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("covered by the GPU tests")
+    c, ty, _keep = _typed(types=np.arange(100) % 2, bonds=[[k, k + 1] for k in range(99)])
+    h = ctypes.c_void_p()
+    rc = lib.vbc_create_typed_system(ctypes.byref(c), ctypes.byref(ty), ctypes.byref(h))
+    assert rc in (vbc.VBC_ERR_CUDA, vbc.VBC_ERR_OOM)
+    assert not h.value
+    assert lib.vbc_create_typed_system(None, None, None) == vbc.VBC_ERR_INVALID_ARG
+
+
 # ----------------------------------------------------------------- serving admission estimate
 def test_device_bytes_estimate_scales_with_n(lib):
     """vbc_estimate_device_bytes touches no device: it sizes the arrays of a
