@@ -115,6 +115,7 @@ struct vbc_system {
     Coef* t_pc = nullptr;
     int *t_mask = nullptr, *t_type = nullptr, *t_tsort = nullptr, *t_inv = nullptr, *t_bto = nullptr;
     long long* t_bptr = nullptr;
+    long long t_nbto = 0;  // entries of t_bto
     void *post = nullptr, *xref = nullptr;
     int cur = 0;
     uint16_t* nbr = nullptr;
@@ -763,7 +764,12 @@ long long device_bytes(const vbc_system* s)
     z.npad = s->npad;
     z.ncell = s->geom.ncell;
     z.smax = s->smax;
-    return device_bytes_of(s->n, s->prec, z);
+    long long b = device_bytes_of(s->n, s->prec, z);
+    if (s->typed) {  // pair table and mask, type, sorted-type and inverse maps, bond partners
+        const long long T = s->tdev.T;
+        b += T * T * ((long long)sizeof(Coef) + 4) + 3 * s->n * 4 + (s->n + 1) * 8 + s->t_nbto * 4;
+    }
+    return b;
 }
 
 bool needs_growth(const vbc_system* s) { return s->st_host->overflow || s->st_host->stage_overflow; }
@@ -1454,6 +1460,7 @@ int vbc_create_typed_system(const vbc_config* cfg, const vbc_types* ty, vbc_syst
     TALLOC(dalloc(s->t_inv, (size_t)n));
     TALLOC(dalloc(s->t_bptr, (size_t)n + 1));
     TALLOC(dalloc(s->t_bto, bto.size()));
+    s->t_nbto = (long long)bto.size();
 #undef TALLOC
     std::vector<int> mask((size_t)T * T), type((size_t)n);
     for (int k = 0; k < T * T; ++k) mask[(size_t)k] = ty->count_mask[k];
