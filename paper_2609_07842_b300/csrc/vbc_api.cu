@@ -1001,8 +1001,9 @@ int launch_pair_graph(vbc_system* s, const StepArgs& a)
     if (!pg.exec || pg.dt != a.dt || pg.c1 != a.c1 || pg.c2 != a.c2 || pg.layout_version != s->layout_version)
         VBC_TRY(build_pair_graph<M>(s, s->cur, a));
     VBC_CUDA(cudaGraphLaunch(pg.exec, s->stream));
-    s->launches += 12;  // two gates, two sets of count, count rows, chain, force rows, step (rebuild bodies
-                        // counted on the device)
+    // two gates, and twice count, count rows, chain, force rows, step (typed: count, chain, force, step);
+    // rebuild bodies are counted on the device
+    s->launches += s->typed ? 10 : 12;
     return VBC_OK;
 }
 
