@@ -1743,7 +1743,7 @@ int vbc_profile_read(vbc_system* s, int which, double* total_ms, int64_t* launch
 int64_t vbc_kernel_launches(vbc_system* s)
 {
     if (!s || check_sys(s) != VBC_OK || read_status(s) != VBC_OK) return -1;
-    return s->launches + REBUILD_KERNELS * s->st_host->graph_rebuild_runs;
+    return s->launches + (REBUILD_KERNELS + (s->typed ? 1 : 0)) * s->st_host->graph_rebuild_runs;  // typed: k_tmaps
 }
 
 int vbc_batch_create(vbc_system* const* systems, int32_t count, vbc_batch** out)
