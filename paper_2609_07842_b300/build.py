@@ -8,6 +8,7 @@ evaluation); the C ABI it exports is declared in include/vbc.h.
 """
 from __future__ import annotations
 
+import glob
 import os
 import subprocess
 import sys
@@ -15,9 +16,9 @@ import sys
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 SRCS = [os.path.join(PKG, "csrc", f) for f in ("vbc_api.cu", "vbc_noalloc.cu", "vbc_serve.cpp")]
-DEPS = [os.path.join(PKG, "csrc", f) for f in ("vbc_api.cu", "vbc_noalloc.cu", "vbc_serve.cpp", "vbc_kernels.cuh",
-                                               "vbc_device.cuh")] + [
-    os.path.join(ROOT, "include", "vbc.h")]
+# every source and header of the library: a change to any of them rebuilds it
+DEPS = sorted(glob.glob(os.path.join(PKG, "csrc", "*.cu")) + glob.glob(os.path.join(PKG, "csrc", "*.cuh")) +
+              glob.glob(os.path.join(PKG, "csrc", "*.cpp")) + glob.glob(os.path.join(ROOT, "include", "*.h")))
 LIB = os.path.join(PKG, "libvbc.so")
 
 NVCC_FLAGS = [

@@ -241,6 +241,7 @@ __global__ void k_clear_halt(Status* st)
     st->stage_overflow = 0;
     st->frozen = 0;
     st->crowded = 0;
+    st->bad_input = 0;
     st->rebuild = 1;
 }
 
@@ -827,6 +828,9 @@ int halt_error(vbc_system* s)
     if (s->st_host->crowded)
         return fail(VBC_ERR_UNSTABLE, "more than %d particles in one cell: the system has collapsed or blown up",
                     MAX_CELL);
+    if (s->st_host->bad_input)
+        return fail(VBC_ERR_UNSTABLE, "a loaded position or velocity is non-finite or beyond the fixed-point range "
+                                      "(|x| < 1024 L, |v| < 2^22)");
     if (s->st_host->frozen) return fail(VBC_ERR_UNSTABLE, "a position, velocity or force became non-finite");
     if (s->st_host->bad_index) return fail(VBC_ERR_CUDA, "internal error: a count met a particle index out of range");
     return VBC_OK;
@@ -1124,11 +1128,13 @@ int load_state(vbc_system* s, const double* pos, const double* vel, int on_devic
     // caller arrays -> staging (xt holds positions, vt velocities) -> sorted state
     VBC_TRY(stage_in(s, (double*)s->xt, pos, 3 * (size_t)s->n, on_device));
     if (vel) VBC_TRY(stage_in(s, (double*)s->vt, vel, 3 * (size_t)s->n, on_device));
+    // a new state clears every halt (and requests a rebuild); the load itself may raise bad_input
+    k_clear_halt<<<1, 1, 0, s->stream>>>(s->st);
+    VBC_TRY(check_launch(s));
     k_load_state<M><<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>((int)s->n, s->geom, (const double*)s->xt,
                                                                   vel ? (const double*)s->vt : nullptr, s->id,
-                                                                  s->x, s->v, (typename M::pos_t*)s->pos[s->cur]);
-    VBC_TRY(check_launch(s));
-    k_clear_halt<<<1, 1, 0, s->stream>>>(s->st);  // also requests a rebuild
+                                                                  s->x, s->v, (typename M::pos_t*)s->pos[s->cur],
+                                                                  s->st);
     return check_launch(s);
 }
 

@@ -91,12 +91,13 @@ struct Status {
                         // neighbours (k_count_near)
     int ngen;           // particles whose force k_force_rows forms (k_count_near, k_chain)
     int bad_index;      // 1: a count was handed a particle index outside [0, n) (k_count_rows; an internal error)
+    int bad_input;      // 1: a loaded position or velocity was non-finite or beyond the fixed-point range (k_load_state)
 };
 
 // Work stops (until the host intervenes) once any of these is raised.
 __device__ __forceinline__ bool halted(const Status* st)
 {
-    return (st->frozen | st->crowded | st->overflow | st->stage_overflow) != 0;
+    return (st->frozen | st->crowded | st->overflow | st->stage_overflow | st->bad_input) != 0;
 }
 
 // ---------------------------------------------------------------- Philox4x32-10

@@ -1972,38 +1972,46 @@ __global__ void __launch_bounds__(RED_TPB) k_reduce_final(int nb, const double* 
 
 // ================================================================ state I/O
 // Caller order [n][3] doubles -> internal state in sorted order, and the
-// fixed-point words.  FP32 mode: X = round(x 2^52 / L) and V = round(v 2^40) (int64).
+// fixed-point words.  FP32 mode: X = round(x 2^52 / L) and V = round(v 2^40)
+// (int64), which hold |x| < 1024 L and |v| < 2^22; a value beyond that, or a
+// non-finite one (which the integer state could not carry), raises bad_input
+// and halts the system until the next load.
 template <class M>
 __global__ void __launch_bounds__(TPB) k_load_state(int n, Geom g, const double* __restrict__ pos_in,
                                                     const double* __restrict__ vel_in, const int* __restrict__ id,
                                                     void* __restrict__ xs, void* __restrict__ vs,
-                                                    typename M::pos_t* __restrict__ pos)
+                                                    typename M::pos_t* __restrict__ pos, Status* st)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int o = id[i];
+    bool bad = false;
     if constexpr (M::fp64) {
         double xx[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             xx[d] = pos_in[3 * (size_t)o + d];
+            const double v = vel_in ? vel_in[3 * (size_t)o + d] : 0.0;
+            bad |= !isfinite(xx[d]) || !isfinite(v);
             ((double*)xs)[(size_t)d * n + i] = xx[d];
-            ((double*)vs)[(size_t)d * n + i] = vel_in ? vel_in[3 * (size_t)o + d] : 0.0;
+            ((double*)vs)[(size_t)d * n + i] = v;
         }
         pos[i] = ModeF64::from_x(xx[0], xx[1], xx[2], g);
     } else {
         int w[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const double x = pos_in[3 * (size_t)o + d];
-            const long long P = __double2ll_rn(x * g.inv32[d] * 1048576.0);  // x 2^52 / L
+            const double xf = pos_in[3 * (size_t)o + d] * g.inv32[d] * 1048576.0;  // x 2^52 / L
+            const double vf = (vel_in ? vel_in[3 * (size_t)o + d] : 0.0) * 1099511627776.0;  // v 2^40
+            bad |= !(fabs(xf) < 4611686018427387904.0) || !(fabs(vf) < 4611686018427387904.0);  // 2^62
+            const long long P = bad ? 0ll : __double2ll_rn(xf);
             ((long long*)xs)[(size_t)d * n + i] = P;
             w[d] = ModeF32::word(P);
-            const double v = vel_in ? vel_in[3 * (size_t)o + d] : 0.0;
-            ((long long*)vs)[(size_t)d * n + i] = __double2ll_rn(v * 1099511627776.0);  // 2^40
+            ((long long*)vs)[(size_t)d * n + i] = bad ? 0ll : __double2ll_rn(vf);
         }
         pos[i] = make_int4(w[0], w[1], w[2], 0);
     }
+    if (bad) st->bad_input = 1;
 }
 
 template <class M>

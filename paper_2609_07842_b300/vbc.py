@@ -414,19 +414,34 @@ class System:
 def compute_forces_noalloc(pos, box: float, prm: PairParams, F, counts=None, stream=None):
     """Counts and forces of one small system without any device allocation
     (vbc_compute_forces_noalloc).  pos [n,3], F [n,3] and counts [n] are CUDA
-    float64 tensors; the library's static scratch holds at most NOALLOC_MAX_N
-    particles.  Meant for callers that cannot allocate device memory."""
+    float64 tensors on one device; the library's static scratch holds at most
+    NOALLOC_MAX_N particles.  Meant for callers that cannot allocate device
+    memory.  Shapes and devices are checked here, before the library is
+    called, so that a wrong buffer never reaches a kernel."""
     import torch
-    for t in (pos, F) + ((counts,) if counts is not None else ()):
+    tensors = [("pos", pos), ("F", F)] + ([("counts", counts)] if counts is not None else [])
+    for name, t in tensors:
         if not (_is_torch(t) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
-            raise TypeError("pos, F and counts must be contiguous CUDA float64 tensors")
-    if stream is None:
-        stream = torch.cuda.current_stream().cuda_stream
+            raise TypeError(f"{name} must be a contiguous CUDA float64 tensor")
+    if pos.dim() != 2 or pos.shape[1] != 3:
+        raise ValueError(f"pos must have shape (n, 3), not {tuple(pos.shape)}")
+    n = int(pos.shape[0])
+    if tuple(F.shape) != (n, 3):
+        raise ValueError(f"F must have shape ({n}, 3), not {tuple(F.shape)}")
+    if counts is not None and tuple(counts.shape) != (n,):
+        raise ValueError(f"counts must have shape ({n},), not {tuple(counts.shape)}")
+    dev = pos.device
+    for name, t in tensors:
+        if t.device != dev:
+            raise ValueError(f"{name} is on {t.device}, pos on {dev}: all tensors must share one device")
     b = (ctypes.c_double * 3)(*np.broadcast_to(np.asarray(box, dtype=np.float64), (3,)))
-    _check(load().vbc_compute_forces_noalloc(int(pos.shape[0]), b, ctypes.c_void_p(pos.data_ptr()),
-                                             ctypes.byref(prm), ctypes.c_void_p(F.data_ptr()),
-                                             ctypes.c_void_p(counts.data_ptr()) if counts is not None else None,
-                                             ctypes.c_void_p(stream) if stream else None))
+    with torch.cuda.device(dev):
+        if stream is None:
+            stream = torch.cuda.current_stream(dev).cuda_stream
+        _check(load().vbc_compute_forces_noalloc(n, b, ctypes.c_void_p(pos.data_ptr()), ctypes.byref(prm),
+                                                 ctypes.c_void_p(F.data_ptr()),
+                                                 ctypes.c_void_p(counts.data_ptr()) if counts is not None else None,
+                                                 ctypes.c_void_p(stream) if stream else None))
 
 
 def _host_config(pos, box, prm: PairParams | None, vel, skin: float, seed: int, precision: int,

@@ -44,6 +44,14 @@ def test_library_targets_sm103a():
     assert "arch=compute_103a,code=sm_103a" in " ".join(vbuild.NVCC_FLAGS)
 
 
+def test_every_source_triggers_a_rebuild():
+    """A change to any source or header of the library makes build() recompile it,
+    so a stale libvbc.so cannot pass for the current sources."""
+    csrc = os.path.join(ROOT, "paper_2609_07842_b300", "csrc")
+    srcs = {os.path.join(csrc, f) for f in os.listdir(csrc)} | {os.path.join(ROOT, "include", "vbc.h")}
+    assert srcs <= set(vbuild.DEPS)
+
+
 def _cfg(n=100, box=(12.0, 12.0, 12.0), prec=vbc.VBC_FP32_SPLIT, skin=0.4, **prm):
     pos = np.zeros((max(n, 1), 3))
     c = vbc._Config(n=n, box=(ctypes.c_double * 3)(*box), pos=ctypes.c_void_p(pos.ctypes.data), vel=None,
