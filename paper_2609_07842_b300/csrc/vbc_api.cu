@@ -154,17 +154,22 @@ struct vbc_system {
     int64_t step = 0;
     int64_t launches = 0;
 
-    // CUDA graphs of two FINISH_START iterations, one per parity of the
-    // position buffer at the first of the two (see steps_impl)
+    // CUDA graphs of the loop iterations (see run_iterations): one per kind of
+    // iteration (G_OPEN, G_PAIR, G_SINGLE, G_CLOSE) and parity of the position
+    // buffer it starts on, all captured together for one set of step
+    // coefficients and one layout
     bool use_graphs = true;
     bool capturing = false;
     cudaStream_t cap_stream = nullptr, body_stream = nullptr;
-    struct PairGraph {
-        cudaGraphExec_t exec = nullptr;
-        double dt = 0, c1 = 0, c2 = 0;
-        long long layout_version = -1;
-    } pair_graph[2];
+    cudaGraphExec_t graphs[4][2] = {};
+    double g_dt = 0, g_c1 = 0, g_c2 = 0;
+    long long g_layout = -1;
     long long layout_version = 0;  // bumps when parameters or capacities (kernel arguments) change
+    // The force slots hold the forces of the current state, as the loop's last
+    // iteration left them: the next run of steps opens with the update alone.
+    // Cleared by every call that changes the state, the sorted order or the
+    // parameters, or that writes the force slots by another path.
+    bool force_fresh = false;
 
     // per-kernel event timing
     bool prof = false;
@@ -459,8 +464,9 @@ void free_all(vbc_system* s)
     s->red_host = nullptr;
     for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
     s->ev.clear();
-    for (auto& pg : s->pair_graph)
-        if (pg.exec) cudaGraphExecDestroy(pg.exec);
+    for (auto& row : s->graphs)
+        for (auto& ex : row)
+            if (ex) cudaGraphExecDestroy(ex);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     if (s->body_stream) cudaStreamDestroy(s->body_stream);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -685,6 +691,14 @@ int force_rebuild_flag(vbc_system* s)
     return check_launch(s);
 }
 
+// After a build outside the step loop the list is current: no rebuild is due
+// (the next pass would otherwise sort and build again, to the same result).
+int clear_rebuild_flag(vbc_system* s)
+{
+    k_set_flag<<<1, 1, 0, s->stream>>>(s->st, 0, 0);
+    return check_launch(s);
+}
+
 int read_status(vbc_system* s)
 {
     VBC_CUDA(cudaMemcpyAsync(s->st_host, s->st, sizeof(Status), cudaMemcpyDeviceToHost, s->stream));
@@ -781,6 +795,7 @@ int grow(vbc_system* s)
 {
     VBC_CUDA(cudaStreamSynchronize(s->stream));
     s->grows += 1;
+    s->force_fresh = false;
     const Status& h = *s->st_host;
     if (h.overflow) {
         const int need = h.max_nnb;
@@ -840,6 +855,7 @@ int halt_error(vbc_system* s)
 template <class M>
 int compute_impl(vbc_system* s, double* F_dev, double* n_dev, bool energy)
 {
+    s->force_fresh = false;  // the force slots are written by the evaluation path
     for (int attempt = 0;; ++attempt) {
         VBC_CUDA(cudaMemsetAsync(s->win, 0, sizeof(long long), s->stream));
         VBC_CUDA(cudaMemsetAsync(&s->st->nwin, 0, 3 * sizeof(int), s->stream));  // nwin, nu, ngen
@@ -863,10 +879,12 @@ int compute_impl(vbc_system* s, double* F_dev, double* n_dev, bool energy)
 template <class M>
 int observables_impl(vbc_system* s, vbc_observables* out, int* z_dev)
 {
+    s->force_fresh = false;  // a due rebuild re-sorts the particles
     if (!s->obs) VBC_TRY(dalloc(s->obs, 2 + ZHIST));
     for (int attempt = 0;; ++attempt) {
         VBC_CUDA(cudaMemsetAsync(s->obs, 0, (2 + ZHIST) * sizeof(unsigned long long), s->stream));
         VBC_TRY(enqueue_rebuild<M>(s));
+        VBC_TRY(clear_rebuild_flag(s));
         k_observe<M><<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>(
             (int)s->n, s->geom, s->coef, (const typename M::pos_t*)s->pos[s->cur], s->caps(), s->aux(), s->nbr,
             s->nnb, s->id, z_dev, s->obs, s->st);
@@ -885,6 +903,21 @@ int observables_impl(vbc_system* s, vbc_observables* out, int* z_dev)
     return VBC_OK;
 }
 
+template <class M>
+int enqueue_force_epi(vbc_system* s, const StepArgs& a, int epi)
+{
+    switch (epi) {
+    case EPI_START: return enqueue_force<M, EPI_START>(s, a);
+    case EPI_FINISH: return enqueue_force<M, EPI_FINISH>(s, a);
+    case EPI_FINISH_START: return enqueue_force<M, EPI_FINISH_START>(s, a);
+    default: return enqueue_force<M, EPI_FORCE>(s, a);
+    }
+}
+
+// Epilogue of loop iteration `it` of nsteps: iteration 0 opens step 0, the
+// last one closes step nsteps - 1, the others close one step and open the next.
+int epi_of(int64_t it, int64_t nsteps) { return it == 0 ? EPI_START : (it < nsteps ? EPI_FINISH_START : EPI_FINISH); }
+
 // One loop iteration with direct launches: gate, rebuild (early exit unless
 // due), count, chain, force with the epilogue of iteration `it`.
 template <class M>
@@ -894,9 +927,26 @@ int direct_iteration(vbc_system* s, const StepArgs& a, int64_t it, int64_t nstep
     VBC_TRY(check_launch(s));
     VBC_TRY(enqueue_rebuild<M>(s));
     VBC_TRY(enqueue_count_chain<M>(s, nullptr, false));
-    if (it == 0) return enqueue_force<M, EPI_START>(s, a);
-    if (it < nsteps) return enqueue_force<M, EPI_FINISH_START>(s, a);
-    return enqueue_force<M, EPI_FINISH>(s, a);
+    return enqueue_force_epi<M>(s, a, epi_of(it, nsteps));
+}
+
+// Opening iteration when the force slots already hold the forces of the
+// current state (force_fresh): the update alone, as iteration 0 of the loop
+// (the noise counter is set to iteration 0 directly, with no gate).
+template <class M>
+int open_from_resident_force(vbc_system* s, const StepArgs& a)
+{
+    using pos_t = typename M::pos_t;
+    k_set_iter<<<1, 1, 0, s->stream>>>(s->st, 0, s->step);
+    VBC_TRY(check_launch(s));
+    {
+        Timed t(s, VBC_K_FORCE);
+        k_step<M, EPI_START><<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>(
+            (int)s->n, s->geom, s->aux(), s->id, (pos_t*)s->pos[s->cur ^ 1], (const pos_t*)s->xref, a, s->st);
+    }
+    VBC_TRY(check_launch(s));
+    s->cur ^= 1;
+    return VBC_OK;
 }
 
 int graph_error(vbc_system* s, const char* what, cudaError_t e)
@@ -905,20 +955,29 @@ int graph_error(vbc_system* s, const char* what, cudaError_t e)
     return fail(VBC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-// Captures two FINISH_START iterations starting on position buffer c into
-// one executable graph.  Each iteration is: k_gate -> IF(rebuild due){the
-// nine rebuild kernels} -> count -> chain -> force, so steps that need no
-// rebuild launch no rebuild kernel at all.
-// Captures the two iterations into graph g, as nodes that depend on no
-// other node of g (so the iterations of several systems captured into one
-// graph run side by side).
+// Kinds of captured iterations: G_OPEN opens step 0 (forces of the initial
+// state, then B A O A), G_PAIR and G_SINGLE close one step and open the next
+// (twice and once), G_CLOSE closes the last step.
+enum GraphKind { G_OPEN = 0, G_PAIR = 1, G_SINGLE = 2, G_CLOSE = 3, G_NKIND = 4 };
+constexpr int KIND_EPIS[G_NKIND][2] = {{EPI_START, -1}, {EPI_FINISH_START, EPI_FINISH_START},
+                                       {EPI_FINISH_START, -1}, {EPI_FINISH, -1}};
+int kind_iters(int k) { return k == G_PAIR ? 2 : 1; }
+int kind_flips(int k) { return k == G_OPEN || k == G_SINGLE ? 1 : 0; }  // position-buffer flips, mod 2
+int iter_launches(const vbc_system* s) { return s->typed ? 5 : 6; }    // gate, count(s), chain, force, step
+
+// Captures the iterations of kind `kind` starting on position buffer c into
+// graph g.  Each iteration is: k_gate -> IF(rebuild due){the rebuild kernels}
+// -> count -> chain -> force, so steps that need no rebuild launch no rebuild
+// kernel at all.  The nodes depend on no other node of g, so that the
+// iterations of several systems captured into one graph run side by side.
 template <class M>
-int capture_pair(vbc_system* s, int c, const StepArgs& a, cudaGraph_t g)
+int capture_iters(vbc_system* s, int c, const StepArgs& a, int kind, cudaGraph_t g)
 {
     if (!s->cap_stream) VBC_CUDA(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
     if (!s->body_stream) VBC_CUDA(cudaStreamCreateWithFlags(&s->body_stream, cudaStreamNonBlocking));
+    const int niter = kind_iters(kind);
     cudaGraphConditionalHandle h[2];
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < niter; ++k) {
         cudaError_t e = cudaGraphConditionalHandleCreate(&h[k], g, 0, cudaGraphCondAssignDefault);
         if (e != cudaSuccess) return graph_error(s, "cudaGraphConditionalHandleCreate", e);
     }
@@ -930,7 +989,7 @@ int capture_pair(vbc_system* s, int c, const StepArgs& a, cudaGraph_t g)
     int rc = VBC_OK;
     cudaError_t e = cudaStreamBeginCaptureToGraph(s->cap_stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) rc = graph_error(s, "cudaStreamBeginCaptureToGraph", e);
-    for (int k = 0; k < 2 && rc == VBC_OK; ++k) {
+    for (int k = 0; k < niter && rc == VBC_OK; ++k) {
         k_gate<<<1, 1, 0, s->cap_stream>>>(s->st, h[k], 1);
         cudaStreamCaptureStatus cst;
         cudaGraph_t cg = nullptr;
@@ -960,7 +1019,7 @@ int capture_pair(vbc_system* s, int c, const StepArgs& a, cudaGraph_t g)
         e = cudaStreamEndCapture(s->body_stream, &body);
         if (rc == VBC_OK && e != cudaSuccess) rc = graph_error(s, "end of the rebuild body capture", e);
         if (rc == VBC_OK) rc = enqueue_count_chain<M>(s, nullptr, false);
-        if (rc == VBC_OK) rc = enqueue_force<M, EPI_FINISH_START>(s, a);
+        if (rc == VBC_OK) rc = enqueue_force_epi<M>(s, a, KIND_EPIS[kind][k]);
     }
     cudaGraph_t out = nullptr;
     e = cudaStreamEndCapture(s->cap_stream, &out);
@@ -971,43 +1030,93 @@ int capture_pair(vbc_system* s, int c, const StepArgs& a, cudaGraph_t g)
     return rc;
 }
 
-template <class M>
-int build_pair_graph(vbc_system* s, int c, const StepArgs& a)
+void destroy_graphs(vbc_system* s)
 {
-    auto& pg = s->pair_graph[c];
-    if (pg.exec) {
-        cudaGraphExecDestroy(pg.exec);
-        pg.exec = nullptr;
-    }
-    cudaGraph_t g = nullptr;
-    VBC_CUDA(cudaGraphCreate(&g, 0));
-    int rc = capture_pair<M>(s, c, a, g);
-    if (rc == VBC_OK) {
-        const cudaError_t e = cudaGraphInstantiate(&pg.exec, g, 0);
-        if (e != cudaSuccess) rc = graph_error(s, "cudaGraphInstantiate", e);
-    }
-    cudaGraphDestroy(g);
-    if (rc != VBC_OK) {
-        pg.exec = nullptr;
-        return rc;
-    }
-    pg.dt = a.dt;
-    pg.c1 = a.c1;
-    pg.c2 = a.c2;
-    pg.layout_version = s->layout_version;
+    for (auto& row : s->graphs)
+        for (auto& ex : row)
+            if (ex) {
+                cudaGraphExecDestroy(ex);
+                ex = nullptr;
+            }
+    s->g_layout = -1;
+}
+
+// Captures every kind of iteration for both parities of the position buffer,
+// so that no later run of steps with these coefficients captures anything.
+template <class M>
+int build_graphs(vbc_system* s, const StepArgs& a)
+{
+    destroy_graphs(s);
+    for (int kind = 0; kind < G_NKIND; ++kind)
+        for (int c = 0; c < 2; ++c) {
+            cudaGraph_t g = nullptr;
+            VBC_CUDA(cudaGraphCreate(&g, 0));
+            int rc = capture_iters<M>(s, c, a, kind, g);
+            if (rc == VBC_OK) {
+                const cudaError_t e = cudaGraphInstantiate(&s->graphs[kind][c], g, 0);
+                if (e != cudaSuccess) rc = graph_error(s, "cudaGraphInstantiate", e);
+            }
+            cudaGraphDestroy(g);
+            if (rc != VBC_OK) {
+                destroy_graphs(s);
+                return rc;
+            }
+        }
+    s->g_dt = a.dt;
+    s->g_c1 = a.c1;
+    s->g_c2 = a.c2;
+    s->g_layout = s->layout_version;
     return VBC_OK;
 }
 
 template <class M>
-int launch_pair_graph(vbc_system* s, const StepArgs& a)
+int launch_graph(vbc_system* s, const StepArgs& a, int kind)
 {
-    auto& pg = s->pair_graph[s->cur];
-    if (!pg.exec || pg.dt != a.dt || pg.c1 != a.c1 || pg.c2 != a.c2 || pg.layout_version != s->layout_version)
-        VBC_TRY(build_pair_graph<M>(s, s->cur, a));
-    VBC_CUDA(cudaGraphLaunch(pg.exec, s->stream));
-    // two gates, and twice count, count rows, chain, force rows, step (typed: count, chain, force, step);
-    // rebuild bodies are counted on the device
-    s->launches += s->typed ? 10 : 12;
+    if (s->g_layout != s->layout_version || s->g_dt != a.dt || s->g_c1 != a.c1 || s->g_c2 != a.c2)
+        VBC_TRY(build_graphs<M>(s, a));
+    VBC_CUDA(cudaGraphLaunch(s->graphs[kind][s->cur], s->stream));
+    s->cur ^= kind_flips(kind);
+    // gates, counts, chains, forces and updates; rebuild bodies are counted on the device
+    s->launches += (int64_t)iter_launches(s) * kind_iters(kind);
+    return VBC_OK;
+}
+
+// Runs loop iterations it .. it_end - 1 of a call of nsteps steps, through the
+// graphs unless per-kernel timing is on.
+template <class M>
+int run_range(vbc_system* s, const StepArgs& a, int64_t it, int64_t it_end, int64_t nsteps)
+{
+    while (it < it_end) {
+        if (s->use_graphs && !s->prof) {
+            const int kind = it == 0 ? G_OPEN
+                                     : (it + 1 <= nsteps - 1 && it + 1 < it_end ? G_PAIR
+                                                                                 : (it < nsteps ? G_SINGLE : G_CLOSE));
+            VBC_TRY(launch_graph<M>(s, a, kind));
+            it += kind_iters(kind);
+        } else {
+            VBC_TRY(direct_iteration<M>(s, a, it, nsteps));
+            ++it;
+        }
+    }
+    return VBC_OK;
+}
+
+// Opens a run of steps at loop iteration it0 (sets the device iteration
+// counter; from the resident forces when it0 == 0 and they are fresh) and
+// returns the first iteration still to run.
+template <class M>
+int open_range(vbc_system* s, const StepArgs& a, int64_t it0, int64_t& next)
+{
+    if (it0 == 0 && s->force_fresh) {
+        s->force_fresh = false;
+        VBC_TRY(open_from_resident_force<M>(s, a));
+        next = 1;
+        return VBC_OK;
+    }
+    s->force_fresh = false;
+    k_set_iter<<<1, 1, 0, s->stream>>>(s->st, it0 - 1, s->step);
+    VBC_TRY(check_launch(s));
+    next = it0;
     return VBC_OK;
 }
 
@@ -1031,30 +1140,26 @@ StepArgs step_args(const vbc_system* s, double dt, double kT, double gamma)
 
 // Iteration 0 opens step 0 (forces at the initial state, then B A O A);
 // iteration it in [1, nsteps) closes step it-1 and opens step it;
-// iteration nsteps closes the last step.  Iterations 1..nsteps-1 run in
-// pairs through a CUDA graph unless per-kernel timing is on.  Runs
-// iterations it0..nsteps; when a list build overflows it grows the
-// capacities and resumes from the overflowing iteration.
+// iteration nsteps closes the last step.  Each kind of iteration runs as a
+// CUDA graph unless per-kernel timing is on; iteration 0 is the update alone
+// when the force slots hold the current state's forces.  Runs iterations
+// it0..nsteps; when a list build overflows it grows the capacities and
+// resumes from the overflowing iteration.  On success the force slots hold
+// the forces of the final state.
 template <class M>
 int run_iterations(vbc_system* s, const StepArgs& a, int64_t it0, int64_t nsteps)
 {
     for (int attempt = 0;; ++attempt) {
-        k_set_iter<<<1, 1, 0, s->stream>>>(s->st, it0 - 1, s->step);
-        VBC_TRY(check_launch(s));
         const int cur0 = s->cur;
         int64_t it = it0;
-        while (it <= nsteps) {
-            if (s->use_graphs && !s->prof && it >= 1 && it + 1 <= nsteps - 1) {
-                VBC_TRY(launch_pair_graph<M>(s, a));  // two buffer flips: s->cur unchanged
-                it += 2;
-            } else {
-                VBC_TRY(direct_iteration<M>(s, a, it, nsteps));
-                ++it;
-            }
-        }
+        VBC_TRY(open_range<M>(s, a, it0, it));
+        VBC_TRY(run_range<M>(s, a, it, nsteps + 1, nsteps));
         VBC_TRY(read_status(s));
         VBC_TRY(halt_error(s));
-        if (!needs_growth(s)) return VBC_OK;
+        if (!needs_growth(s)) {
+            s->force_fresh = true;
+            return VBC_OK;
+        }
         if (attempt >= MAX_RETRIES) return fail(VBC_ERR_NLIST_OVERFLOW, "capacities kept overflowing");
         // The build of iteration frozen_iter overflowed: every kernel after it
         // returned at once.  Iterations it0 .. frozen_iter - 1 ran, each
@@ -1074,19 +1179,20 @@ int steps_impl(vbc_system* s, int64_t nsteps, double dt, double kT, double gamma
     return VBC_OK;
 }
 
+// Iteration 0 of a batched run, on the system's own stream.
 template <class M>
-int batch_iteration0(vbc_system* s, const StepArgs& a, int64_t nsteps)
+int batch_open(vbc_system* s, const StepArgs& a, int64_t nsteps)
 {
-    k_set_iter<<<1, 1, 0, s->stream>>>(s->st, -1, s->step);
-    VBC_TRY(check_launch(s));
-    return direct_iteration<M>(s, a, 0, nsteps);
+    int64_t next = 0;
+    VBC_TRY(open_range<M>(s, a, 0, next));
+    return run_range<M>(s, a, next, 1, nsteps);
 }
 
+// Iterations it0 .. nsteps of a batched run, on the system's own stream.
 template <class M>
 int batch_tail(vbc_system* s, const StepArgs& a, int64_t it0, int64_t nsteps)
 {
-    for (int64_t it = it0; it <= nsteps; ++it) VBC_TRY(direct_iteration<M>(s, a, it, nsteps));
-    return VBC_OK;
+    return run_range<M>(s, a, it0, nsteps + 1, nsteps);
 }
 
 // Status of one system after a batched run; an overflow is grown and the
@@ -1102,6 +1208,7 @@ int batch_settle(vbc_system* s, const StepArgs& a, int cur0, int64_t nsteps)
         VBC_TRY(grow(s));
         VBC_TRY(run_iterations<M>(s, a, it0, nsteps));
     }
+    s->force_fresh = true;
     s->step += nsteps;
     return VBC_OK;
 }
@@ -1125,6 +1232,7 @@ int stage_in(vbc_system* s, double* dst, const double* src, size_t count, int on
 template <class M>
 int load_state(vbc_system* s, const double* pos, const double* vel, int on_device)
 {
+    s->force_fresh = false;
     // caller arrays -> staging (xt holds positions, vt velocities) -> sorted state
     VBC_TRY(stage_in(s, (double*)s->xt, pos, 3 * (size_t)s->n, on_device));
     if (vel) VBC_TRY(stage_in(s, (double*)s->vt, vel, 3 * (size_t)s->n, on_device));
@@ -1141,9 +1249,11 @@ int load_state(vbc_system* s, const double* pos, const double* vel, int on_devic
 template <class M>
 int build_now(vbc_system* s)
 {
+    s->force_fresh = false;  // the particles are re-sorted
     for (int attempt = 0;; ++attempt) {
         VBC_TRY(force_rebuild_flag(s));
         VBC_TRY(enqueue_rebuild<M>(s));
+        VBC_TRY(clear_rebuild_flag(s));
         VBC_TRY(read_status(s));
         VBC_TRY(halt_error(s));
         if (!needs_growth(s)) return VBC_OK;
@@ -1656,6 +1766,7 @@ int vbc_set_params(vbc_system* s, const vbc_pair_params* p)
     VBC_TRY(upload_window_table(s));
     s->lp = make_list_params(c, s->rlist, s->skin, s->geom);
     s->layout_version += 1;
+    s->force_fresh = false;
     // the near/far split of the lists depends on r_r: rebuild before the next pass
     return force_rebuild_flag(s);
 }
@@ -1814,8 +1925,8 @@ int vbc_batch_step(vbc_batch* b, int64_t nsteps, double dt, const double* kT, do
         vbc_system* s = b->sys[k];
         args[k] = step_args(s, dt, kT[k], gamma);
         cur0[k] = s->cur;
-        VBC_TRY(s->prec == VBC_FP64 ? batch_iteration0<ModeF64>(s, args[k], nsteps)
-                                    : batch_iteration0<ModeF32>(s, args[k], nsteps));
+        VBC_TRY(s->prec == VBC_FP64 ? batch_open<ModeF64>(s, args[k], nsteps)
+                                    : batch_open<ModeF32>(s, args[k], nsteps));
         VBC_CUDA(cudaEventRecord(b->ready[k], s->stream));
         VBC_CUDA(cudaStreamWaitEvent(b->stream, b->ready[k], 0));
     }
@@ -1836,8 +1947,8 @@ int vbc_batch_step(vbc_batch* b, int64_t nsteps, double dt, const double* kT, do
             int rc = VBC_OK;
             for (size_t k = 0; k < K && rc == VBC_OK; ++k) {
                 vbc_system* s = b->sys[k];
-                rc = s->prec == VBC_FP64 ? capture_pair<ModeF64>(s, s->cur, args[k], g)
-                                         : capture_pair<ModeF32>(s, s->cur, args[k], g);
+                rc = s->prec == VBC_FP64 ? capture_iters<ModeF64>(s, s->cur, args[k], G_PAIR, g)
+                                         : capture_iters<ModeF32>(s, s->cur, args[k], G_PAIR, g);
             }
             if (rc == VBC_OK) {
                 const cudaError_t e = cudaGraphInstantiate(&b->exec, g, 0);
@@ -1862,7 +1973,7 @@ int vbc_batch_step(vbc_batch* b, int64_t nsteps, double dt, const double* kT, do
             }
         }
         for (int64_t q = 0; q < npairs; ++q) VBC_CUDA(cudaGraphLaunch(b->exec, b->stream));
-        for (vbc_system* s : b->sys) s->launches += 12 * npairs;
+        for (vbc_system* s : b->sys) s->launches += 2 * (int64_t)iter_launches(s) * npairs;
     }
     // the remaining iterations of every system on its own stream, after the graph
     VBC_CUDA(cudaEventRecord(b->join, b->stream));
