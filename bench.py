@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-valency8", action="store_true", help="skip the valency-8 measurement of the same system")
     ap.add_argument("--no-served", action="store_true", help="skip the served leg (p50/p99 latency)")
     ap.add_argument("--served-requests", type=int, default=24)
     ap.add_argument("--served-steps", type=int, default=50_000, help="Langevin steps per served request")
@@ -82,13 +83,15 @@ def parse():
 DT, KT, GAMMA, SKIN, SEED = 0.005, 1.0, 1.0, 0.4, 3
 
 
-def workload(args):
+def workload(args, valency=None):
+    valency = args.valency if valency is None else valency
     return {
         "workload": (f"uniform fluid N={args.n:,} rho={args.rho}, standard VBC(1.5,2.0,0) soft core "
-                     f"E_r=20 E_a={args.E_a:g} valency {args.valency:g}, BAOAB dt={DT} kT={KT} gamma={GAMMA}, "
+                     f"E_r=20 E_a={args.E_a:g} valency {valency:g}, BAOAB dt={DT} kT={KT} gamma={GAMMA}, "
                      f"skin {SKIN}"),
-        "n": args.n, "rho": args.rho, "valency": args.valency, "E_a": args.E_a,
+        "n": args.n, "rho": args.rho, "valency": valency, "E_a": args.E_a,
         "equilibration_steps": args.equil,
+        "start_state": f"the seeded uniform draw after {args.equil} untimed BAOAB steps, grid autotuning and the warm-up",
         "precision": "FP32 pair arithmetic, FP64 state and energy",
         "l2": "no flush: working set per step (~0.4 GB) > L2 (126 MB)",
     }
@@ -241,7 +244,11 @@ def reference_main(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {**workload(args), "precision": "FP64 oracle (cell-list mode)"},
+        "config": {**workload(args), "precision": "FP64 oracle (cell-list mode)", "equilibration_steps": 0,
+                   "start_state": ("the seeded uniform draw itself: the oracle, at about 1.5 steps/s on the full "
+                                   "system, cannot run the B300 arm's 500 untimed equilibration steps inside the "
+                                   "bench's time; its cost per step depends on the state only through the "
+                                   "neighbour counts of its cell lists")},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -493,7 +500,7 @@ def main():
     import torch
     import torch.distributed as dist
 
-    from paper_2609_07842_b300 import inputs, vbc
+    from paper_2609_07842_b300 import vbc
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -506,9 +513,111 @@ def main():
         torch.cuda.synchronize()
 
     stream = torch.cuda.current_stream()
+    main_m, sys_, L = measure(args, args.valency, rank, world, local, barrier, stream, with_clocks=True)
+    ms = main_m["ms"]
+
+    # ---- e2e: the same steps through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        chunk = max(1, min(args.e2e_chunk, args.steps))
+        hp = torch.empty((args.n, 3), dtype=torch.float64).pin_memory().numpy()
+        hv = torch.empty((args.n, 3), dtype=torch.float64).pin_memory().numpy()
+        _, _, stp = sys_.get_state(hp, hv)
+        barrier()
+        t0 = time.perf_counter()
+        done = 0
+        while done < args.steps:
+            c = min(chunk, args.steps - done)
+            sys_.set_state(hp, hv, step=stp)         # h2d: positions + velocities
+            sys_.step(c, DT, KT, GAMMA)
+            _, _, stp = sys_.get_state(hp, hv)       # d2h: positions + velocities
+            done += c
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        e2e_s = max_over_ranks(e2e_s, world)
+        nchunks = -(-args.steps // chunk)
+        e2e = {"value": whole_job_rate(args.steps, e2e_s, world), "unit": UNIT,
+               "h2d_bytes_per_step": int(48 * args.n * nchunks / args.steps),
+               "d2h_bytes_per_step": int(48 * args.n * nchunks / args.steps),
+               "chunk_steps": chunk}
+
+    # ---- valency 8 on the same system shape: the regime where the switching window and the
+    # chain rule are live (most particles unsaturated), timed the same way (rank 0 reports it)
+    v8 = None
+    sys8 = None
+    if not args.no_valency8 and args.valency != 8.0:
+        m8, sys8, _ = measure(args, 8.0, rank, world, local, barrier, stream, with_clocks=True)
+        v8 = {k: m8[k] for k in ("value", "unit", "ms_per_step", "roofline", "step_roofline", "kernel_ms_per_step",
+                                 "rebuilds", "nlist_mean", "in_window_fraction", "steps_per_rebuild",
+                                 "unsaturated_fraction", "pair_interactions_per_s", "thermo", "clocks",
+                                 "gpu_launches", "tuning")}
+        v8["config"] = workload(args, 8.0)
+
+    # ---- served: a Poisson stream of uneven requests through the serving loop,
+    # and the same stream one system at a time (rank 0, N = 1 only)
+    # (each optional leg runs in a process of its own, while this one waits)
+    served = None
+    if rank == 0 and world == 1 and not args.no_served:
+        served = leg_in_child("served", sys.argv[1:], args.leg_timeout)
+
+    # ---- batched: many uneven systems in one graph against one at a time (rank 0, N = 1 only)
+    batched = None
+    if rank == 0 and world == 1 and not args.no_batched:
+        batched = leg_in_child("batched", sys.argv[1:], args.leg_timeout)
+
+    # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only), and the
+    # error of the timed path against it at the state the timed region ended in
+    cpu = None
+    parity = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, k, secs, cores = run_oracle(args, args.steps, args.cpu_budget)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{k} BAOAB steps of the full N={args.n:,} system, FP64 oracle in cell-list mode "
+                         f"(OpenMP), {secs:.1f} s"}
+        parity = {f"valency_{args.valency:g}": end_state_parity(sys_, L, args.E_a, args.valency)}
+        if sys8 is not None:
+            parity["valency_8"] = end_state_parity(sys8, L, args.E_a, 8.0)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": whole_job_rate(args.steps, ms / 1e3, world), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload(args, args.valency),
+            **{k: main_m[k] for k in ("pair_interactions_per_s", "pairs_within_rc", "roofline", "step_roofline",
+                                      "kernel_ms_per_step", "rebuilds", "nlist_mean", "in_window_fraction",
+                                      "steps_per_rebuild", "unsaturated_fraction", "capacities", "thermo",
+                                      "gpu_launches", "clocks", "tuning")},
+            "e2e": e2e,
+            "valency_8": v8,
+            "parity": parity,
+            "served": served,
+            "batched": batched,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    sys_.close()
+    if sys8 is not None:
+        sys8.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def measure(args, valency, rank, world, local, barrier, stream, with_clocks=True):
+    """One N-particle system at the given valency: untimed equilibration, grid
+    autotuning, W warm-up steps, then (1) K timed steps through the production
+    path (CUDA graphs, inputs resident), (2) the same K steps with direct launches
+    and a CUDA event pair around every kernel, for the per-class times, and (3)
+    forced list builds, for the rebuild class.  Returns the measurement, the
+    system (still open) and the box edge."""
+    import torch
+
+    from paper_2609_07842_b300 import inputs, vbc
+
     pos, L = inputs.uniform_positions(args.n, args.rho, seed=SEED + rank)
     vel = inputs.maxwell_velocities(args.n, KT, seed=SEED + 1 + rank)
-    prm = vbc.params(E_a=args.E_a, f=args.valency)
+    prm = vbc.params(E_a=args.E_a, f=valency)
     sys_ = vbc.System(pos, L, prm, vel=vel, skin=SKIN, seed=SEED + rank, stream=stream.cuda_stream)
 
     # untimed equilibration + warm-up
@@ -518,10 +627,10 @@ def main():
     sys_.step(max(args.warmup, 3), DT, KT, GAMMA)
     st0 = sys_.stats()
 
-    # ---- timed region 1: the production path (two-step CUDA graphs with the
-    # rebuild behind a device-side conditional), no per-kernel events
+    # ---- timed region 1: the production path (CUDA graphs with the rebuild behind a
+    # device-side conditional), no per-kernel events
     launches0 = sys_.kernel_launches()
-    clocks = start_clocks(local)
+    clocks = start_clocks(local) if with_clocks else None
     time.sleep(0.3 if clocks else 0.0)
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -533,11 +642,12 @@ def main():
     clk = stop_clocks(clocks)
     launches = sys_.kernel_launches() - launches0
     st1 = sys_.stats()
+    th = sys_.thermo()  # FP64 reductions of the end state (outside the timed region)
 
-    # ---- timed region 2: the same K steps with direct launches and a CUDA event
-    # pair around every kernel on the library's stream, for per-kernel times
-    # (room for the records of the iterations that overflows halt and their retries re-run:
-    # a system still clustering can grow its capacities several times in one call)
+    # ---- timed region 2: the same K steps with direct launches and a CUDA event pair
+    # around every kernel on the library's stream, for per-kernel times (room for the
+    # records of the iterations that overflows halt and their retries re-run: a system
+    # still clustering can grow its capacities several times in one call)
     sys_.profile(True, max_launches=48 * (args.steps + 2) + 64)
     barrier()
     ev0.record(stream)
@@ -578,10 +688,10 @@ def main():
     cb = class_bytes_per_particle(k_mean, phi)
     # per-launch duration of each class; the rebuild class from forced builds
     # (timed region 3), the others from timed region 2
-    per_launch_ms = {"count": count_ms / max(args.steps + 1, 1), "chain": chain_ms / max(args.steps + 1, 1),
-                     "force": force_ms / max(args.steps + 1, 1), "rebuild": build_ms}
-    share_ms = dict(per_launch_ms)
-    share_ms["rebuild"] = build_ms / rebuild_every if rebuilds else 0.0  # amortised per step
+    per_launch_ms = {"count": count_ms / max(count_n, 1), "chain": chain_ms / max(chain_n, 1),
+                     "force": force_ms / max(force_n, 1), "rebuild": build_ms}
+    share_ms = {"count": count_ms / args.steps, "chain": chain_ms / args.steps, "force": force_ms / args.steps,
+                "rebuild": build_ms / rebuild_every if rebuilds else 0.0}  # rebuilds amortised per step
     classes = {}
     for c_, ms_ in per_launch_ms.items():
         b_ = cb[c_] * args.n
@@ -594,102 +704,72 @@ def main():
     if rebuilds:
         step_b += cb["rebuild"] * args.n / rebuild_every
     step_gbs = step_b * (args.steps / (ms / 1e3)) / 1e9
+    m = {
+        "ms": ms, "value": steps_per_s, "unit": UNIT, "ms_per_step": ms / args.steps,
+        "pair_interactions_per_s": pairs * steps_per_s, "pairs_within_rc": pairs,
+        "roofline": {"bound": "hbm", "achieved": classes[dominant]["achieved"], "peak": peak,
+                     "unit": "GB/s", "frac": classes[dominant]["frac"],
+                     "traffic": classes[dominant]["traffic"], "kernel": dominant,
+                     "kernels": KERNELS_OF[dominant], "peak_source": peak_kind,
+                     "timing": ("CUDA events around every launch on the library stream (forced builds for "
+                                "the rebuild class)"),
+                     "algorithmic_bytes_per_launch": classes[dominant]["algorithmic_bytes_per_launch"],
+                     "avg_launch_ms": classes[dominant]["avg_launch_ms"],
+                     "dominant_by": "device time per step (rebuilds amortised)",
+                     "classes": classes},
+        "step_roofline": {"achieved": step_gbs, "frac": step_gbs / peak, "algorithmic_bytes_per_step": step_b,
+                          "bytes_per_particle_step": step_b / args.n, "peak_source": peak_kind},
+        "kernel_ms_per_step": {"rebuild": reb_ms / args.steps, "count": count_ms / args.steps,
+                               "chain": chain_ms / args.steps, "force": force_ms / args.steps,
+                               "build_ms": build_ms,
+                               "source": "timed region 2 (direct launches, CUDA events per kernel); "
+                                         "build_ms: forced builds (region 3)",
+                               "ms_per_step_direct": ms_direct / args.steps,
+                               "rebuilds": rebuilds_direct},
+        "rebuilds": rebuilds, "nlist_mean": k_mean, "in_window_fraction": phi,
+        "steps_per_rebuild": rebuild_every, "unsaturated_fraction": st2.unsaturated / args.n,
+        "capacities": {"stage": st2.stage_cap, "group": st2.group_cap, "segment": st2.segment_cap,
+                       "list": st2.nlist_cap, "groups": st2.groups,
+                       "grows_in_timed_region": st1.capacity_grows - st0.capacity_grows},
+        "thermo": {"energy_per_particle": th.U / args.n, "virial_per_particle": th.W / args.n,
+                   "kinetic_temperature": 2.0 * th.KE / (3.0 * args.n), "mean_count": th.mean_n,
+                   "in_window": th.in_window, "step": th.step,
+                   "source": "vbc_compute_thermo at the end of timed region 1 (FP64 device reductions)"},
+        "energy_per_particle": r.energy / args.n,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "tuning": {"rows_blocks_per_sm": tuning.rows_blocks_per_sm,
+                   "count_blocks_per_sm": tuning.count_blocks_per_sm,
+                   "trial_ms_per_step": tuning.ms_per_step, "note": "0 = as many blocks as fit"},
+    }
+    return m, sys_, L
 
-    # ---- e2e: the same steps through the public API with host buffers
-    e2e = None
-    if not args.no_e2e:
-        chunk = max(1, min(args.e2e_chunk, args.steps))
-        hp = torch.empty((args.n, 3), dtype=torch.float64).pin_memory().numpy()
-        hv = torch.empty((args.n, 3), dtype=torch.float64).pin_memory().numpy()
-        _, _, stp = sys_.get_state(hp, hv)
-        barrier()
-        t0 = time.perf_counter()
-        done = 0
-        while done < args.steps:
-            c = min(chunk, args.steps - done)
-            sys_.set_state(hp, hv, step=stp)         # h2d: positions + velocities
-            sys_.step(c, DT, KT, GAMMA)
-            _, _, stp = sys_.get_state(hp, hv)       # d2h: positions + velocities
-            done += c
-        barrier()
-        e2e_s = time.perf_counter() - t0
-        e2e_s = max_over_ranks(e2e_s, world)
-        nchunks = -(-args.steps // chunk)
-        e2e = {"value": whole_job_rate(args.steps, e2e_s, world), "unit": UNIT,
-               "h2d_bytes_per_step": int(48 * args.n * nchunks / args.steps),
-               "d2h_bytes_per_step": int(48 * args.n * nchunks / args.steps),
-               "chunk_steps": chunk}
 
-    # ---- served: a Poisson stream of uneven requests through the serving loop,
-    # and the same stream one system at a time (rank 0, N = 1 only)
-    # (each optional leg runs in a process of its own, while this one waits)
-    served = None
-    if rank == 0 and world == 1 and not args.no_served:
-        served = leg_in_child("served", sys.argv[1:], args.leg_timeout)
+# Tolerances of the parity tests (tests/test_gpu_parity.py), FP32-split path.
+PARITY_TOL = {"count_abs": 1e-6, "force_rel_rms": 1e-5, "energy_rel": 1e-9}
 
-    # ---- batched: many uneven systems in one graph against one at a time (rank 0, N = 1 only)
-    batched = None
-    if rank == 0 and world == 1 and not args.no_batched:
-        batched = leg_in_child("batched", sys.argv[1:], args.leg_timeout)
 
-    # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, k, secs, cores = run_oracle(args, args.steps, args.cpu_budget)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{k} BAOAB steps of the full N={args.n:,} system, FP64 oracle in cell-list mode "
-                         f"(OpenMP), {secs:.1f} s"}
-
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": steps_per_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload(args),
-            "pair_interactions_per_s": pairs * steps_per_s,
-            "pairs_within_rc": pairs,
-            "roofline": {"bound": "hbm", "achieved": classes[dominant]["achieved"], "peak": peak,
-                         "unit": "GB/s", "frac": classes[dominant]["frac"],
-                         "traffic": classes[dominant]["traffic"], "kernel": dominant,
-                         "kernels": KERNELS_OF[dominant], "peak_source": peak_kind,
-                         "timing": ("CUDA events around every launch on the library stream (forced builds for "
-                                    "the rebuild class)"),
-                         "algorithmic_bytes_per_launch": classes[dominant]["algorithmic_bytes_per_launch"],
-                         "avg_launch_ms": classes[dominant]["avg_launch_ms"],
-                         "dominant_by": "device time per step (rebuilds amortised)",
-                         "classes": classes},
-            "step_roofline": {"achieved": step_gbs, "frac": step_gbs / peak,
-                              "algorithmic_bytes_per_step": step_b,
-                              "bytes_per_particle_step": step_b / args.n},
-            "kernel_ms_per_step": {"rebuild": reb_ms / args.steps, "count": count_ms / args.steps,
-                                   "chain": chain_ms / args.steps, "force": force_ms / args.steps,
-                                   "build_ms": build_ms,
-                                   "source": "timed region 2 (direct launches, CUDA events per kernel); "
-                                             "build_ms: forced builds (region 3)",
-                                   "ms_per_step_direct": ms_direct / args.steps,
-                                   "rebuilds": rebuilds_direct},
-            "rebuilds": rebuilds,
-            "nlist_mean": k_mean, "in_window_fraction": phi, "steps_per_rebuild": rebuild_every,
-            "unsaturated_fraction": st2.unsaturated / args.n,
-            "capacities": {"stage": st2.stage_cap, "group": st2.group_cap, "segment": st2.segment_cap,
-                           "list": st2.nlist_cap, "groups": st2.groups,
-                           "grows_in_timed_region": st1.capacity_grows - st0.capacity_grows},
-            "energy_per_particle": r.energy / args.n,
-            "gpu_launches": launches,
-            "clocks": clk,
-            "e2e": e2e,
-            "tuning": {"rows_blocks_per_sm": tuning.rows_blocks_per_sm,
-                       "count_blocks_per_sm": tuning.count_blocks_per_sm,
-                       "trial_ms_per_step": tuning.ms_per_step, "note": "0 = as many blocks as fit"},
-            "served": served,
-            "batched": batched,
-            "cpu_baseline": cpu,
-        }
-        print(json.dumps(line), flush=True)
-    sys_.close()
-    if world > 1:
-        dist.destroy_process_group()
-    return 0
+def end_state_parity(sys_, L, E_a, valency):
+    """Error of the library against the FP64 oracle at the state a timed run
+    ended in: counts and forces (vbc_compute_forces) and U, element by element
+    over all particles, the oracle in its cell-list mode at the positions read
+    back from the device."""
+    import oracle
+    x, _, step = sys_.get_state()
+    r = sys_.compute(F=True, counts=True, energy=True)
+    t0 = time.perf_counter()
+    ref = oracle.evaluate(x, L, oracle.Params(E_a=E_a, f=valency), mode=1)
+    secs = time.perf_counter() - t0
+    rms = float(np.sqrt(np.mean(np.sum(ref.F ** 2, axis=1))))
+    out = {"max_abs_dcount": float(np.max(np.abs(r.counts - ref.counts))),
+           "max_abs_dF_over_rms": float(np.max(np.abs(r.F - ref.F)) / rms),
+           "rel_dU": abs(r.energy - ref.U) / abs(ref.U),
+           "in_window_fraction": float(np.mean(ref.ds != 0.0)), "step": step,
+           "tolerances": PARITY_TOL, "oracle_seconds": secs}
+    out["ok"] = (out["max_abs_dcount"] <= PARITY_TOL["count_abs"]
+                 and out["max_abs_dF_over_rms"] <= PARITY_TOL["force_rel_rms"]
+                 and out["rel_dU"] <= PARITY_TOL["energy_rel"])
+    return out
 
 
 if __name__ == "__main__":

@@ -216,6 +216,34 @@ int vbc_set_params(vbc_system* sys, const vbc_pair_params* params);
 int vbc_get_stats(vbc_system* sys, vbc_stats* out);
 
 /*
+ * Thermodynamic reductions of the current state, all in FP64 with fixed-order
+ * (deterministic) sums on the device:
+ *   U         = sum_{i<j} [V_r(r_ij) + s_i s_j V_a(r_ij)]        Eq. (Vhat), Sec. 2
+ *   W         = sum_{i<j} -g_ij r_ij, g_ij = dU/dr_ij with the chain-rule term (pair virial)
+ *   KE        = sum_i |v_i|^2 / 2 (unit mass; kinetic temperature 2 KE / (3 N))
+ *   mean_n    = (1/N) sum_i n_i, n_i of Eq. (counter) (masked counts for multi-type systems)
+ *   in_window = particles with f - delta < n_i < f - delta + 1 (s'_i != 0), Eq. (Psidelta)
+ *   pairs_within_rc = unordered pairs with r_ij < r_c
+ *   step      = the step counter of the state
+ * The counts, s, s' and A behind U, W, mean_n and in_window are recomputed in
+ * FP64 from the state (U to 1e-9 relative of the FP64 definition).  The call
+ * changes neither the state nor the forces the next vbc_step_langevin opens
+ * with, so logging between chunks of steps leaves the trajectory bitwise the
+ * same.  out is a host struct.  Errors: INVALID_ARG (NULL), CUDA, UNSTABLE
+ * (halted system), NLIST_OVERFLOW.
+ */
+typedef struct {
+    double U;
+    double W;
+    double KE;
+    double mean_n;
+    int64_t in_window;
+    int64_t pairs_within_rc;
+    int64_t step;
+} vbc_thermo;
+int vbc_compute_thermo(vbc_system* sys, vbc_thermo* out);
+
+/*
  * Per-kernel timing with CUDA events on the system's stream.  enable != 0
  * starts recording one event pair around every kernel launch (up to
  * max_launches launches; further launches are not timed); enable == 0 stops.

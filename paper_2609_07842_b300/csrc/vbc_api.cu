@@ -150,6 +150,10 @@ struct vbc_system {
     long long* win = nullptr;
     double2* e_sd = nullptr;     // FP64 (s, s') of the energy evaluation
     double* e_A = nullptr;       // FP64 A of the energy evaluation
+    double* t_part = nullptr;    // [2 THERMO_GRID] block partials of KE and sum n (vbc_compute_thermo)
+    long long* t_wpart = nullptr;  // [THERMO_GRID] block partials of the window count
+    ThermoOut* t_out = nullptr;    // final sums
+    ThermoOut* t_out_host = nullptr;  // pinned
 
     int64_t step = 0;
     int64_t launches = 0;
@@ -458,6 +462,9 @@ void free_all(vbc_system* s)
     dfree(s->close_k); dfree(s->fcore); dfree(s->glist);
     dfree(s->ds); dfree(s->sA); dfree(s->st); dfree(s->partial); dfree(s->ppairs); dfree(s->red);
     dfree(s->win); dfree(s->e_sd); dfree(s->e_A); dfree(s->wtab); dfree(s->obs); dfree(s->zbuf);
+    dfree(s->t_part); dfree(s->t_wpart); dfree(s->t_out);
+    if (s->t_out_host) cudaFreeHost(s->t_out_host);
+    s->t_out_host = nullptr;
     if (s->st_host) cudaFreeHost(s->st_host);
     if (s->red_host) cudaFreeHost(s->red_host);
     s->st_host = nullptr;
@@ -655,8 +662,10 @@ int enqueue_force(vbc_system* s, const StepArgs& a)
     return VBC_OK;
 }
 
+// U, W and the pair count (FP64, on request); n_sorted, if not null, receives
+// the FP64 count of every particle in sorted order (single-type systems).
 template <class M>
-int enqueue_energy(vbc_system* s)
+int enqueue_energy(vbc_system* s, double* n_sorted = nullptr)
 {
     using pos_t = typename M::pos_t;
     {
@@ -674,7 +683,7 @@ int enqueue_energy(vbc_system* s)
         }
         const int nb = s->nsc;
         k_count_e<M><<<nb, SC_TPB, s->smem_energy(), s->stream>>>(s->geom, s->coef, pos, s->grid(), s->caps(),
-                                                                   s->nbr, s->nnb, s->e_sd, s->st);
+                                                                   s->nbr, s->nnb, s->e_sd, n_sorted, s->st);
         k_chain_e<M><<<nb, SC_TPB, s->smem_energy(), s->stream>>>(s->geom, s->coef, pos, s->grid(), s->caps(),
                                                                    s->nbr, s->nnb, s->e_sd, s->e_A, s->st);
         k_energy<M><<<nb, SC_TPB, s->smem_energy(), s->stream>>>(s->geom, s->coef, pos, s->grid(), s->caps(),
@@ -917,6 +926,65 @@ int enqueue_force_epi(vbc_system* s, const StepArgs& a, int epi)
 // Epilogue of loop iteration `it` of nsteps: iteration 0 opens step 0, the
 // last one closes step nsteps - 1, the others close one step and open the next.
 int epi_of(int64_t it, int64_t nsteps) { return it == 0 ? EPI_START : (it < nsteps ? EPI_FINISH_START : EPI_FINISH); }
+
+// Thermodynamic reductions of the current state (vbc_compute_thermo).  The
+// list is brought up to date first unless the resident forces are fresh (a
+// run of steps left the list current); the single-type evaluation then uses
+// the FP64 energy kernels, which write none of the step loop's arrays, and
+// the multi-type one re-runs its FP64 count and chain-rule walks, which write
+// the same values again.  So the resident forces stay valid.
+template <class M>
+int thermo_impl(vbc_system* s, vbc_thermo* out)
+{
+    if (!s->t_part) {
+        VBC_TRY(dalloc(s->t_part, 2 * (size_t)THERMO_GRID));
+        VBC_TRY(dalloc(s->t_wpart, (size_t)THERMO_GRID));
+        VBC_TRY(dalloc(s->t_out, 1));
+        if (cudaMallocHost((void**)&s->t_out_host, sizeof(ThermoOut)) != cudaSuccess)
+            return fail(VBC_ERR_OOM, "pinned host allocation failed");
+    }
+    const bool keep = s->force_fresh;
+    double* nv = (double*)s->vt;  // FP64 counts (free staging outside a rebuild)
+    for (int attempt = 0;; ++attempt) {
+        VBC_CUDA(cudaMemsetAsync(&s->st->nwin, 0, 3 * sizeof(int), s->stream));  // nwin, nu, ngen
+        if (!keep) {
+            s->force_fresh = false;
+            VBC_TRY(enqueue_rebuild<M>(s));
+            VBC_TRY(clear_rebuild_flag(s));
+        }
+        const double* dsv;
+        int stride;
+        if (s->typed) {
+            VBC_TRY(enqueue_count_chain<M>(s, nv, false));  // counts in caller order
+            dsv = (const double*)s->ds;
+            stride = 1;
+        } else {
+            dsv = (const double*)s->e_sd + 1;  // s' of (s, s')
+            stride = 2;
+        }
+        VBC_TRY(enqueue_energy<M>(s, s->typed ? nullptr : nv));
+        k_thermo_part<M><<<THERMO_GRID, RED_TPB, 0, s->stream>>>((int)s->n, s->v, nv, dsv, stride, s->t_part,
+                                                                 s->t_wpart);
+        k_thermo_final<<<1, RED_TPB, 0, s->stream>>>(THERMO_GRID, s->t_part, s->t_wpart, s->t_out);
+        VBC_TRY(check_launch(s, 2));
+        VBC_TRY(read_status(s));
+        VBC_TRY(halt_error(s));
+        if (!needs_growth(s)) break;
+        if (attempt >= MAX_RETRIES) return fail(VBC_ERR_NLIST_OVERFLOW, "capacities kept overflowing");
+        VBC_TRY(grow(s));
+    }
+    VBC_CUDA(cudaMemcpyAsync(s->red_host, s->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    VBC_CUDA(cudaMemcpyAsync(s->t_out_host, s->t_out, sizeof(ThermoOut), cudaMemcpyDeviceToHost, s->stream));
+    VBC_TRY(read_status(s));
+    out->U = s->red_host[0];
+    out->W = s->red_host[1];
+    out->KE = s->t_out_host->ke;
+    out->mean_n = s->t_out_host->nsum / (double)s->n;
+    out->in_window = s->t_out_host->win;
+    out->pairs_within_rc = s->st_host->pairs;
+    out->step = s->step;
+    return VBC_OK;
+}
 
 // One loop iteration with direct launches: gate, rebuild (early exit unless
 // due), count, chain, force with the epilogue of iteration `it`.
@@ -1792,6 +1860,13 @@ int vbc_get_observables(vbc_system* s, vbc_observables* out, int32_t* z, int on_
         VBC_CUDA(cudaStreamSynchronize(s->stream));
     }
     return VBC_OK;
+}
+
+int vbc_compute_thermo(vbc_system* s, vbc_thermo* out)
+{
+    VBC_TRY(check_sys(s));
+    if (!out) return fail(VBC_ERR_INVALID_ARG, "out must not be NULL");
+    return s->prec == VBC_FP64 ? thermo_impl<ModeF64>(s, out) : thermo_impl<ModeF32>(s, out);
 }
 
 int vbc_get_stats(vbc_system* s, vbc_stats* out)

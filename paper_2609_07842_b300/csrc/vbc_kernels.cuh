@@ -1750,7 +1750,7 @@ template <class M>
 __global__ void __launch_bounds__(SC_TPB) k_count_e(Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
                                                     SuperGrid G, SuperCaps cp, const uint16_t* __restrict__ nbr,
                                                     const int* __restrict__ nnb, double2* __restrict__ sd,
-                                                    const Status* st)
+                                                    double* __restrict__ n_sorted, const Status* st)
 {
     using pos_t = typename M::pos_t;
     if (halted(st)) return;
@@ -1774,6 +1774,7 @@ __global__ void __launch_bounds__(SC_TPB) k_count_e(Geom g, Coef c, const typena
             if (r2 < c.rh2) acc += r2 <= c.rl2 ? 1.0 : omega_d(sqrt(r2), c.r_l, c.r_h);
         }
         sd[p] = make_double2(omega_d(acc, c.fd, c.fd + 1.0), domega_d(acc, c.fd, c.fd + 1.0));
+        if (n_sorted) n_sorted[p] = acc;
     }
 }
 
@@ -1968,6 +1969,87 @@ __global__ void __launch_bounds__(RED_TPB) k_reduce_final(int nb, const double* 
         out[1] = sw[0];
         st->pairs = sp[0] / 2;
     }
+}
+
+// Per-particle sums of the thermodynamic reductions (vbc_compute_thermo):
+// KE = sum_i |v_i|^2 / 2 from the state (unit mass), sum_i n_i from FP64
+// counts nv[0..n), and the particles inside their switching window
+// (dsv[i * ds_stride] != 0).  A fixed grid takes the particles in a
+// grid-stride loop and each block writes its partial sums, so the result
+// depends on n and the state alone.
+constexpr int THERMO_GRID = 592;  // 4 blocks of RED_TPB per SM of a B300
+struct ThermoOut {
+    double ke, nsum;
+    long long win;
+};
+template <class M>
+__global__ void __launch_bounds__(RED_TPB) k_thermo_part(int n, const void* __restrict__ v,
+                                                         const double* __restrict__ nv,
+                                                         const double* __restrict__ dsv, int ds_stride,
+                                                         double* __restrict__ part, long long* __restrict__ wpart)
+{
+    __shared__ double sk[RED_TPB], sn[RED_TPB];
+    __shared__ long long sw[RED_TPB];
+    double ke = 0.0, ns = 0.0;
+    long long w = 0;
+    for (int p = blockIdx.x * RED_TPB + threadIdx.x; p < n; p += gridDim.x * RED_TPB) {
+        double v2 = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double vd;
+            if constexpr (M::fp64) vd = ((const double*)v)[(size_t)d * n + p];
+            else vd = (double)((const long long*)v)[(size_t)d * n + p] * 9.094947017729282e-13;  // 2^-40
+            v2 += vd * vd;
+        }
+        ke += 0.5 * v2;
+        ns += nv[p];
+        w += dsv[(size_t)p * ds_stride] != 0.0 ? 1 : 0;
+    }
+    sk[threadIdx.x] = ke;
+    sn[threadIdx.x] = ns;
+    sw[threadIdx.x] = w;
+    __syncthreads();
+    for (int s = RED_TPB / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sk[threadIdx.x] += sk[threadIdx.x + s];
+            sn[threadIdx.x] += sn[threadIdx.x + s];
+            sw[threadIdx.x] += sw[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = sk[0];
+        part[2 * blockIdx.x + 1] = sn[0];
+        wpart[blockIdx.x] = sw[0];
+    }
+}
+
+// Fixed-order sum of the THERMO_GRID block partials.
+__global__ void __launch_bounds__(RED_TPB) k_thermo_final(int nb, const double* __restrict__ part,
+                                                          const long long* __restrict__ wpart, ThermoOut* out)
+{
+    __shared__ double sk[RED_TPB], sn[RED_TPB];
+    __shared__ long long sw[RED_TPB];
+    double ke = 0.0, ns = 0.0;
+    long long w = 0;
+    for (int b = threadIdx.x; b < nb; b += RED_TPB) {
+        ke += part[2 * b];
+        ns += part[2 * b + 1];
+        w += wpart[b];
+    }
+    sk[threadIdx.x] = ke;
+    sn[threadIdx.x] = ns;
+    sw[threadIdx.x] = w;
+    __syncthreads();
+    for (int s = RED_TPB / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sk[threadIdx.x] += sk[threadIdx.x + s];
+            sn[threadIdx.x] += sn[threadIdx.x + s];
+            sw[threadIdx.x] += sw[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = ThermoOut{sk[0], sn[0], sw[0]};
 }
 
 // ================================================================ state I/O

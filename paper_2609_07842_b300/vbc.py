@@ -35,6 +35,7 @@ K_REBUILD, K_COUNT, K_CHAIN, K_FORCE, K_ENERGY = range(5)
 EXPORTS = ("vbc_create_system", "vbc_create_typed_system", "vbc_build_neighbors", "vbc_compute_forces", "vbc_get_switch",
            "vbc_get_neighbors",
            "vbc_step_langevin", "vbc_get_state", "vbc_set_state", "vbc_set_params", "vbc_get_stats",
+           "vbc_compute_thermo",
            "vbc_profile", "vbc_profile_read", "vbc_kernel_launches", "vbc_destroy", "vbc_last_error",
            "vbc_compute_forces_noalloc", "vbc_estimate_device_bytes", "vbc_get_observables",
            "vbc_batch_create", "vbc_batch_step", "vbc_batch_destroy", "vbc_set_tuning", "vbc_autotune",
@@ -102,6 +103,14 @@ class RequestInfo(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64)]
 
 
+class Thermo(ctypes.Structure):
+    """FP64 reductions of the current state (vbc_compute_thermo): U, the pair
+    virial W, KE, the mean count, the in-window count, the pairs within r_c."""
+    _fields_ = [("U", ctypes.c_double), ("W", ctypes.c_double), ("KE", ctypes.c_double),
+                ("mean_n", ctypes.c_double), ("in_window", ctypes.c_int64), ("pairs_within_rc", ctypes.c_int64),
+                ("step", ctypes.c_int64)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("step", ctypes.c_int64), ("rebuilds", ctypes.c_int64),
                 ("nlist_cap", ctypes.c_int32), ("nlist_max", ctypes.c_int32), ("nlist_mean", ctypes.c_double),
@@ -135,6 +144,8 @@ def load() -> ctypes.CDLL:
     L.vbc_set_state.argtypes = [vp, vp, vp, i64, i32]
     L.vbc_set_params.argtypes = [vp, ctypes.POINTER(PairParams)]
     L.vbc_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+    L.vbc_compute_thermo.argtypes = [vp, ctypes.POINTER(Thermo)]
+    L.vbc_compute_thermo.restype = i32
     L.vbc_profile.argtypes = [vp, i32, i64]
     L.vbc_profile_read.argtypes = [vp, i32, ctypes.POINTER(dp), ctypes.POINTER(i64)]
     L.vbc_kernel_launches.argtypes = [vp]
@@ -392,6 +403,13 @@ class System:
         _check(load().vbc_get_observables(self._h, ctypes.byref(out),
                                           ctypes.c_void_p(zz.ctypes.data) if z else None, 0))
         return out, zz
+
+    def thermo(self) -> Thermo:
+        """U, W, KE, mean count, in-window and pair counts of the current state
+        (vbc_compute_thermo; leaves the trajectory unchanged)."""
+        t = Thermo()
+        _check(load().vbc_compute_thermo(self._h, ctypes.byref(t)))
+        return t
 
     def stats(self) -> Stats:
         s = Stats()
