@@ -740,7 +740,9 @@ def measure(args, valency, rank, world, local, barrier, stream, with_clocks=True
         "clocks": clk,
         "tuning": {"rows_blocks_per_sm": tuning.rows_blocks_per_sm,
                    "count_blocks_per_sm": tuning.count_blocks_per_sm,
-                   "trial_ms_per_step": tuning.ms_per_step, "note": "0 = as many blocks as fit"},
+                   "rows_threads_per_block": tuning.rows_threads_per_block,
+                   "threads_per_row_max": tuning.threads_per_row_max,
+                   "trial_ms_per_step": tuning.ms_per_step, "note": "blocks per SM: 0 = as many as fit"},
     }
     return m, sys_, L
 

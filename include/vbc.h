@@ -326,13 +326,21 @@ void vbc_batch_destroy(vbc_batch* batch);
 /* ------------------------------------------------------------------ autotuning
  * The close-neighbour count and the row walks run resident grids, as many
  * blocks per SM as fit by default.  For small systems (and many systems side
- * by side, as in batches and serving) fewer blocks can be faster.  These
- * settings do not change any result: every row and every cell group is
- * computed the same way whichever block takes it. */
+ * by side, as in batches and serving) fewer blocks can be faster, and dense
+ * walks (most particles unsaturated) can gain from larger blocks, which give
+ * each row more threads.  The grid sizes change no result: every row and
+ * every cell group is computed the same way whichever block takes it.  The
+ * block shape and the threads-per-row cap decide how a dense walk splits a
+ * row between threads, and so the order of its floating-point sums: they
+ * change forces, chain-rule terms and FP64 counts by rounding only (the
+ * FP32-split counts, integer sums, not at all), and every setting is
+ * deterministic. */
 typedef struct {
-    int32_t rows_blocks_per_sm;   /* the row walks' grid, 0 = as many as fit */
-    int32_t count_blocks_per_sm;  /* the close-neighbour count's grid, 0 = as many as fit */
-    double ms_per_step;           /* the best trial's time per step (vbc_autotune's output) */
+    int32_t rows_blocks_per_sm;     /* the row walks' grid, 0 = as many as fit */
+    int32_t count_blocks_per_sm;    /* the close-neighbour count's grid, 0 = as many as fit */
+    int32_t rows_threads_per_block; /* the row walks' block shape: 128, 256 or 512 (0 = 128) */
+    int32_t threads_per_row_max;    /* threads per row of a dense walk, at most: 1, 2, 4, ..., 32 (0 = 32) */
+    double ms_per_step;             /* the best trial's time per step (vbc_autotune's output) */
 } vbc_tuning;
 
 /* Apply grid settings (for example the result of an earlier vbc_autotune on a
@@ -340,12 +348,11 @@ typedef struct {
 int vbc_set_tuning(vbc_system* s, const vbc_tuning* t);
 
 /* Time trial_steps Langevin steps (dt, kT, gamma as vbc_step_langevin) for
- * each candidate setting, one knob at a time, keep the fastest and return it
- * (the default stays unless a setting beats it by 2%).
- * The trials advance the system (about 10 (trial_steps + 2) steps); since the
- * settings change no result, its trajectory is bitwise the one it would have
- * had untuned.  Errors: INVALID_ARG (NULL out, trial_steps < 4), as
- * vbc_step_langevin otherwise. */
+ * each candidate setting, one knob at a time (block shape, row grid, threads
+ * per row, count grid), keep the fastest and return it (the default stays
+ * unless a setting beats it by 2%).  The trials advance the system (about
+ * 14 (trial_steps + 2) steps).  Errors: INVALID_ARG (NULL out, trial_steps
+ * < 4), as vbc_step_langevin otherwise. */
 int vbc_autotune(vbc_system* s, int64_t trial_steps, double dt, double kT, double gamma, vbc_tuning* out);
 
 /* ------------------------------------------------------------------ observables

@@ -136,6 +136,8 @@ struct vbc_system {
     int row_grid = 1;           // blocks of the row walks (count rows, chain-rule pass, force rows)
     int near_grid = 1;          // blocks of k_count_near
     int rows_bps = 0, near_bps = 0;  // blocks per SM of those grids, 0 = as many as fit (vbc_autotune)
+    int row_tpb = 128;               // threads per block of the row walks: 128, 256 or 512
+    int tpp_max = 32;                // threads per row of the dense walks, at most (a power of two <= 32)
     long long grows = 0;        // capacity growths after an overflow
     uint4* wtab = nullptr;      // [WTAB_PIECES + 1] window-weight pieces of the counts (window_weight_tab)
     unsigned long long* obs = nullptr;  // [2 + ZHIST] sums of k_observe
@@ -498,6 +500,18 @@ int set_smem(F* func, size_t bytes)
     return VBC_OK;
 }
 
+// Calls f(std::integral_constant<int, NT>{}) for the row walks' block size
+// NT = tpb (128, 256 or 512) and returns its result.
+template <class F>
+int for_row_tpb(int tpb, F&& f)
+{
+    switch (tpb) {
+    case 256: return f(std::integral_constant<int, 256>{});
+    case 512: return f(std::integral_constant<int, 512>{});
+    default: return f(std::integral_constant<int, 128>{});
+    }
+}
+
 // Raises the dynamic shared-memory limit of every kernel instance of mode M
 // to what the current capacities need.
 template <class M>
@@ -515,23 +529,30 @@ int configure_smem(vbc_system* s)
     VBC_TRY(set_smem(k_chain_e<M>, s->smem_energy()));
     VBC_TRY(set_smem(k_energy<M>, s->smem_energy()));
     VBC_TRY(set_smem(k_store_nlist, s->smem_store()));
-    VBC_TRY(set_smem(k_count_rows<M>, s->smem_rows(0)));
-    VBC_TRY(set_smem(k_chain<M>, s->smem_rows(0)));
-    VBC_TRY(set_smem(k_force_rows<M>, s->smem_rows(s->real_bytes())));
+    VBC_TRY(for_row_tpb(s->row_tpb, [&](auto nt) -> int {
+        constexpr int NT = decltype(nt)::value;
+        VBC_TRY(set_smem(k_count_rows<M, NT>, s->smem_rows(0)));
+        VBC_TRY(set_smem(k_chain<M, NT>, s->smem_rows(0)));
+        return set_smem(k_force_rows<M, NT>, s->smem_rows(s->real_bytes()));
+    }));
     // the row walks run as many blocks as stay resident together
     int occ = 1 << 30;
-    const auto resident = [&](const void* kern, size_t smem) {
+    const auto resident = [&](const void* kern, int tpb, size_t smem) {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, SC_TPB, smem) != cudaSuccess || b < 1) b = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, tpb, smem) != cudaSuccess || b < 1) b = 1;
         occ = std::min(occ, b);
     };
-    resident((const void*)k_count_rows<M>, s->smem_rows(0));
-    resident((const void*)k_chain<M>, s->smem_rows(0));
-    resident((const void*)k_force_rows<M>, s->smem_rows(s->real_bytes()));
+    for_row_tpb(s->row_tpb, [&](auto nt) -> int {
+        constexpr int NT = decltype(nt)::value;
+        resident((const void*)k_count_rows<M, NT>, NT, s->smem_rows(0));
+        resident((const void*)k_chain<M, NT>, NT, s->smem_rows(0));
+        resident((const void*)k_force_rows<M, NT>, NT, s->smem_rows(s->real_bytes()));
+        return VBC_OK;
+    });
     s->row_grid = std::max(1, std::min(s->nsc, (s->rows_bps > 0 ? std::min(occ, s->rows_bps) : occ) * s->sms));
     VBC_TRY(set_smem(k_count_near<M>, s->smem_near()));
     occ = 1 << 30;
-    resident((const void*)k_count_near<M>, s->smem_near());
+    resident((const void*)k_count_near<M>, SC_TPB, s->smem_near());
     s->near_grid = std::max(1, std::min(s->nsc, (s->near_bps > 0 ? std::min(occ, s->near_bps) : occ) * s->sms));
     return VBC_OK;
 }
@@ -617,16 +638,23 @@ int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window)
         k_count_near<M><<<s->near_grid, SC_TPB, s->smem_near(), s->stream>>>(
             s->nsc, s->geom, s->coef, pos, s->grid(), s->caps(), s->aux(), s->nnb, (real*)s->ds, (real2*)s->sA, out,
             s->ulist, s->st);
-        k_count_rows<M><<<s->row_grid, SC_TPB, s->smem_rows(0), s->stream>>>(
-            (int)s->n, s->nsc, s->geom, s->coef, pos, s->grid(), s->caps(), s->aux(), s->nbr, s->nnb, s->id, (real*)s->ds,
-            (real2*)s->sA, out, s->ulist, s->wpart, (const long long*)s->x, s->st);
+        for_row_tpb(s->row_tpb, [&](auto nt) -> int {
+            constexpr int NT = decltype(nt)::value;
+            k_count_rows<M, NT><<<s->row_grid, NT, s->smem_rows(0), s->stream>>>(
+                (int)s->n, s->nsc, s->tpp_max, s->geom, s->coef, pos, s->grid(), s->caps(), s->aux(), s->nbr, s->nnb,
+                s->id, (real*)s->ds, (real2*)s->sA, out, s->ulist, s->wpart, (const long long*)s->x, s->st);
+            return VBC_OK;
+        });
     }
     {
         Timed t(s, VBC_K_CHAIN);
-        k_chain<M><<<s->row_grid, SC_TPB, s->smem_rows(0), s->stream>>>((int)s->n, s->nsc, s->geom, s->coef, pos, s->grid(),
-                                                                    s->caps(), s->aux(), s->nbr, s->nnb,
-                                                                    (const real*)s->ds, (real2*)s->sA, s->wpart,
-                                                                    s->st);
+        for_row_tpb(s->row_tpb, [&](auto nt) -> int {
+            constexpr int NT = decltype(nt)::value;
+            k_chain<M, NT><<<s->row_grid, NT, s->smem_rows(0), s->stream>>>(
+                (int)s->n, s->nsc, s->tpp_max, s->geom, s->coef, pos, s->grid(), s->caps(), s->aux(), s->nbr, s->nnb,
+                (const real*)s->ds, (real2*)s->sA, s->wpart, s->st);
+            return VBC_OK;
+        });
     }
     return check_launch(s, 3);
 }
@@ -651,9 +679,13 @@ int enqueue_force(vbc_system* s, const StepArgs& a)
             }
         }
         if (!done)
-            k_force_rows<M><<<s->row_grid, SC_TPB, s->smem_rows(s->real_bytes()), s->stream>>>(
-                n, s->nsc, s->geom, s->coef, pos, s->grid(), s->caps(), s->aux(), s->nbr, s->nnb,
-                (const real2*)s->sA, s->st);
+            for_row_tpb(s->row_tpb, [&](auto nt) -> int {
+                constexpr int NT = decltype(nt)::value;
+                k_force_rows<M, NT><<<s->row_grid, NT, s->smem_rows(s->real_bytes()), s->stream>>>(
+                    n, s->nsc, s->tpp_max, s->geom, s->coef, pos, s->grid(), s->caps(), s->aux(), s->nbr, s->nnb,
+                    (const real2*)s->sA, s->st);
+                return VBC_OK;
+            });
         k_step<M, EPI><<<blocks_for(n, TPB), TPB, 0, s->stream>>>(n, s->geom, s->aux(), s->id, pos_next,
                                                                   (const pos_t*)s->xref, a, s->st);
     }
@@ -2087,9 +2119,16 @@ int vbc_set_tuning(vbc_system* s, const vbc_tuning* t)
     VBC_TRY(check_sys(s));
     if (!t || t->rows_blocks_per_sm < 0 || t->count_blocks_per_sm < 0)
         return fail(VBC_ERR_INVALID_ARG, "tuning must not be NULL and its block counts must be >= 0");
+    const int tpb = t->rows_threads_per_block, tmax = t->threads_per_row_max;
+    if (tpb != 0 && tpb != 128 && tpb != 256 && tpb != 512)
+        return fail(VBC_ERR_INVALID_ARG, "rows_threads_per_block must be 0, 128, 256 or 512");
+    if (tmax != 0 && (tmax < 1 || tmax > 32 || (tmax & (tmax - 1)) != 0))
+        return fail(VBC_ERR_INVALID_ARG, "threads_per_row_max must be 0 or a power of two in [1, 32]");
     VBC_CUDA(cudaStreamSynchronize(s->stream));
     s->rows_bps = t->rows_blocks_per_sm;
     s->near_bps = t->count_blocks_per_sm;
+    s->row_tpb = tpb ? tpb : 128;
+    s->tpp_max = tmax ? tmax : 32;
     VBC_TRY(configure(s));
     s->layout_version += 1;  // the graphs are captured again with the new grids
     return VBC_OK;
@@ -2114,16 +2153,24 @@ int vbc_autotune(vbc_system* s, int64_t trial_steps, double dt, double kT, doubl
         ms = (double)f / (double)trial_steps;
         return VBC_OK;
     };
-    // one knob at a time: the row walks' grid, then the close count's
-    static const int cand[] = {0, 8, 4, 2, 1};
-    vbc_tuning best{0, 0, 0.0};
+    // one knob at a time: the row walks' block shape, their grid, their threads per
+    // row, then the close count's grid (the first candidate of each is the default)
+    static const int cand_tpb[] = {128, 256, 512};
+    static const int cand_bps[] = {0, 8, 4, 2, 1};
+    static const int cand_tpp[] = {32, 8, 4, 2};
+    vbc_tuning best{0, 0, 128, 32, 0.0};
     double best_ms = 1e300;
     int rc = VBC_OK;
-    for (int knob = 0; knob < 2 && rc == VBC_OK; ++knob) {
-        for (int c : cand) {
+    for (int knob = 0; knob < 4 && rc == VBC_OK; ++knob) {
+        const int* cand = knob == 0 ? cand_tpb : (knob == 2 ? cand_tpp : cand_bps);
+        const int ncand = knob == 0 ? 3 : (knob == 2 ? 4 : 5);
+        for (int i = 0; i < ncand; ++i) {
             vbc_tuning t = best;
-            if (knob == 0) t.rows_blocks_per_sm = c;
-            else t.count_blocks_per_sm = c;
+            if (knob == 0) t.rows_threads_per_block = cand[i];
+            else if (knob == 1) t.rows_blocks_per_sm = cand[i];
+            else if (knob == 2) t.threads_per_row_max = cand[i];
+            else t.count_blocks_per_sm = cand[i];
+            if (knob > 0 && i == 0) continue;  // the current best, already timed
             double ms = 0.0;
             if ((rc = trial(t, ms)) != VBC_OK) break;
             // the default (tried first) is kept unless a setting beats it by 2%: trials that

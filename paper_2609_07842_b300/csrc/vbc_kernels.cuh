@@ -373,9 +373,10 @@ __device__ __forceinline__ int staged_index(const SuperTab& T, int m)
 }
 
 // Copies every staged particle: put(m, get(j)) for staging index m and
-// sorted index j, B loads in flight per thread.
+// sorted index j, B loads in flight per thread; with rec, also records j in
+// rec[m] (the list build's staged-index table).
 template <class V, int B = 4, class Get, class Put>
-__device__ __forceinline__ void stage(const SuperTab& T, int total, Get&& get, Put&& put)
+__device__ __forceinline__ void stage(const SuperTab& T, int total, Get&& get, Put&& put, int* rec = nullptr)
 {
     for (int m0 = threadIdx.x; m0 < total; m0 += SC_TPB * B) {
         int jj[B];
@@ -390,7 +391,10 @@ __device__ __forceinline__ void stage(const SuperTab& T, int total, Get&& get, P
             if (jj[u] >= 0) v[u] = get(jj[u]);
 #pragma unroll
         for (int u = 0; u < B; ++u)
-            if (jj[u] >= 0) put(m0 + u * SC_TPB, v[u]);
+            if (jj[u] >= 0) {
+                put(m0 + u * SC_TPB, v[u]);
+                if (rec) rec[m0 + u * SC_TPB] = jj[u];
+            }
     }
 }
 
@@ -570,13 +574,16 @@ __device__ __forceinline__ void shift192(unsigned long long& a0, unsigned long l
 }
 
 // ================================================================ rebuild: lists
+#ifndef NLIST_MIN_BLOCKS
+#define NLIST_MIN_BLOCKS 8
+#endif
 // One block per cell group: stage the surrounding cells, then each thread
 // takes own particles and scans the 9 contiguous x rows of their 27-cell
 // neighbourhood, writing a two-ended row (near from the front, far from the
 // back) into a per-particle scratch row in global memory; the rows are then
 // packed into the block's segment.
 template <class M, bool REL>
-__global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_t* __restrict__ pos, SuperGrid G,
+__global__ void __launch_bounds__(SC_TPB, NLIST_MIN_BLOCKS) k_nlist(Geom g, const typename M::pos_t* __restrict__ pos, SuperGrid G,
                                                   SuperCaps cp, ListParams lp, uint16_t* __restrict__ scratch,
                                                   uint16_t* __restrict__ nbr, int* __restrict__ nnb, GroupAux aux,
                                                   Status* st)
@@ -610,6 +617,7 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
     int* roff = (int*)(smem + ly.roff);
     int* rnn = (int*)(smem + ly.rnn);
     int* rself = (int*)(smem + ly.rself);  // own staging index of each own particle
+    int* sidx = aux.stage_idx + (size_t)blockIdx.x * cp.smax;  // the staged-index table the passes read
     if constexpr (REL) {
         // reference: the centre of the block's own cells (a cell boundary)
         const int org = __ldg(G.sc_org + blockIdx.x);
@@ -623,15 +631,10 @@ __global__ void __launch_bounds__(SC_TPB) k_nlist(Geom g, const typename M::pos_
                 spos[m] = make_float4((float)(int)((uint32_t)v.x - ref[0]) * g.s32,
                                       (float)(int)((uint32_t)v.y - ref[1]) * g.s32,
                                       (float)(int)((uint32_t)v.z - ref[2]) * g.s32, 0.0f);
-            });
+            },
+            sidx);
     } else {
-        stage<pos_t>(T, total, [&](int j) { return pos[j]; }, [&](int m, const pos_t& v) { spos[m] = v; });
-    }
-    {
-        int* sidx = aux.stage_idx + (size_t)blockIdx.x * cp.smax;
-        for (int m = t; m < total; m += SC_TPB) {
-            sidx[m] = staged_index(T, m);
-        }
+        stage<pos_t>(T, total, [&](int j) { return pos[j]; }, [&](int m, const pos_t& v) { spos[m] = v; }, sidx);
     }
     __syncthreads();
     int mx = 0;
@@ -1165,17 +1168,17 @@ struct __align__(32) F64x4 {
 
 // Copies a group's staged particles: put(m, j) for staging index m and sorted
 // index j, four loads of the index table in flight per thread.
-template <class Put>
+template <int NT = SC_TPB, class Put>
 __device__ __forceinline__ void stage_by_table(const int* __restrict__ sidx, int total, Put&& put)
 {
     constexpr int B = 4;
-    for (int m0 = threadIdx.x; m0 < total; m0 += SC_TPB * B) {
+    for (int m0 = threadIdx.x; m0 < total; m0 += NT * B) {
         int jj[B];
 #pragma unroll
-        for (int u = 0; u < B; ++u) jj[u] = m0 + u * SC_TPB < total ? __ldg(sidx + m0 + u * SC_TPB) : -1;
+        for (int u = 0; u < B; ++u) jj[u] = m0 + u * NT < total ? __ldg(sidx + m0 + u * NT) : -1;
 #pragma unroll
         for (int u = 0; u < B; ++u)
-            if (jj[u] >= 0) put(m0 + u * SC_TPB, jj[u]);
+            if (jj[u] >= 0) put(m0 + u * NT, jj[u]);
     }
 }
 
@@ -1271,18 +1274,21 @@ __global__ void __launch_bounds__(SC_TPB) k_count_near(int ngroups, Geom g, Coef
 // the group's staged-index table.  Dense otherwise: one block per cell group,
 // which stages its neighbourhood in shared memory; a lane group of tpp
 // threads walks each listed own particle's row, tpp the largest power of two
-// (at most 32) with (listed particles) * tpp <= SC_TPB, each thread taking
-// every tpp-th 4-entry chunk.  The order of the terms depends only on the row
-// and the mode, so every result is a function of the state alone.  Both modes
-// run a grid that stays resident (a few blocks per SM), the dense one taking
-// the cell groups in a grid-stride loop.
+// (at most tmax <= 32) with (listed particles) * tpp <= NT, each thread
+// taking every tpp-th 4-entry chunk.  NT (threads per block: 128, 256 or 512)
+// and tmax are grid settings (vbc_set_tuning).  The order of the terms
+// depends only on the row, the mode and these settings, so every result is a
+// function of the state and the settings alone; the integer counts do not
+// depend on the settings at all.  Both modes run a grid that stays resident
+// (a few blocks per SM), the dense one taking the cell groups in a
+// grid-stride loop.
 constexpr int DENSE_DIV = 16;
-constexpr int ROW_WARPS = SC_TPB / 32;
 
-__device__ __forceinline__ int dense_tpp(int nl)
+template <int NT>
+__device__ __forceinline__ int dense_tpp(int nl, int tmax)
 {
-    int t = 32;
-    while (t > 1 && nl * t > SC_TPB) t >>= 1;
+    int t = tmax;
+    while (t > 1 && nl * t > NT) t >>= 1;
     return t;
 }
 
@@ -1304,6 +1310,21 @@ __device__ __forceinline__ void walk_chunks(const uint16_t* __restrict__ row, in
 #pragma unroll
         for (int k = 0; k < 4; ++k)
             if (e0 + k < len) visit(h[k]);
+    }
+}
+
+// The same with the pads visited too: a pad repeats the particle's own
+// staging index (separation 0), which adds exactly nothing to a force sum,
+// so the force walk needs no test per entry.
+template <class Visit>
+__device__ __forceinline__ void walk_chunks_padded(const uint16_t* __restrict__ row, int len, int sub, int tpp,
+                                                   Visit&& visit)
+{
+    for (int e0 = 4 * sub; e0 < len; e0 += 4 * tpp) {
+        int h[4];
+        unpack4(__ldg(reinterpret_cast<const uint2*>(row + e0)), h);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) visit(h[k]);
     }
 }
 
@@ -1333,12 +1354,12 @@ __host__ __device__ inline DenseLayout dense_layout(const SuperCaps& cp, size_t 
 
 // Lists the own particles of group b that pick(j) selects (j from 0); the
 // whole block calls it.  Returns their number.
-template <class Pick>
+template <int NT, class Pick>
 __device__ __forceinline__ int list_own(int n_own, int* plist, int* s_n, Pick&& pick)
 {
     if (threadIdx.x == 0) *s_n = 0;
     __syncthreads();
-    for (int j = threadIdx.x; j < n_own; j += SC_TPB)
+    for (int j = threadIdx.x; j < n_own; j += NT)
         if (pick(j)) plist[atomicAdd(s_n, 1)] = j;
     __syncthreads();
     return *s_n;
@@ -1347,12 +1368,12 @@ __device__ __forceinline__ int list_own(int n_own, int* plist, int* s_n, Pick&& 
 // Runs body(u, sub, tpp) for the listed particles of a dense walk: slot u of
 // the list (u >= nl on idle lanes, which must still take part in the lane
 // group's sums), thread sub of its lane group.
-template <class Body>
-__device__ __forceinline__ void dense_rounds(int nl, Body&& body)
+template <int NT, class Body>
+__device__ __forceinline__ void dense_rounds(int nl, int tmax, Body&& body)
 {
-    const int tpp = dense_tpp(nl), per_warp = 32 / tpp;
+    const int tpp = dense_tpp<NT>(nl, tmax), per_warp = 32 / tpp;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int base = warp * per_warp; base < nl; base += ROW_WARPS * per_warp)
+    for (int base = warp * per_warp; base < nl; base += (NT / 32) * per_warp)
         body(base + lane / tpp, lane & (tpp - 1), tpp);
 }
 
@@ -1423,8 +1444,8 @@ __device__ __forceinline__ void count_row_out(int p, typename M::real s, typenam
     }
 }
 
-template <class M>
-__global__ void __launch_bounds__(SC_TPB) k_count_rows(int n, int ngroups, Geom g, Coef c, typename M::pos_t* __restrict__ pos,
+template <class M, int NT>
+__global__ void __launch_bounds__(NT) k_count_rows(int n, int ngroups, int tmax, Geom g, Coef c, typename M::pos_t* __restrict__ pos,
                                                        SuperGrid G, SuperCaps cp, GroupAux aux,
                                                        const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
                                                        const int* __restrict__ id, typename M::real* __restrict__ ds_out,
@@ -1448,7 +1469,7 @@ __global__ void __launch_bounds__(SC_TPB) k_count_rows(int n, int ngroups, Geom 
     };
     const bool want_n = out.n_out != nullptr;
     if (nu <= n / DENSE_DIV) {
-        for (int k = blockIdx.x * ROW_WARPS + (threadIdx.x >> 5); k < nu; k += gridDim.x * ROW_WARPS) {
+        for (int k = blockIdx.x * (NT / 32) + (threadIdx.x >> 5); k < nu; k += gridDim.x * (NT / 32)) {
             const int p = ulist[k];
             const int ra = __ldg(aux.roff + p), b = ra / cp.seg;
             const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
@@ -1473,16 +1494,16 @@ __global__ void __launch_bounds__(SC_TPB) k_count_rows(int n, int ngroups, Geom 
         __syncthreads();  // the previous group is done with the shared arrays
         const int p0 = __ldg(G.cell_start + OWN_CELLS * b);
         const int n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
-        const int nl = list_own(n_own, plist, &s_n, [&](int j) { return isnan(ds_out[p0 + j]); });
+        const int nl = list_own<NT>(n_own, plist, &s_n, [&](int j) { return isnan(ds_out[p0 + j]); });
         if (nl == 0) continue;
         // the count reads no s_j, so the spare word of a staged position holds its residuals
-        stage_by_table(aux.stage_idx + (size_t)b * cp.smax, __ldg(aux.meta + b).x, [&](int m, int jj) {
+        stage_by_table<NT>(aux.stage_idx + (size_t)b * cp.smax, __ldg(aux.meta + b).x, [&](int m, int jj) {
             pos_t pj = pos[jj];
             if constexpr (!M::fp64) pj.w = resid_of(jj);
             spos[m] = pj;
         });
         __syncthreads();
-        dense_rounds(nl, [&](int u, int sub, int tpp) {
+        dense_rounds<NT>(nl, tmax, [&](int u, int sub, int tpp) {
             const bool act = u < nl;
             const int p = p0 + (act ? plist[u] : 0);
             const uint16_t* row = nbr + __ldg(aux.roff + p);
@@ -1530,8 +1551,8 @@ __device__ __forceinline__ typename M::real chain_row(const typename M::pos_t& p
     return group_sum(acc, width);
 }
 
-template <class M>
-__global__ void __launch_bounds__(SC_TPB) k_chain(int n, int ngroups, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
+template <class M, int NT>
+__global__ void __launch_bounds__(NT) k_chain(int n, int ngroups, int tmax, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
                                                   SuperGrid G, SuperCaps cp, GroupAux aux,
                                                   const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
                                                   const typename M::real* __restrict__ ds,
@@ -1543,7 +1564,7 @@ __global__ void __launch_bounds__(SC_TPB) k_chain(int n, int ngroups, Geom g, Co
     if (halted(st)) return;
     const int nw = st->nwin;
     if (nw <= n / DENSE_DIV) {
-        for (int k = blockIdx.x * ROW_WARPS + (threadIdx.x >> 5); k < nw; k += gridDim.x * ROW_WARPS) {
+        for (int k = blockIdx.x * (NT / 32) + (threadIdx.x >> 5); k < nw; k += gridDim.x * (NT / 32)) {
             const int p = wpart[k];
             const int ra = __ldg(aux.roff + p), b = ra / cp.seg;
             const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
@@ -1572,12 +1593,12 @@ __global__ void __launch_bounds__(SC_TPB) k_chain(int n, int ngroups, Geom g, Co
         __syncthreads();  // the previous group is done with the shared arrays
         const int p0 = __ldg(G.cell_start + OWN_CELLS * b);
         const int n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
-        const int nl = list_own(n_own, plist, &s_n, [&](int j) { return ds[p0 + j] != (real)0; });
+        const int nl = list_own<NT>(n_own, plist, &s_n, [&](int j) { return ds[p0 + j] != (real)0; });
         if (nl == 0) continue;
-        stage_by_table(aux.stage_idx + (size_t)b * cp.smax, __ldg(aux.meta + b).x,
+        stage_by_table<NT>(aux.stage_idx + (size_t)b * cp.smax, __ldg(aux.meta + b).x,
                        [&](int m, int jj) { spos[m] = pos[jj]; });
         __syncthreads();
-        dense_rounds(nl, [&](int u, int sub, int tpp) {
+        dense_rounds<NT>(nl, tmax, [&](int u, int sub, int tpp) {
             const bool act = u < nl;
             const int p = p0 + (act ? plist[u] : 0);
             const uint16_t* row = nbr + __ldg(aux.roff + p);
@@ -1628,8 +1649,8 @@ __device__ __forceinline__ bool tagged_whole(const void* fcore, int p)
     else return static_cast<const float4*>(fcore)[p].w != 0.0f;
 }
 
-template <class M>
-__global__ void __launch_bounds__(SC_TPB) k_force_rows(int n, int ngroups, Geom g, Coef c,
+template <class M, int NT>
+__global__ void __launch_bounds__(NT) k_force_rows(int n, int ngroups, int tmax, Geom g, Coef c,
                                                        const typename M::pos_t* __restrict__ pos, SuperGrid G,
                                                        SuperCaps cp, GroupAux aux, const uint16_t* __restrict__ nbr,
                                                        const int* __restrict__ nnb,
@@ -1642,7 +1663,7 @@ __global__ void __launch_bounds__(SC_TPB) k_force_rows(int n, int ngroups, Geom 
     const bool useA = nw > 0;                  // A_j != 0 only for window particles
     const bool all = nw > n / DENSE_DIV;       // k_chain ran dense and cleared no tag
     if (!all && ng <= n / DENSE_DIV) {
-        for (int k = blockIdx.x * ROW_WARPS + (threadIdx.x >> 5); k < ng; k += gridDim.x * ROW_WARPS) {
+        for (int k = blockIdx.x * (NT / 32) + (threadIdx.x >> 5); k < ng; k += gridDim.x * (NT / 32)) {
             const int p = aux.glist[k];
             const int ra = __ldg(aux.roff + p), b = ra / cp.seg;
             const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
@@ -1674,18 +1695,18 @@ __global__ void __launch_bounds__(SC_TPB) k_force_rows(int n, int ngroups, Geom 
         const int n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
         int nl;
         if (all) {
-            for (int j = threadIdx.x; j < n_own; j += SC_TPB) plist[j] = j;
+            for (int j = threadIdx.x; j < n_own; j += NT) plist[j] = j;
             nl = n_own;
         } else {
-            nl = list_own(n_own, plist, &s_n, [&](int j) { return !tagged_whole<M>(aux.fcore, p0 + j); });
+            nl = list_own<NT>(n_own, plist, &s_n, [&](int j) { return !tagged_whole<M>(aux.fcore, p0 + j); });
         }
         if (nl == 0) continue;
-        stage_by_table(aux.stage_idx + (size_t)b * cp.smax, __ldg(aux.meta + b).x, [&](int m, int jj) {
+        stage_by_table<NT>(aux.stage_idx + (size_t)b * cp.smax, __ldg(aux.meta + b).x, [&](int m, int jj) {
             spos[m] = pos[jj];
             sAj[m] = useA ? sA[jj].y : (real)0;
         });
         __syncthreads();
-        dense_rounds(nl, [&](int u, int sub, int tpp) {
+        dense_rounds<NT>(nl, tmax, [&](int u, int sub, int tpp) {
             const bool act = u < nl;
             const int p = p0 + (act ? plist[u] : 0);
             const uint16_t* row = nbr + __ldg(aux.roff + p);
@@ -1693,7 +1714,7 @@ __global__ void __launch_bounds__(SC_TPB) k_force_rows(int n, int ngroups, Geom 
             const pos_t pi = pos[p];
             real f[3];
             force_row<M>(pi, get_s(pi), useA ? sA[p].y : (real)0,
-                         [&](auto&& v) { walk_chunks(row, len, sub, tpp, v); }, tpp,
+                         [&](auto&& v) { walk_chunks_padded(row, len, sub, tpp, v); }, tpp,
                          [&](int m, real& Aj) {
                              Aj = sAj[m];
                              return spos[m];

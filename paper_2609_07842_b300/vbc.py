@@ -79,6 +79,7 @@ ZHIST = 32
 class Tuning(ctypes.Structure):
     """Grid settings of the close count and the row walks (vbc_autotune)."""
     _fields_ = [("rows_blocks_per_sm", ctypes.c_int32), ("count_blocks_per_sm", ctypes.c_int32),
+                ("rows_threads_per_block", ctypes.c_int32), ("threads_per_row_max", ctypes.c_int32),
                 ("ms_per_step", ctypes.c_double)]
 
 
@@ -392,8 +393,10 @@ class System:
         _check(load().vbc_autotune(self._h, int(trial_steps), dt, kT, gamma, ctypes.byref(t)))
         return t
 
-    def set_tuning(self, rows_blocks_per_sm: int = 0, count_blocks_per_sm: int = 0):
-        t = Tuning(rows_blocks_per_sm=rows_blocks_per_sm, count_blocks_per_sm=count_blocks_per_sm)
+    def set_tuning(self, rows_blocks_per_sm: int = 0, count_blocks_per_sm: int = 0, rows_threads_per_block: int = 0,
+                   threads_per_row_max: int = 0):
+        t = Tuning(rows_blocks_per_sm=rows_blocks_per_sm, count_blocks_per_sm=count_blocks_per_sm,
+                   rows_threads_per_block=rows_threads_per_block, threads_per_row_max=threads_per_row_max)
         _check(load().vbc_set_tuning(self._h, ctypes.byref(t)))
 
     def observables(self, z: bool = False):

@@ -83,11 +83,46 @@ def test_grid_settings_change_no_result(prec):
         b.close()
 
 
+@pytest.mark.parametrize("prec", [vbc.VBC_FP32_SPLIT, vbc.VBC_FP64])
+def test_block_shape_and_threads_per_row_keep_parity(prec):
+    """The row walks' block shape (128, 256, 512 threads) and the cap on threads
+    per row only re-split the dense walks between threads: the FP32-split
+    counts (integer sums) are the same under every setting, the FP64 ones agree
+    to rounding, and forces stay within the parity tolerances of the oracle
+    (1e-5 rms|F| in the FP32 split, 1e-10 in FP64)."""
+    import oracle
+    pos, L = inputs.uniform_positions(30000, 0.5, seed=91)
+    n0 = oracle.evaluate(pos, L, oracle.Params(E_a=8.0), mode=1).counts
+    p = oracle.Params(E_a=8.0, f=inputs.quantile_valency(n0, 0.5))
+    ref = oracle.evaluate(pos, L, p, mode=1)
+    assert np.mean(ref.ds != 0.0) > 0.1
+    rms = np.sqrt(np.mean(np.sum(ref.F ** 2, axis=1)))
+    tol = 1e-5 if prec == vbc.VBC_FP32_SPLIT else 1e-10
+    counts = []
+    with vbc.System(pos, L, vbc.params(E_a=8.0, f=p.f), precision=prec) as s:
+        for tpb, tmax in ((128, 32), (256, 32), (512, 32), (256, 1), (512, 4), (128, 2)):
+            s.set_tuning(rows_threads_per_block=tpb, threads_per_row_max=tmax)
+            r = s.compute(F=True, counts=True)
+            counts.append(r.counts)
+            assert np.max(np.abs(r.counts - ref.counts)) <= 1e-6
+            assert np.max(np.abs(r.F - ref.F)) <= tol * rms
+        with pytest.raises(vbc.VBCError):
+            s.set_tuning(rows_threads_per_block=200)
+        with pytest.raises(vbc.VBCError):
+            s.set_tuning(threads_per_row_max=3)
+    for c in counts[1:]:
+        if prec == vbc.VBC_FP32_SPLIT:
+            np.testing.assert_array_equal(c, counts[0])
+        else:
+            assert np.max(np.abs(c - counts[0])) <= 1e-12
+
+
 def test_autotune_picks_a_setting_and_keeps_stepping():
     c = SYS[1]
     with _make(*c, vbc.VBC_FP32_SPLIT) as s:
         t = s.autotune(trial_steps=8, kT=c[3])
         assert t.rows_blocks_per_sm in (0, 1, 2, 4, 8) and t.count_blocks_per_sm in (0, 1, 2, 4, 8)
+        assert t.rows_threads_per_block in (128, 256, 512) and t.threads_per_row_max in (2, 4, 8, 32)
         assert 0.0 < t.ms_per_step < 100.0
         s.step(20, 0.005, c[3], 1.0)
         assert s.get_state()[2] > 20
