@@ -378,10 +378,11 @@ def batched_systems(args):
 
 
 def run_batched(args):
-    """The uneven systems advanced by args.batched_steps steps, once with one
-    vbc_batch_step (one graph launch per two steps for all of them) and once one
-    system after another (vbc_step_langevin each, its own graphs), after an
-    untimed equilibration; aggregate timesteps/s of each (CUDA events)."""
+    """The uneven systems advanced by args.batched_steps steps with vbc_batch_step
+    in the fused mode (one cooperative launch per iteration for all of them), in
+    the graph mode (one graph launch per two steps), and one system after another
+    (vbc_step_langevin each, its own graphs), after an untimed equilibration;
+    aggregate timesteps/s of each (host clock, device synchronised on both sides)."""
     import torch
     from paper_2609_07842_b300 import inputs, vbc
     cfg = batched_systems(args)
@@ -393,23 +394,32 @@ def run_batched(args):
     kts = [c[3] for c in cfg]
     out = {}
     try:
+        times = {}
         with vbc.Batch(systems) as b:
             b.step(200, DT, kts, GAMMA)                  # equilibration, untimed
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            b.step(args.batched_steps, DT, kts, GAMMA)
-            torch.cuda.synchronize()
-            t_batch = time.perf_counter() - t0
+            for name, mode in (("batched", vbc.VBC_BATCH_FUSED), ("batched_graphs", vbc.VBC_BATCH_GRAPHS)):
+                b.set_mode(mode)
+                b.step(4, DT, kts, GAMMA)                # untimed: captures the graphs of this mode
+                torch.cuda.synchronize()
+                f0 = b.fused_launches()
+                t0 = time.perf_counter()
+                b.step(args.batched_steps, DT, kts, GAMMA)
+                torch.cuda.synchronize()
+                times[name] = time.perf_counter() - t0
+                out[name + "_launches"] = b.fused_launches() - f0
         t0 = time.perf_counter()
         for s, kt in zip(systems, kts):
             s.step(args.batched_steps, DT, kt, GAMMA)
         torch.cuda.synchronize()
-        t_one = time.perf_counter() - t0
+        times["one_at_a_time"] = time.perf_counter() - t0
         nsys, ntot = len(systems), sum(c[0] for c in cfg)
-        for name, t in (("batched", t_batch), ("one_at_a_time", t_one)):
+        for name, t in times.items():
             out[name] = {"seconds": t, "timesteps_per_s": nsys * args.batched_steps / t,
                          "particle_steps_per_s": ntot * args.batched_steps / t}
-        out["speedup"] = t_one / t_batch
+        out["batched"]["how"] = "one cooperative launch per iteration for all systems (fused)"
+        out["batched_graphs"]["how"] = "each system's two-step CUDA graph captured side by side into one graph"
+        out["speedup"] = times["one_at_a_time"] / times["batched"]
+        out["speedup_graphs"] = times["one_at_a_time"] / times["batched_graphs"]
         out["workload"] = (f"{nsys} systems, N log-uniform in [2k, 64k] ({ntot:,} particles), valency 1..6, "
                            f"kT 0.8..1.5, rho 0.2..0.6, E_a {args.E_a}, {args.batched_steps} steps each after 200")
     finally:

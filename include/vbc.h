@@ -323,6 +323,31 @@ int vbc_batch_step(vbc_batch* batch, int64_t nsteps, double dt, const double* kT
 /* Release the batch (not its systems).  NULL-safe. */
 void vbc_batch_destroy(vbc_batch* batch);
 
+/*
+ * How a batch advances (the paper has no counterpart; its parameter sweeps of
+ * Sec. 5 motivate running many systems on one GPU).  VBC_BATCH_FUSED (the
+ * default): iteration 0 of each system on its own stream, then one
+ * cooperative launch per Langevin iteration for all systems together, whose
+ * phases (gate, list rebuilds, counts, chain-rule terms, forces, update) take
+ * the work items of every system and are separated by grid-wide waits; the
+ * result of each system is bitwise the one it gets stepped alone.  It takes
+ * single-type systems of one precision on the default row-walk block shape;
+ * any other batch, or one whose largest system does not fit the launch's
+ * shared memory, runs as VBC_BATCH_GRAPHS: each system's two-step graph
+ * captured side by side into one CUDA graph.
+ * wait_limit: spins (of about 100 ns each) a grid-wide wait makes before it
+ * gives up; < 0 restores the default (2^22, about half a second).  A wait that
+ * gives up ends the launch: vbc_batch_step then returns VBC_ERR_TIMEOUT and
+ * every system of the batch is halted (its state incomplete) until
+ * vbc_set_state loads a state again; the GPU context stays usable.
+ * Errors: INVALID_ARG.
+ */
+enum { VBC_BATCH_FUSED = 0, VBC_BATCH_GRAPHS = 1 };
+int vbc_batch_set_mode(vbc_batch* batch, int mode, int64_t wait_limit);
+
+/* Fused launches the batch has issued (one per iteration of vbc_batch_step). */
+int64_t vbc_batch_fused_launches(vbc_batch* batch);
+
 /* ------------------------------------------------------------------ autotuning
  * The close-neighbour count and the row walks run resident grids, as many
  * blocks per SM as fit by default.  For small systems (and many systems side

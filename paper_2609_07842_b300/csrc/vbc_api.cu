@@ -10,6 +10,7 @@
 // iteration that stopped, so the trajectory is the same as with large enough
 // capacities from the start.
 #include "vbc.h"
+#include "vbc_batch.cuh"
 #include "vbc_kernels.cuh"
 #include "vbc_typed.cuh"
 
@@ -176,6 +177,7 @@ struct vbc_system {
     // Cleared by every call that changes the state, the sorted order or the
     // parameters, or that writes the force slots by another path.
     bool force_fresh = false;
+    bool aborted = false;  // a fused batch iteration gave up waiting (see vbc_batch.cuh)
 
     // per-kernel event timing
     bool prof = false;
@@ -210,6 +212,16 @@ struct vbc_batch {
     std::vector<int> cur;                // position buffer of each system the graph was captured for
     std::vector<long long> layout;
     std::vector<double> dt, c1, c2;      // the step coefficients it was captured with
+    // the fused path: one cooperative launch per iteration for all systems (vbc_batch.cuh)
+    int mode = VBC_BATCH_FUSED;
+    long long wait_limit = 1LL << 22;    // spins of a grid-wide wait before it gives up
+    void* d_desc = nullptr;              // [K] SysDesc of the systems' mode
+    size_t desc_bytes = 0;
+    int* d_offs = nullptr;               // [BK_NKIND][K + 1] item offsets
+    size_t offs_count = 0;
+    BatchCtl* ctl = nullptr;
+    BatchCtl* ctl_host = nullptr;        // pinned
+    long long fused_launches = 0;
 };
 
 namespace {
@@ -246,6 +258,8 @@ __global__ void k_set_flag(Status* st, int which, int value)
     if (which == 0) st->rebuild = value;
 }
 
+__global__ void k_abort(Status* st) { st->aborted = 1; }
+
 __global__ void k_clear_halt(Status* st)
 {
     st->overflow = 0;
@@ -253,6 +267,7 @@ __global__ void k_clear_halt(Status* st)
     st->frozen = 0;
     st->crowded = 0;
     st->bad_input = 0;
+    st->aborted = 0;
     st->rebuild = 1;
 }
 
@@ -622,6 +637,31 @@ int enqueue_typed_count_chain(vbc_system* s, double* n_out, bool want_window)
     return check_launch(s, 2);
 }
 
+// The argument block of the row walks for the current position buffer.
+template <class M>
+RowArgs<M> row_args(const vbc_system* s, const CountOut& out, int cur = -1)
+{
+    RowArgs<M> A{};
+    A.n = (int)s->n;
+    A.g = s->geom;
+    A.c = s->coef;
+    A.pos = (typename M::pos_t*)s->pos[cur < 0 ? s->cur : cur];
+    A.G = s->grid();
+    A.cp = s->caps();
+    A.aux = s->aux();
+    A.nbr = s->nbr;
+    A.nnb = s->nnb;
+    A.id = s->id;
+    A.ds = (typename M::real*)s->ds;
+    A.sA = (typename M::real2*)s->sA;
+    A.out = out;
+    A.ulist = s->ulist;
+    A.wpart = s->wpart;
+    A.X = (const long long*)s->x;
+    A.st = s->st;
+    return A;
+}
+
 template <class M>
 int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window)
 {
@@ -640,9 +680,8 @@ int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window)
             s->ulist, s->st);
         for_row_tpb(s->row_tpb, [&](auto nt) -> int {
             constexpr int NT = decltype(nt)::value;
-            k_count_rows<M, NT><<<s->row_grid, NT, s->smem_rows(0), s->stream>>>(
-                (int)s->n, s->nsc, s->tpp_max, s->geom, s->coef, pos, s->grid(), s->caps(), s->aux(), s->nbr, s->nnb,
-                s->id, (real*)s->ds, (real2*)s->sA, out, s->ulist, s->wpart, (const long long*)s->x, s->st);
+            k_count_rows<M, NT><<<s->row_grid, NT, s->smem_rows(0), s->stream>>>(row_args<M>(s, out), s->nsc,
+                                                                                 s->tpp_max);
             return VBC_OK;
         });
     }
@@ -650,9 +689,7 @@ int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window)
         Timed t(s, VBC_K_CHAIN);
         for_row_tpb(s->row_tpb, [&](auto nt) -> int {
             constexpr int NT = decltype(nt)::value;
-            k_chain<M, NT><<<s->row_grid, NT, s->smem_rows(0), s->stream>>>(
-                (int)s->n, s->nsc, s->tpp_max, s->geom, s->coef, pos, s->grid(), s->caps(), s->aux(), s->nbr, s->nnb,
-                (const real*)s->ds, (real2*)s->sA, s->wpart, s->st);
+            k_chain<M, NT><<<s->row_grid, NT, s->smem_rows(0), s->stream>>>(row_args<M>(s, out), s->nsc, s->tpp_max);
             return VBC_OK;
         });
     }
@@ -682,8 +719,7 @@ int enqueue_force(vbc_system* s, const StepArgs& a)
             for_row_tpb(s->row_tpb, [&](auto nt) -> int {
                 constexpr int NT = decltype(nt)::value;
                 k_force_rows<M, NT><<<s->row_grid, NT, s->smem_rows(s->real_bytes()), s->stream>>>(
-                    n, s->nsc, s->tpp_max, s->geom, s->coef, pos, s->grid(), s->caps(), s->aux(), s->nbr, s->nnb,
-                    (const real2*)s->sA, s->st);
+                    row_args<M>(s, CountOut{nullptr, nullptr}), s->nsc, s->tpp_max);
                 return VBC_OK;
             });
         k_step<M, EPI><<<blocks_for(n, TPB), TPB, 0, s->stream>>>(n, s->geom, s->aux(), s->id, pos_next,
@@ -884,6 +920,9 @@ int halt_error(vbc_system* s)
     if (s->st_host->crowded)
         return fail(VBC_ERR_UNSTABLE, "more than %d particles in one cell: the system has collapsed or blown up",
                     MAX_CELL);
+    if (s->st_host->aborted)
+        return fail(VBC_ERR_TIMEOUT, "a batched step gave up waiting and left this system's state incomplete: "
+                                     "set its state again");
     if (s->st_host->bad_input)
         return fail(VBC_ERR_UNSTABLE, "a loaded position or velocity is non-finite or beyond the fixed-point range "
                                       "(|x| < 1024 L, |v| < 2^22)");
@@ -1336,6 +1375,14 @@ int load_state(vbc_system* s, const double* pos, const double* vel, int on_devic
     // caller arrays -> staging (xt holds positions, vt velocities) -> sorted state
     VBC_TRY(stage_in(s, (double*)s->xt, pos, 3 * (size_t)s->n, on_device));
     if (vel) VBC_TRY(stage_in(s, (double*)s->vt, vel, 3 * (size_t)s->n, on_device));
+    if (s->aborted) {
+        // an interrupted build may have left the sorted order and the cell counters half done:
+        // start both afresh (the state itself comes from the caller)
+        k_iota<<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>((int)s->n, s->id);
+        VBC_TRY(check_launch(s));
+        VBC_CUDA(cudaMemsetAsync(s->cell_count, 0, (size_t)s->npad * sizeof(int), s->stream));
+        s->aborted = false;
+    }
     // a new state clears every halt (and requests a rebuild); the load itself may raise bad_input
     k_clear_halt<<<1, 1, 0, s->stream>>>(s->st);
     VBC_TRY(check_launch(s));
@@ -1399,6 +1446,128 @@ int trim_capacities(vbc_system* s)
 }
 
 }  // namespace
+
+// ------------------------------------------------------------------ fused batches
+template <class M>
+SysDesc<M> make_desc(const vbc_system* s, const StepArgs& a)
+{
+    using pos_t = typename M::pos_t;
+    SysDesc<M> d{};
+    for (int f = 0; f < 2; ++f) {
+        const int c = s->cur ^ f;
+        d.A[f] = row_args<M>(s, CountOut{nullptr, nullptr}, c);
+        d.pnext[f] = (pos_t*)s->pos[c ^ 1];
+    }
+    d.lp = s->lp;
+    d.a = a;
+    d.npad = s->npad;
+    d.nchunk = blocks_for(s->npad, SCAN_CHUNK);
+    d.nsc = s->nsc;
+    d.rel = s->rel_lists ? 1 : 0;
+    d.tmax = s->tpp_max;
+    d.morton_rank = s->morton_rank;
+    d.cell_of = s->cell_of;
+    d.slot_of = s->slot_of;
+    d.order = s->order;
+    d.cell_count = s->cell_count;
+    d.chunk_sum = s->chunk_sum;
+    d.cell_start = s->cell_start;
+    d.x = s->x;
+    d.v = s->v;
+    d.xt = s->xt;
+    d.vt = s->vt;
+    d.idw = s->id;
+    d.idt = s->idt;
+    d.post = (pos_t*)s->post;
+    d.xref = (pos_t*)s->xref;
+    d.scratch = s->scratch;
+    d.nbr = s->nbr;
+    d.nnb = s->nnb;
+    return d;
+}
+
+// Systems a fused batch can take: single type, one precision, the row walks'
+// default block shape, no per-kernel timing.
+bool fusable(const vbc_batch* b)
+{
+    for (const vbc_system* s : b->sys)
+        if (s->typed || s->row_tpb != 128 || s->prof || s->prec != b->sys[0]->prec) return false;
+    return true;
+}
+
+// Iterations 1 .. nsteps of every system as one cooperative launch each (the
+// systems' iteration 0 already ran on their own streams and b->stream waits
+// for them).  Returns VBC_ERR_INVALID_ARG without launching anything when the
+// batch does not fit the fused launch (the caller then uses the graphs).
+template <class M>
+int fused_iterations(vbc_batch* b, int64_t nsteps, const std::vector<StepArgs>& args)
+{
+    const int K = (int)b->sys.size();
+    std::vector<SysDesc<M>> desc((size_t)K);
+    std::vector<int> offs((size_t)BK_NKIND * (K + 1), 0);
+    size_t smem_phase = 0;
+    long long tot[BK_NKIND] = {0, 0, 0, 0};
+    for (int k = 0; k < K; ++k) {
+        const vbc_system* s = b->sys[k];
+        desc[k] = make_desc<M>(s, args[k]);
+        const long long items[BK_NKIND] = {s->n, s->npad, blocks_for(s->npad, SCAN_CHUNK), s->nsc};
+        for (int q = 0; q < BK_NKIND; ++q) {
+            tot[q] += items[q];
+            if (tot[q] >= (1LL << 31)) return fail(VBC_ERR_INVALID_ARG, "batch too large for one fused launch");
+            offs[(size_t)q * (K + 1) + k + 1] = (int)tot[q];
+        }
+        const size_t nl = (!M::fp64 && s->rel_lists) ? s->smem_nlist_rel() : s->smem_nlist();
+        smem_phase = std::max({smem_phase, nl, s->smem_near(), s->smem_rows(s->real_bytes())});
+    }
+    smem_phase = al16(smem_phase);
+    const size_t smem = smem_phase + (size_t)(BK_NKIND + 1) * (K + 1) * sizeof(int);
+    if (smem > MAX_SMEM) return fail(VBC_ERR_INVALID_ARG, "batch too large for one fused launch");
+    const size_t dbytes = desc.size() * sizeof(SysDesc<M>);
+    if (dbytes > b->desc_bytes) {
+        if (b->d_desc) cudaFree(b->d_desc);
+        b->d_desc = nullptr;
+        b->desc_bytes = 0;
+        VBC_TRY(dalloc_bytes(b->d_desc, dbytes));
+        b->desc_bytes = dbytes;
+    }
+    if (offs.size() > b->offs_count) {
+        dfree(b->d_offs);
+        b->offs_count = 0;
+        VBC_TRY(dalloc(b->d_offs, offs.size()));
+        b->offs_count = offs.size();
+    }
+    if (!b->ctl) {
+        VBC_TRY(dalloc(b->ctl, 1));
+        if (cudaMallocHost((void**)&b->ctl_host, sizeof(BatchCtl)) != cudaSuccess)
+            return fail(VBC_ERR_OOM, "pinned host allocation failed");
+    }
+    // pageable sources: each copy has read its source when the call returns
+    VBC_CUDA(cudaMemcpyAsync(b->d_desc, desc.data(), dbytes, cudaMemcpyHostToDevice, b->stream));
+    VBC_CUDA(cudaMemcpyAsync(b->d_offs, offs.data(), offs.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    const BatchCtl c0{0u, 0u, 0, 0, b->wait_limit};
+    VBC_CUDA(cudaMemcpyAsync(b->ctl, &c0, sizeof c0, cudaMemcpyHostToDevice, b->stream));
+    VBC_TRY(set_smem(k_batch_iter<M, EPI_FINISH_START>, smem));
+    VBC_TRY(set_smem(k_batch_iter<M, EPI_FINISH>, smem));
+    int occ = 0;
+    for (const void* f : {(const void*)k_batch_iter<M, EPI_FINISH_START>, (const void*)k_batch_iter<M, EPI_FINISH>}) {
+        int o = 0;
+        VBC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, f, SC_TPB, smem));
+        occ = occ == 0 ? o : std::min(occ, o);
+    }
+    if (occ < 1) return fail(VBC_ERR_INVALID_ARG, "the fused launch does not fit an SM");
+    const int grid = occ * b->sys[0]->sms;
+    const SysDesc<M>* dd = (const SysDesc<M>*)b->d_desc;
+    int smem_phase_i = (int)smem_phase;
+    for (int64_t it = 1; it <= nsteps; ++it) {
+        int flip = (int)((it - 1) & 1);
+        void* kargs[] = {(void*)&dd, (void*)&K, (void*)&b->d_offs, (void*)&b->ctl, (void*)&flip, (void*)&smem_phase_i};
+        const void* f = it < nsteps ? (const void*)k_batch_iter<M, EPI_FINISH_START> : (const void*)k_batch_iter<M, EPI_FINISH>;
+        VBC_CUDA(cudaLaunchCooperativeKernel(f, dim3(grid), dim3(SC_TPB), kargs, smem, b->stream));
+    }
+    b->fused_launches += nsteps;
+    VBC_CUDA(cudaMemcpyAsync(b->ctl_host, b->ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, b->stream));
+    return VBC_OK;
+}
 
 // Lets the other translation unit of the library (vbc_noalloc.cu) report
 // through vbc_last_error(); not exported.
@@ -2018,8 +2187,8 @@ int vbc_batch_step(vbc_batch* b, int64_t nsteps, double dt, const double* kT, do
     for (size_t k = 0; k < K; ++k) bad = bad || !(kT[k] >= 0) || !std::isfinite(kT[k]);
     if (bad) return fail(VBC_ERR_INVALID_ARG, "need dt > 0, kT >= 0, gamma >= 0 (finite)");
     if (nsteps == 0) return VBC_OK;
-    bool plain = nsteps < 3;
-    for (vbc_system* s : b->sys) plain = plain || s->prof || !s->use_graphs;
+    bool plain = nsteps < 3 && !(b->mode == VBC_BATCH_FUSED && fusable(b));
+    for (vbc_system* s : b->sys) plain = plain || s->prof || (!s->use_graphs && b->mode != VBC_BATCH_FUSED);
     if (plain) {
         for (size_t k = 0; k < K; ++k) VBC_TRY(vbc_step_langevin(b->sys[k], nsteps, dt, kT[k], gamma));
         return VBC_OK;
@@ -2027,6 +2196,9 @@ int vbc_batch_step(vbc_batch* b, int64_t nsteps, double dt, const double* kT, do
     VBC_CUDA(cudaSetDevice(b->device));
     std::vector<StepArgs> args(K);
     std::vector<int> cur0(K);
+    for (vbc_system* s : b->sys)
+        if (s->aborted) return fail(VBC_ERR_TIMEOUT, "a system of the batch was left incomplete by an earlier "
+                                                     "batched step that gave up waiting: set its state again");
     // iteration 0 of every system on its own stream; the batch stream waits for all
     for (size_t k = 0; k < K; ++k) {
         vbc_system* s = b->sys[k];
@@ -2036,6 +2208,40 @@ int vbc_batch_step(vbc_batch* b, int64_t nsteps, double dt, const double* kT, do
                                     : batch_open<ModeF32>(s, args[k], nsteps));
         VBC_CUDA(cudaEventRecord(b->ready[k], s->stream));
         VBC_CUDA(cudaStreamWaitEvent(b->stream, b->ready[k], 0));
+    }
+    // the fused path: iterations 1 .. nsteps as one cooperative launch each for all systems
+    if (b->mode == VBC_BATCH_FUSED && fusable(b)) {
+        const bool f64 = b->sys[0]->prec == VBC_FP64;
+        const int rcf = f64 ? fused_iterations<ModeF64>(b, nsteps, args) : fused_iterations<ModeF32>(b, nsteps, args);
+        if (rcf != VBC_OK && rcf != VBC_ERR_INVALID_ARG) return rcf;
+        if (rcf == VBC_OK) {
+            VBC_CUDA(cudaEventRecord(b->join, b->stream));
+            VBC_CUDA(cudaStreamSynchronize(b->stream));
+            const bool timed_out = b->ctl_host->timeout != 0;
+            int rc = VBC_OK;
+            for (size_t k = 0; k < K; ++k) {
+                vbc_system* s = b->sys[k];
+                VBC_CUDA(cudaStreamWaitEvent(s->stream, b->join, 0));
+                s->cur ^= (int)((nsteps - 1) & 1);  // iterations 1 .. nsteps - 1 each flipped the buffers
+                s->launches += nsteps;              // one fused launch per iteration
+                if (timed_out) {
+                    s->aborted = true;
+                    s->force_fresh = false;
+                    k_abort<<<1, 1, 0, s->stream>>>(s->st);
+                    if (rc == VBC_OK) rc = check_launch(s);
+                    continue;
+                }
+                const int r = f64 ? batch_settle<ModeF64>(s, args[k], cur0[k], nsteps)
+                                  : batch_settle<ModeF32>(s, args[k], cur0[k], nsteps);
+                if (rc == VBC_OK) rc = r;
+            }
+            if (timed_out)
+                return fail(VBC_ERR_TIMEOUT, "a grid-wide wait of the fused batch launch gave up after %lld spins; "
+                                             "the systems' states are incomplete: set them again",
+                            (long long)b->wait_limit);
+            return rc;
+        }
+        g_err.clear();  // the batch does not fit one launch: the graphs below take it
     }
     // iterations 1 .. 2 npairs: one graph launch advances every system by two
     const int64_t npairs = (nsteps - 1) / 2;
@@ -2107,12 +2313,29 @@ void vbc_batch_destroy(vbc_batch* b)
     cudaSetDevice(b->device);
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->d_desc) cudaFree(b->d_desc);
+    if (b->d_offs) cudaFree(b->d_offs);
+    if (b->ctl) cudaFree(b->ctl);
+    if (b->ctl_host) cudaFreeHost(b->ctl_host);
     for (cudaEvent_t ev : b->ready)
         if (ev) cudaEventDestroy(ev);
     if (b->join) cudaEventDestroy(b->join);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
+
+int vbc_batch_set_mode(vbc_batch* b, int mode, int64_t wait_limit)
+{
+    g_err.clear();
+    if (!b) return fail(VBC_ERR_INVALID_ARG, "batch handle must not be NULL");
+    if (mode != VBC_BATCH_FUSED && mode != VBC_BATCH_GRAPHS)
+        return fail(VBC_ERR_INVALID_ARG, "mode must be VBC_BATCH_FUSED or VBC_BATCH_GRAPHS");
+    b->mode = mode;
+    b->wait_limit = wait_limit < 0 ? (1LL << 22) : wait_limit;
+    return VBC_OK;
+}
+
+int64_t vbc_batch_fused_launches(vbc_batch* b) { return b ? b->fused_launches : -1; }
 
 int vbc_set_tuning(vbc_system* s, const vbc_tuning* t)
 {

@@ -92,12 +92,13 @@ struct Status {
     int ngen;           // particles whose force k_force_rows forms (k_count_near, k_chain)
     int bad_index;      // 1: a count was handed a particle index outside [0, n) (k_count_rows; an internal error)
     int bad_input;      // 1: a loaded position or velocity was non-finite or beyond the fixed-point range (k_load_state)
+    int aborted;        // 1: a batched iteration gave up waiting and left the state incomplete (host)
 };
 
 // Work stops (until the host intervenes) once any of these is raised.
 __device__ __forceinline__ bool halted(const Status* st)
 {
-    return (st->frozen | st->crowded | st->overflow | st->stage_overflow | st->bad_input) != 0;
+    return (st->frozen | st->crowded | st->overflow | st->stage_overflow | st->bad_input | st->aborted) != 0;
 }
 
 // ---------------------------------------------------------------- Philox4x32-10
@@ -371,10 +372,10 @@ struct ModeF64 {
     }
     __device__ __forceinline__ static unsigned long long word(double x, double inv32)
     {
-        const double t = x * inv32;
+        const double t = __dmul_rn(x, inv32);
         const double fl = floor(t);
         const unsigned long long hi = (unsigned long long)(uint32_t)__double2ll_rd(fl);
-        const unsigned long long lo = (unsigned long long)__double2uint_rz((t - fl) * 4294967296.0);
+        const unsigned long long lo = (unsigned long long)__double2uint_rz(__dmul_rn(t - fl, 4294967296.0));
         return (hi << 32) | lo;
     }
     __device__ __forceinline__ static P64 from_x(double x, double y, double z, const Geom& g)
@@ -398,21 +399,25 @@ __device__ __forceinline__ int3 cell_of_pos(const typename M::pos_t& p, const Ge
 }
 
 // ---------------------------------------------------------------- pair functions (FP64)
-// Used by the FP64 mode and by the FP64 energy/virial evaluation.
+// Used by the FP64 mode and by the FP64 energy/virial evaluation.  Every
+// product that feeds a sum is written as an explicit fused multiply-add (or an
+// explicit product), so that the rounding of each result is fixed by the
+// source and not by how the compiler contracts it in one kernel or another:
+// the batched launch and the single-system kernels then agree bit for bit.
 __device__ __forceinline__ double omega_d(double x, double x1, double x2)
 {
     if (x <= x1) return 1.0;
     if (x >= x2) return 0.0;
     const double t = (x - x1) / (x2 - x1);
-    const double q = 1.0 - t * t;
-    return q * q;
+    const double q = __fma_rn(-t, t, 1.0);
+    return __dmul_rn(q, q);
 }
 __device__ __forceinline__ double domega_d(double x, double x1, double x2)
 {
     if (x <= x1 || x >= x2) return 0.0;
     const double w = x2 - x1;
     const double t = (x - x1) / w;
-    return -4.0 * t * (1.0 - t * t) / w;
+    return __dmul_rn(__dmul_rn(-4.0, t), __fma_rn(-t, t, 1.0)) / w;
 }
 __device__ __forceinline__ double Vr_d(double r2, const Coef& c)
 {
@@ -430,14 +435,14 @@ __device__ __forceinline__ double Va_d(double r, const Coef& c)
 {
     if (r <= c.r_r || r >= c.r_a) return 0.0;
     const double u = (r - c.rm) / c.h;
-    const double q = 1.0 - u * u;
-    return -c.E_a * q * q;
+    const double q = __fma_rn(-u, u, 1.0);
+    return __dmul_rn(__dmul_rn(-c.E_a, q), q);
 }
 __device__ __forceinline__ double dVa_d(double r, const Coef& c)
 {
     if (r <= c.r_r || r >= c.r_a) return 0.0;
     const double u = (r - c.rm) / c.h;
-    return 4.0 * c.E_a * u * (1.0 - u * u) / c.h;
+    return __dmul_rn(__dmul_rn(4.0 * c.E_a, u), __fma_rn(-u, u, 1.0)) / c.h;
 }
 
 }  // namespace vbc

@@ -39,14 +39,16 @@ constexpr int MAX_CELL = 512;     // a denser cell means the system has collapse
 enum Epilogue { EPI_FORCE = 0, EPI_START = 1, EPI_FINISH = 2, EPI_FINISH_START = 3 };
 
 // ================================================================ rebuild: sort by cell
+// The rebuild steps run only when a rebuild is due and nothing is halted.
+__device__ __forceinline__ bool rebuild_on(const Status* st) { return st->rebuild && !st->frozen && !st->crowded; }
+
+// Particle i of the cell binning (0 <= i < n): its cell's Morton rank and its
+// slot in that cell; particle 0 also clears the build statistics.
 template <class M>
-__global__ void __launch_bounds__(TPB) k_bin(const typename M::pos_t* __restrict__ pos, int n,
-                                             Geom g, const int* __restrict__ morton_rank,
-                                             int* __restrict__ cell_of, int* __restrict__ slot_of,
-                                             int* __restrict__ cell_count, Status* st)
+__device__ __forceinline__ void bin_item(int i, const typename M::pos_t* __restrict__ pos, const Geom& g,
+                                         const int* __restrict__ morton_rank, int* __restrict__ cell_of,
+                                         int* __restrict__ slot_of, int* __restrict__ cell_count, Status* st)
 {
-    if (!st->rebuild || st->frozen || st->crowded) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
         st->max_nnb = 0;
         st->nnb_sum = 0;
@@ -54,11 +56,21 @@ __global__ void __launch_bounds__(TPB) k_bin(const typename M::pos_t* __restrict
         st->max_own = 0;
         st->max_seg = 0;
     }
-    if (i >= n) return;
     const int3 c = cell_of_pos<M>(pos[i], g);
     const int key = morton_rank[(c.z * g.nc[1] + c.y) * g.nc[0] + c.x];
     cell_of[i] = key;
     slot_of[i] = atomicAdd(&cell_count[key], 1);
+}
+
+template <class M>
+__global__ void __launch_bounds__(TPB) k_bin(const typename M::pos_t* __restrict__ pos, int n,
+                                             Geom g, const int* __restrict__ morton_rank,
+                                             int* __restrict__ cell_of, int* __restrict__ slot_of,
+                                             int* __restrict__ cell_count, Status* st)
+{
+    if (!rebuild_on(st)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) bin_item<M>(i, pos, g, morton_rank, cell_of, slot_of, cell_count, st);
 }
 
 // Block-wide exclusive scan of one int per thread; returns the block total.
@@ -91,38 +103,43 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* smem_warp, int& 
 }
 
 // Pass 1 of the scan: the sum of each chunk of SCAN_CHUNK cell counts.
-__global__ void __launch_bounds__(SCAN_TPB) k_scan_sums(const int* __restrict__ cell_count, int ncell,
-                                                        int* __restrict__ chunk_sum, const Status* st)
+template <int NT>
+__device__ __forceinline__ void scan_sums_chunk(int b, const int* __restrict__ cell_count, int ncell,
+                                                int* __restrict__ chunk_sum, int* sw)
 {
-    if (!st->rebuild || st->frozen || st->crowded) return;
-    __shared__ int sw[SCAN_TPB / 32];
-    const int base = blockIdx.x * SCAN_CHUNK;
+    const int base = b * SCAN_CHUNK;
     int s = 0;
-    for (int k = threadIdx.x; k < SCAN_CHUNK; k += SCAN_TPB) {
+    for (int k = threadIdx.x; k < SCAN_CHUNK; k += NT) {
         const int c = base + k;
         if (c < ncell) s += cell_count[c];
     }
     int total;
-    block_exclusive_scan<SCAN_TPB>(s, sw, total);
-    if (threadIdx.x == 0) chunk_sum[blockIdx.x] = total;
+    block_exclusive_scan<NT>(s, sw, total);
+    if (threadIdx.x == 0) chunk_sum[b] = total;
+}
+
+__global__ void __launch_bounds__(SCAN_TPB) k_scan_sums(const int* __restrict__ cell_count, int ncell,
+                                                        int* __restrict__ chunk_sum, const Status* st)
+{
+    if (!rebuild_on(st)) return;
+    __shared__ int sw[SCAN_TPB / 32];
+    scan_sums_chunk<SCAN_TPB>(blockIdx.x, cell_count, ncell, chunk_sum, sw);
 }
 
 // Pass 2: chunk offset from the preceding chunk sums, then the local scan.
 // Writes cell_start[0..ncell] and clears cell_count for the next build.
-__global__ void __launch_bounds__(SCAN_TPB) k_scan_apply(int* __restrict__ cell_count, int ncell,
-                                                         const int* __restrict__ chunk_sum,
-                                                         int* __restrict__ cell_start, Status* st)
+template <int NT>
+__device__ __forceinline__ void scan_apply_chunk(int chunk, int* __restrict__ cell_count, int ncell,
+                                                 const int* __restrict__ chunk_sum, int* __restrict__ cell_start,
+                                                 Status* st, int* sw)
 {
-    // raises `crowded` itself, so it does not test it
-    if (!st->rebuild || st->frozen) return;
-    __shared__ int sw[SCAN_TPB / 32];
     int off = 0;
-    for (int b = threadIdx.x; b < (int)blockIdx.x; b += SCAN_TPB) off += chunk_sum[b];
+    for (int b = threadIdx.x; b < chunk; b += NT) off += chunk_sum[b];
     int tot;
-    block_exclusive_scan<SCAN_TPB>(off, sw, tot);
+    block_exclusive_scan<NT>(off, sw, tot);
     off = tot;  // sum over all preceding chunks
-    constexpr int PER = SCAN_CHUNK / SCAN_TPB;
-    const int base = blockIdx.x * SCAN_CHUNK + threadIdx.x * PER;
+    constexpr int PER = SCAN_CHUNK / NT;
+    const int base = chunk * SCAN_CHUNK + threadIdx.x * PER;
     int v[PER];
     int s = 0;
 #pragma unroll
@@ -131,7 +148,7 @@ __global__ void __launch_bounds__(SCAN_TPB) k_scan_apply(int* __restrict__ cell_
         s += v[k];
     }
     int total;
-    int run = off + block_exclusive_scan<SCAN_TPB>(s, sw, total);
+    int run = off + block_exclusive_scan<NT>(s, sw, total);
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
         if (base + k < ncell) {
@@ -144,12 +161,22 @@ __global__ void __launch_bounds__(SCAN_TPB) k_scan_apply(int* __restrict__ cell_
     if (base <= ncell - 1 && ncell - 1 < base + PER) cell_start[ncell] = run;
 }
 
+__global__ void __launch_bounds__(SCAN_TPB) k_scan_apply(int* __restrict__ cell_count, int ncell,
+                                                         const int* __restrict__ chunk_sum,
+                                                         int* __restrict__ cell_start, Status* st)
+{
+    // raises `crowded` itself, so it does not test it
+    if (!st->rebuild || st->frozen) return;
+    __shared__ int sw[SCAN_TPB / 32];
+    scan_apply_chunk<SCAN_TPB>(blockIdx.x, cell_count, ncell, chunk_sum, cell_start, st, sw);
+}
+
 __global__ void __launch_bounds__(TPB) k_scatter(int n, const int* __restrict__ cell_of,
                                                  const int* __restrict__ slot_of,
                                                  const int* __restrict__ cell_start,
                                                  int* __restrict__ order, const Status* st)
 {
-    if (!st->rebuild || st->frozen || st->crowded) return;
+    if (!rebuild_on(st)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     order[cell_start[cell_of[i]] + slot_of[i]] = i;
@@ -160,12 +187,8 @@ __global__ void __launch_bounds__(TPB) k_scatter(int n, const int* __restrict__ 
 // previous layout and the positions only, not of atomic scheduling.  Cells of
 // up to 16 particles are sorted in registers (odd-even transposition), larger
 // ones by insertion in memory.
-__global__ void __launch_bounds__(TPB) k_cellsort(int ncell, const int* __restrict__ cell_start,
-                                                  int* __restrict__ order, const Status* st)
+__device__ __forceinline__ void cellsort_item(int c, const int* __restrict__ cell_start, int* __restrict__ order)
 {
-    if (!st->rebuild || st->frozen || st->crowded) return;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
     const int b = cell_start[c], e = cell_start[c + 1], cnt = e - b;
     if (cnt <= 1) return;
     if (cnt <= 16) {
@@ -197,21 +220,24 @@ __global__ void __launch_bounds__(TPB) k_cellsort(int ncell, const int* __restri
     }
 }
 
+__global__ void __launch_bounds__(TPB) k_cellsort(int ncell, const int* __restrict__ cell_start,
+                                                  int* __restrict__ order, const Status* st)
+{
+    if (!rebuild_on(st)) return;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncell) cellsort_item(c, cell_start, order);
+}
+
 // Gathers the state (8-byte words: positions and velocities of either mode),
 // the original index and the fixed-point position into sorted order.
 template <class M>
-__global__ void __launch_bounds__(TPB) k_permute(int n, const int* __restrict__ order,
-                                                 const unsigned long long* __restrict__ x,
-                                                 const unsigned long long* __restrict__ v,
-                                                 const int* __restrict__ id,
-                                                 const typename M::pos_t* __restrict__ pos,
-                                                 unsigned long long* __restrict__ xt,
-                                                 unsigned long long* __restrict__ vt, int* __restrict__ idt,
-                                                 typename M::pos_t* __restrict__ post, const Status* st)
+__device__ __forceinline__ void permute_item(int k, int n, const int* __restrict__ order,
+                                             const unsigned long long* __restrict__ x,
+                                             const unsigned long long* __restrict__ v, const int* __restrict__ id,
+                                             const typename M::pos_t* __restrict__ pos,
+                                             unsigned long long* __restrict__ xt, unsigned long long* __restrict__ vt,
+                                             int* __restrict__ idt, typename M::pos_t* __restrict__ post)
 {
-    if (!st->rebuild || st->frozen || st->crowded) return;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
     const int o = order[k];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -223,17 +249,13 @@ __global__ void __launch_bounds__(TPB) k_permute(int n, const int* __restrict__ 
 }
 
 template <class M>
-__global__ void __launch_bounds__(TPB) k_copyback(int n, const unsigned long long* __restrict__ xt,
-                                                  const unsigned long long* __restrict__ vt,
-                                                  const int* __restrict__ idt,
-                                                  const typename M::pos_t* __restrict__ post,
-                                                  unsigned long long* __restrict__ x, unsigned long long* __restrict__ v,
-                                                  int* __restrict__ id, typename M::pos_t* __restrict__ pos,
-                                                  typename M::pos_t* __restrict__ xref, const Status* st)
+__device__ __forceinline__ void copyback_item(int k, int n, const unsigned long long* __restrict__ xt,
+                                              const unsigned long long* __restrict__ vt, const int* __restrict__ idt,
+                                              const typename M::pos_t* __restrict__ post,
+                                              unsigned long long* __restrict__ x, unsigned long long* __restrict__ v,
+                                              int* __restrict__ id, typename M::pos_t* __restrict__ pos,
+                                              typename M::pos_t* __restrict__ xref)
 {
-    if (!st->rebuild || st->frozen || st->crowded) return;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         x[(size_t)a * n + k] = xt[(size_t)a * n + k];
@@ -243,6 +265,35 @@ __global__ void __launch_bounds__(TPB) k_copyback(int n, const unsigned long lon
     const typename M::pos_t p = post[k];
     pos[k] = p;
     xref[k] = p;
+}
+
+template <class M>
+__global__ void __launch_bounds__(TPB) k_permute(int n, const int* __restrict__ order,
+                                                 const unsigned long long* __restrict__ x,
+                                                 const unsigned long long* __restrict__ v,
+                                                 const int* __restrict__ id,
+                                                 const typename M::pos_t* __restrict__ pos,
+                                                 unsigned long long* __restrict__ xt,
+                                                 unsigned long long* __restrict__ vt, int* __restrict__ idt,
+                                                 typename M::pos_t* __restrict__ post, const Status* st)
+{
+    if (!rebuild_on(st)) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) permute_item<M>(k, n, order, x, v, id, pos, xt, vt, idt, post);
+}
+
+template <class M>
+__global__ void __launch_bounds__(TPB) k_copyback(int n, const unsigned long long* __restrict__ xt,
+                                                  const unsigned long long* __restrict__ vt,
+                                                  const int* __restrict__ idt,
+                                                  const typename M::pos_t* __restrict__ post,
+                                                  unsigned long long* __restrict__ x, unsigned long long* __restrict__ v,
+                                                  int* __restrict__ id, typename M::pos_t* __restrict__ pos,
+                                                  typename M::pos_t* __restrict__ xref, const Status* st)
+{
+    if (!rebuild_on(st)) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) copyback_item<M>(k, n, xt, vt, idt, post, x, v, id, pos, xref);
 }
 
 
@@ -469,7 +520,7 @@ struct ListTest<ModeF64> {
     {
         double dx, dy, dz;
         ModeF64::delta64(a, b, g, dx, dy, dz);
-        const double r2 = dx * dx + dy * dy + dz * dz;
+        const double r2 = __fma_rn(dx, dx, __fma_rn(dy, dy, __dmul_rn(dz, dz)));
         if (r2 >= lp.rlist2) return -1;
         return r2 < lp.near2 ? 0 : 1;
     }
@@ -582,23 +633,23 @@ __device__ __forceinline__ void shift192(unsigned long long& a0, unsigned long l
 // neighbourhood, writing a two-ended row (near from the front, far from the
 // back) into a per-particle scratch row in global memory; the rows are then
 // packed into the block's segment.
+// The list build of cell group b (the whole block; smem is the dynamic shared
+// memory of nlist_layout).  Raises `overflow` and `stage_overflow` itself.
 template <class M, bool REL>
-__global__ void __launch_bounds__(SC_TPB, NLIST_MIN_BLOCKS) k_nlist(Geom g, const typename M::pos_t* __restrict__ pos, SuperGrid G,
-                                                  SuperCaps cp, ListParams lp, uint16_t* __restrict__ scratch,
-                                                  uint16_t* __restrict__ nbr, int* __restrict__ nnb, GroupAux aux,
-                                                  Status* st)
+__device__ __forceinline__ void nlist_group(int b, const Geom& g, const typename M::pos_t* __restrict__ pos,
+                                            const SuperGrid& G, const SuperCaps& cp, const ListParams& lp,
+                                            uint16_t* __restrict__ scratch, uint16_t* __restrict__ nbr,
+                                            int* __restrict__ nnb, const GroupAux& aux, Status* st,
+                                            unsigned char* smem)
 {
     using pos_t = typename M::pos_t;
     using spos_t = typename std::conditional<REL, float4, pos_t>::type;
-    // raises `overflow` and `stage_overflow` itself, so it does not test them
-    if (!st->rebuild || st->frozen || st->crowded) return;
     __shared__ SuperTab T;
     __shared__ int s_mx;
     __shared__ unsigned long long s_sum;
-    extern __shared__ __align__(16) unsigned char smem[];
     const int t = threadIdx.x;
     int p0, n_own, total;
-    load_group(blockIdx.x, g, G, T, p0, n_own, total);
+    load_group(b, g, G, T, p0, n_own, total);
     if (t == 0) {
         atomicMax(&st->max_stage, total);
         atomicMax(&st->max_own, n_own);
@@ -617,10 +668,10 @@ __global__ void __launch_bounds__(SC_TPB, NLIST_MIN_BLOCKS) k_nlist(Geom g, cons
     int* roff = (int*)(smem + ly.roff);
     int* rnn = (int*)(smem + ly.rnn);
     int* rself = (int*)(smem + ly.rself);  // own staging index of each own particle
-    int* sidx = aux.stage_idx + (size_t)blockIdx.x * cp.smax;  // the staged-index table the passes read
+    int* sidx = aux.stage_idx + (size_t)b * cp.smax;  // the staged-index table the passes read
     if constexpr (REL) {
         // reference: the centre of the block's own cells (a cell boundary)
-        const int org = __ldg(G.sc_org + blockIdx.x);
+        const int org = __ldg(G.sc_org + b);
         const int cx[3] = {(org & 1023) + BXC / 2, ((org >> 10) & 1023) + BYC / 2, (org >> 20) + BZC / 2};
         uint32_t ref[3];
 #pragma unroll
@@ -642,9 +693,9 @@ __global__ void __launch_bounds__(SC_TPB, NLIST_MIN_BLOCKS) k_nlist(Geom g, cons
     bool over = false;
     for (int j = t; j < n_own; j += SC_TPB) {
         const int p = p0 + j;
-        const int b = own_cell(T, p);
-        const int kb = own_staged_cell(b);
-        const int mself = T.off[kb] + (p - T.own[b]);
+        const int ob = own_cell(T, p);
+        const int kb = own_staged_cell(ob);
+        const int mself = T.off[kb] + (p - T.own[ob]);
         const spos_t pi = spos[mself];
         uint16_t* row = scratch + (size_t)p * cp.cap;
         int nn = 0, nf = 0;
@@ -680,7 +731,7 @@ __global__ void __launch_bounds__(SC_TPB, NLIST_MIN_BLOCKS) k_nlist(Geom g, cons
                     } else if constexpr (M::fp64) {
                         double dx, dy, dz;
                         ModeF64::delta64(pi, spos[m], g, dx, dy, dz);
-                        const double r2 = dx * dx + dy * dy + dz * dz;
+                        const double r2 = __fma_rn(dx, dx, __fma_rn(dy, dy, __dmul_rn(dz, dz)));
                         mnear = (mnear << 1) | (r2 < lp.near2 ? 1u : 0u);
                         mlist = (mlist << 1) | (r2 < lp.rlist2 ? 1u : 0u);
                         mrl = (mrl << 1) | (r2 <= lp.rl2 ? 1u : 0u);
@@ -787,7 +838,7 @@ __global__ void __launch_bounds__(SC_TPB, NLIST_MIN_BLOCKS) k_nlist(Geom g, cons
     if (t == 0) {
         atomicMax(&st->max_nnb, s_mx);
         atomicAdd((unsigned long long*)&st->nnb_sum, s_sum);
-        if (blockIdx.x == 0) st->rebuilds += 1;
+        if (b == 0) st->rebuilds += 1;
         if (any_over) {
             st->overflow = 1;
             st->frozen_iter = (int)st->iter;
@@ -795,10 +846,10 @@ __global__ void __launch_bounds__(SC_TPB, NLIST_MIN_BLOCKS) k_nlist(Geom g, cons
     }
     if (any_over) return;
     const int tot = scan_in_place(roff, n_own, T.sw);
-    for (int j = t; j < n_own; j += SC_TPB) aux.roff[p0 + j] = (int)blockIdx.x * cp.seg + roff[j];
+    for (int j = t; j < n_own; j += SC_TPB) aux.roff[p0 + j] = (int)b * cp.seg + roff[j];
     if (t == 0) {
         atomicMax(&st->max_seg, tot);
-        aux.meta[blockIdx.x] = make_int2(total, tot);
+        aux.meta[b] = make_int2(total, tot);
     }
     if (tot > cp.seg) {
         if (t == 0) {
@@ -809,7 +860,7 @@ __global__ void __launch_bounds__(SC_TPB, NLIST_MIN_BLOCKS) k_nlist(Geom g, cons
     }
     // pack: each thread takes an equal contiguous run of the group's 4-entry chunks;
     // chunk c belongs to the row j with roff[j] <= 4c < roff[j + 1]
-    uint2* out = reinterpret_cast<uint2*>(nbr + (size_t)blockIdx.x * cp.seg);
+    uint2* out = reinterpret_cast<uint2*>(nbr + (size_t)b * cp.seg);
     const int nch = tot / 4, per = (nch + SC_TPB - 1) / SC_TPB;
     const int c0 = min(nch, t * per), c1 = min(nch, c0 + per);
     if (c0 < c1) {
@@ -847,6 +898,17 @@ __global__ void __launch_bounds__(SC_TPB, NLIST_MIN_BLOCKS) k_nlist(Geom g, cons
             j = j2;
         }
     }
+}
+
+template <class M, bool REL>
+__global__ void __launch_bounds__(SC_TPB, NLIST_MIN_BLOCKS) k_nlist(Geom g, const typename M::pos_t* __restrict__ pos, SuperGrid G,
+                                                  SuperCaps cp, ListParams lp, uint16_t* __restrict__ scratch,
+                                                  uint16_t* __restrict__ nbr, int* __restrict__ nnb, GroupAux aux,
+                                                  Status* st)
+{
+    if (!rebuild_on(st)) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    nlist_group<M, REL>(blockIdx.x, g, pos, G, cp, lp, scratch, nbr, nnb, aux, st, smem);
 }
 
 // ================================================================ pass 2: forces + BAOAB
@@ -967,19 +1029,20 @@ __device__ __forceinline__ void integrate(int i, int n, const Geom& g, typename 
             xs[d] = ps.X[d];
             vs[d] = ps.V[d];
         }
+        // explicit fused multiply-adds: the rounding does not depend on the kernel this is inlined in
         if constexpr (finish) {
 #pragma unroll
-            for (int d = 0; d < 3; ++d) vs[d] += h * f3[d];
+            for (int d = 0; d < 3; ++d) vs[d] = __fma_rn(h, f3[d], vs[d]);
         }
         if constexpr (start) {
             const double3 z = langevin_normals_d(a.seed, (unsigned long long)(st->step_base + st->iter), ps.id);
             const double zz[3] = {z.x, z.y, z.z};
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                vs[d] += h * f3[d];
-                xs[d] += h * vs[d];
-                vs[d] = a.c1 * vs[d] + a.c2 * zz[d];
-                xs[d] += h * vs[d];
+                vs[d] = __fma_rn(h, f3[d], vs[d]);
+                xs[d] = __fma_rn(h, vs[d], xs[d]);
+                vs[d] = __fma_rn(a.c1, vs[d], __dmul_rn(a.c2, zz[d]));
+                xs[d] = __fma_rn(h, vs[d], xs[d]);
             }
         }
 #pragma unroll
@@ -1054,10 +1117,10 @@ __device__ __forceinline__ void pair_f64(const P64& pi, double si, double Ai, co
     if (r2 >= c.rc2) return;
     const double r = sqrt(r2);
     double gr = dVr_over_r_d(r2, c);
-    if (r > 0.0) gr += (si * sj * dVa_d(r, c) + (Ai + Aj) * domega_d(r, c.r_l, c.r_h)) / r;
-    fx -= gr * dx;
-    fy -= gr * dy;
-    fz -= gr * dz;
+    if (r > 0.0) gr += __fma_rn(Ai + Aj, domega_d(r, c.r_l, c.r_h), __dmul_rn(__dmul_rn(si, sj), dVa_d(r, c))) / r;
+    fx = __fma_rn(-gr, dx, fx);
+    fy = __fma_rn(-gr, dy, fy);
+    fz = __fma_rn(-gr, dz, fz);
 }
 
 
@@ -1151,7 +1214,7 @@ __device__ __forceinline__ double r2_d(const typename M::pos_t& a, const typenam
 {
     double dx, dy, dz;
     M::delta64(a, b, g, dx, dy, dz);
-    return dx * dx + dy * dy + dz * dz;
+    return __fma_rn(dx, dx, __fma_rn(dy, dy, __dmul_rn(dz, dz)));
 }
 
 // s_i into the spare word of a position.
@@ -1190,22 +1253,21 @@ __device__ __forceinline__ void stage_by_table(const int* __restrict__ sidx, int
 // terms need A_j != 0 of a neighbour -- which k_chain rules out by clearing
 // the tag of every list neighbour of a window particle.  Every other particle
 // goes on the list of k_force_rows.
+// The close count of cell group b (the whole block; smem holds the group's
+// staged positions).  Starts with a block barrier, so that it may follow
+// another group's work on the same shared memory.
 template <class M>
-__global__ void __launch_bounds__(SC_TPB) k_count_near(int ngroups, Geom g, Coef c, typename M::pos_t* __restrict__ pos,
-                                                       SuperGrid G, SuperCaps cp, GroupAux aux,
-                                                       const int* __restrict__ nnb, typename M::real* __restrict__ ds_out,
-                                                       typename M::real2* __restrict__ sA, CountOut out,
-                                                       int* __restrict__ ulist, Status* st)
+__device__ __forceinline__ void count_near_group(int b, const Geom& g, const Coef& c, typename M::pos_t* __restrict__ pos,
+                                                 const SuperGrid& G, const SuperCaps& cp, const GroupAux& aux,
+                                                 const int* __restrict__ nnb, typename M::real* __restrict__ ds_out,
+                                                 typename M::real2* __restrict__ sA, const CountOut& out,
+                                                 int* __restrict__ ulist, Status* st, unsigned char* smem)
 {
     using pos_t = typename M::pos_t;
     using real = typename M::real;
     using real2 = typename M::real2;
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->rebuild = 0;
-    if (halted(st)) return;
-    // the group's neighbourhood, staged once for the close-list gathers of its own particles
-    extern __shared__ __align__(16) unsigned char smem[];
     pos_t* spos = (pos_t*)smem;
-    for (int b = blockIdx.x; b < ngroups; b += gridDim.x) {
+    {
         __syncthreads();  // the previous group is done with the shared positions
         const int p0 = __ldg(G.cell_start + OWN_CELLS * b);
         const int n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
@@ -1264,6 +1326,21 @@ __global__ void __launch_bounds__(SC_TPB) k_count_near(int ngroups, Geom g, Coef
             if (!whole) aux.glist[atomicAdd(&st->ngen, 1)] = p;
         }
     }
+}
+
+template <class M>
+__global__ void __launch_bounds__(SC_TPB) k_count_near(int ngroups, Geom g, Coef c, typename M::pos_t* __restrict__ pos,
+                                                       SuperGrid G, SuperCaps cp, GroupAux aux,
+                                                       const int* __restrict__ nnb, typename M::real* __restrict__ ds_out,
+                                                       typename M::real2* __restrict__ sA, CountOut out,
+                                                       int* __restrict__ ulist, Status* st)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->rebuild = 0;
+    if (halted(st)) return;
+    // the group's neighbourhood, staged once for the close-list gathers of its own particles
+    extern __shared__ __align__(16) unsigned char smem[];
+    for (int b = blockIdx.x; b < ngroups; b += gridDim.x)
+        count_near_group<M>(b, g, c, pos, G, cp, aux, nnb, ds_out, sA, out, ulist, st, smem);
 }
 
 // ================================================================ row walks
@@ -1444,78 +1521,114 @@ __device__ __forceinline__ void count_row_out(int p, typename M::real s, typenam
     }
 }
 
+// Everything a row walk reads and writes (all three walks).
+template <class M>
+struct RowArgs {
+    int n;
+    Geom g;
+    Coef c;
+    typename M::pos_t* pos;
+    SuperGrid G;
+    SuperCaps cp;
+    GroupAux aux;
+    const uint16_t* nbr;
+    const int* nnb;
+    const int* id;
+    typename M::real* ds;
+    typename M::real2* sA;
+    CountOut out;
+    int* ulist;
+    int* wpart;
+    const long long* X;  // the state [3][n] (the FP32 mode's residual bits)
+    Status* st;
+};
+
+// Packed residuals of sorted particle j (FP32 mode; X is the state [3][n]); an
+// index outside [0, n) is refused and reported rather than read.
+template <class M>
+__device__ __forceinline__ int resid_of(const RowArgs<M>& A, int j)
+{
+    if (M::fp64) return 0;
+    if ((unsigned)j >= (unsigned)A.n) {
+        A.st->bad_index = 1;
+        return 0;
+    }
+    return pack_resid(A.X, (size_t)A.n, j);
+}
+
+// Sparse count: list entry k of the particles k_count_near could not settle
+// (one warp, one lane per row entry).
+template <class M>
+__device__ __forceinline__ void count_rows_item(const RowArgs<M>& A, int k)
+{
+    using real = typename M::real;
+    const int p = A.ulist[k];
+    const int ra = __ldg(A.aux.roff + p), b = ra / A.cp.seg;
+    const int* sidx = A.aux.stage_idx + (size_t)b * A.cp.smax;
+    const uint16_t* row = A.nbr + ra;
+    const int len = row_len(__ldg(A.nnb + p));
+    real s, ds;
+    double n_val;
+    count_row<M>(A.pos[p], resid_of(A, p), [&](auto&& v) { walk_lanes(row, len, v); }, 32,
+                 [&](int m) { return A.pos[__ldg(sidx + m)]; }, [&](int m) { return resid_of(A, __ldg(sidx + m)); },
+                 A.c, A.g, A.out.n_out != nullptr, s, ds, n_val);
+    if ((threadIdx.x & 31) == 0) count_row_out<M>(p, s, ds, n_val, A.pos, A.ds, A.sA, A.id, A.out, A.wpart, A.st);
+}
+
+// Dense count of cell group b: the own particles that k_count_near marked
+// (s'_i = NaN), the group's neighbourhood staged in smem (whole block;
+// starts with a block barrier).
 template <class M, int NT>
-__global__ void __launch_bounds__(NT) k_count_rows(int n, int ngroups, int tmax, Geom g, Coef c, typename M::pos_t* __restrict__ pos,
-                                                       SuperGrid G, SuperCaps cp, GroupAux aux,
-                                                       const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
-                                                       const int* __restrict__ id, typename M::real* __restrict__ ds_out,
-                                                       typename M::real2* __restrict__ sA, CountOut out,
-                                                       const int* __restrict__ ulist, int* __restrict__ wpart,
-                                                       const long long* __restrict__ X, Status* st)
+__device__ __forceinline__ void count_rows_group(const RowArgs<M>& A, int b, int tmax, unsigned char* smem, int* s_n)
 {
     using pos_t = typename M::pos_t;
     using real = typename M::real;
-    if (halted(st)) return;
-    const int nu = st->nu;
-    // packed residuals of sorted particle j (FP32 mode; X is the state [3][n]); an index
-    // outside [0, n) is refused and reported rather than read
-    auto resid_of = [&](int j) {
-        if (M::fp64) return 0;
-        if ((unsigned)j >= (unsigned)n) {
-            st->bad_index = 1;
-            return 0;
-        }
-        return pack_resid(X, (size_t)n, j);
-    };
-    const bool want_n = out.n_out != nullptr;
-    if (nu <= n / DENSE_DIV) {
-        for (int k = blockIdx.x * (NT / 32) + (threadIdx.x >> 5); k < nu; k += gridDim.x * (NT / 32)) {
-            const int p = ulist[k];
-            const int ra = __ldg(aux.roff + p), b = ra / cp.seg;
-            const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
-            const uint16_t* row = nbr + ra;
-            const int len = row_len(__ldg(nnb + p));
-            real s, ds;
-            double n_val;
-            count_row<M>(pos[p], resid_of(p), [&](auto&& v) { walk_lanes(row, len, v); }, 32,
-                         [&](int m) { return pos[__ldg(sidx + m)]; }, [&](int m) { return resid_of(__ldg(sidx + m)); },
-                         c, g, want_n, s, ds, n_val);
-            if ((threadIdx.x & 31) == 0) count_row_out<M>(p, s, ds, n_val, pos, ds_out, sA, id, out, wpart, st);
-        }
-        return;
-    }
-    // dense: the own particles that k_count_near marked (s'_i = NaN), group by group
-    __shared__ int s_n;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const DenseLayout ly = dense_layout(cp, sizeof(pos_t), 0);
+    const DenseLayout ly = dense_layout(A.cp, sizeof(pos_t), 0);
     pos_t* spos = (pos_t*)smem;
     int* plist = (int*)(smem + ly.plist);
-    for (int b = blockIdx.x; b < ngroups; b += gridDim.x) {
-        __syncthreads();  // the previous group is done with the shared arrays
-        const int p0 = __ldg(G.cell_start + OWN_CELLS * b);
-        const int n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
-        const int nl = list_own<NT>(n_own, plist, &s_n, [&](int j) { return isnan(ds_out[p0 + j]); });
-        if (nl == 0) continue;
-        // the count reads no s_j, so the spare word of a staged position holds its residuals
-        stage_by_table<NT>(aux.stage_idx + (size_t)b * cp.smax, __ldg(aux.meta + b).x, [&](int m, int jj) {
-            pos_t pj = pos[jj];
-            if constexpr (!M::fp64) pj.w = resid_of(jj);
-            spos[m] = pj;
-        });
-        __syncthreads();
-        dense_rounds<NT>(nl, tmax, [&](int u, int sub, int tpp) {
-            const bool act = u < nl;
-            const int p = p0 + (act ? plist[u] : 0);
-            const uint16_t* row = nbr + __ldg(aux.roff + p);
-            const int len = act ? row_len(__ldg(nnb + p)) : 0;
-            real s, ds;
-            double n_val;
-            count_row<M>(pos[p], act ? resid_of(p) : 0, [&](auto&& v) { walk_chunks(row, len, sub, tpp, v); }, tpp,
-                         [&](int m) { return spos[m]; }, [&](int m) { return (int)spos[m].w; }, c, g, want_n, s,
-                         ds, n_val);
-            if (act && sub == 0) count_row_out<M>(p, s, ds, n_val, pos, ds_out, sA, id, out, wpart, st);
-        });
+    __syncthreads();  // the previous group is done with the shared arrays
+    const int p0 = __ldg(A.G.cell_start + OWN_CELLS * b);
+    const int n_own = __ldg(A.G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
+    const int nl = list_own<NT>(n_own, plist, s_n, [&](int j) { return isnan(A.ds[p0 + j]); });
+    if (nl == 0) return;
+    // the count reads no s_j, so the spare word of a staged position holds its residuals
+    stage_by_table<NT>(A.aux.stage_idx + (size_t)b * A.cp.smax, __ldg(A.aux.meta + b).x, [&](int m, int jj) {
+        pos_t pj = A.pos[jj];
+        if constexpr (!M::fp64) pj.w = resid_of(A, jj);
+        spos[m] = pj;
+    });
+    __syncthreads();
+    dense_rounds<NT>(nl, tmax, [&](int u, int sub, int tpp) {
+        const bool act = u < nl;
+        const int p = p0 + (act ? plist[u] : 0);
+        const uint16_t* row = A.nbr + __ldg(A.aux.roff + p);
+        const int len = act ? row_len(__ldg(A.nnb + p)) : 0;
+        real s, ds;
+        double n_val;
+        count_row<M>(A.pos[p], act ? resid_of(A, p) : 0, [&](auto&& v) { walk_chunks(row, len, sub, tpp, v); }, tpp,
+                     [&](int m) { return spos[m]; }, [&](int m) { return (int)spos[m].w; }, A.c, A.g,
+                     A.out.n_out != nullptr, s, ds, n_val);
+        if (act && sub == 0) count_row_out<M>(p, s, ds, n_val, A.pos, A.ds, A.sA, A.id, A.out, A.wpart, A.st);
+    });
+}
+
+// Dense mode of the count walk: more than n / DENSE_DIV unsettled particles.
+template <class M>
+__device__ __forceinline__ bool count_rows_dense(const RowArgs<M>& A) { return A.st->nu > A.n / DENSE_DIV; }
+
+template <class M, int NT>
+__global__ void __launch_bounds__(NT) k_count_rows(RowArgs<M> A, int ngroups, int tmax)
+{
+    if (halted(A.st)) return;
+    if (!count_rows_dense(A)) {
+        const int nu = A.st->nu;
+        for (int k = blockIdx.x * (NT / 32) + (threadIdx.x >> 5); k < nu; k += gridDim.x * (NT / 32))
+            count_rows_item(A, k);
+        return;
     }
+    __shared__ int s_n;
+    extern __shared__ __align__(16) unsigned char smem[];
+    for (int b = blockIdx.x; b < ngroups; b += gridDim.x) count_rows_group<M, NT>(A, b, tmax, smem, &s_n);
 }
 
 // ================================================================ chain-rule pass
@@ -1536,7 +1649,7 @@ __device__ __forceinline__ typename M::real chain_row(const typename M::pos_t& p
         const auto pj = fetch(m);
         if constexpr (M::fp64) {
             const double r2 = r2_d<M>(pi, pj, g);
-            if (r2 > c.rr2 && r2 < c.ra2) acc += get_s(pj) * Va_d(sqrt(r2), c);
+            if (r2 > c.rr2 && r2 < c.ra2) acc = __fma_rn(get_s(pj), Va_d(sqrt(r2), c), acc);
         } else {
             const unsigned long long r2i = r2_fix(pi, pj);
             if (r2i > c.rr2_fix && r2i < c.ra2_fix) {
@@ -1551,63 +1664,74 @@ __device__ __forceinline__ typename M::real chain_row(const typename M::pos_t& p
     return group_sum(acc, width);
 }
 
+// Sparse chain-rule term: window particle k of the list k_count_rows made (one
+// warp, one lane per row entry); clears the whole-force tag of every list
+// neighbour, which then joins the general list of k_force_rows.
+template <class M>
+__device__ __forceinline__ void chain_item(const RowArgs<M>& A, int k)
+{
+    using real = typename M::real;
+    const int p = A.wpart[k];
+    const int ra = __ldg(A.aux.roff + p), b = ra / A.cp.seg;
+    const int* sidx = A.aux.stage_idx + (size_t)b * A.cp.smax;
+    const uint16_t* row = A.nbr + ra;
+    const int len = row_len(__ldg(A.nnb + p));
+    const real acc = chain_row<M>(A.pos[p], [&](auto&& v) { walk_lanes(row, len, v); }, 32, [&](int m) {
+        const int jj = __ldg(sidx + m);
+        // the force of jj needs A_i: if it was tagged whole, it now goes on the general list
+        if constexpr (!M::fp64) {
+            if (atomicExch(reinterpret_cast<float*>(static_cast<float4*>(A.aux.fcore) + jj) + 3, 0.0f) != 0.0f)
+                A.aux.glist[atomicAdd(&A.st->ngen, 1)] = jj;
+        }
+        return A.pos[jj];
+    }, A.c, A.g);
+    if ((threadIdx.x & 31) == 0) A.sA[p].y = A.ds[p] * acc;
+}
+
+// Dense chain-rule terms of cell group b: its own window particles (whole
+// block; starts with a block barrier).
 template <class M, int NT>
-__global__ void __launch_bounds__(NT) k_chain(int n, int ngroups, int tmax, Geom g, Coef c, const typename M::pos_t* __restrict__ pos,
-                                                  SuperGrid G, SuperCaps cp, GroupAux aux,
-                                                  const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
-                                                  const typename M::real* __restrict__ ds,
-                                                  typename M::real2* __restrict__ sA, const int* __restrict__ wpart,
-                                                  Status* st)
+__device__ __forceinline__ void chain_group(const RowArgs<M>& A, int b, int tmax, unsigned char* smem, int* s_n)
 {
     using pos_t = typename M::pos_t;
     using real = typename M::real;
-    if (halted(st)) return;
-    const int nw = st->nwin;
-    if (nw <= n / DENSE_DIV) {
-        for (int k = blockIdx.x * (NT / 32) + (threadIdx.x >> 5); k < nw; k += gridDim.x * (NT / 32)) {
-            const int p = wpart[k];
-            const int ra = __ldg(aux.roff + p), b = ra / cp.seg;
-            const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
-            const uint16_t* row = nbr + ra;
-            const int len = row_len(__ldg(nnb + p));
-            const real acc = chain_row<M>(pos[p], [&](auto&& v) { walk_lanes(row, len, v); }, 32, [&](int m) {
-                const int jj = __ldg(sidx + m);
-                // the force of jj needs A_i: if it was tagged whole, it now goes on the general list
-                if constexpr (!M::fp64) {
-                    if (atomicExch(reinterpret_cast<float*>(static_cast<float4*>(aux.fcore) + jj) + 3, 0.0f) != 0.0f)
-                        aux.glist[atomicAdd(&st->ngen, 1)] = jj;
-                }
-                return pos[jj];
-            }, c, g);
-            if ((threadIdx.x & 31) == 0) sA[p].y = ds[p] * acc;
-        }
-        return;
-    }
-    // dense: the own window particles, group by group
-    __shared__ int s_n;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const DenseLayout ly = dense_layout(cp, sizeof(pos_t), 0);
+    const DenseLayout ly = dense_layout(A.cp, sizeof(pos_t), 0);
     pos_t* spos = (pos_t*)smem;
     int* plist = (int*)(smem + ly.plist);
-    for (int b = blockIdx.x; b < ngroups; b += gridDim.x) {
-        __syncthreads();  // the previous group is done with the shared arrays
-        const int p0 = __ldg(G.cell_start + OWN_CELLS * b);
-        const int n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
-        const int nl = list_own<NT>(n_own, plist, &s_n, [&](int j) { return ds[p0 + j] != (real)0; });
-        if (nl == 0) continue;
-        stage_by_table<NT>(aux.stage_idx + (size_t)b * cp.smax, __ldg(aux.meta + b).x,
-                       [&](int m, int jj) { spos[m] = pos[jj]; });
-        __syncthreads();
-        dense_rounds<NT>(nl, tmax, [&](int u, int sub, int tpp) {
-            const bool act = u < nl;
-            const int p = p0 + (act ? plist[u] : 0);
-            const uint16_t* row = nbr + __ldg(aux.roff + p);
-            const int len = act ? row_len(__ldg(nnb + p)) : 0;
-            const real acc = chain_row<M>(pos[p], [&](auto&& v) { walk_chunks(row, len, sub, tpp, v); }, tpp,
-                                          [&](int m) { return spos[m]; }, c, g);
-            if (act && sub == 0) sA[p].y = ds[p] * acc;
-        });
+    __syncthreads();  // the previous group is done with the shared arrays
+    const int p0 = __ldg(A.G.cell_start + OWN_CELLS * b);
+    const int n_own = __ldg(A.G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
+    const int nl = list_own<NT>(n_own, plist, s_n, [&](int j) { return A.ds[p0 + j] != (real)0; });
+    if (nl == 0) return;
+    stage_by_table<NT>(A.aux.stage_idx + (size_t)b * A.cp.smax, __ldg(A.aux.meta + b).x,
+                       [&](int m, int jj) { spos[m] = A.pos[jj]; });
+    __syncthreads();
+    dense_rounds<NT>(nl, tmax, [&](int u, int sub, int tpp) {
+        const bool act = u < nl;
+        const int p = p0 + (act ? plist[u] : 0);
+        const uint16_t* row = A.nbr + __ldg(A.aux.roff + p);
+        const int len = act ? row_len(__ldg(A.nnb + p)) : 0;
+        const real acc = chain_row<M>(A.pos[p], [&](auto&& v) { walk_chunks(row, len, sub, tpp, v); }, tpp,
+                                      [&](int m) { return spos[m]; }, A.c, A.g);
+        if (act && sub == 0) A.sA[p].y = A.ds[p] * acc;
+    });
+}
+
+template <class M>
+__device__ __forceinline__ bool chain_dense(const RowArgs<M>& A) { return A.st->nwin > A.n / DENSE_DIV; }
+
+template <class M, int NT>
+__global__ void __launch_bounds__(NT) k_chain(RowArgs<M> A, int ngroups, int tmax)
+{
+    if (halted(A.st)) return;
+    if (!chain_dense(A)) {
+        const int nw = A.st->nwin;
+        for (int k = blockIdx.x * (NT / 32) + (threadIdx.x >> 5); k < nw; k += gridDim.x * (NT / 32)) chain_item(A, k);
+        return;
     }
+    __shared__ int s_n;
+    extern __shared__ __align__(16) unsigned char smem[];
+    for (int b = blockIdx.x; b < ngroups; b += gridDim.x) chain_group<M, NT>(A, b, tmax, smem, &s_n);
 }
 
 // ================================================================ pass 2: forces + BAOAB
@@ -1649,92 +1773,109 @@ __device__ __forceinline__ bool tagged_whole(const void* fcore, int p)
     else return static_cast<const float4*>(fcore)[p].w != 0.0f;
 }
 
-template <class M, int NT>
-__global__ void __launch_bounds__(NT) k_force_rows(int n, int ngroups, int tmax, Geom g, Coef c,
-                                                       const typename M::pos_t* __restrict__ pos, SuperGrid G,
-                                                       SuperCaps cp, GroupAux aux, const uint16_t* __restrict__ nbr,
-                                                       const int* __restrict__ nnb,
-                                                       const typename M::real2* __restrict__ sA, const Status* st)
+// The force walk runs dense when k_chain did (it then cleared no tag, and
+// every particle is taken) or when the general list is long.
+template <class M>
+__device__ __forceinline__ bool force_all(const RowArgs<M>& A) { return A.st->nwin > A.n / DENSE_DIV; }
+template <class M>
+__device__ __forceinline__ bool force_dense(const RowArgs<M>& A)
+{
+    return force_all(A) || A.st->ngen > A.n / DENSE_DIV;
+}
+
+// Sparse force: general particle k (one warp, one lane per row entry).
+template <class M>
+__device__ __forceinline__ void force_item(const RowArgs<M>& A, int k)
 {
     using pos_t = typename M::pos_t;
     using real = typename M::real;
-    if (halted(st)) return;
-    const int ng = st->ngen, nw = st->nwin;
-    const bool useA = nw > 0;                  // A_j != 0 only for window particles
-    const bool all = nw > n / DENSE_DIV;       // k_chain ran dense and cleared no tag
-    if (!all && ng <= n / DENSE_DIV) {
-        for (int k = blockIdx.x * (NT / 32) + (threadIdx.x >> 5); k < ng; k += gridDim.x * (NT / 32)) {
-            const int p = aux.glist[k];
-            const int ra = __ldg(aux.roff + p), b = ra / cp.seg;
-            const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
-            const uint16_t* row = nbr + ra;
-            const int len = row_len(__ldg(nnb + p));
-            const pos_t pi = pos[p];
-            real f[3];
-            force_row<M>(pi, get_s(pi), useA ? sA[p].y : (real)0, [&](auto&& v) { walk_lanes(row, len, v); }, 32,
-                         [&](int m, real& Aj) {
-                             const int jj = __ldg(sidx + m);
-                             Aj = useA ? sA[jj].y : (real)0;
-                             return pos[jj];
-                         },
-                         c, g, f);
-            if ((threadIdx.x & 31) == 0) force_out<M>(aux.fcore, p, f);
-        }
-        return;
-    }
-    // dense: the own particles without a whole-force tag (all of them after a dense k_chain), group by group
-    __shared__ int s_n;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const DenseLayout ly = dense_layout(cp, sizeof(pos_t), sizeof(real));
+    const bool useA = A.st->nwin > 0;  // A_j != 0 only for window particles
+    const int p = A.aux.glist[k];
+    const int ra = __ldg(A.aux.roff + p), b = ra / A.cp.seg;
+    const int* sidx = A.aux.stage_idx + (size_t)b * A.cp.smax;
+    const uint16_t* row = A.nbr + ra;
+    const int len = row_len(__ldg(A.nnb + p));
+    const pos_t pi = A.pos[p];
+    real f[3];
+    force_row<M>(pi, get_s(pi), useA ? A.sA[p].y : (real)0, [&](auto&& v) { walk_lanes(row, len, v); }, 32,
+                 [&](int m, real& Aj) {
+                     const int jj = __ldg(sidx + m);
+                     Aj = useA ? A.sA[jj].y : (real)0;
+                     return A.pos[jj];
+                 },
+                 A.c, A.g, f);
+    if ((threadIdx.x & 31) == 0) force_out<M>(A.aux.fcore, p, f);
+}
+
+// Dense forces of cell group b: its own particles without a whole-force tag,
+// all of them after a dense chain-rule pass (whole block; starts with a block
+// barrier).
+template <class M, int NT>
+__device__ __forceinline__ void force_group(const RowArgs<M>& A, int b, int tmax, unsigned char* smem, int* s_n)
+{
+    using pos_t = typename M::pos_t;
+    using real = typename M::real;
+    const bool useA = A.st->nwin > 0;
+    const bool all = force_all(A);
+    const DenseLayout ly = dense_layout(A.cp, sizeof(pos_t), sizeof(real));
     pos_t* spos = (pos_t*)smem;
     real* sAj = (real*)(smem + ly.extra);
     int* plist = (int*)(smem + ly.plist);
-    for (int b = blockIdx.x; b < ngroups; b += gridDim.x) {
-        __syncthreads();  // the previous group is done with the shared arrays
-        const int p0 = __ldg(G.cell_start + OWN_CELLS * b);
-        const int n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
-        int nl;
-        if (all) {
-            for (int j = threadIdx.x; j < n_own; j += NT) plist[j] = j;
-            nl = n_own;
-        } else {
-            nl = list_own<NT>(n_own, plist, &s_n, [&](int j) { return !tagged_whole<M>(aux.fcore, p0 + j); });
-        }
-        if (nl == 0) continue;
-        stage_by_table<NT>(aux.stage_idx + (size_t)b * cp.smax, __ldg(aux.meta + b).x, [&](int m, int jj) {
-            spos[m] = pos[jj];
-            sAj[m] = useA ? sA[jj].y : (real)0;
-        });
-        __syncthreads();
-        dense_rounds<NT>(nl, tmax, [&](int u, int sub, int tpp) {
-            const bool act = u < nl;
-            const int p = p0 + (act ? plist[u] : 0);
-            const uint16_t* row = nbr + __ldg(aux.roff + p);
-            const int len = act ? row_len(__ldg(nnb + p)) : 0;
-            const pos_t pi = pos[p];
-            real f[3];
-            force_row<M>(pi, get_s(pi), useA ? sA[p].y : (real)0,
-                         [&](auto&& v) { walk_chunks_padded(row, len, sub, tpp, v); }, tpp,
-                         [&](int m, real& Aj) {
-                             Aj = sAj[m];
-                             return spos[m];
-                         },
-                         c, g, f);
-            if (act && sub == 0) force_out<M>(aux.fcore, p, f);
-        });
+    __syncthreads();  // the previous group is done with the shared arrays
+    const int p0 = __ldg(A.G.cell_start + OWN_CELLS * b);
+    const int n_own = __ldg(A.G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
+    int nl;
+    if (all) {
+        for (int j = threadIdx.x; j < n_own; j += NT) plist[j] = j;
+        nl = n_own;
+    } else {
+        nl = list_own<NT>(n_own, plist, s_n, [&](int j) { return !tagged_whole<M>(A.aux.fcore, p0 + j); });
     }
+    if (nl == 0) return;
+    stage_by_table<NT>(A.aux.stage_idx + (size_t)b * A.cp.smax, __ldg(A.aux.meta + b).x, [&](int m, int jj) {
+        spos[m] = A.pos[jj];
+        sAj[m] = useA ? A.sA[jj].y : (real)0;
+    });
+    __syncthreads();
+    dense_rounds<NT>(nl, tmax, [&](int u, int sub, int tpp) {
+        const bool act = u < nl;
+        const int p = p0 + (act ? plist[u] : 0);
+        const uint16_t* row = A.nbr + __ldg(A.aux.roff + p);
+        const int len = act ? row_len(__ldg(A.nnb + p)) : 0;
+        const pos_t pi = A.pos[p];
+        real f[3];
+        force_row<M>(pi, get_s(pi), useA ? A.sA[p].y : (real)0,
+                     [&](auto&& v) { walk_chunks_padded(row, len, sub, tpp, v); }, tpp,
+                     [&](int m, real& Aj) {
+                         Aj = sAj[m];
+                         return spos[m];
+                     },
+                     A.c, A.g, f);
+        if (act && sub == 0) force_out<M>(A.aux.fcore, p, f);
+    });
+}
+
+template <class M, int NT>
+__global__ void __launch_bounds__(NT) k_force_rows(RowArgs<M> A, int ngroups, int tmax)
+{
+    if (halted(A.st)) return;
+    if (!force_dense(A)) {
+        const int ng = A.st->ngen;
+        for (int k = blockIdx.x * (NT / 32) + (threadIdx.x >> 5); k < ng; k += gridDim.x * (NT / 32)) force_item(A, k);
+        return;
+    }
+    __shared__ int s_n;
+    extern __shared__ __align__(16) unsigned char smem[];
+    for (int b = blockIdx.x; b < ngroups; b += gridDim.x) force_group<M, NT>(A, b, tmax, smem, &s_n);
 }
 
 // k_step: the BAOAB update of every particle from its force slot (or, for a
 // force evaluation, the forces in caller order).  A streaming kernel.
 template <class M, int EPI>
-__global__ void __launch_bounds__(TPB) k_step(int n, Geom g, GroupAux aux, const int* __restrict__ id,
-                                              typename M::pos_t* __restrict__ pos_next,
-                                              const typename M::pos_t* __restrict__ xref, StepArgs a, Status* st)
+__device__ __forceinline__ void step_item(int p, int n, const Geom& g, const GroupAux& aux, const int* __restrict__ id,
+                                          typename M::pos_t* __restrict__ pos_next,
+                                          const typename M::pos_t* __restrict__ xref, const StepArgs& a, Status* st)
 {
-    if (halted(st)) return;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
     typename M::real f[3];
     if constexpr (M::fp64) {
         const F64x4 fc = static_cast<const F64x4*>(aux.fcore)[p];
@@ -1759,6 +1900,16 @@ __global__ void __launch_bounds__(TPB) k_step(int n, Geom g, GroupAux aux, const
     } else {
         integrate<M, EPI>(p, n, g, f[0], f[1], f[2], a, q, st, pos_next);
     }
+}
+
+template <class M, int EPI>
+__global__ void __launch_bounds__(TPB) k_step(int n, Geom g, GroupAux aux, const int* __restrict__ id,
+                                              typename M::pos_t* __restrict__ pos_next,
+                                              const typename M::pos_t* __restrict__ xref, StepArgs a, Status* st)
+{
+    if (halted(st)) return;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) step_item<M, EPI>(p, n, g, aux, id, pos_next, xref, a, st);
 }
 
 // ================================================================ FP64 energy / virial

@@ -29,6 +29,8 @@ VBC_REQ_QUEUED = 1
 VBC_REQ_RUNNING = 2
 VBC_FP32_SPLIT = 0
 VBC_FP64 = 1
+VBC_BATCH_FUSED = 0
+VBC_BATCH_GRAPHS = 1
 K_REBUILD, K_COUNT, K_CHAIN, K_FORCE, K_ENERGY = range(5)
 
 #: every function the header declares
@@ -38,7 +40,8 @@ EXPORTS = ("vbc_create_system", "vbc_create_typed_system", "vbc_build_neighbors"
            "vbc_compute_thermo",
            "vbc_profile", "vbc_profile_read", "vbc_kernel_launches", "vbc_destroy", "vbc_last_error",
            "vbc_compute_forces_noalloc", "vbc_estimate_device_bytes", "vbc_get_observables",
-           "vbc_batch_create", "vbc_batch_step", "vbc_batch_destroy", "vbc_set_tuning", "vbc_autotune",
+           "vbc_batch_create", "vbc_batch_step", "vbc_batch_destroy", "vbc_batch_set_mode",
+           "vbc_batch_fused_launches", "vbc_set_tuning", "vbc_autotune",
            "vbc_server_create", "vbc_server_submit", "vbc_server_wait", "vbc_server_info",
            "vbc_server_result", "vbc_server_destroy", "vbc_server_last_error")
 
@@ -169,6 +172,10 @@ def load() -> ctypes.CDLL:
     L.vbc_set_tuning.restype = i32
     L.vbc_autotune.argtypes = [vp, i64, dp, dp, dp, ctypes.POINTER(Tuning)]
     L.vbc_autotune.restype = i32
+    L.vbc_batch_set_mode.argtypes = [vp, i32, i64]
+    L.vbc_batch_set_mode.restype = i32
+    L.vbc_batch_fused_launches.argtypes = [vp]
+    L.vbc_batch_fused_launches.restype = i64
     L.vbc_batch_destroy.argtypes = [vp]
     L.vbc_batch_destroy.restype = None
     L.vbc_server_create.argtypes = [ctypes.POINTER(_ServerConfig), ctypes.POINTER(vp)]
@@ -570,6 +577,14 @@ class Batch:
         h = ctypes.c_void_p()
         _check(load().vbc_batch_create(arr, len(self._systems), ctypes.byref(h)))
         self._h = h
+
+    def set_mode(self, mode: int = VBC_BATCH_FUSED, wait_limit: int = -1):
+        """VBC_BATCH_FUSED (one cooperative launch per iteration for all systems) or
+        VBC_BATCH_GRAPHS; wait_limit bounds each grid-wide wait (< 0: the default)."""
+        _check(load().vbc_batch_set_mode(self._h, int(mode), int(wait_limit)))
+
+    def fused_launches(self) -> int:
+        return int(load().vbc_batch_fused_launches(self._h))
 
     def step(self, nsteps: int, dt: float, kT, gamma: float):
         """kT: one temperature for all systems, or one per system."""

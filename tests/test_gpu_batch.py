@@ -1,8 +1,11 @@
 """Batched stepping (vbc_batch_*): systems of uneven size, valency and
-temperature advanced together, their two-step graphs captured side by side
-into one CUDA graph.  Every system must end bitwise where it ends when stepped
-alone, over runs long enough to rebuild the neighbour lists, for odd and even
-step counts (the last iteration runs outside the graph)."""
+temperature advanced together, either by one cooperative launch per iteration
+for all systems (the fused mode, the default) or by their two-step graphs
+captured side by side into one CUDA graph.  Every system must end bitwise
+where it ends when stepped alone, over runs long enough to rebuild the
+neighbour lists, for odd and even step counts.  A grid-wide wait that gives
+up (a wait limit of zero spins) must come back as VBC_ERR_TIMEOUT with the
+GPU context usable and every system halted until its state is loaded again."""
 from __future__ import annotations
 
 import numpy as np
@@ -22,8 +25,9 @@ def _make(n, rho, f, kT, seed, prec):
     return vbc.System(pos, L, vbc.params(E_a=8.0, f=f), vel=vel, seed=seed, precision=prec)
 
 
+@pytest.mark.parametrize("mode", [vbc.VBC_BATCH_FUSED, vbc.VBC_BATCH_GRAPHS])
 @pytest.mark.parametrize("prec", [vbc.VBC_FP32_SPLIT, vbc.VBC_FP64])
-def test_batch_equals_each_system_alone(prec):
+def test_batch_equals_each_system_alone(prec, mode):
     kts = [c[3] for c in SYS]
     alone = []
     for c in SYS:
@@ -34,14 +38,80 @@ def test_batch_equals_each_system_alone(prec):
     systems = [_make(*c, prec) for c in SYS]
     try:
         with vbc.Batch(systems) as b:
+            b.set_mode(mode)
             b.step(151, 0.005, kts, 1.0)
             b.step(40, 0.005, kts, 1.0)
+            assert b.fused_launches() == (191 if mode == vbc.VBC_BATCH_FUSED else 0)
         for s, (pos, vel) in zip(systems, alone):
             p2, v2, step = s.get_state()
             assert step == 191
             np.testing.assert_array_equal(p2, pos)
             np.testing.assert_array_equal(v2, vel)
             assert s.stats().rebuilds > 1
+    finally:
+        for s in systems:
+            s.close()
+
+
+def test_fused_wait_that_gives_up_is_reported_and_recoverable():
+    """With a wait limit of zero every grid-wide wait gives up at once: the step
+    returns VBC_ERR_TIMEOUT, the systems refuse to step until a state is loaded,
+    and after loading one they step bitwise like a fresh system from that state."""
+    kts = [c[3] for c in SYS[:3]]
+    systems = [_make(*c, vbc.VBC_FP32_SPLIT) for c in SYS[:3]]
+    try:
+        states = [s.get_state() for s in systems]
+        with vbc.Batch(systems) as b:
+            b.set_mode(vbc.VBC_BATCH_FUSED, wait_limit=0)
+            with pytest.raises(vbc.VBCError) as e:
+                b.step(10, 0.005, kts, 1.0)
+            assert e.value.code == vbc.VBC_ERR_TIMEOUT
+            with pytest.raises(vbc.VBCError) as e:
+                systems[0].step(2, 0.005, kts[0], 1.0)
+            assert e.value.code == vbc.VBC_ERR_TIMEOUT
+            with pytest.raises(vbc.VBCError) as e:
+                b.step(4, 0.005, kts, 1.0)
+            assert e.value.code == vbc.VBC_ERR_TIMEOUT
+            # load the states again: the default limit, and the batch steps as the systems do alone
+            for s, (x, v, st) in zip(systems, states):
+                s.set_state(x, v, step=st)
+            b.set_mode(vbc.VBC_BATCH_FUSED)
+            b.step(30, 0.005, kts, 1.0)
+        for s, c, (x, v, st) in zip(systems, SYS[:3], states):
+            with _make(*c, vbc.VBC_FP32_SPLIT) as ref:
+                ref.set_state(x, v, step=st)
+                ref.step(30, 0.005, c[3], 1.0)
+                xr, vr, sr = ref.get_state()
+            xb, vb, sb = s.get_state()
+            assert sb == sr
+            np.testing.assert_array_equal(xb, xr)
+            np.testing.assert_array_equal(vb, vr)
+    finally:
+        for s in systems:
+            s.close()
+
+
+def test_batches_the_fused_launch_does_not_take_use_the_graphs():
+    """A system on another row-walk block shape keeps the batch on the graphs;
+    the result is still each system's own."""
+    kts = [c[3] for c in SYS[:2]]
+    alone = []
+    for c in SYS[:2]:
+        with _make(*c, vbc.VBC_FP32_SPLIT) as s:
+            s.set_tuning(rows_threads_per_block=256)
+            s.step(25, 0.005, c[3], 1.0)
+            alone.append(s.get_state()[:2])
+    systems = [_make(*c, vbc.VBC_FP32_SPLIT) for c in SYS[:2]]
+    try:
+        for s in systems:
+            s.set_tuning(rows_threads_per_block=256)
+        with vbc.Batch(systems) as b:
+            b.step(25, 0.005, kts, 1.0)
+            assert b.fused_launches() == 0
+        for s, (pos, vel) in zip(systems, alone):
+            p2, v2, _ = s.get_state()
+            np.testing.assert_array_equal(p2, pos)
+            np.testing.assert_array_equal(v2, vel)
     finally:
         for s in systems:
             s.close()
