@@ -70,6 +70,8 @@ def parse():
                     help="the multi-type sticker-chain workload (31,250 chains of 64 beads at bead density 0.3, "
                          "stickers every 4th bead, FP64 typed path); one JSON line")
     ap.add_argument("--sticker-chains", type=int, default=31_250)
+    ap.add_argument("--sticker-precision", choices=("fp32", "fp64"), default="fp32",
+                    help="arithmetic of the sticker-chain leg: the FP32 split (default) or FP64")
     ap.add_argument("--leg", choices=("served", "batched"), default=None,
                     help="run only this optional leg and print its JSON object (the main run starts each "
                          "optional leg this way, in a process of its own)")
@@ -431,15 +433,16 @@ def run_batched(args):
 def stickers(args):
     """Timesteps/s of bead-spring sticker chains (Sec. 4): spacers and stickers,
     stickers attracting and counting stickers only at valency 1 (E_a 10), every
-    pair with the soft core, harmonic bonds k = 100, r0 = 1; FP64 typed path,
-    after an untimed equilibration."""
+    pair with the soft core, harmonic bonds k = 100, r0 = 1; the typed path in
+    the FP32 split (or FP64), after an untimed equilibration."""
     import torch
     from paper_2609_07842_b300 import inputs, vbc
+    prec = vbc.VBC_FP32_SPLIT if args.sticker_precision == "fp32" else vbc.VBC_FP64
     pos, L, t, bonds = inputs.sticker_chains(args.sticker_chains, 64, 0.3, seed=SEED)
     vel = inputs.maxwell_velocities(pos.shape[0], KT, seed=SEED + 1)
     spacer, mixed, sticker = vbc.params(E_a=0.0, f=2.0), vbc.params(E_a=0.0), vbc.params(E_a=10.0, f=1.0)
     with vbc.System.typed(pos, L, t, [[spacer, mixed], [mixed, sticker]], [[0, 0], [0, 1]], bonds=bonds,
-                          k_bond=100.0, r0_bond=1.0, vel=vel, skin=SKIN, seed=SEED) as s:
+                          k_bond=100.0, r0_bond=1.0, vel=vel, skin=SKIN, seed=SEED, precision=prec) as s:
         s.step(args.equil, DT, KT, GAMMA)
         torch.cuda.synchronize()
         r0 = s.stats().rebuilds
@@ -452,7 +455,10 @@ def stickers(args):
     print(json.dumps({"metric": "sticker-chain timesteps/s", "value": args.steps / sec, "unit": "timesteps/s",
                       "ms_per_step": 1e3 * sec / args.steps, "particle_steps_per_s": n * args.steps / sec,
                       "steps": args.steps, "steps_per_rebuild": args.steps / max(st.rebuilds - r0, 1),
-                      "dtype": "f64", "timing": "host clock around the steps, device synchronised on both sides",
+                      "dtype": "f32" if prec == vbc.VBC_FP32_SPLIT else "f64",
+                      "precision": ("FP32 pair and bond arithmetic, fixed-point counts and state, FP64 energies"
+                                    if prec == vbc.VBC_FP32_SPLIT else "FP64 throughout"),
+                      "timing": "host clock around the steps, device synchronised on both sides",
                       "config": {"workload": (f"{args.sticker_chains:,} chains x 64 beads ({n:,} beads), bead "
                                               f"density 0.3, stickers every 4th bead (valency 1, E_a 10, count "
                                               f"stickers only), harmonic bonds k 100 r0 1, BAOAB dt {DT}"),

@@ -143,8 +143,10 @@ typedef struct {
 /*
  * Create a multi-type system.  cfg is as for vbc_create_system except that
  * cfg->params is ignored (the neighbour list reaches the largest
- * max(r_r, r_a, r_h) of the table plus the skin) and cfg->precision must be
- * VBC_FP64.  Every other call then works on it as on any system, except
+ * max(r_r, r_a, r_h) of the table plus the skin).  cfg->precision selects
+ * the arithmetic as for one type: VBC_FP64, or VBC_FP32_SPLIT (cubic box;
+ * exact fixed-point counts, FP32 pair and bond terms, FP64 state, energies
+ * and virial).  Every other call then works on it as on any system, except
  * vbc_set_params and vbc_get_observables (INVALID_ARG).  Errors as
  * vbc_create_system, and INVALID_ARG for a bad type, table, mask or bond.
  */

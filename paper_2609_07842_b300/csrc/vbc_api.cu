@@ -117,6 +117,7 @@ struct vbc_system {
     int *t_mask = nullptr, *t_type = nullptr, *t_tsort = nullptr, *t_inv = nullptr, *t_bto = nullptr;
     long long* t_bptr = nullptr;
     long long t_nbto = 0;  // entries of t_bto
+    double2* t_esa = nullptr;  // [n] FP64 (s_i, A_i) of the typed energy evaluation
     void *post = nullptr, *xref = nullptr;
     int cur = 0;
     uint16_t* nbr = nullptr;
@@ -471,7 +472,7 @@ void free_all(vbc_system* s)
 {
     dfree(s->x); dfree(s->v); dfree(s->xt); dfree(s->vt); dfree(s->id); dfree(s->idt);
     dfree(s->t_pc); dfree(s->t_mask); dfree(s->t_type); dfree(s->t_tsort); dfree(s->t_inv); dfree(s->t_bptr);
-    dfree(s->t_bto);
+    dfree(s->t_bto); dfree(s->t_esa);
     dfree(s->pos[0]); dfree(s->pos[1]); dfree(s->post); dfree(s->xref);
     dfree(s->nbr); dfree(s->scratch); dfree(s->nnb); dfree(s->cell_of); dfree(s->slot_of); dfree(s->order);
     dfree(s->cell_count); dfree(s->cell_start); dfree(s->morton_rank); dfree(s->sc_org);
@@ -594,11 +595,9 @@ int enqueue_rebuild(vbc_system* s)
                                             (pos_t*)s->post, s->st);
     k_copyback<M><<<nb, TPB, 0, s->stream>>>(n, s->xt, s->vt, s->idt, (const pos_t*)s->post, s->x, s->v, s->id,
                                              pos, (pos_t*)s->xref, s->st);
-    if constexpr (M::fp64) {
-        if (s->typed) {
-            k_tmaps<<<nb, TPB, 0, s->stream>>>(n, s->id, s->tdev);
-            VBC_TRY(check_launch(s));
-        }
+    if (s->typed) {
+        k_tmaps<<<nb, TPB, 0, s->stream>>>(n, s->id, s->tdev);
+        VBC_TRY(check_launch(s));
     }
     if constexpr (!M::fp64) {
         if (s->rel_lists) {
@@ -621,18 +620,33 @@ int typed_grid(const vbc_system* s)
 
 int enqueue_typed_count_chain(vbc_system* s, double* n_out, bool want_window)
 {
-    P64* pos = (P64*)s->pos[s->cur];
     CountOut out{n_out, want_window ? s->win : nullptr};
     const int n = (int)s->n, gb = typed_grid(s);
-    {
-        Timed t(s, VBC_K_COUNT);
-        k_tcount<<<gb, SC_TPB, 0, s->stream>>>(n, s->geom, pos, s->caps(), s->aux(), s->nbr, s->nnb, s->id, s->tdev,
-                                               (double*)s->ds, (double2*)s->sA, out, s->st);
-    }
-    {
-        Timed t(s, VBC_K_CHAIN);
-        k_tchain<<<gb, SC_TPB, 0, s->stream>>>(n, s->geom, pos, s->caps(), s->aux(), s->nbr, s->nnb, s->tdev,
-                                               (const double*)s->ds, (double2*)s->sA, s->st);
+    if (s->prec == VBC_FP64) {
+        P64* pos = (P64*)s->pos[s->cur];
+        {
+            Timed t(s, VBC_K_COUNT);
+            k_tcount<<<gb, SC_TPB, 0, s->stream>>>(n, s->geom, pos, s->caps(), s->aux(), s->nbr, s->nnb, s->id,
+                                                   s->tdev, (double*)s->ds, (double2*)s->sA, out, s->st);
+        }
+        {
+            Timed t(s, VBC_K_CHAIN);
+            k_tchain<<<gb, SC_TPB, 0, s->stream>>>(n, s->geom, pos, s->caps(), s->aux(), s->nbr, s->nnb, s->tdev,
+                                                   (const double*)s->ds, (double2*)s->sA, s->st);
+        }
+    } else {
+        int4* pos = (int4*)s->pos[s->cur];
+        {
+            Timed t(s, VBC_K_COUNT);
+            k_tcount32<<<gb, SC_TPB, 0, s->stream>>>(n, s->geom, pos, s->caps(), s->aux(), s->nbr, s->nnb, s->id,
+                                                     s->tdev, (const long long*)s->x, (float*)s->ds, (float2*)s->sA,
+                                                     out, s->st);
+        }
+        {
+            Timed t(s, VBC_K_CHAIN);
+            k_tchain32<<<gb, SC_TPB, 0, s->stream>>>(n, s->geom, pos, s->caps(), s->aux(), s->nbr, s->nnb, s->tdev,
+                                                     (const float*)s->ds, (float2*)s->sA, s->st);
+        }
     }
     return check_launch(s, 2);
 }
@@ -665,9 +679,7 @@ RowArgs<M> row_args(const vbc_system* s, const CountOut& out, int cur = -1)
 template <class M>
 int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window)
 {
-    if constexpr (M::fp64) {
-        if (s->typed) return enqueue_typed_count_chain(s, n_out, want_window);
-    }
+    if (s->typed) return enqueue_typed_count_chain(s, n_out, want_window);
     using pos_t = typename M::pos_t;
     using real = typename M::real;
     using real2 = typename M::real2;
@@ -707,13 +719,16 @@ int enqueue_force(vbc_system* s, const StepArgs& a)
     {
         Timed t(s, VBC_K_FORCE);
         bool done = false;
-        if constexpr (M::fp64) {
-            if (s->typed) {
+        if (s->typed) {
+            if constexpr (M::fp64)
                 k_tforce<<<typed_grid(s), SC_TPB, 0, s->stream>>>(n, s->geom, pos, s->caps(), s->aux(), s->nbr,
                                                                    s->nnb, s->id, s->tdev, (const double2*)s->sA,
                                                                    s->st);
-                done = true;
-            }
+            else
+                k_tforce32<<<typed_grid(s), SC_TPB, 0, s->stream>>>(n, s->geom, pos, s->caps(), s->aux(), s->nbr,
+                                                                     s->nnb, s->id, s->tdev, (const float2*)s->sA,
+                                                                     s->st);
+            done = true;
         }
         if (!done)
             for_row_tpb(s->row_tpb, [&](auto nt) -> int {
@@ -732,22 +747,27 @@ int enqueue_force(vbc_system* s, const StepArgs& a)
 
 // U, W and the pair count (FP64, on request); n_sorted, if not null, receives
 // the FP64 count of every particle in sorted order (single-type systems).
+// Multi-type systems: FP64 counts, switches and chain terms recomputed from
+// the positions (k_tcount_e, k_tchain_e), then U and W; n_caller receives the
+// FP64 counts in caller order on request.
 template <class M>
-int enqueue_energy(vbc_system* s, double* n_sorted = nullptr)
+int enqueue_energy(vbc_system* s, double* n_sorted = nullptr, double* n_caller = nullptr)
 {
     using pos_t = typename M::pos_t;
     {
         Timed t(s, VBC_K_ENERGY);
         const pos_t* pos = (const pos_t*)s->pos[s->cur];
-        if constexpr (M::fp64) {
-            if (s->typed) {
-                const int gb = std::min(typed_grid(s), s->nsc);  // one partial sum per block
-                k_tenergy<<<gb, SC_TPB, 0, s->stream>>>((int)s->n, s->geom, pos, s->caps(), s->aux(), s->nbr,
-                                                         s->nnb, s->id, s->tdev, (const double2*)s->sA, s->partial,
-                                                         s->ppairs, s->st);
-                k_reduce_final<<<1, RED_TPB, 0, s->stream>>>(gb, s->partial, s->ppairs, s->red, s->st);
-                return check_launch(s, 2);
-            }
+        if (s->typed) {
+            const int n = (int)s->n, gt = typed_grid(s);
+            const int gb = std::min(gt, s->nsc);  // one partial sum per block
+            k_tcount_e<M><<<gt, SC_TPB, 0, s->stream>>>(n, s->geom, pos, s->caps(), s->aux(), s->nbr, s->nnb, s->id,
+                                                        s->tdev, s->e_sd, n_caller, s->st);
+            k_tchain_e<M><<<gt, SC_TPB, 0, s->stream>>>(n, s->geom, pos, s->caps(), s->aux(), s->nbr, s->nnb,
+                                                        s->tdev, s->e_sd, s->t_esa, s->st);
+            k_tenergy<M><<<gb, SC_TPB, 0, s->stream>>>(n, s->geom, pos, s->caps(), s->aux(), s->nbr, s->nnb, s->id,
+                                                       s->tdev, s->t_esa, s->partial, s->ppairs, s->st);
+            k_reduce_final<<<1, RED_TPB, 0, s->stream>>>(gb, s->partial, s->ppairs, s->red, s->st);
+            return check_launch(s, 4);
         }
         const int nb = s->nsc;
         k_count_e<M><<<nb, SC_TPB, s->smem_energy(), s->stream>>>(s->geom, s->coef, pos, s->grid(), s->caps(),
@@ -859,7 +879,7 @@ long long device_bytes(const vbc_system* s)
     long long b = device_bytes_of(s->n, s->prec, z);
     if (s->typed) {  // pair table and mask, type, sorted-type and inverse maps, bond partners
         const long long T = s->tdev.T;
-        b += T * T * ((long long)sizeof(Coef) + 4) + 3 * s->n * 4 + (s->n + 1) * 8 + s->t_nbto * 4;
+        b += T * T * ((long long)sizeof(Coef) + 4) + 3 * s->n * 4 + (s->n + 1) * 8 + s->t_nbto * 4 + s->n * 16;
     }
     return b;
 }
@@ -1000,10 +1020,8 @@ int epi_of(int64_t it, int64_t nsteps) { return it == 0 ? EPI_START : (it < nste
 
 // Thermodynamic reductions of the current state (vbc_compute_thermo).  The
 // list is brought up to date first unless the resident forces are fresh (a
-// run of steps left the list current); the single-type evaluation then uses
-// the FP64 energy kernels, which write none of the step loop's arrays, and
-// the multi-type one re-runs its FP64 count and chain-rule walks, which write
-// the same values again.  So the resident forces stay valid.
+// run of steps left the list current); the FP64 energy kernels then write
+// none of the step loop's arrays, so the resident forces stay valid.
 template <class M>
 int thermo_impl(vbc_system* s, vbc_thermo* out)
 {
@@ -1023,17 +1041,9 @@ int thermo_impl(vbc_system* s, vbc_thermo* out)
             VBC_TRY(enqueue_rebuild<M>(s));
             VBC_TRY(clear_rebuild_flag(s));
         }
-        const double* dsv;
-        int stride;
-        if (s->typed) {
-            VBC_TRY(enqueue_count_chain<M>(s, nv, false));  // counts in caller order
-            dsv = (const double*)s->ds;
-            stride = 1;
-        } else {
-            dsv = (const double*)s->e_sd + 1;  // s' of (s, s')
-            stride = 2;
-        }
-        VBC_TRY(enqueue_energy<M>(s, s->typed ? nullptr : nv));
+        const double* dsv = (const double*)s->e_sd + 1;  // s' of the FP64 (s, s')
+        const int stride = 2;
+        VBC_TRY(s->typed ? enqueue_energy<M>(s, nullptr, nv) : enqueue_energy<M>(s, nv, nullptr));
         k_thermo_part<M><<<THERMO_GRID, RED_TPB, 0, s->stream>>>((int)s->n, s->v, nv, dsv, stride, s->t_part,
                                                                  s->t_wpart);
         k_thermo_final<<<1, RED_TPB, 0, s->stream>>>(THERMO_GRID, s->t_part, s->t_wpart, s->t_out);
@@ -1779,7 +1789,8 @@ int vbc_create_typed_system(const vbc_config* cfg, const vbc_types* ty, vbc_syst
     g_err.clear();
     if (!cfg || !ty || !out) return fail(VBC_ERR_INVALID_ARG, "cfg, types and out must not be NULL");
     *out = nullptr;
-    if (cfg->precision != VBC_FP64) return fail(VBC_ERR_INVALID_ARG, "multi-type systems need VBC_FP64");
+    if (cfg->precision != VBC_FP64 && cfg->precision != VBC_FP32_SPLIT)
+        return fail(VBC_ERR_INVALID_ARG, "precision must be VBC_FP32_SPLIT or VBC_FP64");
     const int T = ty->ntypes;
     if (T < 1 || T > MAX_TYPES) return fail(VBC_ERR_INVALID_ARG, "ntypes must be in [1, %d]", MAX_TYPES);
     if (!ty->type || !ty->pair || !ty->count_mask)
@@ -1788,7 +1799,7 @@ int vbc_create_typed_system(const vbc_config* cfg, const vbc_types* ty, vbc_syst
     const int64_t n = cfg->n;
     for (int64_t i = 0; i < n; ++i)
         if (ty->type[i] < 0 || ty->type[i] >= T) return fail(VBC_ERR_INVALID_ARG, "type of particle %lld out of range", (long long)i);
-    Geom g0{};  // only the FP64 fields of the pair coefficients are used; the box scale keeps the rest finite
+    Geom g0{};  // checks the parameters here; the coefficients are made again for the system's grid below
     for (int a = 0; a < 3; ++a)
         g0.s32d[a] = cfg->box[a] > 0 && std::isfinite(cfg->box[a]) ? cfg->box[a] / 4294967296.0 : 1.0;
     std::vector<Coef> pc((size_t)T * T);
@@ -1846,7 +1857,12 @@ int vbc_create_typed_system(const vbc_config* cfg, const vbc_types* ty, vbc_syst
     TALLOC(dalloc(s->t_inv, (size_t)n));
     TALLOC(dalloc(s->t_bptr, (size_t)n + 1));
     TALLOC(dalloc(s->t_bto, bto.size()));
+    TALLOC(dalloc(s->t_esa, (size_t)n));
     s->t_nbto = (long long)bto.size();
+    // the pair coefficients for the system's grid: the FP32 split's fixed-point radii and switch threshold
+    for (int a = 0; a < T; ++a)
+        for (int b2 = 0; b2 < T; ++b2)
+            if ((rc2 = make_coef(ty->pair[a * T + b2], s->geom, pc[(size_t)a * T + b2])) != VBC_OK) return bail(rc2);
 #undef TALLOC
     std::vector<int> mask((size_t)T * T), type((size_t)n);
     for (int k = 0; k < T * T; ++k) mask[(size_t)k] = ty->count_mask[k];

@@ -12,8 +12,13 @@
 //   A_i  = s'_i sum_j s_j V_a^{ij}(r_ij)
 //   g_ij = V_r^{ij}' + s_i s_j V_a^{ij}' + (mask[t_i][t_j] A_i + mask[t_j][t_i] A_j) omega^{ij}'
 // and a bond (i, j) adds k_b (r - r_0) to g_ij; bonded pairs keep their
-// non-bonded terms.  One warp per particle, one lane per list entry, FP64
-// pair arithmetic on the 64-bit fixed-point positions.
+// non-bonded terms.  One warp per particle, one lane per list entry.  The
+// FP64 mode uses FP64 pair arithmetic on the 64-bit fixed-point positions;
+// the FP32-split mode (k_tcount32, k_tchain32, k_tforce32) the single-type
+// split: exact integer squared separations of the 32-bit fixed-point words,
+// integer counts plus 2^-31 fixed-point window weights (window pairs measured
+// finer with the state's residual bits), FP32 pair and bond terms.  Energies
+// and the virial are FP64 in both modes (k_tcount_e, k_tchain_e, k_tenergy).
 #pragma once
 
 #include "vbc_kernels.cuh"
@@ -184,11 +189,195 @@ __global__ void __launch_bounds__(SC_TPB) k_tforce(int n, Geom g, const P64* __r
     }
 }
 
+// ---------------------------------------------------------------- FP32-split walks
+// Counts over the masked neighbour types in fixed point (the single-type
+// split's arithmetic with the pair's own coefficients); s_i and s'_i from the
+// particle's own type.  X is the state [3][n] (residual bits of window pairs).
+__global__ void __launch_bounds__(SC_TPB) k_tcount32(int n, Geom g, int4* __restrict__ pos, SuperCaps cp,
+                                                     GroupAux aux, const uint16_t* __restrict__ nbr,
+                                                     const int* __restrict__ nnb, const int* __restrict__ id,
+                                                     TypedDev t, const long long* __restrict__ X,
+                                                     float* __restrict__ ds_out, float2* __restrict__ sA,
+                                                     CountOut out, Status* st)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->rebuild = 0;
+    if (halted(st)) return;
+    for (int p = warp_id_global(); p < n; p += warps_total()) {
+        const int4 pi = pos[p];
+        const int ri = pack_resid(X, (size_t)n, p);
+        const int ti = t.tsort[p];
+        int full = 0;
+        unsigned long long q = 0;
+        typed_row(p, aux, cp, nbr, nnb, [&](int j) {
+            const int k = ti * t.T + t.tsort[j];
+            if (!t.mask[k]) return;
+            const Coef& c = t.pc[k];
+            const int4 pj = pos[j];
+            const unsigned long long r2 = r2_fix(pi, pj);
+            if (r2 >= c.rh2_fix) return;
+            if (r2 <= c.rl2_fix) {
+                ++full;
+                return;
+            }
+            // omega has zero slope at both ends of the window: a pair the finer separation
+            // moves across r_l or r_h changes n_i by O(dr^2)
+            const unsigned long long rf = r2_fine(pi, ri, pj, pack_resid(X, (size_t)n, j), r2);
+            if (rf <= c.rl2_fix) q += 2147483648ull;
+            else if (rf < c.rh2_fix) q += window_weight_fix31(rf, rf - c.rl2_fix, c.rl_s, c.w_s);
+        });
+        full = group_sum(full, 32);
+        q = group_sum(q, 32);
+        const Coef& own = t.pc[ti * t.T + ti];
+        const long long T = ((long long)full - own.fd_int) * 2147483648LL + (long long)q - own.fd_frac_fix;
+        float sv, dsv;
+        switch_from_fix(T, sv, dsv);
+        if ((threadIdx.x & 31) == 0) {
+            ds_out[p] = dsv;
+            sA[p] = make_float2(sv, 0.0f);
+            put_w(pos + p, sv);
+            if (out.n_out) out.n_out[id[p]] = (double)full + (double)q * 4.656612873077393e-10;
+            if (dsv != 0.0f && out.in_window) atomicAdd((unsigned long long*)out.in_window, 1ull);
+        }
+    }
+}
+
+// A_i = s'_i sum_j s_j V_a^{ij} (FP32) for the particles inside their window.
+__global__ void __launch_bounds__(SC_TPB) k_tchain32(int n, Geom g, const int4* __restrict__ pos, SuperCaps cp,
+                                                     GroupAux aux, const uint16_t* __restrict__ nbr,
+                                                     const int* __restrict__ nnb, TypedDev t,
+                                                     const float* __restrict__ ds, float2* __restrict__ sA,
+                                                     Status* st)
+{
+    if (halted(st)) return;
+    for (int p = warp_id_global(); p < n; p += warps_total()) {
+        const float dsi = ds[p];
+        if (dsi == 0.0f) continue;  // uniform over the warp
+        const int4 pi = pos[p];
+        const int ti = t.tsort[p];
+        float acc = 0.0f;
+        typed_row(p, aux, cp, nbr, nnb, [&](int j) {
+            const Coef& c = t.pc[ti * t.T + t.tsort[j]];
+            const int4 pj = pos[j];
+            const unsigned long long r2i = r2_fix(pi, pj);
+            if (r2i > c.rr2_fix && r2i < c.ra2_fix) {
+                const float r2 = u64_to_float(r2i) * g.s32sq;
+                const float r = r2 * rsqrtf(r2);
+                const float uu = __fdividef(s64_to_float((long long)r2i - (long long)c.rm2_fix) * c.s2hinv, r + c.rmf);
+                const float qq = 1.0f - uu * uu;
+                acc = __fmaf_rn(get_s(pj), -c.Eaf * qq * qq, acc);
+            }
+        });
+        acc = group_sum(acc, 32);
+        if ((threadIdx.x & 31) == 0) sA[p].y = dsi * acc;
+    }
+}
+
+// Forces of every particle (pairs and bonds, FP32) into its force slot.  A
+// pair's chain-rule factor is mask[t_i][t_j] A_i + mask[t_j][t_i] A_j.
+__global__ void __launch_bounds__(SC_TPB) k_tforce32(int n, Geom g, const int4* __restrict__ pos, SuperCaps cp,
+                                                     GroupAux aux, const uint16_t* __restrict__ nbr,
+                                                     const int* __restrict__ nnb, const int* __restrict__ id,
+                                                     TypedDev t, const float2* __restrict__ sA, Status* st)
+{
+    if (halted(st)) return;
+    for (int p = warp_id_global(); p < n; p += warps_total()) {
+        const int4 pi = pos[p];
+        const int ti = t.tsort[p];
+        const float2 sai = sA[p];
+        float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+        typed_row(p, aux, cp, nbr, nnb, [&](int j) {
+            const int tj = t.tsort[j];
+            const int k = ti * t.T + tj;
+            const float2 saj = sA[j];
+            pair_f32(pi, sai.x, t.mask[k] ? sai.y : 0.0f, pos[j], saj.x, t.mask[tj * t.T + ti] ? saj.y : 0.0f,
+                     t.pc[k], g, fx, fy, fz);
+        });
+        fx = group_sum(fx, 32);
+        fy = group_sum(fy, 32);
+        fz = group_sum(fz, 32);
+        if ((threadIdx.x & 31) == 0) {
+            typed_bonds(p, id, t, [&](int q) {
+                const int4 pq = pos[q];
+                const float dx = (float)(pi.x - pq.x) * g.s32, dy = (float)(pi.y - pq.y) * g.s32,
+                            dz = (float)(pi.z - pq.z) * g.s32;
+                const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz));
+                if (r2 > 0.0f) {
+                    const float rinv = rsqrtf(r2);
+                    const float gr = (float)t.kb * (r2 * rinv - (float)t.r0) * rinv;
+                    fx = __fmaf_rn(-gr, dx, fx);
+                    fy = __fmaf_rn(-gr, dy, fy);
+                    fz = __fmaf_rn(-gr, dz, fz);
+                }
+            });
+            static_cast<float4*>(aux.fcore)[p] = make_float4(fx, fy, fz, 0.0f);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- FP64 energy walks (either mode)
+// FP64 counts, s and s' of every particle from the positions of mode M, into
+// sd (s, s') and, on request, n_out (caller order).
+template <class M>
+__global__ void __launch_bounds__(SC_TPB) k_tcount_e(int n, Geom g, const typename M::pos_t* __restrict__ pos,
+                                                     SuperCaps cp, GroupAux aux, const uint16_t* __restrict__ nbr,
+                                                     const int* __restrict__ nnb, const int* __restrict__ id,
+                                                     TypedDev t, double2* __restrict__ sd, double* __restrict__ n_out,
+                                                     const Status* st)
+{
+    if (halted(st)) return;
+    for (int p = warp_id_global(); p < n; p += warps_total()) {
+        const auto pi = pos[p];
+        const int ti = t.tsort[p];
+        double acc = 0.0;
+        typed_row(p, aux, cp, nbr, nnb, [&](int j) {
+            const int k = ti * t.T + t.tsort[j];
+            if (!t.mask[k]) return;
+            const Coef& c = t.pc[k];
+            const double r2 = r2_d<M>(pi, pos[j], g);
+            if (r2 < c.rh2) acc += r2 <= c.rl2 ? 1.0 : omega_d(sqrt(r2), c.r_l, c.r_h);
+        });
+        acc = group_sum(acc, 32);
+        const Coef& own = t.pc[ti * t.T + ti];
+        if ((threadIdx.x & 31) == 0) {
+            sd[p] = make_double2(omega_d(acc, own.fd, own.fd + 1.0), domega_d(acc, own.fd, own.fd + 1.0));
+            if (n_out) n_out[id[p]] = acc;
+        }
+    }
+}
+
+// FP64 (s_i, A_i) of every particle into sa, from sd.
+template <class M>
+__global__ void __launch_bounds__(SC_TPB) k_tchain_e(int n, Geom g, const typename M::pos_t* __restrict__ pos,
+                                                     SuperCaps cp, GroupAux aux, const uint16_t* __restrict__ nbr,
+                                                     const int* __restrict__ nnb, TypedDev t,
+                                                     const double2* __restrict__ sd, double2* __restrict__ sa,
+                                                     const Status* st)
+{
+    if (halted(st)) return;
+    for (int p = warp_id_global(); p < n; p += warps_total()) {
+        const double2 sdi = sd[p];
+        double acc = 0.0;
+        if (sdi.y != 0.0) {  // uniform over the warp
+            const auto pi = pos[p];
+            const int ti = t.tsort[p];
+            typed_row(p, aux, cp, nbr, nnb, [&](int j) {
+                const Coef& c = t.pc[ti * t.T + t.tsort[j]];
+                const double r2 = r2_d<M>(pi, pos[j], g);
+                if (r2 > c.rr2 && r2 < c.ra2) acc += sd[j].x * Va_d(sqrt(r2), c);
+            });
+            acc = group_sum(acc, 32);
+        }
+        if ((threadIdx.x & 31) == 0) sa[p] = make_double2(sdi.x, sdi.y * acc);
+    }
+}
+
 // U and W: half of every pair and bond from each end, one partial sum per
 // block (the grid has nb blocks, nb <= the partial arrays' length), then
 // k_reduce_final.  Pairs with r < r_c of their types are counted from each end.
-__global__ void __launch_bounds__(SC_TPB) k_tenergy(int n, Geom g, const P64* __restrict__ pos, SuperCaps cp,
-                                                    GroupAux aux, const uint16_t* __restrict__ nbr,
+// sA holds FP64 (s_i, A_i).
+template <class M>
+__global__ void __launch_bounds__(SC_TPB) k_tenergy(int n, Geom g, const typename M::pos_t* __restrict__ pos,
+                                                    SuperCaps cp, GroupAux aux, const uint16_t* __restrict__ nbr,
                                                     const int* __restrict__ nnb, const int* __restrict__ id,
                                                     TypedDev t, const double2* __restrict__ sA,
                                                     double* __restrict__ partial, long long* __restrict__ ppairs,
@@ -200,14 +389,14 @@ __global__ void __launch_bounds__(SC_TPB) k_tenergy(int n, Geom g, const P64* __
     long long np = 0;
     if (!halted(st)) {
         for (int p = warp_id_global(); p < n; p += warps_total()) {
-            const P64 pi = pos[p];
+            const auto pi = pos[p];
             const int ti = t.tsort[p];
             const double2 sai = sA[p];
             double ep = 0.0, wp = 0.0;
             long long npp = 0;
             typed_row(p, aux, cp, nbr, nnb, [&](int j) {
-                const P64 pj = pos[j];
-                const double r2 = r2_d<ModeF64>(pi, pj, g);
+                const auto pj = pos[j];
+                const double r2 = r2_d<M>(pi, pj, g);
                 const int tj = t.tsort[j];
                 const Coef& c = t.pc[ti * t.T + tj];
                 if (r2 >= c.rc2) return;
@@ -220,7 +409,7 @@ __global__ void __launch_bounds__(SC_TPB) k_tenergy(int n, Geom g, const P64* __
             if ((threadIdx.x & 31) == 0) {
                 typed_bonds(p, id, t, [&](int q) {
                     double dx, dy, dz;
-                    ModeF64::delta64(pi, pos[q], g, dx, dy, dz);
+                    M::delta64(pi, pos[q], g, dx, dy, dz);
                     const double r = sqrt(dx * dx + dy * dy + dz * dz), u = r - t.r0;
                     ep += 0.5 * (0.5 * t.kb * u * u);
                     wp += 0.5 * (-t.kb * u * r);

@@ -273,8 +273,8 @@ class System:
 
     @classmethod
     def typed(cls, pos, box, types, pair, count_mask, bonds=None, k_bond: float = 0.0, r0_bond: float = 1.0,
-              vel=None, skin: float = 0.4, seed: int = 1, nlist_cap: int = 0):
-        """A multi-type system (vbc_create_typed_system; FP64): types [n] in [0, T),
+              vel=None, skin: float = 0.4, seed: int = 1, nlist_cap: int = 0, precision: int = VBC_FP64):
+        """A multi-type system (vbc_create_typed_system; FP64 or FP32 split): types [n] in [0, T),
         pair a T x T nested list of PairParams (symmetric; a type's f and delta from
         its diagonal entry), count_mask T x T of 0/1 (row type counts column type),
         bonds [m, 2] particle indices with energy k_bond/2 (r - r0_bond)^2.  Host
@@ -291,7 +291,7 @@ class System:
         b = np.broadcast_to(np.asarray(box, dtype=np.float64), (3,))
         cfg = _Config(n=n, box=(ctypes.c_double * 3)(*b), pos=ctypes.c_void_p(pos.ctypes.data),
                       vel=ctypes.c_void_p(vel.ctypes.data) if vel is not None else None, params=params(),
-                      skin=skin, seed=seed, precision=VBC_FP64, nlist_cap=nlist_cap, stream=None,
+                      skin=skin, seed=seed, precision=precision, nlist_cap=nlist_cap, stream=None,
                       inputs_on_device=0)
         ty = _Types(ntypes=T, type=ctypes.c_void_p(t.ctypes.data), pair=ctypes.cast(tab, ctypes.c_void_p),
                     count_mask=ctypes.c_void_p(m.ctypes.data), nbonds=bd.shape[0],
@@ -303,7 +303,7 @@ class System:
         self._h = h
         self.n = n
         self.box = b.copy()
-        self.precision = VBC_FP64
+        self.precision = precision
         return self
 
     # -- lifetime

@@ -121,7 +121,7 @@ def _typed(n=100, T=2, types=None, pair=None, mask=None, bonds=None, k_bond=100.
 
 
 @pytest.mark.parametrize("kw,needle", [
-    (dict(prec=vbc.VBC_FP32_SPLIT), "VBC_FP64"),
+    (dict(prec=7), "precision"),
     (dict(T=0), "ntypes"),
     (dict(types=np.full(100, 2)), "type of particle"),
     (dict(types=np.full(100, -1)), "type of particle"),

@@ -1,9 +1,13 @@
 """GPU parity of multi-type systems with a count mask and harmonic bonds (the
 counter restricted to chosen neighbour types, Sec. 2; the sticker chains of
-Sec. 4) against the oracle's typed evaluation, element by element.  FP64 path,
-so the FP64 tolerances of the single-type parity tests apply:
-  counts <= 1e-6 absolute (they come out near 1e-13), s and s' <= 1e-12,
-  A_i <= 1e-10 max|A|, forces <= 1e-10 rms|F|, U <= 1e-9 and W <= 1e-9 relative."""
+Sec. 4) against the oracle's typed evaluation, element by element, in both
+precisions, with the tolerances of the single-type parity tests:
+  counts  <= 1e-6 absolute (both)
+  s, s'   <= 1e-12 (FP64), 1e-6 and 4e-6 (FP32 split)
+  A_i     <= 1e-10 max|A| (FP64), 1e-5 max|A| (FP32 split)
+  forces  <= 1e-10 rms|F| (FP64), 1e-5 rms|F| (FP32 split)
+  U       <= 1e-9 relative (both; FP64 energies in both)
+  W       <= 1e-9 relative (FP64), 1e-6 (FP32 split: positions on the 32-bit word grid)"""
 from __future__ import annotations
 
 import numpy as np
@@ -46,55 +50,79 @@ def _mixed(n_chains=300, beads=12, rho=0.45, seed=31):
     return pos, L, t, P, mask, bonds
 
 
-def _create(pos, L, t, P, mask, bonds, k_b, r_0, vel=None, seed=1):
+F32, F64 = vbc.VBC_FP32_SPLIT, vbc.VBC_FP64
+TOL = {F64: dict(s=1e-12, A=1e-10, F=1e-10, W=1e-9), F32: dict(s=1e-6, A=1e-5, F=1e-5, W=1e-6)}
+
+
+def _create(pos, L, t, P, mask, bonds, k_b, r_0, vel=None, seed=1, prec=F64):
     VP = [[_vp(x) for x in row] for row in P]
-    return vbc.System.typed(pos, L, t, VP, mask, bonds=bonds, k_bond=k_b, r0_bond=r_0, vel=vel, seed=seed)
+    return vbc.System.typed(pos, L, t, VP, mask, bonds=bonds, k_bond=k_b, r0_bond=r_0, vel=vel, seed=seed,
+                            precision=prec)
 
 
-def _check(s, pos, L, t, P, mask, bonds, k_b, r_0, min_window=0):
+def _check(s, pos, L, t, P, mask, bonds, k_b, r_0, min_window=0, prec=F64):
+    tol = TOL[prec]
     ref = oracle.evaluate_typed(pos, L, t, P, mask, bonds=bonds, k_b=k_b, r_0=r_0, mode=1)
     r = s.compute(F=True, counts=True, energy=True, virial=True)
     sw, dsw, A = s.switch()
     assert np.max(np.abs(r.counts - ref.counts)) <= 1e-6
     rms = np.sqrt(np.mean(np.sum(ref.F ** 2, axis=1)))
-    assert np.max(np.abs(r.F - ref.F)) <= 1e-10 * rms
-    assert np.max(np.abs(sw - ref.s)) <= 1e-12
-    assert np.max(np.abs(dsw - ref.ds)) <= 4e-12
-    assert np.max(np.abs(A - ref.A)) <= 1e-10 * max(np.max(np.abs(ref.A)), 1e-12)
+    assert np.max(np.abs(r.F - ref.F)) <= tol["F"] * rms
+    assert np.max(np.abs(sw - ref.s)) <= tol["s"]
+    assert np.max(np.abs(dsw - ref.ds)) <= 4 * tol["s"]
+    assert np.max(np.abs(A - ref.A)) <= tol["A"] * max(np.max(np.abs(ref.A)), 1e-12)
     assert abs(r.energy - ref.U) <= 1e-9 * abs(ref.U)
-    assert abs(r.virial - ref.W) <= 1e-9 * abs(ref.W)
+    assert abs(r.virial - ref.W) <= tol["W"] * abs(ref.W)
     assert np.sum(ref.ds != 0.0) >= min_window
     return ref
 
 
-def test_sticker_chains_against_oracle():
+@pytest.mark.parametrize("prec", [F64, F32])
+def test_sticker_chains_against_oracle(prec):
     """Chains of 16 beads at bead density 0.3 with stickers every fourth bead."""
     pos, L, t, bonds = inputs.sticker_chains(1500, 16, 0.3, seed=5)
     P, mask = _sticker_model(f_sticker=1.0)
-    with _create(pos, L, t, P, mask, bonds, 100.0, 1.0) as s:
-        ref = _check(s, pos, L, t, P, mask, bonds, 100.0, 1.0)
+    with _create(pos, L, t, P, mask, bonds, 100.0, 1.0, prec=prec) as s:
+        ref = _check(s, pos, L, t, P, mask, bonds, 100.0, 1.0, prec=prec)
     # spacers count nothing, so they all sit at s = 1
     assert np.all(ref.counts[t == 0] == 0.0)
 
 
-def test_three_types_asymmetric_mask_against_oracle():
+@pytest.mark.parametrize("prec", [F64, F32])
+def test_three_types_asymmetric_mask_against_oracle(prec):
     pos, L, t, P, mask, bonds = _mixed()
-    with _create(pos, L, t, P, mask, bonds, 100.0, 1.0) as s:
-        _check(s, pos, L, t, P, mask, bonds, 100.0, 1.0, min_window=200)
+    with _create(pos, L, t, P, mask, bonds, 100.0, 1.0, prec=prec) as s:
+        _check(s, pos, L, t, P, mask, bonds, 100.0, 1.0, min_window=200, prec=prec)
 
 
-def test_after_steps_and_rebuilds():
+@pytest.mark.parametrize("prec", [F64, F32])
+def test_after_steps_and_rebuilds(prec):
     """After Langevin steps with list rebuilds (the sorted order, the type map and
     the bond partners' sorted indices all change), forces at the new state still
     match the oracle at those positions."""
     pos, L, t, P, mask, bonds = _mixed(seed=32)
     vel = inputs.maxwell_velocities(pos.shape[0], 1.0, seed=9)
-    with _create(pos, L, t, P, mask, bonds, 100.0, 1.0, vel=vel) as s:
+    with _create(pos, L, t, P, mask, bonds, 100.0, 1.0, vel=vel, prec=prec) as s:
         r0 = s.stats().rebuilds
         s.step(300, 0.005, 1.0, 1.0)
         assert s.stats().rebuilds > r0 + 1
         x, _, _ = s.get_state()
-        _check(s, x, L, t, P, mask, bonds, 100.0, 1.0)
+        _check(s, x, L, t, P, mask, bonds, 100.0, 1.0, prec=prec)
+
+
+def test_fp32_split_sticker_trajectory_stays_near_fp64():
+    """The FP32-split typed path and the FP64 one, from the same state and noise,
+    stay within a small distance over 50 steps (the one-step maps differ by
+    rounding only)."""
+    pos, L, t, bonds = inputs.sticker_chains(400, 16, 0.3, seed=7)
+    vel = inputs.maxwell_velocities(pos.shape[0], 1.0, seed=8)
+    P, mask = _sticker_model(f_sticker=1.0)
+    out = []
+    for prec in (F64, F32):
+        with _create(pos, L, t, P, mask, bonds, 100.0, 1.0, vel=vel, seed=3, prec=prec) as s:
+            s.step(50, 0.005, 1.0, 1.0)
+            out.append(s.get_state()[0])
+    assert np.max(np.abs(out[0] - out[1])) < 1e-4
 
 
 def test_one_type_matches_single_type_system():
