@@ -261,8 +261,10 @@ def reference_main(args):
 # ------------------------------------------------------------------ B300 arm
 def profile_run(args):
     """A few launches of every kernel on the bench workload, for a profiler: the
-    state after args.equil steps (cached between runs), one forced list build, one
-    force evaluation and 6 steps."""
+    state after args.equil steps (cached between runs), one forced list build
+    (NVTX range "build"), one force evaluation and 6 steps (NVTX range "steps"),
+    so that a capture can select one kernel inside one range."""
+    import torch
     from paper_2609_07842_b300 import inputs, vbc
     prm = vbc.params(E_a=args.E_a, f=args.valency)
     cache = f"/tmp/vbc_bench_state_n{args.n}_rho{args.rho}_v{args.valency:g}_e{args.equil}.npz"
@@ -275,9 +277,13 @@ def profile_run(args):
         np.savez(cache, pos=p, vel=v, L=L)
     d = np.load(cache)
     with vbc.System(d["pos"], float(d["L"]), prm, vel=d["vel"], skin=SKIN, seed=SEED) as s:
+        torch.cuda.nvtx.range_push("build")
         s.build_neighbors()
+        torch.cuda.nvtx.range_pop()
         s.compute(F=np.zeros((args.n, 3)))
+        torch.cuda.nvtx.range_push("steps")
         s.step(6, DT, KT, GAMMA)
+        torch.cuda.nvtx.range_pop()
         st = s.stats()
     print(f"profile run: n={args.n} list mean {st.nlist_mean:.2f} unsaturated {st.unsaturated}", file=sys.stderr)
     return 0
