@@ -314,6 +314,7 @@ int make_coef(const vbc_pair_params& p, const Geom& g, Coef& c)
     c.rc2_fix = (unsigned long long)std::llround(c.rc2 / s2);
     c.s2hinv = (float)(s2 / c.h);
     c.s2winv = (float)(s2 / c.w);
+    c.rl2_fixf = (float)c.rl2_fix;
     {
         const double rl_s = p.r_l / g.s32d[0], w_s = c.w / g.s32d[0];
         c.rl_s.hi = (float)rl_s;

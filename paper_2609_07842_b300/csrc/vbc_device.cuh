@@ -57,6 +57,7 @@ struct Coef {
     unsigned long long rr2_fix, rl2_fix, rh2_fix, ra2_fix, rm2_fix, rc2_fix;
     float s2hinv;   // s^2 / h: u = (r^2 - r_m^2) / ((r + r_m) h) from an integer difference
     float s2winv;   // s^2 / w: t = (r^2 - r_l^2) / ((r + r_l) w)
+    float rl2_fixf; // rl2_fix as a float (the chain-rule term of the FP32 force)
     f2x rl_s, w_s;                    // r_l / s and (r_h - r_l) / s as two floats, s = L / 2^32
     const uint4* wtab;                // window weights as cubic pieces in r^2 (window_weight_tab), or null
     int wsh;                          // log2 of the r^2 extent of one piece (fixed-point units)

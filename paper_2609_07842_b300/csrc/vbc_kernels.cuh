@@ -1084,10 +1084,14 @@ __device__ __forceinline__ void pair_f32(const int4& pi, float si, float Ai, con
     const bool chain = r2i > c.rl2_fix && r2i < c.rh2_fix && Ai + Aj != 0.0f;
     if (!(core || well || chain)) return;
     const float dx = (float)ix * g.s32, dy = (float)iy * g.s32, dz = (float)iz * g.s32;
+    // the exact r^2 as one float (0.5 ulp): every term below starts from it, except the
+    // well's r - r_m, which takes the exact integer difference (near the well's centre the
+    // force is most sensitive to it)
+    const float R = u64_to_float(r2i);
+    const float r2 = R * g.s32sq;
     float gr = 0.0f;  // g / r
-    if (core) gr = c.Er4f * (u64_to_float(r2i) * g.s32sq * c.rr2invf - 1.0f);
+    if (core) gr = c.Er4f * (r2 * c.rr2invf - 1.0f);
     if (well || chain) {
-        const float r2 = u64_to_float(r2i) * g.s32sq;
         float rinv = rsqrtf(r2);
         rinv = rinv * __fmaf_rn(-0.5f * r2 * rinv, rinv, 1.5f);  // one Newton step
         const float r = r2 * rinv;
@@ -1097,7 +1101,8 @@ __device__ __forceinline__ void pair_f32(const int4& pi, float si, float Ai, con
             gt = si * sj * c.Ea4hf * u * (1.0f - u * u);
         }
         if (chain) {
-            const float tt = __fdividef(u64_to_float(r2i - c.rl2_fix) * c.s2winv, r + c.rlf);
+            // (r - r_l) / w from r^2 - r_l^2 in fixed-point units (R and r_l^2 each within 0.5 ulp)
+            const float tt = __fdividef((R - c.rl2_fixf) * c.s2winv, r + c.rlf);
             gt -= (Ai + Aj) * 4.0f * tt * (1.0f - tt * tt) * c.winvf;
         }
         gr += gt * rinv;

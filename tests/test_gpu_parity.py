@@ -171,8 +171,13 @@ def test_orthorhombic_box_fp64():
 
 # ----------------------------------------------------------------- neighbour list
 @pytest.mark.parametrize("prec", [F32, F64])
-def test_neighbour_list_is_exact(prec):
-    pos, L = inputs.uniform_positions(3000, 0.5, seed=10)
+@pytest.mark.parametrize("n,rho", [(3000, 0.5), (30000, 0.5), (20000, 0.25)])
+def test_neighbour_list_is_exact(prec, n, rho):
+    """The list holds every pair closer than r_c + skin and none beyond.  3000
+    particles give 7 cells per edge (the build on fixed-point words); the larger
+    systems have 8 or more (the build on block-relative floats, which skips
+    whole neighbour cells beyond the list radius)."""
+    pos, L = inputs.uniform_positions(n, rho, seed=10)
     rlist = 2.0 + 0.4
     with vbc.System(pos, L, vbc.params(), precision=prec, skin=0.4) as s:
         nnb, nbr = s.neighbors(cap=256)
@@ -189,12 +194,13 @@ def test_neighbour_list_is_exact(prec):
     sure = pairs[r < rlist - 1e-6]
     for i, j in sure:
         assert (i, j) in got and (j, i) in got
-    # nothing beyond the radius (up to the fixed-point resolution)
+    # nothing beyond the radius: up to the fixed-point resolution, and for the block-relative
+    # float build up to its relative margin of 1e-5 (a few extra entries, never a missing one)
     gi = np.array([a for a, _ in got])
     gj = np.array([b for _, b in got])
     dd = pos[gi] - pos[gj]
     dd -= L * np.round(dd / L)
-    assert np.sqrt((dd * dd).sum(1)).max() < rlist + 1e-6
+    assert np.sqrt((dd * dd).sum(1)).max() < rlist * (1.0 + 1.1e-5) + 1e-6
     assert len(got) >= 2 * len(sure)
 
 
