@@ -134,6 +134,7 @@ struct vbc_system {
     uint16_t* close_k = nullptr;  // [n][CLOSE_K] close entries as staging indices (count, soft-core force)
     void* fcore = nullptr;      // [n] forces and tags, float4 or F64x4 (k_count_near, k_force_rows -> k_step)
     int* glist = nullptr;       // [n] particles whose force k_force_rows forms
+    int* resid = nullptr;       // [n] packed residual bits of the positions (FP32 mode; counts of window pairs)
     int sms = 148;              // SMs of the device
     int row_grid = 1;           // blocks of the row walks (count rows, chain-rule pass, force rows)
     int near_grid = 1;          // blocks of k_count_near
@@ -478,7 +479,7 @@ void free_all(vbc_system* s)
     dfree(s->nbr); dfree(s->scratch); dfree(s->nnb); dfree(s->cell_of); dfree(s->slot_of); dfree(s->order);
     dfree(s->cell_count); dfree(s->cell_start); dfree(s->morton_rank); dfree(s->sc_org);
     dfree(s->chunk_sum); dfree(s->wpart); dfree(s->ulist); dfree(s->stage_idx); dfree(s->gmeta); dfree(s->roff_g);
-    dfree(s->close_k); dfree(s->fcore); dfree(s->glist);
+    dfree(s->close_k); dfree(s->fcore); dfree(s->glist); dfree(s->resid);
     dfree(s->ds); dfree(s->sA); dfree(s->st); dfree(s->partial); dfree(s->ppairs); dfree(s->red);
     dfree(s->win); dfree(s->e_sd); dfree(s->e_A); dfree(s->wtab); dfree(s->obs); dfree(s->zbuf);
     dfree(s->t_part); dfree(s->t_wpart); dfree(s->t_out);
@@ -595,7 +596,7 @@ int enqueue_rebuild(vbc_system* s)
     k_permute<M><<<nb, TPB, 0, s->stream>>>(n, s->order, s->x, s->v, s->id, pos, s->xt, s->vt, s->idt,
                                             (pos_t*)s->post, s->st);
     k_copyback<M><<<nb, TPB, 0, s->stream>>>(n, s->xt, s->vt, s->idt, (const pos_t*)s->post, s->x, s->v, s->id,
-                                             pos, (pos_t*)s->xref, s->st);
+                                             pos, (pos_t*)s->xref, s->resid, s->st);
     if (s->typed) {
         k_tmaps<<<nb, TPB, 0, s->stream>>>(n, s->id, s->tdev);
         VBC_TRY(check_launch(s));
@@ -640,8 +641,7 @@ int enqueue_typed_count_chain(vbc_system* s, double* n_out, bool want_window)
         {
             Timed t(s, VBC_K_COUNT);
             k_tcount32<<<gb, SC_TPB, 0, s->stream>>>(n, s->geom, pos, s->caps(), s->aux(), s->nbr, s->nnb, s->id,
-                                                     s->tdev, (const long long*)s->x, (float*)s->ds, (float2*)s->sA,
-                                                     out, s->st);
+                                                     s->tdev, s->resid, (float*)s->ds, (float2*)s->sA, out, s->st);
         }
         {
             Timed t(s, VBC_K_CHAIN);
@@ -672,7 +672,7 @@ RowArgs<M> row_args(const vbc_system* s, const CountOut& out, int cur = -1)
     A.out = out;
     A.ulist = s->ulist;
     A.wpart = s->wpart;
-    A.X = (const long long*)s->x;
+    A.resid = s->resid;
     A.st = s->st;
     return A;
 }
@@ -862,6 +862,7 @@ long long device_bytes_of(long long n, int prec, const Sizes& z)
     b += (long long)s->nsc * s->smax * 4;                 // stage_idx
     b += (long long)s->nsc * (8 + 16 + 8);                // gmeta, partial, ppairs
     b += (long long)CLOSE_K * n * 2;                      // close_k
+    b += n * 4;                                           // resid
     b += n * (prec == VBC_FP64 ? 32 : 16);                // fcore
     b += 3 * n * rb;                                      // ds, sA
     b += n * (8 + 16);                                    // e_sd, e_A
@@ -1285,6 +1286,7 @@ StepArgs step_args(const vbc_system* s, double dt, double kT, double gamma)
     split_fix(a.c1, a.c1_hi, a.c1_lo);
     a.seed = s->seed;
     a.half_skin2 = (float)(0.25 * s->skin * s->skin);
+    a.resid = s->resid;
     return a;
 }
 
@@ -1400,7 +1402,7 @@ int load_state(vbc_system* s, const double* pos, const double* vel, int on_devic
     k_load_state<M><<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>((int)s->n, s->geom, (const double*)s->xt,
                                                                   vel ? (const double*)s->vt : nullptr, s->id,
                                                                   s->x, s->v, (typename M::pos_t*)s->pos[s->cur],
-                                                                  s->st);
+                                                                  s->resid, s->st);
     return check_launch(s);
 }
 
@@ -1494,6 +1496,7 @@ SysDesc<M> make_desc(const vbc_system* s, const StepArgs& a)
     d.scratch = s->scratch;
     d.nbr = s->nbr;
     d.nnb = s->nnb;
+    d.resid = s->resid;
     return d;
 }
 
@@ -1724,6 +1727,7 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     ALLOC(dalloc(s->close_k, (size_t)CLOSE_K * n));
     ALLOC(dalloc_bytes(s->fcore, n * (s->prec == VBC_FP64 ? sizeof(F64x4) : sizeof(float4))));
     ALLOC(dalloc(s->glist, n));
+    ALLOC(dalloc(s->resid, n));
     ALLOC(dalloc_bytes(s->ds, n * s->real_bytes()));
     ALLOC(dalloc_bytes(s->sA, n * 2 * s->real_bytes()));
     ALLOC(dalloc(s->st, 1));

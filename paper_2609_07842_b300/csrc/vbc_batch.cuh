@@ -48,6 +48,7 @@ struct SysDesc {
     uint16_t* scratch;
     uint16_t* nbr;
     int* nnb;
+    int* resid;
 };
 
 // Offsets of each system's items in the batch-wide numbering (K + 1 entries
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(SC_TPB, BATCH_MIN_BLOCKS) k_batch_iter(const S
             const SysDesc<M>& d = D[k];
             if (rebuild_on(d.A[0].st))
                 copyback_item<M>(i - opart[k], d.A[0].n, d.xt, d.vt, d.idt, d.post, d.x, d.v, d.idw, d.A[flip].pos,
-                                 d.xref);
+                                 d.xref, d.resid);
         }
         if (!grid_wait(ctl, gen)) return;
         for (int w = blockIdx.x; w < ogroup[K]; w += gridDim.x) {

@@ -182,6 +182,31 @@ __global__ void __launch_bounds__(TPB) k_scatter(int n, const int* __restrict__ 
     order[cell_start[cell_of[i]] + slot_of[i]] = i;
 }
 
+// Window pairs of the FP32-split counts are measured finer than the 32-bit
+// words.  A count error dn moves s'_i by s''_i dn, and A_i = s'_i sum_j s_j V_a
+// multiplies that by the well sum, so a window particle of large A_i turns
+// the ~1e-7 count error of the 32-bit position grid (L / 2^32 per axis) into
+// a force error of order 1e-5 rms|F|.  The 64-bit state carries 20 more bits
+// below each word; the top ten of them (P - word(P) 2^20, in [-2^19, 2^19),
+// floored to a multiple of 2^10) are packed three to an int and added to the
+// separation of window pairs only, which puts the count error near 1e-10.
+// The packed ints sit in an array of their own beside the words, written
+// wherever the state is (load, update, the rebuild's copy-back), so that a
+// count reads one int per neighbour rather than three state words.
+__device__ __forceinline__ int resid10(long long P)
+{
+    return (int)(((P + (1ll << 19)) & ((1ll << 20) - 1)) - (1ll << 19)) >> 10;
+}
+// Packed residuals of one particle from its coordinates (units L / 2^52).
+__device__ __forceinline__ int pack_resid3(long long P0, long long P1, long long P2)
+{
+    return (resid10(P0) & 1023) | (resid10(P1) & 1023) << 10 | (resid10(P2) & 1023) << 20;
+}
+// Field k (0, 1, 2) of a packed residual, sign-extended.
+__device__ __forceinline__ long long resid_field(int r, int k)
+{
+    return (long long)((int)((unsigned)r << (22 - 10 * k)) >> 22);
+}
 // Within each cell, order particles by their index in the previous sorted
 // order, so that the layout (and every summation order) is a function of the
 // previous layout and the positions only, not of atomic scheduling.  Cells of
@@ -254,13 +279,16 @@ __device__ __forceinline__ void copyback_item(int k, int n, const unsigned long 
                                               const typename M::pos_t* __restrict__ post,
                                               unsigned long long* __restrict__ x, unsigned long long* __restrict__ v,
                                               int* __restrict__ id, typename M::pos_t* __restrict__ pos,
-                                              typename M::pos_t* __restrict__ xref)
+                                              typename M::pos_t* __restrict__ xref, int* __restrict__ resid)
 {
+    unsigned long long xs[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        x[(size_t)a * n + k] = xt[(size_t)a * n + k];
+        xs[a] = xt[(size_t)a * n + k];
+        x[(size_t)a * n + k] = xs[a];
         v[(size_t)a * n + k] = vt[(size_t)a * n + k];
     }
+    if constexpr (!M::fp64) resid[k] = pack_resid3((long long)xs[0], (long long)xs[1], (long long)xs[2]);
     id[k] = idt[k];
     const typename M::pos_t p = post[k];
     pos[k] = p;
@@ -289,11 +317,12 @@ __global__ void __launch_bounds__(TPB) k_copyback(int n, const unsigned long lon
                                                   const typename M::pos_t* __restrict__ post,
                                                   unsigned long long* __restrict__ x, unsigned long long* __restrict__ v,
                                                   int* __restrict__ id, typename M::pos_t* __restrict__ pos,
-                                                  typename M::pos_t* __restrict__ xref, const Status* st)
+                                                  typename M::pos_t* __restrict__ xref, int* __restrict__ resid,
+                                                  const Status* st)
 {
     if (!rebuild_on(st)) return;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) copyback_item<M>(k, n, xt, vt, idt, post, x, v, id, pos, xref);
+    if (k < n) copyback_item<M>(k, n, xt, vt, idt, post, x, v, id, pos, xref, resid);
 }
 
 
@@ -925,6 +954,7 @@ struct StepArgs {
     unsigned long long c1_hi, c1_lo;        // c1 as integer part and 2^-64 fraction
     unsigned long long seed;
     float half_skin2;     // (skin / 2)^2
+    int* resid;           // [n] packed residuals of the new positions (FP32 mode)
 };
 
 // State of one particle for its BAOAB update, loaded before the force loop
@@ -995,6 +1025,7 @@ __device__ __forceinline__ void integrate(int i, int n, const Geom& g, typename 
             xi[2] = z.z;
         }
         int w[3] = {0, 0, 0};
+        int rp = 0;  // packed residuals of the new position
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             long long v = ps.V[d];
@@ -1008,12 +1039,14 @@ __device__ __forceinline__ void integrate(int i, int n, const Geom& g, typename 
                 P += mul_fix(v, a.dk_hi[d], a.dk_lo[d]);                           // A
                 X[(size_t)d * n + i] = P;
                 w[d] = ModeF32::word(P);
+                rp |= (resid10(P) & 1023) << (10 * d);
             }
             V[(size_t)d * n + i] = v;
         }
         if constexpr (start) {
             const int4 pn = make_int4(w[0], w[1], w[2], 0);
             pos_next[i] = pn;
+            a.resid[i] = rp;
             const float ux = (float)(pn.x - ps.xr.x) * g.s32, uy = (float)(pn.y - ps.xr.y) * g.s32,
                         uz = (float)(pn.z - ps.xr.z) * g.s32;
             if (ux * ux + uy * uy + uz * uz > a.half_skin2) st->rebuild = 1;
@@ -1177,29 +1210,6 @@ __device__ __forceinline__ unsigned long long r2_fix(const int4& a, const int4& 
            (unsigned long long)((long long)dz * dz);
 }
 
-// Window pairs of the FP32-split counts are measured finer than the 32-bit
-// words.  A count error dn moves s'_i by s''_i dn, and A_i = s'_i sum_j s_j V_a
-// multiplies that by the well sum, so a window particle of large A_i turns
-// the ~1e-7 count error of the 32-bit position grid (L / 2^32 per axis) into
-// a force error of order 1e-5 rms|F|.  The 64-bit state carries 20 more bits
-// below each word; the top ten of them (P - word(P) 2^20, in [-2^19, 2^19),
-// floored to a multiple of 2^10) are packed three to an int and added to the
-// separation of window pairs only, which puts the count error near 1e-10.
-__device__ __forceinline__ int resid10(long long P)
-{
-    return (int)(((P + (1ll << 19)) & ((1ll << 20) - 1)) - (1ll << 19)) >> 10;
-}
-// Packed residuals of sorted particle j from the state X ([3][n], units L / 2^52).
-__device__ __forceinline__ int pack_resid(const long long* __restrict__ X, size_t n, int j)
-{
-    return (resid10(__ldg(X + j)) & 1023) | (resid10(__ldg(X + n + j)) & 1023) << 10 |
-           (resid10(__ldg(X + 2 * n + j)) & 1023) << 20;
-}
-// Field k (0, 1, 2) of a packed residual, sign-extended.
-__device__ __forceinline__ long long resid_field(int r, int k)
-{
-    return (long long)((int)((unsigned)r << (22 - 10 * k)) >> 22);
-}
 // r^2 of a window pair in units of (L / 2^32)^2 with the residuals ra, rb
 // added: with d the word difference and e the residual difference (units of
 // 2^-10 word), (d + e / 2^10)^2 = d^2 + 2 d e / 2^10 + e^2 / 2^20 per axis.
@@ -1544,7 +1554,7 @@ struct RowArgs {
     CountOut out;
     int* ulist;
     int* wpart;
-    const long long* X;  // the state [3][n] (the FP32 mode's residual bits)
+    const int* resid;    // [n] packed residuals of the positions (FP32 mode)
     Status* st;
 };
 
@@ -1558,7 +1568,7 @@ __device__ __forceinline__ int resid_of(const RowArgs<M>& A, int j)
         A.st->bad_index = 1;
         return 0;
     }
-    return pack_resid(A.X, (size_t)A.n, j);
+    return __ldg(A.resid + j);
 }
 
 // Sparse count: list entry k of the particles k_count_near could not settle
@@ -2239,7 +2249,8 @@ template <class M>
 __global__ void __launch_bounds__(TPB) k_load_state(int n, Geom g, const double* __restrict__ pos_in,
                                                     const double* __restrict__ vel_in, const int* __restrict__ id,
                                                     void* __restrict__ xs, void* __restrict__ vs,
-                                                    typename M::pos_t* __restrict__ pos, Status* st)
+                                                    typename M::pos_t* __restrict__ pos, int* __restrict__ resid,
+                                                    Status* st)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -2258,6 +2269,7 @@ __global__ void __launch_bounds__(TPB) k_load_state(int n, Geom g, const double*
         pos[i] = ModeF64::from_x(xx[0], xx[1], xx[2], g);
     } else {
         int w[3];
+        long long Ps[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const double xf = pos_in[3 * (size_t)o + d] * g.inv32[d] * 1048576.0;  // x 2^52 / L
@@ -2265,10 +2277,12 @@ __global__ void __launch_bounds__(TPB) k_load_state(int n, Geom g, const double*
             bad |= !(fabs(xf) < 4611686018427387904.0) || !(fabs(vf) < 4611686018427387904.0);  // 2^62
             const long long P = bad ? 0ll : __double2ll_rn(xf);
             ((long long*)xs)[(size_t)d * n + i] = P;
+            Ps[d] = P;
             w[d] = ModeF32::word(P);
             ((long long*)vs)[(size_t)d * n + i] = bad ? 0ll : __double2ll_rn(vf);
         }
         pos[i] = make_int4(w[0], w[1], w[2], 0);
+        resid[i] = pack_resid3(Ps[0], Ps[1], Ps[2]);
     }
     if (bad) st->bad_input = 1;
 }

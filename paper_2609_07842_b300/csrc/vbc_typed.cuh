@@ -192,11 +192,11 @@ __global__ void __launch_bounds__(SC_TPB) k_tforce(int n, Geom g, const P64* __r
 // ---------------------------------------------------------------- FP32-split walks
 // Counts over the masked neighbour types in fixed point (the single-type
 // split's arithmetic with the pair's own coefficients); s_i and s'_i from the
-// particle's own type.  X is the state [3][n] (residual bits of window pairs).
+// particle's own type.  resid holds the packed residual bits of the positions (window pairs).
 __global__ void __launch_bounds__(SC_TPB) k_tcount32(int n, Geom g, int4* __restrict__ pos, SuperCaps cp,
                                                      GroupAux aux, const uint16_t* __restrict__ nbr,
                                                      const int* __restrict__ nnb, const int* __restrict__ id,
-                                                     TypedDev t, const long long* __restrict__ X,
+                                                     TypedDev t, const int* __restrict__ resid,
                                                      float* __restrict__ ds_out, float2* __restrict__ sA,
                                                      CountOut out, Status* st)
 {
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(SC_TPB) k_tcount32(int n, Geom g, int4* __rest
     if (halted(st)) return;
     for (int p = warp_id_global(); p < n; p += warps_total()) {
         const int4 pi = pos[p];
-        const int ri = pack_resid(X, (size_t)n, p);
+        const int ri = __ldg(resid + p);
         const int ti = t.tsort[p];
         int full = 0;
         unsigned long long q = 0;
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(SC_TPB) k_tcount32(int n, Geom g, int4* __rest
             }
             // omega has zero slope at both ends of the window: a pair the finer separation
             // moves across r_l or r_h changes n_i by O(dr^2)
-            const unsigned long long rf = r2_fine(pi, ri, pj, pack_resid(X, (size_t)n, j), r2);
+            const unsigned long long rf = r2_fine(pi, ri, pj, __ldg(resid + j), r2);
             if (rf <= c.rl2_fix) q += 2147483648ull;
             else if (rf < c.rh2_fix) q += window_weight_fix31(rf, rf - c.rl2_fix, c.rl_s, c.w_s);
         });
