@@ -205,7 +205,14 @@ int vbc_step_langevin(vbc_system* sys, int64_t nsteps, double dt, double kT, dou
 
 /* Checkpoint: copy out unwrapped positions, velocities and the step counter
  * (any pointer may be NULL).  Restoring them with vbc_set_state resumes the
- * same trajectory bit for bit. */
+ * trajectory, the same one to rounding: sums follow the sorted layout the
+ * system holds at the time.  vbc_set_state keeps the neighbour list when
+ * every loaded position lies within skin / 2 of the position at the last
+ * build (as the step loop does), and has it rebuilt by the next pass
+ * otherwise, or when the system was halted.  A load clears every halt,
+ * including the one a batched step that gave up (TIMEOUT) leaves.  Errors:
+ * UNSTABLE for a non-finite or out-of-range value (the system then stays
+ * halted until a good state is loaded). */
 int vbc_get_state(vbc_system* sys, double* pos, double* vel, int64_t* step, int on_device);
 int vbc_set_state(vbc_system* sys, const double* pos, const double* vel, int64_t step,
                   int on_device);

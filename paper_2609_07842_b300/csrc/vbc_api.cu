@@ -262,15 +262,17 @@ __global__ void k_set_flag(Status* st, int which, int value)
 
 __global__ void k_abort(Status* st) { st->aborted = 1; }
 
+// Clears every halt; a system that was halted rebuilds its list before the next pass.
 __global__ void k_clear_halt(Status* st)
 {
+    if (halted(st) | st->bad_index) st->rebuild = 1;
     st->overflow = 0;
     st->stage_overflow = 0;
     st->frozen = 0;
     st->crowded = 0;
     st->bad_input = 0;
     st->aborted = 0;
-    st->rebuild = 1;
+    st->bad_index = 0;
 }
 
 // ------------------------------------------------------------------ parameters
@@ -1402,7 +1404,8 @@ int load_state(vbc_system* s, const double* pos, const double* vel, int on_devic
     k_load_state<M><<<blocks_for(s->n, TPB), TPB, 0, s->stream>>>((int)s->n, s->geom, (const double*)s->xt,
                                                                   vel ? (const double*)s->vt : nullptr, s->id,
                                                                   s->x, s->v, (typename M::pos_t*)s->pos[s->cur],
-                                                                  s->resid, s->st);
+                                                                  s->resid, (const typename M::pos_t*)s->xref,
+                                                                  (float)(0.25 * s->skin * s->skin), s->st);
     return check_launch(s);
 }
 
@@ -2036,8 +2039,10 @@ int vbc_set_state(vbc_system* s, const double* pos, const double* vel, int64_t s
     VBC_TRY(s->prec == VBC_FP64 ? load_state<ModeF64>(s, pos, vel, on_device)
                                 : load_state<ModeF32>(s, pos, vel, on_device));
     s->step = step;
-    VBC_TRY(s->prec == VBC_FP64 ? build_now<ModeF64>(s) : build_now<ModeF32>(s));
-    return VBC_OK;
+    // the list is rebuilt by the next pass only if the load requested it (a particle farther than
+    // skin / 2 from its position at the last build, or a system that was halted)
+    VBC_TRY(read_status(s));
+    return halt_error(s);
 }
 
 int vbc_set_params(vbc_system* s, const vbc_pair_params* p)

@@ -2250,12 +2250,14 @@ __global__ void __launch_bounds__(TPB) k_load_state(int n, Geom g, const double*
                                                     const double* __restrict__ vel_in, const int* __restrict__ id,
                                                     void* __restrict__ xs, void* __restrict__ vs,
                                                     typename M::pos_t* __restrict__ pos, int* __restrict__ resid,
+                                                    const typename M::pos_t* __restrict__ xref, float half_skin2,
                                                     Status* st)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int o = id[i];
     bool bad = false;
+    float d2 = 0.0f;  // squared distance from the position at the last list build
     if constexpr (M::fp64) {
         double xx[3];
 #pragma unroll
@@ -2266,7 +2268,14 @@ __global__ void __launch_bounds__(TPB) k_load_state(int n, Geom g, const double*
             ((double*)xs)[(size_t)d * n + i] = xx[d];
             ((double*)vs)[(size_t)d * n + i] = v;
         }
-        pos[i] = ModeF64::from_x(xx[0], xx[1], xx[2], g);
+        const P64 pn = ModeF64::from_x(xx[0], xx[1], xx[2], g);
+        pos[i] = pn;
+        const P64 pr = xref[i];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float u = (float)(int)(ModeF64::hi32(pn, d) - ModeF64::hi32(pr, d)) * (float)g.s32d[d];
+            d2 += u * u;
+        }
     } else {
         int w[3];
         long long Ps[3];
@@ -2283,8 +2292,14 @@ __global__ void __launch_bounds__(TPB) k_load_state(int n, Geom g, const double*
         }
         pos[i] = make_int4(w[0], w[1], w[2], 0);
         resid[i] = pack_resid3(Ps[0], Ps[1], Ps[2]);
+        const int4 pr = xref[i];
+        const float ux = (float)(w[0] - pr.x) * g.s32, uy = (float)(w[1] - pr.y) * g.s32,
+                    uz = (float)(w[2] - pr.z) * g.s32;
+        d2 = ux * ux + uy * uy + uz * uz;
     }
     if (bad) st->bad_input = 1;
+    // the list stays valid while every particle is within skin / 2 of its position at the build
+    if (bad || !(d2 <= half_skin2)) st->rebuild = 1;
 }
 
 template <class M>

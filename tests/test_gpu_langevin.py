@@ -207,3 +207,43 @@ def test_graph_and_direct_launches_agree_bitwise(prec):
             st = s.stats()
     assert st.rebuilds - r0 >= 3
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("prec", [F32, F64])
+def test_set_state_keeps_a_valid_list(prec):
+    """Loading a system's own state back keeps its neighbour list (no particle
+    moved): in FP64 the run then continues bit for bit as if it had not been
+    interrupted; in the FP32 split the double positions of the interface
+    round the 2^-52 L fixed point by up to one unit, so the run continues to
+    within 1e-9 (30 steps).  A load that moves a particle farther than
+    skin / 2 from its position at the last build has the next pass rebuild
+    the list, and one that moves none does not."""
+    pos, vel, L, p = _system(3000, 0.5, seed=9)
+    outs = []
+    for interrupt in (False, True):
+        with vbc.System(pos, L, _vp(p), vel=vel, seed=4, precision=prec) as s:
+            s.step(30, 0.005, 1.0, 1.0)
+            if interrupt:
+                x, v, st = s.get_state()
+                s.set_state(x, v, step=st)
+            s.step(30, 0.005, 1.0, 1.0)
+            outs.append(s.get_state())
+    assert outs[0][2] == outs[1][2] == 60
+    if prec == F64:
+        assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    else:
+        assert np.max(np.abs(outs[0][0] - outs[1][0])) <= 1e-9
+        assert np.max(np.abs(outs[0][1] - outs[1][1])) <= 1e-7
+    skin = 0.4  # the default
+    with vbc.System(pos, L, _vp(p), vel=vel, seed=4, precision=prec) as s:
+        s.step(10, 0.005, 1.0, 1.0)
+        x, v, st = s.get_state()
+        r0 = s.stats().rebuilds
+        s.set_state(x, v, step=st)
+        s.compute(F=True)
+        assert s.stats().rebuilds == r0
+        x2 = x.copy()
+        x2[17, 0] += 0.6 * skin
+        s.set_state(x2, v, step=st)
+        s.compute(F=True)
+        assert s.stats().rebuilds == r0 + 1
