@@ -750,8 +750,7 @@ def measure(args, valency, rank, world, local, barrier, stream, with_clocks=True
                                "rebuilds": rebuilds_direct},
         "rebuilds": rebuilds, "nlist_mean": k_mean, "in_window_fraction": phi,
         "steps_per_rebuild": rebuild_every, "unsaturated_fraction": st2.unsaturated / args.n,
-        "capacities": {"stage": st2.stage_cap, "group": st2.group_cap, "segment": st2.segment_cap,
-                       "list": st2.nlist_cap, "groups": st2.groups,
+        "capacities": {"stage": st2.stage_cap, "group": st2.group_cap, "list": st2.nlist_cap, "groups": st2.groups,
                        "grows_in_timed_region": st1.capacity_grows - st0.capacity_grows},
         "thermo": {"energy_per_particle": th.U / args.n, "virial_per_particle": th.W / args.n,
                    "kinetic_temperature": 2.0 * th.KE / (3.0 * args.n), "mean_count": th.mean_n,

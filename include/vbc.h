@@ -103,7 +103,6 @@ typedef struct {
                                   ceil(f - delta + 1) of their kept near neighbours within r_l */
     int32_t stage_cap;         /* staged particles per cell group (current capacity) */
     int32_t group_cap;         /* particles per cell group (current capacity) */
-    int32_t segment_cap;       /* list entries per cell group (current capacity) */
     int32_t groups;            /* cell groups (units of the list build and of the dense row walks) */
     int64_t capacity_grows;    /* capacity growths after an overflow since creation (each resumes the
                                   interrupted call from the overflowing build) */

@@ -4,8 +4,8 @@
 // all work on one CUDA stream.  The host never waits for the device inside a
 // run of steps: neighbour-list rebuilds are decided on the device, and the
 // host reads the status words once, when the call ends.  If a rebuild found a
-// list longer than its capacity, or a cell group whose neighbourhood or list
-// segment does not fit its capacity, every later kernel of the call stopped without
+// list longer than its capacity, or a cell group whose neighbourhood does not
+// fit its capacity, every later kernel of the call stopped without
 // touching the state; the host then grows the capacity and resumes from the
 // iteration that stopped, so the trajectory is the same as with large enough
 // capacities from the start.
@@ -78,7 +78,7 @@ uint32_t float_bits(float f)
 struct Sizes {
     int nc[3] = {0, 0, 0}, pc[3] = {0, 0, 0};  // real and padded cells per edge
     int ncell = 0, npad = 0, nsc = 0;
-    int cap = 0, smax = 0, omax = 0, seg = 0;
+    int cap = 0, smax = 0, omax = 0;
 };
 
 }  // namespace
@@ -101,7 +101,6 @@ struct vbc_system {
     int cap = 0;       // list capacity per particle (multiple of 8)
     int smax = 0;      // staging capacity in particles per cell group
     int omax = 0;      // particles per cell group
-    int seg = 0;       // list entries per cell group (multiple of 64)
     int npad = 0;      // cells of the padded grid
     int nsc = 0;       // cell groups (npad / OWN_CELLS)
     bool rel_lists = false;  // list build on block-relative float positions
@@ -121,7 +120,6 @@ struct vbc_system {
     void *post = nullptr, *xref = nullptr;
     int cur = 0;
     uint16_t* nbr = nullptr;
-    uint16_t* scratch = nullptr;  // [n][cap] rows of the list build
     int* nnb = nullptr;
     int *cell_of = nullptr, *slot_of = nullptr, *order = nullptr;
     int *cell_count = nullptr, *cell_start = nullptr, *morton_rank = nullptr, *sc_org = nullptr;
@@ -130,7 +128,7 @@ struct vbc_system {
     int* ulist = nullptr;       // [n] particles the count walks in full (k_count_near -> k_count_rows)
     int* stage_idx = nullptr;   // [nsc][smax] sorted index of each staged particle (list build)
     int2* gmeta = nullptr;      // [nsc] staged particles and padded list entries per group
-    int* roff_g = nullptr;      // [n] row offset of each particle in its group's segment
+    int* grp = nullptr;         // [n] cell group of each particle (its row's staging)
     uint16_t* close_k = nullptr;  // [n][CLOSE_K] close entries as staging indices (count, soft-core force)
     void* fcore = nullptr;      // [n] forces and tags, float4 or F64x4 (k_count_near, k_force_rows -> k_step)
     int* glist = nullptr;       // [n] particles whose force k_force_rows forms
@@ -191,11 +189,11 @@ struct vbc_system {
     size_t pos_bytes() const { return prec == VBC_FP64 ? sizeof(P64) : sizeof(int4); }
     size_t real_bytes() const { return prec == VBC_FP64 ? sizeof(double) : sizeof(float); }
     SuperGrid grid() const { return SuperGrid{morton_rank, sc_org, cell_start}; }
-    SuperCaps caps() const { return SuperCaps{smax, omax, seg, cap}; }
-    GroupAux aux() const { return GroupAux{stage_idx, gmeta, roff_g, close_k, fcore, glist}; }
+    SuperCaps caps() const { return SuperCaps{smax, omax, cap}; }
+    GroupAux aux() const { return GroupAux{stage_idx, gmeta, grp, close_k, fcore, glist}; }
     // dynamic shared memory of each kernel family
-    size_t smem_nlist() const { return nlist_layout(caps(), pos_bytes()).total; }
-    size_t smem_nlist_rel() const { return nlist_layout(caps(), sizeof(float4)).total; }
+    size_t smem_nlist() const { return nlist_smem(caps(), pos_bytes()); }
+    size_t smem_nlist_rel() const { return nlist_smem(caps(), sizeof(float4)); }
     size_t smem_energy() const { return pass_layout(caps(), pos_bytes(), sizeof(double2)).total; }
     size_t smem_store() const { return al16((size_t)(omax + 1) * 4); }
     size_t smem_rows(size_t extra) const { return dense_layout(caps(), pos_bytes(), extra).total; }
@@ -478,9 +476,9 @@ void free_all(vbc_system* s)
     dfree(s->t_pc); dfree(s->t_mask); dfree(s->t_type); dfree(s->t_tsort); dfree(s->t_inv); dfree(s->t_bptr);
     dfree(s->t_bto); dfree(s->t_esa);
     dfree(s->pos[0]); dfree(s->pos[1]); dfree(s->post); dfree(s->xref);
-    dfree(s->nbr); dfree(s->scratch); dfree(s->nnb); dfree(s->cell_of); dfree(s->slot_of); dfree(s->order);
+    dfree(s->nbr); dfree(s->nnb); dfree(s->cell_of); dfree(s->slot_of); dfree(s->order);
     dfree(s->cell_count); dfree(s->cell_start); dfree(s->morton_rank); dfree(s->sc_org);
-    dfree(s->chunk_sum); dfree(s->wpart); dfree(s->ulist); dfree(s->stage_idx); dfree(s->gmeta); dfree(s->roff_g);
+    dfree(s->chunk_sum); dfree(s->wpart); dfree(s->ulist); dfree(s->stage_idx); dfree(s->gmeta); dfree(s->grp);
     dfree(s->close_k); dfree(s->fcore); dfree(s->glist); dfree(s->resid);
     dfree(s->ds); dfree(s->sA); dfree(s->st); dfree(s->partial); dfree(s->ppairs); dfree(s->red);
     dfree(s->win); dfree(s->e_sd); dfree(s->e_A); dfree(s->wtab); dfree(s->obs); dfree(s->zbuf);
@@ -539,9 +537,9 @@ int configure_smem(vbc_system* s)
 {
     if (s->smem_nlist() > MAX_SMEM || s->smem_energy() > MAX_SMEM)
         return fail(VBC_ERR_UNSTABLE,
-                    "a cell group's neighbourhood (%d staged, %d own particles, %d list entries) does not fit in "
+                    "a cell group's neighbourhood (%d staged, %d own particles) does not fit in "
                     "shared memory: the system is too dense",
-                    s->smax, s->omax, s->seg);
+                    s->smax, s->omax);
     if (s->smem_nlist_rel() > MAX_SMEM) return fail(VBC_ERR_UNSTABLE, "list build staging too large");
     VBC_TRY(set_smem(k_nlist<M, false>, s->smem_nlist()));
     if constexpr (!M::fp64) VBC_TRY(set_smem(k_nlist<M, true>, s->smem_nlist_rel()));
@@ -606,12 +604,12 @@ int enqueue_rebuild(vbc_system* s)
     if constexpr (!M::fp64) {
         if (s->rel_lists) {
             k_nlist<M, true><<<s->nsc, SC_TPB, s->smem_nlist_rel(), s->stream>>>(
-                s->geom, pos, s->grid(), s->caps(), s->lp, s->scratch, s->nbr, s->nnb, s->aux(), s->st);
+                s->geom, pos, s->grid(), s->caps(), s->lp, s->nbr, s->nnb, s->aux(), s->st);
             return check_launch(s, REBUILD_KERNELS);
         }
     }
     k_nlist<M, false><<<s->nsc, SC_TPB, s->smem_nlist(), s->stream>>>(s->geom, pos, s->grid(), s->caps(), s->lp,
-                                                                       s->scratch, s->nbr, s->nnb, s->aux(), s->st);
+                                                                       s->nbr, s->nnb, s->aux(), s->st);
     return check_launch(s, REBUILD_KERNELS);
 }
 
@@ -838,8 +836,6 @@ int plan_sizes(const vbc_config* cfg, Sizes& z)
     const double rho_cell = (double)cfg->n / z.ncell;
     z.smax = std::min((((int)std::ceil(1.5 * SCELLS * rho_cell) + 64) + 63) / 64 * 64, MAX_STAGE);
     z.omax = std::min(((int)std::ceil(2.0 * OWN_CELLS * rho_cell) + 32 + 31) / 32 * 32, MAX_OWN);
-    const double entries = OWN_CELLS * rho_cell * (std::min(kbar, (double)z.cap) + 4.0);
-    z.seg = (int)std::min(((long long)std::ceil(1.5 * entries) + 256 + 63) / 64 * 64, 1LL << 24);
     return VBC_OK;
 }
 
@@ -849,16 +845,15 @@ long long device_bytes_of(long long n, int prec, const Sizes& z)
 {
     const long long pb = prec == VBC_FP64 ? (long long)sizeof(P64) : 16, rb = prec == VBC_FP64 ? 8 : 4;
     struct {
-        int seg, nsc, cap, npad, ncell, smax;
-    } sz{z.seg, z.nsc, z.cap, z.npad, z.ncell, z.smax};
+        int nsc, cap, npad, ncell, smax;
+    } sz{z.nsc, z.cap, z.npad, z.ncell, z.smax};
     const auto* s = &sz;
     long long b = 0;
     b += 4 * 3 * n * 8;                                   // x, v, xt, vt
     b += 2 * n * 4;                                       // id, idt
     b += 4 * n * pb;                                      // pos[2], post, xref
-    b += (long long)s->seg * s->nsc * 2;                  // nbr
-    b += (long long)s->cap * n * 2;                       // scratch
-    b += 8 * n * 4;                                       // nnb, cell_of, slot_of, order, wpart, ulist, roff_g, glist
+    b += (long long)s->cap * n * 2;                       // nbr (a row slot of cap entries per particle)
+    b += 8 * n * 4;                                       // nnb, cell_of, slot_of, order, wpart, ulist, grp, glist
     b += ((long long)s->npad * 2 + 1 + s->ncell + s->nsc) * 4;  // cell tables
     b += (long long)blocks_for(s->npad, SCAN_CHUNK) * 4;
     b += (long long)s->nsc * s->smax * 4;                 // stage_idx
@@ -874,7 +869,6 @@ long long device_bytes_of(long long n, int prec, const Sizes& z)
 long long device_bytes(const vbc_system* s)
 {
     Sizes z{};
-    z.seg = s->seg;
     z.nsc = s->nsc;
     z.cap = s->cap;
     z.npad = s->npad;
@@ -905,8 +899,8 @@ int grow(vbc_system* s)
                         need, MAX_CAP);
         int cap = std::max(s->cap + s->cap / 2, need + need / 4 + 8);
         cap = std::min((cap + 7) & ~7, MAX_CAP);
-        dfree(s->scratch);
-        VBC_TRY(dalloc(s->scratch, (size_t)cap * (size_t)s->n));
+        dfree(s->nbr);
+        VBC_TRY(dalloc(s->nbr, (size_t)cap * (size_t)s->n));
         s->cap = cap;
     }
     if (h.stage_overflow) {
@@ -925,12 +919,6 @@ int grow(vbc_system* s)
                 return fail(VBC_ERR_UNSTABLE, "a cell group holds %d particles, above the limit %d", h.max_own,
                             MAX_OWN);
             s->omax = omax;
-        }
-        if (h.max_seg > s->seg) {
-            const int seg = ((h.max_seg + h.max_seg / 4 + 63) / 64) * 64;
-            dfree(s->nbr);
-            VBC_TRY(dalloc(s->nbr, (size_t)seg * (size_t)s->nsc));
-            s->seg = seg;
         }
     }
     VBC_TRY(configure(s));
@@ -1436,17 +1424,12 @@ int trim_capacities(vbc_system* s)
     const Status& h = *s->st_host;
     const int smax = std::min(s->smax, std::max((h.max_stage + h.max_stage / 8 + 32 + 63) / 64 * 64, 64));
     const int omax = std::min(s->omax, std::max((h.max_own + h.max_own / 4 + 8 + 31) / 32 * 32, 32));
-    const int seg = std::min(s->seg, std::max((h.max_seg + h.max_seg / 4 + 64 + 63) / 64 * 64, 64));
     const int cap = std::min(s->cap, std::max((h.max_nnb + h.max_nnb / 4 + 8 + 7) & ~7, 8));
-    if (smax == s->smax && omax == s->omax && seg == s->seg && cap == s->cap) return VBC_OK;
+    if (smax == s->smax && omax == s->omax && cap == s->cap) return VBC_OK;
     VBC_CUDA(cudaStreamSynchronize(s->stream));
-    if (seg != s->seg) {
-        dfree(s->nbr);
-        VBC_TRY(dalloc(s->nbr, (size_t)seg * (size_t)s->nsc));
-    }
     if (cap != s->cap) {
-        dfree(s->scratch);
-        VBC_TRY(dalloc(s->scratch, (size_t)cap * (size_t)s->n));
+        dfree(s->nbr);
+        VBC_TRY(dalloc(s->nbr, (size_t)cap * (size_t)s->n));
     }
     if (smax != s->smax) {
         dfree(s->stage_idx);
@@ -1454,7 +1437,6 @@ int trim_capacities(vbc_system* s)
     }
     s->smax = smax;
     s->omax = omax;
-    s->seg = seg;
     s->cap = cap;
     VBC_TRY(configure(s));
     s->layout_version += 1;
@@ -1496,7 +1478,6 @@ SysDesc<M> make_desc(const vbc_system* s, const StepArgs& a)
     d.idt = s->idt;
     d.post = (pos_t*)s->post;
     d.xref = (pos_t*)s->xref;
-    d.scratch = s->scratch;
     d.nbr = s->nbr;
     d.nnb = s->nnb;
     d.resid = s->resid;
@@ -1677,7 +1658,6 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     s->cap = z.cap;
     s->smax = z.smax;
     s->omax = z.omax;
-    s->seg = z.seg;
 
     {
         cudaError_t e = cudaGetDevice(&s->device);
@@ -1711,8 +1691,7 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     ALLOC(dalloc_bytes(s->pos[1], n * s->pos_bytes()));
     ALLOC(dalloc_bytes(s->post, n * s->pos_bytes()));
     ALLOC(dalloc_bytes(s->xref, n * s->pos_bytes()));
-    ALLOC(dalloc(s->nbr, (size_t)s->seg * (size_t)s->nsc));
-    ALLOC(dalloc(s->scratch, (size_t)s->cap * n));
+    ALLOC(dalloc(s->nbr, (size_t)s->cap * n));
     ALLOC(dalloc(s->nnb, n));
     ALLOC(dalloc(s->cell_of, n));
     ALLOC(dalloc(s->slot_of, n));
@@ -1726,7 +1705,7 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
     ALLOC(dalloc(s->ulist, n));
     ALLOC(dalloc(s->stage_idx, (size_t)s->nsc * s->smax));
     ALLOC(dalloc(s->gmeta, (size_t)s->nsc));
-    ALLOC(dalloc(s->roff_g, n));
+    ALLOC(dalloc(s->grp, n));
     ALLOC(dalloc(s->close_k, (size_t)CLOSE_K * n));
     ALLOC(dalloc_bytes(s->fcore, n * (s->prec == VBC_FP64 ? sizeof(F64x4) : sizeof(float4))));
     ALLOC(dalloc(s->glist, n));
@@ -2114,7 +2093,6 @@ int vbc_get_stats(vbc_system* s, vbc_stats* out)
     out->unsaturated = s->st_host->nu;
     out->stage_cap = s->smax;
     out->group_cap = s->omax;
-    out->segment_cap = s->seg;
     out->groups = s->nsc;
     out->capacity_grows = s->grows;
     out->device_bytes = device_bytes(s);

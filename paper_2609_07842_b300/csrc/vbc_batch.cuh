@@ -45,7 +45,6 @@ struct SysDesc {
     int *idw, *idt;
     typename M::pos_t* post;
     typename M::pos_t* xref;
-    uint16_t* scratch;
     uint16_t* nbr;
     int* nnb;
     int* resid;
@@ -234,13 +233,12 @@ __global__ void __launch_bounds__(SC_TPB, BATCH_MIN_BLOCKS) k_batch_iter(const S
             const RowArgs<M>& A = d.A[flip];
             if constexpr (!M::fp64) {
                 if (d.rel) {
-                    nlist_group<M, true>(w - ogroup[k], A.g, A.pos, A.G, A.cp, d.lp, d.scratch, d.nbr, d.nnb, A.aux,
-                                         A.st, smem);
+                    nlist_group<M, true>(w - ogroup[k], A.g, A.pos, A.G, A.cp, d.lp, d.nbr, d.nnb, A.aux, A.st,
+                                         smem);
                     continue;
                 }
             }
-            nlist_group<M, false>(w - ogroup[k], A.g, A.pos, A.G, A.cp, d.lp, d.scratch, d.nbr, d.nnb, A.aux, A.st,
-                                  smem);
+            nlist_group<M, false>(w - ogroup[k], A.g, A.pos, A.G, A.cp, d.lp, d.nbr, d.nnb, A.aux, A.st, smem);
         }
         if (!grid_wait(ctl, gen)) return;
     }

@@ -78,8 +78,7 @@ struct Status {
     int max_nnb;        // longest list found at the last build (uncapped)
     int frozen_iter;    // loop iteration at which the overflow happened
     int max_own;        // largest number of particles of one supercell (last build)
-    int stage_overflow; // 1: a supercell exceeded a staging or list-segment capacity (k_nlist)
-    int max_seg;        // largest list segment (entries) of one supercell (last build)
+    int stage_overflow; // 1: a supercell exceeded its staging or own-particle capacity (k_nlist)
     long long nnb_sum;  // sum of list lengths at the last build
     long long rebuilds; // builds so far
     long long in_window;// particles inside the switching window at the last count

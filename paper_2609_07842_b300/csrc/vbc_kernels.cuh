@@ -54,7 +54,6 @@ __device__ __forceinline__ void bin_item(int i, const typename M::pos_t* __restr
         st->nnb_sum = 0;
         st->max_stage = 0;
         st->max_own = 0;
-        st->max_seg = 0;
     }
     const int3 c = cell_of_pos<M>(pos[i], g);
     const int key = morton_rank[(c.z * g.nc[1] + c.y) * g.nc[0] + c.x];
@@ -359,8 +358,7 @@ struct SuperGrid {
 struct SuperCaps {
     int smax;  // staged particles
     int omax;  // own particles (multiple of 32)
-    int seg;   // list entries of one block (multiple of 64)
-    int cap;   // list entries of one particle (multiple of 8)
+    int cap;   // list entries of one particle: the stride of the row slots (multiple of 8)
 };
 
 // Tables the list build leaves for the passes.
@@ -368,8 +366,8 @@ constexpr int CLOSE_K = 12;          // close entries kept per particle, as stag
 constexpr int CLOSE_NONE = 0xffff;   // an empty close-list slot
 struct GroupAux {
     int* stage_idx;  // [groups][smax] sorted index of each staged particle
-    int2* meta;      // [groups] (staged particles, padded list entries)
-    int* roff;       // [n] start of each particle's row in nbr (group * seg + offset in its segment)
+    int2* meta;      // [groups] (staged particles, own particles)
+    int* grp;        // [n] cell group of each particle (whose staging its row's entries index)
     uint16_t* close; // [n][CLOSE_K] staging indices of close entries (near, then far within r_l), CLOSE_NONE for none
     void* fcore;     // [n] force and tag, float4 (FP32 mode) or F64x4 (w = 1: the particle's whole force)
     int* glist;      // [n] particles whose force the list-walking pass forms (k_count_near, k_chain)
@@ -381,27 +379,6 @@ struct SuperTab {
     int own[OWN_CELLS + 1];       // cell_start of the block's ranks
     int sw[SC_TPB / 32];          // scan scratch
 };
-
-// Exclusive scan of a[0..n) in shared memory, in place, with a[n] = total.
-// Called by the whole block once a[] is written.
-__device__ __forceinline__ int scan_in_place(int* a, int n, int* sw)
-{
-    __syncthreads();
-    const int per = (n + SC_TPB - 1) / SC_TPB;
-    const int b = min(n, (int)threadIdx.x * per), e = min(n, b + per);
-    int s = 0;
-    for (int k = b; k < e; ++k) s += a[k];
-    int total;
-    int off = block_exclusive_scan<SC_TPB>(s, sw, total);
-    for (int k = b; k < e; ++k) {
-        const int v = a[k];
-        a[k] = off;
-        off += v;
-    }
-    if (threadIdx.x == 0) a[n] = total;
-    __syncthreads();
-    return total;
-}
 
 // Reads the staging table of block s (whole block).  Returns the first own
 // particle p0, the number of own particles and of staged particles.
@@ -497,22 +474,13 @@ __device__ __forceinline__ int own_staged_cell(int b)
 }
 
 // ---------------------------------------------------------------- lists
-// The lists of block s occupy nbr[s * seg ...]: the rows of its own
-// particles in sorted order, each padded to a multiple of 4 entries.  A row
-// holds the near entries (closer than r_r + skin at the build) first,
-// then the far ones (up to r_c + skin); pads repeat the particle's own
-// staging index, which adds exactly nothing to a force (d = 0).
-// nnb[p] = near | far << 16.
+// The row of sorted particle p occupies the fixed slot nbr[p * cap ...]: its
+// entries (staging indices of its cell group, grp[p]) in candidate order,
+// padded to a multiple of 4 with the particle's own staging index, which adds
+// exactly nothing to a force (d = 0).  nnb[p] = near | far << 16, near the
+// entries closer than r_r + skin at the build, far the others up to r_c + skin.
 __device__ __forceinline__ int pad4(int v) { return (v + 3) & ~3; }
 __device__ __forceinline__ int row_len(int w) { return (w & 0xffff) + (w >> 16); }
-
-// Row offsets of the own particles (entries from the segment start) in
-// roff[0 .. n_own], computed by the whole block; returns the padded total.
-__device__ __forceinline__ int own_rows(const int* __restrict__ nnb, int p0, int n_own, int* roff, int* sw)
-{
-    for (int j = threadIdx.x; j < n_own; j += SC_TPB) roff[j] = pad4(row_len(__ldg(nnb + p0 + j)));
-    return scan_in_place(roff, n_own, sw);
-}
 
 // The 4 entries of one 8-byte chunk.
 __device__ __forceinline__ void unpack4(const uint2 v, int h[4])
@@ -573,50 +541,21 @@ struct ListTestRel {
 // pieces; the host sizes its launches with the same functions.
 __host__ __device__ constexpr size_t al16(size_t v) { return (v + 15) & ~(size_t)15; }
 
-struct NlistLayout {
-    size_t roff, rnn, rself, total;
-};
-__host__ __device__ inline NlistLayout nlist_layout(const SuperCaps& cp, size_t pos_bytes)
+// The list build: the staged positions.
+__host__ __device__ inline size_t nlist_smem(const SuperCaps& cp, size_t pos_bytes)
 {
-    NlistLayout l{};
-    l.roff = al16((size_t)cp.smax * pos_bytes);
-    l.rnn = l.roff + al16((size_t)(cp.omax + 1) * 4);
-    l.rself = l.rnn + al16((size_t)cp.omax * 4);
-    l.total = l.rself + al16((size_t)cp.omax * 4);
-    return l;
+    return al16((size_t)cp.smax * pos_bytes);
 }
 
-// k_count, k_chain, the energy kernels: staged positions, an optional staged
-// value per particle, row offsets and a particle list.
+// The energy kernels: staged positions and an optional staged value per particle.
 struct PassLayout {
-    size_t val, roff, plist, total;
+    size_t val, total;
 };
 __host__ __device__ inline PassLayout pass_layout(const SuperCaps& cp, size_t pos_bytes, size_t val_bytes)
 {
     PassLayout l{};
     l.val = al16((size_t)cp.smax * pos_bytes);
-    l.roff = l.val + al16((size_t)cp.smax * val_bytes);
-    l.plist = l.roff + al16((size_t)(cp.omax + 1) * 4);
-    l.total = l.plist + al16((size_t)cp.omax * 4);
-    return l;
-}
-
-// k_force: staged positions (with s_j in the spare word) and A_j, the first
-// chunk of each own row and of each owner's visited chunks, the staging index
-// of each own particle, and the forces of owners whose chunks one thread
-// covered completely.
-struct ForceLayout {
-    size_t sA, roff, vpre, ownm, oF, total;
-};
-__host__ __device__ inline ForceLayout force_layout(const SuperCaps& cp, size_t pos_bytes, size_t real_bytes)
-{
-    ForceLayout l{};
-    l.sA = al16((size_t)cp.smax * pos_bytes);
-    l.roff = l.sA + al16((size_t)cp.smax * real_bytes);
-    l.vpre = l.roff + al16((size_t)(cp.omax + 1) * 4);
-    l.ownm = l.vpre + al16((size_t)(cp.omax + 1) * 4);
-    l.oF = l.ownm + al16((size_t)cp.omax * 2);
-    l.total = l.oF + al16((size_t)3 * cp.omax * real_bytes);
+    l.total = l.val + al16((size_t)cp.smax * val_bytes);
     return l;
 }
 
@@ -659,17 +598,16 @@ __device__ __forceinline__ void shift192(unsigned long long& a0, unsigned long l
 #endif
 // One block per cell group: stage the surrounding cells, then each thread
 // takes own particles and scans the 9 contiguous x rows of their 27-cell
-// neighbourhood, writing a two-ended row (near from the front, far from the
-// back) into a per-particle scratch row in global memory; the rows are then
-// packed into the block's segment.
+// neighbourhood, appending the accepted candidates (in candidate order) to
+// the particle's fixed row slot nbr[p * cap ...].  The row is padded to a
+// multiple of 4 entries with the particle's own staging index.
 // The list build of cell group b (the whole block; smem is the dynamic shared
-// memory of nlist_layout).  Raises `overflow` and `stage_overflow` itself.
+// memory of nlist_smem).  Raises `overflow` and `stage_overflow` itself.
 template <class M, bool REL>
 __device__ __forceinline__ void nlist_group(int b, const Geom& g, const typename M::pos_t* __restrict__ pos,
                                             const SuperGrid& G, const SuperCaps& cp, const ListParams& lp,
-                                            uint16_t* __restrict__ scratch, uint16_t* __restrict__ nbr,
-                                            int* __restrict__ nnb, const GroupAux& aux, Status* st,
-                                            unsigned char* smem)
+                                            uint16_t* __restrict__ nbr, int* __restrict__ nnb, const GroupAux& aux,
+                                            Status* st, unsigned char* smem)
 {
     using pos_t = typename M::pos_t;
     using spos_t = typename std::conditional<REL, float4, pos_t>::type;
@@ -684,6 +622,7 @@ __device__ __forceinline__ void nlist_group(int b, const Geom& g, const typename
         atomicMax(&st->max_own, n_own);
         s_mx = 0;
         s_sum = 0;
+        aux.meta[b] = make_int2(total, n_own);
     }
     if (total > cp.smax || n_own > cp.omax) {
         if (t == 0) {
@@ -692,11 +631,7 @@ __device__ __forceinline__ void nlist_group(int b, const Geom& g, const typename
         }
         return;
     }
-    const NlistLayout ly = nlist_layout(cp, sizeof(spos_t));
     spos_t* spos = (spos_t*)smem;
-    int* roff = (int*)(smem + ly.roff);
-    int* rnn = (int*)(smem + ly.rnn);
-    int* rself = (int*)(smem + ly.rself);  // own staging index of each own particle
     int* sidx = aux.stage_idx + (size_t)b * cp.smax;  // the staged-index table the passes read
     if constexpr (REL) {
         // reference: the centre of the block's own cells (a cell boundary)
@@ -726,15 +661,15 @@ __device__ __forceinline__ void nlist_group(int b, const Geom& g, const typename
         const int kb = own_staged_cell(ob);
         const int mself = T.off[kb] + (p - T.own[ob]);
         const spos_t pi = spos[mself];
-        uint16_t* row = scratch + (size_t)p * cp.cap;
-        int nn = 0, nf = 0;
-        // close entries, as staging indices in registers until the end: the first
-        // CLOSE_K near ones (the row's first three 4-entry words) and, in scan order,
-        // up to CLOSE_K far ones within r_l (shifted in from the top of a 192-bit value)
+        uint16_t* row = nbr + (size_t)p * cp.cap;
+        int len = 0, nn = 0;
+        // close entries, as staging indices in registers until the end: up to CLOSE_K near
+        // ones and, in scan order, up to CLOSE_K far ones within r_l (each shifted in from the
+        // top of a 192-bit value)
         unsigned long long nw0 = 0ull, nw1 = 0ull, nw2 = 0ull;
         unsigned long long fw0 = 0ull, fw1 = 0ull, fw2 = 0ull;
-        int nfc = 0;
-        unsigned long long bufn = 0ull, buff = 0ull;  // up to 4 pending near / far entries
+        int nnc = 0, nfc = 0;
+        unsigned long long buf = 0ull;  // up to 4 pending entries
 #pragma unroll 1
         for (int d = 0; d < 9; ++d) {
             const int k0 = kb + (d / 3 - 1) * (SX * SY) + (d % 3 - 1) * SX - 1;
@@ -780,65 +715,57 @@ __device__ __forceinline__ void nlist_group(int b, const Geom& g, const typename
                     mnear &= sb;
                     mlist &= sb;
                 }
-                uint32_t mfar = mlist & ~mnear, mfc = mfar & mrl;
                 const int top = base + cnt - 1;  // the candidate at bit 0
-                // accepted entries go out four at a time, in candidate order (highest bit
-                // first): near ones fill 8-byte words from the front of the scratch row, far
-                // ones from the back (in reverse order)
-                while (mnear) {
-                    const int hb = 31 - __clz(mnear);
-                    mnear ^= 1u << hb;
-                    bufn = (bufn >> 16) | ((unsigned long long)(top - hb) << 48);
-                    if ((++nn & 3) == 0) {
-                        if (nn + nf <= cp.cap) *reinterpret_cast<unsigned long long*>(row + nn - 4) = bufn;
-                        nw0 = nn == 4 ? bufn : nw0;
-                        nw1 = nn == 8 ? bufn : nw1;
-                        nw2 = nn == 12 ? bufn : nw2;
-                    }
+                nn += __popc(mnear);
+                // every accepted entry, in candidate order (highest bit first), four to an
+                // 8-byte word of the row
+                uint32_t ml = mlist;
+                while (ml) {
+                    const int hb = 31 - __clz(ml);
+                    ml ^= 1u << hb;
+                    buf = (buf >> 16) | ((unsigned long long)(top - hb) << 48);
+                    if ((++len & 3) == 0 && len <= cp.cap)
+                        *reinterpret_cast<unsigned long long*>(row + len - 4) = buf;
                 }
-                while (mfar) {
-                    const int hb = 31 - __clz(mfar);
-                    mfar ^= 1u << hb;
-                    buff = (buff << 16) | (unsigned long long)(top - hb);
-                    if ((++nf & 3) == 0 && nn + nf <= cp.cap)
-                        *reinterpret_cast<unsigned long long*>(row + cp.cap - nf) = buff;
+                // close entries: the first CLOSE_K near ones, and far ones within r_l
+                uint32_t mn = mnear;
+                while (mn && nnc < CLOSE_K) {
+                    const int hb = 31 - __clz(mn);
+                    mn ^= 1u << hb;
+                    shift192(nw0, nw1, nw2, 16);
+                    nw2 |= (unsigned long long)(top - hb) << 48;
+                    ++nnc;
                 }
+                uint32_t mfc = mlist & ~mnear & mrl;
                 while (mfc && nfc < CLOSE_K) {
                     const int hb = 31 - __clz(mfc);
                     mfc ^= 1u << hb;
-                    fw0 = (fw0 >> 16) | (fw1 << 48);
-                    fw1 = (fw1 >> 16) | (fw2 << 48);
-                    fw2 = (fw2 >> 16) | ((unsigned long long)(top - hb) << 48);
+                    shift192(fw0, fw1, fw2, 16);
+                    fw2 |= (unsigned long long)(top - hb) << 48;
                     ++nfc;
                 }
             }
         }
-        if (nn + nf <= cp.cap) {
-            // the last 1..3 entries of each kind
-            for (int k = 0; k < (nn & 3); ++k)
-                row[(nn & ~3) + k] = (uint16_t)(bufn >> (16 * (4 - (nn & 3) + k)));
-            for (int k = 0; k < (nf & 3); ++k)
-                row[cp.cap - 1 - ((nf & ~3) + k)] = (uint16_t)(buff >> (16 * ((nf & 3) - 1 - k)));
-        }
-        const int len = nn + nf;
-        nnb[p] = nn | (nf << 16);
-        rnn[j] = nn | (nf << 16);
-        {
-            // up to CLOSE_K close entries as sorted indices: the near entries, then far entries
-            // within r_l at the build (for the per-particle count and soft-core force; a row
-            // with more near entries takes the list-walking force path)
-            const int kn = min(nn, min(CLOSE_K, cp.cap));
-            const int kf = min(nfc, CLOSE_K - kn);
-            if (nn < CLOSE_K) {
-                // the near word in progress: its (nn & 3) entries sit at the top of bufn
-                const unsigned long long part = (nn & 3) ? bufn >> (16 * (4 - (nn & 3))) : 0ull;
-                nw0 = (nn >> 2) == 0 ? part : nw0;
-                nw1 = (nn >> 2) == 1 ? part : nw1;
-                nw2 = (nn >> 2) == 2 ? part : nw2;
+        if (len <= cp.cap) {
+            // the last 1..3 entries and the pads (the particle's own staging index)
+            const int rem = len & 3;
+            if (rem) {
+                unsigned long long w = buf >> (16 * (4 - rem));
+                for (int k = rem; k < 4; ++k) w |= (unsigned long long)mself << (16 * k);
+                *reinterpret_cast<unsigned long long*>(row + (len & ~3)) = w;
             }
-            // far entry i sits at bit 192 - 16 nfc + 16 i; move it to slot kn + i
-            shift192(fw0, fw1, fw2, 16 * (CLOSE_K - nfc - kn));
-            // slots from kn + kf on hold CLOSE_NONE
+        }
+        nnb[p] = nn | ((len - nn) << 16);
+        aux.grp[p] = b;
+        {
+            // up to CLOSE_K close entries: the near entries, then far entries within r_l at the
+            // build (for the per-particle count and soft-core force; a row with more near entries
+            // than the list holds takes the list-walking force path).  Entry i of each kind sits at
+            // bit 192 - 16 n + 16 i of its 192-bit value.
+            const int kn = nnc;
+            const int kf = min(nfc, CLOSE_K - kn);
+            shift192(nw0, nw1, nw2, 16 * (CLOSE_K - kn));             // near entry i to slot i
+            shift192(fw0, fw1, fw2, 16 * (CLOSE_K - nfc - kn));       // far entry i to slot kn + i (past 11: out)
             const int used = 16 * (kn + kf);
             unsigned long long m0 = ~0ull, m1 = ~0ull, m2 = ~0ull;  // ones over the empty slots
             shift192(m0, m1, m2, -used);
@@ -847,8 +774,6 @@ __device__ __forceinline__ void nlist_group(int b, const Geom& g, const typename
 #pragma unroll
             for (int k = 0; k < CLOSE_K / 4; ++k) cvo[k] = make_uint2((uint32_t)w[k], (uint32_t)(w[k] >> 32));
         }
-        roff[j] = pad4(len);
-        rself[j] = mself;
         over |= len > cp.cap;
         mx = max(mx, len);
         sum += len;
@@ -873,71 +798,16 @@ __device__ __forceinline__ void nlist_group(int b, const Geom& g, const typename
             st->frozen_iter = (int)st->iter;
         }
     }
-    if (any_over) return;
-    const int tot = scan_in_place(roff, n_own, T.sw);
-    for (int j = t; j < n_own; j += SC_TPB) aux.roff[p0 + j] = (int)b * cp.seg + roff[j];
-    if (t == 0) {
-        atomicMax(&st->max_seg, tot);
-        aux.meta[b] = make_int2(total, tot);
-    }
-    if (tot > cp.seg) {
-        if (t == 0) {
-            st->stage_overflow = 1;
-            st->frozen_iter = (int)st->iter;
-        }
-        return;
-    }
-    // pack: each thread takes an equal contiguous run of the group's 4-entry chunks;
-    // chunk c belongs to the row j with roff[j] <= 4c < roff[j + 1]
-    uint2* out = reinterpret_cast<uint2*>(nbr + (size_t)b * cp.seg);
-    const int nch = tot / 4, per = (nch + SC_TPB - 1) / SC_TPB;
-    const int c0 = min(nch, t * per), c1 = min(nch, c0 + per);
-    if (c0 < c1) {
-        int j = 0;
-        {
-            int hi = n_own - 1;
-            while (j < hi) {
-                const int mid = (j + hi + 1) >> 1;
-                if (roff[mid] <= 4 * c0) j = mid;
-                else hi = mid - 1;
-            }
-        }
-        // two chunks per round, so that their eight scratch loads are in flight together
-        const auto fetch = [&](int c, int jc, uint32_t h[4]) {
-            const int w = rnn[jc], nn = w & 0xffff, len = nn + (w >> 16);
-            const uint16_t* row = scratch + (size_t)(p0 + jc) * cp.cap;
-            const uint32_t self = (uint32_t)rself[jc];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int e = 4 * c - roff[jc] + u;
-                h[u] = e < nn ? row[e] : (e < len ? row[cp.cap - 1 - (e - nn)] : self);
-            }
-        };
-        for (int c = c0; c < c1; c += 2) {
-            while (4 * c >= roff[j + 1]) ++j;
-            const bool two = c + 1 < c1;
-            int j2 = j;
-            if (two)
-                while (4 * (c + 1) >= roff[j2 + 1]) ++j2;
-            uint32_t h[4], h2[4];
-            fetch(c, j, h);
-            if (two) fetch(c + 1, j2, h2);
-            out[c] = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
-            if (two) out[c + 1] = make_uint2(h2[0] | (h2[1] << 16), h2[2] | (h2[3] << 16));
-            j = j2;
-        }
-    }
 }
 
 template <class M, bool REL>
-__global__ void __launch_bounds__(SC_TPB, NLIST_MIN_BLOCKS) k_nlist(Geom g, const typename M::pos_t* __restrict__ pos, SuperGrid G,
-                                                  SuperCaps cp, ListParams lp, uint16_t* __restrict__ scratch,
-                                                  uint16_t* __restrict__ nbr, int* __restrict__ nnb, GroupAux aux,
-                                                  Status* st)
+__global__ void __launch_bounds__(SC_TPB, NLIST_MIN_BLOCKS)
+    k_nlist(Geom g, const typename M::pos_t* __restrict__ pos, SuperGrid G, SuperCaps cp, ListParams lp,
+            uint16_t* __restrict__ nbr, int* __restrict__ nnb, GroupAux aux, Status* st)
 {
     if (!rebuild_on(st)) return;
     extern __shared__ __align__(16) unsigned char smem[];
-    nlist_group<M, REL>(blockIdx.x, g, pos, G, cp, lp, scratch, nbr, nnb, aux, st, smem);
+    nlist_group<M, REL>(blockIdx.x, g, pos, G, cp, lp, nbr, nnb, aux, st, smem);
 }
 
 // ================================================================ pass 2: forces + BAOAB
@@ -1578,9 +1448,9 @@ __device__ __forceinline__ void count_rows_item(const RowArgs<M>& A, int k)
 {
     using real = typename M::real;
     const int p = A.ulist[k];
-    const int ra = __ldg(A.aux.roff + p), b = ra / A.cp.seg;
+    const int b = __ldg(A.aux.grp + p);
     const int* sidx = A.aux.stage_idx + (size_t)b * A.cp.smax;
-    const uint16_t* row = A.nbr + ra;
+    const uint16_t* row = A.nbr + (size_t)p * A.cp.cap;
     const int len = row_len(__ldg(A.nnb + p));
     real s, ds;
     double n_val;
@@ -1616,7 +1486,7 @@ __device__ __forceinline__ void count_rows_group(const RowArgs<M>& A, int b, int
     dense_rounds<NT>(nl, tmax, [&](int u, int sub, int tpp) {
         const bool act = u < nl;
         const int p = p0 + (act ? plist[u] : 0);
-        const uint16_t* row = A.nbr + __ldg(A.aux.roff + p);
+        const uint16_t* row = A.nbr + (size_t)p * A.cp.cap;
         const int len = act ? row_len(__ldg(A.nnb + p)) : 0;
         real s, ds;
         double n_val;
@@ -1687,9 +1557,9 @@ __device__ __forceinline__ void chain_item(const RowArgs<M>& A, int k)
 {
     using real = typename M::real;
     const int p = A.wpart[k];
-    const int ra = __ldg(A.aux.roff + p), b = ra / A.cp.seg;
+    const int b = __ldg(A.aux.grp + p);
     const int* sidx = A.aux.stage_idx + (size_t)b * A.cp.smax;
-    const uint16_t* row = A.nbr + ra;
+    const uint16_t* row = A.nbr + (size_t)p * A.cp.cap;
     const int len = row_len(__ldg(A.nnb + p));
     const real acc = chain_row<M>(A.pos[p], [&](auto&& v) { walk_lanes(row, len, v); }, 32, [&](int m) {
         const int jj = __ldg(sidx + m);
@@ -1724,7 +1594,7 @@ __device__ __forceinline__ void chain_group(const RowArgs<M>& A, int b, int tmax
     dense_rounds<NT>(nl, tmax, [&](int u, int sub, int tpp) {
         const bool act = u < nl;
         const int p = p0 + (act ? plist[u] : 0);
-        const uint16_t* row = A.nbr + __ldg(A.aux.roff + p);
+        const uint16_t* row = A.nbr + (size_t)p * A.cp.cap;
         const int len = act ? row_len(__ldg(A.nnb + p)) : 0;
         const real acc = chain_row<M>(A.pos[p], [&](auto&& v) { walk_chunks(row, len, sub, tpp, v); }, tpp,
                                       [&](int m) { return spos[m]; }, A.c, A.g);
@@ -1806,9 +1676,9 @@ __device__ __forceinline__ void force_item(const RowArgs<M>& A, int k)
     using real = typename M::real;
     const bool useA = A.st->nwin > 0;  // A_j != 0 only for window particles
     const int p = A.aux.glist[k];
-    const int ra = __ldg(A.aux.roff + p), b = ra / A.cp.seg;
+    const int b = __ldg(A.aux.grp + p);
     const int* sidx = A.aux.stage_idx + (size_t)b * A.cp.smax;
-    const uint16_t* row = A.nbr + ra;
+    const uint16_t* row = A.nbr + (size_t)p * A.cp.cap;
     const int len = row_len(__ldg(A.nnb + p));
     const pos_t pi = A.pos[p];
     real f[3];
@@ -1855,7 +1725,7 @@ __device__ __forceinline__ void force_group(const RowArgs<M>& A, int b, int tmax
     dense_rounds<NT>(nl, tmax, [&](int u, int sub, int tpp) {
         const bool act = u < nl;
         const int p = p0 + (act ? plist[u] : 0);
-        const uint16_t* row = A.nbr + __ldg(A.aux.roff + p);
+        const uint16_t* row = A.nbr + (size_t)p * A.cp.cap;
         const int len = act ? row_len(__ldg(A.nnb + p)) : 0;
         const pos_t pi = A.pos[p];
         real f[3];
@@ -1945,19 +1815,16 @@ __global__ void __launch_bounds__(SC_TPB) k_count_e(Geom g, Coef c, const typena
     extern __shared__ __align__(16) unsigned char smem[];
     int p0, n_own, total;
     load_group(blockIdx.x, g, G, T, p0, n_own, total);
-    const PassLayout ly = pass_layout(cp, sizeof(pos_t), 0);
     pos_t* spos = (pos_t*)smem;
-    int* roff = (int*)(smem + ly.roff);
     stage<pos_t>(T, total, [&](int j) { return pos[j]; }, [&](int m, const pos_t& v) { spos[m] = v; });
-    own_rows(nnb, p0, n_own, roff, T.sw);
-    const uint16_t* seg = nbr + (size_t)blockIdx.x * cp.seg;
+    __syncthreads();
     for (int j = threadIdx.x; j < n_own; j += SC_TPB) {
         const int p = p0 + j;
         const int len = row_len(nnb[p]);
         const pos_t pi = pos[p];
         double acc = 0.0;
         for (int e = 0; e < len; ++e) {
-            const double r2 = r2_d<M>(pi, spos[seg[roff[j] + e]], g);
+            const double r2 = r2_d<M>(pi, spos[nbr[(size_t)p * cp.cap + e]], g);
             if (r2 < c.rh2) acc += r2 <= c.rl2 ? 1.0 : omega_d(sqrt(r2), c.r_l, c.r_h);
         }
         sd[p] = make_double2(omega_d(acc, c.fd, c.fd + 1.0), domega_d(acc, c.fd, c.fd + 1.0));
@@ -1980,7 +1847,6 @@ __global__ void __launch_bounds__(SC_TPB) k_chain_e(Geom g, Coef c, const typena
     const PassLayout ly = pass_layout(cp, sizeof(pos_t), sizeof(double));
     pos_t* spos = (pos_t*)smem;
     double* ss = (double*)(smem + ly.val);
-    int* roff = (int*)(smem + ly.roff);
     struct PS {
         pos_t p;
         double s;
@@ -1991,8 +1857,7 @@ __global__ void __launch_bounds__(SC_TPB) k_chain_e(Geom g, Coef c, const typena
             spos[m] = v.p;
             ss[m] = v.s;
         });
-    own_rows(nnb, p0, n_own, roff, T.sw);
-    const uint16_t* seg = nbr + (size_t)blockIdx.x * cp.seg;
+    __syncthreads();
     for (int j = threadIdx.x; j < n_own; j += SC_TPB) {
         const int p = p0 + j;
         const double dsi = sd[p].y;
@@ -2004,7 +1869,7 @@ __global__ void __launch_bounds__(SC_TPB) k_chain_e(Geom g, Coef c, const typena
         const pos_t pi = pos[p];
         double acc = 0.0;
         for (int e = 0; e < len; ++e) {
-            const int m = seg[roff[j] + e];
+            const int m = nbr[(size_t)p * cp.cap + e];
             const double r2 = r2_d<M>(pi, spos[m], g);
             if (r2 > c.rr2 && r2 < c.ra2) acc += ss[m] * Va_d(sqrt(r2), c);
         }
@@ -2029,7 +1894,6 @@ __global__ void __launch_bounds__(SC_TPB) k_energy(Geom g, Coef c, const typenam
     const PassLayout ly = pass_layout(cp, sizeof(pos_t), sizeof(double2));
     pos_t* spos = (pos_t*)smem;
     double2* ssa = (double2*)(smem + ly.val);  // (s_j, A_j)
-    int* roff = (int*)(smem + ly.roff);
     double e = 0.0, w = 0.0;
     long long pairs = 0;
     if (!halted(st)) {
@@ -2045,15 +1909,14 @@ __global__ void __launch_bounds__(SC_TPB) k_energy(Geom g, Coef c, const typenam
                 spos[m] = v.p;
                 ssa[m] = v.sa;
             });
-        own_rows(nnb, p0, n_own, roff, T.sw);
-        const uint16_t* seg = nbr + (size_t)blockIdx.x * cp.seg;
+        __syncthreads();
         for (int j = threadIdx.x; j < n_own; j += SC_TPB) {
             const int p = p0 + j;
             const int len = row_len(nnb[p]);
             const pos_t pi = pos[p];
             const double si = sd[p].x, Ai = Ad[p];
             for (int k = 0; k < len; ++k) {
-                const int m = seg[roff[j] + k];
+                const int m = nbr[(size_t)p * cp.cap + k];
                 const double r2 = r2_d<M>(pi, spos[m], g);
                 if (r2 >= c.rc2) continue;
                 ++pairs;
@@ -2105,13 +1968,14 @@ __global__ void __launch_bounds__(TPB) k_observe(int n, Geom g, Coef c, const ty
     __syncthreads();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p < n && !halted(st)) {
-        const int ra = __ldg(aux.roff + p), b = ra / cp.seg;
+        const int b = __ldg(aux.grp + p);
         const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
         const int len = row_len(__ldg(nnb + p));
+        const uint16_t* row = nbr + (size_t)p * cp.cap;
         const typename M::pos_t pi = pos[p];
         int z = 0;
         for (int e = 0; e < len; ++e) {
-            const typename M::pos_t pj = pos[__ldg(sidx + __ldg(nbr + ra + e))];
+            const typename M::pos_t pj = pos[__ldg(sidx + __ldg(row + e))];
             if constexpr (M::fp64) z += r2_d<M>(pi, pj, g) < c.ra2;
             else z += r2_fix(pi, pj) < c.ra2_fix;
         }
@@ -2348,12 +2212,8 @@ __global__ void __launch_bounds__(SC_TPB) k_store_nlist(Geom g, SuperGrid G, Sup
                                                         int* __restrict__ nnb_out, int* __restrict__ nbr_out)
 {
     __shared__ SuperTab T;
-    extern __shared__ __align__(16) unsigned char smem[];
-    int* roff = (int*)smem;
     int p0, n_own, total;
     load_group(blockIdx.x, g, G, T, p0, n_own, total);
-    own_rows(nnb, p0, n_own, roff, T.sw);
-    const uint16_t* seg = nbr + (size_t)blockIdx.x * cp.seg;
     for (int j = threadIdx.x; j < n_own; j += SC_TPB) {
         const int p = p0 + j;
         const int o = id[p];
@@ -2361,7 +2221,7 @@ __global__ void __launch_bounds__(SC_TPB) k_store_nlist(Geom g, SuperGrid G, Sup
         if (nnb_out) nnb_out[o] = len;
         if (!nbr_out) continue;
         for (int e = 0; e < len && e < cap_out; ++e)
-            nbr_out[(size_t)o * cap_out + e] = id[staged_index(T, seg[roff[j] + e])];
+            nbr_out[(size_t)o * cap_out + e] = id[staged_index(T, nbr[(size_t)p * cp.cap + e])];
     }
 }
 

@@ -56,9 +56,9 @@ __device__ __forceinline__ void typed_row(int p, const GroupAux& aux, const Supe
                                           const uint16_t* __restrict__ nbr, const int* __restrict__ nnb,
                                           Visit&& visit)
 {
-    const int ra = __ldg(aux.roff + p), b = ra / cp.seg;
+    const int b = __ldg(aux.grp + p);
     const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
-    const uint16_t* row = nbr + ra;
+    const uint16_t* row = nbr + (size_t)p * cp.cap;
     const int len = row_len(__ldg(nnb + p));
     for (int e = threadIdx.x & 31; e < len; e += 32) visit(__ldg(sidx + __ldg(row + e)));
 }

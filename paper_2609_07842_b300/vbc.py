@@ -120,7 +120,7 @@ class Stats(ctypes.Structure):
                 ("nlist_cap", ctypes.c_int32), ("nlist_max", ctypes.c_int32), ("nlist_mean", ctypes.c_double),
                 ("pairs_within_rc", ctypes.c_int64), ("in_window", ctypes.c_int64),
                 ("unsaturated", ctypes.c_int64), ("stage_cap", ctypes.c_int32), ("group_cap", ctypes.c_int32),
-                ("segment_cap", ctypes.c_int32), ("groups", ctypes.c_int32),
+                ("groups", ctypes.c_int32),
                 ("capacity_grows", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
 
 

@@ -65,9 +65,9 @@ def test_budget_admits_one_system_at_a_time():
 
 def test_errors_are_codes():
     pos, L = inputs.uniform_positions(2000, 0.5, seed=1)
-    with vbc.Server(hbm_budget=1 << 20, slots=2, chunk_steps=1000) as srv:
+    with vbc.Server(hbm_budget=1 << 19, slots=2, chunk_steps=1000) as srv:
         with pytest.raises(vbc.VBCError) as e:
-            srv.submit(pos, L, nsteps=10)            # needs more than 1 MiB
+            srv.submit(pos, L, nsteps=10)            # needs about 1 MB, above the 512 KiB budget
         assert e.value.code == vbc.VBC_ERR_OOM
     with vbc.Server(slots=1, chunk_steps=1000) as srv:
         with pytest.raises(vbc.VBCError) as e:
