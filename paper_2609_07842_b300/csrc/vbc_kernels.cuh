@@ -1021,7 +1021,8 @@ __device__ __forceinline__ void pair_f64(const P64& pi, double si, double Ai, co
 {
     double dx, dy, dz;
     ModeF64::delta64(pi, pj, g, dx, dy, dz);
-    const double r2 = dx * dx + dy * dy + dz * dz;
+    // explicit fused multiply-adds, as in r2_d: the same r^2 in every kernel this is inlined in
+    const double r2 = __fma_rn(dx, dx, __fma_rn(dy, dy, __dmul_rn(dz, dz)));
     if (r2 >= c.rc2) return;
     const double r = sqrt(r2);
     double gr = dVr_over_r_d(r2, c);
@@ -1138,9 +1139,92 @@ __device__ __forceinline__ void stage_by_table(const int* __restrict__ sidx, int
 // terms need A_j != 0 of a neighbour -- which k_chain rules out by clearing
 // the tag of every list neighbour of a window particle.  Every other particle
 // goes on the list of k_force_rows.
+
+// What the close count of own particle p reads besides the staging: its
+// position, its close entries and its near-entry count (loaded ahead of the
+// staging, so that the loads overlap).
+template <class M>
+struct NearOwn {
+    typename M::pos_t pi;
+    uint2 cv[CLOSE_K / 4];
+    int nn;
+};
+
+template <class M>
+__device__ __forceinline__ void load_near_own(int p, const typename M::pos_t* __restrict__ pos, const GroupAux& aux,
+                                              const int* __restrict__ nnb, NearOwn<M>& o)
+{
+    o.nn = __ldg(nnb + p) & 0xffff;
+    o.pi = pos[p];
+    const uint2* cv = reinterpret_cast<const uint2*>(aux.close) + (CLOSE_K / 4) * (size_t)p;
+#pragma unroll
+    for (int k = 0; k < CLOSE_K / 4; ++k) o.cv[k] = __ldg(cv + k);
+}
+
+// The close count of own particle p from its close entries (staged positions
+// in spos), with its outputs: s_i = s'_i = 0 and, in the FP32 mode, the
+// soft-core force with the whole-force tag for a saturated particle; the
+// work lists of the row walks for every other one.  With out.n_out (FP64
+// counts wanted) no particle is settled here.
+template <class M>
+__device__ __forceinline__ void count_near_particle(int p, const NearOwn<M>& o, const typename M::pos_t* spos,
+                                                    const Geom& g, const Coef& c, typename M::pos_t* __restrict__ pos,
+                                                    const GroupAux& aux, typename M::real* __restrict__ ds_out,
+                                                    typename M::real2* __restrict__ sA, const CountOut& out,
+                                                    int* __restrict__ ulist, Status* st)
+{
+    using pos_t = typename M::pos_t;
+    using real = typename M::real;
+    using real2 = typename M::real2;
+    int full = 0;
+    float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+    if (!out.n_out) {
+        int q[CLOSE_K];
+#pragma unroll
+        for (int k = 0; k < CLOSE_K / 4; ++k) unpack4(o.cv[k], q + 4 * k);
+        // soft core: g / r = K (r^2 - r_r^2), r^2 in units of (L / 2^32)^2
+        const float kc = c.Er4f * c.rr2invf * g.s32sq;
+#pragma unroll
+        for (int k = 0; k < CLOSE_K; ++k) {
+            if (q[k] == CLOSE_NONE) continue;
+            const pos_t pj = spos[q[k]];
+            if constexpr (M::fp64) {
+                full += r2_d<M>(o.pi, pj, g) <= c.rl2;
+            } else {
+                const unsigned long long r2i = r2_fix(o.pi, pj);
+                full += r2i <= c.rl2_fix;
+                if (r2i < c.rr2_fix) {
+                    const float dx = (float)(o.pi.x - pj.x), dy = (float)(o.pi.y - pj.y), dz = (float)(o.pi.z - pj.z);
+                    const float gr = __fmaf_rn(kc, __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz)), -c.Er4f);
+                    fx = __fmaf_rn(-gr, dx, fx);
+                    fy = __fmaf_rn(-gr, dy, fy);
+                    fz = __fmaf_rn(-gr, dz, fz);
+                }
+            }
+        }
+    }
+    const bool sat = !out.n_out && full >= c.sat_full;
+    if (sat) {
+        ds_out[p] = (real)0;
+        sA[p] = real2{(real)0, (real)0};
+        put_w(pos + p, (real)0);
+    } else {
+        ds_out[p] = (real)NAN;  // marks the particle for k_count_rows
+        ulist[atomicAdd(&st->nu, 1)] = p;
+    }
+    const bool whole = !M::fp64 && sat && o.nn <= CLOSE_K;
+    if constexpr (M::fp64) {
+        static_cast<F64x4*>(aux.fcore)[p] = F64x4{0.0, 0.0, 0.0, 0.0};
+    } else {
+        static_cast<float4*>(aux.fcore)[p] = make_float4(fx * g.s32, fy * g.s32, fz * g.s32, whole ? 1.0f : 0.0f);
+    }
+    if (!whole) aux.glist[atomicAdd(&st->ngen, 1)] = p;
+}
+
 // The close count of cell group b (the whole block; smem holds the group's
 // staged positions).  Starts with a block barrier, so that it may follow
-// another group's work on the same shared memory.
+// another group's work on the same shared memory.  (The fused batch launch;
+// k_count_near runs the same per-particle count with its loads pipelined.)
 template <class M>
 __device__ __forceinline__ void count_near_group(int b, const Geom& g, const Coef& c, typename M::pos_t* __restrict__ pos,
                                                  const SuperGrid& G, const SuperCaps& cp, const GroupAux& aux,
@@ -1149,70 +1233,58 @@ __device__ __forceinline__ void count_near_group(int b, const Geom& g, const Coe
                                                  int* __restrict__ ulist, Status* st, unsigned char* smem)
 {
     using pos_t = typename M::pos_t;
-    using real = typename M::real;
-    using real2 = typename M::real2;
     pos_t* spos = (pos_t*)smem;
-    {
-        __syncthreads();  // the previous group is done with the shared positions
-        const int p0 = __ldg(G.cell_start + OWN_CELLS * b);
-        const int n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
-        if (!out.n_out)
-            stage_by_table(aux.stage_idx + (size_t)b * cp.smax, __ldg(aux.meta + b).x,
-                           [&](int m, int jj) { spos[m] = pos[jj]; });
-        __syncthreads();
-        for (int j = threadIdx.x; j < n_own; j += SC_TPB) {
-            const int p = p0 + j;
-            int full = 0;
-            float fx = 0.0f, fy = 0.0f, fz = 0.0f;
-            const int nn = __ldg(nnb + p) & 0xffff;
-            if (!out.n_out) {
-                const pos_t pi = pos[p];
-                const uint2* cv = reinterpret_cast<const uint2*>(aux.close) + (CLOSE_K / 4) * (size_t)p;
-                int q[CLOSE_K];
-#pragma unroll
-                for (int k = 0; k < CLOSE_K / 4; ++k) unpack4(__ldg(cv + k), q + 4 * k);
-                // soft core: g / r = K (r^2 - r_r^2), r^2 in units of (L / 2^32)^2
-                const float kc = c.Er4f * c.rr2invf * g.s32sq;
-#pragma unroll
-                for (int k = 0; k < CLOSE_K; ++k) {
-                    if (q[k] == CLOSE_NONE) continue;
-                    const pos_t pj = spos[q[k]];
-                    if constexpr (M::fp64) {
-                        full += r2_d<M>(pi, pj, g) <= c.rl2;
-                    } else {
-                        const unsigned long long r2i = r2_fix(pi, pj);
-                        full += r2i <= c.rl2_fix;
-                        if (r2i < c.rr2_fix) {
-                            const float dx = (float)(pi.x - pj.x), dy = (float)(pi.y - pj.y), dz = (float)(pi.z - pj.z);
-                            const float gr = __fmaf_rn(kc, __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz)), -c.Er4f);
-                            fx = __fmaf_rn(-gr, dx, fx);
-                            fy = __fmaf_rn(-gr, dy, fy);
-                            fz = __fmaf_rn(-gr, dz, fz);
-                        }
-                    }
-                }
-            }
-            const bool sat = !out.n_out && full >= c.sat_full;
-            if (sat) {
-                ds_out[p] = (real)0;
-                sA[p] = real2{(real)0, (real)0};
-                put_w(pos + p, (real)0);
-            } else {
-                ds_out[p] = (real)NAN;  // marks the particle for k_count_rows
-                ulist[atomicAdd(&st->nu, 1)] = p;
-            }
-            const bool whole = !M::fp64 && sat && nn <= CLOSE_K;
-            if constexpr (M::fp64) {
-                static_cast<F64x4*>(aux.fcore)[p] = F64x4{0.0, 0.0, 0.0, 0.0};
-            } else {
-                static_cast<float4*>(aux.fcore)[p] =
-                    make_float4(fx * g.s32, fy * g.s32, fz * g.s32, whole ? 1.0f : 0.0f);
-            }
-            if (!whole) aux.glist[atomicAdd(&st->ngen, 1)] = p;
-        }
+    __syncthreads();  // the previous group is done with the shared positions
+    const int p0 = __ldg(G.cell_start + OWN_CELLS * b);
+    const int n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
+    if (!out.n_out)
+        stage_by_table(aux.stage_idx + (size_t)b * cp.smax, __ldg(aux.meta + b).x,
+                       [&](int m, int jj) { spos[m] = pos[jj]; });
+    __syncthreads();
+    for (int j = threadIdx.x; j < n_own; j += SC_TPB) {
+        NearOwn<M> o;
+        load_near_own<M>(p0 + j, pos, aux, nnb, o);
+        count_near_particle<M>(p0 + j, o, spos, g, c, pos, aux, ds_out, sA, out, ulist, st);
     }
 }
 
+// Asynchronous 16-byte copy from global to shared memory (cp.async, bypassing
+// L1), and the wait for every copy this thread issued.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Staged particles per thread whose table entries k_count_near loads one
+// group ahead (the staging of a group holds about 680 particles at
+// rho = 0.5; slots past NEAR_B * SC_TPB are copied synchronously).
+constexpr int NEAR_B = 8;
+
+// Range and staged total of cell group b.
+struct GroupRange {
+    int p0, n_own, total;
+};
+__device__ __forceinline__ GroupRange group_range(int b, const SuperGrid& G, const GroupAux& aux)
+{
+    GroupRange r;
+    r.p0 = __ldg(G.cell_start + OWN_CELLS * b);
+    r.n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - r.p0;
+    r.total = __ldg(aux.meta + b).x;
+    return r;
+}
+
+// k_count_near: the cell groups on a resident grid, each block taking groups
+// b, b + gridDim.x, ...  The loads are pipelined so that each group waits on
+// one memory round trip: the range of the group after next and the
+// staged-index table of the next group are loaded while the current group
+// is counted, and the staging copies (cp.async) overlap the loads of the own
+// particles' close entries.
 template <class M>
 __global__ void __launch_bounds__(SC_TPB) k_count_near(int ngroups, Geom g, Coef c, typename M::pos_t* __restrict__ pos,
                                                        SuperGrid G, SuperCaps cp, GroupAux aux,
@@ -1220,12 +1292,65 @@ __global__ void __launch_bounds__(SC_TPB) k_count_near(int ngroups, Geom g, Coef
                                                        typename M::real2* __restrict__ sA, CountOut out,
                                                        int* __restrict__ ulist, Status* st)
 {
+    using pos_t = typename M::pos_t;
     if (blockIdx.x == 0 && threadIdx.x == 0) st->rebuild = 0;
     if (halted(st)) return;
-    // the group's neighbourhood, staged once for the close-list gathers of its own particles
     extern __shared__ __align__(16) unsigned char smem[];
-    for (int b = blockIdx.x; b < ngroups; b += gridDim.x)
-        count_near_group<M>(b, g, c, pos, G, cp, aux, nnb, ds_out, sA, out, ulist, st, smem);
+    if (out.n_out) {
+        // FP64 counts wanted: no particle is settled here, nothing is staged
+        for (int b = blockIdx.x; b < ngroups; b += gridDim.x)
+            count_near_group<M>(b, g, c, pos, G, cp, aux, nnb, ds_out, sA, out, ulist, st, smem);
+        return;
+    }
+    pos_t* spos = (pos_t*)smem;
+    constexpr int CHUNKS = (int)(sizeof(pos_t) / 16);
+    const int t = threadIdx.x;
+    int b = blockIdx.x;
+    if (b >= ngroups) return;
+    GroupRange cur = group_range(b, G, aux);
+    GroupRange nxt{0, 0, 0};
+    if (b + (int)gridDim.x < ngroups) nxt = group_range(b + gridDim.x, G, aux);
+    int jj[NEAR_B];
+    {
+        const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
+#pragma unroll
+        for (int u = 0; u < NEAR_B; ++u) jj[u] = t + u * SC_TPB < cur.total ? __ldg(sidx + t + u * SC_TPB) : -1;
+    }
+    for (; b < ngroups; b += gridDim.x) {
+        __syncthreads();  // the previous group is done with the shared positions
+        // this group's staging: asynchronous copies, then the rest (if any) synchronously
+#pragma unroll
+        for (int u = 0; u < NEAR_B; ++u)
+            if (jj[u] >= 0)
+#pragma unroll
+                for (int k = 0; k < CHUNKS; ++k)
+                    cp_async16(reinterpret_cast<int4*>(spos + t + u * SC_TPB) + k,
+                               reinterpret_cast<const int4*>(pos + jj[u]) + k);
+        const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
+        for (int m = t + NEAR_B * SC_TPB; m < cur.total; m += SC_TPB) spos[m] = pos[__ldg(sidx + m)];
+        // the first own particle of this thread
+        NearOwn<M> o;
+        const bool own0 = t < cur.n_own;
+        if (own0) load_near_own<M>(cur.p0 + t, pos, aux, nnb, o);
+        // the next group's table and the range of the one after it
+        const int bn = b + gridDim.x;
+        GroupRange nn2{0, 0, 0};
+        if (bn < ngroups) {
+            const int* sn = aux.stage_idx + (size_t)bn * cp.smax;
+#pragma unroll
+            for (int u = 0; u < NEAR_B; ++u) jj[u] = t + u * SC_TPB < nxt.total ? __ldg(sn + t + u * SC_TPB) : -1;
+            if (bn + (int)gridDim.x < ngroups) nn2 = group_range(bn + gridDim.x, G, aux);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        if (own0) count_near_particle<M>(cur.p0 + t, o, spos, g, c, pos, aux, ds_out, sA, out, ulist, st);
+        for (int j = t + SC_TPB; j < cur.n_own; j += SC_TPB) {
+            load_near_own<M>(cur.p0 + j, pos, aux, nnb, o);
+            count_near_particle<M>(cur.p0 + j, o, spos, g, c, pos, aux, ds_out, sA, out, ulist, st);
+        }
+        cur = nxt;
+        nxt = nn2;
+    }
 }
 
 // ================================================================ row walks

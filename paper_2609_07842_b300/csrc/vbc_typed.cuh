@@ -164,7 +164,8 @@ __global__ void __launch_bounds__(SC_TPB) k_tforce(int n, Geom g, const P64* __r
             double dx, dy, dz;
             ModeF64::delta64(pi, pos[j], g, dx, dy, dz);
             const double2 saj = sA[j];
-            const double gr = typed_gr(dx * dx + dy * dy + dz * dz, ti, t.tsort[j], sai.x, sai.y, saj.x, saj.y, t);
+            const double r2 = __fma_rn(dx, dx, __fma_rn(dy, dy, __dmul_rn(dz, dz)));
+            const double gr = typed_gr(r2, ti, t.tsort[j], sai.x, sai.y, saj.x, saj.y, t);
             fx -= gr * dx;
             fy -= gr * dy;
             fz -= gr * dz;
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(SC_TPB) k_tforce(int n, Geom g, const P64* __r
             typed_bonds(p, id, t, [&](int q) {
                 double dx, dy, dz;
                 ModeF64::delta64(pi, pos[q], g, dx, dy, dz);
-                const double r = sqrt(dx * dx + dy * dy + dz * dz);
+                const double r = sqrt(__fma_rn(dx, dx, __fma_rn(dy, dy, __dmul_rn(dz, dz))));
                 if (r > 0.0) {
                     const double gr = t.kb * (r - t.r0) / r;
                     fx -= gr * dx;
@@ -410,7 +411,7 @@ __global__ void __launch_bounds__(SC_TPB) k_tenergy(int n, Geom g, const typenam
                 typed_bonds(p, id, t, [&](int q) {
                     double dx, dy, dz;
                     M::delta64(pi, pos[q], g, dx, dy, dz);
-                    const double r = sqrt(dx * dx + dy * dy + dz * dz), u = r - t.r0;
+                    const double r = sqrt(__fma_rn(dx, dx, __fma_rn(dy, dy, __dmul_rn(dz, dz)))), u = r - t.r0;
                     ep += 0.5 * (0.5 * t.kb * u * u);
                     wp += 0.5 * (-t.kb * u * r);
                 });
