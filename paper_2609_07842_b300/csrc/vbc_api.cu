@@ -62,7 +62,7 @@ constexpr int MAX_STAGE = 65535;       // staged particles per cell group (16-bi
 constexpr int MAX_OWN = 4096;          // particles of one cell group
 constexpr size_t MAX_SMEM = 227 * 1024;
 constexpr int MAX_RETRIES = 12;
-constexpr int REBUILD_KERNELS = 8;     // kernels of one neighbour-list rebuild
+constexpr int REBUILD_KERNELS = 7;     // kernels of one neighbour-list rebuild
 constexpr int WTAB_PIECES = 1024;      // pieces of the window-weight table (at most)
 
 int blocks_for(int64_t n, int tpb) { return (int)((n + tpb - 1) / tpb); }
@@ -162,13 +162,13 @@ struct vbc_system {
     int64_t launches = 0;
 
     // CUDA graphs of the loop iterations (see run_iterations): one per kind of
-    // iteration (G_OPEN, G_PAIR, G_SINGLE, G_CLOSE) and parity of the position
+    // iteration (G_OPEN, G_PAIR, G_SINGLE, G_CLOSE, G_RUN) and parity of the position
     // buffer it starts on, all captured together for one set of step
     // coefficients and one layout
     bool use_graphs = true;
     bool capturing = false;
     cudaStream_t cap_stream = nullptr, body_stream = nullptr;
-    cudaGraphExec_t graphs[4][2] = {};
+    cudaGraphExec_t graphs[5][2] = {};
     double g_dt = 0, g_c1 = 0, g_c2 = 0;
     long long g_layout = -1;
     long long layout_version = 0;  // bumps when parameters or capacities (kernel arguments) change
@@ -595,22 +595,28 @@ int enqueue_rebuild(vbc_system* s)
     k_cellsort<<<blocks_for(s->npad, TPB), TPB, 0, s->stream>>>(s->npad, s->cell_start, s->order, s->st);
     k_permute<M><<<nb, TPB, 0, s->stream>>>(n, s->order, s->x, s->v, s->id, pos, s->xt, s->vt, s->idt,
                                             (pos_t*)s->post, s->st);
-    k_copyback<M><<<nb, TPB, 0, s->stream>>>(n, s->xt, s->vt, s->idt, (const pos_t*)s->post, s->x, s->v, s->id,
-                                             pos, (pos_t*)s->xref, s->resid, s->st);
-    if (s->typed) {
-        k_tmaps<<<nb, TPB, 0, s->stream>>>(n, s->id, s->tdev);
-        VBC_TRY(check_launch(s));
-    }
+    // the list build stages the gathered positions and copies the gathered state back, each
+    // block its own particles' (no separate copy-back pass)
+    const CopyBack<M> cb{n, s->xt, s->vt, s->idt, (const pos_t*)s->post, s->x, s->v, s->id, pos, (pos_t*)s->xref,
+                         s->resid};
+    bool launched = false;
     if constexpr (!M::fp64) {
         if (s->rel_lists) {
             k_nlist<M, true><<<s->nsc, SC_TPB, s->smem_nlist_rel(), s->stream>>>(
-                s->geom, pos, s->grid(), s->caps(), s->lp, s->nbr, s->nnb, s->aux(), s->st);
-            return check_launch(s, REBUILD_KERNELS);
+                s->geom, s->grid(), s->caps(), s->lp, s->nbr, s->nnb, s->aux(), s->st, cb);
+            launched = true;
         }
     }
-    k_nlist<M, false><<<s->nsc, SC_TPB, s->smem_nlist(), s->stream>>>(s->geom, pos, s->grid(), s->caps(), s->lp,
-                                                                       s->nbr, s->nnb, s->aux(), s->st);
-    return check_launch(s, REBUILD_KERNELS);
+    if (!launched)
+        k_nlist<M, false><<<s->nsc, SC_TPB, s->smem_nlist(), s->stream>>>(s->geom, s->grid(), s->caps(), s->lp,
+                                                                           s->nbr, s->nnb, s->aux(), s->st, cb);
+    VBC_TRY(check_launch(s, REBUILD_KERNELS));
+    if (s->typed) {
+        // the type maps follow the sorted order the build copied back
+        k_tmaps<<<nb, TPB, 0, s->stream>>>(n, s->id, s->tdev);
+        VBC_TRY(check_launch(s));
+    }
+    return VBC_OK;
 }
 
 // Resident grid of the typed walks (one warp per particle, grid-stride).
@@ -1097,13 +1103,15 @@ int graph_error(vbc_system* s, const char* what, cudaError_t e)
 }
 
 // Kinds of captured iterations: G_OPEN opens step 0 (forces of the initial
-// state, then B A O A), G_PAIR and G_SINGLE close one step and open the next
-// (twice and once), G_CLOSE closes the last step.
-enum GraphKind { G_OPEN = 0, G_PAIR = 1, G_SINGLE = 2, G_CLOSE = 3, G_NKIND = 4 };
-constexpr int KIND_EPIS[G_NKIND][2] = {{EPI_START, -1}, {EPI_FINISH_START, EPI_FINISH_START},
-                                       {EPI_FINISH_START, -1}, {EPI_FINISH, -1}};
-int kind_iters(int k) { return k == G_PAIR ? 2 : 1; }
+// state, then B A O A), G_RUN, G_PAIR and G_SINGLE close one step and open
+// the next (RUN_ITERS times, twice and once), G_CLOSE closes the last step.
+// Long calls run mostly G_RUN graphs: fewer graph launches, each a boundary
+// the device pays a few microseconds for.
+enum GraphKind { G_OPEN = 0, G_PAIR = 1, G_SINGLE = 2, G_CLOSE = 3, G_RUN = 4, G_NKIND = 5 };
+constexpr int RUN_ITERS = 8;  // middle iterations of one G_RUN graph
+int kind_iters(int k) { return k == G_PAIR ? 2 : (k == G_RUN ? RUN_ITERS : 1); }
 int kind_flips(int k) { return k == G_OPEN || k == G_SINGLE ? 1 : 0; }  // position-buffer flips, mod 2
+int kind_epi(int k) { return k == G_OPEN ? EPI_START : (k == G_CLOSE ? EPI_FINISH : EPI_FINISH_START); }
 int iter_launches(const vbc_system* s) { return s->typed ? 5 : 6; }    // gate, count(s), chain, force, step
 
 // Captures the iterations of kind `kind` starting on position buffer c into
@@ -1117,7 +1125,7 @@ int capture_iters(vbc_system* s, int c, const StepArgs& a, int kind, cudaGraph_t
     if (!s->cap_stream) VBC_CUDA(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
     if (!s->body_stream) VBC_CUDA(cudaStreamCreateWithFlags(&s->body_stream, cudaStreamNonBlocking));
     const int niter = kind_iters(kind);
-    cudaGraphConditionalHandle h[2];
+    cudaGraphConditionalHandle h[RUN_ITERS];
     for (int k = 0; k < niter; ++k) {
         cudaError_t e = cudaGraphConditionalHandleCreate(&h[k], g, 0, cudaGraphCondAssignDefault);
         if (e != cudaSuccess) return graph_error(s, "cudaGraphConditionalHandleCreate", e);
@@ -1160,7 +1168,7 @@ int capture_iters(vbc_system* s, int c, const StepArgs& a, int kind, cudaGraph_t
         e = cudaStreamEndCapture(s->body_stream, &body);
         if (rc == VBC_OK && e != cudaSuccess) rc = graph_error(s, "end of the rebuild body capture", e);
         if (rc == VBC_OK) rc = enqueue_count_chain<M>(s, nullptr, false);
-        if (rc == VBC_OK) rc = enqueue_force_epi<M>(s, a, KIND_EPIS[kind][k]);
+        if (rc == VBC_OK) rc = enqueue_force_epi<M>(s, a, kind_epi(kind));
     }
     cudaGraph_t out = nullptr;
     e = cudaStreamEndCapture(s->cap_stream, &out);
@@ -1230,8 +1238,10 @@ int run_range(vbc_system* s, const StepArgs& a, int64_t it, int64_t it_end, int6
     while (it < it_end) {
         if (s->use_graphs && !s->prof) {
             const int kind = it == 0 ? G_OPEN
-                                     : (it + 1 <= nsteps - 1 && it + 1 < it_end ? G_PAIR
-                                                                                 : (it < nsteps ? G_SINGLE : G_CLOSE));
+                             : (it + RUN_ITERS - 1 <= nsteps - 1 && it + RUN_ITERS - 1 < it_end
+                                    ? G_RUN
+                                    : (it + 1 <= nsteps - 1 && it + 1 < it_end ? G_PAIR
+                                                                                : (it < nsteps ? G_SINGLE : G_CLOSE)));
             VBC_TRY(launch_graph<M>(s, a, kind));
             it += kind_iters(kind);
         } else {

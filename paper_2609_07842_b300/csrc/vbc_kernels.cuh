@@ -13,7 +13,7 @@
 // One MD step:
 //   rebuild (only when a particle moved more than skin/2 since the last build):
 //     k_bin -> k_scan_sums -> k_scan_apply -> k_scatter -> k_cellsort ->
-//     k_permute -> k_copyback -> k_nlist
+//     k_permute -> k_nlist (which also copies the gathered state back)
 //   k_count   pass 1: n_i, s_i, s'_i                        (Eqs. counter, Psidelta)
 //   k_chain   A_i = s'_i sum_j s_j V_a(r_ij), window particles only
 //   k_force   pass 2: F_i, fused with the BAOAB update of the state
@@ -68,8 +68,32 @@ __global__ void __launch_bounds__(TPB) k_bin(const typename M::pos_t* __restrict
                                              int* __restrict__ cell_count, Status* st)
 {
     if (!rebuild_on(st)) return;
+    // as bin_item, with one atomic per cell and warp: particles arrive in the previous sorted
+    // order, so neighbouring lanes mostly share a cell (the order within a cell is settled by
+    // k_cellsort, whatever the slots)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) bin_item<M>(i, pos, g, morton_rank, cell_of, slot_of, cell_count, st);
+    const bool act = i < n;
+    int key = -1;
+    if (act) {
+        if (i == 0) {
+            st->max_nnb = 0;
+            st->nnb_sum = 0;
+            st->max_stage = 0;
+            st->max_own = 0;
+        }
+        const int3 c = cell_of_pos<M>(pos[i], g);
+        key = morton_rank[(c.z * g.nc[1] + c.y) * g.nc[0] + c.x];
+        cell_of[i] = key;
+    }
+    const unsigned active = __ballot_sync(0xffffffffu, act);
+    if (!act) return;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned peers = __match_any_sync(active, key);
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if ((int)lane == leader) base = atomicAdd(&cell_count[key], __popc(peers));
+    base = __shfl_sync(active, base, leader);
+    slot_of[i] = base + __popc(peers & ((1u << lane) - 1u));
 }
 
 // Block-wide exclusive scan of one int per thread; returns the block total.
@@ -308,22 +332,6 @@ __global__ void __launch_bounds__(TPB) k_permute(int n, const int* __restrict__ 
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n) permute_item<M>(k, n, order, x, v, id, pos, xt, vt, idt, post);
 }
-
-template <class M>
-__global__ void __launch_bounds__(TPB) k_copyback(int n, const unsigned long long* __restrict__ xt,
-                                                  const unsigned long long* __restrict__ vt,
-                                                  const int* __restrict__ idt,
-                                                  const typename M::pos_t* __restrict__ post,
-                                                  unsigned long long* __restrict__ x, unsigned long long* __restrict__ v,
-                                                  int* __restrict__ id, typename M::pos_t* __restrict__ pos,
-                                                  typename M::pos_t* __restrict__ xref, int* __restrict__ resid,
-                                                  const Status* st)
-{
-    if (!rebuild_on(st)) return;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) copyback_item<M>(k, n, xt, vt, idt, post, x, v, id, pos, xref, resid);
-}
-
 
 // ================================================================ blocks of cells
 // The cell grid is padded with empty phantom cells to extents that are
@@ -603,11 +611,38 @@ __device__ __forceinline__ void shift192(unsigned long long& a0, unsigned long l
 // multiple of 4 entries with the particle's own staging index.
 // The list build of cell group b (the whole block; smem is the dynamic shared
 // memory of nlist_smem).  Raises `overflow` and `stage_overflow` itself.
+// The copy-back of the sorted state, which the list build takes over from a
+// pass of its own: the gathered state of the block's own particles moves
+// from the sort's temporaries to the state arrays (copyback_item), while the
+// build stages its neighbourhood from the temporaries.
+template <class M>
+struct CopyBack {
+    int n;
+    const unsigned long long *xt, *vt;
+    const int* idt;
+    const typename M::pos_t* post;
+    unsigned long long *x, *v;
+    int* id;
+    typename M::pos_t *pos, *xref;
+    int* resid;
+};
+
+template <class M>
+__device__ __forceinline__ void copy_own(const CopyBack<M>* cb, int p0, int n_own)
+{
+    if (!cb) return;
+    for (int j = threadIdx.x; j < n_own; j += SC_TPB)
+        copyback_item<M>(p0 + j, cb->n, cb->xt, cb->vt, cb->idt, cb->post, cb->x, cb->v, cb->id, cb->pos, cb->xref,
+                         cb->resid);
+}
+
+// With cb, pos is the sort's gathered positions (post) and the block also
+// copies its own particles' state back (copy_own).
 template <class M, bool REL>
 __device__ __forceinline__ void nlist_group(int b, const Geom& g, const typename M::pos_t* __restrict__ pos,
                                             const SuperGrid& G, const SuperCaps& cp, const ListParams& lp,
                                             uint16_t* __restrict__ nbr, int* __restrict__ nnb, const GroupAux& aux,
-                                            Status* st, unsigned char* smem)
+                                            Status* st, unsigned char* smem, const CopyBack<M>* cb = nullptr)
 {
     using pos_t = typename M::pos_t;
     using spos_t = typename std::conditional<REL, float4, pos_t>::type;
@@ -629,6 +664,7 @@ __device__ __forceinline__ void nlist_group(int b, const Geom& g, const typename
             st->stage_overflow = 1;
             st->frozen_iter = (int)st->iter;
         }
+        copy_own<M>(cb, p0, n_own);  // the state is complete even when the build is redone
         return;
     }
     spos_t* spos = (spos_t*)smem;
@@ -778,6 +814,7 @@ __device__ __forceinline__ void nlist_group(int b, const Geom& g, const typename
         mx = max(mx, len);
         sum += len;
     }
+    copy_own<M>(cb, p0, n_own);
     // list statistics
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -800,14 +837,15 @@ __device__ __forceinline__ void nlist_group(int b, const Geom& g, const typename
     }
 }
 
+// (The FP64 mode's wider positions take more registers: it asks for fewer resident blocks.)
 template <class M, bool REL>
-__global__ void __launch_bounds__(SC_TPB, NLIST_MIN_BLOCKS)
-    k_nlist(Geom g, const typename M::pos_t* __restrict__ pos, SuperGrid G, SuperCaps cp, ListParams lp,
-            uint16_t* __restrict__ nbr, int* __restrict__ nnb, GroupAux aux, Status* st)
+__global__ void __launch_bounds__(SC_TPB, M::fp64 ? NLIST_MIN_BLOCKS / 2 : NLIST_MIN_BLOCKS)
+    k_nlist(Geom g, SuperGrid G, SuperCaps cp, ListParams lp, uint16_t* __restrict__ nbr, int* __restrict__ nnb,
+            GroupAux aux, Status* st, CopyBack<M> cb)
 {
     if (!rebuild_on(st)) return;
     extern __shared__ __align__(16) unsigned char smem[];
-    nlist_group<M, REL>(blockIdx.x, g, pos, G, cp, lp, nbr, nnb, aux, st, smem);
+    nlist_group<M, REL>(blockIdx.x, g, cb.post, G, cp, lp, nbr, nnb, aux, st, smem, &cb);
 }
 
 // ================================================================ pass 2: forces + BAOAB

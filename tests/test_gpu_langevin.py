@@ -173,22 +173,22 @@ def test_kernel_launch_accounting():
     pos, vel, L, p = _system(2000, 0.5, seed=9)
     with vbc.System(pos, L, _vp(p), vel=vel) as s:
         # direct launches (per-kernel timing on): one iteration counter reset, then per
-        # iteration a gate, 8 rebuild kernels (returning at once when no rebuild is due),
+        # iteration a gate, 7 rebuild kernels (returning at once when no rebuild is due),
         # the two count kernels, chain, force rows and the update
         s.profile(True)
         before = s.kernel_launches()
         s.step(10, 0.005, 1.0, 1.0)
-        assert s.kernel_launches() - before == 1 + 11 * 14
+        assert s.kernel_launches() - before == 1 + 11 * 13
         s.profile(False)
         # graphs: the previous call left the forces of the current state in place, so
         # iteration 0 is the iteration counter and the update alone; iterations 1..8 run
-        # as four two-step graphs of 12 kernels, 9 and 10 as one-iteration graphs of 6,
-        # plus 8 kernels for every rebuild the graphs' conditionals executed
+        # as one eight-step graph of 48 kernels, 9 and 10 as one-iteration graphs of 6,
+        # plus 7 kernels for every rebuild the graphs' conditionals executed
         before = s.kernel_launches()
         s.step(10, 0.005, 1.0, 1.0)
         d = s.kernel_launches() - before
-        base = 2 + 4 * 12 + 2 * 6
-        assert d >= base and (d - base) % 8 == 0
+        base = 2 + 8 * 6 + 2 * 6
+        assert d >= base and (d - base) % 7 == 0
 
 
 @pytest.mark.parametrize("prec", [F32, F64])
