@@ -695,7 +695,7 @@ int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window)
     {
         Timed t(s, VBC_K_COUNT);
         k_count_near<M><<<s->near_grid, SC_TPB, s->smem_near(), s->stream>>>(
-            s->nsc, s->geom, s->coef, pos, s->grid(), s->caps(), s->aux(), s->nnb, (real*)s->ds, (real2*)s->sA, out,
+            s->nsc, (int)s->n, s->geom, s->coef, pos, s->grid(), s->caps(), s->aux(), s->nnb, (real*)s->ds, (real2*)s->sA, out,
             s->ulist, s->st);
         for_row_tpb(s->row_tpb, [&](auto nt) -> int {
             constexpr int NT = decltype(nt)::value;
@@ -945,7 +945,9 @@ int halt_error(vbc_system* s)
         return fail(VBC_ERR_UNSTABLE, "a loaded position or velocity is non-finite or beyond the fixed-point range "
                                       "(|x| < 1024 L, |v| < 2^22)");
     if (s->st_host->frozen) return fail(VBC_ERR_UNSTABLE, "a position, velocity or force became non-finite");
-    if (s->st_host->bad_index) return fail(VBC_ERR_CUDA, "internal error: a count met a particle index out of range");
+    if (s->st_host->bad_index)
+        return fail(VBC_ERR_CUDA, "internal error: a device-side index check failed (code %d); the access was skipped",
+                    s->st_host->bad_index);
     return VBC_OK;
 }
 

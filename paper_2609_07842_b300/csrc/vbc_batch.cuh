@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(SC_TPB, BATCH_MIN_BLOCKS) k_batch_iter(const S
         const int b = w - ogroup[k];
         if (b == 0 && threadIdx.x == 0) A.st->rebuild = 0;
         if (halted(A.st)) continue;
-        count_near_group<M>(b, A.g, A.c, A.pos, A.G, A.cp, A.aux, A.nnb, A.ds, A.sA, A.out, A.ulist, A.st, smem);
+        count_near_group<M>(b, A.n, A.g, A.c, A.pos, A.G, A.cp, A.aux, A.nnb, A.ds, A.sA, A.out, A.ulist, A.st, smem);
     }
     if (!grid_wait(ctl, gen)) return;
 

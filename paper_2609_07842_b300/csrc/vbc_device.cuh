@@ -90,7 +90,7 @@ struct Status {
     int nu;             // particles the last count walked in full: not saturated by their kept close
                         // neighbours (k_count_near)
     int ngen;           // particles whose force k_force_rows forms (k_count_near, k_chain)
-    int bad_index;      // 1: a count was handed a particle index outside [0, n) (k_count_rows; an internal error)
+    int bad_index;      // nonzero: a device-side index check failed (BadIndex; an internal error)
     int bad_input;      // 1: a loaded position or velocity was non-finite or beyond the fixed-point range (k_load_state)
     int aborted;        // 1: a batched iteration gave up waiting and left the state incomplete (host)
 };

@@ -1153,19 +1153,49 @@ struct __align__(32) F64x4 {
     double x, y, z, w;
 };
 
+// Index checks of the table-driven gathers.  The tables are consistent by
+// construction (the list build writes them together and halts the system when
+// a group outgrows its capacities); a check that fails anyway records the
+// internal error in `bad` (reported by the host when the call ends) and the
+// access is skipped, or redirected to particle 0, instead of leaving the
+// buffers.
+enum BadIndex { BAD_SORTED = 1, BAD_STAGED = 2, BAD_STAGING_SIZE = 3 };
+
+__device__ __forceinline__ int checked_sorted(int jj, int n, int* bad)
+{
+    if ((unsigned)jj < (unsigned)n) return jj;
+    *bad = BAD_SORTED;
+    return 0;
+}
+__device__ __forceinline__ int checked_staged(int m, int cap, int* bad)
+{
+    if ((unsigned)m < (unsigned)cap) return m;
+    *bad = BAD_STAGED;
+    return 0;
+}
+
 // Copies a group's staged particles: put(m, j) for staging index m and sorted
-// index j, four loads of the index table in flight per thread.
+// index j, four loads of the index table in flight per thread.  total is
+// checked against the staging capacity cap and every j against n.
 template <int NT = SC_TPB, class Put>
-__device__ __forceinline__ void stage_by_table(const int* __restrict__ sidx, int total, Put&& put)
+__device__ __forceinline__ void stage_by_table(const int* __restrict__ sidx, int total, int cap, int n, int* bad,
+                                               Put&& put)
 {
     constexpr int B = 4;
+    if (total > cap) {
+        *bad = BAD_STAGING_SIZE;
+        total = cap;
+    }
     for (int m0 = threadIdx.x; m0 < total; m0 += NT * B) {
         int jj[B];
 #pragma unroll
         for (int u = 0; u < B; ++u) jj[u] = m0 + u * NT < total ? __ldg(sidx + m0 + u * NT) : -1;
 #pragma unroll
         for (int u = 0; u < B; ++u)
-            if (jj[u] >= 0) put(m0 + u * NT, jj[u]);
+            if (m0 + u * NT < total) {
+                if ((unsigned)jj[u] < (unsigned)n) put(m0 + u * NT, jj[u]);
+                else *bad = BAD_SORTED;
+            }
     }
 }
 
@@ -1206,7 +1236,7 @@ __device__ __forceinline__ void load_near_own(int p, const typename M::pos_t* __
 // counts wanted) no particle is settled here.
 template <class M>
 __device__ __forceinline__ void count_near_particle(int p, const NearOwn<M>& o, const typename M::pos_t* spos,
-                                                    const Geom& g, const Coef& c, typename M::pos_t* __restrict__ pos,
+                                                    int total, const Geom& g, const Coef& c, typename M::pos_t* __restrict__ pos,
                                                     const GroupAux& aux, typename M::real* __restrict__ ds_out,
                                                     typename M::real2* __restrict__ sA, const CountOut& out,
                                                     int* __restrict__ ulist, Status* st)
@@ -1225,7 +1255,7 @@ __device__ __forceinline__ void count_near_particle(int p, const NearOwn<M>& o, 
 #pragma unroll
         for (int k = 0; k < CLOSE_K; ++k) {
             if (q[k] == CLOSE_NONE) continue;
-            const pos_t pj = spos[q[k]];
+            const pos_t pj = spos[checked_staged(q[k], total, &st->bad_index)];
             if constexpr (M::fp64) {
                 full += r2_d<M>(o.pi, pj, g) <= c.rl2;
             } else {
@@ -1264,8 +1294,9 @@ __device__ __forceinline__ void count_near_particle(int p, const NearOwn<M>& o, 
 // another group's work on the same shared memory.  (The fused batch launch;
 // k_count_near runs the same per-particle count with its loads pipelined.)
 template <class M>
-__device__ __forceinline__ void count_near_group(int b, const Geom& g, const Coef& c, typename M::pos_t* __restrict__ pos,
-                                                 const SuperGrid& G, const SuperCaps& cp, const GroupAux& aux,
+__device__ __forceinline__ void count_near_group(int b, int n, const Geom& g, const Coef& c,
+                                                 typename M::pos_t* __restrict__ pos, const SuperGrid& G,
+                                                 const SuperCaps& cp, const GroupAux& aux,
                                                  const int* __restrict__ nnb, typename M::real* __restrict__ ds_out,
                                                  typename M::real2* __restrict__ sA, const CountOut& out,
                                                  int* __restrict__ ulist, Status* st, unsigned char* smem)
@@ -1275,14 +1306,15 @@ __device__ __forceinline__ void count_near_group(int b, const Geom& g, const Coe
     __syncthreads();  // the previous group is done with the shared positions
     const int p0 = __ldg(G.cell_start + OWN_CELLS * b);
     const int n_own = __ldg(G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
+    const int total = min(__ldg(aux.meta + b).x, cp.smax);
     if (!out.n_out)
-        stage_by_table(aux.stage_idx + (size_t)b * cp.smax, __ldg(aux.meta + b).x,
+        stage_by_table(aux.stage_idx + (size_t)b * cp.smax, __ldg(aux.meta + b).x, cp.smax, n, &st->bad_index,
                        [&](int m, int jj) { spos[m] = pos[jj]; });
     __syncthreads();
     for (int j = threadIdx.x; j < n_own; j += SC_TPB) {
         NearOwn<M> o;
         load_near_own<M>(p0 + j, pos, aux, nnb, o);
-        count_near_particle<M>(p0 + j, o, spos, g, c, pos, aux, ds_out, sA, out, ulist, st);
+        count_near_particle<M>(p0 + j, o, spos, total, g, c, pos, aux, ds_out, sA, out, ulist, st);
     }
 }
 
@@ -1324,7 +1356,8 @@ __device__ __forceinline__ GroupRange group_range(int b, const SuperGrid& G, con
 // is counted, and the staging copies (cp.async) overlap the loads of the own
 // particles' close entries.
 template <class M>
-__global__ void __launch_bounds__(SC_TPB) k_count_near(int ngroups, Geom g, Coef c, typename M::pos_t* __restrict__ pos,
+__global__ void __launch_bounds__(SC_TPB) k_count_near(int ngroups, int n, Geom g, Coef c,
+                                                       typename M::pos_t* __restrict__ pos,
                                                        SuperGrid G, SuperCaps cp, GroupAux aux,
                                                        const int* __restrict__ nnb, typename M::real* __restrict__ ds_out,
                                                        typename M::real2* __restrict__ sA, CountOut out,
@@ -1337,7 +1370,7 @@ __global__ void __launch_bounds__(SC_TPB) k_count_near(int ngroups, Geom g, Coef
     if (out.n_out) {
         // FP64 counts wanted: no particle is settled here, nothing is staged
         for (int b = blockIdx.x; b < ngroups; b += gridDim.x)
-            count_near_group<M>(b, g, c, pos, G, cp, aux, nnb, ds_out, sA, out, ulist, st, smem);
+            count_near_group<M>(b, n, g, c, pos, G, cp, aux, nnb, ds_out, sA, out, ulist, st, smem);
         return;
     }
     pos_t* spos = (pos_t*)smem;
@@ -1348,9 +1381,14 @@ __global__ void __launch_bounds__(SC_TPB) k_count_near(int ngroups, Geom g, Coef
     GroupRange cur = group_range(b, G, aux);
     GroupRange nxt{0, 0, 0};
     if (b + (int)gridDim.x < ngroups) nxt = group_range(b + gridDim.x, G, aux);
+    int* bad = &st->bad_index;
     int jj[NEAR_B];
     {
         const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
+        if (cur.total > cp.smax) {
+            *bad = BAD_STAGING_SIZE;
+            cur.total = cp.smax;
+        }
 #pragma unroll
         for (int u = 0; u < NEAR_B; ++u) jj[u] = t + u * SC_TPB < cur.total ? __ldg(sidx + t + u * SC_TPB) : -1;
     }
@@ -1359,13 +1397,15 @@ __global__ void __launch_bounds__(SC_TPB) k_count_near(int ngroups, Geom g, Coef
         // this group's staging: asynchronous copies, then the rest (if any) synchronously
 #pragma unroll
         for (int u = 0; u < NEAR_B; ++u)
-            if (jj[u] >= 0)
+            if (t + u * SC_TPB < cur.total) {
+                const int j = checked_sorted(jj[u], n, bad);
 #pragma unroll
                 for (int k = 0; k < CHUNKS; ++k)
                     cp_async16(reinterpret_cast<int4*>(spos + t + u * SC_TPB) + k,
-                               reinterpret_cast<const int4*>(pos + jj[u]) + k);
+                               reinterpret_cast<const int4*>(pos + j) + k);
+            }
         const int* sidx = aux.stage_idx + (size_t)b * cp.smax;
-        for (int m = t + NEAR_B * SC_TPB; m < cur.total; m += SC_TPB) spos[m] = pos[__ldg(sidx + m)];
+        for (int m = t + NEAR_B * SC_TPB; m < cur.total; m += SC_TPB) spos[m] = pos[checked_sorted(__ldg(sidx + m), n, bad)];
         // the first own particle of this thread
         NearOwn<M> o;
         const bool own0 = t < cur.n_own;
@@ -1379,12 +1419,16 @@ __global__ void __launch_bounds__(SC_TPB) k_count_near(int ngroups, Geom g, Coef
             for (int u = 0; u < NEAR_B; ++u) jj[u] = t + u * SC_TPB < nxt.total ? __ldg(sn + t + u * SC_TPB) : -1;
             if (bn + (int)gridDim.x < ngroups) nn2 = group_range(bn + gridDim.x, G, aux);
         }
+        if (nxt.total > cp.smax) {
+            *bad = BAD_STAGING_SIZE;
+            nxt.total = cp.smax;
+        }
         cp_async_wait_all();
         __syncthreads();
-        if (own0) count_near_particle<M>(cur.p0 + t, o, spos, g, c, pos, aux, ds_out, sA, out, ulist, st);
+        if (own0) count_near_particle<M>(cur.p0 + t, o, spos, cur.total, g, c, pos, aux, ds_out, sA, out, ulist, st);
         for (int j = t + SC_TPB; j < cur.n_own; j += SC_TPB) {
             load_near_own<M>(cur.p0 + j, pos, aux, nnb, o);
-            count_near_particle<M>(cur.p0 + j, o, spos, g, c, pos, aux, ds_out, sA, out, ulist, st);
+            count_near_particle<M>(cur.p0 + j, o, spos, cur.total, g, c, pos, aux, ds_out, sA, out, ulist, st);
         }
         cur = nxt;
         nxt = nn2;
@@ -1477,17 +1521,22 @@ __host__ __device__ inline DenseLayout dense_layout(const SuperCaps& cp, size_t 
 }
 
 
-// Lists the own particles of group b that pick(j) selects (j from 0); the
-// whole block calls it.  Returns their number.
+// Lists the own particles of group b that pick(j) selects (j from 0), at
+// most cap of them (the list's capacity; more is an internal error recorded
+// in bad); the whole block calls it.  Returns their number.
 template <int NT, class Pick>
-__device__ __forceinline__ int list_own(int n_own, int* plist, int* s_n, Pick&& pick)
+__device__ __forceinline__ int list_own(int n_own, int* plist, int* s_n, int cap, int* bad, Pick&& pick)
 {
     if (threadIdx.x == 0) *s_n = 0;
     __syncthreads();
     for (int j = threadIdx.x; j < n_own; j += NT)
-        if (pick(j)) plist[atomicAdd(s_n, 1)] = j;
+        if (pick(j)) {
+            const int k = atomicAdd(s_n, 1);
+            if (k < cap) plist[k] = j;
+            else *bad = BAD_STAGING_SIZE;
+        }
     __syncthreads();
-    return *s_n;
+    return min(*s_n, cap);
 }
 
 // Runs body(u, sub, tpp) for the listed particles of a dense walk: slot u of
@@ -1604,6 +1653,14 @@ __device__ __forceinline__ int resid_of(const RowArgs<M>& A, int j)
     return __ldg(A.resid + j);
 }
 
+// Sorted index of row entry m of a particle of the group whose staged-index
+// table is sidx (sparse walks), both indices checked.
+template <class M>
+__device__ __forceinline__ int table_index(const RowArgs<M>& A, const int* sidx, int m)
+{
+    return checked_sorted(__ldg(sidx + checked_staged(m, A.cp.smax, &A.st->bad_index)), A.n, &A.st->bad_index);
+}
+
 // Sparse count: list entry k of the particles k_count_near could not settle
 // (one warp, one lane per row entry).
 template <class M>
@@ -1618,8 +1675,9 @@ __device__ __forceinline__ void count_rows_item(const RowArgs<M>& A, int k)
     real s, ds;
     double n_val;
     count_row<M>(A.pos[p], resid_of(A, p), [&](auto&& v) { walk_lanes(row, len, v); }, 32,
-                 [&](int m) { return A.pos[__ldg(sidx + m)]; }, [&](int m) { return resid_of(A, __ldg(sidx + m)); },
-                 A.c, A.g, A.out.n_out != nullptr, s, ds, n_val);
+                 [&](int m) { return A.pos[table_index(A, sidx, m)]; },
+                 [&](int m) { return resid_of(A, table_index(A, sidx, m)); }, A.c, A.g, A.out.n_out != nullptr, s, ds,
+                 n_val);
     if ((threadIdx.x & 31) == 0) count_row_out<M>(p, s, ds, n_val, A.pos, A.ds, A.sA, A.id, A.out, A.wpart, A.st);
 }
 
@@ -1637,14 +1695,16 @@ __device__ __forceinline__ void count_rows_group(const RowArgs<M>& A, int b, int
     __syncthreads();  // the previous group is done with the shared arrays
     const int p0 = __ldg(A.G.cell_start + OWN_CELLS * b);
     const int n_own = __ldg(A.G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
-    const int nl = list_own<NT>(n_own, plist, s_n, [&](int j) { return isnan(A.ds[p0 + j]); });
+    const int nl = list_own<NT>(n_own, plist, s_n, A.cp.omax, &A.st->bad_index,
+                                [&](int j) { return isnan(A.ds[p0 + j]); });
     if (nl == 0) return;
     // the count reads no s_j, so the spare word of a staged position holds its residuals
-    stage_by_table<NT>(A.aux.stage_idx + (size_t)b * A.cp.smax, __ldg(A.aux.meta + b).x, [&](int m, int jj) {
-        pos_t pj = A.pos[jj];
-        if constexpr (!M::fp64) pj.w = resid_of(A, jj);
-        spos[m] = pj;
-    });
+    stage_by_table<NT>(A.aux.stage_idx + (size_t)b * A.cp.smax, __ldg(A.aux.meta + b).x, A.cp.smax, A.n,
+                       &A.st->bad_index, [&](int m, int jj) {
+                           pos_t pj = A.pos[jj];
+                           if constexpr (!M::fp64) pj.w = resid_of(A, jj);
+                           spos[m] = pj;
+                       });
     __syncthreads();
     dense_rounds<NT>(nl, tmax, [&](int u, int sub, int tpp) {
         const bool act = u < nl;
@@ -1654,7 +1714,8 @@ __device__ __forceinline__ void count_rows_group(const RowArgs<M>& A, int b, int
         real s, ds;
         double n_val;
         count_row<M>(A.pos[p], act ? resid_of(A, p) : 0, [&](auto&& v) { walk_chunks(row, len, sub, tpp, v); }, tpp,
-                     [&](int m) { return spos[m]; }, [&](int m) { return (int)spos[m].w; }, A.c, A.g,
+                     [&](int m) { return spos[checked_staged(m, A.cp.smax, &A.st->bad_index)]; },
+                     [&](int m) { return (int)spos[checked_staged(m, A.cp.smax, &A.st->bad_index)].w; }, A.c, A.g,
                      A.out.n_out != nullptr, s, ds, n_val);
         if (act && sub == 0) count_row_out<M>(p, s, ds, n_val, A.pos, A.ds, A.sA, A.id, A.out, A.wpart, A.st);
     });
@@ -1725,7 +1786,7 @@ __device__ __forceinline__ void chain_item(const RowArgs<M>& A, int k)
     const uint16_t* row = A.nbr + (size_t)p * A.cp.cap;
     const int len = row_len(__ldg(A.nnb + p));
     const real acc = chain_row<M>(A.pos[p], [&](auto&& v) { walk_lanes(row, len, v); }, 32, [&](int m) {
-        const int jj = __ldg(sidx + m);
+        const int jj = table_index(A, sidx, m);
         // the force of jj needs A_i: if it was tagged whole, it now goes on the general list
         if constexpr (!M::fp64) {
             if (atomicExch(reinterpret_cast<float*>(static_cast<float4*>(A.aux.fcore) + jj) + 3, 0.0f) != 0.0f)
@@ -1749,10 +1810,11 @@ __device__ __forceinline__ void chain_group(const RowArgs<M>& A, int b, int tmax
     __syncthreads();  // the previous group is done with the shared arrays
     const int p0 = __ldg(A.G.cell_start + OWN_CELLS * b);
     const int n_own = __ldg(A.G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
-    const int nl = list_own<NT>(n_own, plist, s_n, [&](int j) { return A.ds[p0 + j] != (real)0; });
+    const int nl = list_own<NT>(n_own, plist, s_n, A.cp.omax, &A.st->bad_index,
+                                [&](int j) { return A.ds[p0 + j] != (real)0; });
     if (nl == 0) return;
-    stage_by_table<NT>(A.aux.stage_idx + (size_t)b * A.cp.smax, __ldg(A.aux.meta + b).x,
-                       [&](int m, int jj) { spos[m] = A.pos[jj]; });
+    stage_by_table<NT>(A.aux.stage_idx + (size_t)b * A.cp.smax, __ldg(A.aux.meta + b).x, A.cp.smax, A.n,
+                       &A.st->bad_index, [&](int m, int jj) { spos[m] = A.pos[jj]; });
     __syncthreads();
     dense_rounds<NT>(nl, tmax, [&](int u, int sub, int tpp) {
         const bool act = u < nl;
@@ -1760,7 +1822,8 @@ __device__ __forceinline__ void chain_group(const RowArgs<M>& A, int b, int tmax
         const uint16_t* row = A.nbr + (size_t)p * A.cp.cap;
         const int len = act ? row_len(__ldg(A.nnb + p)) : 0;
         const real acc = chain_row<M>(A.pos[p], [&](auto&& v) { walk_chunks(row, len, sub, tpp, v); }, tpp,
-                                      [&](int m) { return spos[m]; }, A.c, A.g);
+                                      [&](int m) { return spos[checked_staged(m, A.cp.smax, &A.st->bad_index)]; },
+                                      A.c, A.g);
         if (act && sub == 0) A.sA[p].y = A.ds[p] * acc;
     });
 }
@@ -1847,7 +1910,7 @@ __device__ __forceinline__ void force_item(const RowArgs<M>& A, int k)
     real f[3];
     force_row<M>(pi, get_s(pi), useA ? A.sA[p].y : (real)0, [&](auto&& v) { walk_lanes(row, len, v); }, 32,
                  [&](int m, real& Aj) {
-                     const int jj = __ldg(sidx + m);
+                     const int jj = table_index(A, sidx, m);
                      Aj = useA ? A.sA[jj].y : (real)0;
                      return A.pos[jj];
                  },
@@ -1874,16 +1937,19 @@ __device__ __forceinline__ void force_group(const RowArgs<M>& A, int b, int tmax
     const int n_own = __ldg(A.G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
     int nl;
     if (all) {
-        for (int j = threadIdx.x; j < n_own; j += NT) plist[j] = j;
-        nl = n_own;
+        nl = min(n_own, A.cp.omax);
+        if (n_own > A.cp.omax && threadIdx.x == 0) A.st->bad_index = BAD_STAGING_SIZE;
+        for (int j = threadIdx.x; j < nl; j += NT) plist[j] = j;
     } else {
-        nl = list_own<NT>(n_own, plist, s_n, [&](int j) { return !tagged_whole<M>(A.aux.fcore, p0 + j); });
+        nl = list_own<NT>(n_own, plist, s_n, A.cp.omax, &A.st->bad_index,
+                          [&](int j) { return !tagged_whole<M>(A.aux.fcore, p0 + j); });
     }
     if (nl == 0) return;
-    stage_by_table<NT>(A.aux.stage_idx + (size_t)b * A.cp.smax, __ldg(A.aux.meta + b).x, [&](int m, int jj) {
-        spos[m] = A.pos[jj];
-        sAj[m] = useA ? A.sA[jj].y : (real)0;
-    });
+    stage_by_table<NT>(A.aux.stage_idx + (size_t)b * A.cp.smax, __ldg(A.aux.meta + b).x, A.cp.smax, A.n,
+                       &A.st->bad_index, [&](int m, int jj) {
+                           spos[m] = A.pos[jj];
+                           sAj[m] = useA ? A.sA[jj].y : (real)0;
+                       });
     __syncthreads();
     dense_rounds<NT>(nl, tmax, [&](int u, int sub, int tpp) {
         const bool act = u < nl;
@@ -1895,6 +1961,7 @@ __device__ __forceinline__ void force_group(const RowArgs<M>& A, int b, int tmax
         force_row<M>(pi, get_s(pi), useA ? A.sA[p].y : (real)0,
                      [&](auto&& v) { walk_chunks_padded(row, len, sub, tpp, v); }, tpp,
                      [&](int m, real& Aj) {
+                         m = checked_staged(m, A.cp.smax, &A.st->bad_index);
                          Aj = sAj[m];
                          return spos[m];
                      },
