@@ -455,15 +455,37 @@ void dfree(T*& p)
     p = nullptr;
 }
 
+// Host <-> device copies of the system's tables and read-backs, ordered on the
+// system's own stream and complete on return.  A plain cudaMemcpy would run
+// on the legacy default stream, which a non-blocking stream does not wait
+// for: from pageable memory it may return before the data has landed, and
+// kernels enqueued next on the system's stream could read the old contents
+// of the allocation (memory that another system just released).
+int upload(vbc_system* s, void* dst, const void* src, size_t bytes)
+{
+    if (bytes == 0) return VBC_OK;
+    VBC_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s->stream));
+    VBC_CUDA(cudaStreamSynchronize(s->stream));
+    return VBC_OK;
+}
+
+int download(vbc_system* s, void* dst, const void* src, size_t bytes)
+{
+    if (bytes == 0) return VBC_OK;
+    VBC_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s->stream));
+    VBC_CUDA(cudaStreamSynchronize(s->stream));
+    return VBC_OK;
+}
+
 // Builds the window-weight table of the system's parameters and points its
-// coefficients at it (host copy; the stream holds no work that reads it).
+// coefficients at it (a copy ordered after the work already on the stream).
 int upload_window_table(vbc_system* s)
 {
     std::vector<uint4> tab;
     int sh = 0;
     make_window_table(s->coef, s->geom, tab, sh);
     if (!s->wtab) VBC_TRY(dalloc(s->wtab, (size_t)WTAB_PIECES + 2));
-    VBC_CUDA(cudaMemcpy(s->wtab, tab.data(), tab.size() * sizeof(uint4), cudaMemcpyHostToDevice));
+    VBC_TRY(upload(s, s->wtab, tab.data(), tab.size() * sizeof(uint4)));
     s->coef.wtab = s->wtab;
     s->coef.wsh = sh;
     return VBC_OK;
@@ -996,7 +1018,7 @@ int observables_impl(vbc_system* s, vbc_observables* out, int* z_dev)
         VBC_TRY(grow(s));
     }
     unsigned long long h[2 + ZHIST];
-    VBC_CUDA(cudaMemcpy(h, s->obs, sizeof h, cudaMemcpyDeviceToHost));
+    VBC_TRY(download(s, h, s->obs, sizeof h));
     out->mean_z = (double)h[0] / (double)s->n;
     out->p_err = (double)h[1] / (double)s->n;
     for (int k = 0; k < ZHIST; ++k) out->z_hist[k] = (int64_t)h[2 + k];
@@ -1107,10 +1129,15 @@ int graph_error(vbc_system* s, const char* what, cudaError_t e)
 // Kinds of captured iterations: G_OPEN opens step 0 (forces of the initial
 // state, then B A O A), G_RUN, G_PAIR and G_SINGLE close one step and open
 // the next (RUN_ITERS times, twice and once), G_CLOSE closes the last step.
-// Long calls run mostly G_RUN graphs: fewer graph launches, each a boundary
-// the device pays a few microseconds for.
+// Long calls of large systems run mostly G_RUN graphs: fewer graph launches,
+// each a boundary the device pays a few microseconds for.
 enum GraphKind { G_OPEN = 0, G_PAIR = 1, G_SINGLE = 2, G_CLOSE = 3, G_RUN = 4, G_NKIND = 5 };
 constexpr int RUN_ITERS = 8;  // middle iterations of one G_RUN graph
+// Systems from this size on run G_RUN graphs.  Smaller ones keep the two-step
+// graphs: they often share the GPU with other systems on other streams (the
+// serving loop), and there longer graphs measured as less overlap between
+// the streams (aggregate rate of a 16-slot mix 2.6 -> 2.3 x 10^4 steps/s).
+constexpr int64_t RUN_MIN_N = 1 << 18;
 int kind_iters(int k) { return k == G_PAIR ? 2 : (k == G_RUN ? RUN_ITERS : 1); }
 int kind_flips(int k) { return k == G_OPEN || k == G_SINGLE ? 1 : 0; }  // position-buffer flips, mod 2
 int kind_epi(int k) { return k == G_OPEN ? EPI_START : (k == G_CLOSE ? EPI_FINISH : EPI_FINISH_START); }
@@ -1240,7 +1267,7 @@ int run_range(vbc_system* s, const StepArgs& a, int64_t it, int64_t it_end, int6
     while (it < it_end) {
         if (s->use_graphs && !s->prof) {
             const int kind = it == 0 ? G_OPEN
-                             : (it + RUN_ITERS - 1 <= nsteps - 1 && it + RUN_ITERS - 1 < it_end
+                             : (s->n >= RUN_MIN_N && it + RUN_ITERS - 1 <= nsteps - 1 && it + RUN_ITERS - 1 < it_end
                                     ? G_RUN
                                     : (it + 1 <= nsteps - 1 && it + 1 < it_end ? G_PAIR
                                                                                 : (it < nsteps ? G_SINGLE : G_CLOSE)));
@@ -1759,9 +1786,9 @@ int vbc_create_system(const vbc_config* cfg, vbc_system** out)
             if (r % OWN_CELLS == 0) org[r / OWN_CELLS] = x | (y << 10) | (z << 20);
             if (x < g.nc[0] && y < g.nc[1] && z < g.nc[2]) rank[(z * g.nc[1] + y) * g.nc[0] + x] = r;
         }
-        if (cudaMemcpy(s->morton_rank, rank.data(), rank.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(s->sc_org, org.data(), org.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
-            return bail(fail(VBC_ERR_CUDA, "upload of the Morton tables failed"));
+        if ((rc = upload(s, s->morton_rank, rank.data(), rank.size() * sizeof(int))) != VBC_OK ||
+            (rc = upload(s, s->sc_org, org.data(), org.size() * sizeof(int))) != VBC_OK)
+            return bail(rc);
     }
     if (cudaMemsetAsync(s->cell_count, 0, (size_t)s->npad * sizeof(int), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->st, 0, sizeof(Status), s->stream) != cudaSuccess ||
@@ -1866,12 +1893,12 @@ int vbc_create_typed_system(const vbc_config* cfg, const vbc_types* ty, vbc_syst
     std::vector<int> mask((size_t)T * T), type((size_t)n);
     for (int k = 0; k < T * T; ++k) mask[(size_t)k] = ty->count_mask[k];
     for (int64_t i = 0; i < n; ++i) type[(size_t)i] = ty->type[i];
-    if (cudaMemcpy(s->t_pc, pc.data(), pc.size() * sizeof(Coef), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(s->t_mask, mask.data(), mask.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(s->t_type, type.data(), type.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(s->t_bptr, bptr.data(), bptr.size() * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(s->t_bto, bto.data(), bto.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
-        return bail(fail(VBC_ERR_CUDA, "upload of the type tables failed"));
+    if ((rc2 = upload(s, s->t_pc, pc.data(), pc.size() * sizeof(Coef))) != VBC_OK ||
+        (rc2 = upload(s, s->t_mask, mask.data(), mask.size() * sizeof(int))) != VBC_OK ||
+        (rc2 = upload(s, s->t_type, type.data(), type.size() * sizeof(int))) != VBC_OK ||
+        (rc2 = upload(s, s->t_bptr, bptr.data(), bptr.size() * sizeof(long long))) != VBC_OK ||
+        (rc2 = upload(s, s->t_bto, bto.data(), bto.size() * sizeof(int))) != VBC_OK)
+        return bail(rc2);
     s->tdev = TypedDev{s->t_pc, s->t_mask, T, s->t_type, s->t_tsort, s->t_inv, s->t_bptr, s->t_bto, ty->k_bond,
                        ty->r0_bond};
     s->typed = true;
@@ -2100,7 +2127,7 @@ int vbc_get_stats(vbc_system* s, vbc_stats* out)
     out->nlist_mean = (double)s->st_host->nnb_sum / (double)s->n;
     out->pairs_within_rc = s->st_host->pairs;
     long long w = 0;
-    VBC_CUDA(cudaMemcpy(&w, s->win, sizeof(long long), cudaMemcpyDeviceToHost));
+    VBC_TRY(download(s, &w, s->win, sizeof(long long)));
     out->in_window = w;
     out->unsaturated = s->st_host->nu;
     out->stage_cap = s->smax;

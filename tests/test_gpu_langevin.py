@@ -182,8 +182,9 @@ def test_kernel_launch_accounting():
         s.profile(False)
         # graphs: the previous call left the forces of the current state in place, so
         # iteration 0 is the iteration counter and the update alone; iterations 1..8 run
-        # as one eight-step graph of 48 kernels, 9 and 10 as one-iteration graphs of 6,
-        # plus 7 kernels for every rebuild the graphs' conditionals executed
+        # as four two-step graphs of 12 kernels (a system this small takes no eight-step
+        # graphs), 9 and 10 as one-iteration graphs of 6, plus 7 kernels for every
+        # rebuild the graphs' conditionals executed
         before = s.kernel_launches()
         s.step(10, 0.005, 1.0, 1.0)
         d = s.kernel_launches() - before
@@ -206,6 +207,27 @@ def test_graph_and_direct_launches_agree_bitwise(prec):
             outs.append(s.get_state())
             st = s.stats()
     assert st.rebuilds - r0 >= 3
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_eight_step_graphs_agree_with_direct_launches():
+    """Large systems run their middle iterations as eight-step graphs; 300 000
+    particles (the throughput workload's rho = 0.5, E_a = 8, valency 2) over 40
+    steps, rebuilds included, end bitwise where plain launches end."""
+    n = 300_000
+    pos, L = inputs.uniform_positions(n, 0.5, seed=12)
+    vel = inputs.maxwell_velocities(n, 1.0, seed=13)
+    p = Params(E_a=8.0, f=2.0)
+    outs = []
+    for direct in (False, True):
+        with vbc.System(pos, L, _vp(p), vel=vel, seed=6) as s:
+            if direct:
+                s.profile(True, 1 << 14)
+            r0 = s.stats().rebuilds
+            s.step(40, 0.005, 1.0, 1.0)
+            outs.append(s.get_state())
+            st = s.stats()
+    assert st.rebuilds - r0 >= 1
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
 
 
