@@ -197,6 +197,11 @@ struct vbc_system {
     size_t smem_energy() const { return pass_layout(caps(), pos_bytes(), sizeof(double2)).total; }
     size_t smem_store() const { return al16((size_t)(omax + 1) * 4); }
     size_t smem_rows(size_t extra) const { return dense_layout(caps(), pos_bytes(), extra).total; }
+    // the count walk: chunk-parallel in the FP32 split, the row walk's layout in FP64
+    size_t smem_count() const
+    {
+        return prec == VBC_FP64 ? smem_rows(0) : count_layout(caps(), pos_bytes()).total;
+    }
     size_t smem_near() const { return (size_t)smax * pos_bytes(); }
 };
 
@@ -333,6 +338,7 @@ int make_coef(const vbc_pair_params& p, const Geom& g, Coef& c)
     }
     c.fd_int = (long long)fi;
     c.fd_frac_fix = frac;
+    c.fd_fix = c.fd_int * 2147483648LL + frac;
     c.sat_full = c.fd_int + 1 + (frac > 0 ? 1 : 0);
     return VBC_OK;
 }
@@ -571,7 +577,7 @@ int configure_smem(vbc_system* s)
     VBC_TRY(set_smem(k_store_nlist, s->smem_store()));
     VBC_TRY(for_row_tpb(s->row_tpb, [&](auto nt) -> int {
         constexpr int NT = decltype(nt)::value;
-        VBC_TRY(set_smem(k_count_rows<M, NT>, s->smem_rows(0)));
+        VBC_TRY(set_smem(k_count_rows<M, NT>, s->smem_count()));
         VBC_TRY(set_smem(k_chain<M, NT>, s->smem_rows(0)));
         return set_smem(k_force_rows<M, NT>, s->smem_rows(s->real_bytes()));
     }));
@@ -584,7 +590,7 @@ int configure_smem(vbc_system* s)
     };
     for_row_tpb(s->row_tpb, [&](auto nt) -> int {
         constexpr int NT = decltype(nt)::value;
-        resident((const void*)k_count_rows<M, NT>, NT, s->smem_rows(0));
+        resident((const void*)k_count_rows<M, NT>, NT, s->smem_count());
         resident((const void*)k_chain<M, NT>, NT, s->smem_rows(0));
         resident((const void*)k_force_rows<M, NT>, NT, s->smem_rows(s->real_bytes()));
         return VBC_OK;
@@ -721,7 +727,7 @@ int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window)
             s->ulist, s->st);
         for_row_tpb(s->row_tpb, [&](auto nt) -> int {
             constexpr int NT = decltype(nt)::value;
-            k_count_rows<M, NT><<<s->row_grid, NT, s->smem_rows(0), s->stream>>>(row_args<M>(s, out), s->nsc,
+            k_count_rows<M, NT><<<s->row_grid, NT, s->smem_count(), s->stream>>>(row_args<M>(s, out), s->nsc,
                                                                                  s->tpp_max);
             return VBC_OK;
         });
@@ -1554,7 +1560,7 @@ int fused_iterations(vbc_batch* b, int64_t nsteps, const std::vector<StepArgs>& 
             offs[(size_t)q * (K + 1) + k + 1] = (int)tot[q];
         }
         const size_t nl = (!M::fp64 && s->rel_lists) ? s->smem_nlist_rel() : s->smem_nlist();
-        smem_phase = std::max({smem_phase, nl, s->smem_near(), s->smem_rows(s->real_bytes())});
+        smem_phase = std::max({smem_phase, nl, s->smem_near(), s->smem_rows(s->real_bytes()), s->smem_count()});
     }
     smem_phase = al16(smem_phase);
     const size_t smem = smem_phase + (size_t)(BK_NKIND + 1) * (K + 1) * sizeof(int);

@@ -63,6 +63,8 @@ struct Coef {
     int wsh;                          // log2 of the r^2 extent of one piece (fixed-point units)
     long long fd_int;                 // floor(f - delta)
     long long fd_frac_fix;            // (f - delta - fd_int) * 2^31, rounded
+    long long fd_fix;                 // f - delta in 2^-31 fixed point: fd_int * 2^31 + fd_frac_fix (host-formed;
+                                      // a count's threshold difference is n 2^31 + q - fd_fix)
     long long sat_full;               // ceil(f - delta + 1): this many neighbours inside r_l give s = s' = 0
 };
 

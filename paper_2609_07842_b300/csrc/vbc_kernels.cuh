@@ -24,7 +24,10 @@
 // atomics, so results do not depend on scheduling.
 #pragma once
 
+#include <climits>
 #include <type_traits>
+
+#include <cooperative_groups.h>
 
 #include "vbc_device.cuh"
 
@@ -37,6 +40,19 @@ constexpr int SCAN_TPB = 256;
 constexpr int MAX_CELL = 512;     // a denser cell means the system has collapsed
 
 enum Epilogue { EPI_FORCE = 0, EPI_START = 1, EPI_FINISH = 2, EPI_FINISH_START = 3 };
+
+// Appends p to a work list whose length is *counter, with one atomic per set
+// of lanes that append together (the counter is one word that every block
+// of the grid appends to).  The order of a list is not part of any result:
+// every listed particle is processed on its own.
+__device__ __forceinline__ void list_append(int* __restrict__ list, int* counter, int p)
+{
+    const cooperative_groups::coalesced_group g = cooperative_groups::coalesced_threads();
+    int base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(counter, (int)g.size());
+    base = g.shfl(base, 0);
+    list[base + (int)g.thread_rank()] = p;
+}
 
 // ================================================================ rebuild: sort by cell
 // The rebuild steps run only when a rebuild is due and nothing is halted.
@@ -1520,6 +1536,22 @@ __host__ __device__ inline DenseLayout dense_layout(const SuperCaps& cp, size_t 
     return l;
 }
 
+// Shared memory of the chunk-parallel dense count (FP32 split): staged
+// positions, the list of own particles, each listed row's first chunk
+// (exclusive scan, one extra slot for the total) and its fixed-point sum.
+struct CountLayout {
+    size_t plist, cstart, acc, total;
+};
+__host__ __device__ inline CountLayout count_layout(const SuperCaps& cp, size_t pos_bytes)
+{
+    CountLayout l{};
+    l.plist = al16((size_t)cp.smax * pos_bytes);
+    l.cstart = l.plist + al16((size_t)cp.omax * 4);
+    l.acc = l.cstart + al16((size_t)(cp.omax + 1) * 4);
+    l.total = l.acc + (size_t)cp.omax * 8;
+    return l;
+}
+
 
 // Lists the own particles of group b that pick(j) selects (j from 0), at
 // most cap of them (the list's capacity; more is an internal error recorded
@@ -1591,7 +1623,7 @@ __device__ __forceinline__ void count_row(const typename M::pos_t& pi, int ri, W
         });
         full = group_sum(full, width);
         q = group_sum(q, width);
-        const long long Tf = ((long long)full - c.fd_int) * 2147483648LL + (long long)q - c.fd_frac_fix;
+        const long long Tf = ((long long)full << 31) + (long long)q - c.fd_fix;
         switch_from_fix(Tf, s, ds);
         n_val = 0.0;
         if (want_n) n_val = (double)full + (double)q * 4.656612873077393e-10;
@@ -1613,7 +1645,7 @@ __device__ __forceinline__ void count_row_out(int p, typename M::real s, typenam
     if (out.n_out) out.n_out[id[p]] = n_val;
     if (ds != (real)0) {
         // the chain-rule pass visits the window particles listed here
-        wpart[atomicAdd(&st->nwin, 1)] = p;
+        list_append(wpart, &st->nwin, p);
         if (out.in_window) atomicAdd((unsigned long long*)out.in_window, 1ull);
     }
 }
@@ -1684,11 +1716,18 @@ __device__ __forceinline__ void count_rows_item(const RowArgs<M>& A, int k)
 // Dense count of cell group b: the own particles that k_count_near marked
 // (s'_i = NaN), the group's neighbourhood staged in smem (whole block;
 // starts with a block barrier).
+template <int NT>
+__device__ void count_rows_group_chunks(const RowArgs<ModeF32>& A, int b, unsigned char* smem, int* s_n);
+
 template <class M, int NT>
 __device__ __forceinline__ void count_rows_group(const RowArgs<M>& A, int b, int tmax, unsigned char* smem, int* s_n)
 {
     using pos_t = typename M::pos_t;
     using real = typename M::real;
+    if constexpr (!M::fp64) {
+        count_rows_group_chunks<NT>(A, b, smem, s_n);
+        return;
+    }
     const DenseLayout ly = dense_layout(A.cp, sizeof(pos_t), 0);
     pos_t* spos = (pos_t*)smem;
     int* plist = (int*)(smem + ly.plist);
@@ -1719,6 +1758,163 @@ __device__ __forceinline__ void count_rows_group(const RowArgs<M>& A, int b, int
                      A.out.n_out != nullptr, s, ds, n_val);
         if (act && sub == 0) count_row_out<M>(p, s, ds, n_val, A.pos, A.ds, A.sA, A.id, A.out, A.wpart, A.st);
     });
+}
+
+// s_i, s'_i (and n_i) of sorted particle p from its fixed-point count acc
+// = n_i 2^31 (the FP32 split's integer count and window weights, exact),
+// then the outputs of a counted row.
+__device__ __forceinline__ void finish_count_fix(const RowArgs<ModeF32>& A, int p, unsigned long long acc)
+{
+    const long long Tf = (long long)acc - A.c.fd_fix;
+    float s, ds;
+    switch_from_fix(Tf, s, ds);
+    const double n_val = A.out.n_out ? (double)acc * 4.656612873077393e-10 : 0.0;  // exact: acc < 2^53
+    count_row_out<ModeF32>(p, s, ds, n_val, A.pos, A.ds, A.sA, A.id, A.out, A.wpart, A.st);
+}
+
+// Dense count of cell group b, FP32 split, parallel over the 4-entry chunks
+// of the listed rows rather than over rows: the rows of the group's
+// unsettled own particles are laid end to end in chunk order (an exclusive
+// scan of their chunk counts), each warp takes a contiguous range of chunks
+// and each lane one chunk of it, so that every lane has work and a warp
+// reads consecutive chunks of the same rows.  A lane finds its row from the
+// row starts that fall inside its warp's 32-chunk window (a ballot over the
+// next 32 rows, which is enough because every listed row is nonempty; empty
+// rows are settled while listing).  The lanes of one row combine their
+// fixed-point sums by a segmented shuffle reduction, and the first lane of
+// each row segment adds it to the row's shared accumulator.  The sums are
+// integers, so the result does not depend on how the rows are split: it is
+// the row walk's, bit for bit.
+template <int NT>
+__device__ void count_rows_group_chunks(const RowArgs<ModeF32>& A, int b, unsigned char* smem, int* s_n)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr unsigned long long ONE = 2147483648ull;  // one neighbour inside r_l, in units of 2^-31
+    const CountLayout ly = count_layout(A.cp, sizeof(int4));
+    int4* spos = (int4*)smem;
+    int* plist = (int*)(smem + ly.plist);
+    int* cstart = (int*)(smem + ly.cstart);
+    unsigned long long* acc = (unsigned long long*)(smem + ly.acc);
+    __shared__ int s_wsum[NT / 32];
+    int* bad = &A.st->bad_index;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    __syncthreads();  // the previous group is done with the shared arrays
+    const int p0 = __ldg(A.G.cell_start + OWN_CELLS * b);
+    const int n_own = __ldg(A.G.cell_start + OWN_CELLS * b + OWN_CELLS) - p0;
+    // the unsettled own particles (s'_i = NaN from k_count_near); an empty row is settled here
+    const int nl = list_own<NT>(n_own, plist, s_n, A.cp.omax, bad, [&](int j) {
+        if (!isnan(A.ds[p0 + j])) return false;
+        if (row_len(__ldg(A.nnb + p0 + j)) > 0) return true;
+        finish_count_fix(A, p0 + j, 0ull);
+        return false;
+    });
+    if (nl == 0) return;
+    // the count reads no s_j, so the spare word of a staged position holds its residuals
+    stage_by_table<NT>(A.aux.stage_idx + (size_t)b * A.cp.smax, __ldg(A.aux.meta + b).x, A.cp.smax, A.n, bad,
+                       [&](int m, int jj) {
+                           int4 pj = A.pos[jj];
+                           pj.w = resid_of(A, jj);
+                           spos[m] = pj;
+                       });
+    // chunk counts -> first chunk of each row: each thread scans a contiguous run of rows
+    const int per = (nl + NT - 1) / NT;
+    const int u0 = min(nl, t * per), u1 = min(nl, u0 + per);
+    int loc = 0;
+    for (int u = u0; u < u1; ++u) {
+        const int nch = (row_len(__ldg(A.nnb + p0 + plist[u])) + 3) >> 2;
+        cstart[u] = nch;
+        loc += nch;
+    }
+    int inc = loc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_wsum[warp] = inc;
+    __syncthreads();
+    int run = inc - loc, total = 0;
+    for (int w = 0; w < NT / 32; ++w) {
+        const int v = s_wsum[w];
+        if (w < warp) run += v;
+        total += v;
+    }
+    for (int u = u0; u < u1; ++u) {
+        const int nch = cstart[u];
+        cstart[u] = run;
+        run += nch;
+        acc[u] = 0ull;
+    }
+    if (t == 0) cstart[nl] = total;
+    __syncthreads();
+    // this warp's chunks [c_begin, c_end); r_prev is the row holding chunk c0 - 1 (-1 before the first)
+    const int cw = (total + NT / 32 - 1) / (NT / 32);
+    const int c_begin = min(total, warp * cw), c_end = min(total, c_begin + cw);
+    int r_prev;
+    {
+        int lo = 0, hi = nl;  // rows whose first chunk is below c_begin
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (cstart[mid] < c_begin) lo = mid + 1;
+            else hi = mid;
+        }
+        r_prev = lo - 1;
+    }
+    const Coef& c = A.c;
+    for (int c0 = c_begin; c0 < c_end; c0 += 32) {
+        // rows starting inside [c0, c0 + 32): r_prev + 1 .. r_prev + k (rows are nonempty)
+        const int cand = r_prev + 1 + lane;
+        const int cs = cand < nl ? cstart[cand] : INT_MAX;
+        const bool starts = (unsigned)(cs - c0) < 32u;
+        const unsigned bits = __reduce_or_sync(FULL, starts ? 1u << (cs - c0) : 0u);
+        int u = r_prev + __popc(bits & (FULL >> (31 - lane)));  // row of chunk c0 + lane
+        r_prev += __popc(__ballot_sync(FULL, starts));
+        const int ch = c0 + lane;
+        unsigned long long a = 0ull;
+        if (ch >= c_end) {
+            u = -1;
+        } else if ((unsigned)u >= (unsigned)nl) {
+            *bad = BAD_STAGING_SIZE;
+            u = -1;
+        } else {
+            const int p = p0 + plist[u];
+            const int4 pi = A.pos[p];
+            const int ri = resid_of(A, p);
+            const int len = row_len(__ldg(A.nnb + p));
+            const int e0 = 4 * (ch - cstart[u]);
+            int h[4];
+            unpack4(__ldg(reinterpret_cast<const uint2*>(A.nbr + (size_t)p * A.cp.cap + e0)), h);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (e0 + k >= len) break;
+                const int4 pj = spos[checked_staged(h[k], A.cp.smax, bad)];
+                const unsigned long long r2 = r2_fix(pi, pj);
+                if (r2 < c.rh2_fix) {
+                    if (r2 <= c.rl2_fix) {
+                        a += ONE;
+                    } else {
+                        // omega has zero slope at both ends of the window, so a pair that the
+                        // finer separation moves across r_l or r_h changes n_i by O(dr^2)
+                        const unsigned long long rf = r2_fine(pi, ri, pj, pj.w, r2);
+                        if (rf <= c.rl2_fix) a += ONE;
+                        else if (rf < c.rh2_fix) a += window_weight_tab(rf - c.rl2_fix, c.wtab, c.wsh);
+                    }
+                }
+            }
+        }
+        // segmented sum over the lanes of each row (a row's lanes are contiguous): after the
+        // step of width o a lane holds the sum over [lane, lane + 2o) within its row
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_down_sync(FULL, a, o);
+            const int uy = __shfl_down_sync(FULL, u, o);
+            if (lane + o < 32 && uy == u) a += y;
+        }
+        const int up = __shfl_up_sync(FULL, u, 1);
+        if (u >= 0 && (lane == 0 || up != u)) atomicAdd(&acc[u], a);
+    }
+    __syncthreads();
+    for (int u = t; u < nl; u += NT) finish_count_fix(A, p0 + plist[u], acc[u]);
 }
 
 // Dense mode of the count walk: more than n / DENSE_DIV unsettled particles.
@@ -1790,7 +1986,7 @@ __device__ __forceinline__ void chain_item(const RowArgs<M>& A, int k)
         // the force of jj needs A_i: if it was tagged whole, it now goes on the general list
         if constexpr (!M::fp64) {
             if (atomicExch(reinterpret_cast<float*>(static_cast<float4*>(A.aux.fcore) + jj) + 3, 0.0f) != 0.0f)
-                A.aux.glist[atomicAdd(&A.st->ngen, 1)] = jj;
+                list_append(A.aux.glist, &A.st->ngen, jj);
         }
         return A.pos[jj];
     }, A.c, A.g);

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(NA_TPB) k_na_count(int n, NAConst k, const int
         }
     }
     if (i >= n) return;
-    const long long T = ((long long)full - k.c.fd_int) * 2147483648LL + (long long)q - k.c.fd_frac_fix;
+    const long long T = ((long long)full << 31) + (long long)q - k.c.fd_fix;
     float s = 1.0f, d = 0.0f;
     if (T >= 2147483648LL) {
         s = 0.0f;
@@ -294,6 +294,7 @@ int vbc_compute_forces_noalloc(int32_t n, const double* box, const double* pos, 
         }
         c.fd_int = (long long)fi;
         c.fd_frac_fix = frac;
+        c.fd_fix = c.fd_int * 2147483648LL + frac;
     }
 
     cudaStream_t st = (cudaStream_t)stream;

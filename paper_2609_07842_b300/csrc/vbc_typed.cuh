@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(SC_TPB) k_tcount32(int n, Geom g, int4* __rest
         full = group_sum(full, 32);
         q = group_sum(q, 32);
         const Coef& own = t.pc[ti * t.T + ti];
-        const long long T = ((long long)full - own.fd_int) * 2147483648LL + (long long)q - own.fd_frac_fix;
+        const long long T = ((long long)full << 31) + (long long)q - own.fd_fix;
         float sv, dsv;
         switch_from_fix(T, sv, dsv);
         if ((threadIdx.x & 31) == 0) {
