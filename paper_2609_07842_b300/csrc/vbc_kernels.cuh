@@ -1040,33 +1040,38 @@ __device__ __forceinline__ void pair_f32(const int4& pi, float si, float Ai, con
     const bool well = r2i > c.rr2_fix && r2i < c.ra2_fix && si * sj != 0.0f;
     const bool chain = r2i > c.rl2_fix && r2i < c.rh2_fix && Ai + Aj != 0.0f;
     if (!(core || well || chain)) return;
-    const float dx = (float)ix * g.s32, dy = (float)iy * g.s32, dz = (float)iz * g.s32;
+    // Every product and sum is spelt out (round-to-nearest intrinsics), so that no kernel
+    // that inlines this contracts a multiply and an add differently from another: the
+    // single-system walks and the batched launch give the same bits.
+    const float dx = __fmul_rn((float)ix, g.s32), dy = __fmul_rn((float)iy, g.s32), dz = __fmul_rn((float)iz, g.s32);
     // the exact r^2 as one float (0.5 ulp): every term below starts from it, except the
     // well's r - r_m, which takes the exact integer difference (near the well's centre the
     // force is most sensitive to it)
     const float R = u64_to_float(r2i);
-    const float r2 = R * g.s32sq;
+    const float r2 = __fmul_rn(R, g.s32sq);
     float gr = 0.0f;  // g / r
-    if (core) gr = c.Er4f * (r2 * c.rr2invf - 1.0f);
+    if (core) gr = __fmul_rn(c.Er4f, __fmaf_rn(r2, c.rr2invf, -1.0f));
     if (well || chain) {
         float rinv = rsqrtf(r2);
-        rinv = rinv * __fmaf_rn(-0.5f * r2 * rinv, rinv, 1.5f);  // one Newton step
-        const float r = r2 * rinv;
+        rinv = __fmul_rn(rinv, __fmaf_rn(__fmul_rn(__fmul_rn(-0.5f, r2), rinv), rinv, 1.5f));  // one Newton step
+        const float r = __fmul_rn(r2, rinv);
         float gt = 0.0f;  // g from the well and the counts
         if (well) {
-            const float u = __fdividef(s64_to_float((long long)r2i - (long long)c.rm2_fix) * c.s2hinv, r + c.rmf);
-            gt = si * sj * c.Ea4hf * u * (1.0f - u * u);
+            const float u = __fdividef(__fmul_rn(s64_to_float((long long)r2i - (long long)c.rm2_fix), c.s2hinv),
+                                       __fadd_rn(r, c.rmf));
+            gt = __fmul_rn(__fmul_rn(__fmul_rn(__fmul_rn(si, sj), c.Ea4hf), u), __fmaf_rn(-u, u, 1.0f));
         }
         if (chain) {
             // (r - r_l) / w from r^2 - r_l^2 in fixed-point units (R and r_l^2 each within 0.5 ulp)
-            const float tt = __fdividef((R - c.rl2_fixf) * c.s2winv, r + c.rlf);
-            gt -= (Ai + Aj) * 4.0f * tt * (1.0f - tt * tt) * c.winvf;
+            const float tt = __fdividef(__fmul_rn(__fsub_rn(R, c.rl2_fixf), c.s2winv), __fadd_rn(r, c.rlf));
+            const float h = __fmul_rn(__fmul_rn(__fmul_rn(__fadd_rn(Ai, Aj), 4.0f), tt), __fmaf_rn(-tt, tt, 1.0f));
+            gt = __fmaf_rn(-h, c.winvf, gt);
         }
-        gr += gt * rinv;
+        gr = __fmaf_rn(gt, rinv, gr);
     }
-    fx -= gr * dx;
-    fy -= gr * dy;
-    fz -= gr * dz;
+    fx = __fmaf_rn(-gr, dx, fx);
+    fy = __fmaf_rn(-gr, dy, fy);
+    fz = __fmaf_rn(-gr, dz, fz);
 }
 
 // All terms of one pair in the FP64 mode.
@@ -1958,11 +1963,13 @@ __device__ __forceinline__ typename M::real chain_row(const typename M::pos_t& p
         } else {
             const unsigned long long r2i = r2_fix(pi, pj);
             if (r2i > c.rr2_fix && r2i < c.ra2_fix) {
-                const float r2 = u64_to_float(r2i) * g.s32sq;
-                const float r = r2 * rsqrtf(r2);
-                const float uu = __fdividef(s64_to_float((long long)r2i - (long long)c.rm2_fix) * c.s2hinv, r + c.rmf);
-                const float q = 1.0f - uu * uu;
-                acc += get_s(pj) * (-c.Eaf * q * q);
+                // spelt-out products and sums (no contraction that could differ between kernels)
+                const float r2 = __fmul_rn(u64_to_float(r2i), g.s32sq);
+                const float r = __fmul_rn(r2, rsqrtf(r2));
+                const float uu = __fdividef(__fmul_rn(s64_to_float((long long)r2i - (long long)c.rm2_fix), c.s2hinv),
+                                            __fadd_rn(r, c.rmf));
+                const float q = __fmaf_rn(-uu, uu, 1.0f);
+                acc = __fmaf_rn(get_s(pj), __fmul_rn(__fmul_rn(-c.Eaf, q), q), acc);
             }
         }
     });
