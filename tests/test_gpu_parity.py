@@ -88,6 +88,16 @@ def test_paper_shape_low_density_clusters(prec, f):
 
 
 @pytest.mark.parametrize("prec", [F32, F64])
+def test_dense_rows_longer_than_a_chunk_window(prec):
+    """Tight clusters of 160: rows of about 140 list entries, 83% of them longer than 128
+    (the dense count's 32 chunks of 4), so that rows continue across lane windows and across
+    the warps of a group; counts, switch and forces against the oracle."""
+    pos, L = inputs.clustered_positions(3200, 0.05, seed=21, cluster_size=160, spread=1.2)
+    p = with_quantile_valency(pos, L, Params(E_a=5.0), 0.5, mode=1)
+    compare(pos, L, p, prec, mode=1)
+
+
+@pytest.mark.parametrize("prec", [F32, F64])
 def test_optimised_vbc(prec):
     """VBC(1.29, 1.50, 0.30) of Sec. 4."""
     pos, L = inputs.clustered_positions(1500, 0.1, seed=4, cluster_size=4, spread=0.8)
