@@ -712,19 +712,29 @@ RowArgs<M> row_args(const vbc_system* s, const CountOut& out, int cur = -1)
 }
 
 template <class M>
-int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window)
+int enqueue_count_near(vbc_system* s, double* n_out, bool want_window, int gated)
 {
-    if (s->typed) return enqueue_typed_count_chain(s, n_out, want_window);
     using pos_t = typename M::pos_t;
     using real = typename M::real;
     using real2 = typename M::real2;
     pos_t* pos = (pos_t*)s->pos[s->cur];  // the count writes s_i into the positions' spare word
     CountOut out{n_out, want_window ? s->win : nullptr};
+    k_count_near<M><<<s->near_grid, SC_TPB, s->smem_near(), s->stream>>>(
+        s->nsc, (int)s->n, s->geom, s->coef, pos, s->grid(), s->caps(), s->aux(), s->nnb, (real*)s->ds, (real2*)s->sA, out,
+        s->ulist, s->st, gated);
+    return check_launch(s);
+}
+
+// The counts and the chain-rule terms; with_near = false leaves out the close
+// count, which a captured iteration launches itself (beside its conditional).
+template <class M>
+int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window, bool with_near = true)
+{
+    if (s->typed) return enqueue_typed_count_chain(s, n_out, want_window);
+    CountOut out{n_out, want_window ? s->win : nullptr};
     {
         Timed t(s, VBC_K_COUNT);
-        k_count_near<M><<<s->near_grid, SC_TPB, s->smem_near(), s->stream>>>(
-            s->nsc, (int)s->n, s->geom, s->coef, pos, s->grid(), s->caps(), s->aux(), s->nnb, (real*)s->ds, (real2*)s->sA, out,
-            s->ulist, s->st);
+        if (with_near) VBC_TRY(enqueue_count_near<M>(s, n_out, want_window, 0));
         for_row_tpb(s->row_tpb, [&](auto nt) -> int {
             constexpr int NT = decltype(nt)::value;
             k_count_rows<M, NT><<<s->row_grid, NT, s->smem_count(), s->stream>>>(row_args<M>(s, out), s->nsc,
@@ -740,7 +750,7 @@ int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window)
             return VBC_OK;
         });
     }
-    return check_launch(s, 3);
+    return check_launch(s, 2);
 }
 
 template <class M, int EPI>
@@ -1188,21 +1198,46 @@ int capture_iters(vbc_system* s, int c, const StepArgs& a, int kind, cudaGraph_t
         cp.conditional.type = cudaGraphCondTypeIf;
         cp.conditional.size = 1;
         cudaGraphNode_t cn = nullptr;
-        e = cudaGraphAddNode(&cn, cg, deps, ed, nd, &cp);
+        if (nd != 1) { rc = graph_error(s, "capture of the gate", cudaErrorInvalidValue); break; }
+        cudaGraphNode_t gate = deps[0];  // copied: later capture calls may move the dependency list
+        e = cudaGraphAddNode(&cn, cg, &gate, ed, 1, &cp);
         if (e != cudaSuccess) { rc = graph_error(s, "cudaGraphAddNode(conditional)", e); break; }
-        e = cudaStreamUpdateCaptureDependencies(s->cap_stream, &cn, nullptr, 1, cudaStreamSetCaptureDependencies);
-        if (e != cudaSuccess) { rc = graph_error(s, "cudaStreamUpdateCaptureDependencies", e); break; }
-        // the rebuild kernels go into the conditional's body graph
+        // The rebuild kernels go into the conditional's body graph.  For a single-type system
+        // the close count goes in after them, and a second close count depends on the gate
+        // alone and runs beside the conditional (it returns when the gate decided to
+        // rebuild): on the steps without a rebuild the conditional's own latency then hides
+        // behind that count instead of delaying it.  The row walks wait for both.
+        const bool near_beside = !s->typed;
         e = cudaStreamBeginCaptureToGraph(s->body_stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                           cudaStreamCaptureModeRelaxed);
         if (e != cudaSuccess) { rc = graph_error(s, "capture of the rebuild body", e); break; }
         s->stream = s->body_stream;
         rc = enqueue_rebuild<M>(s);
+        if (rc == VBC_OK && near_beside) rc = enqueue_count_near<M>(s, nullptr, false, 0);
         s->stream = s->cap_stream;
         cudaGraph_t body = nullptr;
         e = cudaStreamEndCapture(s->body_stream, &body);
         if (rc == VBC_OK && e != cudaSuccess) rc = graph_error(s, "end of the rebuild body capture", e);
-        if (rc == VBC_OK) rc = enqueue_count_chain<M>(s, nullptr, false);
+        if (rc != VBC_OK) break;
+        cudaGraphNode_t join[2] = {cn, nullptr};
+        int njoin = 1;
+        if (near_beside) {
+            e = cudaStreamUpdateCaptureDependencies(s->cap_stream, &gate, nullptr, 1, cudaStreamSetCaptureDependencies);
+            if (e != cudaSuccess) { rc = graph_error(s, "cudaStreamUpdateCaptureDependencies", e); break; }
+            rc = enqueue_count_near<M>(s, nullptr, false, 1);
+            if (rc != VBC_OK) break;
+            const cudaGraphNode_t* nd2 = nullptr;
+            size_t nn2 = 0;
+            e = cudaStreamGetCaptureInfo(s->cap_stream, &cst, nullptr, &cg, &nd2, nullptr, &nn2);
+            if (e != cudaSuccess || nn2 != 1) {
+                rc = graph_error(s, "capture of the close count", e != cudaSuccess ? e : cudaErrorInvalidValue);
+                break;
+            }
+            join[njoin++] = nd2[0];
+        }
+        e = cudaStreamUpdateCaptureDependencies(s->cap_stream, join, nullptr, njoin, cudaStreamSetCaptureDependencies);
+        if (e != cudaSuccess) { rc = graph_error(s, "cudaStreamUpdateCaptureDependencies", e); break; }
+        rc = enqueue_count_chain<M>(s, nullptr, false, !near_beside);
         if (rc == VBC_OK) rc = enqueue_force_epi<M>(s, a, kind_epi(kind));
     }
     cudaGraph_t out = nullptr;
@@ -2185,7 +2220,8 @@ int vbc_profile_read(vbc_system* s, int which, double* total_ms, int64_t* launch
 int64_t vbc_kernel_launches(vbc_system* s)
 {
     if (!s || check_sys(s) != VBC_OK || read_status(s) != VBC_OK) return -1;
-    return s->launches + (REBUILD_KERNELS + (s->typed ? 1 : 0)) * s->st_host->graph_rebuild_runs;  // typed: k_tmaps
+    // a graph's rebuild body: the rebuild kernels and k_tmaps (typed) or the close count (single type)
+    return s->launches + (REBUILD_KERNELS + 1) * s->st_host->graph_rebuild_runs;
 }
 
 int vbc_batch_create(vbc_system* const* systems, int32_t count, vbc_batch** out)

@@ -1382,8 +1382,10 @@ __global__ void __launch_bounds__(SC_TPB) k_count_near(int ngroups, int n, Geom 
                                                        SuperGrid G, SuperCaps cp, GroupAux aux,
                                                        const int* __restrict__ nnb, typename M::real* __restrict__ ds_out,
                                                        typename M::real2* __restrict__ sA, CountOut out,
-                                                       int* __restrict__ ulist, Status* st)
+                                                       int* __restrict__ ulist, Status* st, int gated)
 {
+    // the launch beside a graph iteration's conditional: the rebuild body counts instead
+    if (gated && st->gate_due) return;
     using pos_t = typename M::pos_t;
     if (blockIdx.x == 0 && threadIdx.x == 0) st->rebuild = 0;
     if (halted(st)) return;
@@ -1482,11 +1484,26 @@ __device__ __forceinline__ int dense_tpp(int nl, int tmax)
     return t;
 }
 
-// Sparse walk: entry e on lane e mod 32.
-template <class Visit>
-__device__ __forceinline__ void walk_lanes(const uint16_t* __restrict__ row, int len, Visit&& visit)
+// The sparse walk of particle p's row with the lane's first entry loaded up
+// front, beside the row length and the group index rather than after them
+// (one dependent round trip less per listed particle).  Every lane below cap
+// reads inside the particle's row slot; entries at or past len are not used.
+struct LaneRow {
+    const uint16_t* row;
+    int h0;
+};
+__device__ __forceinline__ LaneRow lane_row(const uint16_t* __restrict__ nbr, int p, int cap)
 {
-    for (int e = threadIdx.x & 31; e < len; e += 32) visit((int)__ldg(row + e));
+    const uint16_t* row = nbr + (size_t)p * cap;
+    const int lane = threadIdx.x & 31;
+    return LaneRow{row, lane < cap ? (int)__ldg(row + lane) : 0};
+}
+template <class Visit>
+__device__ __forceinline__ void walk_lanes_from(const LaneRow& r, int len, Visit&& visit)
+{
+    const int lane = threadIdx.x & 31;
+    if (lane < len) visit(r.h0);
+    for (int e = lane + 32; e < len; e += 32) visit((int)__ldg(r.row + e));
 }
 
 // Dense walk: 4-entry chunk k on thread k mod tpp of the lane group.  Rows
@@ -1705,13 +1722,13 @@ __device__ __forceinline__ void count_rows_item(const RowArgs<M>& A, int k)
 {
     using real = typename M::real;
     const int p = A.ulist[k];
+    const LaneRow lr = lane_row(A.nbr, p, A.cp.cap);
     const int b = __ldg(A.aux.grp + p);
     const int* sidx = A.aux.stage_idx + (size_t)b * A.cp.smax;
-    const uint16_t* row = A.nbr + (size_t)p * A.cp.cap;
     const int len = row_len(__ldg(A.nnb + p));
     real s, ds;
     double n_val;
-    count_row<M>(A.pos[p], resid_of(A, p), [&](auto&& v) { walk_lanes(row, len, v); }, 32,
+    count_row<M>(A.pos[p], resid_of(A, p), [&](auto&& v) { walk_lanes_from(lr, len, v); }, 32,
                  [&](int m) { return A.pos[table_index(A, sidx, m)]; },
                  [&](int m) { return resid_of(A, table_index(A, sidx, m)); }, A.c, A.g, A.out.n_out != nullptr, s, ds,
                  n_val);
@@ -1984,11 +2001,11 @@ __device__ __forceinline__ void chain_item(const RowArgs<M>& A, int k)
 {
     using real = typename M::real;
     const int p = A.wpart[k];
+    const LaneRow lr = lane_row(A.nbr, p, A.cp.cap);
     const int b = __ldg(A.aux.grp + p);
     const int* sidx = A.aux.stage_idx + (size_t)b * A.cp.smax;
-    const uint16_t* row = A.nbr + (size_t)p * A.cp.cap;
     const int len = row_len(__ldg(A.nnb + p));
-    const real acc = chain_row<M>(A.pos[p], [&](auto&& v) { walk_lanes(row, len, v); }, 32, [&](int m) {
+    const real acc = chain_row<M>(A.pos[p], [&](auto&& v) { walk_lanes_from(lr, len, v); }, 32, [&](int m) {
         const int jj = table_index(A, sidx, m);
         // the force of jj needs A_i: if it was tagged whole, it now goes on the general list
         if constexpr (!M::fp64) {
@@ -2105,13 +2122,13 @@ __device__ __forceinline__ void force_item(const RowArgs<M>& A, int k)
     using real = typename M::real;
     const bool useA = A.st->nwin > 0;  // A_j != 0 only for window particles
     const int p = A.aux.glist[k];
+    const LaneRow lr = lane_row(A.nbr, p, A.cp.cap);
     const int b = __ldg(A.aux.grp + p);
     const int* sidx = A.aux.stage_idx + (size_t)b * A.cp.smax;
-    const uint16_t* row = A.nbr + (size_t)p * A.cp.cap;
     const int len = row_len(__ldg(A.nnb + p));
     const pos_t pi = A.pos[p];
     real f[3];
-    force_row<M>(pi, get_s(pi), useA ? A.sA[p].y : (real)0, [&](auto&& v) { walk_lanes(row, len, v); }, 32,
+    force_row<M>(pi, get_s(pi), useA ? A.sA[p].y : (real)0, [&](auto&& v) { walk_lanes_from(lr, len, v); }, 32,
                  [&](int m, real& Aj) {
                      const int jj = table_index(A, sidx, m);
                      Aj = useA ? A.sA[jj].y : (real)0;
@@ -2672,6 +2689,7 @@ __global__ void k_gate(Status* st, cudaGraphConditionalHandle h, int in_graph)
     if (in_graph) {
         const bool due = st->rebuild && !halted(st);
         if (due) st->graph_rebuild_runs += 1;
+        st->gate_due = due ? 1 : 0;
         cudaGraphSetConditional(h, due ? 1u : 0u);
     }
 }
