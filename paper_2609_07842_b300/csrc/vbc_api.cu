@@ -1155,6 +1155,11 @@ constexpr int RUN_ITERS = 8;  // middle iterations of one G_RUN graph
 // the streams (aggregate rate of a 16-slot mix 2.6 -> 2.3 x 10^4 steps/s).
 constexpr int64_t RUN_MIN_N = 1 << 18;
 int kind_iters(int k) { return k == G_PAIR ? 2 : (k == G_RUN ? RUN_ITERS : 1); }
+// The same size threshold decides whether a captured iteration runs its close count beside the
+// conditional (hiding the conditional's latency) or after it: with many small systems side by side
+// (the serving loop, the batch graph) the extra branch measured slower (served stream 3.0 -> 2.4,
+// batch graph 6.3 -> 5.2 x 10^4 steps/s).
+bool near_beside(const vbc_system* s) { return !s->typed && s->n >= RUN_MIN_N; }
 int kind_flips(int k) { return k == G_OPEN || k == G_SINGLE ? 1 : 0; }  // position-buffer flips, mod 2
 int kind_epi(int k) { return k == G_OPEN ? EPI_START : (k == G_CLOSE ? EPI_FINISH : EPI_FINISH_START); }
 int iter_launches(const vbc_system* s) { return s->typed ? 5 : 6; }    // gate, count(s), chain, force, step
@@ -1207,13 +1212,13 @@ int capture_iters(vbc_system* s, int c, const StepArgs& a, int kind, cudaGraph_t
         // alone and runs beside the conditional (it returns when the gate decided to
         // rebuild): on the steps without a rebuild the conditional's own latency then hides
         // behind that count instead of delaying it.  The row walks wait for both.
-        const bool near_beside = !s->typed;
+        const bool beside = near_beside(s);
         e = cudaStreamBeginCaptureToGraph(s->body_stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                           cudaStreamCaptureModeRelaxed);
         if (e != cudaSuccess) { rc = graph_error(s, "capture of the rebuild body", e); break; }
         s->stream = s->body_stream;
         rc = enqueue_rebuild<M>(s);
-        if (rc == VBC_OK && near_beside) rc = enqueue_count_near<M>(s, nullptr, false, 0);
+        if (rc == VBC_OK && beside) rc = enqueue_count_near<M>(s, nullptr, false, 0);
         s->stream = s->cap_stream;
         cudaGraph_t body = nullptr;
         e = cudaStreamEndCapture(s->body_stream, &body);
@@ -1221,7 +1226,7 @@ int capture_iters(vbc_system* s, int c, const StepArgs& a, int kind, cudaGraph_t
         if (rc != VBC_OK) break;
         cudaGraphNode_t join[2] = {cn, nullptr};
         int njoin = 1;
-        if (near_beside) {
+        if (beside) {
             e = cudaStreamUpdateCaptureDependencies(s->cap_stream, &gate, nullptr, 1, cudaStreamSetCaptureDependencies);
             if (e != cudaSuccess) { rc = graph_error(s, "cudaStreamUpdateCaptureDependencies", e); break; }
             rc = enqueue_count_near<M>(s, nullptr, false, 1);
@@ -1237,7 +1242,7 @@ int capture_iters(vbc_system* s, int c, const StepArgs& a, int kind, cudaGraph_t
         }
         e = cudaStreamUpdateCaptureDependencies(s->cap_stream, join, nullptr, njoin, cudaStreamSetCaptureDependencies);
         if (e != cudaSuccess) { rc = graph_error(s, "cudaStreamUpdateCaptureDependencies", e); break; }
-        rc = enqueue_count_chain<M>(s, nullptr, false, !near_beside);
+        rc = enqueue_count_chain<M>(s, nullptr, false, !beside);
         if (rc == VBC_OK) rc = enqueue_force_epi<M>(s, a, kind_epi(kind));
     }
     cudaGraph_t out = nullptr;
@@ -2220,8 +2225,9 @@ int vbc_profile_read(vbc_system* s, int which, double* total_ms, int64_t* launch
 int64_t vbc_kernel_launches(vbc_system* s)
 {
     if (!s || check_sys(s) != VBC_OK || read_status(s) != VBC_OK) return -1;
-    // a graph's rebuild body: the rebuild kernels and k_tmaps (typed) or the close count (single type)
-    return s->launches + (REBUILD_KERNELS + 1) * s->st_host->graph_rebuild_runs;
+    // a graph's rebuild body: the rebuild kernels, and k_tmaps (typed) or the close count (beside)
+    const int body = REBUILD_KERNELS + (s->typed || near_beside(s) ? 1 : 0);
+    return s->launches + body * s->st_host->graph_rebuild_runs;
 }
 
 int vbc_batch_create(vbc_system* const* systems, int32_t count, vbc_batch** out)
