@@ -1110,7 +1110,7 @@ int thermo_impl(vbc_system* s, vbc_thermo* out)
 template <class M>
 int direct_iteration(vbc_system* s, const StepArgs& a, int64_t it, int64_t nsteps)
 {
-    k_gate<<<1, 1, 0, s->stream>>>(s->st, 0, 0);
+    k_gate<<<1, 1, 0, s->stream>>>(s->st, 0, 0, 1);
     VBC_TRY(check_launch(s));
     VBC_TRY(enqueue_rebuild<M>(s));
     VBC_TRY(enqueue_count_chain<M>(s, nullptr, false));
@@ -1188,31 +1188,54 @@ int capture_iters(vbc_system* s, int c, const StepArgs& a, int kind, cudaGraph_t
     int rc = VBC_OK;
     cudaError_t e = cudaStreamBeginCaptureToGraph(s->cap_stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) rc = graph_error(s, "cudaStreamBeginCaptureToGraph", e);
+    // For a single-type system of 2^18 particles or more the close count is captured twice: in
+    // the conditional's body after the rebuild kernels, and beside the gate and the conditional,
+    // on the previous update alone (it returns when the iteration rebuilds).  On the steps
+    // without a rebuild neither the gate nor the conditional's own latency then delays the
+    // count.  The row walks wait for both the conditional and that count.
+    const bool beside = near_beside(s);
     for (int k = 0; k < niter && rc == VBC_OK; ++k) {
-        k_gate<<<1, 1, 0, s->cap_stream>>>(s->st, h[k], 1);
         cudaStreamCaptureStatus cst;
         cudaGraph_t cg = nullptr;
         const cudaGraphNode_t* deps = nullptr;
         const cudaGraphEdgeData* ed = nullptr;
         size_t nd = 0;
+        cudaGraphNode_t near_node = nullptr;
+        if (beside) {
+            // the nodes this iteration starts after: the previous update, or none
+            e = cudaStreamGetCaptureInfo(s->cap_stream, &cst, nullptr, &cg, &deps, nullptr, &nd);
+            if (e != cudaSuccess || nd > 1) {
+                rc = graph_error(s, "capture of an iteration", e != cudaSuccess ? e : cudaErrorInvalidValue);
+                break;
+            }
+            cudaGraphNode_t prev = nd ? deps[0] : nullptr;  // copied: later calls may move the list
+            const size_t nprev = nd;
+            rc = enqueue_count_near<M>(s, nullptr, false, 1);
+            if (rc != VBC_OK) break;
+            e = cudaStreamGetCaptureInfo(s->cap_stream, &cst, nullptr, &cg, &deps, nullptr, &nd);
+            if (e != cudaSuccess || nd != 1) {
+                rc = graph_error(s, "capture of the close count", e != cudaSuccess ? e : cudaErrorInvalidValue);
+                break;
+            }
+            near_node = deps[0];
+            e = cudaStreamUpdateCaptureDependencies(s->cap_stream, nprev ? &prev : nullptr, nullptr, nprev,
+                                                    cudaStreamSetCaptureDependencies);
+            if (e != cudaSuccess) { rc = graph_error(s, "cudaStreamUpdateCaptureDependencies", e); break; }
+        }
+        k_gate<<<1, 1, 0, s->cap_stream>>>(s->st, h[k], 1, beside ? 0 : 1);
         e = cudaStreamGetCaptureInfo(s->cap_stream, &cst, nullptr, &cg, &deps, &ed, &nd);
         if (e != cudaSuccess) { rc = graph_error(s, "cudaStreamGetCaptureInfo", e); break; }
+        if (nd != 1) { rc = graph_error(s, "capture of the gate", cudaErrorInvalidValue); break; }
         cudaGraphNodeParams cp{};
         cp.type = cudaGraphNodeTypeConditional;
         cp.conditional.handle = h[k];
         cp.conditional.type = cudaGraphCondTypeIf;
         cp.conditional.size = 1;
         cudaGraphNode_t cn = nullptr;
-        if (nd != 1) { rc = graph_error(s, "capture of the gate", cudaErrorInvalidValue); break; }
-        cudaGraphNode_t gate = deps[0];  // copied: later capture calls may move the dependency list
+        const cudaGraphNode_t gate = deps[0];
         e = cudaGraphAddNode(&cn, cg, &gate, ed, 1, &cp);
         if (e != cudaSuccess) { rc = graph_error(s, "cudaGraphAddNode(conditional)", e); break; }
-        // The rebuild kernels go into the conditional's body graph.  For a single-type system
-        // the close count goes in after them, and a second close count depends on the gate
-        // alone and runs beside the conditional (it returns when the gate decided to
-        // rebuild): on the steps without a rebuild the conditional's own latency then hides
-        // behind that count instead of delaying it.  The row walks wait for both.
-        const bool beside = near_beside(s);
+        // the rebuild kernels (and, beside, the close count) go into the conditional's body graph
         e = cudaStreamBeginCaptureToGraph(s->body_stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                           cudaStreamCaptureModeRelaxed);
         if (e != cudaSuccess) { rc = graph_error(s, "capture of the rebuild body", e); break; }
@@ -1224,23 +1247,9 @@ int capture_iters(vbc_system* s, int c, const StepArgs& a, int kind, cudaGraph_t
         e = cudaStreamEndCapture(s->body_stream, &body);
         if (rc == VBC_OK && e != cudaSuccess) rc = graph_error(s, "end of the rebuild body capture", e);
         if (rc != VBC_OK) break;
-        cudaGraphNode_t join[2] = {cn, nullptr};
-        int njoin = 1;
-        if (beside) {
-            e = cudaStreamUpdateCaptureDependencies(s->cap_stream, &gate, nullptr, 1, cudaStreamSetCaptureDependencies);
-            if (e != cudaSuccess) { rc = graph_error(s, "cudaStreamUpdateCaptureDependencies", e); break; }
-            rc = enqueue_count_near<M>(s, nullptr, false, 1);
-            if (rc != VBC_OK) break;
-            const cudaGraphNode_t* nd2 = nullptr;
-            size_t nn2 = 0;
-            e = cudaStreamGetCaptureInfo(s->cap_stream, &cst, nullptr, &cg, &nd2, nullptr, &nn2);
-            if (e != cudaSuccess || nn2 != 1) {
-                rc = graph_error(s, "capture of the close count", e != cudaSuccess ? e : cudaErrorInvalidValue);
-                break;
-            }
-            join[njoin++] = nd2[0];
-        }
-        e = cudaStreamUpdateCaptureDependencies(s->cap_stream, join, nullptr, njoin, cudaStreamSetCaptureDependencies);
+        cudaGraphNode_t join[2] = {cn, near_node};
+        e = cudaStreamUpdateCaptureDependencies(s->cap_stream, join, nullptr, beside ? 2 : 1,
+                                                cudaStreamSetCaptureDependencies);
         if (e != cudaSuccess) { rc = graph_error(s, "cudaStreamUpdateCaptureDependencies", e); break; }
         rc = enqueue_count_chain<M>(s, nullptr, false, !beside);
         if (rc == VBC_OK) rc = enqueue_force_epi<M>(s, a, kind_epi(kind));

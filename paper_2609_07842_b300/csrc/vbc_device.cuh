@@ -95,8 +95,6 @@ struct Status {
     int bad_index;      // nonzero: a device-side index check failed (BadIndex; an internal error)
     int bad_input;      // 1: a loaded position or velocity was non-finite or beyond the fixed-point range (k_load_state)
     int aborted;        // 1: a batched iteration gave up waiting and left the state incomplete (host)
-    int gate_due;       // 1: the current graph iteration rebuilds (k_gate): the count beside the
-                        // conditional returns, the one in its rebuild body counts
 };
 
 // Work stops (until the host intervenes) once any of these is raised.

@@ -1384,10 +1384,12 @@ __global__ void __launch_bounds__(SC_TPB) k_count_near(int ngroups, int n, Geom 
                                                        typename M::real2* __restrict__ sA, CountOut out,
                                                        int* __restrict__ ulist, Status* st, int gated)
 {
-    // the launch beside a graph iteration's conditional: the rebuild body counts instead
-    if (gated && st->gate_due) return;
+    // The launch beside a graph iteration's conditional returns when the iteration rebuilds
+    // (the conditional's body then counts).  It decides from the flags the previous update
+    // left: the rebuild flag is cleared only by k_count_rows, which waits for both counts,
+    // and a halt the rebuild raises meanwhile makes every block return below as well.
+    if (gated && st->rebuild && !halted(st)) return;
     using pos_t = typename M::pos_t;
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->rebuild = 0;
     if (halted(st)) return;
     extern __shared__ __align__(16) unsigned char smem[];
     if (out.n_out) {
@@ -1946,6 +1948,8 @@ __device__ __forceinline__ bool count_rows_dense(const RowArgs<M>& A) { return A
 template <class M, int NT>
 __global__ void __launch_bounds__(NT) k_count_rows(RowArgs<M> A, int ngroups, int tmax)
 {
+    // the list this step's counts used is current: clear the request (after both close counts)
+    if (blockIdx.x == 0 && threadIdx.x == 0) A.st->rebuild = 0;
     if (halted(A.st)) return;
     if (!count_rows_dense(A)) {
         const int nu = A.st->nu;
@@ -2243,6 +2247,15 @@ __global__ void __launch_bounds__(TPB) k_step(int n, Geom g, GroupAux aux, const
                                               const typename M::pos_t* __restrict__ xref, StepArgs a, Status* st)
 {
     if (halted(st)) return;
+    // An update that opens a step empties the work lists of the next iteration (their readers,
+    // the row walks, are done); the last update of a call keeps them for the statistics.
+    if constexpr (EPI == EPI_START || EPI == EPI_FINISH_START) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->nwin = 0;
+            st->nu = 0;
+            st->ngen = 0;
+        }
+    }
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p < n) step_item<M, EPI>(p, n, g, aux, id, pos_next, xref, a, st);
 }
@@ -2680,16 +2693,21 @@ __global__ void __launch_bounds__(SC_TPB) k_store_nlist(Geom g, SuperGrid G, Sup
 // keys the Langevin noise) and, inside a CUDA graph, sets the conditional
 // that runs the rebuild body only when a rebuild is due; clears the list of
 // window particles that the iteration's count fills.
-__global__ void k_gate(Status* st, cudaGraphConditionalHandle h, int in_graph)
+// The gate of a loop iteration: advances the iteration counter and, in a graph,
+// opens the rebuild conditional.  reset clears the work-list counters here; a
+// graph whose close count runs beside the conditional (not after this gate)
+// has them cleared by the previous update (k_step) or by k_set_iter instead.
+__global__ void k_gate(Status* st, cudaGraphConditionalHandle h, int in_graph, int reset)
 {
     st->iter += 1;
-    st->nwin = 0;
-    st->nu = 0;
-    st->ngen = 0;
+    if (reset) {
+        st->nwin = 0;
+        st->nu = 0;
+        st->ngen = 0;
+    }
     if (in_graph) {
         const bool due = st->rebuild && !halted(st);
         if (due) st->graph_rebuild_runs += 1;
-        st->gate_due = due ? 1 : 0;
         cudaGraphSetConditional(h, due ? 1u : 0u);
     }
 }
@@ -2698,6 +2716,9 @@ __global__ void k_set_iter(Status* st, long long iter, long long step_base)
 {
     st->iter = iter;
     st->step_base = step_base;
+    st->nwin = 0;  // the work lists of the first iteration start empty
+    st->nu = 0;
+    st->ngen = 0;
 }
 
 __global__ void k_iota(int n, int* __restrict__ id)

@@ -212,24 +212,30 @@ def test_graph_and_direct_launches_agree_bitwise(prec):
 
 
 def test_eight_step_graphs_agree_with_direct_launches():
-    """Large systems run their middle iterations as eight-step graphs; 300 000
-    particles (the throughput workload's rho = 0.5, E_a = 8, valency 2) over 40
-    steps, rebuilds included, end bitwise where plain launches end."""
+    """Large systems run their middle iterations as eight-step graphs, with the close
+    count beside the rebuild conditional; 300 000 particles (the throughput
+    workload's rho = 0.5, E_a = 8, valency 2) over 40 steps, rebuilds included, end
+    bitwise where plain launches end, and where uneven calls with reads between them
+    end (the work-list counters restart at every call and step)."""
     n = 300_000
     pos, L = inputs.uniform_positions(n, 0.5, seed=12)
     vel = inputs.maxwell_velocities(n, 1.0, seed=13)
     p = Params(E_a=8.0, f=2.0)
     outs = []
-    for direct in (False, True):
+    for mode in ("graphs", "direct", "chunks"):
         with vbc.System(pos, L, _vp(p), vel=vel, seed=6) as s:
-            if direct:
+            if mode == "direct":
                 s.profile(True, 1 << 14)
             r0 = s.stats().rebuilds
-            s.step(40, 0.005, 1.0, 1.0)
+            for c in ((40,) if mode != "chunks" else (7, 1, 13, 19)):
+                s.step(c, 0.005, 1.0, 1.0)
+                st = s.stats()
+                assert 0 < st.unsaturated < n // 16  # the last iteration's count, kept for the statistics
             outs.append(s.get_state())
-            st = s.stats()
-    assert st.rebuilds - r0 >= 1
-    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+        assert st.rebuilds - r0 >= 1
+    for o in outs[1:]:
+        assert o[2] == 40
+        assert np.array_equal(outs[0][0], o[0]) and np.array_equal(outs[0][1], o[1])
 
 
 @pytest.mark.parametrize("prec", [F32, F64])
