@@ -84,3 +84,41 @@ def test_errors_are_codes():
             srv.result(rid)                          # not finished
         assert e.value.code == vbc.VBC_ERR_INVALID_ARG
     # closing stopped the long request after its current chunk
+
+
+def test_systems_created_side_by_side_equal_systems_alone():
+    """Sixteen systems of different sizes created and stepped from sixteen host
+    threads at once, each on its own stream, while others release their memory:
+    every state ends bitwise where the same system created and stepped alone ends.
+    (Each system's tables reach the device in copies ordered on its own stream, so
+    its first kernels never read an allocation's previous contents.)"""
+    import threading
+
+    cases = [(1000 + 2500 * k, 0.5, 1.0 + k % 6, 100 + k) for k in range(16)]
+
+    def run(n, rho, f, seed):
+        pos, L = inputs.uniform_positions(n, rho, seed=seed)
+        with vbc.System(pos, L, vbc.params(E_a=8.0, f=f), seed=seed) as s:
+            s.step(60, 0.005, 1.0, 1.0)
+            return s.get_state()
+
+    alone = [run(*c) for c in cases]
+    mixed = [None] * len(cases)
+    errors = []
+
+    def worker(k):
+        try:
+            for _ in range(2):  # create, step, release twice: later creations reuse released memory
+                mixed[k] = run(*cases[k])
+        except Exception as e:  # reported below, in the test's own thread
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=worker, args=(k,)) for k in range(len(cases))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for a, m in zip(alone, mixed):
+        assert m[2] == a[2] == 60
+        assert np.array_equal(a[0], m[0]) and np.array_equal(a[1], m[1])
