@@ -135,6 +135,8 @@ struct vbc_system {
     int* resid = nullptr;       // [n] packed residual bits of the positions (FP32 mode; counts of window pairs)
     int sms = 148;              // SMs of the device
     int row_grid = 1;           // blocks of the row walks (count rows, chain-rule pass, force rows)
+    bool pdl = false;           // graphs launch the chain, force and update kernels with programmatic
+                                // stream serialization (choose_pdl)
     int near_grid = 1;          // blocks of k_count_near
     int rows_bps = 0, near_bps = 0;  // blocks per SM of those grids, 0 = as many as fit (vbc_autotune)
     int row_tpb = 128;               // threads per block of the row walks: 128, 256 or 512
@@ -711,6 +713,32 @@ RowArgs<M> row_args(const vbc_system* s, const CountOut& out, int cur = -1)
     return A;
 }
 
+// Launches kern; while a graph is being captured for a system with pdl set,
+// with programmatic stream serialization, so that its launch overlaps the end
+// of the preceding kernel (the kernel waits for that kernel's completion
+// itself: wait_for_predecessor).
+template <class... KArgs, class... Args>
+int launch_pdl(vbc_system* s, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, Args&&... args)
+{
+    if (!(s->pdl && s->capturing)) {
+        kern<<<grid, block, smem, s->stream>>>(std::forward<Args>(args)...);
+        return VBC_OK;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s->stream;
+    cudaLaunchAttribute at{};
+    at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+    if (e != cudaSuccess) return fail(VBC_ERR_CUDA, "cudaLaunchKernelEx: %s", cudaGetErrorString(e));
+    return VBC_OK;
+}
+
 template <class M>
 int enqueue_count_near(vbc_system* s, double* n_out, bool want_window, int gated)
 {
@@ -744,11 +772,11 @@ int enqueue_count_chain(vbc_system* s, double* n_out, bool want_window, bool wit
     }
     {
         Timed t(s, VBC_K_CHAIN);
-        for_row_tpb(s->row_tpb, [&](auto nt) -> int {
+        VBC_TRY(for_row_tpb(s->row_tpb, [&](auto nt) -> int {
             constexpr int NT = decltype(nt)::value;
-            k_chain<M, NT><<<s->row_grid, NT, s->smem_rows(0), s->stream>>>(row_args<M>(s, out), s->nsc, s->tpp_max);
-            return VBC_OK;
-        });
+            return launch_pdl(s, k_chain<M, NT>, s->row_grid, NT, s->smem_rows(0), row_args<M>(s, out), (int)s->nsc,
+                              (int)s->tpp_max);
+        }));
     }
     return check_launch(s, 2);
 }
@@ -776,14 +804,13 @@ int enqueue_force(vbc_system* s, const StepArgs& a)
             done = true;
         }
         if (!done)
-            for_row_tpb(s->row_tpb, [&](auto nt) -> int {
+            VBC_TRY(for_row_tpb(s->row_tpb, [&](auto nt) -> int {
                 constexpr int NT = decltype(nt)::value;
-                k_force_rows<M, NT><<<s->row_grid, NT, s->smem_rows(s->real_bytes()), s->stream>>>(
-                    row_args<M>(s, CountOut{nullptr, nullptr}), s->nsc, s->tpp_max);
-                return VBC_OK;
-            });
-        k_step<M, EPI><<<blocks_for(n, TPB), TPB, 0, s->stream>>>(n, s->geom, s->aux(), s->id, pos_next,
-                                                                  (const pos_t*)s->xref, a, s->st);
+                return launch_pdl(s, k_force_rows<M, NT>, s->row_grid, NT, s->smem_rows(s->real_bytes()),
+                                  row_args<M>(s, CountOut{nullptr, nullptr}), (int)s->nsc, (int)s->tpp_max);
+            }));
+        VBC_TRY(launch_pdl(s, k_step<M, EPI>, blocks_for(n, TPB), TPB, 0, n, s->geom, s->aux(), (const int*)s->id,
+                           pos_next, (const pos_t*)s->xref, a, s->st));
     }
     VBC_TRY(check_launch(s, 2));
     if (EPI == EPI_START || EPI == EPI_FINISH_START) s->cur ^= 1;
@@ -1160,6 +1187,28 @@ int kind_iters(int k) { return k == G_PAIR ? 2 : (k == G_RUN ? RUN_ITERS : 1); }
 // (the serving loop, the batch graph) the extra branch measured slower (served stream 3.0 -> 2.4,
 // batch graph 6.3 -> 5.2 x 10^4 steps/s).
 bool near_beside(const vbc_system* s) { return !s->typed && s->n >= RUN_MIN_N; }
+
+// Programmatic stream serialization for the chain, force and update kernels of
+// a large system's graphs, while its row walks run sparse: all three work lists
+// below n / 64 at the end of the last call (on), above n / 32 (off); between,
+// the choice stays.  With the dense walks the early-launched blocks took the
+// resident slots the walks need (valency 8 measured about 10% slower).  A change
+// takes effect when the graphs are next captured; results do not depend on it.
+void choose_pdl(vbc_system* s)
+{
+    bool want = false;
+    if (near_beside(s) && s->st_host) {
+        const long long m = std::max({(long long)s->st_host->nu, (long long)s->st_host->ngen,
+                                      (long long)s->st_host->nwin});
+        want = s->pdl;
+        if (m * 64 < s->n) want = true;
+        else if (m * 32 > s->n) want = false;
+    }
+    if (want != s->pdl) {
+        s->pdl = want;
+        s->layout_version += 1;
+    }
+}
 int kind_flips(int k) { return k == G_OPEN || k == G_SINGLE ? 1 : 0; }  // position-buffer flips, mod 2
 int kind_epi(int k) { return k == G_OPEN ? EPI_START : (k == G_CLOSE ? EPI_FINISH : EPI_FINISH_START); }
 int iter_launches(const vbc_system* s) { return s->typed ? 5 : 6; }    // gate, count(s), chain, force, step
@@ -1412,6 +1461,7 @@ int steps_impl(vbc_system* s, int64_t nsteps, double dt, double kT, double gamma
 {
     VBC_TRY(run_iterations<M>(s, step_args(s, dt, kT, gamma), 0, nsteps));
     s->step += nsteps;
+    choose_pdl(s);
     return VBC_OK;
 }
 

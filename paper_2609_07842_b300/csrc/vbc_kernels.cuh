@@ -41,6 +41,12 @@ constexpr int MAX_CELL = 512;     // a denser cell means the system has collapse
 
 enum Epilogue { EPI_FORCE = 0, EPI_START = 1, EPI_FINISH = 2, EPI_FINISH_START = 3 };
 
+// Waits until the preceding kernel of the stream has completed and its writes
+// are visible.  A kernel launched with programmatic stream serialization may
+// start before then (its launch overlaps the predecessor's last blocks); one
+// launched plainly starts after it anyway, and the wait returns at once.
+__device__ __forceinline__ void wait_for_predecessor() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Appends p to a work list whose length is *counter, with one atomic per set
 // of lanes that append together (the counter is one word that every block
 // of the grid appends to).  The order of a list is not part of any result:
@@ -2058,6 +2064,7 @@ __device__ __forceinline__ bool chain_dense(const RowArgs<M>& A) { return A.st->
 template <class M, int NT>
 __global__ void __launch_bounds__(NT) k_chain(RowArgs<M> A, int ngroups, int tmax)
 {
+    wait_for_predecessor();
     if (halted(A.st)) return;
     if (!chain_dense(A)) {
         const int nw = A.st->nwin;
@@ -2197,6 +2204,7 @@ __device__ __forceinline__ void force_group(const RowArgs<M>& A, int b, int tmax
 template <class M, int NT>
 __global__ void __launch_bounds__(NT) k_force_rows(RowArgs<M> A, int ngroups, int tmax)
 {
+    wait_for_predecessor();
     if (halted(A.st)) return;
     if (!force_dense(A)) {
         const int ng = A.st->ngen;
@@ -2246,6 +2254,7 @@ __global__ void __launch_bounds__(TPB) k_step(int n, Geom g, GroupAux aux, const
                                               typename M::pos_t* __restrict__ pos_next,
                                               const typename M::pos_t* __restrict__ xref, StepArgs a, Status* st)
 {
+    wait_for_predecessor();
     if (halted(st)) return;
     // An update that opens a step empties the work lists of the next iteration (their readers,
     // the row walks, are done); the last update of a call keeps them for the statistics.
