@@ -72,7 +72,8 @@ struct Coef {
 // Each flag has one writer kernel, and no kernel reads a flag that it writes,
 // so every early exit is uniform within a kernel launch.
 struct Status {
-    int rebuild;        // 1: neighbour list must be rebuilt (k_force sets, k_count clears)
+    int rebuild;        // 1: neighbour list must be rebuilt (k_step sets; k_count_rows, after both
+                        // close counts, clears)
     int overflow;       // 1: a list exceeded the capacity at the last build (k_nlist)
     int frozen;         // 1: a non-finite position or velocity was produced (k_force)
     int crowded;        // 1: a cell held more than MAX_CELL particles (k_scan_apply)
